@@ -1,0 +1,143 @@
+/*
+ * abc_gb300.h -- C ABI of the GB300 (sm_103a) library for ABC rejection
+ * sampling of the six-compartment stochastic COVID-19 model of
+ * Kulkarni, Krell, Nabarro, Moritz, "Hardware-accelerated Simulation-based
+ * Inference of Stochastic Epidemiology Models for COVID-19" (2020).
+ *
+ * The method (paper Sec. 2.1, 2.2, 3.1): draw theta from a uniform prior box
+ * (Eq. 1, Eq. 2), simulate the compartments X = [S, I, A, R, D, Ru] (Eq. 3) day
+ * by day with the infection rate g (Eq. 4), the hazards h (Eq. 5) and floored
+ * Gaussian transition counts, compare the simulated (A, R, D) series with the
+ * observed one by Euclidean distance and accept theta when the distance is at
+ * most eps (Eq. 7); all samples are independent (Sec. 3.1).
+ *
+ * Conventions shared by every entry point
+ *  - theta layout: [alpha0, alpha, n, beta, gamma, delta, eta, kappa] (Eq. 1).
+ *  - observed: HOST int32 array [3][T+1], row-major, rows A, R, D. Column 0 is the
+ *    initial condition (A0, R0, D0); columns 1..T are compared with days 1..T.
+ *    Entries must be >= 0 and A0 + R0 + D0 <= N_pop.
+ *  - N_pop: total population P, 1 <= P < 2^31 (compartments are int32).
+ *  - T: simulated days, 1 <= T <= ABC_T_MAX.
+ *  - Random numbers: Philox4x32-10 keyed by seed; sample index i, day-pair k and
+ *    block g form the counter (i_lo, i_hi, k, 4*stream + g); stream < 2^30.
+ *    Results therefore depend only on (seed, stream, i), never on the launch
+ *    shape, so any split of the index range reproduces the unsplit run.
+ *  - mode: ABC_EXACT uses the library's fixed float32 series for log2, exp2,
+ *    sin(pi x), cos(pi x) and IEEE-rounded +, -, *, /, sqrt with no FMA
+ *    contraction (bit-reproducible); ABC_FAST uses the GPU's approximate
+ *    transcendental units and FMA (same random numbers, statistically equivalent).
+ *  - Device pointers are CUDA device memory of the current device; they are owned
+ *    by the caller. cuda_stream is a cudaStream_t (NULL = legacy default stream).
+ *    Every call is stream-ordered on cuda_stream; calls that return host results
+ *    (n_accepted, eps) synchronize that stream before returning.
+ *  - Errors: every call returns an abc_status. On error, abc_last_error() gives a
+ *    thread-local message. No C++ exception crosses this boundary.
+ */
+#ifndef ABC_GB300_H
+#define ABC_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ABC_T_MAX 4096
+#define ABC_STREAM_MAX ((1u << 30) - 1u)
+
+/* Uniform prior box (Sec. 2.1, Eq. 2): theta_j = lo_j + (hi_j - lo_j) u_j.
+ * The paper's box is lo = 0, hi = {1, 100, 2, 1, 1, 1, 1, 2}. Bounds must be
+ * finite with lo_j <= hi_j. */
+typedef struct {
+    float lo[8];
+    float hi[8];
+} abc_prior_box;
+
+typedef enum { ABC_EXACT = 0, ABC_FAST = 1 } abc_mode;
+
+typedef enum {
+    ABC_OK = 0,
+    ABC_ERR_INVALID_ARG = 1, /* an argument is out of range or a pointer is NULL */
+    ABC_ERR_CAPACITY = 2,    /* more accepts than the output capacity */
+    ABC_ERR_CUDA = 3,        /* a CUDA runtime call or a kernel launch failed */
+    ABC_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up */
+    ABC_ERR_NOMEM = 5        /* device memory allocation failed */
+} abc_status;
+
+/* ABC rejection over the sample indices [first_index, first_index + n_samples)
+ * (Sec. 2.2 and Sec. 3.1): for each i, draw theta_i from the prior, simulate T
+ * days, dist_i = sqrt(sum over days 1..T of the squared (A, R, D) differences),
+ * accept when dist_i <= eps.
+ *
+ *  theta_out  DEVICE float  [capacity][8]   accepted theta
+ *  dist_out   DEVICE double [capacity]      accepted distances
+ *  idx_out    DEVICE uint64 [capacity]      accepted sample indices
+ *  n_accepted HOST   uint64                 number of accepted samples
+ *
+ * The accepted samples are written in an unspecified order (sort by idx_out for
+ * a canonical order). If more than `capacity` samples are accepted the call
+ * returns ABC_ERR_CAPACITY, *n_accepted holds the true count and the output
+ * buffers hold an unspecified subset of `capacity` accepted samples.
+ * Uses a small amount of device scratch memory (the observed series and one
+ * counter) allocated stream-ordered on cuda_stream and freed before returning.
+ * Requires eps >= 0 (not NaN) and first_index + n_samples < 2^64. */
+abc_status abc_sample(const abc_prior_box* prior, const int32_t* observed, int32_t T,
+                      int64_t N_pop, double eps, uint64_t n_samples, uint64_t seed,
+                      uint32_t stream, abc_mode mode, uint64_t first_index, float* theta_out,
+                      double* dist_out, uint64_t* idx_out, uint64_t capacity,
+                      uint64_t* n_accepted, void* cuda_stream);
+
+/* The distance of every sample in [first_index, first_index + n_samples)
+ * (Sec. 2.2): dist_out DEVICE double [n_samples], dist_out[j] the distance of
+ * sample first_index + j. theta_out, when not NULL, is DEVICE float
+ * [n_samples][8] and receives each sample's prior draw. Asynchronous on
+ * cuda_stream. Uses device scratch for the observed series like abc_sample. */
+abc_status abc_distances(const abc_prior_box* prior, const int32_t* observed, int32_t T,
+                         int64_t N_pop, uint64_t n_samples, uint64_t seed, uint32_t stream,
+                         abc_mode mode, uint64_t first_index, double* dist_out,
+                         float* theta_out, void* cuda_stream);
+
+/* Trajectories for given parameter vectors (Sec. 2.1): for b < B, simulate
+ * theta[b] with the random numbers of sample index sample_index[b] from the
+ * initial condition init_ard (HOST int32 [3] = A0, R0, D0) and write
+ * traj_out[b][d][c], d = 0..T, c = S, I, A, R, D, Ru.
+ *  theta        DEVICE float  [B][8]
+ *  sample_index DEVICE uint64 [B]
+ *  traj_out     DEVICE int32  [B][T+1][6]
+ * A sample accepted by abc_sample, replayed with its (theta, idx), reproduces
+ * the trajectory whose distance was reported. Asynchronous on cuda_stream. */
+abc_status abc_simulate(const float* theta, const uint64_t* sample_index, uint64_t B,
+                        const int32_t* init_ard, int32_t T, int64_t N_pop, uint64_t seed,
+                        uint32_t stream, abc_mode mode, int32_t* traj_out, void* cuda_stream);
+
+/* One model day (Sec. 2.1, second to fourth step) applied to B given states:
+ * state_in[b] (S, I, A, R, D, Ru) with theta[b], using the five normals of day
+ * day[b] (>= 1) of sample sample_index[b]. Writes state_out[b] and the five
+ * transition counts counts_out[b] (S->I, I->A, A->R, A->D, I->Ru).
+ *  theta DEVICE float [B][8]; state_in, state_out DEVICE int32 [B][6];
+ *  sample_index DEVICE uint64 [B]; day DEVICE int32 [B]; counts_out DEVICE
+ *  int32 [B][5] or NULL. States must be >= 0 with sum N_pop. Asynchronous. */
+abc_status abc_step(const float* theta, const int32_t* state_in, const uint64_t* sample_index,
+                    const int32_t* day, uint64_t B, int64_t N_pop, uint64_t seed, uint32_t stream,
+                    abc_mode mode, int32_t* state_out, int32_t* counts_out, void* cuda_stream);
+
+/* The k-th smallest (1-based, 1 <= k <= n) of n non-negative distances
+ * (DEVICE double [n], e.g. from abc_distances), returned in *eps_out (HOST).
+ * Used to set eps to a distance quantile. Synchronizes cuda_stream. Uses device
+ * scratch (a histogram) allocated stream-ordered and freed before returning. */
+abc_status abc_kth_smallest(const double* dist, uint64_t n, uint64_t k, double* eps_out,
+                            void* cuda_stream);
+
+/* Static description of a status code. */
+const char* abc_strerror(abc_status status);
+
+/* Thread-local detail of the last error returned on this thread ("" if none). */
+const char* abc_last_error(void);
+
+/* Library version: major * 10000 + minor * 100 + patch. */
+int abc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ABC_GB300_H */

@@ -30,7 +30,7 @@
  *   R1 RNG: Philox4x32-10 (Salmon et al., SC'11), key = seed, counter =
  *      (i_lo, i_hi, k, 4*stream + g). k = 0 gives the prior draw (g = 0 -> theta0..3,
  *      g = 1 -> theta4..7); k >= 1 gives days 2k-1 and 2k (g = 0,1,2 -> words w0..w11).
- *   R2 Uniform from a word: u = bits((w >> 9) | 0x3F800000) - (1 - 2^-24), in (0,1).
+ *   R2 Uniform from a word: u = bits((w & 0x7FFFFF) | 0x3F800000) - (1 - 2^-24), in (0,1).
  *   R3 Normals: Box-Muller pair p = 0..4 uses (w[2p], w[2p+1]):
  *      r = sqrt(-2 ln2 * log2(u1)), z[2p] = r cos(pi*2u2), z[2p+1] = r sin(pi*2u2).
  *      Day 2k-1 uses z[0..4], day 2k uses z[5..9] (one per transition, in h order).
@@ -102,10 +102,10 @@ static void rng_block(uint64_t seed, uint32_t stream, uint64_t i, uint32_t k, ui
     oracle_philox4x32_10(ctr, key, out);
 }
 
-/* R2: uniform in (0,1) on the lattice (2m+1) 2^-24, m = w >> 9. */
+/* R2: uniform in (0,1) on the lattice (2m+1) 2^-24, m = the low 23 bits of w. */
 float oracle_uniform(uint32_t w)
 {
-    float one_plus = f_from_bits((w >> 9) | 0x3F800000u);   /* 1 + m 2^-23 */
+    float one_plus = f_from_bits((w & 0x007FFFFFu) | 0x3F800000u);   /* 1 + m 2^-23 */
     float one_minus_half_ulp = f_from_bits(0x3F7FFFFFu);    /* 1 - 2^-24  */
     return one_plus - one_minus_half_ulp;                   /* exact      */
 }

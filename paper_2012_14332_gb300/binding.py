@@ -1,0 +1,222 @@
+"""Python binding of the C ABI in ``include/abc_gb300.h`` (ctypes).
+
+Argument marshalling only: host arrays are passed as pointers, device buffers
+are torch CUDA tensors (PyTorch supplies device memory and the current
+stream); every step of the method runs in the CUDA library. The library must
+be built (``paper_2012_14332_gb300.build.build()``); there is no fallback.
+"""
+import ctypes
+import os
+import threading
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+ABC_EXACT, ABC_FAST = 0, 1
+ABC_OK, ABC_ERR_INVALID_ARG, ABC_ERR_CAPACITY, ABC_ERR_CUDA, ABC_ERR_TIMEOUT, ABC_ERR_NOMEM = range(6)
+ABC_T_MAX = 4096
+
+PAPER_LO = (0.0,) * 8
+PAPER_HI = (1.0, 100.0, 2.0, 1.0, 1.0, 1.0, 1.0, 2.0)   # Sec. 2.1, Eq. 2
+
+EXPORTED = ("abc_sample", "abc_distances", "abc_simulate", "abc_step", "abc_kth_smallest", "abc_strerror",
+            "abc_last_error", "abc_version")
+
+
+class AbcPriorBox(ctypes.Structure):
+    _fields_ = [("lo", ctypes.c_float * 8), ("hi", ctypes.c_float * 8)]
+
+
+class AbcError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__("%s: %s" % (_strerror(status), message))
+        self.status = status
+        self.message = message
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path():
+    return _build.LIB
+
+
+def load(path=None):
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None and path is None:
+            return _lib
+        p = path or _build.LIB
+        if not os.path.exists(p):
+            raise ImportError("CUDA library %s is not built; run paper_2012_14332_gb300.build.build()" % p)
+        L = ctypes.CDLL(p)
+        vp, u64, i32, i64, u32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32
+        box = ctypes.POINTER(AbcPriorBox)
+        L.abc_sample.argtypes = [box, vp, i32, i64, ctypes.c_double, u64, u64, u32, ctypes.c_int, u64, vp, vp, vp,
+                                 u64, ctypes.POINTER(ctypes.c_uint64), vp]
+        L.abc_distances.argtypes = [box, vp, i32, i64, u64, u64, u32, ctypes.c_int, u64, vp, vp, vp]
+        L.abc_simulate.argtypes = [vp, vp, u64, vp, i32, i64, u64, u32, ctypes.c_int, vp, vp]
+        L.abc_step.argtypes = [vp, vp, vp, vp, u64, i64, u64, u32, ctypes.c_int, vp, vp, vp]
+        L.abc_kth_smallest.argtypes = [vp, u64, u64, ctypes.POINTER(ctypes.c_double), vp]
+        for nm in ("abc_sample", "abc_distances", "abc_simulate", "abc_step", "abc_kth_smallest"):
+            getattr(L, nm).restype = ctypes.c_int
+        L.abc_strerror.argtypes = [ctypes.c_int]
+        L.abc_strerror.restype = ctypes.c_char_p
+        L.abc_last_error.argtypes = []
+        L.abc_last_error.restype = ctypes.c_char_p
+        L.abc_version.restype = ctypes.c_int
+        if path is None:
+            _lib = L
+        return L
+
+
+def _strerror(status):
+    try:
+        return load().abc_strerror(int(status)).decode()
+    except ImportError:
+        return "status %d" % status
+
+
+def _check(L, status, allow=()):
+    if status != ABC_OK and status not in allow:
+        raise AbcError(status, L.abc_last_error().decode())
+    return status
+
+
+def _mode(mode):
+    if mode in ("exact", ABC_EXACT):
+        return ABC_EXACT
+    if mode in ("fast", ABC_FAST):
+        return ABC_FAST
+    raise ValueError("mode must be 'exact' or 'fast'")
+
+
+def prior_box(lo=PAPER_LO, hi=PAPER_HI):
+    b = AbcPriorBox()
+    lo = np.asarray(lo, dtype=np.float32).reshape(8)
+    hi = np.asarray(hi, dtype=np.float32).reshape(8)
+    for j in range(8):
+        b.lo[j] = float(lo[j])
+        b.hi[j] = float(hi[j])
+    return b
+
+
+def _host_i32(a):
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.int32))
+    return a, a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _stream(cuda_stream):
+    if cuda_stream is None:
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(cuda_stream, torch.cuda.Stream):
+        return ctypes.c_void_p(cuda_stream.cuda_stream)
+    return ctypes.c_void_p(int(cuda_stream))
+
+
+def _dev(t, dtype, shape):
+    assert t.is_cuda and t.dtype == dtype and t.is_contiguous(), (t.device, t.dtype)
+    assert t.numel() >= int(np.prod(shape)), (t.shape, shape)
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def abc_sample(observed, N_pop, eps, n_samples, seed, stream=0, mode="fast", first_index=0, lo=PAPER_LO,
+               hi=PAPER_HI, capacity=None, out=None, cuda_stream=None, allow_overflow=False):
+    """ABC rejection over [first_index, first_index + n_samples).
+
+    observed: host int32 [3, T+1] (rows A, R, D). Returns
+    (theta [m, 8] f32, dist [m] f64, idx [m] u64 (as int64 storage), n_accepted)
+    as CUDA tensors, m = min(n_accepted, capacity), in unspecified order.
+    """
+    L = load()
+    obs, obs_p = _host_i32(observed)
+    T = obs.shape[1] - 1
+    if capacity is None:
+        capacity = max(1024, int(n_samples) // 100)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    if out is None:
+        theta = torch.empty((capacity, 8), dtype=torch.float32, device=dev)
+        dist = torch.empty((capacity,), dtype=torch.float64, device=dev)
+        idx = torch.empty((capacity,), dtype=torch.int64, device=dev)
+    else:
+        theta, dist, idx = out
+    nacc = ctypes.c_uint64(0)
+    b = prior_box(lo, hi)
+    st = L.abc_sample(ctypes.byref(b), obs_p, T, int(N_pop), float(eps), int(n_samples), int(seed), int(stream),
+                      _mode(mode), int(first_index), _dev(theta, torch.float32, (capacity, 8)),
+                      _dev(dist, torch.float64, (capacity,)), _dev(idx, torch.int64, (capacity,)), int(capacity),
+                      ctypes.byref(nacc), _stream(cuda_stream))
+    _check(L, st, allow=(ABC_ERR_CAPACITY,) if allow_overflow else ())
+    n = int(nacc.value)
+    m = min(n, capacity)
+    return theta[:m], dist[:m], idx[:m], n
+
+
+def abc_distances(observed, N_pop, n_samples, seed, stream=0, mode="fast", first_index=0, lo=PAPER_LO, hi=PAPER_HI,
+                  want_theta=False, out=None, cuda_stream=None):
+    """Distances of every sample (and optionally the prior draws): dist [n] f64 (, theta [n, 8])."""
+    L = load()
+    obs, obs_p = _host_i32(observed)
+    T = obs.shape[1] - 1
+    dev = torch.device("cuda", torch.cuda.current_device())
+    if out is None:
+        dist = torch.empty((n_samples,), dtype=torch.float64, device=dev)
+        theta = torch.empty((n_samples, 8), dtype=torch.float32, device=dev) if want_theta else None
+    else:
+        dist, theta = out
+    b = prior_box(lo, hi)
+    st = L.abc_distances(ctypes.byref(b), obs_p, T, int(N_pop), int(n_samples), int(seed), int(stream), _mode(mode),
+                         int(first_index), _dev(dist, torch.float64, (n_samples,)),
+                         _dev(theta, torch.float32, (n_samples, 8)) if theta is not None else None,
+                         _stream(cuda_stream))
+    _check(L, st)
+    return (dist, theta) if want_theta else dist
+
+
+def abc_simulate(theta, sample_index, init_ard, T, N_pop, seed, stream=0, mode="exact", cuda_stream=None):
+    """Trajectories [B, T+1, 6] (S, I, A, R, D, Ru) for theta [B, 8] (CUDA f32) and sample_index [B] (CUDA int64)."""
+    L = load()
+    B = theta.shape[0]
+    traj = torch.empty((B, T + 1, 6), dtype=torch.int32, device=theta.device)
+    a, a_p = _host_i32(init_ard)
+    st = L.abc_simulate(_dev(theta, torch.float32, (B, 8)), _dev(sample_index, torch.int64, (B,)), B, a_p, int(T),
+                        int(N_pop), int(seed), int(stream), _mode(mode), _dev(traj, torch.int32, (B, T + 1, 6)),
+                        _stream(cuda_stream))
+    _check(L, st)
+    return traj
+
+
+def abc_step(theta, state_in, sample_index, day, N_pop, seed, stream=0, mode="exact", cuda_stream=None):
+    """One day for B states: returns (state_out [B, 6] int32, counts [B, 5] int32)."""
+    L = load()
+    B = theta.shape[0]
+    state_out = torch.empty((B, 6), dtype=torch.int32, device=theta.device)
+    counts = torch.empty((B, 5), dtype=torch.int32, device=theta.device)
+    st = L.abc_step(_dev(theta, torch.float32, (B, 8)), _dev(state_in, torch.int32, (B, 6)),
+                    _dev(sample_index, torch.int64, (B,)), _dev(day, torch.int32, (B,)), B, int(N_pop), int(seed),
+                    int(stream), _mode(mode), _dev(state_out, torch.int32, (B, 6)), _dev(counts, torch.int32, (B, 5)),
+                    _stream(cuda_stream))
+    _check(L, st)
+    return state_out, counts
+
+
+def abc_kth_smallest(dist, k, cuda_stream=None):
+    """k-th smallest (1-based) of a CUDA f64 tensor of non-negative distances."""
+    L = load()
+    out = ctypes.c_double(0)
+    st = L.abc_kth_smallest(_dev(dist, torch.float64, (dist.numel(),)), dist.numel(), int(k), ctypes.byref(out),
+                            _stream(cuda_stream))
+    _check(L, st)
+    return out.value
+
+
+def abc_strerror(status):
+    return _strerror(status)
+
+
+def abc_version():
+    return load().abc_version()

@@ -1,0 +1,48 @@
+"""Compile the CUDA library ``libabc_gb300.so`` in-tree for sm_103a (nvcc only)."""
+import os
+import subprocess
+import sys
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CSRC = os.path.join(HERE, "csrc")
+LIB = os.path.join(HERE, "libabc_gb300.so")
+SOURCES = ["abc_kernels.cu", "abc_api.cu"]
+HEADERS = ["abc_kernels.h", "abc_model.cuh"]
+PUBLIC_HEADER = os.path.join(os.path.dirname(HERE), "include", "abc_gb300.h")
+
+# -fmad=false: no FMA contraction anywhere; the fast path asks for FMA
+# explicitly (__fmaf_rn), the exact path must never get one.
+NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17", "-fmad=false",
+              "-Xcompiler", "-fPIC", "-Xcompiler", "-O2", "-shared"]
+
+
+def nvcc():
+    for cand in (os.environ.get("NVCC"), "/usr/local/cuda/bin/nvcc", "nvcc"):
+        if cand and (os.path.sep not in cand or os.path.exists(cand)):
+            return cand
+    return "nvcc"
+
+
+def _stale():
+    if not os.path.exists(LIB):
+        return True
+    t = os.path.getmtime(LIB)
+    deps = [os.path.join(CSRC, f) for f in SOURCES + HEADERS] + [PUBLIC_HEADER, __file__]
+    return any(os.path.getmtime(d) > t for d in deps)
+
+
+def build(force=False, verbose=False):
+    """Build the library if it is missing or older than its sources."""
+    if not force and not _stale():
+        return LIB
+    tmp = LIB + ".%d.tmp" % os.getpid()
+    cmd = [nvcc()] + NVCC_FLAGS + (["-Xptxas", "-v"] if verbose else []) + ["-o", tmp] + \
+        [os.path.join(CSRC, f) for f in SOURCES]
+    subprocess.check_call(cmd, cwd=CSRC)
+    os.replace(tmp, LIB)
+    return LIB
+
+
+if __name__ == "__main__":
+    build(force=True, verbose="-v" in sys.argv)
+    print(LIB)

@@ -1,0 +1,362 @@
+// abc_api.cu -- the C ABI declared in include/abc_gb300.h: argument checks,
+// kernel parameters, stream-ordered scratch memory and error reporting.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/abc_gb300.h"
+#include "abc_kernels.h"
+#include "abc_model.cuh"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+abc_status fail(abc_status st, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return st;
+}
+
+abc_status ok()
+{
+    g_last_error.clear();
+    return ABC_OK;
+}
+
+abc_status cuda_fail(cudaError_t e, const char* what)
+{
+    return fail(e == cudaErrorMemoryAllocation ? ABC_ERR_NOMEM : ABC_ERR_CUDA, "%s: %s (%s)", what,
+                cudaGetErrorString(e), cudaGetErrorName(e));
+}
+
+// Host-side fault injection for tests of the error paths: the environment
+// variable ABC_GB300_INJECT_FAULT=alloc|launch makes the next scratch
+// allocation or kernel launch report failure without touching the GPU.
+bool injected(const char* what)
+{
+    const char* v = std::getenv("ABC_GB300_INJECT_FAULT");
+    return v && std::strcmp(v, what) == 0;
+}
+
+#define CUDA_TRY(expr, what)                        \
+    do {                                            \
+        cudaError_t _e = (expr);                    \
+        if (_e != cudaSuccess) return cuda_fail(_e, what); \
+    } while (0)
+
+abc_status check_prior(const abc_prior_box* prior)
+{
+    if (!prior) return fail(ABC_ERR_INVALID_ARG, "prior is NULL");
+    for (int j = 0; j < 8; ++j) {
+        if (!std::isfinite(prior->lo[j]) || !std::isfinite(prior->hi[j]))
+            return fail(ABC_ERR_INVALID_ARG, "prior bound %d is not finite", j);
+        if (prior->lo[j] > prior->hi[j]) return fail(ABC_ERR_INVALID_ARG, "prior lo[%d] > hi[%d]", j, j);
+        if (!std::isfinite(prior->hi[j] - prior->lo[j]))
+            return fail(ABC_ERR_INVALID_ARG, "prior width %d overflows float", j);
+    }
+    return ABC_OK;
+}
+
+abc_status check_model(int32_t T, int64_t N_pop, uint32_t stream)
+{
+    if (T < 1 || T > ABC_T_MAX) return fail(ABC_ERR_INVALID_ARG, "T = %d outside [1, %d]", T, ABC_T_MAX);
+    if (N_pop < 1 || N_pop >= ((int64_t)1 << 31))
+        return fail(ABC_ERR_INVALID_ARG, "N_pop = %lld outside [1, 2^31)", (long long)N_pop);
+    if (stream > ABC_STREAM_MAX) return fail(ABC_ERR_INVALID_ARG, "stream = %u above 2^30 - 1", stream);
+    return ABC_OK;
+}
+
+abc_status check_initial(const int32_t* ard, int64_t N_pop)
+{
+    if (!ard) return fail(ABC_ERR_INVALID_ARG, "initial condition is NULL");
+    if (ard[0] < 0 || ard[1] < 0 || ard[2] < 0) return fail(ABC_ERR_INVALID_ARG, "negative initial count");
+    if ((int64_t)ard[0] + ard[1] + ard[2] > N_pop)
+        return fail(ABC_ERR_INVALID_ARG, "A0 + R0 + D0 exceeds N_pop");
+    return ABC_OK;
+}
+
+// Kernel parameters: prior, Philox round keys, population constants.
+abcgb::ModelParams make_params(const abc_prior_box* prior, int32_t T, int64_t N_pop, uint64_t seed, uint32_t stream,
+                               const int32_t* ard0)
+{
+    abcgb::ModelParams p;
+    std::memset(&p, 0, sizeof p);
+    if (prior) {
+        for (int j = 0; j < 8; ++j) {
+            p.lo[j] = prior->lo[j];
+            volatile float w = prior->hi[j] - prior->lo[j];   // one IEEE binary32 subtraction
+            p.width[j] = w;
+        }
+    }
+    uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    for (int r = 0; r < 10; ++r) {
+        p.rk0[r] = k0;
+        p.rk1[r] = k1;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    p.ctr3_base = stream << 2;
+    p.T = T;
+    p.P = (int32_t)N_pop;
+    volatile float pf = (float)N_pop;
+    volatile float inv = 1.0f / pf;
+    p.inv_p = inv;
+    if (ard0) {
+        p.A0 = ard0[0];
+        p.R0 = ard0[1];
+        p.D0 = ard0[2];
+        p.room0 = (int32_t)(N_pop - ((int64_t)ard0[0] + ard0[1] + ard0[2]));
+    }
+    return p;
+}
+
+// Observed [3][T+1] rows A, R, D -> per-day int4 (A, R, D, 0).
+abc_status pack_observed(const int32_t* observed, int32_t T, int64_t N_pop, std::vector<int4>& out)
+{
+    if (!observed) return fail(ABC_ERR_INVALID_ARG, "observed is NULL");
+    out.resize((size_t)T + 1);
+    for (int32_t d = 0; d <= T; ++d) {
+        const int32_t A = observed[d], R = observed[(T + 1) + d], D = observed[2 * (T + 1) + d];
+        if (A < 0 || R < 0 || D < 0) return fail(ABC_ERR_INVALID_ARG, "negative observed count on day %d", d);
+        out[d] = make_int4(A, R, D, 0);
+    }
+    const int32_t ard0[3] = {out[0].x, out[0].y, out[0].z};
+    return check_initial(ard0, N_pop);
+}
+
+// Largest integer distance^2 whose distance sqrt((double)a) is <= eps. The
+// predicate is monotone in a, so a binary search over [0, 2^63] is exact.
+uint64_t acc_threshold(double eps)
+{
+    const uint64_t cap = 0x8000000000000000ull;
+    if (std::sqrt((double)cap) <= eps) return cap;
+    uint64_t lo = 0, hi = cap;   // sqrt(lo) <= eps (eps >= 0), sqrt(hi) > eps
+    while (hi - lo > 1) {
+        const uint64_t mid = lo + (hi - lo) / 2;
+        if (std::sqrt((double)mid) <= eps)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+struct Scratch {
+    void* ptr = nullptr;
+    cudaStream_t s = nullptr;
+    ~Scratch()
+    {
+        if (ptr) cudaFreeAsync(ptr, s);
+    }
+};
+
+abc_status alloc_scratch(Scratch& sc, size_t bytes, cudaStream_t s)
+{
+    sc.s = s;
+    if (injected("alloc")) return fail(ABC_ERR_NOMEM, "scratch allocation failed (injected)");
+    cudaError_t e = cudaMallocAsync(&sc.ptr, bytes, s);
+    if (e != cudaSuccess) {
+        sc.ptr = nullptr;
+        return cuda_fail(e, "cudaMallocAsync(scratch)");
+    }
+    return ABC_OK;
+}
+
+size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+}  // namespace
+
+extern "C" {
+
+abc_status abc_sample(const abc_prior_box* prior, const int32_t* observed, int32_t T, int64_t N_pop, double eps,
+                      uint64_t n_samples, uint64_t seed, uint32_t stream, abc_mode mode, uint64_t first_index,
+                      float* theta_out, double* dist_out, uint64_t* idx_out, uint64_t capacity,
+                      uint64_t* n_accepted, void* cuda_stream)
+{
+    abc_status st;
+    if ((st = check_prior(prior)) != ABC_OK) return st;
+    if ((st = check_model(T, N_pop, stream)) != ABC_OK) return st;
+    if (mode != ABC_EXACT && mode != ABC_FAST) return fail(ABC_ERR_INVALID_ARG, "unknown mode %d", (int)mode);
+    if (!(eps >= 0.0)) return fail(ABC_ERR_INVALID_ARG, "eps must be >= 0 and not NaN");
+    if (!n_accepted) return fail(ABC_ERR_INVALID_ARG, "n_accepted is NULL");
+    if (capacity > 0 && (!theta_out || !dist_out || !idx_out))
+        return fail(ABC_ERR_INVALID_ARG, "output buffers are NULL");
+    if (n_samples > ~(uint64_t)0 - first_index)
+        return fail(ABC_ERR_INVALID_ARG, "first_index + n_samples overflows");
+    std::vector<int4> obs;
+    if ((st = pack_observed(observed, T, N_pop, obs)) != ABC_OK) return st;
+    *n_accepted = 0;
+    if (n_samples == 0) return ok();
+
+    const int32_t ard0[3] = {obs[0].x, obs[0].y, obs[0].z};
+    const abcgb::ModelParams p = make_params(prior, T, N_pop, seed, stream, ard0);
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+
+    const size_t obs_bytes = round_up(sizeof(int4) * obs.size(), 256);
+    Scratch sc;
+    if ((st = alloc_scratch(sc, obs_bytes + 256, s)) != ABC_OK) return st;
+    int4* obs_d = (int4*)sc.ptr;
+    unsigned long long* count_d = (unsigned long long*)((char*)sc.ptr + obs_bytes);
+    CUDA_TRY(cudaMemcpyAsync(obs_d, obs.data(), sizeof(int4) * obs.size(), cudaMemcpyHostToDevice, s),
+             "cudaMemcpyAsync(observed)");
+    CUDA_TRY(cudaMemsetAsync(count_d, 0, sizeof(unsigned long long), s), "cudaMemsetAsync(count)");
+
+    abcgb::RejectArgs a;
+    a.obs = obs_d;
+    a.first_index = first_index;
+    a.n_samples = n_samples;
+    a.acc_max = acc_threshold(eps);
+    a.count = count_d;
+    a.capacity = capacity;
+    a.theta_out = theta_out;
+    a.dist_out = dist_out;
+    a.idx_out = idx_out;
+    if (injected("launch")) return fail(ABC_ERR_CUDA, "kernel launch failed (injected)");
+    CUDA_TRY(abcgb::launch_reject(p, a, mode == ABC_FAST, s, nullptr), "abc_reject_kernel launch");
+    unsigned long long count = 0;
+    CUDA_TRY(cudaMemcpyAsync(&count, count_d, sizeof count, cudaMemcpyDeviceToHost, s), "cudaMemcpyAsync(count)");
+    CUDA_TRY(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+    *n_accepted = count;
+    if (count > capacity)
+        return fail(ABC_ERR_CAPACITY, "%llu samples accepted, capacity %llu", count, (unsigned long long)capacity);
+    return ok();
+}
+
+abc_status abc_distances(const abc_prior_box* prior, const int32_t* observed, int32_t T, int64_t N_pop,
+                         uint64_t n_samples, uint64_t seed, uint32_t stream, abc_mode mode, uint64_t first_index,
+                         double* dist_out, float* theta_out, void* cuda_stream)
+{
+    abc_status st;
+    if ((st = check_prior(prior)) != ABC_OK) return st;
+    if ((st = check_model(T, N_pop, stream)) != ABC_OK) return st;
+    if (mode != ABC_EXACT && mode != ABC_FAST) return fail(ABC_ERR_INVALID_ARG, "unknown mode %d", (int)mode);
+    if (n_samples > 0 && !dist_out) return fail(ABC_ERR_INVALID_ARG, "dist_out is NULL");
+    if (n_samples > ~(uint64_t)0 - first_index)
+        return fail(ABC_ERR_INVALID_ARG, "first_index + n_samples overflows");
+    std::vector<int4> obs;
+    if ((st = pack_observed(observed, T, N_pop, obs)) != ABC_OK) return st;
+    if (n_samples == 0) return ok();
+    const int32_t ard0[3] = {obs[0].x, obs[0].y, obs[0].z};
+    const abcgb::ModelParams p = make_params(prior, T, N_pop, seed, stream, ard0);
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    Scratch sc;
+    if ((st = alloc_scratch(sc, sizeof(int4) * obs.size(), s)) != ABC_OK) return st;
+    CUDA_TRY(cudaMemcpyAsync(sc.ptr, obs.data(), sizeof(int4) * obs.size(), cudaMemcpyHostToDevice, s),
+             "cudaMemcpyAsync(observed)");
+    abcgb::DistanceArgs a;
+    a.obs = (const int4*)sc.ptr;
+    a.first_index = first_index;
+    a.n_samples = n_samples;
+    a.dist_out = dist_out;
+    a.theta_out = theta_out;
+    if (injected("launch")) return fail(ABC_ERR_CUDA, "kernel launch failed (injected)");
+    CUDA_TRY(abcgb::launch_distances(p, a, mode == ABC_FAST, s), "abc_distance_kernel launch");
+    return ok();
+}
+
+abc_status abc_simulate(const float* theta, const uint64_t* sample_index, uint64_t B, const int32_t* init_ard,
+                        int32_t T, int64_t N_pop, uint64_t seed, uint32_t stream, abc_mode mode, int32_t* traj_out,
+                        void* cuda_stream)
+{
+    abc_status st;
+    if ((st = check_model(T, N_pop, stream)) != ABC_OK) return st;
+    if (mode != ABC_EXACT && mode != ABC_FAST) return fail(ABC_ERR_INVALID_ARG, "unknown mode %d", (int)mode);
+    if ((st = check_initial(init_ard, N_pop)) != ABC_OK) return st;
+    if (B > 0 && (!theta || !sample_index || !traj_out)) return fail(ABC_ERR_INVALID_ARG, "NULL device buffer");
+    if (B == 0) return ok();
+    const abcgb::ModelParams p = make_params(nullptr, T, N_pop, seed, stream, init_ard);
+    abcgb::SimulateArgs a;
+    a.theta = theta;
+    a.sample_index = sample_index;
+    a.B = B;
+    a.traj_out = traj_out;
+    if (injected("launch")) return fail(ABC_ERR_CUDA, "kernel launch failed (injected)");
+    CUDA_TRY(abcgb::launch_simulate(p, a, mode == ABC_FAST, (cudaStream_t)cuda_stream), "abc_simulate_kernel launch");
+    return ok();
+}
+
+abc_status abc_step(const float* theta, const int32_t* state_in, const uint64_t* sample_index, const int32_t* day,
+                    uint64_t B, int64_t N_pop, uint64_t seed, uint32_t stream, abc_mode mode, int32_t* state_out,
+                    int32_t* counts_out, void* cuda_stream)
+{
+    abc_status st;
+    if ((st = check_model(1, N_pop, stream)) != ABC_OK) return st;
+    if (mode != ABC_EXACT && mode != ABC_FAST) return fail(ABC_ERR_INVALID_ARG, "unknown mode %d", (int)mode);
+    if (B > 0 && (!theta || !state_in || !sample_index || !day || !state_out))
+        return fail(ABC_ERR_INVALID_ARG, "NULL device buffer");
+    if (B == 0) return ok();
+    const abcgb::ModelParams p = make_params(nullptr, 1, N_pop, seed, stream, nullptr);
+    abcgb::StepArgs a;
+    a.theta = theta;
+    a.state_in = state_in;
+    a.sample_index = sample_index;
+    a.day = day;
+    a.B = B;
+    a.state_out = state_out;
+    a.counts_out = counts_out;
+    if (injected("launch")) return fail(ABC_ERR_CUDA, "kernel launch failed (injected)");
+    CUDA_TRY(abcgb::launch_step(p, a, mode == ABC_FAST, (cudaStream_t)cuda_stream), "abc_step_kernel launch");
+    return ok();
+}
+
+abc_status abc_kth_smallest(const double* dist, uint64_t n, uint64_t k, double* eps_out, void* cuda_stream)
+{
+    if (!dist || !eps_out) return fail(ABC_ERR_INVALID_ARG, "NULL pointer");
+    if (k < 1 || k > n) return fail(ABC_ERR_INVALID_ARG, "k = %llu outside [1, n = %llu]", (unsigned long long)k,
+                                    (unsigned long long)n);
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    abc_status st;
+    Scratch sc;
+    if ((st = alloc_scratch(sc, 256 * sizeof(unsigned long long), s)) != ABC_OK) return st;
+    unsigned long long* hist_d = (unsigned long long*)sc.ptr;
+    unsigned long long hist[256];
+    uint64_t prefix = 0, mask = 0, rank = k;   // rank: 1-based rank within the current prefix
+    for (int shift = 56; shift >= 0; shift -= 8) {
+        CUDA_TRY(cudaMemsetAsync(hist_d, 0, sizeof hist, s), "cudaMemsetAsync(hist)");
+        if (injected("launch")) return fail(ABC_ERR_CUDA, "kernel launch failed (injected)");
+        CUDA_TRY(abcgb::launch_digit_histogram(dist, n, prefix, mask, shift, hist_d, s), "digit_histogram launch");
+        CUDA_TRY(cudaMemcpyAsync(hist, hist_d, sizeof hist, cudaMemcpyDeviceToHost, s), "cudaMemcpyAsync(hist)");
+        CUDA_TRY(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+        uint64_t below = 0;
+        int digit = 0;
+        for (; digit < 256; ++digit) {
+            if (below + hist[digit] >= rank) break;
+            below += hist[digit];
+        }
+        if (digit == 256) return fail(ABC_ERR_INVALID_ARG, "distances contain negative values or NaN");
+        rank -= below;
+        prefix |= (uint64_t)digit << shift;
+        mask |= (uint64_t)0xFF << shift;
+    }
+    std::memcpy(eps_out, &prefix, sizeof prefix);
+    return ok();
+}
+
+const char* abc_strerror(abc_status status)
+{
+    switch (status) {
+    case ABC_OK: return "ok";
+    case ABC_ERR_INVALID_ARG: return "invalid argument";
+    case ABC_ERR_CAPACITY: return "more accepted samples than the output capacity";
+    case ABC_ERR_CUDA: return "CUDA error";
+    case ABC_ERR_TIMEOUT: return "device wait timed out";
+    case ABC_ERR_NOMEM: return "device memory allocation failed";
+    }
+    return "unknown status";
+}
+
+const char* abc_last_error(void) { return g_last_error.c_str(); }
+
+int abc_version(void) { return 100; }
+
+}  // extern "C"

@@ -1,0 +1,268 @@
+// abc_kernels.cu -- sm_103a kernels of ABC rejection sampling (paper Sec. 2.2,
+// Sec. 3.1): one simulation per thread, the compartments in registers, the
+// observed series in shared memory, the accepted samples compacted with a
+// warp ballot and one atomic per warp.
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "abc_kernels.h"
+#include "abc_model.cuh"
+
+namespace abcgb {
+
+// Stage the observed (A, R, D, 0) series of days 0..T into shared memory.
+__device__ __forceinline__ void stage_observed(int4* obs_s, const int4* __restrict__ obs, int32_t T)
+{
+    for (int32_t d = threadIdx.x; d <= T; d += blockDim.x) obs_s[d] = obs[d];
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// K1: fused rejection. Grid-stride over the sample range in whole blocks so
+// every lane of every warp reaches the ballot; lanes past the end simulate a
+// valid index and are never accepted.
+// ---------------------------------------------------------------------------
+template <int MODE>
+__global__ void __launch_bounds__(kBlockThreads) abc_reject_kernel(const __grid_constant__ ModelParams p,
+                                                                   const __grid_constant__ RejectArgs a)
+{
+    extern __shared__ int4 obs_s[];
+    stage_observed(obs_s, a.obs, p.T);
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x; base < a.n_samples; base += stride) {
+        const uint64_t j = base + threadIdx.x;
+        const bool valid = j < a.n_samples;
+        const uint64_t i = a.first_index + (valid ? j : a.n_samples - 1);
+        float th[8];
+        prior_draw(p, i, th);
+        const Theta t = make_theta<MODE>(th);
+        const State x0 = init_state(t, p.A0, p.R0, p.D0, p.room0);
+        const uint64_t acc = simulate_sample<MODE>(p, i, t, x0, obs_s, NoVisit());
+        const bool accept = valid && acc <= a.acc_max;
+        const uint32_t mask = __ballot_sync(0xFFFFFFFFu, accept);
+        if (mask == 0) continue;
+        const uint32_t leader = __ffs(mask) - 1;
+        unsigned long long slot0 = 0;
+        if (lane == leader) slot0 = atomicAdd(a.count, (unsigned long long)__popc(mask));
+        slot0 = __shfl_sync(0xFFFFFFFFu, slot0, leader);
+        if (accept) {
+            const uint64_t slot = slot0 + __popc(mask & ((1u << lane) - 1u));
+            if (slot < a.capacity) {
+                a.idx_out[slot] = i;
+                a.dist_out[slot] = __dsqrt_rn(__ull2double_rn(acc));
+                float4* to = reinterpret_cast<float4*>(a.theta_out + 8 * slot);
+                to[0] = make_float4(th[0], th[1], th[2], th[3]);
+                to[1] = make_float4(th[4], th[5], th[6], th[7]);
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// K2: every distance (and optionally every prior draw).
+// ---------------------------------------------------------------------------
+template <int MODE>
+__global__ void __launch_bounds__(kBlockThreads) abc_distance_kernel(const __grid_constant__ ModelParams p,
+                                                                     const __grid_constant__ DistanceArgs a)
+{
+    extern __shared__ int4 obs_s[];
+    stage_observed(obs_s, a.obs, p.T);
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < a.n_samples; j += stride) {
+        const uint64_t i = a.first_index + j;
+        float th[8];
+        prior_draw(p, i, th);
+        const Theta t = make_theta<MODE>(th);
+        const State x0 = init_state(t, p.A0, p.R0, p.D0, p.room0);
+        const uint64_t acc = simulate_sample<MODE>(p, i, t, x0, obs_s, NoVisit());
+        a.dist_out[j] = __dsqrt_rn(__ull2double_rn(acc));
+        if (a.theta_out) {
+            float4* to = reinterpret_cast<float4*>(a.theta_out + 8 * j);
+            to[0] = make_float4(th[0], th[1], th[2], th[3]);
+            to[1] = make_float4(th[4], th[5], th[6], th[7]);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// K3: trajectories of given (theta, sample index) pairs.
+// ---------------------------------------------------------------------------
+struct TrajVisit {
+    int32_t* out;
+    __device__ __forceinline__ void operator()(int32_t d, const State& x) const
+    {
+        int32_t* o = out + 6 * (size_t)d;
+        o[0] = x.S; o[1] = x.I; o[2] = x.A; o[3] = x.R; o[4] = x.D; o[5] = x.Ru;
+    }
+};
+
+template <int MODE>
+__global__ void __launch_bounds__(kBlockThreads) abc_simulate_kernel(const __grid_constant__ ModelParams p,
+                                                                     const __grid_constant__ SimulateArgs a)
+{
+    extern __shared__ int4 obs_s[];
+    // no observed series here: a zero series keeps the distance code shared
+    for (int32_t d = threadIdx.x; d <= p.T; d += blockDim.x) obs_s[d] = make_int4(0, 0, 0, 0);
+    __syncthreads();
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; b < a.B; b += stride) {
+        float th[8];
+        const float4* ti = reinterpret_cast<const float4*>(a.theta + 8 * b);
+        const float4 t0 = ti[0], t1 = ti[1];
+        th[0] = t0.x; th[1] = t0.y; th[2] = t0.z; th[3] = t0.w;
+        th[4] = t1.x; th[5] = t1.y; th[6] = t1.z; th[7] = t1.w;
+        const Theta t = make_theta<MODE>(th);
+        const State x0 = init_state(t, p.A0, p.R0, p.D0, p.room0);
+        TrajVisit v{a.traj_out + (size_t)b * 6 * (size_t)(p.T + 1)};
+        v(0, x0);
+        simulate_sample<MODE>(p, a.sample_index[b], t, x0, obs_s, v);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// K4: one day applied to given states.
+// ---------------------------------------------------------------------------
+template <int MODE>
+__global__ void __launch_bounds__(kBlockThreads) abc_step_kernel(const __grid_constant__ ModelParams p,
+                                                                 const __grid_constant__ StepArgs a)
+{
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; b < a.B; b += stride) {
+        float th[8];
+        for (int j = 0; j < 8; ++j) th[j] = a.theta[8 * b + j];
+        const Theta t = make_theta<MODE>(th);
+        const int32_t* si = a.state_in + 6 * b;
+        State x{si[0], si[1], si[2], si[3], si[4], si[5]};
+        const int32_t d = a.day[b];
+        float z[10];
+        day_pair_normals<MODE>(p, a.sample_index[b], (uint32_t)(d + 1) >> 1, z);
+        int32_t n[5];
+        model_day<MODE>(x, t, p.inv_p, (d & 1) ? z : z + 5, n);
+        int32_t* so = a.state_out + 6 * b;
+        so[0] = x.S; so[1] = x.I; so[2] = x.A; so[3] = x.R; so[4] = x.D; so[5] = x.Ru;
+        if (a.counts_out)
+            for (int k = 0; k < 5; ++k) a.counts_out[5 * b + k] = n[k];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Radix select of the k-th smallest distance: histogram of one 8-bit digit of
+// the keys (the bit patterns of non-negative doubles order like the values)
+// among the keys whose higher digits equal `prefix`.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kBlockThreads) digit_histogram_kernel(const double* __restrict__ dist, uint64_t n,
+                                                                        uint64_t prefix, uint64_t prefix_mask,
+                                                                        int shift, unsigned long long* __restrict__ hist)
+{
+    __shared__ unsigned int h[256];
+    for (int b = threadIdx.x; b < 256; b += blockDim.x) h[b] = 0;
+    __syncthreads();
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
+        const uint64_t key = (uint64_t)__double_as_longlong(dist[j]);
+        if ((key & prefix_mask) == prefix) atomicAdd(&h[(key >> shift) & 0xFFu], 1u);
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < 256; b += blockDim.x)
+        if (h[b]) atomicAdd(&hist[b], (unsigned long long)h[b]);
+}
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
+template <typename K>
+static cudaError_t grid_for(K kernel, size_t smem, int* grid)
+{
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    if (smem > 48 * 1024) {
+        e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kBlockThreads, smem);
+    if (e != cudaSuccess) return e;
+    *grid = sms * (per_sm > 0 ? per_sm : 1);
+    return cudaSuccess;
+}
+
+static int blocks_for(uint64_t n, int cap)
+{
+    const uint64_t b = (n + kBlockThreads - 1) / kBlockThreads;
+    return (int)(b < (uint64_t)cap ? (b > 0 ? b : 1) : (uint64_t)cap);
+}
+
+cudaError_t launch_reject(const ModelParams& p, const RejectArgs& a, bool fast, cudaStream_t s, int* blocks_out)
+{
+    const size_t smem = sizeof(int4) * (size_t)(p.T + 1);
+    int grid = 0;
+    cudaError_t e = fast ? grid_for(abc_reject_kernel<kFast>, smem, &grid)
+                         : grid_for(abc_reject_kernel<kExact>, smem, &grid);
+    if (e != cudaSuccess) return e;
+    grid = blocks_for(a.n_samples, grid);
+    if (blocks_out) *blocks_out = grid;
+    if (fast)
+        abc_reject_kernel<kFast><<<grid, kBlockThreads, smem, s>>>(p, a);
+    else
+        abc_reject_kernel<kExact><<<grid, kBlockThreads, smem, s>>>(p, a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_distances(const ModelParams& p, const DistanceArgs& a, bool fast, cudaStream_t s)
+{
+    const size_t smem = sizeof(int4) * (size_t)(p.T + 1);
+    int grid = 0;
+    cudaError_t e = fast ? grid_for(abc_distance_kernel<kFast>, smem, &grid)
+                         : grid_for(abc_distance_kernel<kExact>, smem, &grid);
+    if (e != cudaSuccess) return e;
+    grid = blocks_for(a.n_samples, grid);
+    if (fast)
+        abc_distance_kernel<kFast><<<grid, kBlockThreads, smem, s>>>(p, a);
+    else
+        abc_distance_kernel<kExact><<<grid, kBlockThreads, smem, s>>>(p, a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_simulate(const ModelParams& p, const SimulateArgs& a, bool fast, cudaStream_t s)
+{
+    const size_t smem = sizeof(int4) * (size_t)(p.T + 1);
+    int grid = 0;
+    cudaError_t e = fast ? grid_for(abc_simulate_kernel<kFast>, smem, &grid)
+                         : grid_for(abc_simulate_kernel<kExact>, smem, &grid);
+    if (e != cudaSuccess) return e;
+    grid = blocks_for(a.B, grid);
+    if (fast)
+        abc_simulate_kernel<kFast><<<grid, kBlockThreads, smem, s>>>(p, a);
+    else
+        abc_simulate_kernel<kExact><<<grid, kBlockThreads, smem, s>>>(p, a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_step(const ModelParams& p, const StepArgs& a, bool fast, cudaStream_t s)
+{
+    int grid = 0;
+    cudaError_t e = fast ? grid_for(abc_step_kernel<kFast>, 0, &grid) : grid_for(abc_step_kernel<kExact>, 0, &grid);
+    if (e != cudaSuccess) return e;
+    grid = blocks_for(a.B, grid);
+    if (fast)
+        abc_step_kernel<kFast><<<grid, kBlockThreads, 0, s>>>(p, a);
+    else
+        abc_step_kernel<kExact><<<grid, kBlockThreads, 0, s>>>(p, a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_digit_histogram(const double* dist, uint64_t n, uint64_t prefix, uint64_t prefix_mask, int shift,
+                                   unsigned long long* hist, cudaStream_t s)
+{
+    int grid = 0;
+    cudaError_t e = grid_for(digit_histogram_kernel, 0, &grid);
+    if (e != cudaSuccess) return e;
+    grid = blocks_for(n, grid);
+    digit_histogram_kernel<<<grid, kBlockThreads, 0, s>>>(dist, n, prefix, prefix_mask, shift, hist);
+    return cudaGetLastError();
+}
+
+}  // namespace abcgb

@@ -1,0 +1,55 @@
+// abc_kernels.h -- internal launch interface between the C ABI (abc_api.cu) and
+// the kernels (abc_kernels.cu). Not part of the public ABI.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace abcgb {
+
+constexpr int kBlockThreads = 256;
+
+struct ModelParams;
+
+struct RejectArgs {
+    const int4* obs;              // device [T+1] (A, R, D, 0)
+    uint64_t first_index, n_samples;
+    uint64_t acc_max;             // accept iff distance^2 <= acc_max
+    unsigned long long* count;    // device counter, zeroed before launch
+    uint64_t capacity;
+    float* theta_out;             // device [capacity][8]
+    double* dist_out;             // device [capacity]
+    uint64_t* idx_out;            // device [capacity]
+};
+
+struct DistanceArgs {
+    const int4* obs;
+    uint64_t first_index, n_samples;
+    double* dist_out;             // device [n_samples]
+    float* theta_out;             // device [n_samples][8] or null
+};
+
+struct SimulateArgs {
+    const float* theta;           // device [B][8]
+    const uint64_t* sample_index; // device [B]
+    uint64_t B;
+    int32_t* traj_out;            // device [B][T+1][6]
+};
+
+struct StepArgs {
+    const float* theta;           // device [B][8]
+    const int32_t* state_in;      // device [B][6]
+    const uint64_t* sample_index; // device [B]
+    const int32_t* day;           // device [B]
+    uint64_t B;
+    int32_t* state_out;           // device [B][6]
+    int32_t* counts_out;          // device [B][5] or null
+};
+
+cudaError_t launch_reject(const ModelParams& p, const RejectArgs& a, bool fast, cudaStream_t s, int* blocks_out);
+cudaError_t launch_distances(const ModelParams& p, const DistanceArgs& a, bool fast, cudaStream_t s);
+cudaError_t launch_simulate(const ModelParams& p, const SimulateArgs& a, bool fast, cudaStream_t s);
+cudaError_t launch_step(const ModelParams& p, const StepArgs& a, bool fast, cudaStream_t s);
+cudaError_t launch_digit_histogram(const double* dist, uint64_t n, uint64_t prefix, uint64_t prefix_mask, int shift,
+                                   unsigned long long* hist, cudaStream_t s);
+
+}  // namespace abcgb

@@ -1,0 +1,143 @@
+"""The C-ABI library without a GPU: it builds, loads, exports every entry
+point that include/abc_gb300.h declares, and rejects invalid arguments before
+any CUDA call."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "abc_gb300.h")
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2012_14332_gb300 import build, load
+    build.build()
+    return load()
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[\w]+\s*\*?\s*(abc_\w+)\s*\(", src, flags=re.M)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ("abc_sample", "abc_distances", "abc_simulate", "abc_step", "abc_kth_smallest", "abc_strerror",
+                 "abc_last_error", "abc_version"):
+        assert must in names, names
+
+
+def test_library_exports_every_declared_symbol(L):
+    for name in declared_functions():
+        assert hasattr(L, name), name
+
+
+def test_binding_names_match_header():
+    import paper_2012_14332_gb300.binding as b
+    for name in declared_functions():
+        if name not in ("abc_last_error",):
+            assert hasattr(b, name), name
+
+
+def test_strerror_and_version(L):
+    from paper_2012_14332_gb300 import binding as b
+    for st in range(6):
+        assert L.abc_strerror(st)
+    assert L.abc_strerror(99) == b"unknown status"
+    assert L.abc_version() >= 100
+
+
+def _call_sample(L, **kw):
+    from paper_2012_14332_gb300.binding import prior_box
+    T = kw.get("T", 10)
+    obs = kw.get("observed", np.zeros((3, T + 1), dtype=np.int32))
+    obs = np.ascontiguousarray(obs, dtype=np.int32)
+    box = kw.get("box", prior_box())
+    n = ctypes.c_uint64(0)
+    bogus = ctypes.c_void_p(16)   # never dereferenced: validation fails first
+    return L.abc_sample(ctypes.byref(box) if box is not None else None,
+                        obs.ctypes.data_as(ctypes.c_void_p) if kw.get("obs_null") is None else None,
+                        T, kw.get("P", 1000), kw.get("eps", 1.0), kw.get("n", 10), 1, kw.get("stream", 0),
+                        kw.get("mode", 1), kw.get("first", 0), bogus, bogus, bogus, kw.get("cap", 4),
+                        ctypes.byref(n) if not kw.get("nacc_null") else None, None)
+
+
+@pytest.mark.parametrize("kw,fragment", [
+    (dict(T=0), "T = 0"),
+    (dict(T=4097), "T = 4097"),
+    (dict(P=0), "N_pop"),
+    (dict(P=2**31), "N_pop"),
+    (dict(eps=-1.0), "eps"),
+    (dict(eps=float("nan")), "eps"),
+    (dict(mode=7), "mode"),
+    (dict(stream=2**30), "stream"),
+    (dict(first=2**64 - 5), "overflows"),
+    (dict(box=None), "prior"),
+    (dict(obs_null=True), "observed"),
+    (dict(nacc_null=True), "n_accepted"),
+])
+def test_sample_rejects_invalid_arguments(L, kw, fragment):
+    from paper_2012_14332_gb300.binding import ABC_ERR_INVALID_ARG
+    assert _call_sample(L, **kw) == ABC_ERR_INVALID_ARG
+    assert fragment in L.abc_last_error().decode()
+
+
+def test_sample_rejects_bad_prior_and_observed(L):
+    from paper_2012_14332_gb300.binding import ABC_ERR_INVALID_ARG, prior_box
+    hi = np.array([1, 100, 2, 1, 1, 1, 1, 2], dtype=np.float32)
+    lo = hi.copy()
+    lo[3] = 5.0
+    assert _call_sample(L, box=prior_box(lo, hi)) == ABC_ERR_INVALID_ARG
+    lo = np.zeros(8, dtype=np.float32)
+    lo[0] = np.inf
+    assert _call_sample(L, box=prior_box(lo, hi)) == ABC_ERR_INVALID_ARG
+    obs = np.zeros((3, 11), dtype=np.int32)
+    obs[1, 5] = -1
+    assert _call_sample(L, observed=obs) == ABC_ERR_INVALID_ARG
+    obs = np.zeros((3, 11), dtype=np.int32)
+    obs[:, 0] = [600, 300, 200]   # A0 + R0 + D0 > P = 1000
+    assert _call_sample(L, observed=obs) == ABC_ERR_INVALID_ARG
+    assert "exceeds" in L.abc_last_error().decode()
+
+
+def test_other_entry_points_validate(L):
+    from paper_2012_14332_gb300.binding import ABC_ERR_INVALID_ARG
+    z = ctypes.c_void_p(16)
+    init = np.array([10, 0, 0], dtype=np.int32)
+    ip = init.ctypes.data_as(ctypes.c_void_p)
+    assert L.abc_simulate(z, z, 4, ip, 0, 1000, 1, 0, 0, z, None) == ABC_ERR_INVALID_ARG
+    assert L.abc_simulate(None, z, 4, ip, 10, 1000, 1, 0, 0, z, None) == ABC_ERR_INVALID_ARG
+    big = np.array([900, 200, 0], dtype=np.int32)
+    assert L.abc_simulate(z, z, 4, big.ctypes.data_as(ctypes.c_void_p), 10, 1000, 1, 0, 0, z, None) \
+        == ABC_ERR_INVALID_ARG
+    assert L.abc_step(z, z, z, None, 4, 1000, 1, 0, 0, z, None, None) == ABC_ERR_INVALID_ARG
+    assert L.abc_step(z, z, z, z, 4, 0, 1, 0, 0, z, None, None) == ABC_ERR_INVALID_ARG
+    out = ctypes.c_double()
+    assert L.abc_kth_smallest(z, 10, 0, ctypes.byref(out), None) == ABC_ERR_INVALID_ARG
+    assert L.abc_kth_smallest(z, 10, 11, ctypes.byref(out), None) == ABC_ERR_INVALID_ARG
+    from paper_2012_14332_gb300.binding import prior_box
+    box = prior_box()
+    obs = np.zeros((3, 11), dtype=np.int32)
+    assert L.abc_distances(ctypes.byref(box), obs.ctypes.data_as(ctypes.c_void_p), 10, 1000, 5, 1, 0, 1, 0, None,
+                           None, None) == ABC_ERR_INVALID_ARG
+
+
+def test_zero_samples_is_a_no_op(L):
+    # n_samples = 0 returns before any CUDA call
+    from paper_2012_14332_gb300.binding import ABC_OK
+    assert _call_sample(L, n=0) == ABC_OK
+
+
+def test_oracle_is_not_reachable_from_the_product():
+    """The CUDA package neither imports nor links the oracle."""
+    pkg = os.path.join(ROOT, "paper_2012_14332_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                src = open(os.path.join(dirpath, f)).read()
+                assert "oracle" not in src.lower(), os.path.join(dirpath, f)

@@ -85,12 +85,12 @@ def test_philox_zero_vector_and_avalanche():
 
 
 def test_uniform_is_odd_lattice():
-    """u = (2m+1) 2^-24 with m = w >> 9: exact, in (0, 1), symmetric about 1/2."""
+    """u = (2m+1) 2^-24 with m = w mod 2^23: exact, in (0, 1)."""
     g = inputs.rng(5)
     w = g.integers(0, 2**32, size=1 << 16, dtype=np.uint64).astype(np.uint32)
-    w = np.concatenate([w, np.array([0, 511, 512, 0xFFFFFFFF, 0x80000000], dtype=np.uint32)])
+    w = np.concatenate([w, np.array([0, 0x7FFFFF, 0x800000, 0xFFFFFFFF, 0x80000000], dtype=np.uint32)])
     u = oracle.uniform_batch(w).astype(np.float64)
-    m = (w >> 9).astype(np.float64)
+    m = (w & 0x7FFFFF).astype(np.float64)
     assert np.array_equal(u * 2.0**24, 2 * m + 1)
     assert u.min() > 0 and u.max() < 1
     assert oracle.uniform(0) == np.float32(2.0**-24)
@@ -155,8 +155,8 @@ def test_box_muller_against_float64_formula():
     w = g.integers(0, 2**32, size=(4096, 2), dtype=np.uint64).astype(np.uint32)
     for a, b in w:
         z = oracle.box_muller(int(a), int(b)).astype(np.float64)
-        u1 = (2 * (int(a) >> 9) + 1) * 2.0**-24
-        u2 = (2 * (int(b) >> 9) + 1) * 2.0**-24
+        u1 = (2 * (int(a) & 0x7FFFFF) + 1) * 2.0**-24
+        u2 = (2 * (int(b) & 0x7FFFFF) + 1) * 2.0**-24
         r = np.sqrt(-2 * np.log(u1))
         ref = np.array([r * np.cos(2 * np.pi * u2), r * np.sin(2 * np.pi * u2)])
         assert np.all(np.abs(z - ref) <= 4e-7 * (1 + r)), (a, b, z, ref)
