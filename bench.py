@@ -1,0 +1,328 @@
+"""Benchmark: ABC rejection sampling on synthetic series shaped like the paper's
+country data (Sec. 4, Sec. 5), one JSON line on stdout.
+
+One step = one abc_sample launch over 2^24 prior samples of the P = 6e7,
+T = 100 workload at its fixed eps (fast mode), each step on fresh sample
+indices. Default: 1 GPU, 10 timed steps after 3 warm-up steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+N > 1 runs under torchrun, one rank per GPU; ranks take disjoint sample index
+ranges (weak scaling, no data-path collective). --impl reference times the CPU
+oracle (the plain restatement of the method) on the host cores instead.
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "region_6e7_T100"
+METRIC = json.load(open(os.path.join(ROOT, "BASELINE.json")))["metric"] if os.path.exists(
+    os.path.join(ROOT, "BASELINE.json")) else "accepted ABC samples/s at fixed eps; sims*days/s"
+UNIT = "accepted samples/s"
+
+# Algorithmic operations of one simulated day (fast mode), by the pipe that
+# executes them (per-SM per-clock rates: FP32 128, INT32 64, SFU/conversion 16).
+# Philox: 1.5 blocks x 10 rounds x (2 32x32->64 multiplies + 2 three-input xors);
+# 2.5 Box-Muller pairs (lg2, sqrt, sin, cos each on the SFU); pow = lg2 + ex2;
+# one reciprocal; five sqrt; four int->float and five float->int conversions;
+# integer clamps, state update and the exact distance accumulation.
+OPS_PER_SIM_DAY = {"sfu": 27.0, "int": 100.0, "fp32": 35.0}
+PIPE_RATE_PER_SM_CLK = {"sfu": 16.0, "int": 64.0, "fp32": 128.0}
+
+
+def load_workload():
+    with open(os.path.join(ROOT, "tests", "golden", "workloads.json")) as f:
+        w = json.load(f)[WORKLOAD]
+    w["observed"] = np.array(w["observed"], dtype=np.int32)
+    return w
+
+
+def describe(w):
+    return ("%s: one synthetic region, P=%d, T=%d days, %d uniform prior samples per launch, fixed eps=%g "
+            "(1e-4 quantile of a %d-sample pilot), %s mode" % (WORKLOAD, w["P"], w["T"], w["n_samples"], w["eps"],
+                                                               w["pilot"], w["mode"]))
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f)
+    return None
+
+
+def roofline(sim_days_per_launch, launch_ms, sm_count, sm_max_mhz):
+    """ALU roofline: the fastest a launch could run if the busiest pipe for the
+    method's operations (OPS_PER_SIM_DAY) were saturated on every SM at the
+    maximum SM clock. Reported in simulated days per second."""
+    clk_per_sim_day = max(OPS_PER_SIM_DAY[k] / PIPE_RATE_PER_SM_CLK[k] for k in OPS_PER_SIM_DAY)
+    bound_pipe = max(OPS_PER_SIM_DAY, key=lambda k: OPS_PER_SIM_DAY[k] / PIPE_RATE_PER_SM_CLK[k])
+    peak = sm_count * sm_max_mhz * 1e6 / clk_per_sim_day
+    achieved = sim_days_per_launch / (launch_ms * 1e-3)
+    return {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Gsim*days/s",
+            "frac": achieved / peak, "traffic": None, "pipe": bound_pipe,
+            "peak_basis": "%d SMs x %.0f MHz (max SM clock) / %.3f clk per sim-day on the %s pipe" % (
+                sm_count, sm_max_mhz, clk_per_sim_day, bound_pipe)}
+
+
+def oracle_sample(w, n, first_index, threads=0):
+    """The CPU oracle (exact arithmetic) on n samples of the workload."""
+    import oracle
+    t0 = time.perf_counter()
+    r = oracle.abc(w["observed"], w["P"], w["eps"], n, w["seed"], first_index=first_index,
+                   capacity=max(64, n // 100), n_threads=threads)
+    return time.perf_counter() - t0, r["n_accepted"]
+
+
+def cpu_baseline(w, n=1 << 20):
+    cores = os.cpu_count() or 1
+    dt, acc = oracle_sample(w, n, 0, cores)
+    return {"value": acc / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sims_days_per_s": n * w["T"] / dt, "accepted": acc, "seconds": dt,
+            "sample": "%d prior samples (indices 0..%d) of the same workload and eps, C oracle, %d threads" % (
+                n, n - 1, cores)}
+
+
+def run_reference(args):
+    """The reference arm: the CPU oracle as it stands, on the host cores."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = load_workload()
+    n = 1 << 18
+    for s in range(args.warmup):
+        oracle_sample(w, n, s * n)
+    tot, acc = 0.0, 0
+    for s in range(args.steps):
+        dt, a = oracle_sample(w, n, (args.warmup + s) * n)
+        tot += dt
+        acc += a
+    cores = os.cpu_count() or 1
+    value = acc / tot
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": {"workload": describe(w), "samples_per_step": n,
+                                            "parallelism": "host threads"},
+            "sims_days_per_s": n * args.steps * w["T"] / tot,
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "%d prior samples per step of the same workload and eps" % n},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--samples", type=int, default=0,
+                    help="samples per launch (profiling runs on a smaller case; not a benchmark value)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import paper_2012_14332_gb300 as abc
+    from paper_2012_14332_gb300 import build as abc_build
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0 or not os.path.exists(abc_build.LIB):
+        abc_build.build()
+    if dist is not None:
+        dist.barrier()
+    abc.load()
+
+    w = load_workload()
+    if args.samples:
+        w["n_samples"] = args.samples
+    obs, P, T, n, seed, eps = w["observed"], w["P"], w["T"], w["n_samples"], w["seed"], w["eps"]
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    cap = 1 << 16
+    outs = (torch.empty((cap, 8), dtype=torch.float32, device=dev), torch.empty((cap,), dtype=torch.float64, device=dev),
+            torch.empty((cap,), dtype=torch.int64, device=dev))
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
+
+    def first_index(step):
+        return (step * world + rank) * n
+
+    def step(s):
+        _, _, _, a = abc.abc_sample(obs, P, eps, n, seed, mode=w["mode"], first_index=first_index(s), capacity=cap,
+                                    out=outs)
+        return a
+
+    for s in range(args.warmup):
+        step(s)
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    region0, region1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    accepted = 0
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    region0.record(stream)
+    for s in range(args.steps):
+        flush.fill_(s & 0xFF)                       # evict L2 between steps
+        starts[s].record(stream)
+        accepted += step(args.warmup + s)
+        ends[s].record(stream)
+    region1.record(stream)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    clocks = sampler.stop()
+    region_ms = region0.elapsed_time(region1)
+    launch_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+    t_region = torch.tensor([region_ms, float(accepted)], dtype=torch.float64, device=dev)
+    if dist is not None:
+        tmax = t_region.clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        tsum = t_region.clone()
+        dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
+        region_ms, accepted = float(tmax[0]), int(tsum[1])
+    ms_per_step = region_ms / args.steps
+    sims_per_step = n * world
+    value = accepted / (region_ms * 1e-3)
+
+    # end to end through the public call with host buffers: observed series from
+    # pinned host memory inside the call, accepted samples copied back to pinned
+    # host memory inside the timed region
+    host_theta = torch.empty((cap, 8), dtype=torch.float32, pin_memory=True)
+    host_dist = torch.empty((cap,), dtype=torch.float64, pin_memory=True)
+    host_idx = torch.empty((cap,), dtype=torch.int64, pin_memory=True)
+    obs_pinned = torch.from_numpy(obs).pin_memory().numpy()
+    e2e_steps = 0 if args.no_e2e else max(3, args.steps // 2)
+    d2h, e2e_accepted = 0, 0
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for s in range(e2e_steps):
+        th, di, ix, a = abc.abc_sample(obs_pinned, P, eps, n, seed, mode=w["mode"],
+                                       first_index=first_index(args.warmup + args.steps + s), capacity=cap, out=outs)
+        m = th.shape[0]
+        e2e_accepted += a
+        host_theta[:m].copy_(th, non_blocking=True)
+        host_dist[:m].copy_(di, non_blocking=True)
+        host_idx[:m].copy_(ix, non_blocking=True)
+        d2h += 8 + m * (32 + 8 + 8)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e_t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+    e2e_n = torch.tensor([float(e2e_accepted)], dtype=torch.float64, device=dev)
+    if dist is not None:
+        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(e2e_n, op=dist.ReduceOp.SUM)
+    e2e_s, e2e_accepted = float(e2e_t[0]), int(e2e_n[0])
+
+    if rank == 0:
+        props = torch.cuda.get_device_properties(dev)
+        peaks = measured_peaks() or {}
+        sm_max = clocks.get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2070.0
+        rf = roofline(n * T, float(np.mean(launch_ms)), props.multi_processor_count, sm_max)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": describe(w), "samples_per_step": sims_per_step,
+                       "parallelism": "dp%d" % world, "l2": "flushed between steps (256 MiB write)",
+                       "eps": eps, "seed": seed},
+            "sims_days_per_s": sims_per_step * T / (ms_per_step * 1e-3),
+            "accepted_per_step": accepted / args.steps,
+            "acceptance": accepted / (args.steps * sims_per_step),
+            "launch_ms_mean": float(np.mean(launch_ms)),
+            "e2e": ({"value": e2e_accepted / e2e_s, "unit": UNIT, "ms_per_step": e2e_s / e2e_steps * 1e3,
+                     "h2d_bytes_per_step": 16 * (T + 1), "d2h_bytes_per_step": int(d2h / e2e_steps)}
+                    if e2e_steps else None),
+            "gpu_launches": args.steps,
+            "roofline": rf,
+            "clocks": clocks,
+        }
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(w)
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

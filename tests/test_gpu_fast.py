@@ -1,0 +1,119 @@
+"""Fast mode (SFU transcendentals, FMA) judged statistically against exact mode
+and the oracle:
+
+  * teacher-forced steps: the fast day applied to exact states (from the
+    oracle) with the same random numbers gives every transition count within
+    one count plus 1e-6 relative of the exact count (a floor of two reals that
+    agree to 1e-6 relative can differ by one);
+  * distances: at least 98 % of samples within 1e-6 relative of exact mode;
+  * acceptance rate within binomial error of exact mode at the same eps;
+  * posterior: accepted theta of fast mode vs exact mode on independent seeds,
+    per coordinate two-sample KS p > 0.01, means and quantiles within Monte
+    Carlo error."""
+import numpy as np
+import pytest
+from scipy import stats
+
+import oracle
+from tests import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_2012_14332_gb300 as abc  # noqa: E402
+from paper_2012_14332_gb300 import build as _build  # noqa: E402
+
+_build.build()
+DEV = torch.device("cuda", 0)
+
+
+@pytest.mark.parametrize("name", ["region_6e7_T100", "region_3p3e8_T120", "region_1e6_T49"])
+def test_teacher_forced_step_disagreement(name):
+    w = inputs.workload(name)
+    obs, P, T, seed = w["observed"], w["P"], w["T"], w["seed"]
+    B = 300
+    th = oracle.prior_batch(seed, 0, 0, B)
+    X, TH, IX, DY = [], [], [], []
+    for b in range(B):
+        tr = oracle.simulate(th[b], obs[:, 0], T, P, seed, 0, b)
+        X.append(tr[:-1])
+        TH.append(np.tile(th[b], (T, 1)))
+        IX.append(np.full(T, b))
+        DY.append(np.arange(1, T + 1))
+    X = torch.from_numpy(np.concatenate(X).astype(np.int32)).to(DEV)
+    TH = torch.from_numpy(np.concatenate(TH).astype(np.float32)).to(DEV)
+    IX = torch.from_numpy(np.concatenate(IX).astype(np.int64)).to(DEV)
+    DY = torch.from_numpy(np.concatenate(DY).astype(np.int32)).to(DEV)
+    _, ne = abc.abc_step(TH, X, IX, DY, P, seed, mode="exact")
+    Yf, nf = abc.abc_step(TH, X, IX, DY, P, seed, mode="fast")
+    ne = ne.cpu().numpy().astype(np.int64)
+    nf = nf.cpu().numpy().astype(np.int64)
+    diff = np.abs(nf - ne)
+    beyond = diff > 1 + 1e-6 * ne
+    assert beyond.mean() < 1e-6, (beyond.sum(), diff.size)
+    assert (diff > 0).mean() < 1e-2
+    Yf = Yf.cpu().numpy().astype(np.int64)
+    assert np.all(Yf.sum(axis=1) == P) and np.all(Yf >= 0)
+
+
+def test_fast_distances_relative_error():
+    w = inputs.workload("region_6e7_T100")
+    obs, P, seed = w["observed"], w["P"], w["seed"]
+    n = 1 << 20
+    de = abc.abc_distances(obs, P, n, seed, mode="exact").cpu().numpy()
+    df = abc.abc_distances(obs, P, n, seed, mode="fast").cpu().numpy()
+    rel = np.abs(df - de) / np.maximum(de, 1.0)
+    assert np.mean(rel <= 1e-6) >= 0.98
+    assert np.median(rel) == 0.0
+    for q in (1e-4, 1e-3, 1e-2):
+        k = int(q * n)
+        a, b = np.sort(de)[k], np.sort(df)[k]
+        assert abs(a - b) <= 1e-3 * a, (q, a, b)
+
+
+def test_fast_acceptance_and_posterior_match_exact():
+    w = inputs.workload("region_1e6_T49")
+    obs, P = w["observed"], w["P"]
+    n = 1 << 22
+    # eps at the 1e-3 quantile of an exact pilot
+    pilot = abc.abc_distances(obs, P, 1 << 20, 5, mode="exact")
+    eps = abc.abc_kth_smallest(pilot, 1 << 10)
+    cap = 1 << 15
+    th_e, _, _, n_e = abc.abc_sample(obs, P, eps, n, 1001, mode="exact", capacity=cap)
+    th_f, _, _, n_f = abc.abc_sample(obs, P, eps, n, 2002, mode="fast", capacity=cap)
+    p = n_e / n
+    sd = np.sqrt(2 * p * (1 - p) / n)
+    assert abs(n_f / n - p) < 5 * sd, (n_e, n_f)
+    a, b = th_e.cpu().numpy().astype(np.float64), th_f.cpu().numpy().astype(np.float64)
+    assert len(a) > 2000 and len(b) > 2000
+    for j in range(8):
+        assert stats.ks_2samp(a[:, j], b[:, j]).pvalue > 0.01, j
+        se = np.sqrt(a[:, j].var() / len(a) + b[:, j].var() / len(b))
+        assert abs(a[:, j].mean() - b[:, j].mean()) < 4 * se, j
+        for q in (0.1, 0.5, 0.9):
+            qa, qb = np.quantile(a[:, j], q), np.quantile(b[:, j], q)
+            # quantile standard error: sqrt(q(1-q)/n) / density, density from the sample
+            h = 0.05 * (a[:, j].max() - a[:, j].min()) + 1e-12
+            dens = max(np.mean(np.abs(a[:, j] - qa) < h) / (2 * h), 1e-12)
+            qse = np.sqrt(q * (1 - q) * (1 / len(a) + 1 / len(b))) / dens
+            assert abs(qa - qb) < 5 * qse, (j, q, qa, qb)
+
+
+def test_injected_faults_leave_the_context_usable(monkeypatch):
+    w = inputs.workload("region_1e6_T49")
+    obs, P = w["observed"], w["P"]
+    monkeypatch.setenv("ABC_GB300_INJECT_FAULT", "alloc")
+    with pytest.raises(abc.AbcError) as e:
+        abc.abc_sample(obs, P, w["eps"], 4096, 1, mode="fast")
+    assert e.value.status == abc.binding.ABC_ERR_NOMEM
+    monkeypatch.setenv("ABC_GB300_INJECT_FAULT", "launch")
+    with pytest.raises(abc.AbcError) as e:
+        abc.abc_sample(obs, P, w["eps"], 4096, 1, mode="fast")
+    assert e.value.status == abc.binding.ABC_ERR_CUDA
+    monkeypatch.delenv("ABC_GB300_INJECT_FAULT")
+    d = abc.abc_distances(obs, P, 4096, 1, mode="exact")
+    ref = oracle.abc(obs, P, 0.0, 4096, 1, want_all=True, capacity=1)
+    assert np.array_equal(d.cpu().numpy(), ref["dist_all"])
