@@ -30,14 +30,16 @@ METRIC = json.load(open(os.path.join(ROOT, "BASELINE.json")))["metric"] if os.pa
     os.path.join(ROOT, "BASELINE.json")) else "accepted ABC samples/s at fixed eps; sims*days/s"
 UNIT = "accepted samples/s"
 
-# Algorithmic operations of one simulated day (fast mode), by the pipe that
-# executes them (per-SM per-clock rates: FP32 128, INT32 64, SFU/conversion 16).
-# Philox: 1.5 blocks x 10 rounds x (2 32x32->64 multiplies + 2 three-input xors);
-# 2.5 Box-Muller pairs (lg2, sqrt, sin, cos each on the SFU); pow = lg2 + ex2;
-# one reciprocal; five sqrt; four int->float and five float->int conversions;
-# integer clamps, state update and the exact distance accumulation.
-OPS_PER_SIM_DAY = {"sfu": 27.0, "int": 100.0, "fp32": 35.0}
-PIPE_RATE_PER_SM_CLK = {"sfu": 16.0, "int": 64.0, "fp32": 128.0}
+# Algorithmic work of one simulated day (fast mode), in instructions per thread:
+# Philox 1.5 blocks x 10 rounds x (2 wide multiplies + 2 three-input xors),
+# less the words the three blocks of a day pair share (53); uniforms (7.5);
+# 2.5 Box-Muller pairs of 9 (22.5); hazards incl. the pow and four int->float
+# (19); five transitions of sqrt, fma, floor, clamp plus two caps (22); state
+# update (7); exact distance (11); loop (2). 144 issue slots, 18 of them SFU
+# transcendentals. Issue: 4 warp-instructions (128 threads) per clock per SM;
+# SFU: 16 per clock per SM.
+OPS_PER_SIM_DAY = {"issue": 144.0, "sfu": 18.0}
+PIPE_RATE_PER_SM_CLK = {"issue": 128.0, "sfu": 16.0}
 
 
 def load_workload():
@@ -114,9 +116,10 @@ def measured_peaks():
 
 
 def roofline(sim_days_per_launch, launch_ms, sm_count, sm_max_mhz):
-    """ALU roofline: the fastest a launch could run if the busiest pipe for the
-    method's operations (OPS_PER_SIM_DAY) were saturated on every SM at the
-    maximum SM clock. Reported in simulated days per second."""
+    """ALU roofline: the fastest a launch could run if the tighter of issue
+    slots and SFU throughput for the method's instructions (OPS_PER_SIM_DAY)
+    were saturated on every SM at the maximum SM clock. In simulated days/s,
+    counting the days the launch actually simulated."""
     clk_per_sim_day = max(OPS_PER_SIM_DAY[k] / PIPE_RATE_PER_SM_CLK[k] for k in OPS_PER_SIM_DAY)
     bound_pipe = max(OPS_PER_SIM_DAY, key=lambda k: OPS_PER_SIM_DAY[k] / PIPE_RATE_PER_SM_CLK[k])
     peak = sm_count * sm_max_mhz * 1e6 / clk_per_sim_day
@@ -219,14 +222,18 @@ def main():
     def first_index(step):
         return (step * world + rank) * n
 
+    sim_days = [0]
+
     def step(s):
         _, _, _, a = abc.abc_sample(obs, P, eps, n, seed, mode=w["mode"], first_index=first_index(s), capacity=cap,
                                     out=outs)
+        sim_days[0] += abc.abc_last_simulated_days()
         return a
 
     for s in range(args.warmup):
         step(s)
     torch.cuda.synchronize()
+    sim_days[0] = 0
 
     sampler = ClockSampler(local)
     sampler.start()
@@ -297,7 +304,7 @@ def main():
         props = torch.cuda.get_device_properties(dev)
         peaks = measured_peaks() or {}
         sm_max = clocks.get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2070.0
-        rf = roofline(n * T, float(np.mean(launch_ms)), props.multi_processor_count, sm_max)
+        rf = roofline(sim_days[0] / args.steps, float(np.mean(launch_ms)), props.multi_processor_count, sm_max)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -306,6 +313,9 @@ def main():
                        "parallelism": "dp%d" % world, "l2": "flushed between steps (256 MiB write)",
                        "eps": eps, "seed": seed},
             "sims_days_per_s": sims_per_step * T / (ms_per_step * 1e-3),
+            "simulated_days_per_step": sim_days[0] / args.steps,
+            "early_rejection": "samples whose running distance^2 exceeds eps^2 stop early; sims_days_per_s counts "
+                               "n_samples * T, simulated_days_per_step the days actually run",
             "accepted_per_step": accepted / args.steps,
             "acceptance": accepted / (args.steps * sims_per_step),
             "launch_ms_mean": float(np.mean(launch_ms)),

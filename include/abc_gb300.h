@@ -78,8 +78,10 @@ typedef enum {
  * a canonical order). If more than `capacity` samples are accepted the call
  * returns ABC_ERR_CAPACITY, *n_accepted holds the true count and the output
  * buffers hold an unspecified subset of `capacity` accepted samples.
- * Uses a small amount of device scratch memory (the observed series and one
- * counter) allocated stream-ordered on cuda_stream and freed before returning.
+ * Samples whose running distance^2 exceeds eps^2 are abandoned early (partial
+ * sums only grow); the result is that of simulating all T days of every sample.
+ * Uses a small amount of device scratch memory (the observed series and three
+ * counters) allocated stream-ordered on cuda_stream and freed before returning.
  * Requires eps >= 0 (not NaN) and first_index + n_samples < 2^64. */
 abc_status abc_sample(const abc_prior_box* prior, const int32_t* observed, int32_t T,
                       int64_t N_pop, double eps, uint64_t n_samples, uint64_t seed,
@@ -127,6 +129,13 @@ abc_status abc_step(const float* theta, const int32_t* state_in, const uint64_t*
  * scratch (a histogram) allocated stream-ordered and freed before returning. */
 abc_status abc_kth_smallest(const double* dist, uint64_t n, uint64_t k, double* eps_out,
                             void* cuda_stream);
+
+/* Number of model days simulated by the last successful abc_sample call on
+ * this thread. abc_sample stops simulating a sample once its running distance^2
+ * exceeds eps^2 (the partial sums only grow, so it could not be accepted); the
+ * accept set is the same as simulating all T days of every sample. This count is
+ * the work actually done: at most n_samples * T. */
+uint64_t abc_last_simulated_days(void);
 
 /* Static description of a status code. */
 const char* abc_strerror(abc_status status);

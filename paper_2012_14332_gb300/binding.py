@@ -22,7 +22,7 @@ PAPER_LO = (0.0,) * 8
 PAPER_HI = (1.0, 100.0, 2.0, 1.0, 1.0, 1.0, 1.0, 2.0)   # Sec. 2.1, Eq. 2
 
 EXPORTED = ("abc_sample", "abc_distances", "abc_simulate", "abc_step", "abc_kth_smallest", "abc_strerror",
-            "abc_last_error", "abc_version")
+            "abc_last_error", "abc_version", "abc_last_simulated_days")
 
 
 class AbcPriorBox(ctypes.Structure):
@@ -69,6 +69,8 @@ def load(path=None):
         L.abc_last_error.argtypes = []
         L.abc_last_error.restype = ctypes.c_char_p
         L.abc_version.restype = ctypes.c_int
+        L.abc_last_simulated_days.argtypes = []
+        L.abc_last_simulated_days.restype = ctypes.c_uint64
         if path is None:
             _lib = L
         return L
@@ -220,3 +222,8 @@ def abc_strerror(status):
 
 def abc_version():
     return load().abc_version()
+
+
+def abc_last_simulated_days():
+    """Model days simulated by the last abc_sample call on this thread."""
+    return int(load().abc_last_simulated_days())

@@ -15,6 +15,7 @@
 namespace {
 
 thread_local std::string g_last_error;
+thread_local uint64_t g_last_sim_days = 0;
 
 abc_status fail(abc_status st, const char* fmt, ...)
 {
@@ -196,12 +197,15 @@ abc_status abc_sample(const abc_prior_box* prior, const int32_t* observed, int32
     std::vector<int4> obs;
     if ((st = pack_observed(observed, T, N_pop, obs)) != ABC_OK) return st;
     *n_accepted = 0;
+    g_last_sim_days = 0;
     if (n_samples == 0) return ok();
 
     const int32_t ard0[3] = {obs[0].x, obs[0].y, obs[0].z};
     const abcgb::ModelParams p = make_params(prior, T, N_pop, seed, stream, ard0);
     cudaStream_t s = (cudaStream_t)cuda_stream;
 
+    // scratch: the observed series, then three counters (accepts, claimed
+    // indices, simulated days)
     const size_t obs_bytes = round_up(sizeof(int4) * obs.size(), 256);
     Scratch sc;
     if ((st = alloc_scratch(sc, obs_bytes + 256, s)) != ABC_OK) return st;
@@ -209,7 +213,7 @@ abc_status abc_sample(const abc_prior_box* prior, const int32_t* observed, int32
     unsigned long long* count_d = (unsigned long long*)((char*)sc.ptr + obs_bytes);
     CUDA_TRY(cudaMemcpyAsync(obs_d, obs.data(), sizeof(int4) * obs.size(), cudaMemcpyHostToDevice, s),
              "cudaMemcpyAsync(observed)");
-    CUDA_TRY(cudaMemsetAsync(count_d, 0, sizeof(unsigned long long), s), "cudaMemsetAsync(count)");
+    CUDA_TRY(cudaMemsetAsync(count_d, 0, 3 * sizeof(unsigned long long), s), "cudaMemsetAsync(counters)");
 
     abcgb::RejectArgs a;
     a.obs = obs_d;
@@ -217,15 +221,20 @@ abc_status abc_sample(const abc_prior_box* prior, const int32_t* observed, int32
     a.n_samples = n_samples;
     a.acc_max = acc_threshold(eps);
     a.count = count_d;
+    a.next = count_d + 1;
+    a.sim_days = count_d + 2;
     a.capacity = capacity;
     a.theta_out = theta_out;
     a.dist_out = dist_out;
     a.idx_out = idx_out;
     if (injected("launch")) return fail(ABC_ERR_CUDA, "kernel launch failed (injected)");
     CUDA_TRY(abcgb::launch_reject(p, a, mode == ABC_FAST, s, nullptr), "abc_reject_kernel launch");
-    unsigned long long count = 0;
-    CUDA_TRY(cudaMemcpyAsync(&count, count_d, sizeof count, cudaMemcpyDeviceToHost, s), "cudaMemcpyAsync(count)");
+    unsigned long long counters[3] = {0, 0, 0};
+    CUDA_TRY(cudaMemcpyAsync(counters, count_d, sizeof counters, cudaMemcpyDeviceToHost, s),
+             "cudaMemcpyAsync(counters)");
     CUDA_TRY(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+    const unsigned long long count = counters[0];
+    g_last_sim_days = counters[2];
     *n_accepted = count;
     if (count > capacity)
         return fail(ABC_ERR_CAPACITY, "%llu samples accepted, capacity %llu", count, (unsigned long long)capacity);
@@ -356,6 +365,8 @@ const char* abc_strerror(abc_status status)
 }
 
 const char* abc_last_error(void) { return g_last_error.c_str(); }
+
+uint64_t abc_last_simulated_days(void) { return g_last_sim_days; }
 
 int abc_version(void) { return 100; }
 

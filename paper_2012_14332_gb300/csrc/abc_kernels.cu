@@ -18,45 +18,140 @@ __device__ __forceinline__ void stage_observed(int4* obs_s, const int4* __restri
 }
 
 // ---------------------------------------------------------------------------
-// K1: fused rejection. Grid-stride over the sample range in whole blocks so
-// every lane of every warp reaches the ballot; lanes past the end simulate a
-// valid index and are never accepted.
+// K1: fused rejection with early rejection and lane refill.
+//
+// The partial sums of the distance^2 only grow, so a sample whose running sum
+// exceeds acc_max after some day pair can never be accepted: its lane drops it
+// and takes the next sample (the accept set and the accepted distances are
+// exactly those of running every sample for all T days). Each warp keeps a
+// 64-entry ring of prior draws in shared memory, refilled 32 at a time by the
+// whole warp (sample indices claimed with one atomicAdd per 32), so the theta
+// draw of a new sample costs one shared-memory read for the lane that needs
+// it. The loop advances every active lane by one day pair; all ring
+// bookkeeping is warp-uniform. Accepted samples are compacted with a ballot
+// and one atomicAdd per warp; their theta is re-drawn from the index.
 // ---------------------------------------------------------------------------
-template <int MODE>
+constexpr int kRing = 64;
+constexpr int kWarpsPerBlock = kBlockThreads / 32;
+
+struct WarpRing {
+    float4 lo[kRing];     // theta0..3
+    float4 hi[kRing];     // theta4..7
+    uint64_t idx[kRing];  // sample index
+};
+
+template <int MODE, bool BELOW62>
 __global__ void __launch_bounds__(kBlockThreads) abc_reject_kernel(const __grid_constant__ ModelParams p,
                                                                    const __grid_constant__ RejectArgs a)
 {
     extern __shared__ int4 obs_s[];
     stage_observed(obs_s, a.obs, p.T);
+    WarpRing* rings = reinterpret_cast<WarpRing*>(obs_s + (p.T + 1));
     const uint32_t lane = threadIdx.x & 31u;
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x; base < a.n_samples; base += stride) {
-        const uint64_t j = base + threadIdx.x;
-        const bool valid = j < a.n_samples;
-        const uint64_t i = a.first_index + (valid ? j : a.n_samples - 1);
-        float th[8];
-        prior_draw(p, i, th);
-        const Theta t = make_theta<MODE>(th);
-        const State x0 = init_state(t, p.A0, p.R0, p.D0, p.room0);
-        const uint64_t acc = simulate_sample<MODE>(p, i, t, x0, obs_s, NoVisit());
-        const bool accept = valid && acc <= a.acc_max;
+    WarpRing& ring = rings[threadIdx.x >> 5];
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    const int32_t T = p.T;
+
+    bool active = false;
+    uint64_t i = 0, acc = 0;
+    uint32_t k = 0, days = 0;
+    Theta t;
+    State x;
+    uint32_t head = 0, tail = 0;     // ring entries consumed / produced (warp-uniform)
+    bool exhausted = false;          // no indices left to claim (warp-uniform)
+
+    while (true) {
+        const uint32_t idle = __ballot_sync(0xFFFFFFFFu, !active);
+        if (idle) {
+            const uint32_t need = __popc(idle);
+            if (tail - head < need && !exhausted) {
+                unsigned long long base = 0;
+                if (lane == 0) base = atomicAdd(a.next, 32ull);
+                base = __shfl_sync(0xFFFFFFFFu, base, 0);
+                if (base >= a.n_samples) {
+                    exhausted = true;
+                } else {
+                    const uint64_t left = a.n_samples - base;
+                    const uint32_t made = left < 32 ? (uint32_t)left : 32u;
+                    if (lane < made) {
+                        const uint64_t ii = a.first_index + base + lane;
+                        float th[8];
+                        prior_draw(p, ii, th);
+                        const uint32_t slot = (tail + lane) & (kRing - 1);
+                        ring.lo[slot] = make_float4(th[0], th[1], th[2], th[3]);
+                        ring.hi[slot] = make_float4(th[4], th[5], th[6], th[7]);
+                        ring.idx[slot] = ii;
+                    }
+                    tail += made;
+                    if (made < 32 || base + 32 >= a.n_samples) exhausted = true;
+                    __syncwarp();
+                }
+            }
+            const uint32_t avail = tail - head;
+            if (!active) {
+                const uint32_t rank = __popc(idle & lt_mask);
+                if (rank < avail) {
+                    const uint32_t slot = (head + rank) & (kRing - 1);
+                    const float4 l = ring.lo[slot], h = ring.hi[slot];
+                    const float th[8] = {l.x, l.y, l.z, l.w, h.x, h.y, h.z, h.w};
+                    i = ring.idx[slot];
+                    t = make_theta<MODE>(th, p.inv_p);
+                    x = init_state(t, p.A0, p.R0, p.D0, p.room0);
+                    acc = 0;
+                    k = 1;
+                    active = true;
+                }
+            }
+            head += need < avail ? need : avail;
+            __syncwarp();
+        }
+        if (__ballot_sync(0xFFFFFFFFu, active) == 0) break;
+
+        bool accept = false;
+        if (active) {
+            float z[10];
+            day_pair_normals<MODE>(p, i, k, z);
+            const int32_t d1 = (int32_t)(2 * k - 1);
+            model_day<MODE>(x, t, p.inv_p, z);
+            acc = BELOW62 ? add_day_sq_below62(acc, x, obs_s[d1]) : add_day_sq(acc, x, obs_s[d1]);
+            if (d1 < T) {
+                model_day<MODE>(x, t, p.inv_p, z + 5);
+                acc = BELOW62 ? add_day_sq_below62(acc, x, obs_s[d1 + 1]) : add_day_sq(acc, x, obs_s[d1 + 1]);
+                days += 2;
+            } else {
+                days += 1;
+            }
+            const bool over = acc > a.acc_max;
+            const bool last = d1 + 1 >= T;
+            accept = !over && last;
+            active = !(over || last);
+            ++k;
+        }
         const uint32_t mask = __ballot_sync(0xFFFFFFFFu, accept);
-        if (mask == 0) continue;
-        const uint32_t leader = __ffs(mask) - 1;
-        unsigned long long slot0 = 0;
-        if (lane == leader) slot0 = atomicAdd(a.count, (unsigned long long)__popc(mask));
-        slot0 = __shfl_sync(0xFFFFFFFFu, slot0, leader);
-        if (accept) {
-            const uint64_t slot = slot0 + __popc(mask & ((1u << lane) - 1u));
-            if (slot < a.capacity) {
-                a.idx_out[slot] = i;
-                a.dist_out[slot] = __dsqrt_rn(__ull2double_rn(acc));
-                float4* to = reinterpret_cast<float4*>(a.theta_out + 8 * slot);
-                to[0] = make_float4(th[0], th[1], th[2], th[3]);
-                to[1] = make_float4(th[4], th[5], th[6], th[7]);
+        if (mask) {
+            const uint32_t leader = __ffs(mask) - 1;
+            unsigned long long slot0 = 0;
+            if (lane == leader) slot0 = atomicAdd(a.count, (unsigned long long)__popc(mask));
+            slot0 = __shfl_sync(0xFFFFFFFFu, slot0, leader);
+            if (accept) {
+                const uint64_t slot = slot0 + __popc(mask & lt_mask);
+                if (slot < a.capacity) {
+                    float th[8];
+                    prior_draw(p, i, th);
+                    a.idx_out[slot] = i;
+                    a.dist_out[slot] = __dsqrt_rn(__ull2double_rn(acc));
+                    float4* to = reinterpret_cast<float4*>(a.theta_out + 8 * slot);
+                    to[0] = make_float4(th[0], th[1], th[2], th[3]);
+                    to[1] = make_float4(th[4], th[5], th[6], th[7]);
+                }
             }
         }
     }
+    // simulated model days of this warp (for throughput accounting)
+    unsigned long long d = days;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) d += __shfl_down_sync(0xFFFFFFFFu, d, off);
+    if (lane == 0 && a.sim_days) atomicAdd(a.sim_days, d);
 }
 
 // ---------------------------------------------------------------------------
@@ -73,7 +168,7 @@ __global__ void __launch_bounds__(kBlockThreads) abc_distance_kernel(const __gri
         const uint64_t i = a.first_index + j;
         float th[8];
         prior_draw(p, i, th);
-        const Theta t = make_theta<MODE>(th);
+        const Theta t = make_theta<MODE>(th, p.inv_p);
         const State x0 = init_state(t, p.A0, p.R0, p.D0, p.room0);
         const uint64_t acc = simulate_sample<MODE>(p, i, t, x0, obs_s, NoVisit());
         a.dist_out[j] = __dsqrt_rn(__ull2double_rn(acc));
@@ -112,7 +207,7 @@ __global__ void __launch_bounds__(kBlockThreads) abc_simulate_kernel(const __gri
         const float4 t0 = ti[0], t1 = ti[1];
         th[0] = t0.x; th[1] = t0.y; th[2] = t0.z; th[3] = t0.w;
         th[4] = t1.x; th[5] = t1.y; th[6] = t1.z; th[7] = t1.w;
-        const Theta t = make_theta<MODE>(th);
+        const Theta t = make_theta<MODE>(th, p.inv_p);
         const State x0 = init_state(t, p.A0, p.R0, p.D0, p.room0);
         TrajVisit v{a.traj_out + (size_t)b * 6 * (size_t)(p.T + 1)};
         v(0, x0);
@@ -131,7 +226,7 @@ __global__ void __launch_bounds__(kBlockThreads) abc_step_kernel(const __grid_co
     for (uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; b < a.B; b += stride) {
         float th[8];
         for (int j = 0; j < 8; ++j) th[j] = a.theta[8 * b + j];
-        const Theta t = make_theta<MODE>(th);
+        const Theta t = make_theta<MODE>(th, p.inv_p);
         const int32_t* si = a.state_in + 6 * b;
         State x{si[0], si[1], si[2], si[3], si[4], si[5]};
         const int32_t d = a.day[b];
@@ -195,20 +290,30 @@ static int blocks_for(uint64_t n, int cap)
     return (int)(b < (uint64_t)cap ? (b > 0 ? b : 1) : (uint64_t)cap);
 }
 
+size_t reject_smem_bytes(int32_t T) { return sizeof(int4) * (size_t)(T + 1) + sizeof(WarpRing) * kWarpsPerBlock; }
+
+template <int MODE, bool BELOW62>
+static cudaError_t launch_reject_t(const ModelParams& p, const RejectArgs& a, cudaStream_t s, int* blocks_out)
+{
+    const size_t smem = reject_smem_bytes(p.T);
+    int grid = 0;
+    cudaError_t e = grid_for(abc_reject_kernel<MODE, BELOW62>, smem, &grid);
+    if (e != cudaSuccess) return e;
+    // persistent: every resident block loops over claimed index chunks
+    const uint64_t chunks = (a.n_samples + 31) / 32;
+    const uint64_t want = (chunks + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    if (want < (uint64_t)grid) grid = (int)(want > 0 ? want : 1);
+    if (blocks_out) *blocks_out = grid;
+    abc_reject_kernel<MODE, BELOW62><<<grid, kBlockThreads, smem, s>>>(p, a);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_reject(const ModelParams& p, const RejectArgs& a, bool fast, cudaStream_t s, int* blocks_out)
 {
-    const size_t smem = sizeof(int4) * (size_t)(p.T + 1);
-    int grid = 0;
-    cudaError_t e = fast ? grid_for(abc_reject_kernel<kFast>, smem, &grid)
-                         : grid_for(abc_reject_kernel<kExact>, smem, &grid);
-    if (e != cudaSuccess) return e;
-    grid = blocks_for(a.n_samples, grid);
-    if (blocks_out) *blocks_out = grid;
+    const bool below62 = a.acc_max < 0x4000000000000000ull;
     if (fast)
-        abc_reject_kernel<kFast><<<grid, kBlockThreads, smem, s>>>(p, a);
-    else
-        abc_reject_kernel<kExact><<<grid, kBlockThreads, smem, s>>>(p, a);
-    return cudaGetLastError();
+        return below62 ? launch_reject_t<kFast, true>(p, a, s, blocks_out) : launch_reject_t<kFast, false>(p, a, s, blocks_out);
+    return below62 ? launch_reject_t<kExact, true>(p, a, s, blocks_out) : launch_reject_t<kExact, false>(p, a, s, blocks_out);
 }
 
 cudaError_t launch_distances(const ModelParams& p, const DistanceArgs& a, bool fast, cudaStream_t s)

@@ -14,7 +14,9 @@ struct RejectArgs {
     const int4* obs;              // device [T+1] (A, R, D, 0)
     uint64_t first_index, n_samples;
     uint64_t acc_max;             // accept iff distance^2 <= acc_max
-    unsigned long long* count;    // device counter, zeroed before launch
+    unsigned long long* count;    // device counter of accepts, zeroed before launch
+    unsigned long long* next;     // device counter of claimed indices, zeroed before launch
+    unsigned long long* sim_days; // device counter of simulated days (zeroed) or null
     uint64_t capacity;
     float* theta_out;             // device [capacity][8]
     double* dist_out;             // device [capacity]
@@ -45,6 +47,7 @@ struct StepArgs {
     int32_t* counts_out;          // device [B][5] or null
 };
 
+size_t reject_smem_bytes(int32_t T);
 cudaError_t launch_reject(const ModelParams& p, const RejectArgs& a, bool fast, cudaStream_t s, int* blocks_out);
 cudaError_t launch_distances(const ModelParams& p, const DistanceArgs& a, bool fast, cudaStream_t s);
 cudaError_t launch_simulate(const ModelParams& p, const SimulateArgs& a, bool fast, cudaStream_t s);

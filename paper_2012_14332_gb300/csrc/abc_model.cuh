@@ -172,12 +172,14 @@ __device__ __forceinline__ void sincospix(float v, float& s_out, float& c_out)
 // Fast mode: the SFU (MUFU) approximations and FMA.
 // ---------------------------------------------------------------------------
 namespace fast {
-__device__ __forceinline__ float lg2(float x) { float y; asm("lg2.approx.f32 %0, %1;" : "=f"(y) : "f"(x)); return y; }
-__device__ __forceinline__ float ex2(float x) { float y; asm("ex2.approx.f32 %0, %1;" : "=f"(y) : "f"(x)); return y; }
-__device__ __forceinline__ float sqrt_a(float x) { float y; asm("sqrt.approx.f32 %0, %1;" : "=f"(y) : "f"(x)); return y; }
-__device__ __forceinline__ float rcp(float x) { float y; asm("rcp.approx.f32 %0, %1;" : "=f"(y) : "f"(x)); return y; }
-__device__ __forceinline__ float sin_a(float x) { float y; asm("sin.approx.f32 %0, %1;" : "=f"(y) : "f"(x)); return y; }
-__device__ __forceinline__ float cos_a(float x) { float y; asm("cos.approx.f32 %0, %1;" : "=f"(y) : "f"(x)); return y; }
+// flush-to-zero forms: the sampler's inputs are never subnormal (u >= 2^-24,
+// counts are integers), and .ftz spares the subnormal fix-up code.
+__device__ __forceinline__ float lg2(float x) { float y; asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x)); return y; }
+__device__ __forceinline__ float ex2(float x) { float y; asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x)); return y; }
+__device__ __forceinline__ float sqrt_a(float x) { float y; asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x)); return y; }
+__device__ __forceinline__ float rcp(float x) { float y; asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x)); return y; }
+__device__ __forceinline__ float sin_a(float x) { float y; asm("sin.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x)); return y; }
+__device__ __forceinline__ float cos_a(float x) { float y; asm("cos.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x)); return y; }
 }  // namespace fast
 
 // One Box-Muller pair: r = sqrt(-2 ln u1), (z0, z1) = r (cos, sin)(2 pi u2).
@@ -185,8 +187,8 @@ template <int MODE>
 __device__ __forceinline__ void box_muller(uint32_t w_radius, uint32_t w_angle, float& z0, float& z1)
 {
     const float u1 = uniform01(w_radius);
-    const float u2 = uniform01(w_angle);
     if (MODE == kExact) {
+        const float u2 = uniform01(w_angle);
         const float r = __fsqrt_rn(__fmul_rn(exact::kNeg2Ln2, exact::log2x(u1)));
         float s, c;
         exact::sincospix(__fmul_rn(u2, 2.0f), s, c);
@@ -194,8 +196,10 @@ __device__ __forceinline__ void box_muller(uint32_t w_radius, uint32_t w_angle, 
         z1 = __fmul_rn(r, s);
     } else {
         const float r = fast::sqrt_a(-0x1.62e430p+0f * fast::lg2(u1));
-        // angle 2 pi u2 = 2 pi (u2 - 1/2) + pi: centred for the SFU's best range
-        const float a = 6.28318530717958647692f * (u2 - 0.5f);
+        // angle 2 pi u2 = 2 pi (u2 - 1/2) + pi, centred on 0 for the SFU; one FMA
+        // from the word's mantissa bits b in [1, 2): u2 - 1/2 = b - (3/2 - 2^-24)
+        const float b = __uint_as_float((w_angle & 0x007FFFFFu) | 0x3F800000u);
+        const float a = __fmaf_rn(b, 6.28318530717958647692f, -9.42477758f);
         z0 = -r * fast::cos_a(a);
         z1 = -r * fast::sin_a(a);
     }
@@ -225,10 +229,13 @@ __device__ __forceinline__ void prior_draw(const ModelParams& p, uint64_t i, flo
     for (int j = 0; j < 8; ++j) th[j] = __fadd_rn(p.lo[j], __fmul_rn(p.width[j], uniform01(w[j])));
 }
 
-// n = min(max(floor x, 0), c): cvt.rmi saturates to int32 and maps NaN to 0.
+// n = min(max(floor x, 0), c): cvt.rmi saturates to int32 and maps NaN to 0;
+// for c >= 0, min.relu(f, c) = max(min(f, c), 0) is the same clamp.
 __device__ __forceinline__ int32_t clamp_count(float x, int32_t c)
 {
-    return min(max(__float2int_rd(x), 0), c);
+    int32_t n;
+    asm("min.relu.s32 %0, %1, %2;" : "=r"(n) : "r"(__float2int_rd(x)), "r"(c));
+    return n;
 }
 
 // ---------------------------------------------------------------------------
@@ -238,13 +245,19 @@ struct Theta {
     float a0, a, n, beta, gamma, delta, beta_eta, kappa;
 };
 
+// Exact mode keeps the paper's factors; fast mode folds 1/P into alpha0 and
+// alpha (g/P = alpha0/P + (alpha/P) / (1 + U^n)), saving a multiply per day.
 template <int MODE>
-__device__ __forceinline__ Theta make_theta(const float th[8])
+__device__ __forceinline__ Theta make_theta(const float th[8], float inv_p)
 {
     Theta t;
     t.a0 = th[0]; t.a = th[1]; t.n = th[2]; t.beta = th[3]; t.gamma = th[4]; t.delta = th[5];
     t.beta_eta = __fmul_rn(th[3], th[6]);
     t.kappa = th[7];
+    if (MODE == kFast) {
+        t.a0 = th[0] * inv_p;
+        t.a = th[1] * inv_p;
+    }
     return t;
 }
 
@@ -285,8 +298,8 @@ __device__ __forceinline__ void model_day(State& x, const Theta& t, float inv_p,
         v4 = __fadd_rn(h4, __fmul_rn(__fsqrt_rn(h4), z[4]));
     } else {
         const float pw = (U != 0) ? fast::ex2(t.n * fast::lg2(__int2float_rn(U))) : 0.0f;
-        const float g = __fmaf_rn(t.a, fast::rcp(1.0f + pw), t.a0);
-        h0 = g * Sf * If * inv_p;
+        const float g_over_p = __fmaf_rn(t.a, fast::rcp(1.0f + pw), t.a0);   // a0, a carry 1/P
+        h0 = (g_over_p * Sf) * If;
         h1 = t.gamma * If;
         h2 = t.beta * Af;
         h3 = t.delta * Af;
@@ -312,6 +325,20 @@ __device__ __forceinline__ void model_day(State& x, const Theta& t, float inv_p,
     if (n_out) {
         n_out[0] = n_si; n_out[1] = n_ia; n_out[2] = n_ar; n_out[3] = n_ad; n_out[4] = n_iu;
     }
+}
+
+// Distance^2 accumulation of one day when only "acc <= acc_max < 2^62" and the
+// exact value of accepted samples matter: clamp the running sum at 2^62 before
+// adding the three squares (each < 2^62, so no wrap). Every partial sum of an
+// accepted sample is <= acc_max < 2^62, so its sum is never clamped.
+__device__ __forceinline__ uint64_t add_day_sq_below62(uint64_t acc, const State& x, int4 obs)
+{
+    const int32_t dA = x.A - obs.x, dR = x.R - obs.y, dD = x.D - obs.z;
+    acc = acc < 0x4000000000000000ull ? acc : 0x4000000000000000ull;
+    acc += (uint64_t)((int64_t)dA * dA);
+    acc += (uint64_t)((int64_t)dR * dR);
+    acc += (uint64_t)((int64_t)dD * dD);
+    return acc;
 }
 
 // Saturating distance^2 accumulation of one day: three exact squares summed in

@@ -209,6 +209,11 @@ def test_edge_cases():
     theta, dist, idx, n_acc = abc.abc_sample(obs, P, 1e30, 3000, 9, mode="exact", capacity=100, allow_overflow=True)
     assert n_acc == 3000 and theta.shape[0] == 100
     assert len(set(idx.cpu().numpy().tolist())) == 100
+    # nothing is rejected early when everything is accepted
+    assert abc.abc_last_simulated_days() == 3000 * w["T"]
+    # early rejection simulates fewer days, never more
+    abc.abc_sample(obs, P, w["eps"], 3000, 9, mode="exact")
+    assert 0 < abc.abc_last_simulated_days() < 3000 * w["T"]
     # capacity zero with accepts
     _, _, _, n_acc = abc.abc_sample(obs, P, 1e30, 50, 9, mode="exact", capacity=0, allow_overflow=True)
     assert n_acc == 50
