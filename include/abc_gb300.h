@@ -130,6 +130,32 @@ abc_status abc_step(const float* theta, const int32_t* state_in, const uint64_t*
 abc_status abc_kth_smallest(const double* dist, uint64_t n, uint64_t k, double* eps_out,
                             void* cuda_stream);
 
+/* Variant of abc_sample that allocates no memory. It is for callers that must
+ * not allocate device memory while sampling: code running inside a host
+ * framework that owns the GPU's memory pool and forbids other allocators, or
+ * services that allocate everything once at start-up and must not allocate
+ * (or risk an out-of-memory failure) in their steady state. It has no
+ * counterpart in the paper; it only changes where the scratch memory comes from.
+ *
+ * Arguments, outputs, errors and results are those of abc_sample (the same
+ * kernel runs), for T <= ABC_NOALLOC_T_MAX; a larger T returns
+ * ABC_ERR_INVALID_ARG. The scratch (three counters and the observed series) is
+ * a fixed ABC_NOALLOC_SCRATCH_BYTES array of device memory declared at file
+ * scope in this library, so every GPU that loads the library holds it until the
+ * process exits. The first call on each device looks up that array's device
+ * address with the device current (a one-time set-up done by that call); make
+ * the first call on a device before any stream capture. All calls share the one
+ * array and each call zeroes the counters it uses: calls that overlap on the GPU
+ * (different streams or host threads) race on it and must be serialized by the
+ * caller. Calls no cudaMalloc, cudaMallocAsync or cudaFree. */
+#define ABC_NOALLOC_T_MAX 1024
+#define ABC_NOALLOC_SCRATCH_BYTES (256 + 16 * (ABC_NOALLOC_T_MAX + 1))
+abc_status abc_sample_noalloc(const abc_prior_box* prior, const int32_t* observed, int32_t T,
+                              int64_t N_pop, double eps, uint64_t n_samples, uint64_t seed,
+                              uint32_t stream, abc_mode mode, uint64_t first_index,
+                              float* theta_out, double* dist_out, uint64_t* idx_out,
+                              uint64_t capacity, uint64_t* n_accepted, void* cuda_stream);
+
 /* Number of model days simulated by the last successful abc_sample call on
  * this thread. abc_sample stops simulating a sample once its running distance^2
  * exceeds eps^2 (the partial sums only grow, so it could not be accepted); the

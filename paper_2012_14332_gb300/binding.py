@@ -22,7 +22,8 @@ PAPER_LO = (0.0,) * 8
 PAPER_HI = (1.0, 100.0, 2.0, 1.0, 1.0, 1.0, 1.0, 2.0)   # Sec. 2.1, Eq. 2
 
 EXPORTED = ("abc_sample", "abc_distances", "abc_simulate", "abc_step", "abc_kth_smallest", "abc_strerror",
-            "abc_last_error", "abc_version", "abc_last_simulated_days")
+            "abc_last_error", "abc_version", "abc_last_simulated_days", "abc_sample_noalloc")
+ABC_NOALLOC_T_MAX = 1024
 
 
 class AbcPriorBox(ctypes.Structure):
@@ -58,11 +59,13 @@ def load(path=None):
         box = ctypes.POINTER(AbcPriorBox)
         L.abc_sample.argtypes = [box, vp, i32, i64, ctypes.c_double, u64, u64, u32, ctypes.c_int, u64, vp, vp, vp,
                                  u64, ctypes.POINTER(ctypes.c_uint64), vp]
+        L.abc_sample_noalloc.argtypes = list(L.abc_sample.argtypes)
         L.abc_distances.argtypes = [box, vp, i32, i64, u64, u64, u32, ctypes.c_int, u64, vp, vp, vp]
         L.abc_simulate.argtypes = [vp, vp, u64, vp, i32, i64, u64, u32, ctypes.c_int, vp, vp]
         L.abc_step.argtypes = [vp, vp, vp, vp, u64, i64, u64, u32, ctypes.c_int, vp, vp, vp]
         L.abc_kth_smallest.argtypes = [vp, u64, u64, ctypes.POINTER(ctypes.c_double), vp]
-        for nm in ("abc_sample", "abc_distances", "abc_simulate", "abc_step", "abc_kth_smallest"):
+        for nm in ("abc_sample", "abc_sample_noalloc", "abc_distances", "abc_simulate", "abc_step",
+                   "abc_kth_smallest"):
             getattr(L, nm).restype = ctypes.c_int
         L.abc_strerror.argtypes = [ctypes.c_int]
         L.abc_strerror.restype = ctypes.c_char_p
@@ -152,6 +155,31 @@ def abc_sample(observed, N_pop, eps, n_samples, seed, stream=0, mode="fast", fir
                       _mode(mode), int(first_index), _dev(theta, torch.float32, (capacity, 8)),
                       _dev(dist, torch.float64, (capacity,)), _dev(idx, torch.int64, (capacity,)), int(capacity),
                       ctypes.byref(nacc), _stream(cuda_stream))
+    _check(L, st, allow=(ABC_ERR_CAPACITY,) if allow_overflow else ())
+    n = int(nacc.value)
+    m = min(n, capacity)
+    return theta[:m], dist[:m], idx[:m], n
+
+
+def abc_sample_noalloc(observed, N_pop, eps, n_samples, seed, out, stream=0, mode="fast", first_index=0,
+                       lo=PAPER_LO, hi=PAPER_HI, cuda_stream=None, allow_overflow=False):
+    """abc_sample for callers that cannot allocate device memory while sampling:
+    the library allocates nothing (its scratch is a fixed device array) and the
+    caller passes the output buffers out = (theta [cap, 8] f32, dist [cap] f64,
+    idx [cap] int64) it allocated up front. T <= ABC_NOALLOC_T_MAX; calls that
+    overlap on the GPU race on the shared scratch and must be serialized.
+    Returns (theta, dist, idx, n_accepted) views like abc_sample."""
+    L = load()
+    obs, obs_p = _host_i32(observed)
+    T = obs.shape[1] - 1
+    theta, dist, idx = out
+    capacity = theta.shape[0]
+    nacc = ctypes.c_uint64(0)
+    b = prior_box(lo, hi)
+    st = L.abc_sample_noalloc(ctypes.byref(b), obs_p, T, int(N_pop), float(eps), int(n_samples), int(seed),
+                              int(stream), _mode(mode), int(first_index), _dev(theta, torch.float32, (capacity, 8)),
+                              _dev(dist, torch.float64, (capacity,)), _dev(idx, torch.int64, (capacity,)),
+                              int(capacity), ctypes.byref(nacc), _stream(cuda_stream))
     _check(L, st, allow=(ABC_ERR_CAPACITY,) if allow_overflow else ())
     n = int(nacc.value)
     m = min(n, capacity)

@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -174,6 +175,41 @@ abc_status alloc_scratch(Scratch& sc, size_t bytes, cudaStream_t s)
 }
 
 size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+}  // namespace
+
+// Scratch of abc_sample_noalloc: bytes [0, 24) hold the three counters
+// (accepts, claimed indices, simulated days), bytes [256, 256 + 16 (T+1)) the
+// observed series. Host code must not pass this name to a kernel (on the host
+// it is a stand-in, not a device address); noalloc_scratch() returns the
+// device address.
+static __device__ __align__(256) unsigned char abc_noalloc_scratch[ABC_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int kNoallocMaxDevices = 256;
+
+struct NoallocDevice {
+    std::once_flag once;
+    void* ptr = nullptr;
+    cudaError_t err = cudaSuccess;
+};
+
+NoallocDevice g_noalloc_devices[kNoallocMaxDevices];
+
+// Device address of abc_noalloc_scratch on the current device, looked up once
+// per device (with that device current) and kept for the life of the process.
+abc_status noalloc_scratch(void** out)
+{
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev), "cudaGetDevice");
+    if (dev < 0 || dev >= kNoallocMaxDevices) return fail(ABC_ERR_INVALID_ARG, "device ordinal %d too large", dev);
+    NoallocDevice& d = g_noalloc_devices[dev];
+    std::call_once(d.once, [&d]() { d.err = cudaGetSymbolAddress(&d.ptr, abc_noalloc_scratch); });
+    if (d.err != cudaSuccess) return cuda_fail(d.err, "cudaGetSymbolAddress(abc_noalloc_scratch)");
+    *out = d.ptr;
+    return ABC_OK;
+}
 
 }  // namespace
 
@@ -348,6 +384,72 @@ abc_status abc_kth_smallest(const double* dist, uint64_t n, uint64_t k, double* 
         mask |= (uint64_t)0xFF << shift;
     }
     std::memcpy(eps_out, &prefix, sizeof prefix);
+    return ok();
+}
+
+abc_status abc_sample_noalloc(const abc_prior_box* prior, const int32_t* observed, int32_t T, int64_t N_pop,
+                              double eps, uint64_t n_samples, uint64_t seed, uint32_t stream, abc_mode mode,
+                              uint64_t first_index, float* theta_out, double* dist_out, uint64_t* idx_out,
+                              uint64_t capacity, uint64_t* n_accepted, void* cuda_stream)
+{
+    abc_status st;
+    if ((st = check_prior(prior)) != ABC_OK) return st;
+    if ((st = check_model(T, N_pop, stream)) != ABC_OK) return st;
+    if (T > ABC_NOALLOC_T_MAX)
+        return fail(ABC_ERR_INVALID_ARG, "T = %d exceeds the no-alloc scratch limit of %d days", T,
+                    ABC_NOALLOC_T_MAX);
+    if (mode != ABC_EXACT && mode != ABC_FAST) return fail(ABC_ERR_INVALID_ARG, "unknown mode %d", (int)mode);
+    if (!(eps >= 0.0)) return fail(ABC_ERR_INVALID_ARG, "eps must be >= 0 and not NaN");
+    if (!n_accepted) return fail(ABC_ERR_INVALID_ARG, "n_accepted is NULL");
+    if (capacity > 0 && (!theta_out || !dist_out || !idx_out))
+        return fail(ABC_ERR_INVALID_ARG, "output buffers are NULL");
+    if (n_samples > ~(uint64_t)0 - first_index)
+        return fail(ABC_ERR_INVALID_ARG, "first_index + n_samples overflows");
+    if (!observed) return fail(ABC_ERR_INVALID_ARG, "observed is NULL");
+    // the observed series, packed on the stack (no heap allocation either)
+    int4 obs[ABC_NOALLOC_T_MAX + 1];
+    for (int32_t d = 0; d <= T; ++d) {
+        const int32_t A = observed[d], R = observed[(T + 1) + d], D = observed[2 * (T + 1) + d];
+        if (A < 0 || R < 0 || D < 0) return fail(ABC_ERR_INVALID_ARG, "negative observed count on day %d", d);
+        obs[d] = make_int4(A, R, D, 0);
+    }
+    const int32_t ard0[3] = {obs[0].x, obs[0].y, obs[0].z};
+    if ((st = check_initial(ard0, N_pop)) != ABC_OK) return st;
+    *n_accepted = 0;
+    g_last_sim_days = 0;
+    if (n_samples == 0) return ok();
+
+    void* base = nullptr;
+    if ((st = noalloc_scratch(&base)) != ABC_OK) return st;
+    unsigned long long* count_d = (unsigned long long*)base;
+    int4* obs_d = (int4*)((char*)base + 256);
+    const abcgb::ModelParams p = make_params(prior, T, N_pop, seed, stream, ard0);
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    CUDA_TRY(cudaMemcpyAsync(obs_d, obs, sizeof(int4) * (size_t)(T + 1), cudaMemcpyHostToDevice, s),
+             "cudaMemcpyAsync(observed)");
+    CUDA_TRY(cudaMemsetAsync(count_d, 0, 3 * sizeof(unsigned long long), s), "cudaMemsetAsync(counters)");
+    abcgb::RejectArgs a;
+    a.obs = obs_d;
+    a.first_index = first_index;
+    a.n_samples = n_samples;
+    a.acc_max = acc_threshold(eps);
+    a.count = count_d;
+    a.next = count_d + 1;
+    a.sim_days = count_d + 2;
+    a.capacity = capacity;
+    a.theta_out = theta_out;
+    a.dist_out = dist_out;
+    a.idx_out = idx_out;
+    CUDA_TRY(abcgb::launch_reject(p, a, mode == ABC_FAST, s, nullptr), "abc_reject_kernel launch");
+    unsigned long long counters[3] = {0, 0, 0};
+    CUDA_TRY(cudaMemcpyAsync(counters, count_d, sizeof counters, cudaMemcpyDeviceToHost, s),
+             "cudaMemcpyAsync(counters)");
+    CUDA_TRY(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+    g_last_sim_days = counters[2];
+    *n_accepted = counters[0];
+    if (counters[0] > capacity)
+        return fail(ABC_ERR_CAPACITY, "%llu samples accepted, capacity %llu", counters[0],
+                    (unsigned long long)capacity);
     return ok();
 }
 
