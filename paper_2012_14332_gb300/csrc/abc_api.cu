@@ -174,7 +174,47 @@ abc_status alloc_scratch(Scratch& sc, size_t bytes, cudaStream_t s)
     return ABC_OK;
 }
 
-size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+// Per-thread, per-device scratch of abc_sample: device memory for the observed
+// series and counters, pinned host memory to stage them. Kept across calls and
+// grown when a longer series needs more; abc_sample synchronizes its stream
+// before returning, so the next call on this thread can reuse it.
+struct SampleScratch {
+    void* dev = nullptr;
+    void* host = nullptr;
+    size_t bytes = 0;
+};
+
+constexpr int kMaxCachedDevices = 64;
+thread_local SampleScratch g_sample_scratch[kMaxCachedDevices];
+
+abc_status sample_scratch(size_t bytes, SampleScratch** out)
+{
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev), "cudaGetDevice");
+    if (dev < 0 || dev >= kMaxCachedDevices) return fail(ABC_ERR_INVALID_ARG, "device ordinal %d too large", dev);
+    SampleScratch& sc = g_sample_scratch[dev];
+    if (sc.bytes < bytes) {
+        if (injected("alloc")) return fail(ABC_ERR_NOMEM, "scratch allocation failed (injected)");
+        if (sc.dev) cudaFree(sc.dev);
+        if (sc.host) cudaFreeHost(sc.host);
+        sc = SampleScratch();
+        void* d = nullptr;
+        void* h = nullptr;
+        CUDA_TRY(cudaMalloc(&d, bytes), "cudaMalloc(scratch)");
+        cudaError_t e = cudaMallocHost(&h, bytes);
+        if (e != cudaSuccess) {
+            cudaFree(d);
+            return cuda_fail(e, "cudaMallocHost(staging)");
+        }
+        sc.dev = d;
+        sc.host = h;
+        sc.bytes = bytes;
+    } else if (injected("alloc")) {
+        return fail(ABC_ERR_NOMEM, "scratch allocation failed (injected)");
+    }
+    *out = &sc;
+    return ABC_OK;
+}
 
 }  // namespace
 
@@ -240,16 +280,25 @@ abc_status abc_sample(const abc_prior_box* prior, const int32_t* observed, int32
     const abcgb::ModelParams p = make_params(prior, T, N_pop, seed, stream, ard0);
     cudaStream_t s = (cudaStream_t)cuda_stream;
 
-    // scratch: the observed series, then three counters (accepts, claimed
-    // indices, simulated days)
-    const size_t obs_bytes = round_up(sizeof(int4) * obs.size(), 256);
-    Scratch sc;
-    if ((st = alloc_scratch(sc, obs_bytes + 256, s)) != ABC_OK) return st;
-    int4* obs_d = (int4*)sc.ptr;
-    unsigned long long* count_d = (unsigned long long*)((char*)sc.ptr + obs_bytes);
-    CUDA_TRY(cudaMemcpyAsync(obs_d, obs.data(), sizeof(int4) * obs.size(), cudaMemcpyHostToDevice, s),
-             "cudaMemcpyAsync(observed)");
-    CUDA_TRY(cudaMemsetAsync(count_d, 0, 3 * sizeof(unsigned long long), s), "cudaMemsetAsync(counters)");
+    // scratch: three counters (accepts, claimed indices, simulated days), then
+    // the observed series; staged through pinned host memory
+    const size_t obs_off = 256;
+    SampleScratch* sc = nullptr;
+    if ((st = sample_scratch(obs_off + sizeof(int4) * obs.size(), &sc)) != ABC_OK) return st;
+    unsigned long long* count_h = (unsigned long long*)sc->host;
+    count_h[0] = count_h[1] = count_h[2] = 0;
+    std::memcpy((char*)sc->host + obs_off, obs.data(), sizeof(int4) * obs.size());
+    unsigned long long* count_d = (unsigned long long*)sc->dev;
+    int4* obs_d = (int4*)((char*)sc->dev + obs_off);
+    if (injected("launch")) return fail(ABC_ERR_CUDA, "kernel launch failed (injected)");
+    // from here on the pinned staging buffer may be in use by the stream: every
+    // error return first waits for the stream so the next call can reuse it
+    auto drain = [s](abc_status e) {
+        cudaStreamSynchronize(s);
+        return e;
+    };
+    cudaError_t ce = cudaMemcpyAsync(sc->dev, sc->host, obs_off + sizeof(int4) * obs.size(), cudaMemcpyHostToDevice, s);
+    if (ce != cudaSuccess) return drain(cuda_fail(ce, "cudaMemcpyAsync(observed, counters)"));
 
     abcgb::RejectArgs a;
     a.obs = obs_d;
@@ -263,14 +312,13 @@ abc_status abc_sample(const abc_prior_box* prior, const int32_t* observed, int32
     a.theta_out = theta_out;
     a.dist_out = dist_out;
     a.idx_out = idx_out;
-    if (injected("launch")) return fail(ABC_ERR_CUDA, "kernel launch failed (injected)");
-    CUDA_TRY(abcgb::launch_reject(p, a, mode == ABC_FAST, s, nullptr), "abc_reject_kernel launch");
-    unsigned long long counters[3] = {0, 0, 0};
-    CUDA_TRY(cudaMemcpyAsync(counters, count_d, sizeof counters, cudaMemcpyDeviceToHost, s),
-             "cudaMemcpyAsync(counters)");
+    ce = abcgb::launch_reject(p, a, mode == ABC_FAST, s, nullptr);
+    if (ce != cudaSuccess) return drain(cuda_fail(ce, "abc_reject_kernel launch"));
+    ce = cudaMemcpyAsync(count_h, count_d, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
+    if (ce != cudaSuccess) return drain(cuda_fail(ce, "cudaMemcpyAsync(counters)"));
     CUDA_TRY(cudaStreamSynchronize(s), "cudaStreamSynchronize");
-    const unsigned long long count = counters[0];
-    g_last_sim_days = counters[2];
+    const unsigned long long count = count_h[0];
+    g_last_sim_days = count_h[2];
     *n_accepted = count;
     if (count > capacity)
         return fail(ABC_ERR_CAPACITY, "%llu samples accepted, capacity %llu", count, (unsigned long long)capacity);

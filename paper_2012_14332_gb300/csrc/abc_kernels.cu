@@ -3,6 +3,9 @@
 // observed series in shared memory, the accepted samples compacted with a
 // warp ballot and one atomic per warp.
 #include <cstdint>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <cuda_runtime.h>
 
 #include "abc_kernels.h"
@@ -266,12 +269,27 @@ __global__ void __launch_bounds__(kBlockThreads) digit_histogram_kernel(const do
 // ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
+// Resident blocks per SM times the SM count, for a kernel, dynamic shared
+// memory size and device; looked up once and cached (the launch path then
+// makes no attribute or occupancy query).
 template <typename K>
 static cudaError_t grid_for(K kernel, size_t smem, int* grid)
 {
-    int dev = 0, sms = 0, per_sm = 0;
+    static std::mutex mu;
+    static std::map<std::tuple<const void*, int, size_t>, int> cache;
+    int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
+    const auto key = std::make_tuple((const void*)kernel, dev, smem);
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        auto it = cache.find(key);
+        if (it != cache.end()) {
+            *grid = it->second;
+            return cudaSuccess;
+        }
+    }
+    int sms = 0, per_sm = 0;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
     if (smem > 48 * 1024) {
@@ -281,6 +299,8 @@ static cudaError_t grid_for(K kernel, size_t smem, int* grid)
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kBlockThreads, smem);
     if (e != cudaSuccess) return e;
     *grid = sms * (per_sm > 0 ? per_sm : 1);
+    std::lock_guard<std::mutex> lock(mu);
+    cache[key] = *grid;
     return cudaSuccess;
 }
 
