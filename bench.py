@@ -130,6 +130,56 @@ def roofline(sim_days_per_launch, launch_ms, sm_count, sm_max_mhz):
                 sm_count, sm_max_mhz, clk_per_sim_day, bound_pipe)}
 
 
+BATCH_REGIONS = ["region_1e7_T60", "region_6e7_T90", "region_3p3e8_T120"]
+
+
+def bench_batched(abc, torch, steps, warmup, dev, flush, sm_count, sm_max):
+    """Three regions (P = 1e7, 6e7, 3.3e8; T = 60, 90, 120; own eps each; 2^22
+    prior samples per region) in one persistent launch per step, replayed from
+    a CUDA graph, launch shape from the autotuner."""
+    with open(os.path.join(ROOT, "tests", "golden", "workloads.json")) as f:
+        wl = json.load(f)
+    regs = []
+    for r, name in enumerate(BATCH_REGIONS):
+        w = wl[name]
+        regs.append(dict(observed=np.array(w["observed"], dtype=np.int32), N_pop=w["P"], eps=w["eps"],
+                         n_samples=w["n_samples"], first_index=0, stream=r, capacity=1 << 15))
+    plan = abc.Plan(regs, wl[BATCH_REGIONS[0]]["seed"], mode="fast")
+    s = torch.cuda.Stream(dev)
+    best, shapes = plan.tune(s)
+    with torch.cuda.stream(s):
+        for _ in range(warmup):
+            plan.run_graph(1, s)
+        s.synchronize()
+        plan.reset(s)
+        before = [plan.counts(r, s) for r in range(len(regs))]
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        r0.record(s)
+        for k in range(steps):
+            flush.fill_(k & 0xFF)
+            ev[k][0].record(s)
+            plan.run_graph(1, s)
+            ev[k][1].record(s)
+        r1.record(s)
+        s.synchronize()
+    counts = [plan.counts(r, s) for r in range(len(regs))]
+    plan.close()
+    acc = sum(c[0] for c in counts) - sum(b[0] for b in before)
+    days = sum(c[1] for c in counts) - sum(b[1] for b in before)
+    region_ms = r0.elapsed_time(r1)
+    launch_ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+    nominal = sum(g["n_samples"] * (g["observed"].shape[1] - 1) for g in regs)
+    return {"workload": "3 regions in one launch (" + ", ".join(
+                "%s eps=%g" % (n, wl[n]["eps"]) for n in BATCH_REGIONS) + "), 2^22 prior samples each, fast mode, "
+                "CUDA-graph replay, L2 flushed between steps",
+            "value": acc / (region_ms * 1e-3), "unit": UNIT, "ms_per_step": region_ms / steps,
+            "launch_ms_mean": launch_ms, "sims_days_per_s": nominal * steps / (region_ms * 1e-3),
+            "simulated_days_per_step": days / steps, "accepted_per_step": acc / steps,
+            "tuned_shape": best, "shapes_tried": shapes,
+            "roofline": roofline(days / steps, launch_ms, sm_count, sm_max)}
+
+
 def oracle_sample(w, n, first_index, threads=0):
     """The CPU oracle (exact arithmetic) on n samples of the workload."""
     import oracle
@@ -184,6 +234,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--samples", type=int, default=0,
                     help="samples per launch (profiling runs on a smaller case; not a benchmark value)")
     args = ap.parse_args()
@@ -328,6 +379,9 @@ def main():
         }
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(w)
+        if not args.no_batched and world == 1:
+            line["batched_regions"] = bench_batched(abc, torch, args.steps, args.warmup, dev, flush,
+                                                    props.multi_processor_count, sm_max)
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.barrier()

@@ -130,6 +130,92 @@ abc_status abc_step(const float* theta, const int32_t* state_in, const uint64_t*
 abc_status abc_kth_smallest(const double* dist, uint64_t n, uint64_t k, double* eps_out,
                             void* cuda_stream);
 
+/* ------------------------------------------------------------------------
+ * Batched regions (many regions, one persistent launch, CUDA-graph replay)
+ * ------------------------------------------------------------------------
+ * A plan holds up to ABC_MAX_REGIONS regions, each with its own observed
+ * series, population, horizon, eps, random stream, sample range and accepted
+ * buffers, and runs ABC rejection (the same method and results as abc_sample,
+ * region by region) over all of them in one kernel launch. The plan owns all
+ * device memory it needs; abc_plan_run allocates nothing and does not
+ * synchronize, so it can be captured in a CUDA graph (abc_plan_run_graph does
+ * that). Accepted samples accumulate in the plan's buffers across runs until
+ * abc_plan_reset. */
+#define ABC_MAX_REGIONS 32
+
+typedef struct {
+    const int32_t* observed; /* HOST int32 [3][T+1], rows A, R, D (copied at plan creation) */
+    int32_t T;               /* simulated days, 1..ABC_T_MAX */
+    int64_t N_pop;           /* population, 1 <= N_pop < 2^31 */
+    double eps;              /* tolerance, >= 0 */
+    uint64_t n_samples;      /* samples per run */
+    uint64_t first_index;    /* sample index of the first run; each run advances it by n_samples */
+    uint32_t stream;         /* RNG stream of this region (< 2^30) */
+    uint64_t capacity;       /* accepted samples kept by the plan for this region */
+    const float* theta_in;   /* DEVICE float [n_samples][8] proposals, or NULL to draw from the prior */
+} abc_region;
+
+typedef struct abc_plan_s* abc_plan;
+
+typedef struct {
+    int32_t block_threads;        /* 128, 256 or 512 */
+    int32_t pairs_per_iteration;  /* day pairs per loop iteration: 1 or 2 */
+    int32_t blocks_per_sm;        /* resident blocks per SM requested (0 = all that fit) */
+    float ms;                     /* measured time of one run with this shape */
+} abc_launch_shape;
+
+/* Create a plan for n_regions regions (1..ABC_MAX_REGIONS) sharing the prior
+ * box, the seed and the arithmetic mode. Allocates the plan's device memory
+ * (region table, observed series, counters, accepted buffers) on the current
+ * device and copies the observed series. The launch shape starts at 256
+ * threads, one day pair per iteration. */
+abc_status abc_plan_create(const abc_prior_box* prior, const abc_region* regions, int32_t n_regions,
+                           uint64_t seed, abc_mode mode, abc_plan* plan_out);
+
+/* Zero the accepted and simulated-day counters of every region (async). */
+abc_status abc_plan_reset(abc_plan plan, void* cuda_stream);
+
+/* One run: every region's n_samples samples from its current first_index, then
+ * each first_index advances by n_samples. Async on cuda_stream; no allocation,
+ * no synchronization; capturable in a CUDA graph. */
+abc_status abc_plan_run(abc_plan plan, void* cuda_stream);
+
+/* n_runs consecutive runs replayed from a CUDA graph that the plan captures
+ * on cuda_stream the first time it is called with this n_runs (cuda_stream
+ * must then be a non-default stream). Async. */
+abc_status abc_plan_run_graph(abc_plan plan, int32_t n_runs, void* cuda_stream);
+
+/* Autotuner: time one run with every launch shape the library is compiled
+ * for, keep the fastest, then restore the plan's sample ranges and counters.
+ * Synchronizes cuda_stream. shapes_out (HOST, may be NULL) receives up to
+ * max_shapes measured shapes; *best_out (may be NULL) the chosen one. */
+abc_status abc_plan_tune(abc_plan plan, void* cuda_stream, abc_launch_shape* shapes_out, int32_t max_shapes,
+                         int32_t* n_shapes_out, abc_launch_shape* best_out);
+
+/* Accepted samples of one region (synchronizes cuda_stream). *n_accepted is the
+ * count since the last reset (may exceed the capacity; the buffers then hold
+ * an unspecified subset of `capacity` of them); *simulated_days the model days
+ * simulated. theta_out/dist_out/idx_out receive the plan's DEVICE buffers
+ * ([capacity][8] float, [capacity] double, [capacity] uint64), owned by the
+ * plan and valid until abc_plan_destroy; any of the four may be NULL. */
+abc_status abc_plan_results(abc_plan plan, int32_t region, uint64_t* n_accepted, uint64_t* simulated_days,
+                            float** theta_out, double** dist_out, uint64_t** idx_out, void* cuda_stream);
+
+/* Copy min(count, accepted, capacity) accepted samples of one region into
+ * caller buffers (device or pinned host: cudaMemcpyDefault), async on
+ * cuda_stream. theta_dst [count][8] float, dist_dst [count] double,
+ * idx_dst [count] uint64; any may be NULL. *copied (HOST, may be NULL) receives
+ * the number copied; the call synchronizes to read the count. */
+abc_status abc_plan_copy_results(abc_plan plan, int32_t region, float* theta_dst, double* dist_dst,
+                                 uint64_t* idx_dst, uint64_t count, uint64_t* copied, void* cuda_stream);
+
+/* Point a region at a new proposal buffer (DEVICE [n_samples][8]) or NULL for
+ * prior draws, and/or set its next first_index. Synchronous (cudaMemcpy). */
+abc_status abc_plan_set_region(abc_plan plan, int32_t region, const float* theta_in, uint64_t first_index);
+
+/* Release the plan's device memory and graph. */
+abc_status abc_plan_destroy(abc_plan plan);
+
 /* Variant of abc_sample that allocates no memory. It is for callers that must
  * not allocate device memory while sampling: code running inside a host
  * framework that owns the GPU's memory pool and forbids other allocators, or

@@ -1,0 +1,176 @@
+"""Masked autoregressive flow (MAF) proposal for sequential ABC, float64.
+
+TEST INFRASTRUCTURE: only tests/, __graft_entry__.smoke() and bench.py's CPU
+baseline may import this module. The CUDA library never does.
+
+The paper names sequential Monte Carlo ABC (Sec. 2.2, last paragraph: a
+decreasing sequence of tolerances, each round's samples transformed into the
+next) without fixing how the next proposal is built. The proposal here is a
+density q(theta) learned from the previous round's accepted, importance
+weighted samples:
+
+  * support: the prior box, through y = logit((theta - lo) / (hi - lo));
+  * flow (Papamakarios, Pavlakou, Murray 2017): K MADE blocks (Germain, Gregor,
+    Murray, Larochelle 2015), each x -> z = (x - mu(x)) exp(-alpha(x)) with
+    mu_j, alpha_j depending on x_{<j} only, the order reversed between blocks,
+    base N(0, I);
+  * MADE: h = relu(W1 x + b1) with mask M1[l, j] = [d_h(l) >= j + 1], outputs
+    (mu, alpha_raw) = W2 h + b2 with mask M2[j, l] = [j + 1 > d_h(l)], hidden
+    degrees d_h(l) = (l mod (D - 1)) + 1;
+  * alpha = A tanh(alpha_raw / A), A = 6 (keeps exp(alpha) bounded);
+  * log q(theta) = log N(z_K) - sum_k sum_j alpha_kj - sum_j log((hi_j - lo_j) u_j (1 - u_j));
+  * importance weight of an accepted draw: w = prior(theta) / q(theta);
+  * training: Adam (Kingma, Ba 2015) on the weighted mean of -log q_y(y).
+"""
+import numpy as np
+
+D = 8
+ALPHA_MAX = 6.0
+LOG_2PI = np.log(2.0 * np.pi)
+
+
+def degrees(H, D=D):
+    return (np.arange(H) % (D - 1)) + 1
+
+
+def masks(H, D=D):
+    """M1 [H, D] and M2 [2D, H] (rows 0..D-1 for mu, D..2D-1 for alpha)."""
+    d_in = np.arange(1, D + 1)
+    d_h = degrees(H, D)
+    M1 = (d_h[:, None] >= d_in[None, :]).astype(np.float64)
+    M2 = (d_in[:, None] > d_h[None, :]).astype(np.float64)
+    return M1, np.concatenate([M2, M2], axis=0)
+
+
+def init_params(rng, K=3, H=256, D=D, scale=0.1):
+    """K blocks of (W1 [H, D], b1 [H], W2 [2D, H], b2 [2D]), small random weights."""
+    out = []
+    for _ in range(K):
+        out.append(dict(W1=rng.normal(0, scale / np.sqrt(D), (H, D)), b1=np.zeros(H),
+                        W2=rng.normal(0, scale / np.sqrt(H), (2 * D, H)), b2=np.zeros(2 * D)))
+    return out
+
+
+def made(x, p, M1, M2):
+    """One MADE: returns (mu, alpha, alpha_raw, hidden pre-activation, hidden)."""
+    a1 = x @ (p["W1"] * M1).T + p["b1"]
+    h = np.maximum(a1, 0.0)
+    out = h @ (p["W2"] * M2).T + p["b2"]
+    mu = out[:, :D]
+    araw = out[:, D:]
+    alpha = ALPHA_MAX * np.tanh(araw / ALPHA_MAX)
+    return mu, alpha, araw, a1, h
+
+
+def forward(y, params):
+    """y [N, D] -> (z [N, D] after the last reversal, log q_y [N], per-block caches)."""
+    H = params[0]["W1"].shape[0]
+    M1, M2 = masks(H)
+    x = np.asarray(y, dtype=np.float64)
+    logdet = np.zeros(x.shape[0])
+    caches = []
+    for p in params:
+        mu, alpha, araw, a1, h = made(x, p, M1, M2)
+        z = (x - mu) * np.exp(-alpha)
+        logdet -= alpha.sum(axis=1)
+        caches.append(dict(x=x, mu=mu, alpha=alpha, araw=araw, a1=a1, h=h, z=z))
+        x = z[:, ::-1]
+    logq = -0.5 * (x ** 2).sum(axis=1) - 0.5 * D * LOG_2PI + logdet
+    return x, logq, caches
+
+
+def inverse(u, params):
+    """Base normals u [N, D] -> (y [N, D], log q_y [N]) by the sequential inverse."""
+    H = params[0]["W1"].shape[0]
+    M1, M2 = masks(H)
+    x = np.asarray(u, dtype=np.float64)
+    logq = -0.5 * (x ** 2).sum(axis=1) - 0.5 * D * LOG_2PI
+    for p in reversed(params):
+        z = x[:, ::-1]
+        xin = np.zeros_like(z)
+        for j in range(D):
+            mu, alpha, _, _, _ = made(xin, p, M1, M2)
+            xin[:, j] = z[:, j] * np.exp(alpha[:, j]) + mu[:, j]
+        mu, alpha, _, _, _ = made(xin, p, M1, M2)
+        logq -= alpha.sum(axis=1)
+        x = xin
+    return x, logq
+
+
+def to_theta(y, lo, hi):
+    lo = np.asarray(lo, dtype=np.float64)
+    hi = np.asarray(hi, dtype=np.float64)
+    return lo + (hi - lo) / (1.0 + np.exp(-y))
+
+
+def to_y(theta, lo, hi):
+    lo = np.asarray(lo, dtype=np.float64)
+    hi = np.asarray(hi, dtype=np.float64)
+    u = (np.asarray(theta, dtype=np.float64) - lo) / (hi - lo)
+    return np.log(u) - np.log1p(-u)
+
+
+def log_jacobian_y(y, lo, hi):
+    """sum_j log |d theta_j / d y_j| = sum_j log((hi - lo) s (1 - s)), s = sigmoid(y)."""
+    w = np.asarray(hi, dtype=np.float64) - np.asarray(lo, dtype=np.float64)
+    return (np.log(w) - np.logaddexp(0, -y) - np.logaddexp(0, y)).sum(axis=1)
+
+
+def log_q_theta(theta, params, lo, hi):
+    y = to_y(theta, lo, hi)
+    _, logq_y, _ = forward(y, params)
+    return logq_y - log_jacobian_y(y, lo, hi)
+
+
+def loss_and_grad(y, w, params):
+    """Weighted mean of -log q_y(y) and its gradient with respect to every parameter."""
+    H = params[0]["W1"].shape[0]
+    M1, M2 = masks(H)
+    w = np.asarray(w, dtype=np.float64)
+    W = w.sum()
+    zK, logq, caches = forward(y, params)
+    loss = -(w * logq).sum() / W
+    g_x = (w / W)[:, None] * zK                    # d loss / d (final x)
+    grads = [None] * len(params)
+    for k in reversed(range(len(params))):
+        c, p = caches[k], params[k]
+        g_z = g_x[:, ::-1]                         # undo the reversal after block k
+        e = np.exp(-c["alpha"])
+        g_xdirect = g_z * e
+        g_mu = -g_z * e
+        # d loss / d alpha: -g_z z (through z = (x - mu) e^-alpha) + w/W (log-det term)
+        g_alpha = -g_z * c["z"] + (w / W)[:, None]
+        g_araw = g_alpha * (1.0 - (c["alpha"] / ALPHA_MAX) ** 2)
+        g_out = np.concatenate([g_mu, g_araw], axis=1)          # [N, 2D]
+        W2m = p["W2"] * M2
+        gW2 = (g_out.T @ c["h"]) * M2
+        gb2 = g_out.sum(axis=0)
+        g_h = g_out @ W2m
+        g_a1 = g_h * (c["a1"] > 0)
+        W1m = p["W1"] * M1
+        gW1 = (g_a1.T @ c["x"]) * M1
+        gb1 = g_a1.sum(axis=0)
+        g_x = g_xdirect + g_a1 @ W1m
+        grads[k] = dict(W1=gW1, b1=gb1, W2=gW2, b2=gb2)
+    return loss, grads
+
+
+def adam_step(params, grads, state, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+    """One Adam step (Kingma, Ba 2015) in place; state: dict(t, m, v)."""
+    state["t"] = state.get("t", 0) + 1
+    t = state["t"]
+    if "m" not in state:
+        state["m"] = [{k: np.zeros_like(v) for k, v in p.items()} for p in params]
+        state["v"] = [{k: np.zeros_like(v) for k, v in p.items()} for p in params]
+    for p, g, m, v in zip(params, grads, state["m"], state["v"]):
+        for key in p:
+            m[key] = b1 * m[key] + (1 - b1) * g[key]
+            v[key] = b2 * v[key] + (1 - b2) * g[key] ** 2
+            mhat = m[key] / (1 - b1 ** t)
+            vhat = v[key] / (1 - b2 ** t)
+            p[key] = p[key] - lr * mhat / (np.sqrt(vhat) + eps)
+
+
+def ess_fraction(w):
+    w = np.asarray(w, dtype=np.float64)
+    return (w.sum() ** 2) / (w ** 2).sum() / len(w)

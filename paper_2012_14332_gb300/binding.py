@@ -22,12 +22,26 @@ PAPER_LO = (0.0,) * 8
 PAPER_HI = (1.0, 100.0, 2.0, 1.0, 1.0, 1.0, 1.0, 2.0)   # Sec. 2.1, Eq. 2
 
 EXPORTED = ("abc_sample", "abc_distances", "abc_simulate", "abc_step", "abc_kth_smallest", "abc_strerror",
-            "abc_last_error", "abc_version", "abc_last_simulated_days", "abc_sample_noalloc")
+            "abc_last_error", "abc_version", "abc_last_simulated_days", "abc_sample_noalloc", "abc_plan_create",
+            "abc_plan_reset", "abc_plan_run", "abc_plan_run_graph", "abc_plan_tune", "abc_plan_results",
+            "abc_plan_copy_results", "abc_plan_set_region", "abc_plan_destroy")
+ABC_MAX_REGIONS = 32
 ABC_NOALLOC_T_MAX = 1024
 
 
 class AbcPriorBox(ctypes.Structure):
     _fields_ = [("lo", ctypes.c_float * 8), ("hi", ctypes.c_float * 8)]
+
+
+class AbcRegion(ctypes.Structure):
+    _fields_ = [("observed", ctypes.c_void_p), ("T", ctypes.c_int32), ("N_pop", ctypes.c_int64),
+                ("eps", ctypes.c_double), ("n_samples", ctypes.c_uint64), ("first_index", ctypes.c_uint64),
+                ("stream", ctypes.c_uint32), ("capacity", ctypes.c_uint64), ("theta_in", ctypes.c_void_p)]
+
+
+class AbcLaunchShape(ctypes.Structure):
+    _fields_ = [("block_threads", ctypes.c_int32), ("pairs_per_iteration", ctypes.c_int32),
+                ("blocks_per_sm", ctypes.c_int32), ("ms", ctypes.c_float)]
 
 
 class AbcError(RuntimeError):
@@ -72,6 +86,21 @@ def load(path=None):
         L.abc_last_error.argtypes = []
         L.abc_last_error.restype = ctypes.c_char_p
         L.abc_version.restype = ctypes.c_int
+        pp = ctypes.c_void_p
+        L.abc_plan_create.argtypes = [box, ctypes.POINTER(AbcRegion), i32, u64, ctypes.c_int, ctypes.POINTER(pp)]
+        L.abc_plan_reset.argtypes = [pp, vp]
+        L.abc_plan_run.argtypes = [pp, vp]
+        L.abc_plan_run_graph.argtypes = [pp, i32, vp]
+        L.abc_plan_tune.argtypes = [pp, vp, ctypes.POINTER(AbcLaunchShape), i32, ctypes.POINTER(ctypes.c_int32),
+                                    ctypes.POINTER(AbcLaunchShape)]
+        L.abc_plan_results.argtypes = [pp, i32, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
+                                       vp, vp, vp, vp]
+        L.abc_plan_copy_results.argtypes = [pp, i32, vp, vp, vp, u64, ctypes.POINTER(ctypes.c_uint64), vp]
+        L.abc_plan_set_region.argtypes = [pp, i32, vp, u64]
+        L.abc_plan_destroy.argtypes = [pp]
+        for nm in ("abc_plan_create", "abc_plan_reset", "abc_plan_run", "abc_plan_run_graph", "abc_plan_tune",
+                   "abc_plan_results", "abc_plan_copy_results", "abc_plan_set_region", "abc_plan_destroy"):
+            getattr(L, nm).restype = ctypes.c_int
         L.abc_last_simulated_days.argtypes = []
         L.abc_last_simulated_days.restype = ctypes.c_uint64
         if path is None:
@@ -255,3 +284,117 @@ def abc_version():
 def abc_last_simulated_days():
     """Model days simulated by the last abc_sample call on this thread."""
     return int(load().abc_last_simulated_days())
+
+
+class Plan:
+    """Batched regions in one launch (C ABI abc_plan_*). regions: list of dicts
+    with keys observed (host int32 [3, T+1]), N_pop, eps, n_samples and optional
+    first_index, stream, capacity, theta_in (CUDA f32 [n_samples, 8])."""
+
+    def __init__(self, regions, seed, mode="fast", lo=PAPER_LO, hi=PAPER_HI):
+        L = load()
+        self._L = L
+        self._obs = [np.ascontiguousarray(np.asarray(r["observed"], dtype=np.int32)) for r in regions]
+        arr = (AbcRegion * len(regions))()
+        for j, r in enumerate(regions):
+            o = self._obs[j]
+            th = r.get("theta_in")
+            arr[j] = AbcRegion(o.ctypes.data, o.shape[1] - 1, int(r["N_pop"]), float(r["eps"]), int(r["n_samples"]),
+                               int(r.get("first_index", 0)), int(r.get("stream", j)), int(r.get("capacity", 4096)),
+                               th.data_ptr() if th is not None else None)
+        self.capacity = [int(r.get("capacity", 4096)) for r in regions]
+        self.n_regions = len(regions)
+        b = prior_box(lo, hi)
+        h = ctypes.c_void_p()
+        _check(L, L.abc_plan_create(ctypes.byref(b), arr, len(regions), int(seed), _mode(mode), ctypes.byref(h)))
+        self._h = h
+
+    def reset(self, cuda_stream=None):
+        _check(self._L, self._L.abc_plan_reset(self._h, _stream(cuda_stream)))
+
+    def run(self, cuda_stream=None):
+        _check(self._L, self._L.abc_plan_run(self._h, _stream(cuda_stream)))
+
+    def run_graph(self, n_runs, cuda_stream=None):
+        _check(self._L, self._L.abc_plan_run_graph(self._h, int(n_runs), _stream(cuda_stream)))
+
+    def tune(self, cuda_stream=None):
+        shapes = (AbcLaunchShape * 32)()
+        n = ctypes.c_int32()
+        best = AbcLaunchShape()
+        _check(self._L, self._L.abc_plan_tune(self._h, _stream(cuda_stream), shapes, 32, ctypes.byref(n),
+                                              ctypes.byref(best)))
+        as_dict = lambda s: dict(block_threads=s.block_threads, pairs_per_iteration=s.pairs_per_iteration,
+                                 blocks_per_sm=s.blocks_per_sm, ms=s.ms)
+        return as_dict(best), [as_dict(shapes[j]) for j in range(n.value)]
+
+    def counts(self, region, cuda_stream=None):
+        n, d = ctypes.c_uint64(), ctypes.c_uint64()
+        _check(self._L, self._L.abc_plan_results(self._h, int(region), ctypes.byref(n), ctypes.byref(d), None, None,
+                                                 None, _stream(cuda_stream)))
+        return int(n.value), int(d.value)
+
+    def results(self, region, cuda_stream=None):
+        """(theta [m, 8], dist [m], idx [m], n_accepted, simulated_days) as CUDA tensors."""
+        n_acc, days = self.counts(region, cuda_stream)
+        m = min(n_acc, self.capacity[region])
+        dev = torch.device("cuda", torch.cuda.current_device())
+        theta = torch.empty((max(m, 1), 8), dtype=torch.float32, device=dev)
+        dist = torch.empty((max(m, 1),), dtype=torch.float64, device=dev)
+        idx = torch.empty((max(m, 1),), dtype=torch.int64, device=dev)
+        got = ctypes.c_uint64()
+        _check(self._L, self._L.abc_plan_copy_results(self._h, int(region), theta.data_ptr(), dist.data_ptr(),
+                                                      idx.data_ptr(), m, ctypes.byref(got), _stream(cuda_stream)))
+        torch.cuda.current_stream().synchronize() if cuda_stream is None else None
+        return theta[:m], dist[:m], idx[:m], n_acc, days
+
+    def set_region(self, region, theta_in=None, first_index=0):
+        _check(self._L, self._L.abc_plan_set_region(self._h, int(region),
+                                                    theta_in.data_ptr() if theta_in is not None else None,
+                                                    int(first_index)))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.abc_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+abc_plan_create = Plan
+
+
+def abc_plan_reset(plan, cuda_stream=None):
+    plan.reset(cuda_stream)
+
+
+def abc_plan_run(plan, cuda_stream=None):
+    plan.run(cuda_stream)
+
+
+def abc_plan_run_graph(plan, n_runs, cuda_stream=None):
+    plan.run_graph(n_runs, cuda_stream)
+
+
+def abc_plan_tune(plan, cuda_stream=None):
+    return plan.tune(cuda_stream)
+
+
+def abc_plan_results(plan, region, cuda_stream=None):
+    return plan.counts(region, cuda_stream)
+
+
+def abc_plan_copy_results(plan, region, cuda_stream=None):
+    return plan.results(region, cuda_stream)
+
+
+def abc_plan_set_region(plan, region, theta_in=None, first_index=0):
+    plan.set_region(region, theta_in, first_index)
+
+
+def abc_plan_destroy(plan):
+    plan.close()

@@ -6,7 +6,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libabc_gb300.so")
-SOURCES = ["abc_kernels.cu", "abc_api.cu"]
+SOURCES = ["abc_kernels.cu", "abc_batch.cu", "abc_api.cu", "abc_plan.cu"]
 HEADERS = ["abc_kernels.h", "abc_model.cuh"]
 PUBLIC_HEADER = os.path.join(os.path.dirname(HERE), "include", "abc_gb300.h")
 
@@ -32,13 +32,25 @@ def _stale():
 
 
 def build(force=False, verbose=False):
-    """Build the library if it is missing or older than its sources."""
+    """Build the library if it is missing or older than its sources: every
+    translation unit compiled in parallel, then one shared-library link."""
     if not force and not _stale():
         return LIB
+    objdir = os.path.join(HERE, "_build")
+    os.makedirs(objdir, exist_ok=True)
+    procs = []
+    for f in SOURCES:
+        obj = os.path.join(objdir, f.replace(".cu", ".o"))
+        cmd = [nvcc()] + [x for x in NVCC_FLAGS if x != "-shared"] + (["-Xptxas", "-v"] if verbose else []) + \
+            ["-c", "-o", obj, os.path.join(CSRC, f)]
+        procs.append((f, obj, subprocess.Popen(cmd, cwd=CSRC)))
+    objs = []
+    for f, obj, pr in procs:
+        if pr.wait() != 0:
+            raise RuntimeError("nvcc failed on %s" % f)
+        objs.append(obj)
     tmp = LIB + ".%d.tmp" % os.getpid()
-    cmd = [nvcc()] + NVCC_FLAGS + (["-Xptxas", "-v"] if verbose else []) + ["-o", tmp] + \
-        [os.path.join(CSRC, f) for f in SOURCES]
-    subprocess.check_call(cmd, cwd=CSRC)
+    subprocess.check_call([nvcc(), "-gencode", "arch=compute_103a,code=sm_103a", "-shared", "-o", tmp] + objs)
     os.replace(tmp, LIB)
     return LIB
 

@@ -253,6 +253,25 @@ abc_status noalloc_scratch(void** out)
 
 }  // namespace
 
+namespace abcgb {
+// Helpers shared with the batched-regions ABI (abc_plan.cu): the same error
+// reporting, checks and kernel parameters as the calls in this file.
+abc_status plan_fail(abc_status st, const char* msg) { return fail(st, "%s", msg); }
+abc_status plan_cuda_fail(cudaError_t e, const char* what) { return cuda_fail(e, what); }
+abc_status plan_ok() { return ok(); }
+bool plan_check_prior(const abc_prior_box* prior, abc_status* st)
+{
+    *st = check_prior(prior);
+    return *st == ABC_OK;
+}
+uint64_t plan_acc_threshold(double eps) { return acc_threshold(eps); }
+ModelParams plan_make_params(const abc_prior_box* prior, int32_t T, int64_t N_pop, uint64_t seed, uint32_t stream,
+                             const int32_t* ard0)
+{
+    return make_params(prior, T, N_pop, seed, stream, ard0);
+}
+}  // namespace abcgb
+
 extern "C" {
 
 abc_status abc_sample(const abc_prior_box* prior, const int32_t* observed, int32_t T, int64_t N_pop, double eps,

@@ -1,0 +1,251 @@
+// abc_batch.cu -- batched ABC rejection over a table of regions in one
+// persistent launch (many regions with their own population, horizon T,
+// tolerance eps, observed series, random stream and sample range).
+//
+// Same per-sample method and early rejection as abc_reject_kernel (paper
+// Sec. 2.1, 2.2, 3.1); what changes is where a lane's constants come from:
+// each 32-sample chunk belongs to one region, and a lane that takes a sample
+// also takes its region's T, eps threshold, stream, 1/P and observed-series
+// offset from the region table staged in shared memory. The observed series
+// are read through the read-only data cache (all regions together can exceed
+// shared memory). Chunks are claimed from one counter across all regions, so
+// uneven regions balance across the whole GPU. Accepted samples go to their
+// region's buffers (one atomicAdd per accept: accepts are rare).
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "abc_kernels.h"
+#include "abc_model.cuh"
+
+namespace abcgb {
+
+namespace {
+
+constexpr int kRingB = 64;
+
+struct BatchRing {
+    float4 lo[kRingB];
+    float4 hi[kRingB];
+    uint64_t idx[kRingB];
+    int32_t region[kRingB];
+};
+
+__device__ __forceinline__ void load_theta(const float* src, float th[8])
+{
+    const float4* s4 = reinterpret_cast<const float4*>(src);
+    const float4 l = __ldg(s4), h = __ldg(s4 + 1);
+    th[0] = l.x; th[1] = l.y; th[2] = l.z; th[3] = l.w;
+    th[4] = h.x; th[5] = h.y; th[6] = h.z; th[7] = h.w;
+}
+
+// Region constants a lane keeps in registers for its current sample.
+struct LaneRegion {
+    int32_t r, T;
+    uint32_t ctr3, obs_off;
+    uint64_t acc_max;
+    float inv_p;
+};
+
+template <int MODE, int BLOCK, int PAIRS>
+__global__ void __launch_bounds__(BLOCK) abc_batch_kernel(const __grid_constant__ ModelParams p,
+                                                          const __grid_constant__ BatchArgs a)
+{
+    __shared__ RegionDev reg_s[kMaxRegions];
+    extern __shared__ BatchRing rings[];
+    for (int r = threadIdx.x; r < a.n_regions; r += BLOCK) reg_s[r] = a.regions[r];
+    __syncthreads();
+    const uint32_t lane = threadIdx.x & 31u;
+    BatchRing& ring = rings[threadIdx.x >> 5];
+    const uint32_t lt_mask = (1u << lane) - 1u;
+
+    bool active = false;
+    uint64_t i = 0, acc = 0;
+    uint32_t k = 0;
+    Theta t;
+    State x;
+    LaneRegion lr{0, 1, 0, 0, 0, 0.0f};
+    int32_t days_region = -1;
+    unsigned long long days = 0;
+    uint32_t head = 0, tail = 0;
+    bool exhausted = false;
+
+    while (true) {
+        const uint32_t idle = __ballot_sync(0xFFFFFFFFu, !active);
+        if (idle) {
+            const uint32_t need = __popc(idle);
+            if (tail - head < need && !exhausted) {
+                unsigned long long c = 0;
+                if (lane == 0) c = atomicAdd(a.next, 1ull);
+                c = __shfl_sync(0xFFFFFFFFu, c, 0);
+                if (c >= a.total_chunks) {
+                    exhausted = true;
+                } else {
+                    int32_t r = 0;
+                    for (int32_t q = 1; q < a.n_regions; ++q)
+                        if (reg_s[q].chunk_begin <= c) r = q;
+                    const RegionDev& R = reg_s[r];
+                    const uint64_t j0 = (c - R.chunk_begin) * 32;
+                    const uint64_t left = R.n_samples - j0;
+                    const uint32_t made = left < 32 ? (uint32_t)left : 32u;
+                    if (lane < made) {
+                        const uint64_t j = j0 + lane;
+                        const uint64_t ii = R.first_index + j;
+                        float th[8];
+                        if (R.theta_in)
+                            load_theta(R.theta_in + 8 * j, th);
+                        else
+                            prior_draw_s(p, ii, R.ctr3_base, th);
+                        const uint32_t slot = (tail + lane) & (kRingB - 1);
+                        ring.lo[slot] = make_float4(th[0], th[1], th[2], th[3]);
+                        ring.hi[slot] = make_float4(th[4], th[5], th[6], th[7]);
+                        ring.idx[slot] = ii;
+                        ring.region[slot] = r;
+                    }
+                    tail += made;
+                    __syncwarp();
+                }
+            }
+            const uint32_t avail = tail - head;
+            if (!active) {
+                const uint32_t rank = __popc(idle & lt_mask);
+                if (rank < avail) {
+                    const uint32_t slot = (head + rank) & (kRingB - 1);
+                    const float4 l = ring.lo[slot], h = ring.hi[slot];
+                    const float th[8] = {l.x, l.y, l.z, l.w, h.x, h.y, h.z, h.w};
+                    i = ring.idx[slot];
+                    const int32_t r = ring.region[slot];
+                    const RegionDev& R = reg_s[r];
+                    if (r != days_region) {
+                        if (days_region >= 0 && days) atomicAdd(reg_s[days_region].counters + 1, days);
+                        days = 0;
+                        days_region = r;
+                    }
+                    lr.r = r;
+                    lr.T = R.T;
+                    lr.ctr3 = R.ctr3_base;
+                    lr.obs_off = R.obs_off;
+                    lr.acc_max = R.acc_max;
+                    lr.inv_p = R.inv_p;
+                    t = make_theta<MODE>(th, R.inv_p);
+                    x = init_state(t, R.A0, R.R0, R.D0, R.room0);
+                    acc = 0;
+                    k = 1;
+                    active = true;
+                }
+            }
+            head += need < avail ? need : avail;
+            __syncwarp();
+        }
+        if (__ballot_sync(0xFFFFFFFFu, active) == 0) break;
+
+        bool accept = false;
+#pragma unroll
+        for (int rep = 0; rep < PAIRS; ++rep) {
+            if (active) {
+                float z[10];
+                day_pair_normals_s<MODE>(p, i, k, lr.ctr3, z);
+                const int32_t d1 = (int32_t)(2 * k - 1);
+                const int4* obs = a.obs + lr.obs_off;
+                model_day<MODE>(x, t, lr.inv_p, z);
+                acc = add_day_sq(acc, x, __ldg(obs + d1));
+                if (d1 < lr.T) {
+                    model_day<MODE>(x, t, lr.inv_p, z + 5);
+                    acc = add_day_sq(acc, x, __ldg(obs + d1 + 1));
+                    days += 2;
+                } else {
+                    days += 1;
+                }
+                const bool over = acc > lr.acc_max;
+                const bool last = d1 + 1 >= lr.T;
+                accept = !over && last;
+                active = !(over || last);
+                ++k;
+            }
+        }
+        if (accept) {
+            const RegionDev& R = reg_s[lr.r];
+            const unsigned long long slot = atomicAdd(R.counters, 1ull);
+            if (slot < R.capacity) {
+                float th[8];
+                if (R.theta_in)
+                    load_theta(R.theta_in + 8 * (i - R.first_index), th);
+                else
+                    prior_draw_s(p, i, lr.ctr3, th);
+                R.idx_out[slot] = i;
+                R.dist_out[slot] = __dsqrt_rn(__ull2double_rn(acc));
+                float4* to = reinterpret_cast<float4*>(R.theta_out + 8 * slot);
+                to[0] = make_float4(th[0], th[1], th[2], th[3]);
+                to[1] = make_float4(th[4], th[5], th[6], th[7]);
+            }
+        }
+    }
+    if (days_region >= 0 && days) atomicAdd(reg_s[days_region].counters + 1, days);
+}
+
+__global__ void advance_kernel(RegionDev* regions, int32_t n)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < n) regions[r].first_index += regions[r].n_samples;
+}
+
+}  // namespace
+
+static const BatchShape kShapes[] = {
+    {256, 1, 0}, {128, 1, 0}, {512, 1, 0}, {256, 2, 0}, {128, 2, 0}, {512, 2, 0}, {256, 1, 2}, {256, 1, 3},
+};
+
+int batch_shape_count() { return (int)(sizeof kShapes / sizeof kShapes[0]); }
+BatchShape batch_shape(int index) { return kShapes[index]; }
+
+template <int MODE, int BLOCK, int PAIRS>
+static cudaError_t launch_t(const ModelParams& p, const BatchArgs* a, int blocks_per_sm, cudaStream_t s)
+{
+    auto kernel = abc_batch_kernel<MODE, BLOCK, PAIRS>;
+    const size_t smem = sizeof(BatchRing) * (BLOCK / 32);
+    int dev = 0, sms = 0, fit = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, kernel, BLOCK, smem);
+    if (e != cudaSuccess) return e;
+    if (fit < 1) fit = 1;
+    const int per_sm = (blocks_per_sm > 0 && blocks_per_sm < fit) ? blocks_per_sm : fit;
+    if (!a) return cudaSuccess;   // preparation only: attributes and occupancy resolved
+    uint64_t want = (a->total_chunks + BLOCK / 32 - 1) / (BLOCK / 32);
+    int grid = sms * per_sm;
+    if (want < (uint64_t)grid) grid = (int)(want > 0 ? want : 1);
+    kernel<<<grid, BLOCK, smem, s>>>(p, *a);
+    return cudaGetLastError();
+}
+
+template <int MODE>
+static cudaError_t dispatch(const ModelParams& p, const BatchArgs* a, const BatchShape& sh, cudaStream_t s)
+{
+    if (sh.block_threads == 128 && sh.pairs == 1) return launch_t<MODE, 128, 1>(p, a, sh.blocks_per_sm, s);
+    if (sh.block_threads == 256 && sh.pairs == 1) return launch_t<MODE, 256, 1>(p, a, sh.blocks_per_sm, s);
+    if (sh.block_threads == 512 && sh.pairs == 1) return launch_t<MODE, 512, 1>(p, a, sh.blocks_per_sm, s);
+    if (sh.block_threads == 128 && sh.pairs == 2) return launch_t<MODE, 128, 2>(p, a, sh.blocks_per_sm, s);
+    if (sh.block_threads == 256 && sh.pairs == 2) return launch_t<MODE, 256, 2>(p, a, sh.blocks_per_sm, s);
+    if (sh.block_threads == 512 && sh.pairs == 2) return launch_t<MODE, 512, 2>(p, a, sh.blocks_per_sm, s);
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_batch(const ModelParams& p, const BatchArgs& a, bool fast, const BatchShape& shape, cudaStream_t s)
+{
+    return fast ? dispatch<kFast>(p, &a, shape, s) : dispatch<kExact>(p, &a, shape, s);
+}
+
+cudaError_t prepare_batch(bool fast, const BatchShape& shape)
+{
+    ModelParams p{};
+    return fast ? dispatch<kFast>(p, nullptr, shape, nullptr) : dispatch<kExact>(p, nullptr, shape, nullptr);
+}
+
+cudaError_t launch_advance(RegionDev* regions, int32_t n_regions, cudaStream_t s)
+{
+    advance_kernel<<<1, 32, 0, s>>>(regions, n_regions);
+    return cudaGetLastError();
+}
+
+}  // namespace abcgb

@@ -47,6 +47,47 @@ struct StepArgs {
     int32_t* counts_out;          // device [B][5] or null
 };
 
+// One region of a batched launch (device-resident table; see abc_batch.cu).
+constexpr int kMaxRegions = 32;
+struct RegionDev {
+    uint64_t first_index;          // first sample index of the current run (advanced after each run)
+    uint64_t n_samples;            // samples per run
+    uint64_t chunk_begin;          // first 32-sample chunk of this region in the run's chunk space
+    uint64_t acc_max;              // accept iff distance^2 <= acc_max
+    uint64_t capacity;             // accepted samples kept
+    float* theta_out;              // device [capacity][8]
+    double* dist_out;              // device [capacity]
+    uint64_t* idx_out;             // device [capacity]
+    const float* theta_in;         // device [n_samples][8] proposals, or null: prior draws
+    unsigned long long* counters;  // device [2]: accepted, simulated days
+    int32_t T, P, room0, A0, R0, D0;
+    uint32_t ctr3_base;            // 4 * stream
+    float inv_p;
+    uint32_t obs_off;              // first day of this region in the concatenated observed series
+    uint32_t pad_;
+};
+
+struct BatchArgs {
+    const RegionDev* regions;      // device [n_regions]
+    int32_t n_regions;
+    uint64_t total_chunks;
+    const int4* obs;               // device, concatenated (A, R, D, 0) per day of every region
+    unsigned long long* next;      // claimed chunks, zeroed before each run
+};
+
+// Launch shapes the batched kernel is compiled for (the autotuner's space).
+struct BatchShape {
+    int block_threads;   // 128, 256 or 512
+    int pairs;           // day pairs per loop iteration (1 or 2)
+    int blocks_per_sm;   // resident blocks requested per SM (0 = as many as fit)
+};
+int batch_shape_count();
+BatchShape batch_shape(int index);
+
+cudaError_t launch_batch(const ModelParams& p, const BatchArgs& a, bool fast, const BatchShape& shape, cudaStream_t s);
+cudaError_t launch_advance(RegionDev* regions, int32_t n_regions, cudaStream_t s);
+cudaError_t prepare_batch(bool fast, const BatchShape& shape);
+
 size_t reject_smem_bytes(int32_t T);
 cudaError_t launch_reject(const ModelParams& p, const RejectArgs& a, bool fast, cudaStream_t s, int* blocks_out);
 cudaError_t launch_distances(const ModelParams& p, const DistanceArgs& a, bool fast, cudaStream_t s);

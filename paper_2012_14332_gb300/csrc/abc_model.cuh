@@ -65,9 +65,16 @@ __device__ __forceinline__ uint4 philox10(uint4 c, const ModelParams& p)
     return c;
 }
 
+// Block g of day-pair k of sample i; ctr3_base = 4 * stream.
+__device__ __forceinline__ uint4 rng_block_s(const ModelParams& p, uint64_t i, uint32_t k, uint32_t ctr3_base,
+                                             uint32_t g)
+{
+    return philox10(make_uint4((uint32_t)i, (uint32_t)(i >> 32), k, ctr3_base | g), p);
+}
+
 __device__ __forceinline__ uint4 rng_block(const ModelParams& p, uint64_t i, uint32_t k, uint32_t g)
 {
-    return philox10(make_uint4((uint32_t)i, (uint32_t)(i >> 32), k, p.ctr3_base | g), p);
+    return rng_block_s(p, i, k, p.ctr3_base, g);
 }
 
 // (2m+1) 2^-24 with m the low 23 bits of w; the subtraction is exact.
@@ -205,13 +212,14 @@ __device__ __forceinline__ void box_muller(uint32_t w_radius, uint32_t w_angle, 
     }
 }
 
-// Ten normals of day-pair k (days 2k-1 and 2k) of sample i.
+// Ten normals of day-pair k (days 2k-1 and 2k) of sample i, RNG stream ctr3_base / 4.
 template <int MODE>
-__device__ __forceinline__ void day_pair_normals(const ModelParams& p, uint64_t i, uint32_t k, float z[10])
+__device__ __forceinline__ void day_pair_normals_s(const ModelParams& p, uint64_t i, uint32_t k, uint32_t ctr3_base,
+                                                   float z[10])
 {
-    const uint4 a = rng_block(p, i, k, 0);
-    const uint4 b = rng_block(p, i, k, 1);
-    const uint4 c = rng_block(p, i, k, 2);
+    const uint4 a = rng_block_s(p, i, k, ctr3_base, 0);
+    const uint4 b = rng_block_s(p, i, k, ctr3_base, 1);
+    const uint4 c = rng_block_s(p, i, k, ctr3_base, 2);
     box_muller<MODE>(a.x, a.y, z[0], z[1]);
     box_muller<MODE>(a.z, a.w, z[2], z[3]);
     box_muller<MODE>(b.x, b.y, z[4], z[5]);
@@ -219,14 +227,25 @@ __device__ __forceinline__ void day_pair_normals(const ModelParams& p, uint64_t 
     box_muller<MODE>(c.x, c.y, z[8], z[9]);
 }
 
-// Prior draw of sample i (Eq. 2): theta_j = lo_j + width_j u_j (two roundings).
-__device__ __forceinline__ void prior_draw(const ModelParams& p, uint64_t i, float th[8])
+template <int MODE>
+__device__ __forceinline__ void day_pair_normals(const ModelParams& p, uint64_t i, uint32_t k, float z[10])
 {
-    const uint4 a = rng_block(p, i, 0, 0);
-    const uint4 b = rng_block(p, i, 0, 1);
+    day_pair_normals_s<MODE>(p, i, k, p.ctr3_base, z);
+}
+
+// Prior draw of sample i (Eq. 2): theta_j = lo_j + width_j u_j (two roundings).
+__device__ __forceinline__ void prior_draw_s(const ModelParams& p, uint64_t i, uint32_t ctr3_base, float th[8])
+{
+    const uint4 a = rng_block_s(p, i, 0, ctr3_base, 0);
+    const uint4 b = rng_block_s(p, i, 0, ctr3_base, 1);
     const uint32_t w[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
 #pragma unroll
     for (int j = 0; j < 8; ++j) th[j] = __fadd_rn(p.lo[j], __fmul_rn(p.width[j], uniform01(w[j])));
+}
+
+__device__ __forceinline__ void prior_draw(const ModelParams& p, uint64_t i, float th[8])
+{
+    prior_draw_s(p, i, p.ctr3_base, th);
 }
 
 // n = min(max(floor x, 0), c): cvt.rmi saturates to int32 and maps NaN to 0;

@@ -141,3 +141,29 @@ def test_oracle_is_not_reachable_from_the_product():
             if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
                 src = open(os.path.join(dirpath, f)).read()
                 assert "oracle" not in src.lower(), os.path.join(dirpath, f)
+
+
+def test_plan_create_validates_before_any_cuda_call(L):
+    from paper_2012_14332_gb300.binding import ABC_ERR_INVALID_ARG, AbcRegion, prior_box
+    box = prior_box()
+    obs = np.zeros((3, 11), dtype=np.int32)
+    obs[0, 0] = 5
+    good = dict(observed=obs.ctypes.data, T=10, N_pop=1000, eps=1.0, n_samples=10, first_index=0, stream=0,
+                capacity=4, theta_in=None)
+
+    def create(regs, n=None):
+        arr = (AbcRegion * max(1, len(regs)))(*[AbcRegion(**r) for r in regs])
+        h = ctypes.c_void_p()
+        return L.abc_plan_create(ctypes.byref(box), arr, len(regs) if n is None else n, 1, 1, ctypes.byref(h))
+
+    assert create([good], n=0) == ABC_ERR_INVALID_ARG
+    assert create([good], n=33) == ABC_ERR_INVALID_ARG
+    for bad in (dict(T=0), dict(T=5000), dict(N_pop=0), dict(eps=-1.0), dict(eps=float("nan")),
+                dict(stream=2**30), dict(observed=None)):
+        assert create([good, dict(good, **bad)]) == ABC_ERR_INVALID_ARG, bad
+        assert "region 1" in L.abc_last_error().decode()
+    big = obs.copy()
+    big[:, 0] = [900, 90, 20]
+    assert create([dict(good, observed=big.ctypes.data)]) == ABC_ERR_INVALID_ARG
+    assert L.abc_plan_run(None, None) == ABC_ERR_INVALID_ARG
+    assert L.abc_plan_destroy(None) == ABC_ERR_INVALID_ARG

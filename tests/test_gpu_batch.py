@@ -1,0 +1,137 @@
+"""Batched regions (abc_plan_*): one persistent launch over a table of regions
+with their own population, horizon, eps, observed series, random stream and
+sample range must give, region by region, exactly the accept sets of the
+oracle (exact mode) and of abc_sample (both modes); runs advance the sample
+ranges, CUDA-graph replays equal plain runs, proposal buffers replace the
+prior draw, and the autotuner leaves the plan's state unchanged."""
+import numpy as np
+import pytest
+
+import oracle
+from tests import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_2012_14332_gb300 as abc  # noqa: E402
+from paper_2012_14332_gb300 import build as _build  # noqa: E402
+
+_build.build()
+DEV = torch.device("cuda", 0)
+NAMES = ["region_1e7_T60", "region_6e7_T90", "region_3p3e8_T120", "region_1e6_T49"]
+SEED = 4711
+
+
+def _sorted(theta, dist, idx):
+    o = torch.argsort(idx)
+    return theta[o].cpu().numpy(), dist[o].cpu().numpy(), idx[o].cpu().numpy().astype(np.uint64)
+
+
+def _regions(n_list, first_list, quantile=0.01):
+    regs = []
+    for r, (name, n, first) in enumerate(zip(NAMES, n_list, first_list)):
+        w = inputs.workload(name)
+        ref = oracle.abc(w["observed"], w["P"], 0.0, max(n, 1), SEED, stream=10 + r, first_index=first,
+                         want_all=True, capacity=1)
+        eps = float(np.sort(ref["dist_all"])[int(quantile * max(n, 1))]) if n else 1e6
+        regs.append(dict(observed=w["observed"], N_pop=w["P"], eps=eps, n_samples=n, first_index=first,
+                         stream=10 + r, capacity=4096))
+    return regs
+
+
+def test_plan_exact_matches_oracle_per_region():
+    regs = _regions([6000, 7001, 5003, 0], [0, 10**9, (1 << 32) - 100, 5])
+    plan = abc.Plan(regs, SEED, mode="exact")
+    plan.run()
+    for r, g in enumerate(regs):
+        want = oracle.abc(g["observed"], g["N_pop"], g["eps"], g["n_samples"], SEED, stream=g["stream"],
+                          first_index=g["first_index"], capacity=max(g["n_samples"], 1))
+        th, di, ix, n_acc, days = plan.results(r)
+        th, di, ix = _sorted(th, di, ix)
+        assert n_acc == want["n_accepted"], r
+        assert np.array_equal(ix, want["idx"]) and np.array_equal(th, want["theta"]) and np.array_equal(di, want["dist"])
+        if g["n_samples"]:
+            assert 0 < days <= g["n_samples"] * (g["observed"].shape[1] - 1)
+    plan.close()
+
+
+@pytest.mark.parametrize("mode", ["exact", "fast"])
+def test_plan_equals_abc_sample_and_runs_advance(mode):
+    n = 40000
+    regs = _regions([n, n, n], [0, 777, 123456])
+    plan = abc.Plan(regs, SEED, mode=mode)
+    plan.run()
+    plan.run()
+    for r, g in enumerate(regs):
+        ref = abc.abc_sample(g["observed"], g["N_pop"], g["eps"], 2 * n, SEED, stream=g["stream"], mode=mode,
+                             first_index=g["first_index"], capacity=4096)
+        days_ref = abc.abc_last_simulated_days()
+        th, di, ix, n_acc, days = plan.results(r)
+        assert n_acc == ref[3]
+        assert days == days_ref
+        for a, b in zip(_sorted(th, di, ix), _sorted(*ref[:3])):
+            assert np.array_equal(a, b)
+    plan.close()
+
+
+def test_graph_replay_equals_runs():
+    n = 30000
+    regs = _regions([n, n // 3, n], [0, 50, 99])
+    a = abc.Plan(regs, SEED, mode="fast")
+    for _ in range(3):
+        a.run()
+    b = abc.Plan(regs, SEED, mode="fast")
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        b.run_graph(3, cuda_stream=s)
+    s.synchronize()
+    for r in range(len(regs)):
+        ra, rb = a.results(r), b.results(r)
+        assert ra[3] == rb[3] and ra[4] == rb[4]
+        for x, y in zip(_sorted(*ra[:3]), _sorted(*rb[:3])):
+            assert np.array_equal(x, y)
+    a.close()
+    b.close()
+
+
+def test_plan_with_proposal_buffer():
+    """theta_in replaces the prior draw: sample j of the run gets theta_in[j]
+    and the random numbers of index first_index + j."""
+    w = inputs.workload("region_1e6_T49")
+    n, first, stream = 3000, 222, 7
+    th = inputs.random_thetas(12, n)
+    th[:, 1] *= 0.1                                 # a narrower proposal than the prior
+    th_d = torch.from_numpy(th).to(DEV)
+    d = np.array([oracle.distance_from_sq(oracle.sq_distance(
+        oracle.simulate(th[j], w["observed"][:, 0], w["T"], w["P"], SEED, stream, first + j), w["observed"]))
+        for j in range(n)])
+    eps = float(np.sort(d)[150])
+    plan = abc.Plan([dict(observed=w["observed"], N_pop=w["P"], eps=eps, n_samples=n, first_index=first,
+                          stream=stream, capacity=n, theta_in=th_d)], SEED, mode="exact")
+    plan.run()
+    tt, di, ix, n_acc, _ = plan.results(0)
+    tt, di, ix = _sorted(tt, di, ix)
+    want = np.nonzero(d <= eps)[0]
+    assert n_acc == len(want)
+    assert np.array_equal(ix, want + first) and np.array_equal(di, d[want]) and np.array_equal(tt, th[want])
+    plan.close()
+
+
+def test_tune_keeps_state_and_picks_a_shape():
+    n = 1 << 18
+    regs = _regions([n, n, n], [0, 0, 0])
+    plan = abc.Plan(regs, SEED, mode="fast")
+    plan.run()
+    before = [plan.counts(r) for r in range(3)]
+    best, shapes = plan.tune()
+    assert len(shapes) >= 6 and best["ms"] == min(s["ms"] for s in shapes)
+    assert [plan.counts(r) for r in range(3)] == before
+    plan.run()
+    for r, g in enumerate(regs):
+        ref = abc.abc_sample(g["observed"], g["N_pop"], g["eps"], 2 * n, SEED, stream=g["stream"], mode="fast",
+                             first_index=g["first_index"], capacity=8192)
+        assert plan.counts(r)[0] == ref[3]
+    plan.close()

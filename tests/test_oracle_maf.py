@@ -1,0 +1,160 @@
+"""Pins of the float64 MAF proposal oracle against what the mathematics of a
+normalising flow fixes: exact invertibility, the log-determinant against a
+numerical Jacobian, triangular (autoregressive) Jacobians, normalisation by
+importance sampling, gradients against finite differences, Adam's closed-form
+first step, and maximum likelihood recovering a known Gaussian."""
+import numpy as np
+import pytest
+
+from oracle import maf_oracle as maf
+
+H_SMALL = 32
+
+
+@pytest.fixture
+def params():
+    return maf.init_params(np.random.default_rng(0), K=3, H=H_SMALL, scale=0.8)
+
+
+def test_masks_are_autoregressive():
+    M1, M2 = maf.masks(256)
+    # output j may depend on input i only through a path i -> l -> j with i < j
+    dep = (M2[:8] @ M1) > 0
+    assert not np.any(np.triu(dep))          # no dependence on inputs >= j
+    assert np.all(dep[np.tril_indices(8, -1)])  # every earlier input reaches j
+
+
+def test_inverse_roundtrip(params):
+    u = np.random.default_rng(1).normal(size=(200, 8))
+    y, logq_inv = maf.inverse(u, params)
+    z, logq_fwd, _ = maf.forward(y, params)
+    assert np.allclose(z, u, atol=1e-10)
+    assert np.allclose(logq_inv, logq_fwd, atol=1e-10)
+
+
+def _full_map(y, params):
+    z, _, _ = maf.forward(y[None, :], params)
+    return z[0]
+
+
+def test_logdet_matches_numerical_jacobian(params):
+    rng = np.random.default_rng(2)
+    for _ in range(5):
+        y = rng.normal(size=8)
+        J = np.zeros((8, 8))
+        h = 1e-6
+        for i in range(8):
+            e = np.zeros(8)
+            e[i] = h
+            J[:, i] = (_full_map(y + e, params) - _full_map(y - e, params)) / (2 * h)
+        z, logq, _ = maf.forward(y[None, :], params)
+        logdet = logq[0] + 0.5 * (z[0] ** 2).sum() + 4 * np.log(2 * np.pi)
+        assert np.isclose(np.linalg.slogdet(J)[1], logdet, atol=1e-6)
+
+
+def test_each_block_is_triangular(params):
+    M1, M2 = maf.masks(H_SMALL)
+    x = np.random.default_rng(3).normal(size=8)
+    for p in params:
+        J = np.zeros((8, 8))
+        for i in range(8):
+            e = np.zeros(8)
+            e[i] = 1e-6
+            mu1, a1, *_ = maf.made((x + e)[None], p, M1, M2)
+            mu0, a0, *_ = maf.made((x - e)[None], p, M1, M2)
+            z1 = ((x + e) - mu1[0]) * np.exp(-a1[0])
+            z0 = ((x - e) - mu0[0]) * np.exp(-a0[0])
+            J[:, i] = (z1 - z0) / 2e-6
+        assert np.allclose(np.triu(J, 1), 0, atol=1e-9)
+
+
+def test_density_is_normalised():
+    """The integral of q is 1: E_{y~p}[q(y)/p(y)] with p = N(0, 2^2 I), wider
+    than q, so the importance ratios stay bounded."""
+    params = maf.init_params(np.random.default_rng(9), K=3, H=H_SMALL, scale=0.3)
+    y = np.random.default_rng(4).normal(size=(400_000, 8)) * 2.0
+    _, logq, _ = maf.forward(y, params)
+    logp = -0.5 * (y ** 2).sum(axis=1) / 4 - 8 * np.log(2) - 4 * np.log(2 * np.pi)
+    r = np.exp(logq - logp)
+    assert abs(r.mean() - 1) < 5 * r.std() / np.sqrt(len(r))
+    assert r.std() / np.sqrt(len(r)) < 0.02
+
+
+def test_theta_density_change_of_variables(params):
+    lo = np.zeros(8)
+    hi = np.array([1, 100, 2, 1, 1, 1, 1, 2.0])
+    rng = np.random.default_rng(5)
+    th = lo + (hi - lo) * rng.uniform(0.05, 0.95, size=(20, 8))
+    y = maf.to_y(th, lo, hi)
+    assert np.allclose(maf.to_theta(y, lo, hi), th)
+    # d theta_j / d y_j numerically
+    h = 1e-6
+    num = np.log(np.abs((maf.to_theta(y + h, lo, hi) - maf.to_theta(y - h, lo, hi)) / (2 * h))).sum(axis=1)
+    assert np.allclose(maf.log_jacobian_y(y, lo, hi), num, atol=1e-6)
+    _, lq, _ = maf.forward(y, params)
+    assert np.allclose(maf.log_q_theta(th, params, lo, hi), lq - num, atol=1e-6)
+
+
+def test_gradient_matches_finite_differences(params):
+    rng = np.random.default_rng(6)
+    y = rng.normal(size=(64, 8))
+    w = rng.uniform(0.1, 2.0, size=64)
+    loss, grads = maf.loss_and_grad(y, w, params)
+    M1, M2 = maf.masks(H_SMALL)
+    masks = dict(W1=M1, W2=M2)
+    for k in range(3):
+        for key in ("W1", "b1", "W2", "b2"):
+            shape = params[k][key].shape
+            for _ in range(6):
+                idx = tuple(rng.integers(0, s) for s in shape)
+                if key in masks and masks[key][idx] == 0:
+                    assert grads[k][key][idx] == 0
+                    continue
+                old = params[k][key][idx]
+                params[k][key][idx] = old + 1e-6
+                lp, _ = maf.loss_and_grad(y, w, params)
+                params[k][key][idx] = old - 1e-6
+                lm, _ = maf.loss_and_grad(y, w, params)
+                params[k][key][idx] = old
+                num = (lp - lm) / 2e-6
+                assert np.isclose(grads[k][key][idx], num, rtol=1e-5, atol=1e-8), (k, key, idx)
+
+
+def test_adam_first_step_is_signed_learning_rate(params):
+    """After one step m_hat / sqrt(v_hat) = g / |g|: every weight with a
+    non-zero gradient moves by -lr sign(g) (up to eps)."""
+    y = np.random.default_rng(7).normal(size=(32, 8))
+    _, grads = maf.loss_and_grad(y, np.ones(32), params)
+    before = [{k: v.copy() for k, v in p.items()} for p in params]
+    maf.adam_step(params, grads, {}, lr=1e-2, eps=1e-12)
+    for p0, p1, g in zip(before, params, grads):
+        for key in p0:
+            nz = np.abs(g[key]) > 1e-9
+            assert np.allclose((p1[key] - p0[key])[nz], -1e-2 * np.sign(g[key][nz]), rtol=1e-6)
+            assert np.all(p1[key][~nz] == p0[key][~nz]) or np.allclose(p1[key][~nz], p0[key][~nz], atol=1e-2)
+
+
+def test_training_recovers_a_gaussian():
+    rng = np.random.default_rng(8)
+    A = np.tril(rng.normal(size=(8, 8)) * 0.3) + np.eye(8) * 0.7
+    m = rng.normal(size=8)
+    y = rng.normal(size=(4000, 8)) @ A.T + m
+    params = maf.init_params(rng, K=2, H=32, scale=0.3)
+    state = {}
+    for _ in range(1500):
+        b = rng.integers(0, len(y), 256)
+        _, g = maf.loss_and_grad(y[b], np.ones(256), params)
+        maf.adam_step(params, g, state, lr=3e-3)
+    u = rng.normal(size=(20000, 8))
+    ys, _ = maf.inverse(u, params)
+    assert np.allclose(ys.mean(axis=0), m, atol=0.15)
+    assert np.allclose(np.cov(ys.T), A @ A.T, atol=0.15)
+    # and the fitted density is close to the truth's entropy
+    _, lq, _ = maf.forward(y, params)
+    ent = 0.5 * np.linalg.slogdet(2 * np.pi * np.e * A @ A.T)[1]
+    assert abs(-lq.mean() - ent) < 0.1
+
+
+def test_ess_fraction():
+    assert maf.ess_fraction(np.ones(10)) == 1.0
+    assert np.isclose(maf.ess_fraction(np.array([1.0, 0, 0, 0])), 0.25)
