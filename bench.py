@@ -180,6 +180,39 @@ def bench_batched(abc, torch, steps, warmup, dev, flush, sm_count, sm_max):
             "roofline": roofline(days / steps, launch_ms, sm_count, sm_max)}
 
 
+def bench_learned(abc, torch, w, prior_value, peaks):
+    """Sequential ABC with the learned flow proposal on the P = 6e7, T = 100
+    region: 5 rounds of 2^22 simulations, eps shrinking by 0.7 per round to the
+    headline eps, flow of 3 MADE blocks x 256 hidden units (BF16 weights, FP32
+    accumulation). Compared with plain prior ABC at the same (final) eps."""
+    rounds, n, factor = 5, 1 << 22, 0.7
+    eps0 = w["eps"] / factor ** (rounds - 1)
+    info, th, wt, dist = abc.abc_smc_run(w["observed"], w["P"], eps0, rounds=rounds, sims_per_round=n,
+                                         eps_factor=factor, flow_blocks=3, flow_hidden=256, train_steps=500,
+                                         train_batch=1024, train_lr=1e-3, seed=w["seed"] + 17, capacity=1 << 18,
+                                         mode="fast")
+    last = info[-1]
+    ms = last["ms_propose"] + last["ms_simulate"]
+    flops = 3 * 8 * (16 * 256 + 32 * 256) * n      # per proposal: 3 blocks x 8 inverse passes x 2 products
+    peak = (peaks or {}).get("bf16_tflops", 1900.0)
+    out = {"workload": "sequential ABC, region_6e7_T100, %d rounds x %d simulations, eps0=%g, factor %g, final "
+                       "eps=%g (the headline eps), flow 3 x 256 BF16" % (rounds, n, eps0, factor, w["eps"]),
+           "rounds": [{k: (round(v, 4) if isinstance(v, float) else v) for k, v in r.items()} for r in info],
+           "final_round_accepted_per_s": last["n_accepted"] / (ms * 1e-3),
+           "final_round_effective_accepted_per_s": last["n_accepted"] * last["ess_fraction"] / (ms * 1e-3),
+           "final_round_acceptance": last["n_accepted"] / n,
+           "prior_accepted_per_s_same_eps": prior_value,
+           "gain_effective_vs_prior": last["n_accepted"] * last["ess_fraction"] / (ms * 1e-3) / prior_value,
+           "all_rounds_seconds": sum(r["ms_propose"] + r["ms_simulate"] + r["ms_train"] for r in info) * 1e-3}
+    if last["proposal"] == 1 and last["ms_propose"] > 0:
+        achieved = flops / (last["ms_propose"] * 1e-3) / 1e12
+        out["sampler_roofline"] = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                                   "frac": achieved / peak, "traffic": None,
+                                   "basis": "%d FLOP per proposal (3 blocks x 8 passes x (16 H + 32 H), H = 256), "
+                                            "peak = measured cuBLAS bf16 burst" % (flops // n)}
+    return out
+
+
 def oracle_sample(w, n, first_index, threads=0):
     """The CPU oracle (exact arithmetic) on n samples of the workload."""
     import oracle
@@ -235,6 +268,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--samples", type=int, default=0,
                     help="samples per launch (profiling runs on a smaller case; not a benchmark value)")
     args = ap.parse_args()
@@ -379,6 +413,8 @@ def main():
         }
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(w)
+        if not args.no_learned and world == 1:
+            line["learned_proposal"] = bench_learned(abc, torch, w, value, peaks)
         if not args.no_batched and world == 1:
             line["batched_regions"] = bench_batched(abc, torch, args.steps, args.warmup, dev, flush,
                                                     props.multi_processor_count, sm_max)

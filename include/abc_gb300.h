@@ -130,6 +130,20 @@ abc_status abc_step(const float* theta, const int32_t* state_in, const uint64_t*
 abc_status abc_kth_smallest(const double* dist, uint64_t n, uint64_t k, double* eps_out,
                             void* cuda_stream);
 
+/* Posterior-predictive projection (Sec. 5: accepted samples simulated forward
+ * for 120 days, plotted as 5th to 95th percentile bands). For b < B simulate
+ * theta[b] (DEVICE float [B][8]) with the random numbers of sample_index[b]
+ * (DEVICE uint64 [B]) from init_ard (HOST int32 [3]) for T days, then for every
+ * day d = 0..T and observed compartment c = A, R, D (0, 1, 2) write the
+ * q-quantiles of the B simulated values: bands_out[k][d][c] (DEVICE float
+ * [n_q][T+1][3]) = the floor(q_k (B - 1))-th smallest (order statistic,
+ * 0-based). quantiles: HOST double [n_q] in [0, 1]. 1 <= B <= 8192. Uses
+ * stream-ordered device scratch for the trajectories. Async on cuda_stream. */
+#define ABC_PROJECT_MAX_B 8192
+abc_status abc_project(const float* theta, const uint64_t* sample_index, uint64_t B, const int32_t* init_ard,
+                       int32_t T, int64_t N_pop, uint64_t seed, uint32_t stream, abc_mode mode,
+                       const double* quantiles, int32_t n_q, float* bands_out, void* cuda_stream);
+
 /* ------------------------------------------------------------------------
  * Batched regions (many regions, one persistent launch, CUDA-graph replay)
  * ------------------------------------------------------------------------
@@ -215,6 +229,139 @@ abc_status abc_plan_set_region(abc_plan plan, int32_t region, const float* theta
 
 /* Release the plan's device memory and graph. */
 abc_status abc_plan_destroy(abc_plan plan);
+
+/* ------------------------------------------------------------------------
+ * Learned proposal for sequential ABC: a masked autoregressive flow (MAF)
+ * ------------------------------------------------------------------------
+ * The paper's Sec. 2.2 points to sequential Monte Carlo ABC: a decreasing
+ * sequence of tolerances, each round built from the previous round's
+ * accepted samples. The library's proposal for the next round is a density
+ * q(theta) on the prior box, learned from the previous round's accepted,
+ * importance-weighted samples:
+ *  - y = logit((theta - lo) / (hi - lo)) (support = the box);
+ *  - n_blocks MADE blocks (one hidden ReLU layer of `hidden` units; output j
+ *    depends on inputs < j), each x -> z = (x - mu(x)) exp(-alpha(x)) with
+ *    alpha = 6 tanh(alpha_raw / 6), the order reversed between blocks; base
+ *    N(0, I);
+ *  - log q(theta) = log N(z) - sum alpha - sum_j log((hi_j - lo_j) s_j (1 - s_j)),
+ *    s = sigmoid(y).
+ * Weights live in FP32 (the master copy trained by Adam) and in masked BF16
+ * copies used by tensor-core products (mma.sync m16n8k8 / m16n8k16 BF16 with
+ * FP32 accumulation). Activations entering a product are rounded to BF16;
+ * everything else is FP32.
+ *
+ * Parameter order (host float arrays): for each block b = 0..n_blocks-1:
+ *   W1 [hidden][8] row-major, b1 [hidden], W2 [16][hidden] row-major
+ *   (rows 0..7 mu, 8..15 alpha_raw), b2 [16].
+ * Masked entries (W1[l][j] with (l mod 7) + 1 < j + 1, W2[o][l] with
+ * (o mod 8) + 1 <= (l mod 7) + 1) are ignored. */
+typedef struct abc_maf_s* abc_maf;
+
+/* Create a flow with n_blocks (1..4) blocks of `hidden` units (a multiple of
+ * 16, 16..256) on the prior box, parameters zero (q = the box's logistic
+ * image of N(0, I)). Allocates its device memory on the current device. */
+abc_status abc_maf_create(int32_t n_blocks, int32_t hidden, const abc_prior_box* box, abc_maf* maf_out);
+
+/* Random initial parameters: W1 ~ N(0, scale^2 / 8), W2 ~ N(0, scale^2 / hidden),
+ * zero biases (so the ReLU units start active and the flow near the base
+ * density), from a host generator seeded with `seed`; resets Adam. */
+abc_status abc_maf_init_random(abc_maf maf, uint64_t seed, float scale);
+
+/* Number of parameters (floats) in the order above. */
+int64_t abc_maf_param_count(abc_maf maf);
+
+/* Copy parameters from / to HOST float arrays (synchronous). Setting
+ * parameters also resets the Adam moments. */
+abc_status abc_maf_set_params(abc_maf maf, const float* params);
+abc_status abc_maf_get_params(abc_maf maf, float* params);
+
+/* Draw n proposals: base normals u (DEVICE float [n][8], or NULL to draw them
+ * with Philox from (seed, stream, first_index + j)), the sequential inverse of
+ * the flow, theta = lo + (hi - lo) sigmoid(y). theta_out DEVICE float [n][8];
+ * logq_out DEVICE float [n] (log q(theta)) or NULL. Async. */
+abc_status abc_maf_sample(abc_maf maf, uint64_t n, const float* base_normals, uint64_t seed, uint32_t stream,
+                          uint64_t first_index, float* theta_out, float* logq_out, void* cuda_stream);
+
+/* log q(theta) for n points (DEVICE float [n][8] inside the box) into logq_out
+ * (DEVICE float [n]). Async. */
+abc_status abc_maf_log_q(abc_maf maf, uint64_t n, const float* theta, float* logq_out, void* cuda_stream);
+
+/* Gradient of the weighted mean of -log q_y(y(theta)) over n points (theta
+ * DEVICE [n][8], weights DEVICE [n] >= 0 or NULL for all ones) into the flow's
+ * gradient buffer; *loss_out (HOST, may be NULL) gets the loss. Synchronizes
+ * cuda_stream. grads_out (HOST, may be NULL) receives the gradient in the
+ * parameter order. */
+abc_status abc_maf_gradient(abc_maf maf, uint64_t n, const float* theta, const float* weights, float* loss_out,
+                            float* grads_out, void* cuda_stream);
+
+/* One Adam step (Kingma and Ba) of the master parameters with the flow's
+ * current gradient, then refresh the BF16 copies. Async. */
+abc_status abc_maf_adam_step(abc_maf maf, float lr, float beta1, float beta2, float eps, void* cuda_stream);
+
+/* Weighted maximum-likelihood training: n_steps Adam steps, each on a batch of
+ * `batch` rows drawn with replacement (Philox, seed) from the n points
+ * (theta DEVICE [n][8], weights DEVICE [n] or NULL). The steps are captured in
+ * a CUDA graph and replayed. *loss_out (HOST, may be NULL) gets the full-data
+ * loss after training. Synchronizes cuda_stream (a non-default stream is
+ * required for the graph). */
+abc_status abc_maf_train(abc_maf maf, uint64_t n, const float* theta, const float* weights, int32_t n_steps,
+                         int32_t batch, float lr, uint64_t seed, float* loss_out, void* cuda_stream);
+
+abc_status abc_maf_destroy(abc_maf maf);
+
+/* Sequential ABC with the learned proposal (the SMC-ABC idea of Sec. 2.2):
+ * round r simulates sims_per_round proposals at tolerance
+ * eps_r = eps0 * eps_factor^r. Round 0 draws from the prior. After each round
+ * the flow is trained (weighted maximum likelihood) on that round's accepted
+ * samples with importance weights w = prior(theta) / q(theta) (w = 1 for
+ * prior draws), and the next round draws from the flow, unless the round's
+ * effective sample size (sum w)^2 / sum w^2 fell below ess_min times its
+ * accept count (or it accepted fewer than 64), in which case the next round
+ * falls back to the prior. A flow round draws a fraction `defensive` of its
+ * proposals from the prior and weights every proposal by the mixture density
+ * q_mix = (1 - defensive) q + defensive * prior (defensive importance sampling,
+ * Hesterberg 1995), so w = prior / q_mix <= 1 / defensive.
+ * Accepted draws keep their weights, so the weighted
+ * accepted samples of every round estimate the ABC posterior at its
+ * tolerance (Eq. 7). Simulations use (seed, stream 0, index r *
+ * sims_per_round + j); flow draws use (seed, stream 1, the same index). */
+typedef struct {
+    int32_t rounds;           /* >= 1 */
+    uint64_t sims_per_round;  /* proposals simulated per round */
+    double eps0;              /* tolerance of round 0 */
+    double eps_factor;        /* in (0, 1] */
+    double ess_min;           /* fraction, e.g. 0.1 */
+    int32_t flow_blocks;      /* 1..4 */
+    int32_t flow_hidden;      /* multiple of 16, <= 256 */
+    int32_t train_steps;      /* Adam steps per round */
+    int32_t train_batch;      /* rows per step (>= 16) */
+    float train_lr;
+    uint64_t seed;
+    uint64_t capacity;        /* accepted samples kept per round */
+    abc_mode mode;
+    double defensive;         /* prior fraction of a flow round's proposals, in [0, 1) (e.g. 0.1) */
+} abc_smc_config;
+
+typedef struct {
+    double eps;
+    int32_t proposal;         /* 0 = prior, 1 = flow */
+    uint64_t n_sims;
+    uint64_t n_accepted;
+    uint64_t simulated_days;
+    double ess_fraction;      /* ESS / n_accepted of this round's weights */
+    float train_loss;         /* flow loss after training on this round (0 if not trained) */
+    float ms_propose, ms_simulate, ms_train;
+} abc_smc_round;
+
+/* Run cfg->rounds rounds on one region (observed HOST [3][T+1], population
+ * N_pop). rounds_out (HOST [cfg->rounds]) receives per-round statistics. The
+ * last round's accepted samples go to theta_out (DEVICE float [capacity][8]),
+ * weight_out (DEVICE double [capacity], w = prior / q, normalised to sum 1),
+ * dist_out (DEVICE double [capacity]); *n_out (HOST) their number (at most
+ * capacity). Synchronizes cuda_stream (a non-default stream is required). */
+abc_status abc_smc_run(const abc_prior_box* prior, const int32_t* observed, int32_t T, int64_t N_pop,
+                       const abc_smc_config* cfg, abc_smc_round* rounds_out, float* theta_out,
+                       double* weight_out, double* dist_out, uint64_t* n_out, void* cuda_stream);
 
 /* Variant of abc_sample that allocates no memory. It is for callers that must
  * not allocate device memory while sampling: code running inside a host

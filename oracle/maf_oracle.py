@@ -51,18 +51,32 @@ def init_params(rng, K=3, H=256, D=D, scale=0.1):
     return out
 
 
-def made(x, p, M1, M2):
-    """One MADE: returns (mu, alpha, alpha_raw, hidden pre-activation, hidden)."""
-    a1 = x @ (p["W1"] * M1).T + p["b1"]
+def round_bf16(a):
+    """Round to the nearest bfloat16 (ties to even), returned as float64."""
+    f = np.asarray(a, dtype=np.float32)
+    b = f.view(np.uint32).astype(np.uint64)
+    r = ((b + 0x7FFF + ((b >> 16) & 1)) >> 16) << 16
+    out = r.astype(np.uint32).view(np.float32).astype(np.float64)
+    return np.where(np.isfinite(f), out, f.astype(np.float64))
+
+
+def made(x, p, M1, M2, bf16=False):
+    """One MADE: returns (mu, alpha, alpha_raw, hidden pre-activation, hidden).
+    bf16=True rounds the two matrix products' inputs (x, h and the weights) to
+    bfloat16, the precision of a BF16 tensor-core product with FP32 sums."""
+    W1, W2 = p["W1"] * M1, p["W2"] * M2
+    if bf16:
+        x, W1, W2 = round_bf16(x), round_bf16(W1), round_bf16(W2)
+    a1 = x @ W1.T + p["b1"]
     h = np.maximum(a1, 0.0)
-    out = h @ (p["W2"] * M2).T + p["b2"]
+    out = (round_bf16(h) if bf16 else h) @ W2.T + p["b2"]
     mu = out[:, :D]
     araw = out[:, D:]
     alpha = ALPHA_MAX * np.tanh(araw / ALPHA_MAX)
     return mu, alpha, araw, a1, h
 
 
-def forward(y, params):
+def forward(y, params, bf16=False):
     """y [N, D] -> (z [N, D] after the last reversal, log q_y [N], per-block caches)."""
     H = params[0]["W1"].shape[0]
     M1, M2 = masks(H)
@@ -70,7 +84,7 @@ def forward(y, params):
     logdet = np.zeros(x.shape[0])
     caches = []
     for p in params:
-        mu, alpha, araw, a1, h = made(x, p, M1, M2)
+        mu, alpha, araw, a1, h = made(x, p, M1, M2, bf16)
         z = (x - mu) * np.exp(-alpha)
         logdet -= alpha.sum(axis=1)
         caches.append(dict(x=x, mu=mu, alpha=alpha, araw=araw, a1=a1, h=h, z=z))
@@ -79,7 +93,7 @@ def forward(y, params):
     return x, logq, caches
 
 
-def inverse(u, params):
+def inverse(u, params, bf16=False):
     """Base normals u [N, D] -> (y [N, D], log q_y [N]) by the sequential inverse."""
     H = params[0]["W1"].shape[0]
     M1, M2 = masks(H)
@@ -89,9 +103,9 @@ def inverse(u, params):
         z = x[:, ::-1]
         xin = np.zeros_like(z)
         for j in range(D):
-            mu, alpha, _, _, _ = made(xin, p, M1, M2)
+            mu, alpha, _, _, _ = made(xin, p, M1, M2, bf16)
             xin[:, j] = z[:, j] * np.exp(alpha[:, j]) + mu[:, j]
-        mu, alpha, _, _, _ = made(xin, p, M1, M2)
+        mu, alpha, _, _, _ = made(xin, p, M1, M2, bf16)
         logq -= alpha.sum(axis=1)
         x = xin
     return x, logq
@@ -116,9 +130,9 @@ def log_jacobian_y(y, lo, hi):
     return (np.log(w) - np.logaddexp(0, -y) - np.logaddexp(0, y)).sum(axis=1)
 
 
-def log_q_theta(theta, params, lo, hi):
+def log_q_theta(theta, params, lo, hi, bf16=False):
     y = to_y(theta, lo, hi)
-    _, logq_y, _ = forward(y, params)
+    _, logq_y, _ = forward(y, params, bf16)
     return logq_y - log_jacobian_y(y, lo, hi)
 
 
@@ -174,3 +188,20 @@ def adam_step(params, grads, state, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
 def ess_fraction(w):
     w = np.asarray(w, dtype=np.float64)
     return (w.sum() ** 2) / (w ** 2).sum() / len(w)
+
+
+def flat(params):
+    """Parameters in the library's order: per block W1, b1, W2, b2 (row-major)."""
+    return np.concatenate([np.concatenate([p["W1"].ravel(), p["b1"], p["W2"].ravel(), p["b2"]]) for p in params])
+
+
+def unflat(v, K, H):
+    out, o = [], 0
+    for _ in range(K):
+        W1 = v[o:o + H * D].reshape(H, D); o += H * D
+        b1 = v[o:o + H]; o += H
+        W2 = v[o:o + 2 * D * H].reshape(2 * D, H); o += 2 * D * H
+        b2 = v[o:o + 2 * D]; o += 2 * D
+        out.append(dict(W1=W1.astype(np.float64), b1=b1.astype(np.float64), W2=W2.astype(np.float64),
+                        b2=b2.astype(np.float64)))
+    return out

@@ -4,6 +4,7 @@ COVID-19 model (Kulkarni, Krell, Nabarro, Moritz 2020).
 The computation runs in the CUDA library ``libabc_gb300.so`` behind the C ABI
 of ``include/abc_gb300.h``; ``binding`` marshals arguments to it.
 """
-from .binding import (ABC_EXACT, ABC_FAST, ABC_T_MAX, PAPER_HI, PAPER_LO, AbcError, Plan, abc_distances,  # noqa: F401
-                      abc_kth_smallest, abc_last_simulated_days, abc_sample, abc_sample_noalloc, abc_simulate, abc_step, abc_strerror, abc_version, load,
-                      prior_box)
+from .binding import (ABC_EXACT, ABC_FAST, ABC_MAX_REGIONS, ABC_NOALLOC_T_MAX, ABC_T_MAX,  # noqa: F401
+                      PAPER_HI, PAPER_LO, AbcError, Flow, Plan, abc_distances, abc_kth_smallest,
+                      abc_last_simulated_days, abc_project, abc_sample, abc_sample_noalloc, abc_simulate,
+                      abc_smc_run, abc_step, abc_strerror, abc_version, load, prior_box)

@@ -24,7 +24,9 @@ PAPER_HI = (1.0, 100.0, 2.0, 1.0, 1.0, 1.0, 1.0, 2.0)   # Sec. 2.1, Eq. 2
 EXPORTED = ("abc_sample", "abc_distances", "abc_simulate", "abc_step", "abc_kth_smallest", "abc_strerror",
             "abc_last_error", "abc_version", "abc_last_simulated_days", "abc_sample_noalloc", "abc_plan_create",
             "abc_plan_reset", "abc_plan_run", "abc_plan_run_graph", "abc_plan_tune", "abc_plan_results",
-            "abc_plan_copy_results", "abc_plan_set_region", "abc_plan_destroy")
+            "abc_plan_copy_results", "abc_plan_set_region", "abc_plan_destroy", "abc_maf_create",
+            "abc_maf_init_random", "abc_maf_param_count", "abc_maf_set_params", "abc_maf_get_params", "abc_maf_sample", "abc_maf_log_q",
+            "abc_maf_gradient", "abc_maf_adam_step", "abc_maf_train", "abc_maf_destroy", "abc_smc_run", "abc_project")
 ABC_MAX_REGIONS = 32
 ABC_NOALLOC_T_MAX = 1024
 
@@ -42,6 +44,21 @@ class AbcRegion(ctypes.Structure):
 class AbcLaunchShape(ctypes.Structure):
     _fields_ = [("block_threads", ctypes.c_int32), ("pairs_per_iteration", ctypes.c_int32),
                 ("blocks_per_sm", ctypes.c_int32), ("ms", ctypes.c_float)]
+
+
+class AbcSmcConfig(ctypes.Structure):
+    _fields_ = [("rounds", ctypes.c_int32), ("sims_per_round", ctypes.c_uint64), ("eps0", ctypes.c_double),
+                ("eps_factor", ctypes.c_double), ("ess_min", ctypes.c_double), ("flow_blocks", ctypes.c_int32),
+                ("flow_hidden", ctypes.c_int32), ("train_steps", ctypes.c_int32), ("train_batch", ctypes.c_int32),
+                ("train_lr", ctypes.c_float), ("seed", ctypes.c_uint64), ("capacity", ctypes.c_uint64),
+                ("mode", ctypes.c_int), ("defensive", ctypes.c_double)]
+
+
+class AbcSmcRound(ctypes.Structure):
+    _fields_ = [("eps", ctypes.c_double), ("proposal", ctypes.c_int32), ("n_sims", ctypes.c_uint64),
+                ("n_accepted", ctypes.c_uint64), ("simulated_days", ctypes.c_uint64),
+                ("ess_fraction", ctypes.c_double), ("train_loss", ctypes.c_float), ("ms_propose", ctypes.c_float),
+                ("ms_simulate", ctypes.c_float), ("ms_train", ctypes.c_float)]
 
 
 class AbcError(RuntimeError):
@@ -101,6 +118,28 @@ def load(path=None):
         for nm in ("abc_plan_create", "abc_plan_reset", "abc_plan_run", "abc_plan_run_graph", "abc_plan_tune",
                    "abc_plan_results", "abc_plan_copy_results", "abc_plan_set_region", "abc_plan_destroy"):
             getattr(L, nm).restype = ctypes.c_int
+        L.abc_maf_create.argtypes = [i32, i32, box, ctypes.POINTER(pp)]
+        L.abc_maf_init_random.argtypes = [pp, u64, ctypes.c_float]
+        L.abc_maf_init_random.restype = ctypes.c_int
+        L.abc_maf_param_count.argtypes = [pp]
+        L.abc_maf_param_count.restype = ctypes.c_int64
+        L.abc_maf_set_params.argtypes = [pp, vp]
+        L.abc_maf_get_params.argtypes = [pp, vp]
+        L.abc_maf_sample.argtypes = [pp, u64, vp, u64, u32, u64, vp, vp, vp]
+        L.abc_maf_log_q.argtypes = [pp, u64, vp, vp, vp]
+        L.abc_maf_gradient.argtypes = [pp, u64, vp, vp, ctypes.POINTER(ctypes.c_float), vp, vp]
+        L.abc_maf_adam_step.argtypes = [pp, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, vp]
+        L.abc_maf_train.argtypes = [pp, u64, vp, vp, i32, i32, ctypes.c_float, u64, ctypes.POINTER(ctypes.c_float),
+                                    vp]
+        L.abc_maf_destroy.argtypes = [pp]
+        for nm in ("abc_maf_create", "abc_maf_set_params", "abc_maf_get_params", "abc_maf_sample", "abc_maf_log_q",
+                   "abc_maf_gradient", "abc_maf_adam_step", "abc_maf_train", "abc_maf_destroy", "abc_smc_run", "abc_project"):
+            getattr(L, nm).restype = ctypes.c_int
+        L.abc_project.argtypes = [vp, vp, u64, vp, i32, i64, u64, u32, ctypes.c_int, vp, i32, vp, vp]
+        L.abc_project.restype = ctypes.c_int
+        L.abc_smc_run.argtypes = [box, vp, i32, i64, ctypes.POINTER(AbcSmcConfig), ctypes.POINTER(AbcSmcRound), vp, vp,
+                                  vp, ctypes.POINTER(ctypes.c_uint64), vp]
+        L.abc_smc_run.restype = ctypes.c_int
         L.abc_last_simulated_days.argtypes = []
         L.abc_last_simulated_days.restype = ctypes.c_uint64
         if path is None:
@@ -398,3 +437,170 @@ def abc_plan_set_region(plan, region, theta_in=None, first_index=0):
 
 def abc_plan_destroy(plan):
     plan.close()
+
+
+
+class Flow:
+    """Masked autoregressive flow proposal on the prior box (C ABI abc_maf_*)."""
+
+    def __init__(self, n_blocks=3, hidden=256, lo=PAPER_LO, hi=PAPER_HI):
+        L = load()
+        self._L = L
+        h = ctypes.c_void_p()
+        b = prior_box(lo, hi)
+        _check(L, L.abc_maf_create(int(n_blocks), int(hidden), ctypes.byref(b), ctypes.byref(h)))
+        self._h = h
+        self.n_blocks, self.hidden = int(n_blocks), int(hidden)
+        self.n_params = int(L.abc_maf_param_count(h))
+
+    def init_random(self, seed=0, scale=0.3):
+        _check(self._L, self._L.abc_maf_init_random(self._h, int(seed), float(scale)))
+
+    def set_params(self, params):
+        v = np.ascontiguousarray(np.asarray(params, dtype=np.float32).ravel())
+        assert v.size == self.n_params
+        _check(self._L, self._L.abc_maf_set_params(self._h, v.ctypes.data))
+
+    def get_params(self):
+        v = np.empty(self.n_params, dtype=np.float32)
+        _check(self._L, self._L.abc_maf_get_params(self._h, v.ctypes.data))
+        return v
+
+    def sample(self, n, seed=0, stream=0, first_index=0, base_normals=None, want_logq=True, out=None,
+               cuda_stream=None):
+        dev = torch.device("cuda", torch.cuda.current_device())
+        if out is None:
+            theta = torch.empty((n, 8), dtype=torch.float32, device=dev)
+            logq = torch.empty((n,), dtype=torch.float32, device=dev) if want_logq else None
+        else:
+            theta, logq = out
+        u = base_normals.data_ptr() if base_normals is not None else None
+        _check(self._L, self._L.abc_maf_sample(self._h, int(n), u, int(seed), int(stream), int(first_index),
+                                               theta.data_ptr(), logq.data_ptr() if logq is not None else None,
+                                               _stream(cuda_stream)))
+        return theta, logq
+
+    def log_q(self, theta, cuda_stream=None):
+        n = theta.shape[0]
+        out = torch.empty((n,), dtype=torch.float32, device=theta.device)
+        _check(self._L, self._L.abc_maf_log_q(self._h, n, theta.data_ptr(), out.data_ptr(), _stream(cuda_stream)))
+        return out
+
+    def gradient(self, theta, weights=None, cuda_stream=None):
+        """(loss, gradient as a float32 numpy vector in the parameter order)."""
+        loss = ctypes.c_float()
+        g = np.empty(self.n_params, dtype=np.float32)
+        _check(self._L, self._L.abc_maf_gradient(self._h, theta.shape[0], theta.data_ptr(),
+                                                 weights.data_ptr() if weights is not None else None,
+                                                 ctypes.byref(loss), g.ctypes.data, _stream(cuda_stream)))
+        return float(loss.value), g
+
+    def adam_step(self, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, cuda_stream=None):
+        _check(self._L, self._L.abc_maf_adam_step(self._h, lr, beta1, beta2, eps, _stream(cuda_stream)))
+
+    def train(self, theta, weights=None, n_steps=500, batch=1024, lr=1e-3, seed=0, cuda_stream=None):
+        s = cuda_stream if cuda_stream is not None else torch.cuda.Stream()
+        torch.cuda.current_stream().synchronize()
+        loss = ctypes.c_float()
+        _check(self._L, self._L.abc_maf_train(self._h, theta.shape[0], theta.data_ptr(),
+                                              weights.data_ptr() if weights is not None else None, int(n_steps),
+                                              int(batch), float(lr), int(seed), ctypes.byref(loss), _stream(s)))
+        return float(loss.value)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.abc_maf_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+abc_maf_create = Flow
+
+
+def abc_maf_init_random(flow, seed=0, scale=0.3):
+    flow.init_random(seed, scale)
+
+
+def abc_maf_param_count(flow):
+    return flow.n_params
+
+
+def abc_maf_set_params(flow, params):
+    flow.set_params(params)
+
+
+def abc_maf_get_params(flow):
+    return flow.get_params()
+
+
+def abc_maf_sample(flow, n, **kw):
+    return flow.sample(n, **kw)
+
+
+def abc_maf_log_q(flow, theta, cuda_stream=None):
+    return flow.log_q(theta, cuda_stream)
+
+
+def abc_maf_gradient(flow, theta, weights=None, cuda_stream=None):
+    return flow.gradient(theta, weights, cuda_stream)
+
+
+def abc_maf_adam_step(flow, **kw):
+    flow.adam_step(**kw)
+
+
+def abc_maf_train(flow, theta, weights=None, **kw):
+    return flow.train(theta, weights, **kw)
+
+
+def abc_maf_destroy(flow):
+    flow.close()
+
+
+
+def abc_smc_run(observed, N_pop, eps0, rounds=5, sims_per_round=1 << 22, eps_factor=0.7, ess_min=0.1,
+                flow_blocks=3, flow_hidden=256, train_steps=500, train_batch=1024, train_lr=1e-3, seed=0,
+                capacity=1 << 16, mode="fast", defensive=0.1, lo=PAPER_LO, hi=PAPER_HI, cuda_stream=None):
+    """Sequential ABC with the learned flow proposal. Returns (rounds: list of
+    dicts, theta [m, 8], weights [m] (f64, sum 1), dist [m]) of the last round."""
+    L = load()
+    obs, obs_p = _host_i32(observed)
+    T = obs.shape[1] - 1
+    cfg = AbcSmcConfig(int(rounds), int(sims_per_round), float(eps0), float(eps_factor), float(ess_min),
+                       int(flow_blocks), int(flow_hidden), int(train_steps), int(train_batch), float(train_lr),
+                       int(seed), int(capacity), _mode(mode), float(defensive))
+    rr = (AbcSmcRound * int(rounds))()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    theta = torch.empty((capacity, 8), dtype=torch.float32, device=dev)
+    w = torch.empty((capacity,), dtype=torch.float64, device=dev)
+    dist = torch.empty((capacity,), dtype=torch.float64, device=dev)
+    n = ctypes.c_uint64()
+    s = cuda_stream if cuda_stream is not None else torch.cuda.Stream()
+    torch.cuda.current_stream().synchronize()
+    b = prior_box(lo, hi)
+    _check(L, L.abc_smc_run(ctypes.byref(b), obs_p, T, int(N_pop), ctypes.byref(cfg), rr, theta.data_ptr(),
+                            w.data_ptr(), dist.data_ptr(), ctypes.byref(n), _stream(s)))
+    out = [dict((f, getattr(r, f)) for f, _ in AbcSmcRound._fields_) for r in rr]
+    m = int(n.value)
+    return out, theta[:m], w[:m], dist[:m]
+
+
+
+def abc_project(theta, sample_index, init_ard, T, N_pop, seed, quantiles=(0.05, 0.5, 0.95), stream=0, mode="fast",
+                cuda_stream=None):
+    """Quantile bands [n_q, T+1, 3] (A, R, D) of trajectories simulated from
+    theta [B, 8] (CUDA f32) with sample_index [B] (CUDA int64)."""
+    L = load()
+    B = theta.shape[0]
+    q = np.ascontiguousarray(np.asarray(quantiles, dtype=np.float64))
+    bands = torch.empty((len(q), T + 1, 3), dtype=torch.float32, device=theta.device)
+    a, a_p = _host_i32(init_ard)
+    _check(L, L.abc_project(_dev(theta, torch.float32, (B, 8)), _dev(sample_index, torch.int64, (B,)), B, a_p,
+                            int(T), int(N_pop), int(seed), int(stream), _mode(mode), q.ctypes.data, len(q),
+                            bands.data_ptr(), _stream(cuda_stream)))
+    return bands

@@ -421,6 +421,43 @@ abc_status abc_step(const float* theta, const int32_t* state_in, const uint64_t*
     return ok();
 }
 
+abc_status abc_project(const float* theta, const uint64_t* sample_index, uint64_t B, const int32_t* init_ard,
+                       int32_t T, int64_t N_pop, uint64_t seed, uint32_t stream, abc_mode mode,
+                       const double* quantiles, int32_t n_q, float* bands_out, void* cuda_stream)
+{
+    abc_status st;
+    if ((st = check_model(T, N_pop, stream)) != ABC_OK) return st;
+    if (mode != ABC_EXACT && mode != ABC_FAST) return fail(ABC_ERR_INVALID_ARG, "unknown mode %d", (int)mode);
+    if ((st = check_initial(init_ard, N_pop)) != ABC_OK) return st;
+    if (B < 1 || B > ABC_PROJECT_MAX_B) return fail(ABC_ERR_INVALID_ARG, "B must be in [1, %d]", ABC_PROJECT_MAX_B);
+    if (!theta || !sample_index || !bands_out || !quantiles || n_q < 1 || n_q > 1024)
+        return fail(ABC_ERR_INVALID_ARG, "NULL buffer or n_q outside [1, 1024]");
+    std::vector<float> qpos((size_t)n_q);
+    for (int32_t k = 0; k < n_q; ++k) {
+        if (!(quantiles[k] >= 0.0 && quantiles[k] <= 1.0)) return fail(ABC_ERR_INVALID_ARG, "quantile outside [0, 1]");
+        qpos[k] = (float)std::floor(quantiles[k] * (double)(B - 1));
+    }
+    const abcgb::ModelParams p = make_params(nullptr, T, N_pop, seed, stream, init_ard);
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    Scratch sc;
+    const size_t traj_bytes = sizeof(int32_t) * 6 * (size_t)(T + 1) * B;
+    if ((st = alloc_scratch(sc, traj_bytes + sizeof(float) * n_q, s)) != ABC_OK) return st;
+    int32_t* traj = (int32_t*)sc.ptr;
+    float* qd = (float*)((char*)sc.ptr + traj_bytes);
+    CUDA_TRY(cudaMemcpyAsync(qd, qpos.data(), sizeof(float) * n_q, cudaMemcpyHostToDevice, s), "cudaMemcpyAsync(q)");
+    abcgb::SimulateArgs a;
+    a.theta = theta;
+    a.sample_index = sample_index;
+    a.B = B;
+    a.traj_out = traj;
+    if (injected("launch")) return fail(ABC_ERR_CUDA, "kernel launch failed (injected)");
+    CUDA_TRY(abcgb::launch_simulate(p, a, mode == ABC_FAST, s), "abc_simulate_kernel launch");
+    CUDA_TRY(abcgb::launch_bands(traj, (uint32_t)B, T, qd, n_q, bands_out, s), "band_kernel launch");
+    // qpos (host) was staged synchronously enough: wait for the copy before it leaves scope
+    CUDA_TRY(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+    return ok();
+}
+
 abc_status abc_kth_smallest(const double* dist, uint64_t n, uint64_t k, double* eps_out, void* cuda_stream)
 {
     if (!dist || !eps_out) return fail(ABC_ERR_INVALID_ARG, "NULL pointer");

@@ -245,6 +245,44 @@ __global__ void __launch_bounds__(kBlockThreads) abc_step_kernel(const __grid_co
 }
 
 // ---------------------------------------------------------------------------
+// Quantile bands of trajectories: one block per (day, compartment) column,
+// the B values sorted in shared memory by a bitonic network (padded to a power
+// of two with INT_MAX), then order statistics floor(q (B - 1)).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kBlockThreads) band_kernel(const int32_t* __restrict__ traj, uint32_t B, int32_t T,
+                                                             const float* __restrict__ qpos, int32_t n_q,
+                                                             float* __restrict__ bands)
+{
+    extern __shared__ int32_t v[];
+    const int32_t d = blockIdx.x / 3, c = blockIdx.x % 3;
+    uint32_t n2 = 1;
+    while (n2 < B) n2 <<= 1;
+    for (uint32_t b = threadIdx.x; b < n2; b += blockDim.x)
+        v[b] = b < B ? traj[((size_t)b * (T + 1) + d) * 6 + 2 + c] : 0x7FFFFFFF;
+    __syncthreads();
+    for (uint32_t k = 2; k <= n2; k <<= 1) {
+        for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+            for (uint32_t i = threadIdx.x; i < n2; i += blockDim.x) {
+                const uint32_t p = i ^ j;
+                if (p > i) {
+                    const bool up = (i & k) == 0;
+                    const int32_t a = v[i], b2 = v[p];
+                    if ((a > b2) == up) {
+                        v[i] = b2;
+                        v[p] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int32_t k = threadIdx.x; k < n_q; k += blockDim.x) {
+        const uint32_t r = (uint32_t)qpos[k];
+        bands[((size_t)k * (T + 1) + d) * 3 + c] = (float)v[r];
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Radix select of the k-th smallest distance: histogram of one 8-bit digit of
 // the keys (the bit patterns of non-negative doubles order like the values)
 // among the keys whose higher digits equal `prefix`.
@@ -376,6 +414,20 @@ cudaError_t launch_step(const ModelParams& p, const StepArgs& a, bool fast, cuda
         abc_step_kernel<kFast><<<grid, kBlockThreads, 0, s>>>(p, a);
     else
         abc_step_kernel<kExact><<<grid, kBlockThreads, 0, s>>>(p, a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bands(const int32_t* traj, uint32_t B, int32_t T, const float* qpos, int32_t n_q, float* bands,
+                         cudaStream_t s)
+{
+    uint32_t n2 = 1;
+    while (n2 < B) n2 <<= 1;
+    const size_t smem = sizeof(int32_t) * n2;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(band_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    band_kernel<<<3 * (T + 1), kBlockThreads, smem, s>>>(traj, B, T, qpos, n_q, bands);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,1018 @@
+// abc_maf.cu -- masked autoregressive flow proposal for sequential ABC:
+// density, sampling (sequential inverse), weighted maximum-likelihood
+// gradient and Adam, with BF16 tensor-core products (mma.sync m16n8k8 and
+// m16n8k16, FP32 accumulation).
+//
+// A warp owns 16 rows (samples). A row's eight coordinates sit in the
+// accumulator layout of an m16n8 tile: lane (g = lane / 4, t = lane % 4) holds
+// columns 2t, 2t+1 of rows g and g+8. That is also the A-operand layout of an
+// m16n8k8 product, so a MADE block runs entirely in registers:
+//   layer 1  a1 = x W1^T + b1  : per 16 hidden units two m16n8k8 products;
+//   layer 2  out = relu(a1) W2^T + b2 : the two layer-1 accumulator tiles are
+//            exactly the A fragment of one m16n8k16 step, so the hidden layer
+//            never leaves registers (16 units at a time).
+// The order reversal between blocks (column j <-> 7 - j) is a shuffle with
+// lane ^ 3; row sums are shuffles over the 4 lanes of a row.
+// Weight gradients reduce over rows, so their products take operands staged
+// transposed in shared memory and accumulate in shared memory per CTA.
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <random>
+#include <vector>
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "../../include/abc_gb300.h"
+#include "abc_kernels.h"
+#include "abc_model.cuh"
+
+namespace abcgb {
+abc_status plan_fail(abc_status st, const char* msg);
+abc_status plan_cuda_fail(cudaError_t e, const char* what);
+abc_status plan_ok();
+bool plan_check_prior(const abc_prior_box* prior, abc_status* st);
+ModelParams plan_make_params(const abc_prior_box* prior, int32_t T, int64_t N_pop, uint64_t seed, uint32_t stream,
+                             const int32_t* ard0);
+
+namespace maf {
+
+constexpr int kD = 8;
+constexpr int kHMax = 256;
+constexpr int kKMax = 4;
+constexpr float kAlphaMax = 6.0f;
+constexpr float kLog2Pi = 1.8378770664093453f;
+constexpr uint32_t kFull = 0xFFFFFFFFu;
+
+// Master (FP32) parameters of one block: W1 [H][8], b1 [H], W2 [16][H], b2 [16].
+__host__ __device__ inline int master_block(int H) { return 25 * H + 16; }
+
+// Published BF16 layout of one block, in 32-bit words (two bf16 per word):
+//   w1  [H][4]        B operand of x W1^T      (n = hidden l, k = input j)
+//   w2  [16][H/2+4]   B operand of h W2^T      (n = output o, k = l), padded rows
+//   w1t [8][H/2+4]    B operand of g_a1 W1     (n = j, k = l)
+//   w2t [H][12]       B operand of g_out W2    (n = l, k = o)
+//   b1 [H], b2 [16]   FP32 biases
+struct Layout {
+    int w1, w2, w1t, w2t, b1, b2, words;
+};
+__host__ __device__ inline Layout layout(int H)
+{
+    Layout L;
+    int o = 0;
+    L.w1 = o; o += H * 4;
+    L.w2 = o; o += 16 * (H / 2 + 4);
+    L.w1t = o; o += 8 * (H / 2 + 4);
+    L.w2t = o; o += H * 12;
+    L.b1 = o; o += H;
+    L.b2 = o; o += 16;
+    L.words = o;
+    return L;
+}
+
+// MADE masks (Germain et al.): hidden degree (l mod 7) + 1; input j and output
+// j (mu_j and alpha_j, o = j and o = 8 + j) have degree j + 1.
+__host__ __device__ inline bool mask1(int l, int j) { return (l % 7) + 1 >= j + 1; }
+__host__ __device__ inline bool mask2(int o, int l) { return (o % 8) + 1 > (l % 7) + 1; }
+
+struct Box {
+    float lo[8], w[8], logw[8];
+};
+
+__device__ __forceinline__ uint32_t pack2(float lo, float hi)
+{
+    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t*>(&v);
+}
+
+__device__ __forceinline__ void mma_k8(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t b0)
+{
+    asm volatile("mma.sync.aligned.m16n8k8.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5}, {%6}, {%0,%1,%2,%3};\n"
+                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+                 : "r"(a0), "r"(a1), "r"(b0));
+}
+
+__device__ __forceinline__ void mma_k16(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, uint32_t b0,
+                                        uint32_t b1)
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+struct BlockView {
+    const uint32_t* w1;
+    const uint32_t* w2;
+    const uint32_t* w1t;
+    const uint32_t* w2t;
+    const float* b1;
+    const float* b2;
+};
+
+__device__ __forceinline__ BlockView view(const uint32_t* base, const Layout& L)
+{
+    BlockView v;
+    v.w1 = base + L.w1;
+    v.w2 = base + L.w2;
+    v.w1t = base + L.w1t;
+    v.w2t = base + L.w2t;
+    v.b1 = reinterpret_cast<const float*>(base + L.b1);
+    v.b2 = reinterpret_cast<const float*>(base + L.b2);
+    return v;
+}
+
+__device__ __forceinline__ float quad_sum(float v)
+{
+    v += __shfl_xor_sync(kFull, v, 1);
+    v += __shfl_xor_sync(kFull, v, 2);
+    return v;
+}
+
+// column j <-> 7 - j within each row (accumulator layout)
+__device__ __forceinline__ void reverse_cols(float (&v)[4])
+{
+    const float n0 = __shfl_xor_sync(kFull, v[1], 3), n1 = __shfl_xor_sync(kFull, v[0], 3);
+    const float n2 = __shfl_xor_sync(kFull, v[3], 3), n3 = __shfl_xor_sync(kFull, v[2], 3);
+    v[0] = n0; v[1] = n1; v[2] = n2; v[3] = n3;
+}
+
+__device__ __forceinline__ float soft_alpha(float ar) { return kAlphaMax * tanhf(ar / kAlphaMax); }
+
+// One MADE on the warp's 16 rows: mu and alpha_raw in the accumulator layout.
+__device__ __forceinline__ void made_fwd(const BlockView& v, int H, const float (&x)[4], float (&mu)[4],
+                                         float (&ar)[4])
+{
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const uint32_t a0 = pack2(x[0], x[1]), a1 = pack2(x[2], x[3]);
+    float o0[4] = {0.f, 0.f, 0.f, 0.f}, o1[4] = {0.f, 0.f, 0.f, 0.f};
+    const int w2s = H / 2 + 4;
+    for (int s = 0; s < H / 16; ++s) {
+        float c0[4] = {0.f, 0.f, 0.f, 0.f}, c1[4] = {0.f, 0.f, 0.f, 0.f};
+        mma_k8(c0, a0, a1, v.w1[(16 * s + g) * 4 + t]);
+        mma_k8(c1, a0, a1, v.w1[(16 * s + 8 + g) * 4 + t]);
+        const float2 ba = *reinterpret_cast<const float2*>(v.b1 + 16 * s + 2 * t);
+        const float2 bb = *reinterpret_cast<const float2*>(v.b1 + 16 * s + 8 + 2 * t);
+        const uint32_t A0 = pack2(fmaxf(c0[0] + ba.x, 0.f), fmaxf(c0[1] + ba.y, 0.f));
+        const uint32_t A1 = pack2(fmaxf(c0[2] + ba.x, 0.f), fmaxf(c0[3] + ba.y, 0.f));
+        const uint32_t A2 = pack2(fmaxf(c1[0] + bb.x, 0.f), fmaxf(c1[1] + bb.y, 0.f));
+        const uint32_t A3 = pack2(fmaxf(c1[2] + bb.x, 0.f), fmaxf(c1[3] + bb.y, 0.f));
+        mma_k16(o0, A0, A1, A2, A3, v.w2[g * w2s + 8 * s + t], v.w2[g * w2s + 8 * s + 4 + t]);
+        mma_k16(o1, A0, A1, A2, A3, v.w2[(8 + g) * w2s + 8 * s + t], v.w2[(8 + g) * w2s + 8 * s + 4 + t]);
+    }
+    const float2 bm = *reinterpret_cast<const float2*>(v.b2 + 2 * t);
+    const float2 bs = *reinterpret_cast<const float2*>(v.b2 + 8 + 2 * t);
+    mu[0] = o0[0] + bm.x; mu[1] = o0[1] + bm.y; mu[2] = o0[2] + bm.x; mu[3] = o0[3] + bm.y;
+    ar[0] = o1[0] + bs.x; ar[1] = o1[1] + bs.y; ar[2] = o1[2] + bs.x; ar[3] = o1[3] + bs.y;
+}
+
+// theta -> y = logit((theta - lo) / w) and the log-Jacobian term log(w u (1 - u)).
+__device__ __forceinline__ void to_y(const Box& b, int j, float th, float& y, float& jac)
+{
+    const float u = (th - b.lo[j]) / b.w[j];
+    const float lu = logf(u), l1u = log1pf(-u);
+    y = lu - l1u;
+    jac = b.logw[j] + lu + l1u;
+}
+
+// y -> theta = lo + w sigmoid(y) and log(w s (1 - s)).
+__device__ __forceinline__ void to_theta(const Box& b, int j, float y, float& th, float& jac)
+{
+    const float e = expf(-fabsf(y));
+    const float l = log1pf(e);
+    const float ls = fminf(y, 0.f) - l, l1s = fminf(-y, 0.f) - l;
+    const float s = y >= 0.f ? 1.f / (1.f + e) : e / (1.f + e);
+    th = b.lo[j] + b.w[j] * s;
+    jac = b.logw[j] + ls + l1s;
+}
+
+__device__ __forceinline__ void stage_weights(uint32_t* sm, const uint32_t* pub, int words)
+{
+    const uint4* src = reinterpret_cast<const uint4*>(pub);
+    uint4* dst = reinterpret_cast<uint4*>(sm);
+    for (int i = threadIdx.x; i < words / 4; i += blockDim.x) dst[i] = src[i];
+    for (int i = (words / 4) * 4 + threadIdx.x; i < words; i += blockDim.x) sm[i] = pub[i];
+}
+
+// ---------------------------------------------------------------------------
+// publish: masked BF16 copies (and biases) from the FP32 master parameters
+// ---------------------------------------------------------------------------
+__global__ void publish_kernel(const float* __restrict__ master, uint32_t* __restrict__ pub, int K, int H)
+{
+    const Layout L = layout(H);
+    const int per = L.words, mb = master_block(H), hw = H / 2 + 4;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < K * per; idx += gridDim.x * blockDim.x) {
+        const int b = idx / per, w = idx % per;
+        const float* M = master + (size_t)b * mb;
+        const float* W1 = M;
+        const float* b1 = M + 8 * H;
+        const float* W2 = M + 9 * H;
+        const float* b2 = M + 25 * H;
+        uint32_t out = 0;
+        if (w < L.w2) {
+            const int r = w - L.w1, l = r / 4, j0 = 2 * (r % 4);
+            __nv_bfloat162 v = __floats2bfloat162_rn(mask1(l, j0) ? W1[l * 8 + j0] : 0.f,
+                                                     mask1(l, j0 + 1) ? W1[l * 8 + j0 + 1] : 0.f);
+            out = *reinterpret_cast<uint32_t*>(&v);
+        } else if (w < L.w1t) {
+            const int r = w - L.w2, o = r / hw, c = r % hw;
+            if (c < H / 2) {
+                const int l0 = 2 * c;
+                __nv_bfloat162 v = __floats2bfloat162_rn(mask2(o, l0) ? W2[o * H + l0] : 0.f,
+                                                         mask2(o, l0 + 1) ? W2[o * H + l0 + 1] : 0.f);
+                out = *reinterpret_cast<uint32_t*>(&v);
+            }
+        } else if (w < L.w2t) {
+            const int r = w - L.w1t, j = r / hw, c = r % hw;
+            if (c < H / 2) {
+                const int l0 = 2 * c;
+                __nv_bfloat162 v = __floats2bfloat162_rn(mask1(l0, j) ? W1[l0 * 8 + j] : 0.f,
+                                                         mask1(l0 + 1, j) ? W1[(l0 + 1) * 8 + j] : 0.f);
+                out = *reinterpret_cast<uint32_t*>(&v);
+            }
+        } else if (w < L.b1) {
+            const int r = w - L.w2t, l = r / 12, c = r % 12;
+            if (c < 8) {
+                const int o0 = 2 * c;
+                __nv_bfloat162 v = __floats2bfloat162_rn(mask2(o0, l) ? W2[o0 * H + l] : 0.f,
+                                                         mask2(o0 + 1, l) ? W2[(o0 + 1) * H + l] : 0.f);
+                out = *reinterpret_cast<uint32_t*>(&v);
+            }
+        } else if (w < L.b2) {
+            out = __float_as_uint(b1[w - L.b1]);
+        } else {
+            out = __float_as_uint(b2[w - L.b2]);
+        }
+        pub[idx] = out;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// density: log q(theta)
+// ---------------------------------------------------------------------------
+template <int K>
+__global__ void __launch_bounds__(128) logq_kernel(const uint32_t* __restrict__ pub, int H, Box box,
+                                                   const float* __restrict__ theta, uint64_t n,
+                                                   float* __restrict__ logq)
+{
+    extern __shared__ __align__(16) uint32_t sm[];
+    const Layout L = layout(H);
+    stage_weights(sm, pub, K * L.words);
+    __syncthreads();
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const uint64_t tiles = (n + 15) / 16;
+    const int warps = blockDim.x / 32;
+    for (uint64_t tile = (uint64_t)blockIdx.x * warps + (threadIdx.x >> 5); tile < tiles;
+         tile += (uint64_t)gridDim.x * warps) {
+        const uint64_t r0 = tile * 16 + g, r1 = r0 + 8;
+        float x[4], jac[4];
+        const float mid[2] = {box.lo[2 * t] + 0.5f * box.w[2 * t], box.lo[2 * t + 1] + 0.5f * box.w[2 * t + 1]};
+        const float2 ta = r0 < n ? *reinterpret_cast<const float2*>(theta + 8 * r0 + 2 * t) : make_float2(mid[0], mid[1]);
+        const float2 tb = r1 < n ? *reinterpret_cast<const float2*>(theta + 8 * r1 + 2 * t) : make_float2(mid[0], mid[1]);
+        to_y(box, 2 * t, ta.x, x[0], jac[0]);
+        to_y(box, 2 * t + 1, ta.y, x[1], jac[1]);
+        to_y(box, 2 * t, tb.x, x[2], jac[2]);
+        to_y(box, 2 * t + 1, tb.y, x[3], jac[3]);
+        float ld[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int b = 0; b < K; ++b) {
+            float mu[4], ar[4];
+            made_fwd(view(sm + b * L.words, L), H, x, mu, ar);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const float al = soft_alpha(ar[e]);
+                x[e] = (x[e] - mu[e]) * expf(-al);
+                ld[e] -= al;
+            }
+            reverse_cols(x);
+        }
+        const float q0 = quad_sum(-0.5f * (x[0] * x[0] + x[1] * x[1]) + ld[0] + ld[1] - jac[0] - jac[1]);
+        const float q1 = quad_sum(-0.5f * (x[2] * x[2] + x[3] * x[3]) + ld[2] + ld[3] - jac[2] - jac[3]);
+        if (t == 0) {
+            if (r0 < n) logq[r0] = q0 - 4.f * kLog2Pi;
+            if (r1 < n) logq[r1] = q1 - 4.f * kLog2Pi;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// sampling: base normals -> sequential inverse -> theta, log q(theta)
+// ---------------------------------------------------------------------------
+template <int K>
+__global__ void __launch_bounds__(128) sample_kernel(const uint32_t* __restrict__ pub, int H, Box box,
+                                                     const float* __restrict__ u_in, const __grid_constant__ ModelParams p,
+                                                     uint32_t ctr3, uint64_t first, uint64_t n,
+                                                     float* __restrict__ theta_out, float* __restrict__ logq_out)
+{
+    extern __shared__ __align__(16) uint32_t sm[];
+    const Layout L = layout(H);
+    stage_weights(sm, pub, K * L.words);
+    __syncthreads();
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const uint64_t tiles = (n + 15) / 16;
+    const int warps = blockDim.x / 32;
+    for (uint64_t tile = (uint64_t)blockIdx.x * warps + (threadIdx.x >> 5); tile < tiles;
+         tile += (uint64_t)gridDim.x * warps) {
+        const uint64_t r0 = tile * 16 + g, r1 = r0 + 8;
+        float x[4];
+        if (u_in) {
+            const float2 ua = r0 < n ? *reinterpret_cast<const float2*>(u_in + 8 * r0 + 2 * t) : make_float2(0.f, 0.f);
+            const float2 ub = r1 < n ? *reinterpret_cast<const float2*>(u_in + 8 * r1 + 2 * t) : make_float2(0.f, 0.f);
+            x[0] = ua.x; x[1] = ua.y; x[2] = ub.x; x[3] = ub.y;
+        } else {
+            // row r: Philox block (t / 2) of sample first + r; lane t takes words
+            // (x, y) for even t and (z, w) for odd t: one Box-Muller pair per row
+            const uint4 wa = rng_block_s(p, first + r0, 0, ctr3, (uint32_t)(t >> 1));
+            const uint4 wb = rng_block_s(p, first + r1, 0, ctr3, (uint32_t)(t >> 1));
+            box_muller<kFast>((t & 1) ? wa.z : wa.x, (t & 1) ? wa.w : wa.y, x[0], x[1]);
+            box_muller<kFast>((t & 1) ? wb.z : wb.x, (t & 1) ? wb.w : wb.y, x[2], x[3]);
+        }
+        float lq[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) lq[e] = -0.5f * x[e] * x[e];
+#pragma unroll
+        for (int bb = K - 1; bb >= 0; --bb) {
+            const BlockView v = view(sm + bb * L.words, L);
+            float z[4] = {x[0], x[1], x[2], x[3]};
+            reverse_cols(z);
+            float xin[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int j = 0; j < kD; ++j) {
+                float mu[4], ar[4];
+                made_fwd(v, H, xin, mu, ar);
+                if (t == (j >> 1)) {
+                    const int e = j & 1;
+                    const float al0 = soft_alpha(ar[e]), al1 = soft_alpha(ar[2 + e]);
+                    xin[e] = z[e] * expf(al0) + mu[e];
+                    xin[2 + e] = z[2 + e] * expf(al1) + mu[2 + e];
+                    lq[e] -= al0;
+                    lq[2 + e] -= al1;
+                }
+            }
+            x[0] = xin[0]; x[1] = xin[1]; x[2] = xin[2]; x[3] = xin[3];
+        }
+        float th[4], jac[4];
+        to_theta(box, 2 * t, x[0], th[0], jac[0]);
+        to_theta(box, 2 * t + 1, x[1], th[1], jac[1]);
+        to_theta(box, 2 * t, x[2], th[2], jac[2]);
+        to_theta(box, 2 * t + 1, x[3], th[3], jac[3]);
+        const float q0 = quad_sum(lq[0] + lq[1] - jac[0] - jac[1]) - 4.f * kLog2Pi;
+        const float q1 = quad_sum(lq[2] + lq[3] - jac[2] - jac[3]) - 4.f * kLog2Pi;
+        if (r0 < n) *reinterpret_cast<float2*>(theta_out + 8 * r0 + 2 * t) = make_float2(th[0], th[1]);
+        if (r1 < n) *reinterpret_cast<float2*>(theta_out + 8 * r1 + 2 * t) = make_float2(th[2], th[3]);
+        if (t == 0 && logq_out) {
+            if (r0 < n) logq_out[r0] = q0;
+            if (r1 < n) logq_out[r1] = q1;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// gradient of sum_r w_r (-log q_y(y_r)) (unnormalised; Adam divides by sum w)
+// ---------------------------------------------------------------------------
+constexpr int kGradWarps = 4;
+constexpr int kStage = 12;   // staging row stride in 32-bit words (8 data + 4 pad)
+
+struct WarpStage {
+    uint32_t goutT[16 * kStage];   // [o][row] bf16
+    uint32_t hT[16 * kStage];      // [l (16 of a chunk)][row]
+    uint32_t gaT[16 * kStage];     // [l][row]
+    uint32_t xT[8 * kStage];       // [j][row]
+};
+
+__device__ __forceinline__ void put_bf16(uint32_t* base, int row, int col, float v)
+{
+    reinterpret_cast<__nv_bfloat16*>(base)[row * 2 * kStage + col] = __float2bfloat16_rn(v);
+}
+
+template <int K>
+__global__ void __launch_bounds__(kGradWarps * 32) grad_kernel(const uint32_t* __restrict__ pub, int H, Box box,
+                                                               const float* __restrict__ theta,
+                                                               const float* __restrict__ weights,
+                                                               const uint32_t* __restrict__ rows, uint64_t n_rows,
+                                                               float* __restrict__ grad, float* __restrict__ sums)
+{
+    extern __shared__ __align__(16) uint32_t sm[];
+    const Layout L = layout(H);
+    const int mb = master_block(H);
+    uint32_t* wsm = sm;
+    float* gsm = reinterpret_cast<float*>(sm + K * L.words);
+    WarpStage* stages = reinterpret_cast<WarpStage*>(gsm + K * mb);
+    stage_weights(wsm, pub, K * L.words);
+    for (int i = threadIdx.x; i < K * mb; i += blockDim.x) gsm[i] = 0.f;
+    __shared__ float ssum[2];
+    if (threadIdx.x < 2) ssum[threadIdx.x] = 0.f;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    WarpStage& st = stages[threadIdx.x >> 5];
+    const uint64_t tiles = (n_rows + 15) / 16;
+    const int hw = H / 2 + 4;
+    for (uint64_t tile = (uint64_t)blockIdx.x * kGradWarps + (threadIdx.x >> 5); tile < tiles;
+         tile += (uint64_t)gridDim.x * kGradWarps) {
+        const uint64_t q0 = tile * 16 + g, q1 = q0 + 8;
+        const uint64_t i0 = q0 < n_rows ? (rows ? rows[q0] : q0) : 0;
+        const uint64_t i1 = q1 < n_rows ? (rows ? rows[q1] : q1) : 0;
+        const float w0 = q0 < n_rows ? (weights ? weights[i0] : 1.f) : 0.f;
+        const float w1 = q1 < n_rows ? (weights ? weights[i1] : 1.f) : 0.f;
+        const float2 ta = *reinterpret_cast<const float2*>(theta + 8 * i0 + 2 * t);
+        const float2 tb = *reinterpret_cast<const float2*>(theta + 8 * i1 + 2 * t);
+        float x[4], jac;
+        to_y(box, 2 * t, ta.x, x[0], jac);
+        to_y(box, 2 * t + 1, ta.y, x[1], jac);
+        to_y(box, 2 * t, tb.x, x[2], jac);
+        to_y(box, 2 * t + 1, tb.y, x[3], jac);
+        float xs[K][4], ms[K][4], as[K][4], zs[K][4];
+        float ld0 = 0.f, ld1 = 0.f;
+#pragma unroll
+        for (int b = 0; b < K; ++b) {
+            float mu[4], ar[4];
+            made_fwd(view(wsm + b * L.words, L), H, x, mu, ar);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                xs[b][e] = x[e];
+                ms[b][e] = mu[e];
+                as[b][e] = soft_alpha(ar[e]);
+                zs[b][e] = (x[e] - mu[e]) * expf(-as[b][e]);
+                x[e] = zs[b][e];
+            }
+            ld0 += as[b][0] + as[b][1];
+            ld1 += as[b][2] + as[b][3];
+            reverse_cols(x);
+        }
+        // nll = 0.5 |z|^2 + sum alpha + 4 log 2 pi
+        const float n0 = quad_sum(0.5f * (x[0] * x[0] + x[1] * x[1]) + ld0) + 4.f * kLog2Pi;
+        const float n1 = quad_sum(0.5f * (x[2] * x[2] + x[3] * x[3]) + ld1) + 4.f * kLog2Pi;
+        float contrib = (t == 0) ? (w0 * n0 + w1 * n1) : 0.f;
+        float wsum = (t == 0) ? (w0 + w1) : 0.f;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            contrib += __shfl_xor_sync(kFull, contrib, off);
+            wsum += __shfl_xor_sync(kFull, wsum, off);
+        }
+        if (lane == 0) {
+            atomicAdd(&ssum[0], contrib);
+            atomicAdd(&ssum[1], wsum);
+        }
+        // d/dz_K of sum w (0.5 |z|^2)
+        float gx[4] = {w0 * x[0], w0 * x[1], w1 * x[2], w1 * x[3]};
+        const float wr[4] = {w0, w0, w1, w1};
+#pragma unroll
+        for (int b = K - 1; b >= 0; --b) {
+            const BlockView v = view(wsm + b * L.words, L);
+            float* GW1 = gsm + b * mb;
+            float* GB1 = GW1 + 8 * H;
+            float* GW2 = GW1 + 9 * H;
+            float* GB2 = GW1 + 25 * H;
+            reverse_cols(gx);   // gradient with respect to this block's output z
+            float gmu[4], gar[4], gxd[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const float ex = expf(-as[b][e]);
+                gxd[e] = gx[e] * ex;
+                gmu[e] = -gx[e] * ex;
+                const float ga = -gx[e] * zs[b][e] + wr[e];
+                const float r = as[b][e] / kAlphaMax;
+                gar[e] = ga * (1.f - r * r);
+            }
+            // stage g_out^T [o][row] and x^T [j][row]
+            put_bf16(st.goutT, 2 * t, g, gmu[0]);
+            put_bf16(st.goutT, 2 * t + 1, g, gmu[1]);
+            put_bf16(st.goutT, 2 * t, g + 8, gmu[2]);
+            put_bf16(st.goutT, 2 * t + 1, g + 8, gmu[3]);
+            put_bf16(st.goutT, 8 + 2 * t, g, gar[0]);
+            put_bf16(st.goutT, 9 + 2 * t, g, gar[1]);
+            put_bf16(st.goutT, 8 + 2 * t, g + 8, gar[2]);
+            put_bf16(st.goutT, 9 + 2 * t, g + 8, gar[3]);
+            put_bf16(st.xT, 2 * t, g, xs[b][0]);
+            put_bf16(st.xT, 2 * t + 1, g, xs[b][1]);
+            put_bf16(st.xT, 2 * t, g + 8, xs[b][2]);
+            put_bf16(st.xT, 2 * t + 1, g + 8, xs[b][3]);
+            // db2[o] = sum over rows of g_out
+            {
+                float d[4] = {gmu[0] + gmu[2], gmu[1] + gmu[3], gar[0] + gar[2], gar[1] + gar[3]};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    d[e] += __shfl_xor_sync(kFull, d[e], 4);
+                    d[e] += __shfl_xor_sync(kFull, d[e], 8);
+                    d[e] += __shfl_xor_sync(kFull, d[e], 16);
+                }
+                if (g == 0) {
+                    atomicAdd(&GB2[2 * t], d[0]);
+                    atomicAdd(&GB2[2 * t + 1], d[1]);
+                    atomicAdd(&GB2[8 + 2 * t], d[2]);
+                    atomicAdd(&GB2[9 + 2 * t], d[3]);
+                }
+            }
+            __syncwarp();
+            const uint32_t A0 = pack2(gmu[0], gmu[1]), A1 = pack2(gmu[2], gmu[3]);
+            const uint32_t A2 = pack2(gar[0], gar[1]), A3 = pack2(gar[2], gar[3]);
+            const uint32_t xa0 = pack2(xs[b][0], xs[b][1]), xa1 = pack2(xs[b][2], xs[b][3]);
+            float accx[4] = {0.f, 0.f, 0.f, 0.f};
+            for (int s = 0; s < H / 16; ++s) {
+                // recompute the pre-activations of hidden units 16s .. 16s+15
+                float c0[4] = {0.f, 0.f, 0.f, 0.f}, c1[4] = {0.f, 0.f, 0.f, 0.f};
+                mma_k8(c0, xa0, xa1, v.w1[(16 * s + g) * 4 + t]);
+                mma_k8(c1, xa0, xa1, v.w1[(16 * s + 8 + g) * 4 + t]);
+                const float2 ba = *reinterpret_cast<const float2*>(v.b1 + 16 * s + 2 * t);
+                const float2 bb = *reinterpret_cast<const float2*>(v.b1 + 16 * s + 8 + 2 * t);
+                c0[0] += ba.x; c0[1] += ba.y; c0[2] += ba.x; c0[3] += ba.y;
+                c1[0] += bb.x; c1[1] += bb.y; c1[2] += bb.x; c1[3] += bb.y;
+                // h^T [l][row]
+                put_bf16(st.hT, 2 * t, g, fmaxf(c0[0], 0.f));
+                put_bf16(st.hT, 2 * t + 1, g, fmaxf(c0[1], 0.f));
+                put_bf16(st.hT, 2 * t, g + 8, fmaxf(c0[2], 0.f));
+                put_bf16(st.hT, 2 * t + 1, g + 8, fmaxf(c0[3], 0.f));
+                put_bf16(st.hT, 8 + 2 * t, g, fmaxf(c1[0], 0.f));
+                put_bf16(st.hT, 9 + 2 * t, g, fmaxf(c1[1], 0.f));
+                put_bf16(st.hT, 8 + 2 * t, g + 8, fmaxf(c1[2], 0.f));
+                put_bf16(st.hT, 9 + 2 * t, g + 8, fmaxf(c1[3], 0.f));
+                // g_h = g_out W2 for these units, then through the ReLU
+                float d0[4] = {0.f, 0.f, 0.f, 0.f}, d1[4] = {0.f, 0.f, 0.f, 0.f};
+                mma_k16(d0, A0, A1, A2, A3, v.w2t[(16 * s + g) * 12 + t], v.w2t[(16 * s + g) * 12 + 4 + t]);
+                mma_k16(d1, A0, A1, A2, A3, v.w2t[(16 * s + 8 + g) * 12 + t], v.w2t[(16 * s + 8 + g) * 12 + 4 + t]);
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    d0[e] = c0[e] > 0.f ? d0[e] : 0.f;
+                    d1[e] = c1[e] > 0.f ? d1[e] : 0.f;
+                }
+                put_bf16(st.gaT, 2 * t, g, d0[0]);
+                put_bf16(st.gaT, 2 * t + 1, g, d0[1]);
+                put_bf16(st.gaT, 2 * t, g + 8, d0[2]);
+                put_bf16(st.gaT, 2 * t + 1, g + 8, d0[3]);
+                put_bf16(st.gaT, 8 + 2 * t, g, d1[0]);
+                put_bf16(st.gaT, 9 + 2 * t, g, d1[1]);
+                put_bf16(st.gaT, 8 + 2 * t, g + 8, d1[2]);
+                put_bf16(st.gaT, 9 + 2 * t, g + 8, d1[3]);
+                // db1[l] = sum over rows of g_a1
+                {
+                    float d[4] = {d0[0] + d0[2], d0[1] + d0[3], d1[0] + d1[2], d1[1] + d1[3]};
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        d[e] += __shfl_xor_sync(kFull, d[e], 4);
+                        d[e] += __shfl_xor_sync(kFull, d[e], 8);
+                        d[e] += __shfl_xor_sync(kFull, d[e], 16);
+                    }
+                    if (g == 0) {
+                        atomicAdd(&GB1[16 * s + 2 * t], d[0]);
+                        atomicAdd(&GB1[16 * s + 2 * t + 1], d[1]);
+                        atomicAdd(&GB1[16 * s + 8 + 2 * t], d[2]);
+                        atomicAdd(&GB1[16 * s + 9 + 2 * t], d[3]);
+                    }
+                }
+                // g_x += g_a1 W1 (this chunk's 16 hidden units as k)
+                mma_k16(accx, pack2(d0[0], d0[1]), pack2(d0[2], d0[3]), pack2(d1[0], d1[1]), pack2(d1[2], d1[3]),
+                        v.w1t[g * hw + 8 * s + t], v.w1t[g * hw + 8 * s + 4 + t]);
+                __syncwarp();
+                // dW2[o][l] += sum_rows g_out[row][o] h[row][l]
+                {
+                    const uint32_t a0 = st.goutT[g * kStage + t], a1 = st.goutT[(g + 8) * kStage + t];
+                    const uint32_t a2 = st.goutT[g * kStage + 4 + t], a3 = st.goutT[(g + 8) * kStage + 4 + t];
+                    float e0[4] = {0.f, 0.f, 0.f, 0.f}, e1[4] = {0.f, 0.f, 0.f, 0.f};
+                    mma_k16(e0, a0, a1, a2, a3, st.hT[g * kStage + t], st.hT[g * kStage + 4 + t]);
+                    mma_k16(e1, a0, a1, a2, a3, st.hT[(8 + g) * kStage + t], st.hT[(8 + g) * kStage + 4 + t]);
+                    const int la = 16 * s + 2 * t, lb = 16 * s + 8 + 2 * t;
+                    if (mask2(g, la)) atomicAdd(&GW2[g * H + la], e0[0]);
+                    if (mask2(g, la + 1)) atomicAdd(&GW2[g * H + la + 1], e0[1]);
+                    if (mask2(g + 8, la)) atomicAdd(&GW2[(g + 8) * H + la], e0[2]);
+                    if (mask2(g + 8, la + 1)) atomicAdd(&GW2[(g + 8) * H + la + 1], e0[3]);
+                    if (mask2(g, lb)) atomicAdd(&GW2[g * H + lb], e1[0]);
+                    if (mask2(g, lb + 1)) atomicAdd(&GW2[g * H + lb + 1], e1[1]);
+                    if (mask2(g + 8, lb)) atomicAdd(&GW2[(g + 8) * H + lb], e1[2]);
+                    if (mask2(g + 8, lb + 1)) atomicAdd(&GW2[(g + 8) * H + lb + 1], e1[3]);
+                }
+                // dW1[l][j] += sum_rows g_a1[row][l] x[row][j]
+                {
+                    const uint32_t a0 = st.gaT[g * kStage + t], a1 = st.gaT[(g + 8) * kStage + t];
+                    const uint32_t a2 = st.gaT[g * kStage + 4 + t], a3 = st.gaT[(g + 8) * kStage + 4 + t];
+                    float e0[4] = {0.f, 0.f, 0.f, 0.f};
+                    mma_k16(e0, a0, a1, a2, a3, st.xT[g * kStage + t], st.xT[g * kStage + 4 + t]);
+                    const int la = 16 * s + g, lb = la + 8;
+                    if (mask1(la, 2 * t)) atomicAdd(&GW1[la * 8 + 2 * t], e0[0]);
+                    if (mask1(la, 2 * t + 1)) atomicAdd(&GW1[la * 8 + 2 * t + 1], e0[1]);
+                    if (mask1(lb, 2 * t)) atomicAdd(&GW1[lb * 8 + 2 * t], e0[2]);
+                    if (mask1(lb, 2 * t + 1)) atomicAdd(&GW1[lb * 8 + 2 * t + 1], e0[3]);
+                }
+                __syncwarp();
+            }
+#pragma unroll
+            for (int e = 0; e < 4; ++e) gx[e] = gxd[e] + accx[e];
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < K * mb; i += blockDim.x) {
+        const float v = gsm[i];
+        if (v != 0.f) atomicAdd(&grad[i], v);
+    }
+    if (threadIdx.x < 2) atomicAdd(&sums[threadIdx.x], ssum[threadIdx.x]);
+}
+
+// batch rows for one training step: uniform indices with replacement
+__global__ void batch_rows_kernel(const __grid_constant__ ModelParams p, const int* __restrict__ step, uint64_t n,
+                                  uint32_t batch, uint32_t* __restrict__ rows)
+{
+    const uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= batch) return;
+    const uint4 w = philox10(make_uint4(b, (uint32_t)*step, 0xB47C4u, 0x5EEDu), p);
+    const uint64_t r = (((uint64_t)w.y << 32) | w.x) % n;
+    rows[b] = (uint32_t)r;
+}
+
+__global__ void tick_kernel(int* step) { *step += 1; }
+
+__global__ void adam_kernel(float* __restrict__ params, const float* __restrict__ grad, float* __restrict__ m,
+                            float* __restrict__ v, const float* __restrict__ sums, const int* __restrict__ step, int n,
+                            float lr, float b1, float b2, float eps)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float W = sums[1];
+    if (!(W > 0.f)) return;
+    const int t = *step;
+    const float gr = grad[i] / W;
+    const float mi = b1 * m[i] + (1.f - b1) * gr;
+    const float vi = b2 * v[i] + (1.f - b2) * gr * gr;
+    m[i] = mi;
+    v[i] = vi;
+    const float mh = mi / (1.f - powf(b1, (float)t));
+    const float vh = vi / (1.f - powf(b2, (float)t));
+    params[i] -= lr * mh / (sqrtf(vh) + eps);
+}
+
+}  // namespace maf
+}  // namespace abcgb
+
+using namespace abcgb;
+
+struct abc_maf_s {
+    int device = 0;
+    int K = 0, H = 0;
+    maf::Box box{};
+    int64_t n_params = 0;
+    int pub_words = 0;
+    float* d_params = nullptr;
+    float* d_m = nullptr;
+    float* d_v = nullptr;
+    float* d_grad = nullptr;
+    uint32_t* d_pub = nullptr;
+    float* d_sums = nullptr;
+    int* d_step = nullptr;
+    uint32_t* d_rows = nullptr;
+    uint32_t rows_cap = 0;
+    cudaGraphExec_t graph = nullptr;
+    // what the captured training step was built for
+    uint64_t g_n = 0;
+    const float* g_theta = nullptr;
+    const float* g_w = nullptr;
+    int32_t g_batch = 0;
+    float g_lr = 0.f;
+    uint64_t g_seed = 0;
+    cudaStream_t g_stream = nullptr;
+};
+
+namespace {
+
+#define MAF_TRY(expr, what)                                   \
+    do {                                                      \
+        cudaError_t _e = (expr);                              \
+        if (_e != cudaSuccess) return plan_cuda_fail(_e, what); \
+    } while (0)
+
+size_t fwd_smem(const abc_maf_s* f) { return sizeof(uint32_t) * (size_t)f->K * maf::layout(f->H).words; }
+
+size_t grad_smem(const abc_maf_s* f)
+{
+    return fwd_smem(f) + sizeof(float) * (size_t)f->K * maf::master_block(f->H) +
+           sizeof(maf::WarpStage) * maf::kGradWarps;
+}
+
+abc_status check(abc_maf f)
+{
+    if (!f) return plan_fail(ABC_ERR_INVALID_ARG, "flow is NULL");
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != f->device)
+        return plan_fail(ABC_ERR_INVALID_ARG, "the flow's device is not the current device");
+    return ABC_OK;
+}
+
+int sm_count()
+{
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms > 0 ? sms : 1;
+}
+
+template <typename Kern>
+cudaError_t allow_smem(Kern k, size_t bytes)
+{
+    return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+cudaError_t publish(abc_maf f, cudaStream_t s)
+{
+    const int n = f->K * f->pub_words;
+    maf::publish_kernel<<<(n + 255) / 256, 256, 0, s>>>(f->d_params, f->d_pub, f->K, f->H);
+    return cudaGetLastError();
+}
+
+template <int K>
+cudaError_t launch_logq(abc_maf f, uint64_t n, const float* theta, float* logq, cudaStream_t s)
+{
+    const size_t smem = fwd_smem(f);
+    cudaError_t e = allow_smem(maf::logq_kernel<K>, smem);
+    if (e != cudaSuccess) return e;
+    const uint64_t tiles = (n + 15) / 16;
+    const uint64_t want = (tiles + 3) / 4;
+    const int grid = (int)(want < (uint64_t)sm_count() * 2 ? (want > 0 ? want : 1) : (uint64_t)sm_count() * 2);
+    maf::logq_kernel<K><<<grid, 128, smem, s>>>(f->d_pub, f->H, f->box, theta, n, logq);
+    return cudaGetLastError();
+}
+
+template <int K>
+cudaError_t launch_sample(abc_maf f, uint64_t n, const float* u, const ModelParams& p, uint32_t ctr3, uint64_t first,
+                          float* theta, float* logq, cudaStream_t s)
+{
+    const size_t smem = fwd_smem(f);
+    cudaError_t e = allow_smem(maf::sample_kernel<K>, smem);
+    if (e != cudaSuccess) return e;
+    const uint64_t tiles = (n + 15) / 16;
+    const uint64_t want = (tiles + 3) / 4;
+    const int grid = (int)(want < (uint64_t)sm_count() * 2 ? (want > 0 ? want : 1) : (uint64_t)sm_count() * 2);
+    maf::sample_kernel<K><<<grid, 128, smem, s>>>(f->d_pub, f->H, f->box, u, p, ctr3, first, n, theta, logq);
+    return cudaGetLastError();
+}
+
+template <int K>
+cudaError_t launch_grad(abc_maf f, uint64_t n_rows, const float* theta, const float* w, const uint32_t* rows,
+                        cudaStream_t s)
+{
+    const size_t smem = grad_smem(f);
+    cudaError_t e = allow_smem(maf::grad_kernel<K>, smem);
+    if (e != cudaSuccess) return e;
+    const uint64_t tiles = (n_rows + 15) / 16;
+    const uint64_t want = (tiles + maf::kGradWarps - 1) / maf::kGradWarps;
+    const int grid = (int)(want < (uint64_t)sm_count() ? (want > 0 ? want : 1) : (uint64_t)sm_count());
+    maf::grad_kernel<K><<<grid, maf::kGradWarps * 32, smem, s>>>(f->d_pub, f->H, f->box, theta, w, rows, n_rows,
+                                                                 f->d_grad, f->d_sums);
+    return cudaGetLastError();
+}
+
+#define MAF_DISPATCH(fn, ...)                      \
+    (f->K == 1 ? fn<1>(__VA_ARGS__)                \
+     : f->K == 2 ? fn<2>(__VA_ARGS__)              \
+     : f->K == 3 ? fn<3>(__VA_ARGS__)              \
+                 : fn<4>(__VA_ARGS__))
+
+cudaError_t full_gradient(abc_maf f, uint64_t n, const float* theta, const float* w, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(f->d_grad, 0, sizeof(float) * f->n_params, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(f->d_sums, 0, 2 * sizeof(float), s);
+    if (e == cudaSuccess) e = MAF_DISPATCH(launch_grad, f, n, theta, w, nullptr, s);
+    return e;
+}
+
+}  // namespace
+
+extern "C" {
+
+abc_status abc_maf_create(int32_t n_blocks, int32_t hidden, const abc_prior_box* box, abc_maf* maf_out)
+{
+    abc_status st;
+    if (!maf_out) return plan_fail(ABC_ERR_INVALID_ARG, "maf_out is NULL");
+    *maf_out = nullptr;
+    if (!plan_check_prior(box, &st)) return st;
+    if (n_blocks < 1 || n_blocks > maf::kKMax) return plan_fail(ABC_ERR_INVALID_ARG, "n_blocks must be in 1..4");
+    if (hidden < 16 || hidden > maf::kHMax || hidden % 16)
+        return plan_fail(ABC_ERR_INVALID_ARG, "hidden must be a multiple of 16 in 16..256");
+    for (int j = 0; j < 8; ++j)
+        if (!(box->hi[j] > box->lo[j])) return plan_fail(ABC_ERR_INVALID_ARG, "the flow needs lo < hi in every coordinate");
+    abc_maf_s* f = new abc_maf_s();
+    f->K = n_blocks;
+    f->H = hidden;
+    for (int j = 0; j < 8; ++j) {
+        f->box.lo[j] = box->lo[j];
+        f->box.w[j] = box->hi[j] - box->lo[j];
+        f->box.logw[j] = logf(f->box.w[j]);
+    }
+    f->n_params = (int64_t)n_blocks * maf::master_block(hidden);
+    f->pub_words = maf::layout(hidden).words;
+    auto fail_free = [f](abc_status e) {
+        abc_maf_destroy(f);
+        return e;
+    };
+    cudaError_t e;
+    if ((e = cudaGetDevice(&f->device)) != cudaSuccess ||
+        (e = cudaMalloc(&f->d_params, sizeof(float) * f->n_params)) != cudaSuccess ||
+        (e = cudaMalloc(&f->d_m, sizeof(float) * f->n_params)) != cudaSuccess ||
+        (e = cudaMalloc(&f->d_v, sizeof(float) * f->n_params)) != cudaSuccess ||
+        (e = cudaMalloc(&f->d_grad, sizeof(float) * f->n_params)) != cudaSuccess ||
+        (e = cudaMalloc(&f->d_pub, sizeof(uint32_t) * (size_t)f->K * f->pub_words)) != cudaSuccess ||
+        (e = cudaMalloc(&f->d_sums, 2 * sizeof(float))) != cudaSuccess ||
+        (e = cudaMalloc(&f->d_step, sizeof(int))) != cudaSuccess)
+        return fail_free(plan_cuda_fail(e, "cudaMalloc(flow)"));
+    if ((e = cudaMemset(f->d_params, 0, sizeof(float) * f->n_params)) != cudaSuccess ||
+        (e = cudaMemset(f->d_m, 0, sizeof(float) * f->n_params)) != cudaSuccess ||
+        (e = cudaMemset(f->d_v, 0, sizeof(float) * f->n_params)) != cudaSuccess ||
+        (e = cudaMemset(f->d_step, 0, sizeof(int))) != cudaSuccess || (e = publish(f, nullptr)) != cudaSuccess ||
+        (e = cudaDeviceSynchronize()) != cudaSuccess)
+        return fail_free(plan_cuda_fail(e, "flow initialisation"));
+    *maf_out = f;
+    return plan_ok();
+}
+
+int64_t abc_maf_param_count(abc_maf f) { return f ? f->n_params : -1; }
+
+abc_status abc_maf_init_random(abc_maf f, uint64_t seed, float scale)
+{
+    abc_status st;
+    if ((st = check(f)) != ABC_OK) return st;
+    if (!(scale >= 0.f)) return plan_fail(ABC_ERR_INVALID_ARG, "scale must be >= 0");
+    std::vector<float> v((size_t)f->n_params, 0.f);
+    std::mt19937_64 gen(seed);
+    std::normal_distribution<float> nd(0.f, 1.f);
+    const int H = f->H, mb = maf::master_block(H);
+    for (int b = 0; b < f->K; ++b) {
+        float* M = v.data() + (size_t)b * mb;
+        for (int i = 0; i < 8 * H; ++i) M[i] = nd(gen) * scale / sqrtf(8.f);
+        for (int i = 0; i < 16 * H; ++i) M[9 * H + i] = nd(gen) * scale / sqrtf((float)H);
+    }
+    return abc_maf_set_params(f, v.data());
+}
+
+abc_status abc_maf_set_params(abc_maf f, const float* params)
+{
+    abc_status st;
+    if ((st = check(f)) != ABC_OK) return st;
+    if (!params) return plan_fail(ABC_ERR_INVALID_ARG, "params is NULL");
+    MAF_TRY(cudaMemcpy(f->d_params, params, sizeof(float) * f->n_params, cudaMemcpyHostToDevice), "cudaMemcpy(params)");
+    MAF_TRY(cudaMemset(f->d_m, 0, sizeof(float) * f->n_params), "cudaMemset");
+    MAF_TRY(cudaMemset(f->d_v, 0, sizeof(float) * f->n_params), "cudaMemset");
+    MAF_TRY(cudaMemset(f->d_step, 0, sizeof(int)), "cudaMemset");
+    MAF_TRY(publish(f, nullptr), "publish");
+    MAF_TRY(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
+    return plan_ok();
+}
+
+abc_status abc_maf_get_params(abc_maf f, float* params)
+{
+    abc_status st;
+    if ((st = check(f)) != ABC_OK) return st;
+    if (!params) return plan_fail(ABC_ERR_INVALID_ARG, "params is NULL");
+    MAF_TRY(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
+    MAF_TRY(cudaMemcpy(params, f->d_params, sizeof(float) * f->n_params, cudaMemcpyDeviceToHost), "cudaMemcpy(params)");
+    return plan_ok();
+}
+
+abc_status abc_maf_sample(abc_maf f, uint64_t n, const float* base_normals, uint64_t seed, uint32_t stream,
+                          uint64_t first_index, float* theta_out, float* logq_out, void* cuda_stream)
+{
+    abc_status st;
+    if ((st = check(f)) != ABC_OK) return st;
+    if (n && !theta_out) return plan_fail(ABC_ERR_INVALID_ARG, "theta_out is NULL");
+    if (stream > ABC_STREAM_MAX) return plan_fail(ABC_ERR_INVALID_ARG, "stream above 2^30 - 1");
+    if (n == 0) return plan_ok();
+    const ModelParams p = plan_make_params(nullptr, 1, 1, seed, stream, nullptr);
+    MAF_TRY(MAF_DISPATCH(launch_sample, f, n, base_normals, p, stream << 2, first_index, theta_out, logq_out,
+                         (cudaStream_t)cuda_stream),
+            "flow sample launch");
+    return plan_ok();
+}
+
+abc_status abc_maf_log_q(abc_maf f, uint64_t n, const float* theta, float* logq_out, void* cuda_stream)
+{
+    abc_status st;
+    if ((st = check(f)) != ABC_OK) return st;
+    if (n && (!theta || !logq_out)) return plan_fail(ABC_ERR_INVALID_ARG, "NULL device buffer");
+    if (n == 0) return plan_ok();
+    MAF_TRY(MAF_DISPATCH(launch_logq, f, n, theta, logq_out, (cudaStream_t)cuda_stream), "flow log_q launch");
+    return plan_ok();
+}
+
+abc_status abc_maf_gradient(abc_maf f, uint64_t n, const float* theta, const float* weights, float* loss_out,
+                            float* grads_out, void* cuda_stream)
+{
+    abc_status st;
+    if ((st = check(f)) != ABC_OK) return st;
+    if (n == 0 || !theta) return plan_fail(ABC_ERR_INVALID_ARG, "need n > 0 points");
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    MAF_TRY(full_gradient(f, n, theta, weights, s), "flow gradient");
+    float sums[2] = {0.f, 0.f};
+    MAF_TRY(cudaMemcpyAsync(sums, f->d_sums, sizeof sums, cudaMemcpyDeviceToHost, s), "cudaMemcpyAsync(sums)");
+    MAF_TRY(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+    if (loss_out) *loss_out = sums[1] > 0.f ? sums[0] / sums[1] : 0.f;
+    if (grads_out) {
+        MAF_TRY(cudaMemcpy(grads_out, f->d_grad, sizeof(float) * f->n_params, cudaMemcpyDeviceToHost),
+                "cudaMemcpy(grad)");
+        const float W = sums[1] > 0.f ? sums[1] : 1.f;
+        for (int64_t i = 0; i < f->n_params; ++i) grads_out[i] /= W;
+    }
+    return plan_ok();
+}
+
+abc_status abc_maf_adam_step(abc_maf f, float lr, float beta1, float beta2, float eps, void* cuda_stream)
+{
+    abc_status st;
+    if ((st = check(f)) != ABC_OK) return st;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    maf::tick_kernel<<<1, 1, 0, s>>>(f->d_step);
+    maf::adam_kernel<<<(int)((f->n_params + 255) / 256), 256, 0, s>>>(f->d_params, f->d_grad, f->d_m, f->d_v, f->d_sums,
+                                                                      f->d_step, (int)f->n_params, lr, beta1, beta2, eps);
+    MAF_TRY(cudaGetLastError(), "adam launch");
+    MAF_TRY(publish(f, s), "publish");
+    return plan_ok();
+}
+
+abc_status abc_maf_train(abc_maf f, uint64_t n, const float* theta, const float* weights, int32_t n_steps,
+                         int32_t batch, float lr, uint64_t seed, float* loss_out, void* cuda_stream)
+{
+    abc_status st;
+    if ((st = check(f)) != ABC_OK) return st;
+    if (n == 0 || !theta || n_steps < 0 || batch < 16)
+        return plan_fail(ABC_ERR_INVALID_ARG, "need n > 0 points, n_steps >= 0 and batch >= 16");
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    if (!s && n_steps > 0) return plan_fail(ABC_ERR_INVALID_ARG, "training needs a non-default stream");
+    if ((uint32_t)batch > f->rows_cap) {
+        cudaFree(f->d_rows);
+        f->d_rows = nullptr;
+        f->rows_cap = 0;
+        MAF_TRY(cudaMalloc(&f->d_rows, sizeof(uint32_t) * (size_t)batch), "cudaMalloc(rows)");
+        f->rows_cap = (uint32_t)batch;
+        if (f->graph) {
+            cudaGraphExecDestroy(f->graph);
+            f->graph = nullptr;
+        }
+    }
+    // fresh Adam moments for this training run
+    MAF_TRY(cudaMemsetAsync(f->d_m, 0, sizeof(float) * f->n_params, s), "cudaMemsetAsync");
+    MAF_TRY(cudaMemsetAsync(f->d_v, 0, sizeof(float) * f->n_params, s), "cudaMemsetAsync");
+    MAF_TRY(cudaMemsetAsync(f->d_step, 0, sizeof(int), s), "cudaMemsetAsync");
+    if (n_steps > 0) {
+        const bool same = f->graph && f->g_n == n && f->g_theta == theta && f->g_w == weights && f->g_batch == batch &&
+                          f->g_lr == lr && f->g_seed == seed && f->g_stream == s;
+        if (!same) {
+            if (f->graph) {
+                cudaGraphExecDestroy(f->graph);
+                f->graph = nullptr;
+            }
+            const ModelParams p = plan_make_params(nullptr, 1, 1, seed, 0, nullptr);
+            cudaGraph_t gph = nullptr;
+            MAF_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
+            maf::batch_rows_kernel<<<(batch + 127) / 128, 128, 0, s>>>(p, f->d_step, n, (uint32_t)batch, f->d_rows);
+            cudaMemsetAsync(f->d_grad, 0, sizeof(float) * f->n_params, s);
+            cudaMemsetAsync(f->d_sums, 0, 2 * sizeof(float), s);
+            cudaError_t e = MAF_DISPATCH(launch_grad, f, (uint64_t)batch, theta, weights, f->d_rows, s);
+            maf::tick_kernel<<<1, 1, 0, s>>>(f->d_step);
+            maf::adam_kernel<<<(int)((f->n_params + 255) / 256), 256, 0, s>>>(
+                f->d_params, f->d_grad, f->d_m, f->d_v, f->d_sums, f->d_step, (int)f->n_params, lr, 0.9f, 0.999f, 1e-8f);
+            if (e == cudaSuccess) e = publish(f, s);
+            cudaError_t ec = cudaStreamEndCapture(s, &gph);
+            if (e != cudaSuccess || ec != cudaSuccess) {
+                if (gph) cudaGraphDestroy(gph);
+                return plan_cuda_fail(e != cudaSuccess ? e : ec, "capturing the training step");
+            }
+            e = cudaGraphInstantiate(&f->graph, gph, 0);
+            cudaGraphDestroy(gph);
+            if (e != cudaSuccess) {
+                f->graph = nullptr;
+                return plan_cuda_fail(e, "cudaGraphInstantiate(training step)");
+            }
+            f->g_n = n;
+            f->g_theta = theta;
+            f->g_w = weights;
+            f->g_batch = batch;
+            f->g_lr = lr;
+            f->g_seed = seed;
+            f->g_stream = s;
+        }
+        for (int32_t i = 0; i < n_steps; ++i) MAF_TRY(cudaGraphLaunch(f->graph, s), "cudaGraphLaunch");
+    }
+    if (loss_out) {
+        MAF_TRY(full_gradient(f, n, theta, weights, s), "flow loss");
+        float sums[2] = {0.f, 0.f};
+        MAF_TRY(cudaMemcpyAsync(sums, f->d_sums, sizeof sums, cudaMemcpyDeviceToHost, s), "cudaMemcpyAsync(sums)");
+        MAF_TRY(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+        *loss_out = sums[1] > 0.f ? sums[0] / sums[1] : 0.f;
+    } else {
+        MAF_TRY(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+    }
+    return plan_ok();
+}
+
+abc_status abc_maf_destroy(abc_maf f)
+{
+    if (!f) return plan_fail(ABC_ERR_INVALID_ARG, "flow is NULL");
+    if (f->graph) cudaGraphExecDestroy(f->graph);
+    cudaFree(f->d_params);
+    cudaFree(f->d_m);
+    cudaFree(f->d_v);
+    cudaFree(f->d_grad);
+    cudaFree(f->d_pub);
+    cudaFree(f->d_sums);
+    cudaFree(f->d_step);
+    cudaFree(f->d_rows);
+    delete f;
+    return plan_ok();
+}
+
+}  // extern "C"

@@ -1,0 +1,175 @@
+"""The flow proposal's BF16 tensor-core kernels against the float64 oracle.
+
+Parity is checked against the oracle's bf16 mode, which rounds the inputs of
+both matrix products (x, the hidden activations and the masked weights) to
+bfloat16 exactly where the tensor-core products do; what remains is FP32
+versus FP64 accumulation and elementwise math, plus the rare activation that
+sits on a bfloat16 rounding boundary. Tolerances below are set from that:
+typical |error| ~1e-5, bounded worst cases. Gradients (bf16 products in the
+backward pass, float64 oracle) are compared by relative norm and direction."""
+import numpy as np
+import pytest
+
+from oracle import maf_oracle as mo
+from tests import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_2012_14332_gb300 as abc  # noqa: E402
+from paper_2012_14332_gb300 import build as _build  # noqa: E402
+
+_build.build()
+DEV = torch.device("cuda", 0)
+LO = np.zeros(8)
+HI = np.array([1, 100, 2, 1, 1, 1, 1, 2.0])
+
+
+def _flow(K, H, seed, scale):
+    params = mo.init_params(np.random.default_rng(seed), K=K, H=H, scale=scale)
+    for p in params:
+        p["b1"] = np.random.default_rng(seed + 1).normal(0, 0.2, p["b1"].shape)
+        p["b2"] = np.random.default_rng(seed + 2).normal(0, 0.2, p["b2"].shape)
+    v = mo.flat(params).astype(np.float32)
+    f = abc.Flow(K, H)
+    f.set_params(v)
+    return f, mo.unflat(v.astype(np.float64), K, H)
+
+
+def _thetas(n, seed):
+    u = np.random.default_rng(seed).uniform(0.02, 0.98, size=(n, 8))
+    return (LO + (HI - LO) * u).astype(np.float32)
+
+
+@pytest.mark.parametrize("K,H", [(3, 256), (1, 16), (2, 64), (4, 128)])
+def test_log_q_matches_oracle(K, H):
+    f, params = _flow(K, H, 10 + K, 0.3)
+    th = _thetas(5003, K)
+    got = f.log_q(torch.from_numpy(th).to(DEV)).cpu().numpy().astype(np.float64)
+    want = mo.log_q_theta(th.astype(np.float64), params, LO, HI, bf16=True)
+    err = np.abs(got - want)
+    print("log_q K=%d H=%d: median %.2e p99 %.2e max %.2e" % (K, H, np.median(err), np.quantile(err, 0.99), err.max()))
+    assert np.median(err) < 1e-4 and np.quantile(err, 0.99) < 2e-3 and err.max() < 5e-2
+    f.close()
+
+
+@pytest.mark.parametrize("K,H", [(3, 256), (2, 32)])
+def test_sample_matches_oracle_inverse(K, H):
+    f, params = _flow(K, H, 20 + K, 0.3)
+    n = 3001
+    u = np.random.default_rng(3).normal(size=(n, 8)).astype(np.float32)
+    th, lq = f.sample(n, base_normals=torch.from_numpy(u).to(DEV))
+    th, lq = th.cpu().numpy().astype(np.float64), lq.cpu().numpy().astype(np.float64)
+    y, lqy = mo.inverse(u.astype(np.float64), params, bf16=True)
+    th_ref = mo.to_theta(y, LO, HI)
+    lq_ref = lqy - mo.log_jacobian_y(y, LO, HI)
+    rel = np.abs(th - th_ref) / (HI - LO)
+    errq = np.abs(lq - lq_ref)
+    print("sample K=%d H=%d: theta/width median %.2e p99 %.2e max %.2e; logq median %.2e p99 %.2e" % (
+        K, H, np.median(rel), np.quantile(rel, 0.99), rel.max(), np.median(errq), np.quantile(errq, 0.99)))
+    assert np.median(rel) < 1e-5 and np.quantile(rel, 0.99) < 1e-3
+    assert np.median(errq) < 1e-4 and np.quantile(errq, 0.99) < 5e-3
+    # the density kernel agrees with the log-density the sampler reports
+    lq2 = f.log_q(torch.from_numpy(th.astype(np.float32)).to(DEV)).cpu().numpy()
+    inside = np.all((th_ref > LO + 1e-4 * (HI - LO)) & (th_ref < HI - 1e-4 * (HI - LO)), axis=1)
+    ok = np.all(rel < 1e-3, axis=1) & inside
+    assert np.median(np.abs(lq2[ok] - lq[ok])) < 1e-3
+    f.close()
+
+
+def test_sampler_draws_follow_the_flow():
+    """Philox base normals: samples of a flow with zero parameters are the
+    box's logistic image of N(0, I) (u_j = sigmoid(z), z ~ N(0,1))."""
+    f = abc.Flow(3, 256)
+    n = 1 << 18
+    th, lq = f.sample(n, seed=5, stream=3)
+    th = th.cpu().numpy().astype(np.float64)
+    z = mo.to_y(th, LO, HI)
+    from scipy import stats
+    for j in range(8):
+        assert stats.kstest(z[:, j], "norm").pvalue > 1e-3, j
+    assert abs(np.corrcoef(z.T)[0, 1]) < 0.02
+    # log q of such a flow is log N(z) - log-Jacobian
+    ref = -0.5 * (z ** 2).sum(1) - 4 * np.log(2 * np.pi) - mo.log_jacobian_y(z, LO, HI)
+    assert np.median(np.abs(lq.cpu().numpy() - ref)) < 1e-3
+    f.close()
+
+
+def test_gradient_matches_oracle():
+    K, H = 3, 64
+    f, params = _flow(K, H, 31, 0.7)
+    n = 4096
+    th = _thetas(n, 7)
+    w = np.random.default_rng(8).uniform(0.2, 2.0, size=n).astype(np.float32)
+    loss, g = f.gradient(torch.from_numpy(th).to(DEV), torch.from_numpy(w).to(DEV))
+    y = mo.to_y(th.astype(np.float64), LO, HI)
+    bfp = [dict(W1=mo.round_bf16(p["W1"] * mo.masks(H)[0]), b1=p["b1"],
+                W2=mo.round_bf16(p["W2"] * mo.masks(H)[1]), b2=p["b2"]) for p in params]
+    loss_ref, grads = mo.loss_and_grad(y, w.astype(np.float64), bfp)
+    gref = mo.flat(grads)
+    rel = np.linalg.norm(g - gref) / np.linalg.norm(gref)
+    cos = g @ gref / (np.linalg.norm(g) * np.linalg.norm(gref))
+    print("gradient: loss %.6f vs %.6f, relative norm error %.3e, cosine %.6f" % (loss, loss_ref, rel, cos))
+    assert abs(loss - loss_ref) < 2e-3 * abs(loss_ref) + 1e-3
+    assert rel < 3e-2 and cos > 0.9995
+    # masked entries have exactly zero gradient
+    M1, M2 = mo.masks(H)
+    zero = mo.flat([dict(W1=1 - M1, b1=np.zeros(H), W2=1 - M2, b2=np.zeros(16))] * K) > 0
+    assert np.all(g[zero] == 0)
+    f.close()
+
+
+def test_adam_step_matches_oracle():
+    K, H = 2, 32
+    f, params = _flow(K, H, 41, 0.5)
+    th = _thetas(1000, 9)
+    thd = torch.from_numpy(th).to(DEV)
+    p0 = f.get_params().astype(np.float64)
+    state = {}
+    pv = mo.unflat(p0, K, H)
+    for step in range(3):
+        _, g = f.gradient(thd)
+        f.adam_step(lr=1e-2)
+        mo.adam_step(pv, mo.unflat(g.astype(np.float64), K, H), state, lr=1e-2)
+    got = f.get_params().astype(np.float64)
+    want = mo.flat(pv)
+    assert np.max(np.abs(got - want)) < 1e-5
+    f.close()
+
+
+def test_training_fits_a_known_density():
+    """Weighted maximum likelihood on the GPU: points from a correlated
+    Gaussian in y = logit space are fitted by a randomly initialised flow; the
+    trained flow's cross-entropy approaches the truth's entropy and its samples
+    match the truth's moments. The same data, initialisation scale and
+    schedule trained by the float64 oracle reach the same loss."""
+    rng = np.random.default_rng(12)
+    A = np.tril(rng.normal(size=(8, 8)) * 0.3) + np.eye(8) * 0.6
+    m = rng.normal(size=8) * 0.5
+    y = rng.normal(size=(20000, 8)) @ A.T + m
+    th = mo.to_theta(y, LO, HI).astype(np.float32)
+    ent = 0.5 * np.linalg.slogdet(2 * np.pi * np.e * A @ A.T)[1]
+    f = abc.Flow(3, 128)
+    f.init_random(seed=3, scale=0.3)
+    thd = torch.from_numpy(th).to(DEV)
+    loss = f.train(thd, None, n_steps=1500, batch=1024, lr=2e-3, seed=1)
+    # oracle: same data, same kind of initialisation and schedule
+    params = mo.init_params(np.random.default_rng(3), K=3, H=128, scale=0.3)
+    state = {}
+    yy = mo.to_y(th.astype(np.float64), LO, HI)
+    for _ in range(1500):
+        b = rng.integers(0, len(yy), 1024)
+        _, g = mo.loss_and_grad(yy[b], np.ones(1024), params)
+        mo.adam_step(params, g, state, lr=2e-3)
+    _, lq_o, _ = mo.forward(yy, params)
+    print("train: GPU loss %.4f, oracle loss %.4f, truth entropy %.4f" % (loss, -lq_o.mean(), ent))
+    assert loss < ent + 0.1
+    assert abs(loss - (-lq_o.mean())) < 0.05
+    ts, _ = f.sample(20000, seed=2)
+    ys = mo.to_y(ts.cpu().numpy().astype(np.float64), LO, HI)
+    assert np.allclose(ys.mean(0), m, atol=0.08)
+    assert np.allclose(np.cov(ys.T), A @ A.T, atol=0.1)
+    f.close()

@@ -1,0 +1,77 @@
+"""Sequential ABC with the learned flow proposal against plain prior ABC at
+the same final tolerance: the learned proposal must accept far more of its
+simulations (what the trained network gains), while its importance-weighted
+accepted samples estimate the same ABC posterior (Eq. 7) as plain rejection
+from the prior: weighted means within Monte-Carlo error and a weighted
+two-sample Kolmogorov-Smirnov test per coordinate with p > 0.01."""
+import numpy as np
+import pytest
+from scipy import stats
+
+from tests import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_2012_14332_gb300 as abc  # noqa: E402
+from paper_2012_14332_gb300 import build as _build  # noqa: E402
+
+_build.build()
+
+
+def weighted_ks(x, w, y):
+    """sup |F_w - G| between a weighted sample (n_eff = ESS) and a plain one,
+    with the asymptotic Kolmogorov p-value."""
+    o = np.argsort(x)
+    xs, ws = x[o], w[o] / w.sum()
+    ys = np.sort(y)
+    grid = np.concatenate([xs, ys])
+    Fw = np.concatenate([[0.0], np.cumsum(ws)])[np.searchsorted(xs, grid, side="right")]
+    G = np.searchsorted(ys, grid, side="right") / len(ys)
+    D = np.max(np.abs(Fw - G))
+    ne = w.sum() ** 2 / (w ** 2).sum()
+    en = np.sqrt(ne * len(y) / (ne + len(y)))
+    return D, stats.kstwobign.sf(D * en)
+
+
+def test_learned_proposal_gains_and_keeps_the_posterior():
+    w = inputs.workload("region_1e6_T49")
+    obs, P = w["observed"], w["P"]
+    pilot = abc.abc_distances(obs, P, 1 << 20, 99, mode="fast")
+    eps0 = abc.abc_kth_smallest(pilot, 1 << 13)          # ~0.8 % prior acceptance in round 0
+    rounds, N = 4, 1 << 20
+    info, th, wt, dist = abc.abc_smc_run(obs, P, eps0, rounds=rounds, sims_per_round=N, eps_factor=0.7,
+                                         flow_blocks=3, flow_hidden=128, train_steps=400, train_batch=1024,
+                                         train_lr=2e-3, seed=5, capacity=1 << 17, mode="fast")
+    for r in info:
+        print("round eps %.4g proposal %d accepted %d / %d  ESS %.3f  loss %.3f" % (
+            r["eps"], r["proposal"], r["n_accepted"], r["n_sims"], r["ess_fraction"], r["train_loss"]))
+    eps_f = info[-1]["eps"]
+    assert info[0]["proposal"] == 0 and info[-1]["proposal"] == 1
+    assert all(r["ess_fraction"] > 0.1 for r in info)
+    # plain prior ABC at the final tolerance
+    n_plain = 1 << 26
+    th_p, _, _, n_acc_p = abc.abc_sample(obs, P, eps_f, n_plain, 12345, mode="fast", capacity=1 << 18)
+    p_prior = n_acc_p / n_plain
+    p_flow = info[-1]["n_accepted"] / N
+    ess = info[-1]["ess_fraction"]
+    print("final eps %.4g: prior acceptance %.3e, flow acceptance %.3e (ESS fraction %.3f)" % (eps_f, p_prior, p_flow,
+                                                                                                 ess))
+    assert n_acc_p > 500
+    assert p_flow * ess > 5 * p_prior
+    # the weighted flow posterior against plain ABC
+    a = th.cpu().numpy().astype(np.float64)
+    wa = wt.cpu().numpy()
+    b = th_p.cpu().numpy().astype(np.float64)
+    ne = 1.0 / (wa ** 2).sum()
+    for j in range(8):
+        mw = (wa * a[:, j]).sum()
+        vw = (wa * (a[:, j] - mw) ** 2).sum()
+        se = np.sqrt(vw / ne + b[:, j].var() / len(b))
+        assert abs(mw - b[:, j].mean()) < 5 * se + 1e-9, j
+        D, p = weighted_ks(a[:, j], wa, b[:, j])
+        print("coordinate %d: weighted mean %.4f vs %.4f, KS D %.4f p %.3f" % (j, mw, b[:, j].mean(), D, p))
+        assert p > 0.01, j

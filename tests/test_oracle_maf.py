@@ -158,3 +158,25 @@ def test_training_recovers_a_gaussian():
 def test_ess_fraction():
     assert maf.ess_fraction(np.ones(10)) == 1.0
     assert np.isclose(maf.ess_fraction(np.array([1.0, 0, 0, 0])), 0.25)
+
+
+def test_bf16_rounding_is_round_to_nearest_even():
+    import struct
+    vals = np.array([1.0, 1.0 + 2**-8, 1.0 + 2**-9, 1.0 + 3 * 2**-9, -2.5, 1e-3, 3.14159265, 65504.0, 0.0])
+    r = maf.round_bf16(vals)
+    for v, got in zip(vals, r):
+        b = struct.unpack("<I", struct.pack("<f", np.float32(v)))[0]
+        lo, hi = b & 0xFFFF0000, (b & 0xFFFF0000) + 0x10000
+        fl = [struct.unpack("<f", struct.pack("<I", x))[0] for x in (lo, hi)]
+        d = [abs(np.float32(v) - f) for f in fl]
+        want = fl[0] if d[0] < d[1] else fl[1] if d[1] < d[0] else fl[0 if ((lo >> 16) & 1) == 0 else 1]
+        assert got == want, (v, got, want)
+
+
+def test_flat_roundtrip(params):
+    v = maf.flat(params)
+    assert len(v) == 3 * (H_SMALL * 8 + H_SMALL + 16 * H_SMALL + 16)
+    back = maf.unflat(v, 3, H_SMALL)
+    for a, b in zip(params, back):
+        for k in a:
+            assert np.array_equal(a[k], b[k])
