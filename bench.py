@@ -250,8 +250,9 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic", "config": {"workload": describe(w), "samples_per_step": n,
-                                            "parallelism": "host threads"},
+            "data": "synthetic", "config": {"workload": describe(w) + "; reference arm = the C oracle "
+                                                            "(exact-mode arithmetic) on the host cores",
+                                            "samples_per_step": n, "parallelism": "host threads"},
             "sims_days_per_s": n * args.steps * w["T"] / tot,
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": "%d prior samples per step of the same workload and eps" % n},
@@ -269,6 +270,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--leg", default="all", choices=["all", "headline", "batched", "learned"],
+                    help="run one leg only (profiling); 'all' is the benchmark")
     ap.add_argument("--samples", type=int, default=0,
                     help="samples per launch (profiling runs on a smaller case; not a benchmark value)")
     args = ap.parse_args()
@@ -315,6 +318,16 @@ def main():
         sim_days[0] += abc.abc_last_simulated_days()
         return a
 
+    if args.leg in ("batched", "learned"):
+        props = torch.cuda.get_device_properties(dev)
+        peaks = measured_peaks() or {}
+        if args.leg == "batched":
+            out = bench_batched(abc, torch, args.steps, args.warmup, dev, flush, props.multi_processor_count,
+                                peaks.get("sm_max_mhz", 2070.0))
+        else:
+            out = bench_learned(abc, torch, w, float("nan"), peaks)
+        print(json.dumps({"leg": args.leg, **out}), flush=True)
+        return
     for s in range(args.warmup):
         step(s)
     torch.cuda.synchronize()
@@ -413,6 +426,8 @@ def main():
         }
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(w)
+        if args.leg == "headline":
+            args.no_learned = args.no_batched = True
         if not args.no_learned and world == 1:
             line["learned_proposal"] = bench_learned(abc, torch, w, value, peaks)
         if not args.no_batched and world == 1:

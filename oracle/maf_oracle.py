@@ -9,7 +9,8 @@ next) without fixing how the next proposal is built. The proposal here is a
 density q(theta) learned from the previous round's accepted, importance
 weighted samples:
 
-  * support: the prior box, through y = logit((theta - lo) / (hi - lo));
+  * support: the prior box, through y = logit((theta - lo) / (hi - lo)),
+    with (theta - lo) / (hi - lo) held in [2^-24, 1 - 2^-24];
   * flow (Papamakarios, Pavlakou, Murray 2017): K MADE blocks (Germain, Gregor,
     Murray, Larochelle 2015), each x -> z = (x - mu(x)) exp(-alpha(x)) with
     mu_j, alpha_j depending on x_{<j} only, the order reversed between blocks,
@@ -121,6 +122,8 @@ def to_y(theta, lo, hi):
     lo = np.asarray(lo, dtype=np.float64)
     hi = np.asarray(hi, dtype=np.float64)
     u = (np.asarray(theta, dtype=np.float64) - lo) / (hi - lo)
+    # a point on the box's edge is read as 2^-24 of the width inside
+    u = np.clip(u, 2.0**-24, 1 - 2.0**-24)
     return np.log(u) - np.log1p(-u)
 
 

@@ -48,14 +48,16 @@ constexpr uint32_t kFull = 0xFFFFFFFFu;
 // Master (FP32) parameters of one block: W1 [H][8], b1 [H], W2 [16][H], b2 [16].
 __host__ __device__ inline int master_block(int H) { return 25 * H + 16; }
 
-// Published BF16 layout of one block, in 32-bit words (two bf16 per word):
+// Published BF16 layout of one block, in 32-bit words (two bf16 per word).
+// The forward operands come first, so density and sampling kernels stage only
+// fwd_words per block; the gradient kernel stages all words.
 //   w1  [H][4]        B operand of x W1^T      (n = hidden l, k = input j)
 //   w2  [16][H/2+4]   B operand of h W2^T      (n = output o, k = l), padded rows
+//   b1 [H], b2 [16]   FP32 biases
 //   w1t [8][H/2+4]    B operand of g_a1 W1     (n = j, k = l)
 //   w2t [H][12]       B operand of g_out W2    (n = l, k = o)
-//   b1 [H], b2 [16]   FP32 biases
 struct Layout {
-    int w1, w2, w1t, w2t, b1, b2, words;
+    int w1, w2, b1, b2, w1t, w2t, fwd_words, words;
 };
 __host__ __device__ inline Layout layout(int H)
 {
@@ -63,10 +65,11 @@ __host__ __device__ inline Layout layout(int H)
     int o = 0;
     L.w1 = o; o += H * 4;
     L.w2 = o; o += 16 * (H / 2 + 4);
-    L.w1t = o; o += 8 * (H / 2 + 4);
-    L.w2t = o; o += H * 12;
     L.b1 = o; o += H;
     L.b2 = o; o += 16;
+    L.fwd_words = o;
+    L.w1t = o; o += 8 * (H / 2 + 4);
+    L.w2t = o; o += H * 12;
     L.words = o;
     return L;
 }
@@ -168,9 +171,11 @@ __device__ __forceinline__ void made_fwd(const BlockView& v, int H, const float 
 }
 
 // theta -> y = logit((theta - lo) / w) and the log-Jacobian term log(w u (1 - u)).
+// u is held in [2^-24, 1 - 2^-24]: a point on the box's edge (a flow draw whose
+// sigmoid rounded to 0 or 1) is read as lying 2^-24 of the width inside.
 __device__ __forceinline__ void to_y(const Box& b, int j, float th, float& y, float& jac)
 {
-    const float u = (th - b.lo[j]) / b.w[j];
+    const float u = fminf(fmaxf((th - b.lo[j]) / b.w[j], 0x1p-24f), 0x1.fffffep-1f);
     const float lu = logf(u), l1u = log1pf(-u);
     y = lu - l1u;
     jac = b.logw[j] + lu + l1u;
@@ -185,6 +190,13 @@ __device__ __forceinline__ void to_theta(const Box& b, int j, float y, float& th
     const float s = y >= 0.f ? 1.f / (1.f + e) : e / (1.f + e);
     th = b.lo[j] + b.w[j] * s;
     jac = b.logw[j] + ls + l1s;
+}
+
+// the forward words of each of K blocks, packed block after block (stride fwd_words)
+__device__ __forceinline__ void stage_forward(uint32_t* sm, const uint32_t* pub, int K, const Layout& L)
+{
+    for (int b = 0; b < K; ++b)
+        for (int i = threadIdx.x; i < L.fwd_words; i += blockDim.x) sm[b * L.fwd_words + i] = pub[b * L.words + i];
 }
 
 __device__ __forceinline__ void stage_weights(uint32_t* sm, const uint32_t* pub, int words)
@@ -215,7 +227,7 @@ __global__ void publish_kernel(const float* __restrict__ master, uint32_t* __res
             __nv_bfloat162 v = __floats2bfloat162_rn(mask1(l, j0) ? W1[l * 8 + j0] : 0.f,
                                                      mask1(l, j0 + 1) ? W1[l * 8 + j0 + 1] : 0.f);
             out = *reinterpret_cast<uint32_t*>(&v);
-        } else if (w < L.w1t) {
+        } else if (w < L.b1) {
             const int r = w - L.w2, o = r / hw, c = r % hw;
             if (c < H / 2) {
                 const int l0 = 2 * c;
@@ -223,6 +235,10 @@ __global__ void publish_kernel(const float* __restrict__ master, uint32_t* __res
                                                          mask2(o, l0 + 1) ? W2[o * H + l0 + 1] : 0.f);
                 out = *reinterpret_cast<uint32_t*>(&v);
             }
+        } else if (w < L.b2) {
+            out = __float_as_uint(b1[w - L.b1]);
+        } else if (w < L.w1t) {
+            out = __float_as_uint(b2[w - L.b2]);
         } else if (w < L.w2t) {
             const int r = w - L.w1t, j = r / hw, c = r % hw;
             if (c < H / 2) {
@@ -231,7 +247,7 @@ __global__ void publish_kernel(const float* __restrict__ master, uint32_t* __res
                                                          mask1(l0 + 1, j) ? W1[(l0 + 1) * 8 + j] : 0.f);
                 out = *reinterpret_cast<uint32_t*>(&v);
             }
-        } else if (w < L.b1) {
+        } else {
             const int r = w - L.w2t, l = r / 12, c = r % 12;
             if (c < 8) {
                 const int o0 = 2 * c;
@@ -239,10 +255,6 @@ __global__ void publish_kernel(const float* __restrict__ master, uint32_t* __res
                                                          mask2(o0 + 1, l) ? W2[(o0 + 1) * H + l] : 0.f);
                 out = *reinterpret_cast<uint32_t*>(&v);
             }
-        } else if (w < L.b2) {
-            out = __float_as_uint(b1[w - L.b1]);
-        } else {
-            out = __float_as_uint(b2[w - L.b2]);
         }
         pub[idx] = out;
     }
@@ -258,7 +270,7 @@ __global__ void __launch_bounds__(128) logq_kernel(const uint32_t* __restrict__ 
 {
     extern __shared__ __align__(16) uint32_t sm[];
     const Layout L = layout(H);
-    stage_weights(sm, pub, K * L.words);
+    stage_forward(sm, pub, K, L);
     __syncthreads();
     const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
     const uint64_t tiles = (n + 15) / 16;
@@ -278,7 +290,7 @@ __global__ void __launch_bounds__(128) logq_kernel(const uint32_t* __restrict__ 
 #pragma unroll
         for (int b = 0; b < K; ++b) {
             float mu[4], ar[4];
-            made_fwd(view(sm + b * L.words, L), H, x, mu, ar);
+            made_fwd(view(sm + b * L.fwd_words, L), H, x, mu, ar);
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
                 const float al = soft_alpha(ar[e]);
@@ -307,7 +319,7 @@ __global__ void __launch_bounds__(128) sample_kernel(const uint32_t* __restrict_
 {
     extern __shared__ __align__(16) uint32_t sm[];
     const Layout L = layout(H);
-    stage_weights(sm, pub, K * L.words);
+    stage_forward(sm, pub, K, L);
     __syncthreads();
     const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
     const uint64_t tiles = (n + 15) / 16;
@@ -333,14 +345,23 @@ __global__ void __launch_bounds__(128) sample_kernel(const uint32_t* __restrict_
         for (int e = 0; e < 4; ++e) lq[e] = -0.5f * x[e] * x[e];
 #pragma unroll
         for (int bb = K - 1; bb >= 0; --bb) {
-            const BlockView v = view(sm + bb * L.words, L);
+            const BlockView v = view(sm + bb * L.fwd_words, L);
             float z[4] = {x[0], x[1], x[2], x[3]};
             reverse_cols(z);
             float xin[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
             for (int j = 0; j < kD; ++j) {
                 float mu[4], ar[4];
-                made_fwd(v, H, xin, mu, ar);
+                if (j == 0) {
+                    // output 0 has degree 1: every weight into it is masked, mu_0 and
+                    // alpha_0 are the biases
+                    const float2 bm = *reinterpret_cast<const float2*>(v.b2 + 2 * t);
+                    const float2 bs = *reinterpret_cast<const float2*>(v.b2 + 8 + 2 * t);
+                    mu[0] = mu[2] = bm.x; mu[1] = mu[3] = bm.y;
+                    ar[0] = ar[2] = bs.x; ar[1] = ar[3] = bs.y;
+                } else {
+                    made_fwd(v, H, xin, mu, ar);
+                }
                 if (t == (j >> 1)) {
                     const int e = j & 1;
                     const float al0 = soft_alpha(ar[e]), al1 = soft_alpha(ar[2 + e]);
@@ -678,12 +699,12 @@ namespace {
         if (_e != cudaSuccess) return plan_cuda_fail(_e, what); \
     } while (0)
 
-size_t fwd_smem(const abc_maf_s* f) { return sizeof(uint32_t) * (size_t)f->K * maf::layout(f->H).words; }
+size_t fwd_smem(const abc_maf_s* f) { return sizeof(uint32_t) * (size_t)f->K * maf::layout(f->H).fwd_words; }
 
 size_t grad_smem(const abc_maf_s* f)
 {
-    return fwd_smem(f) + sizeof(float) * (size_t)f->K * maf::master_block(f->H) +
-           sizeof(maf::WarpStage) * maf::kGradWarps;
+    return sizeof(uint32_t) * (size_t)f->K * maf::layout(f->H).words +
+           sizeof(float) * (size_t)f->K * maf::master_block(f->H) + sizeof(maf::WarpStage) * maf::kGradWarps;
 }
 
 abc_status check(abc_maf f)
@@ -702,6 +723,18 @@ int sm_count()
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     return sms > 0 ? sms : 1;
 }
+
+// blocks to launch: all that fit on the GPU at once, or fewer if the work is smaller
+template <typename Kern>
+int fill_grid(Kern k, int threads, size_t smem, uint64_t want)
+{
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, smem) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    const uint64_t cap = (uint64_t)sm_count() * per_sm;
+    return (int)(want < cap ? (want > 0 ? want : 1) : cap);
+}
+
 
 template <typename Kern>
 cudaError_t allow_smem(Kern k, size_t bytes)
@@ -723,8 +756,7 @@ cudaError_t launch_logq(abc_maf f, uint64_t n, const float* theta, float* logq, 
     cudaError_t e = allow_smem(maf::logq_kernel<K>, smem);
     if (e != cudaSuccess) return e;
     const uint64_t tiles = (n + 15) / 16;
-    const uint64_t want = (tiles + 3) / 4;
-    const int grid = (int)(want < (uint64_t)sm_count() * 2 ? (want > 0 ? want : 1) : (uint64_t)sm_count() * 2);
+    const int grid = fill_grid(maf::logq_kernel<K>, 128, smem, (tiles + 3) / 4);
     maf::logq_kernel<K><<<grid, 128, smem, s>>>(f->d_pub, f->H, f->box, theta, n, logq);
     return cudaGetLastError();
 }
@@ -737,8 +769,7 @@ cudaError_t launch_sample(abc_maf f, uint64_t n, const float* u, const ModelPara
     cudaError_t e = allow_smem(maf::sample_kernel<K>, smem);
     if (e != cudaSuccess) return e;
     const uint64_t tiles = (n + 15) / 16;
-    const uint64_t want = (tiles + 3) / 4;
-    const int grid = (int)(want < (uint64_t)sm_count() * 2 ? (want > 0 ? want : 1) : (uint64_t)sm_count() * 2);
+    const int grid = fill_grid(maf::sample_kernel<K>, 128, smem, (tiles + 3) / 4);
     maf::sample_kernel<K><<<grid, 128, smem, s>>>(f->d_pub, f->H, f->box, u, p, ctr3, first, n, theta, logq);
     return cudaGetLastError();
 }

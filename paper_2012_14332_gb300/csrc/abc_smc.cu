@@ -138,14 +138,16 @@ extern "C" abc_status abc_smc_run(const abc_prior_box* prior, const int32_t* obs
             // (1 - defensive) N flow draws, the rest prior draws, all weighted by the mixture density
             const uint64_t n_prior = (uint64_t)std::floor(cfg->defensive * (double)N);
             const uint64_t n_flow = N - n_prior;
-            if (n_flow) SMC_ST(abc_maf_sample(gd.flow, n_flow, nullptr, cfg->seed, 1, first, d_prop, nullptr, s));
+            // flow draws carry the sampler's log q (exact for the drawn point); the
+            // prior draws get the flow's density evaluated at them
+            if (n_flow) SMC_ST(abc_maf_sample(gd.flow, n_flow, nullptr, cfg->seed, 1, first, d_prop, d_logq, s));
             if (n_prior) {
                 const abcgb::ModelParams pp = abcgb::plan_make_params(prior, 1, 1, cfg->seed, 0, nullptr);
                 prior_theta_kernel<<<(unsigned)((n_prior + 255) / 256), 256, 0, s>>>(pp, first + n_flow, n_prior,
                                                                                    d_prop + 8 * n_flow);
                 SMC_TRY(cudaGetLastError(), "prior draw launch");
+                SMC_ST(abc_maf_log_q(gd.flow, n_prior, d_prop + 8 * n_flow, d_logq + n_flow, s));
             }
-            SMC_ST(abc_maf_log_q(gd.flow, N, d_prop, d_logq, s));
             if (cfg->defensive > 0.0) {
                 mixture_logq_kernel<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(
                     d_logq, N, (float)std::log1p(-cfg->defensive), (float)(std::log(cfg->defensive) + log_prior));

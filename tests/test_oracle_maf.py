@@ -180,3 +180,10 @@ def test_flat_roundtrip(params):
     for a, b in zip(params, back):
         for k in a:
             assert np.array_equal(a[k], b[k])
+
+
+def test_edge_points_are_clamped_inside():
+    y = maf.to_y(np.array([[0.0, 100.0, 1.0, 0.5, 0.5, 0.5, 0.5, 1.0]]), np.zeros(8),
+                 np.array([1, 100, 2, 1, 1, 1, 1, 2.0]))
+    assert np.all(np.isfinite(y))
+    assert np.isclose(y[0, 0], np.log(2.0**-24) - np.log1p(-2.0**-24))
