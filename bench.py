@@ -180,6 +180,43 @@ def bench_batched(abc, torch, steps, warmup, dev, flush, sm_count, sm_max):
             "roofline": roofline(days / steps, launch_ms, sm_count, sm_max)}
 
 
+def bench_streamed(abc, torch, dev, flush, sm_count, sm_max, chunks=16):
+    """Sixteen regions (P log-uniform in 1e6 .. 3e8, T uniform in 30 .. 180,
+    own eps each) streamed in 2^24-sample chunks (2^20 per region per chunk),
+    2^28 simulations in all, with the accepted samples accumulating in the
+    plan's device-resident buffers; the chunks are one CUDA-graph replay."""
+    with open(os.path.join(ROOT, "tests", "golden", "workloads.json")) as f:
+        wl = json.load(f)
+    names = sorted(k for k in wl if k.startswith("stream16_"))
+    regs = [dict(observed=np.array(wl[nm]["observed"], dtype=np.int32), N_pop=wl[nm]["P"], eps=wl[nm]["eps"],
+                 n_samples=wl[nm]["n_samples"], first_index=0, stream=r, capacity=1 << 16)
+            for r, nm in enumerate(names)]
+    plan = abc.Plan(regs, wl[names[0]]["seed"], mode="fast")
+    s = torch.cuda.Stream(dev)
+    best, _ = plan.tune(s)
+    with torch.cuda.stream(s):
+        plan.run_graph(chunks, s)          # warm-up replay (captures the graph)
+        s.synchronize()
+        plan.reset(s)
+        flush.fill_(1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        plan.run_graph(chunks, s)
+        e1.record(s)
+        s.synchronize()
+    ms = e0.elapsed_time(e1)
+    counts = [plan.counts(r, s) for r in range(len(regs))]
+    plan.close()
+    acc = sum(c[0] for c in counts)
+    days = sum(c[1] for c in counts)
+    nominal = chunks * sum(g["n_samples"] * (g["observed"].shape[1] - 1) for g in regs)
+    return {"workload": "16 regions (P log-uniform 1e6..3e8, T uniform 30..180, own eps each), 2^28 prior samples "
+                        "streamed in %d chunks of 2^24 in one CUDA-graph replay, fast mode" % chunks,
+            "value": acc / (ms * 1e-3), "unit": UNIT, "ms_total": ms, "accepted": acc,
+            "sims_days_per_s": nominal / (ms * 1e-3), "simulated_days": days, "tuned_shape": best,
+            "roofline": roofline(days, ms, sm_count, sm_max)}
+
+
 def bench_learned(abc, torch, w, prior_value, peaks):
     """Sequential ABC with the learned flow proposal on the P = 6e7, T = 100
     region: 5 rounds of 2^22 simulations, eps shrinking by 0.7 per round to the
@@ -270,7 +307,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
-    ap.add_argument("--leg", default="all", choices=["all", "headline", "batched", "learned"],
+    ap.add_argument("--no-streamed", action="store_true")
+    ap.add_argument("--leg", default="all", choices=["all", "headline", "batched", "learned", "streamed"],
                     help="run one leg only (profiling); 'all' is the benchmark")
     ap.add_argument("--samples", type=int, default=0,
                     help="samples per launch (profiling runs on a smaller case; not a benchmark value)")
@@ -318,12 +356,14 @@ def main():
         sim_days[0] += abc.abc_last_simulated_days()
         return a
 
-    if args.leg in ("batched", "learned"):
+    if args.leg in ("batched", "learned", "streamed"):
         props = torch.cuda.get_device_properties(dev)
         peaks = measured_peaks() or {}
         if args.leg == "batched":
             out = bench_batched(abc, torch, args.steps, args.warmup, dev, flush, props.multi_processor_count,
                                 peaks.get("sm_max_mhz", 2070.0))
+        elif args.leg == "streamed":
+            out = bench_streamed(abc, torch, dev, flush, props.multi_processor_count, peaks.get("sm_max_mhz", 2070.0))
         else:
             out = bench_learned(abc, torch, w, float("nan"), peaks)
         print(json.dumps({"leg": args.leg, **out}), flush=True)
@@ -427,12 +467,14 @@ def main():
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(w)
         if args.leg == "headline":
-            args.no_learned = args.no_batched = True
+            args.no_learned = args.no_batched = args.no_streamed = True
         if not args.no_learned and world == 1:
             line["learned_proposal"] = bench_learned(abc, torch, w, value, peaks)
         if not args.no_batched and world == 1:
             line["batched_regions"] = bench_batched(abc, torch, args.steps, args.warmup, dev, flush,
                                                     props.multi_processor_count, sm_max)
+        if not args.no_streamed and world == 1:
+            line["streamed_regions"] = bench_streamed(abc, torch, dev, flush, props.multi_processor_count, sm_max)
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.barrier()

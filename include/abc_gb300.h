@@ -166,7 +166,8 @@ typedef struct {
     uint64_t first_index;    /* sample index of the first run; each run advances it by n_samples */
     uint32_t stream;         /* RNG stream of this region (< 2^30) */
     uint64_t capacity;       /* accepted samples kept by the plan for this region */
-    const float* theta_in;   /* DEVICE float [n_samples][8] proposals, or NULL to draw from the prior */
+    const float* theta_in;   /* DEVICE float [n_samples][8] proposals, or NULL to draw from the prior;
+                                a proposal whose first coordinate is NaN is skipped (not simulated) */
 } abc_region;
 
 typedef struct abc_plan_s* abc_plan;
@@ -362,6 +363,54 @@ typedef struct {
 abc_status abc_smc_run(const abc_prior_box* prior, const int32_t* observed, int32_t T, int64_t N_pop,
                        const abc_smc_config* cfg, abc_smc_round* rounds_out, float* theta_out,
                        double* weight_out, double* dist_out, uint64_t* n_out, void* cuda_stream);
+
+/* Plain sequential ABC: population Monte Carlo ABC (Beaumont, Cornuet, Marin,
+ * Robert 2009), the SMC-ABC the paper names in Sec. 2.2. Round 0 is rejection
+ * from the prior at eps0; round t (eps_t = eps0 * eps_factor^t) proposes
+ * theta = theta_j + L z, parent j drawn with probability proportional to its
+ * weight, z ~ N(0, I), L L^T = 2 Cov_w(previous population); proposals
+ * outside the prior box are not simulated; an accepted particle gets the
+ * weight 1 / sum_j w_j exp(-|L^-1 (theta - theta_j)|^2 / 2) (prior over the
+ * Gaussian mixture, constants cancelling), normalised to sum 1. Each round
+ * simulates batches of `batch` proposals until it holds at least
+ * n_particles accepted ones (at most max_batches); all accepted ones of those
+ * batches form the population. Simulations use (seed, stream 0, index),
+ * proposals (seed, stream 2, index). */
+typedef struct {
+    int32_t rounds;
+    uint64_t n_particles;
+    uint64_t batch;
+    int32_t max_batches;
+    double eps0;
+    double eps_factor;
+    uint64_t seed;
+    uint64_t capacity;        /* population buffer size (>= n_particles) */
+    abc_mode mode;
+} abc_pmc_config;
+
+typedef struct {
+    double eps;
+    uint64_t n_sims;          /* proposals generated */
+    uint64_t n_accepted;      /* population size */
+    double ess_fraction;
+    float ms;
+} abc_pmc_round;
+
+abc_status abc_pmc_run(const abc_prior_box* prior, const int32_t* observed, int32_t T, int64_t N_pop,
+                       const abc_pmc_config* cfg, abc_pmc_round* rounds_out, float* theta_out,
+                       double* weight_out, double* dist_out, uint64_t* n_out, void* cuda_stream);
+
+/* The population Monte Carlo pieces on their own, for tests and custom loops:
+ * proposals (DEVICE float [n][8], NaN first coordinate = outside the box) from
+ * a weighted population (DEVICE float [m][8], DEVICE double weights [m]) and
+ * the lower-triangular L (HOST float [8][8], row-major); and the weights of
+ * new particles (DEVICE float [n][8] -> DEVICE double [n]) against the old
+ * population. Async on cuda_stream. */
+abc_status abc_pmc_propose(const abc_prior_box* prior, const float* theta_old, const double* w_old, uint64_t m,
+                           const float* L, uint64_t seed, uint64_t first_index, uint64_t n, float* theta_out,
+                           void* cuda_stream);
+abc_status abc_pmc_weights(const float* theta_new, uint64_t n, const float* theta_old, const double* w_old,
+                           uint64_t m, const float* L, double* w_out, void* cuda_stream);
 
 /* Variant of abc_sample that allocates no memory. It is for callers that must
  * not allocate device memory while sampling: code running inside a host

@@ -26,7 +26,8 @@ EXPORTED = ("abc_sample", "abc_distances", "abc_simulate", "abc_step", "abc_kth_
             "abc_plan_reset", "abc_plan_run", "abc_plan_run_graph", "abc_plan_tune", "abc_plan_results",
             "abc_plan_copy_results", "abc_plan_set_region", "abc_plan_destroy", "abc_maf_create",
             "abc_maf_init_random", "abc_maf_param_count", "abc_maf_set_params", "abc_maf_get_params", "abc_maf_sample", "abc_maf_log_q",
-            "abc_maf_gradient", "abc_maf_adam_step", "abc_maf_train", "abc_maf_destroy", "abc_smc_run", "abc_project")
+            "abc_maf_gradient", "abc_maf_adam_step", "abc_maf_train", "abc_maf_destroy", "abc_smc_run", "abc_project", "abc_pmc_run", "abc_pmc_propose",
+            "abc_pmc_weights")
 ABC_MAX_REGIONS = 32
 ABC_NOALLOC_T_MAX = 1024
 
@@ -59,6 +60,17 @@ class AbcSmcRound(ctypes.Structure):
                 ("n_accepted", ctypes.c_uint64), ("simulated_days", ctypes.c_uint64),
                 ("ess_fraction", ctypes.c_double), ("train_loss", ctypes.c_float), ("ms_propose", ctypes.c_float),
                 ("ms_simulate", ctypes.c_float), ("ms_train", ctypes.c_float)]
+
+
+class AbcPmcConfig(ctypes.Structure):
+    _fields_ = [("rounds", ctypes.c_int32), ("n_particles", ctypes.c_uint64), ("batch", ctypes.c_uint64),
+                ("max_batches", ctypes.c_int32), ("eps0", ctypes.c_double), ("eps_factor", ctypes.c_double),
+                ("seed", ctypes.c_uint64), ("capacity", ctypes.c_uint64), ("mode", ctypes.c_int)]
+
+
+class AbcPmcRound(ctypes.Structure):
+    _fields_ = [("eps", ctypes.c_double), ("n_sims", ctypes.c_uint64), ("n_accepted", ctypes.c_uint64),
+                ("ess_fraction", ctypes.c_double), ("ms", ctypes.c_float)]
 
 
 class AbcError(RuntimeError):
@@ -133,10 +145,17 @@ def load(path=None):
                                     vp]
         L.abc_maf_destroy.argtypes = [pp]
         for nm in ("abc_maf_create", "abc_maf_set_params", "abc_maf_get_params", "abc_maf_sample", "abc_maf_log_q",
-                   "abc_maf_gradient", "abc_maf_adam_step", "abc_maf_train", "abc_maf_destroy", "abc_smc_run", "abc_project"):
+                   "abc_maf_gradient", "abc_maf_adam_step", "abc_maf_train", "abc_maf_destroy", "abc_smc_run", "abc_project", "abc_pmc_run", "abc_pmc_propose",
+            "abc_pmc_weights"):
             getattr(L, nm).restype = ctypes.c_int
         L.abc_project.argtypes = [vp, vp, u64, vp, i32, i64, u64, u32, ctypes.c_int, vp, i32, vp, vp]
         L.abc_project.restype = ctypes.c_int
+        L.abc_pmc_run.argtypes = [box, vp, i32, i64, ctypes.POINTER(AbcPmcConfig), ctypes.POINTER(AbcPmcRound), vp, vp,
+                                  vp, ctypes.POINTER(ctypes.c_uint64), vp]
+        L.abc_pmc_propose.argtypes = [box, vp, vp, u64, vp, u64, u64, u64, vp, vp]
+        L.abc_pmc_weights.argtypes = [vp, u64, vp, vp, u64, vp, vp, vp]
+        for nm in ("abc_pmc_run", "abc_pmc_propose", "abc_pmc_weights"):
+            getattr(L, nm).restype = ctypes.c_int
         L.abc_smc_run.argtypes = [box, vp, i32, i64, ctypes.POINTER(AbcSmcConfig), ctypes.POINTER(AbcSmcRound), vp, vp,
                                   vp, ctypes.POINTER(ctypes.c_uint64), vp]
         L.abc_smc_run.restype = ctypes.c_int
@@ -604,3 +623,52 @@ def abc_project(theta, sample_index, init_ard, T, N_pop, seed, quantiles=(0.05, 
                             int(T), int(N_pop), int(seed), int(stream), _mode(mode), q.ctypes.data, len(q),
                             bands.data_ptr(), _stream(cuda_stream)))
     return bands
+
+
+
+def abc_pmc_run(observed, N_pop, eps0, rounds=4, n_particles=4096, batch=1 << 20, max_batches=64, eps_factor=0.7,
+                seed=0, capacity=1 << 17, mode="fast", lo=PAPER_LO, hi=PAPER_HI, cuda_stream=None):
+    """Population Monte Carlo ABC. Returns (rounds: list of dicts, theta [m, 8],
+    weights [m] (f64, sum 1), dist [m]) of the last population."""
+    L = load()
+    obs, obs_p = _host_i32(observed)
+    T = obs.shape[1] - 1
+    cfg = AbcPmcConfig(int(rounds), int(n_particles), int(batch), int(max_batches), float(eps0), float(eps_factor),
+                       int(seed), int(capacity), _mode(mode))
+    rr = (AbcPmcRound * int(rounds))()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    theta = torch.empty((capacity, 8), dtype=torch.float32, device=dev)
+    w = torch.empty((capacity,), dtype=torch.float64, device=dev)
+    dist = torch.empty((capacity,), dtype=torch.float64, device=dev)
+    n = ctypes.c_uint64()
+    s = cuda_stream if cuda_stream is not None else torch.cuda.Stream()
+    torch.cuda.current_stream().synchronize()
+    b = prior_box(lo, hi)
+    _check(L, L.abc_pmc_run(ctypes.byref(b), obs_p, T, int(N_pop), ctypes.byref(cfg), rr, theta.data_ptr(),
+                            w.data_ptr(), dist.data_ptr(), ctypes.byref(n), _stream(s)))
+    out = [dict((f, getattr(r, f)) for f, _ in AbcPmcRound._fields_) for r in rr]
+    m = int(n.value)
+    return out, theta[:m], w[:m], dist[:m]
+
+
+def abc_pmc_propose(theta_old, w_old, Lmat, n, seed=0, first_index=0, lo=PAPER_LO, hi=PAPER_HI, cuda_stream=None):
+    """n proposals from a weighted population (CUDA f32 [m, 8], CUDA f64 [m]) and
+    the host lower-triangular L [8, 8]; NaN first coordinate = outside the box."""
+    L = load()
+    Lh = np.ascontiguousarray(np.asarray(Lmat, dtype=np.float32).reshape(8, 8))
+    out = torch.empty((n, 8), dtype=torch.float32, device=theta_old.device)
+    b = prior_box(lo, hi)
+    _check(L, L.abc_pmc_propose(ctypes.byref(b), theta_old.data_ptr(), w_old.data_ptr(), theta_old.shape[0],
+                                Lh.ctypes.data, int(seed), int(first_index), int(n), out.data_ptr(),
+                                _stream(cuda_stream)))
+    return out
+
+
+def abc_pmc_weights(theta_new, theta_old, w_old, Lmat, cuda_stream=None):
+    """Unnormalised population Monte Carlo weights of theta_new (CUDA f64 [n])."""
+    L = load()
+    Lh = np.ascontiguousarray(np.asarray(Lmat, dtype=np.float32).reshape(8, 8))
+    out = torch.empty((theta_new.shape[0],), dtype=torch.float64, device=theta_new.device)
+    _check(L, L.abc_pmc_weights(theta_new.data_ptr(), theta_new.shape[0], theta_old.data_ptr(), w_old.data_ptr(),
+                                theta_old.shape[0], Lh.ctypes.data, out.data_ptr(), _stream(cuda_stream)))
+    return out

@@ -6,7 +6,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libabc_gb300.so")
-SOURCES = ["abc_kernels.cu", "abc_batch.cu", "abc_maf.cu", "abc_api.cu", "abc_plan.cu", "abc_smc.cu"]
+SOURCES = ["abc_kernels.cu", "abc_batch.cu", "abc_maf.cu", "abc_api.cu", "abc_plan.cu", "abc_smc.cu", "abc_pmc.cu"]
 HEADERS = ["abc_kernels.h", "abc_model.cuh"]
 PUBLIC_HEADER = os.path.join(os.path.dirname(HERE), "include", "abc_gb300.h")
 

@@ -87,21 +87,25 @@ __global__ void __launch_bounds__(BLOCK) abc_batch_kernel(const __grid_constant_
                     const uint64_t j0 = (c - R.chunk_begin) * 32;
                     const uint64_t left = R.n_samples - j0;
                     const uint32_t made = left < 32 ? (uint32_t)left : 32u;
+                    float th[8];
+                    bool keep = false;
                     if (lane < made) {
-                        const uint64_t j = j0 + lane;
-                        const uint64_t ii = R.first_index + j;
-                        float th[8];
                         if (R.theta_in)
-                            load_theta(R.theta_in + 8 * j, th);
+                            load_theta(R.theta_in + 8 * (j0 + lane), th);
                         else
-                            prior_draw_s(p, ii, R.ctr3_base, th);
-                        const uint32_t slot = (tail + lane) & (kRingB - 1);
+                            prior_draw_s(p, R.first_index + j0 + lane, R.ctr3_base, th);
+                        // a proposal whose first coordinate is NaN is skipped (no simulation)
+                        keep = th[0] == th[0];
+                    }
+                    const uint32_t kept = __ballot_sync(0xFFFFFFFFu, keep);
+                    if (keep) {
+                        const uint32_t slot = (tail + __popc(kept & lt_mask)) & (kRingB - 1);
                         ring.lo[slot] = make_float4(th[0], th[1], th[2], th[3]);
                         ring.hi[slot] = make_float4(th[4], th[5], th[6], th[7]);
-                        ring.idx[slot] = ii;
+                        ring.idx[slot] = R.first_index + j0 + lane;
                         ring.region[slot] = r;
                     }
-                    tail += made;
+                    tail += __popc(kept);
                     __syncwarp();
                 }
             }

@@ -343,32 +343,44 @@ __global__ void __launch_bounds__(128) sample_kernel(const uint32_t* __restrict_
         float lq[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) lq[e] = -0.5f * x[e] * x[e];
-#pragma unroll
+        // blocks and passes are runtime loops (a fully unrolled 3 x 8 inverse
+        // overflows the instruction cache); passes go in pairs so every
+        // register index stays static: pass 2p+1 fills column 2p+1 (lane t = p,
+        // element 1), pass 2p+2 fills column 2p+2 (lane t = p+1, element 0)
+#pragma unroll 1
         for (int bb = K - 1; bb >= 0; --bb) {
             const BlockView v = view(sm + bb * L.fwd_words, L);
             float z[4] = {x[0], x[1], x[2], x[3]};
             reverse_cols(z);
             float xin[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-            for (int j = 0; j < kD; ++j) {
+            if (t == 0) {
+                // column 0 has degree 1: every weight into mu_0, alpha_0 is masked
+                const float al0 = soft_alpha(v.b2[8]);
+                xin[0] = z[0] * expf(al0) + v.b2[0];
+                xin[2] = z[2] * expf(al0) + v.b2[0];
+                lq[0] -= al0;
+                lq[2] -= al0;
+            }
+#pragma unroll 1
+            for (int pj = 0; pj < kD / 2; ++pj) {
                 float mu[4], ar[4];
-                if (j == 0) {
-                    // output 0 has degree 1: every weight into it is masked, mu_0 and
-                    // alpha_0 are the biases
-                    const float2 bm = *reinterpret_cast<const float2*>(v.b2 + 2 * t);
-                    const float2 bs = *reinterpret_cast<const float2*>(v.b2 + 8 + 2 * t);
-                    mu[0] = mu[2] = bm.x; mu[1] = mu[3] = bm.y;
-                    ar[0] = ar[2] = bs.x; ar[1] = ar[3] = bs.y;
-                } else {
-                    made_fwd(v, H, xin, mu, ar);
+                made_fwd(v, H, xin, mu, ar);
+                if (t == pj) {
+                    const float al0 = soft_alpha(ar[1]), al1 = soft_alpha(ar[3]);
+                    xin[1] = z[1] * expf(al0) + mu[1];
+                    xin[3] = z[3] * expf(al1) + mu[3];
+                    lq[1] -= al0;
+                    lq[3] -= al1;
                 }
-                if (t == (j >> 1)) {
-                    const int e = j & 1;
-                    const float al0 = soft_alpha(ar[e]), al1 = soft_alpha(ar[2 + e]);
-                    xin[e] = z[e] * expf(al0) + mu[e];
-                    xin[2 + e] = z[2 + e] * expf(al1) + mu[2 + e];
-                    lq[e] -= al0;
-                    lq[2 + e] -= al1;
+                if (pj < kD / 2 - 1) {
+                    made_fwd(v, H, xin, mu, ar);
+                    if (t == pj + 1) {
+                        const float al0 = soft_alpha(ar[0]), al1 = soft_alpha(ar[2]);
+                        xin[0] = z[0] * expf(al0) + mu[0];
+                        xin[2] = z[2] * expf(al1) + mu[2];
+                        lq[0] -= al0;
+                        lq[2] -= al1;
+                    }
                 }
             }
             x[0] = xin[0]; x[1] = xin[1]; x[2] = xin[2]; x[3] = xin[3];

@@ -47,6 +47,21 @@ WORKLOADS = {
 }
 
 
+# sixteen regions for the streamed batch: populations log-uniform in 1e6 .. 3e8,
+# horizons uniform in 30 .. 180 days (seeded), 2^24 / 16 = 2^20 samples each per chunk
+def stream_regions():
+    g = np.random.default_rng(20210101)
+    out = {}
+    for r in range(16):
+        P = int(round(10 ** g.uniform(6, np.log10(3e8))))
+        T = int(g.integers(30, 181))
+        out["stream16_r%02d" % r] = dict(P=P, T=T, n_samples=1 << 20, quantile=1e-4, pilot=1 << 18, mode="fast")
+    return out
+
+
+WORKLOADS.update(stream_regions())
+
+
 def round_sig(x, sig=3):
     if x == 0:
         return 0.0

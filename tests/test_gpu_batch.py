@@ -135,3 +135,24 @@ def test_tune_keeps_state_and_picks_a_shape():
                              first_index=g["first_index"], capacity=8192)
         assert plan.counts(r)[0] == ref[3]
     plan.close()
+
+
+def test_nan_proposals_are_skipped():
+    w = inputs.workload("region_1e6_T49")
+    n, first, stream = 2000, 10, 3
+    th = inputs.random_thetas(13, n)
+    skip = np.zeros(n, dtype=bool)
+    skip[::3] = True
+    skip[1500:1540] = True
+    th_nan = th.copy()
+    th_nan[skip, 0] = np.nan
+    eps = 1e12   # accept every simulated sample
+    plan = abc.Plan([dict(observed=w["observed"], N_pop=w["P"], eps=eps, n_samples=n, first_index=first,
+                          stream=stream, capacity=n, theta_in=torch.from_numpy(th_nan).to(DEV))], SEED, mode="exact")
+    plan.run()
+    tt, di, ix, n_acc, days = plan.results(0)
+    tt, di, ix = _sorted(tt, di, ix)
+    keep = np.nonzero(~skip)[0]
+    assert n_acc == len(keep) and np.array_equal(ix, keep + first) and np.array_equal(tt, th[keep])
+    assert days == len(keep) * w["T"]
+    plan.close()
