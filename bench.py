@@ -217,6 +217,54 @@ def bench_streamed(abc, torch, dev, flush, sm_count, sm_max, chunks=16):
             "roofline": roofline(days, ms, sm_count, sm_max)}
 
 
+def ess(w):
+    w = np.asarray(w, dtype=np.float64)
+    return float(w.sum() ** 2 / (w ** 2).sum()) if len(w) else 0.0
+
+
+def bench_learned_stream(abc, torch, prior_stream=None):
+    """Sixteen regions (the streamed leg's), one flow proposal per region:
+    16 rounds, each one batched launch of 2^20 simulations per region (2^24
+    per chunk, 2^28 in all); eps shrinks by 0.7 per round to each region's
+    final eps over the first 4 rounds, then stays there while the samples
+    accepted at the final eps pool in device buffers with their importance
+    weights; the 16 flows (3 x 256, BF16) train together after every round,
+    a region falling back to the prior whenever its ESS drops below 10 %."""
+    with open(os.path.join(ROOT, "tests", "golden", "workloads.json")) as f:
+        wl = json.load(f)
+    names = sorted(k for k in wl if k.startswith("stream16_"))
+    regs = [dict(observed=np.array(wl[nm]["observed"], dtype=np.int32), N_pop=wl[nm]["P"], eps=wl[nm]["eps"],
+                 pool=1 << 21) for nm in names]
+    rounds, shrink, n = 16, 4, 1 << 20
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    info, res = abc.abc_smc_run_regions(regs, rounds=rounds, shrink_rounds=shrink, sims_per_round=n, eps_factor=0.7,
+                                        flow_blocks=3, flow_hidden=256, train_steps=500, train_steps_warm=100,
+                                        train_batch=4096, train_lr=1e-3, seed=wl[names[0]]["seed"] + 29,
+                                        capacity=1 << 20, mode="fast")
+    wall = time.perf_counter() - t0
+    pooled = sum(r[3] for r in res)
+    eff = sum(ess(r[1].cpu().numpy()) for r in res)
+    dev_s = sum(info[r][0]["ms_propose"] + info[r][0]["ms_simulate"] + info[r][0]["ms_train"] for r in range(rounds))
+    out = {"workload": "16 regions (P log-uniform 1e6..3e8, T uniform 30..180, own final eps each), one flow "
+                       "proposal per region (3 x 256 BF16), %d rounds x 2^20 simulations per region (2^24 per "
+                       "chunk, 2^28 in all), eps x0.7 per round over the first %d rounds, fast mode" % (rounds, shrink),
+           "seconds": wall, "device_seconds_by_round_events": dev_s * 1e-3,
+           "propose_seconds": sum(info[r][0]["ms_propose"] for r in range(rounds)) * 1e-3,
+           "simulate_seconds": sum(info[r][0]["ms_simulate"] for r in range(rounds)) * 1e-3,
+           "weights_and_train_seconds": sum(info[r][0]["ms_train"] for r in range(rounds)) * 1e-3,
+           "pooled_accepted_at_final_eps": pooled, "pooled_effective": eff,
+           "accepted_per_s": pooled / wall, "effective_accepted_per_s": eff / wall,
+           "flow_rounds": int(sum(info[r][g]["proposal"] for r in range(rounds) for g in range(len(regs)))),
+           "fallback_rounds": int(sum(1 - info[r][g]["proposal"] for r in range(1, rounds) for g in range(len(regs)))),
+           "min_ess_fraction": min(info[r][g]["ess_fraction"] for r in range(rounds) for g in range(len(regs))
+                                   if info[r][g]["n_accepted"] > 0)}
+    if prior_stream:
+        out["prior_stream_accepted_per_s"] = prior_stream["value"]
+        out["gain_effective_vs_prior_stream"] = out["effective_accepted_per_s"] / prior_stream["value"]
+    return out
+
+
 def bench_learned(abc, torch, w, prior_value, peaks):
     """Sequential ABC with the learned flow proposal on the P = 6e7, T = 100
     region: 5 rounds of 2^22 simulations, eps shrinking by 0.7 per round to the
@@ -226,7 +274,7 @@ def bench_learned(abc, torch, w, prior_value, peaks):
     eps0 = w["eps"] / factor ** (rounds - 1)
     info, th, wt, dist = abc.abc_smc_run(w["observed"], w["P"], eps0, rounds=rounds, sims_per_round=n,
                                          eps_factor=factor, flow_blocks=3, flow_hidden=256, train_steps=500,
-                                         train_batch=1024, train_lr=1e-3, seed=w["seed"] + 17, capacity=1 << 18,
+                                         train_batch=4096, train_lr=1e-3, seed=w["seed"] + 17, capacity=1 << 18,
                                          mode="fast")
     last = info[-1]
     ms = last["ms_propose"] + last["ms_simulate"]
@@ -308,7 +356,9 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--no-streamed", action="store_true")
-    ap.add_argument("--leg", default="all", choices=["all", "headline", "batched", "learned", "streamed"],
+    ap.add_argument("--no-learned-stream", action="store_true")
+    ap.add_argument("--leg", default="all", choices=["all", "headline", "batched", "learned", "streamed",
+                                                     "learned_stream"],
                     help="run one leg only (profiling); 'all' is the benchmark")
     ap.add_argument("--samples", type=int, default=0,
                     help="samples per launch (profiling runs on a smaller case; not a benchmark value)")
@@ -348,15 +398,17 @@ def main():
     def first_index(step):
         return (step * world + rank) * n
 
-    sim_days = [0]
+    # the observed series is uploaded once; each step enqueues one launch whose
+    # counters (accepted, processed, simulated days) stay on the device until
+    # the timed region ends, so steps run back to back with no host round trip
+    obs_dev = abc.Observed(obs, P)
+    counters = torch.zeros((args.warmup + args.steps, 4), dtype=torch.int64, device=dev)
 
     def step(s):
-        _, _, _, a = abc.abc_sample(obs, P, eps, n, seed, mode=w["mode"], first_index=first_index(s), capacity=cap,
-                                    out=outs)
-        sim_days[0] += abc.abc_last_simulated_days()
-        return a
+        abc.abc_sample_async(obs_dev, eps, n, seed, outs, counters[s], mode=w["mode"], first_index=first_index(s),
+                             cuda_stream=stream)
 
-    if args.leg in ("batched", "learned", "streamed"):
+    if args.leg in ("batched", "learned", "streamed", "learned_stream"):
         props = torch.cuda.get_device_properties(dev)
         peaks = measured_peaks() or {}
         if args.leg == "batched":
@@ -364,6 +416,8 @@ def main():
                                 peaks.get("sm_max_mhz", 2070.0))
         elif args.leg == "streamed":
             out = bench_streamed(abc, torch, dev, flush, props.multi_processor_count, peaks.get("sm_max_mhz", 2070.0))
+        elif args.leg == "learned_stream":
+            out = bench_learned_stream(abc, torch)
         else:
             out = bench_learned(abc, torch, w, float("nan"), peaks)
         print(json.dumps({"leg": args.leg, **out}), flush=True)
@@ -371,7 +425,6 @@ def main():
     for s in range(args.warmup):
         step(s)
     torch.cuda.synchronize()
-    sim_days[0] = 0
 
     sampler = ClockSampler(local)
     sampler.start()
@@ -379,7 +432,6 @@ def main():
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     region0, region1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    accepted = 0
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
@@ -387,10 +439,15 @@ def main():
     for s in range(args.steps):
         flush.fill_(s & 0xFF)                       # evict L2 between steps
         starts[s].record(stream)
-        accepted += step(args.warmup + s)
+        step(args.warmup + s)
         ends[s].record(stream)
     region1.record(stream)
     torch.cuda.synchronize()
+    cnt = counters[args.warmup:].cpu().numpy()
+    if (cnt[:, 0] > cap).any():
+        raise RuntimeError("more accepted samples in a step than the output capacity %d" % cap)
+    accepted = int(cnt[:, 0].sum())
+    sim_days = [int(cnt[:, 2].sum())]
     if dist is not None:
         dist.barrier()
     clocks = sampler.stop()
@@ -449,6 +506,8 @@ def main():
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": describe(w), "samples_per_step": sims_per_step,
                        "parallelism": "dp%d" % world, "l2": "flushed between steps (256 MiB write)",
+                       "timed_call": "abc_sample_async: observed series resident on the device, one launch per step, "
+                                     "counters read after the timed region",
                        "eps": eps, "seed": seed},
             "sims_days_per_s": sims_per_step * T / (ms_per_step * 1e-3),
             "simulated_days_per_step": sim_days[0] / args.steps,
@@ -467,7 +526,7 @@ def main():
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(w)
         if args.leg == "headline":
-            args.no_learned = args.no_batched = args.no_streamed = True
+            args.no_learned = args.no_batched = args.no_streamed = args.no_learned_stream = True
         if not args.no_learned and world == 1:
             line["learned_proposal"] = bench_learned(abc, torch, w, value, peaks)
         if not args.no_batched and world == 1:
@@ -475,6 +534,8 @@ def main():
                                                     props.multi_processor_count, sm_max)
         if not args.no_streamed and world == 1:
             line["streamed_regions"] = bench_streamed(abc, torch, dev, flush, props.multi_processor_count, sm_max)
+        if not args.no_learned_stream and world == 1:
+            line["learned_stream"] = bench_learned_stream(abc, torch, line.get("streamed_regions"))
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.barrier()

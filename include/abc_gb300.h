@@ -81,13 +81,41 @@ typedef enum {
  * Samples whose running distance^2 exceeds eps^2 are abandoned early (partial
  * sums only grow); the result is that of simulating all T days of every sample.
  * Uses a small amount of device scratch memory (the observed series and three
- * counters) allocated stream-ordered on cuda_stream and freed before returning.
- * Requires eps >= 0 (not NaN) and first_index + n_samples < 2^64. */
+ * counters) and pinned host memory to stage it, allocated on the first call of
+ * each host thread on each device, grown when a longer series needs more and
+ * kept for the life of the thread. The call synchronises cuda_stream before it
+ * returns. Requires eps >= 0 (not NaN) and first_index + n_samples < 2^64. */
 abc_status abc_sample(const abc_prior_box* prior, const int32_t* observed, int32_t T,
                       int64_t N_pop, double eps, uint64_t n_samples, uint64_t seed,
                       uint32_t stream, abc_mode mode, uint64_t first_index, float* theta_out,
                       double* dist_out, uint64_t* idx_out, uint64_t capacity,
                       uint64_t* n_accepted, void* cuda_stream);
+
+/* A region's observed series, checked and copied to device memory once, for
+ * repeated asynchronous sampling (abc_sample_async). observed is HOST int32
+ * [3][T+1] as for abc_sample; the handle keeps a device copy and the initial
+ * condition (column 0). Create and destroy synchronise the current device; a
+ * handle belongs to the device that was current at creation. */
+typedef struct abc_observed_s* abc_observed;
+abc_status abc_observed_create(const int32_t* observed, int32_t T, int64_t N_pop, abc_observed* out);
+abc_status abc_observed_destroy(abc_observed obs);
+
+/* abc_sample without a host round trip (Sec. 2.2 and Sec. 3.1; the same kernel,
+ * accept set and outputs), for pipelined chunks of one region: the call zeroes
+ * counters_dev (DEVICE uint64 [3]) on cuda_stream, enqueues the kernel and
+ * returns without synchronising. When the stream reaches that point,
+ * counters_dev[0] holds the number of accepted samples (the true count, which
+ * may exceed capacity: then the outputs hold an unspecified subset of
+ * `capacity` of them), counters_dev[1] the kernel's claim counter (index
+ * chunks are claimed 32 at a time, so it ends at or above n_samples) and
+ * counters_dev[2] the number of model days simulated.
+ * Outputs and counters must stay untouched until then. Allocates nothing and
+ * may be captured in a CUDA graph. Errors reported are argument errors and
+ * launch failures; the capacity check is the caller's. */
+abc_status abc_sample_async(const abc_prior_box* prior, abc_observed obs, double eps, uint64_t n_samples,
+                            uint64_t seed, uint32_t stream, abc_mode mode, uint64_t first_index,
+                            float* theta_out, double* dist_out, uint64_t* idx_out, uint64_t capacity,
+                            uint64_t* counters_dev, void* cuda_stream);
 
 /* The distance of every sample in [first_index, first_index + n_samples)
  * (Sec. 2.2): dist_out DEVICE double [n_samples], dist_out[j] the distance of
@@ -228,6 +256,10 @@ abc_status abc_plan_copy_results(abc_plan plan, int32_t region, float* theta_dst
  * prior draws, and/or set its next first_index. Synchronous (cudaMemcpy). */
 abc_status abc_plan_set_region(abc_plan plan, int32_t region, const float* theta_in, uint64_t first_index);
 
+/* Set a region's tolerance for the following runs (eps >= 0, not NaN).
+ * Synchronous (cudaMemcpy of the one table field). */
+abc_status abc_plan_set_eps(abc_plan plan, int32_t region, double eps);
+
 /* Release the plan's device memory and graph. */
 abc_status abc_plan_destroy(abc_plan plan);
 
@@ -263,16 +295,28 @@ typedef struct abc_maf_s* abc_maf;
  * image of N(0, I)). Allocates its device memory on the current device. */
 abc_status abc_maf_create(int32_t n_blocks, int32_t hidden, const abc_prior_box* box, abc_maf* maf_out);
 
+/* A set of n_flows (1..ABC_MAF_MAX_FLOWS) independent flows of the same shape
+ * in one object, one per region of a batched run: their parameters sit one
+ * flow after another, abc_maf_train_flows trains all of them in the same
+ * launches, and the *_at calls sample or evaluate one of them. An object made
+ * by abc_maf_create is a set of one flow; the calls without a flow index act
+ * on flow 0, except set/get/init, which cover every flow. */
+#define ABC_MAF_MAX_FLOWS 64
+abc_status abc_maf_create_multi(int32_t n_flows, int32_t n_blocks, int32_t hidden, const abc_prior_box* box,
+                                abc_maf* maf_out);
+int32_t abc_maf_flow_count(abc_maf maf);
+
 /* Random initial parameters: W1 ~ N(0, scale^2 / 8), W2 ~ N(0, scale^2 / hidden),
  * zero biases (so the ReLU units start active and the flow near the base
  * density), from a host generator seeded with `seed`; resets Adam. */
 abc_status abc_maf_init_random(abc_maf maf, uint64_t seed, float scale);
 
-/* Number of parameters (floats) in the order above. */
+/* Number of parameters (floats) of one flow, in the order above. */
 int64_t abc_maf_param_count(abc_maf maf);
 
-/* Copy parameters from / to HOST float arrays (synchronous). Setting
- * parameters also resets the Adam moments. */
+/* Copy parameters from / to HOST float arrays [n_flows][param_count]
+ * (synchronous). Setting parameters also resets the Adam moments. The random
+ * initialisation draws the flows one after another from the one generator. */
 abc_status abc_maf_set_params(abc_maf maf, const float* params);
 abc_status abc_maf_get_params(abc_maf maf, float* params);
 
@@ -282,10 +326,15 @@ abc_status abc_maf_get_params(abc_maf maf, float* params);
  * logq_out DEVICE float [n] (log q(theta)) or NULL. Async. */
 abc_status abc_maf_sample(abc_maf maf, uint64_t n, const float* base_normals, uint64_t seed, uint32_t stream,
                           uint64_t first_index, float* theta_out, float* logq_out, void* cuda_stream);
+abc_status abc_maf_sample_at(abc_maf maf, int32_t flow, uint64_t n, const float* base_normals, uint64_t seed,
+                             uint32_t stream, uint64_t first_index, float* theta_out, float* logq_out,
+                             void* cuda_stream);
 
 /* log q(theta) for n points (DEVICE float [n][8] inside the box) into logq_out
  * (DEVICE float [n]). Async. */
 abc_status abc_maf_log_q(abc_maf maf, uint64_t n, const float* theta, float* logq_out, void* cuda_stream);
+abc_status abc_maf_log_q_at(abc_maf maf, int32_t flow, uint64_t n, const float* theta, float* logq_out,
+                            void* cuda_stream);
 
 /* Gradient of the weighted mean of -log q_y(y(theta)) over n points (theta
  * DEVICE [n][8], weights DEVICE [n] >= 0 or NULL for all ones) into the flow's
@@ -296,7 +345,8 @@ abc_status abc_maf_gradient(abc_maf maf, uint64_t n, const float* theta, const f
                             float* grads_out, void* cuda_stream);
 
 /* One Adam step (Kingma and Ba) of the master parameters with the flow's
- * current gradient, then refresh the BF16 copies. Async. */
+ * current gradient, then refresh the BF16 copies; flows of a set whose
+ * current gradient has no points keep their parameters. Async. */
 abc_status abc_maf_adam_step(abc_maf maf, float lr, float beta1, float beta2, float eps, void* cuda_stream);
 
 /* Weighted maximum-likelihood training: n_steps Adam steps, each on a batch of
@@ -307,6 +357,17 @@ abc_status abc_maf_adam_step(abc_maf maf, float lr, float beta1, float beta2, fl
  * required for the graph). */
 abc_status abc_maf_train(abc_maf maf, uint64_t n, const float* theta, const float* weights, int32_t n_steps,
                          int32_t batch, float lr, uint64_t seed, float* loss_out, void* cuda_stream);
+
+/* abc_maf_train for every flow of a set at once, each on its own data: HOST
+ * arrays [n_flows] of DEVICE pointers theta[r] ([n[r]][8]) and weights[r]
+ * ([n[r]] or NULL; `weights` itself may be NULL for all ones) and of counts
+ * n[r] < 2^32; a flow with n[r] = 0 is left as it is. Each step draws `batch`
+ * rows per flow and updates all flows with one gradient launch (one CTA row of
+ * the grid per flow) and one Adam launch. loss_out HOST float [n_flows] or
+ * NULL. Synchronizes cuda_stream (non-default). */
+abc_status abc_maf_train_flows(abc_maf maf, const float* const* theta, const float* const* weights, const uint64_t* n,
+                               int32_t n_steps, int32_t batch, float lr, uint64_t seed, float* loss_out,
+                               void* cuda_stream);
 
 abc_status abc_maf_destroy(abc_maf maf);
 
@@ -363,6 +424,49 @@ typedef struct {
 abc_status abc_smc_run(const abc_prior_box* prior, const int32_t* observed, int32_t T, int64_t N_pop,
                        const abc_smc_config* cfg, abc_smc_round* rounds_out, float* theta_out,
                        double* weight_out, double* dist_out, uint64_t* n_out, void* cuda_stream);
+
+/* Sequential ABC with one learned proposal per region, for many regions at
+ * once (a stream of chunks): round r runs every region's sims_per_round
+ * proposals in one batched launch (abc_plan_*). Region g's tolerance shrinks
+ * geometrically to its own final eps over the first shrink_rounds rounds,
+ * eps_{g,r} = eps_g / eps_factor^(shrink_rounds - 1 - r), and stays at eps_g
+ * afterwards. Each region has its own flow (one set, abc_maf_create_multi);
+ * after every round the flows of all regions whose round was good enough are
+ * trained together (abc_maf_train_flows) on that round's weighted accepts, and
+ * a region whose effective sample size fell below ess_min of its accepts (or
+ * that accepted fewer than 64) falls back to the prior for its next round, as
+ * in abc_smc_run (defensive mixture included). Every sample accepted at the
+ * region's final eps (all rounds from shrink_rounds - 1 on) is pooled in the
+ * region's output buffers with its unnormalised weight prior / q_mix (1 for
+ * prior rounds): the weighted pool estimates the ABC posterior at eps_g
+ * (Eq. 7). Region g simulates with (seed, stream g, index r *
+ * sims_per_round + j) and its flow draws with (seed, stream n_regions + g,
+ * the same index). The first training of the flows runs base.train_steps
+ * Adam steps, later ones (warm starts) train_steps_warm. */
+typedef struct {
+    const int32_t* observed;  /* HOST int32 [3][T+1] */
+    int32_t T;
+    int64_t N_pop;
+    double eps;               /* the region's final tolerance */
+    float* theta_out;         /* DEVICE float [capacity][8]: pooled samples at eps */
+    double* weight_out;       /* DEVICE double [capacity]: their unnormalised weights */
+    double* dist_out;         /* DEVICE double [capacity] */
+    uint64_t capacity;
+    uint64_t n_pooled;        /* out: accepted at eps over all rounds (may exceed capacity) */
+    uint64_t n_out;           /* out: samples written, min(n_pooled, capacity) */
+} abc_smc_region;
+
+typedef struct {
+    abc_smc_config base;      /* rounds, sims_per_round (per region), eps_factor, ess_min, flow shape and
+                                 training, seed, capacity (per round and region), mode, defensive; eps0 unused */
+    int32_t shrink_rounds;    /* 1..rounds */
+    int32_t train_steps_warm; /* Adam steps of every later training */
+} abc_smc_stream_config;
+
+/* rounds_out HOST [rounds][n_regions]. n_regions in 1..ABC_MAX_REGIONS.
+ * Synchronizes cuda_stream (non-default). */
+abc_status abc_smc_run_regions(const abc_prior_box* prior, abc_smc_region* regions, int32_t n_regions,
+                               const abc_smc_stream_config* cfg, abc_smc_round* rounds_out, void* cuda_stream);
 
 /* Plain sequential ABC: population Monte Carlo ABC (Beaumont, Cornuet, Marin,
  * Robert 2009), the SMC-ABC the paper names in Sec. 2.2. Round 0 is rejection

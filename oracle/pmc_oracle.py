@@ -39,6 +39,16 @@ def kernel_factor(theta, w, jitter=1e-12):
     raise np.linalg.LinAlgError("covariance not positive definite")
 
 
+def parent_uniform(w0, w1):
+    """The parent draw's uniform in [0, 1) from two 32-bit random words: the
+    top 27 bits of w0 and the top 26 bits of w1 form a 53-bit integer, scaled
+    by 2^-53 (a double with every value k 2^-53, k < 2^53, equally likely)."""
+    w0 = np.asarray(w0, dtype=np.uint64)
+    w1 = np.asarray(w1, dtype=np.uint64)
+    k = ((w0 >> np.uint64(5)) << np.uint64(26)) | (w1 >> np.uint64(6))
+    return k.astype(np.float64) * 2.0 ** -53
+
+
 def propose(theta, w, L, u, z, lo, hi):
     """Parents from uniforms u (inverse CDF of the cumulative weights), moves
     L z; rows outside the box become NaN."""

@@ -62,6 +62,17 @@ class AbcSmcRound(ctypes.Structure):
                 ("ms_simulate", ctypes.c_float), ("ms_train", ctypes.c_float)]
 
 
+class AbcSmcRegion(ctypes.Structure):
+    _fields_ = [("observed", ctypes.c_void_p), ("T", ctypes.c_int32), ("N_pop", ctypes.c_int64),
+                ("eps", ctypes.c_double), ("theta_out", ctypes.c_void_p), ("weight_out", ctypes.c_void_p),
+                ("dist_out", ctypes.c_void_p), ("capacity", ctypes.c_uint64), ("n_pooled", ctypes.c_uint64),
+                ("n_out", ctypes.c_uint64)]
+
+
+class AbcSmcStreamConfig(ctypes.Structure):
+    _fields_ = [("base", AbcSmcConfig), ("shrink_rounds", ctypes.c_int32), ("train_steps_warm", ctypes.c_int32)]
+
+
 class AbcPmcConfig(ctypes.Structure):
     _fields_ = [("rounds", ctypes.c_int32), ("n_particles", ctypes.c_uint64), ("batch", ctypes.c_uint64),
                 ("max_batches", ctypes.c_int32), ("eps0", ctypes.c_double), ("eps_factor", ctypes.c_double),
@@ -107,8 +118,12 @@ def load(path=None):
         L.abc_simulate.argtypes = [vp, vp, u64, vp, i32, i64, u64, u32, ctypes.c_int, vp, vp]
         L.abc_step.argtypes = [vp, vp, vp, vp, u64, i64, u64, u32, ctypes.c_int, vp, vp, vp]
         L.abc_kth_smallest.argtypes = [vp, u64, u64, ctypes.POINTER(ctypes.c_double), vp]
+        L.abc_observed_create.argtypes = [vp, i32, i64, ctypes.POINTER(ctypes.c_void_p)]
+        L.abc_observed_destroy.argtypes = [vp]
+        L.abc_sample_async.argtypes = [box, vp, ctypes.c_double, u64, u64, u32, ctypes.c_int, u64, vp, vp, vp, u64,
+                                       vp, vp]
         for nm in ("abc_sample", "abc_sample_noalloc", "abc_distances", "abc_simulate", "abc_step",
-                   "abc_kth_smallest"):
+                   "abc_kth_smallest", "abc_observed_create", "abc_observed_destroy", "abc_sample_async"):
             getattr(L, nm).restype = ctypes.c_int
         L.abc_strerror.argtypes = [ctypes.c_int]
         L.abc_strerror.restype = ctypes.c_char_p
@@ -144,6 +159,14 @@ def load(path=None):
         L.abc_maf_train.argtypes = [pp, u64, vp, vp, i32, i32, ctypes.c_float, u64, ctypes.POINTER(ctypes.c_float),
                                     vp]
         L.abc_maf_destroy.argtypes = [pp]
+        L.abc_maf_create_multi.argtypes = [i32, i32, i32, box, ctypes.POINTER(pp)]
+        L.abc_maf_flow_count.argtypes = [pp]
+        L.abc_maf_flow_count.restype = ctypes.c_int32
+        L.abc_maf_sample_at.argtypes = [pp, i32, u64, vp, u64, u32, u64, vp, vp, vp]
+        L.abc_maf_log_q_at.argtypes = [pp, i32, u64, vp, vp, vp]
+        L.abc_maf_train_flows.argtypes = [pp, vp, vp, vp, i32, i32, ctypes.c_float, u64, vp, vp]
+        for nm in ("abc_maf_create_multi", "abc_maf_sample_at", "abc_maf_log_q_at", "abc_maf_train_flows"):
+            getattr(L, nm).restype = ctypes.c_int
         for nm in ("abc_maf_create", "abc_maf_set_params", "abc_maf_get_params", "abc_maf_sample", "abc_maf_log_q",
                    "abc_maf_gradient", "abc_maf_adam_step", "abc_maf_train", "abc_maf_destroy", "abc_smc_run", "abc_project", "abc_pmc_run", "abc_pmc_propose",
             "abc_pmc_weights"):
@@ -159,6 +182,11 @@ def load(path=None):
         L.abc_smc_run.argtypes = [box, vp, i32, i64, ctypes.POINTER(AbcSmcConfig), ctypes.POINTER(AbcSmcRound), vp, vp,
                                   vp, ctypes.POINTER(ctypes.c_uint64), vp]
         L.abc_smc_run.restype = ctypes.c_int
+        L.abc_smc_run_regions.argtypes = [box, ctypes.POINTER(AbcSmcRegion), i32, ctypes.POINTER(AbcSmcStreamConfig),
+                                          ctypes.POINTER(AbcSmcRound), vp]
+        L.abc_smc_run_regions.restype = ctypes.c_int
+        L.abc_plan_set_eps.argtypes = [pp, i32, ctypes.c_double]
+        L.abc_plan_set_eps.restype = ctypes.c_int
         L.abc_last_simulated_days.argtypes = []
         L.abc_last_simulated_days.restype = ctypes.c_uint64
         if path is None:
@@ -246,6 +274,65 @@ def abc_sample(observed, N_pop, eps, n_samples, seed, stream=0, mode="fast", fir
     n = int(nacc.value)
     m = min(n, capacity)
     return theta[:m], dist[:m], idx[:m], n
+
+
+class Observed:
+    """A region's observed series (host int32 [3, T+1]) uploaded once to the
+    current device, for abc_sample_async."""
+
+    def __init__(self, observed, N_pop):
+        L = load()
+        obs, obs_p = _host_i32(observed)
+        self.T = obs.shape[1] - 1
+        self.N_pop = int(N_pop)
+        h = ctypes.c_void_p()
+        _check(L, L.abc_observed_create(obs_p, self.T, self.N_pop, ctypes.byref(h)))
+        self._h = h
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise ValueError("observed series handle is closed")
+        return self._h
+
+    def close(self):
+        if self._h is not None:
+            _check(load(), load().abc_observed_destroy(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def abc_observed_create(observed, N_pop):
+    """The observed series uploaded to the current device (an Observed)."""
+    return Observed(observed, N_pop)
+
+
+def abc_observed_destroy(obs):
+    obs.close()
+
+
+def abc_sample_async(obs, eps, n_samples, seed, out, counters, stream=0, mode="fast", first_index=0, lo=PAPER_LO,
+                     hi=PAPER_HI, cuda_stream=None):
+    """Enqueue ABC rejection for one chunk without waiting for it: obs is an
+    Observed, out = (theta [cap, 8] f32, dist [cap] f64, idx [cap] int64) and
+    counters a CUDA int64 tensor of >= 3 entries, all on the current device.
+    When the stream gets there, counters[0] = accepted (may exceed cap),
+    counters[1] = the claim counter (>= n_samples), counters[2] = simulated days."""
+    L = load()
+    theta, dist, idx = out
+    capacity = theta.shape[0]
+    if counters.dtype != torch.int64 or not counters.is_cuda or counters.numel() < 3 or not counters.is_contiguous():
+        raise ValueError("counters must be a contiguous CUDA int64 tensor of >= 3 entries")
+    b = prior_box(lo, hi)
+    _check(L, L.abc_sample_async(ctypes.byref(b), obs.handle, float(eps), int(n_samples), int(seed), int(stream),
+                                 _mode(mode), int(first_index), _dev(theta, torch.float32, (capacity, 8)),
+                                 _dev(dist, torch.float64, (capacity,)), _dev(idx, torch.int64, (capacity,)),
+                                 int(capacity), counters.data_ptr(), _stream(cuda_stream)))
 
 
 def abc_sample_noalloc(observed, N_pop, eps, n_samples, seed, out, stream=0, mode="fast", first_index=0,
@@ -411,6 +498,9 @@ class Plan:
                                                     theta_in.data_ptr() if theta_in is not None else None,
                                                     int(first_index)))
 
+    def set_eps(self, region, eps):
+        _check(self._L, self._L.abc_plan_set_eps(self._h, int(region), float(eps)))
+
     def close(self):
         if getattr(self, "_h", None):
             self._L.abc_plan_destroy(self._h)
@@ -454,39 +544,70 @@ def abc_plan_set_region(plan, region, theta_in=None, first_index=0):
     plan.set_region(region, theta_in, first_index)
 
 
+def abc_plan_set_eps(plan, region, eps):
+    plan.set_eps(region, eps)
+
+
 def abc_plan_destroy(plan):
     plan.close()
 
 
 
 class Flow:
-    """Masked autoregressive flow proposal on the prior box (C ABI abc_maf_*)."""
+    """Masked autoregressive flow proposal on the prior box (C ABI abc_maf_*);
+    n_flows > 1 holds that many independent flows of the same shape."""
 
-    def __init__(self, n_blocks=3, hidden=256, lo=PAPER_LO, hi=PAPER_HI):
+    def __init__(self, n_blocks=3, hidden=256, lo=PAPER_LO, hi=PAPER_HI, n_flows=1):
         L = load()
         self._L = L
         h = ctypes.c_void_p()
         b = prior_box(lo, hi)
-        _check(L, L.abc_maf_create(int(n_blocks), int(hidden), ctypes.byref(b), ctypes.byref(h)))
+        _check(L, L.abc_maf_create_multi(int(n_flows), int(n_blocks), int(hidden), ctypes.byref(b), ctypes.byref(h)))
         self._h = h
-        self.n_blocks, self.hidden = int(n_blocks), int(hidden)
+        self.n_blocks, self.hidden, self.n_flows = int(n_blocks), int(hidden), int(n_flows)
         self.n_params = int(L.abc_maf_param_count(h))
 
     def init_random(self, seed=0, scale=0.3):
         _check(self._L, self._L.abc_maf_init_random(self._h, int(seed), float(scale)))
 
     def set_params(self, params):
+        """params: [n_params] (one flow) or [n_flows, n_params]."""
         v = np.ascontiguousarray(np.asarray(params, dtype=np.float32).ravel())
-        assert v.size == self.n_params
+        assert v.size == self.n_params * self.n_flows
         _check(self._L, self._L.abc_maf_set_params(self._h, v.ctypes.data))
 
     def get_params(self):
-        v = np.empty(self.n_params, dtype=np.float32)
+        v = np.empty(self.n_params * self.n_flows, dtype=np.float32)
         _check(self._L, self._L.abc_maf_get_params(self._h, v.ctypes.data))
-        return v
+        return v if self.n_flows == 1 else v.reshape(self.n_flows, self.n_params)
+
+    def train_flows(self, thetas, weights=None, n_steps=500, batch=1024, lr=1e-3, seed=0, cuda_stream=None):
+        """Train every flow on its own data in the same launches: thetas is a
+        list of n_flows CUDA f32 [n_r, 8] tensors (None or empty = leave that
+        flow as it is), weights a matching list or None. Returns the losses."""
+        R = self.n_flows
+        th = (ctypes.c_void_p * R)()
+        wt = (ctypes.c_void_p * R)()
+        nn = (ctypes.c_uint64 * R)()
+        for r in range(R):
+            t = thetas[r]
+            if t is not None and t.shape[0] > 0:
+                th[r] = t.data_ptr()
+                nn[r] = t.shape[0]
+                if weights is not None and weights[r] is not None:
+                    wt[r] = weights[r].data_ptr()
+        loss = (ctypes.c_float * R)()
+        s = cuda_stream if cuda_stream is not None else torch.cuda.Stream()
+        torch.cuda.current_stream().synchronize()
+        _check(self._L, self._L.abc_maf_train_flows(self._h, ctypes.cast(th, ctypes.c_void_p),
+                                                    ctypes.cast(wt, ctypes.c_void_p) if weights is not None else None,
+                                                    ctypes.cast(nn, ctypes.c_void_p), int(n_steps), int(batch),
+                                                    float(lr), int(seed), ctypes.cast(loss, ctypes.c_void_p),
+                                                    _stream(s)))
+        return np.array(loss[:], dtype=np.float64)
 
     def sample(self, n, seed=0, stream=0, first_index=0, base_normals=None, want_logq=True, out=None,
-               cuda_stream=None):
+               cuda_stream=None, flow=0):
         dev = torch.device("cuda", torch.cuda.current_device())
         if out is None:
             theta = torch.empty((n, 8), dtype=torch.float32, device=dev)
@@ -494,15 +615,16 @@ class Flow:
         else:
             theta, logq = out
         u = base_normals.data_ptr() if base_normals is not None else None
-        _check(self._L, self._L.abc_maf_sample(self._h, int(n), u, int(seed), int(stream), int(first_index),
-                                               theta.data_ptr(), logq.data_ptr() if logq is not None else None,
-                                               _stream(cuda_stream)))
+        _check(self._L, self._L.abc_maf_sample_at(self._h, int(flow), int(n), u, int(seed), int(stream),
+                                                  int(first_index), theta.data_ptr(),
+                                                  logq.data_ptr() if logq is not None else None, _stream(cuda_stream)))
         return theta, logq
 
-    def log_q(self, theta, cuda_stream=None):
+    def log_q(self, theta, cuda_stream=None, flow=0):
         n = theta.shape[0]
         out = torch.empty((n,), dtype=torch.float32, device=theta.device)
-        _check(self._L, self._L.abc_maf_log_q(self._h, n, theta.data_ptr(), out.data_ptr(), _stream(cuda_stream)))
+        _check(self._L, self._L.abc_maf_log_q_at(self._h, int(flow), n, theta.data_ptr(), out.data_ptr(),
+                                                 _stream(cuda_stream)))
         return out
 
     def gradient(self, theta, weights=None, cuda_stream=None):
@@ -539,6 +661,10 @@ class Flow:
 
 
 abc_maf_create = Flow
+
+
+def abc_maf_create_multi(n_flows, n_blocks=3, hidden=256, lo=PAPER_LO, hi=PAPER_HI):
+    return Flow(n_blocks, hidden, lo, hi, n_flows=n_flows)
 
 
 def abc_maf_init_random(flow, seed=0, scale=0.3):
@@ -581,6 +707,22 @@ def abc_maf_destroy(flow):
     flow.close()
 
 
+def abc_maf_flow_count(flow):
+    return flow.n_flows
+
+
+def abc_maf_sample_at(flow, r, n, **kw):
+    return flow.sample(n, flow=r, **kw)
+
+
+def abc_maf_log_q_at(flow, r, theta, cuda_stream=None):
+    return flow.log_q(theta, cuda_stream, flow=r)
+
+
+def abc_maf_train_flows(flow, thetas, weights=None, **kw):
+    return flow.train_flows(thetas, weights, **kw)
+
+
 
 def abc_smc_run(observed, N_pop, eps0, rounds=5, sims_per_round=1 << 22, eps_factor=0.7, ess_min=0.1,
                 flow_blocks=3, flow_hidden=256, train_steps=500, train_batch=1024, train_lr=1e-3, seed=0,
@@ -608,6 +750,49 @@ def abc_smc_run(observed, N_pop, eps0, rounds=5, sims_per_round=1 << 22, eps_fac
     m = int(n.value)
     return out, theta[:m], w[:m], dist[:m]
 
+
+
+def abc_smc_run_regions(regions, rounds=16, shrink_rounds=4, sims_per_round=1 << 20, eps_factor=0.7, ess_min=0.1,
+                        flow_blocks=3, flow_hidden=256, train_steps=500, train_steps_warm=100, train_batch=1024,
+                        train_lr=1e-3, seed=0, capacity=1 << 16, mode="fast", defensive=0.1, lo=PAPER_LO, hi=PAPER_HI,
+                        cuda_stream=None):
+    """Sequential ABC with one flow proposal per region, all regions in one
+    batched launch per round. regions: list of dicts with observed (host int32
+    [3, T+1]), N_pop, eps (final) and pool (samples kept at the final eps).
+    Returns (rounds [rounds][n_regions] of dicts, per region a tuple
+    (theta [m, 8], weights [m] f64 unnormalised, dist [m], n_pooled))."""
+    L = load()
+    R = len(regions)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    keep, outs = [], []
+    arr = (AbcSmcRegion * R)()
+    for g, reg in enumerate(regions):
+        obs, obs_p = _host_i32(reg["observed"])
+        keep.append(obs)
+        pool = int(reg.get("pool", 1 << 16))
+        th = torch.empty((max(pool, 1), 8), dtype=torch.float32, device=dev)
+        w = torch.empty((max(pool, 1),), dtype=torch.float64, device=dev)
+        d = torch.empty((max(pool, 1),), dtype=torch.float64, device=dev)
+        outs.append((th, w, d))
+        arr[g] = AbcSmcRegion(ctypes.cast(obs_p, ctypes.c_void_p), obs.shape[1] - 1, int(reg["N_pop"]),
+                              float(reg["eps"]), th.data_ptr(), w.data_ptr(), d.data_ptr(), pool, 0, 0)
+    base = AbcSmcConfig(int(rounds), int(sims_per_round), 0.0, float(eps_factor), float(ess_min), int(flow_blocks),
+                        int(flow_hidden), int(train_steps), int(train_batch), float(train_lr), int(seed),
+                        int(capacity), _mode(mode), float(defensive))
+    cfg = AbcSmcStreamConfig(base, int(shrink_rounds), int(train_steps_warm))
+    rr = (AbcSmcRound * (int(rounds) * R))()
+    s = cuda_stream if cuda_stream is not None else torch.cuda.Stream()
+    torch.cuda.current_stream().synchronize()
+    b = prior_box(lo, hi)
+    _check(L, L.abc_smc_run_regions(ctypes.byref(b), arr, R, ctypes.byref(cfg), rr, _stream(s)))
+    info = [[dict((f, getattr(rr[r * R + g], f)) for f, _ in AbcSmcRound._fields_) for g in range(R)]
+            for r in range(int(rounds))]
+    res = []
+    for g in range(R):
+        m = int(arr[g].n_out)
+        th, w, d = outs[g]
+        res.append((th[:m], w[:m], d[:m], int(arr[g].n_pooled)))
+    return info, res
 
 
 def abc_project(theta, sample_index, init_ard, T, N_pop, seed, quantiles=(0.05, 0.5, 0.95), stream=0, mode="fast",

@@ -218,6 +218,15 @@ abc_status sample_scratch(size_t bytes, SampleScratch** out)
 
 }  // namespace
 
+// A region's observed series on the device (abc_observed_create).
+struct abc_observed_s {
+    int device = 0;
+    int32_t T = 0;
+    int64_t N_pop = 0;
+    int32_t ard0[3] = {0, 0, 0};
+    void* dev = nullptr;   // int4 [T+1] (A, R, D, 0)
+};
+
 // Scratch of abc_sample_noalloc: bytes [0, 24) hold the three counters
 // (accepts, claimed indices, simulated days), bytes [256, 256 + 16 (T+1)) the
 // observed series. Host code must not pass this name to a kernel (on the host
@@ -341,6 +350,83 @@ abc_status abc_sample(const abc_prior_box* prior, const int32_t* observed, int32
     *n_accepted = count;
     if (count > capacity)
         return fail(ABC_ERR_CAPACITY, "%llu samples accepted, capacity %llu", count, (unsigned long long)capacity);
+    return ok();
+}
+
+abc_status abc_observed_create(const int32_t* observed, int32_t T, int64_t N_pop, abc_observed* out)
+{
+    abc_status st;
+    if (!out) return fail(ABC_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if ((st = check_model(T, N_pop, 0)) != ABC_OK) return st;
+    std::vector<int4> obs;
+    if ((st = pack_observed(observed, T, N_pop, obs)) != ABC_OK) return st;
+    abc_observed_s* o = new abc_observed_s();
+    o->T = T;
+    o->N_pop = N_pop;
+    o->ard0[0] = obs[0].x;
+    o->ard0[1] = obs[0].y;
+    o->ard0[2] = obs[0].z;
+    cudaError_t e = cudaGetDevice(&o->device);
+    if (e == cudaSuccess) e = cudaMalloc(&o->dev, sizeof(int4) * obs.size());
+    if (e == cudaSuccess) e = cudaMemcpy(o->dev, obs.data(), sizeof(int4) * obs.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        if (o->dev) cudaFree(o->dev);
+        delete o;
+        return cuda_fail(e, "observed series upload");
+    }
+    *out = o;
+    return ok();
+}
+
+abc_status abc_observed_destroy(abc_observed obs)
+{
+    if (!obs) return fail(ABC_ERR_INVALID_ARG, "observed handle is NULL");
+    cudaError_t e = cudaDeviceSynchronize();
+    cudaFree(obs->dev);
+    delete obs;
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
+    return ok();
+}
+
+abc_status abc_sample_async(const abc_prior_box* prior, abc_observed obs, double eps, uint64_t n_samples,
+                            uint64_t seed, uint32_t stream, abc_mode mode, uint64_t first_index, float* theta_out,
+                            double* dist_out, uint64_t* idx_out, uint64_t capacity, uint64_t* counters_dev,
+                            void* cuda_stream)
+{
+    abc_status st;
+    if ((st = check_prior(prior)) != ABC_OK) return st;
+    if (!obs) return fail(ABC_ERR_INVALID_ARG, "observed handle is NULL");
+    if ((st = check_model(obs->T, obs->N_pop, stream)) != ABC_OK) return st;
+    if (mode != ABC_EXACT && mode != ABC_FAST) return fail(ABC_ERR_INVALID_ARG, "unknown mode %d", (int)mode);
+    if (!(eps >= 0.0)) return fail(ABC_ERR_INVALID_ARG, "eps must be >= 0 and not NaN");
+    if (!counters_dev) return fail(ABC_ERR_INVALID_ARG, "counters_dev is NULL");
+    if (capacity > 0 && (!theta_out || !dist_out || !idx_out))
+        return fail(ABC_ERR_INVALID_ARG, "output buffers are NULL");
+    if (n_samples > ~(uint64_t)0 - first_index)
+        return fail(ABC_ERR_INVALID_ARG, "first_index + n_samples overflows");
+    int dev = -1;
+    CUDA_TRY(cudaGetDevice(&dev), "cudaGetDevice");
+    if (dev != obs->device) return fail(ABC_ERR_INVALID_ARG, "the observed handle belongs to another device");
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    CUDA_TRY(cudaMemsetAsync(counters_dev, 0, 3 * sizeof(uint64_t), s), "cudaMemsetAsync(counters)");
+    if (n_samples == 0) return ok();
+    const abcgb::ModelParams p = make_params(prior, obs->T, obs->N_pop, seed, stream, obs->ard0);
+    abcgb::RejectArgs a;
+    a.obs = (const int4*)obs->dev;
+    a.first_index = first_index;
+    a.n_samples = n_samples;
+    a.acc_max = acc_threshold(eps);
+    unsigned long long* c = reinterpret_cast<unsigned long long*>(counters_dev);
+    a.count = c;
+    a.next = c + 1;
+    a.sim_days = c + 2;
+    a.capacity = capacity;
+    a.theta_out = theta_out;
+    a.dist_out = dist_out;
+    a.idx_out = idx_out;
+    if (injected("launch")) return fail(ABC_ERR_CUDA, "kernel launch failed (injected)");
+    CUDA_TRY(abcgb::launch_reject(p, a, mode == ABC_FAST, s, nullptr), "abc_reject_kernel launch");
     return ok();
 }
 

@@ -214,6 +214,8 @@ __global__ void publish_kernel(const float* __restrict__ master, uint32_t* __res
 {
     const Layout L = layout(H);
     const int per = L.words, mb = master_block(H), hw = H / 2 + 4;
+    master += (size_t)blockIdx.y * K * mb;   // flow blockIdx.y
+    pub += (size_t)blockIdx.y * K * per;
     for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < K * per; idx += gridDim.x * blockDim.x) {
         const int b = idx / per, w = idx % per;
         const float* M = master + (size_t)b * mb;
@@ -419,16 +421,34 @@ __device__ __forceinline__ void put_bf16(uint32_t* base, int row, int col, float
     reinterpret_cast<__nv_bfloat16*>(base)[row * 2 * kStage + col] = __float2bfloat16_rn(v);
 }
 
+// Training data of one flow: points theta [n][8], weights [n] (NULL = 1).
+struct TrainSlot {
+    const float* theta;
+    const float* w;
+    uint64_t n;
+};
+
+// Flow f = blockIdx.y reads slots[f]: with rows, the batch of rows
+// rows[f * batch ..] (none if the flow has no points), else all its n points.
 template <int K>
 __global__ void __launch_bounds__(kGradWarps * 32) grad_kernel(const uint32_t* __restrict__ pub, int H, Box box,
-                                                               const float* __restrict__ theta,
-                                                               const float* __restrict__ weights,
-                                                               const uint32_t* __restrict__ rows, uint64_t n_rows,
+                                                               const TrainSlot* __restrict__ slots,
+                                                               const uint32_t* __restrict__ rows_all, uint32_t batch,
                                                                float* __restrict__ grad, float* __restrict__ sums)
 {
     extern __shared__ __align__(16) uint32_t sm[];
     const Layout L = layout(H);
     const int mb = master_block(H);
+    const int f = blockIdx.y;
+    const TrainSlot slot = slots[f];
+    const uint64_t n_rows = rows_all ? (slot.n ? batch : 0) : slot.n;
+    if (n_rows == 0) return;   // uniform over the block
+    const float* __restrict__ theta = slot.theta;
+    const float* __restrict__ weights = slot.w;
+    const uint32_t* __restrict__ rows = rows_all ? rows_all + (size_t)f * batch : nullptr;
+    pub += (size_t)f * K * L.words;
+    grad += (size_t)f * K * mb;
+    sums += 2 * f;
     uint32_t* wsm = sm;
     float* gsm = reinterpret_cast<float*>(sm + K * L.words);
     WarpStage* stages = reinterpret_cast<WarpStage*>(gsm + K * mb);
@@ -641,25 +661,29 @@ __global__ void __launch_bounds__(kGradWarps * 32) grad_kernel(const uint32_t* _
 }
 
 // batch rows for one training step: uniform indices with replacement
-__global__ void batch_rows_kernel(const __grid_constant__ ModelParams p, const int* __restrict__ step, uint64_t n,
-                                  uint32_t batch, uint32_t* __restrict__ rows)
+__global__ void batch_rows_kernel(const __grid_constant__ ModelParams p, const int* __restrict__ step,
+                                  const TrainSlot* __restrict__ slots, uint32_t batch, uint32_t* __restrict__ rows)
 {
     const uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= batch) return;
-    const uint4 w = philox10(make_uint4(b, (uint32_t)*step, 0xB47C4u, 0x5EEDu), p);
+    const uint32_t f = blockIdx.y;
+    const uint64_t n = slots[f].n;
+    if (b >= batch || n == 0) return;
+    const uint4 w = philox10(make_uint4(b, (uint32_t)*step, 0xB47C4u, 0x5EEDu + (f << 16)), p);
     const uint64_t r = (((uint64_t)w.y << 32) | w.x) % n;
-    rows[b] = (uint32_t)r;
+    rows[(size_t)f * batch + b] = (uint32_t)r;
 }
 
 __global__ void tick_kernel(int* step) { *step += 1; }
 
+// n_params per flow; flows one after another. A flow whose weight sum is 0
+// (no points this step) keeps its parameters and moments.
 __global__ void adam_kernel(float* __restrict__ params, const float* __restrict__ grad, float* __restrict__ m,
-                            float* __restrict__ v, const float* __restrict__ sums, const int* __restrict__ step, int n,
-                            float lr, float b1, float b2, float eps)
+                            float* __restrict__ v, const float* __restrict__ sums, const int* __restrict__ step,
+                            int64_t n_params, int64_t n, float lr, float b1, float b2, float eps)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const float W = sums[1];
+    const float W = sums[2 * (i / n_params) + 1];
     if (!(W > 0.f)) return;
     const int t = *step;
     const float gr = grad[i] / W;
@@ -679,24 +703,24 @@ using namespace abcgb;
 
 struct abc_maf_s {
     int device = 0;
+    int R = 1;                 // flows, all with K blocks of H hidden units
     int K = 0, H = 0;
     maf::Box box{};
-    int64_t n_params = 0;
-    int pub_words = 0;
-    float* d_params = nullptr;
+    int64_t n_params = 0;      // per flow
+    int pub_words = 0;         // per block
+    float* d_params = nullptr; // [R][n_params] FP32 master parameters
     float* d_m = nullptr;
     float* d_v = nullptr;
     float* d_grad = nullptr;
-    uint32_t* d_pub = nullptr;
-    float* d_sums = nullptr;
+    uint32_t* d_pub = nullptr; // [R][K][pub_words] published BF16 operands
+    float* d_sums = nullptr;   // [R][2] (weighted loss sum, weight sum)
     int* d_step = nullptr;
     uint32_t* d_rows = nullptr;
-    uint32_t rows_cap = 0;
+    uint32_t rows_cap = 0;     // batch rows per flow
+    maf::TrainSlot* d_slots = nullptr;   // [R] training data of each flow
+    maf::TrainSlot* h_slots = nullptr;   // pinned host mirror
     cudaGraphExec_t graph = nullptr;
     // what the captured training step was built for
-    uint64_t g_n = 0;
-    const float* g_theta = nullptr;
-    const float* g_w = nullptr;
     int32_t g_batch = 0;
     float g_lr = 0.f;
     uint64_t g_seed = 0;
@@ -728,6 +752,14 @@ abc_status check(abc_maf f)
     return ABC_OK;
 }
 
+abc_status check_flow(abc_maf f, int32_t r)
+{
+    abc_status st;
+    if ((st = check(f)) != ABC_OK) return st;
+    if (r < 0 || r >= f->R) return plan_fail(ABC_ERR_INVALID_ARG, "flow index out of range");
+    return ABC_OK;
+}
+
 int sm_count()
 {
     int dev = 0, sms = 0;
@@ -754,50 +786,53 @@ cudaError_t allow_smem(Kern k, size_t bytes)
     return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+const uint32_t* flow_pub(abc_maf f, int r) { return f->d_pub + (size_t)r * f->K * f->pub_words; }
+
 cudaError_t publish(abc_maf f, cudaStream_t s)
 {
     const int n = f->K * f->pub_words;
-    maf::publish_kernel<<<(n + 255) / 256, 256, 0, s>>>(f->d_params, f->d_pub, f->K, f->H);
+    maf::publish_kernel<<<dim3((n + 255) / 256, f->R), 256, 0, s>>>(f->d_params, f->d_pub, f->K, f->H);
     return cudaGetLastError();
 }
 
 template <int K>
-cudaError_t launch_logq(abc_maf f, uint64_t n, const float* theta, float* logq, cudaStream_t s)
+cudaError_t launch_logq(abc_maf f, int r, uint64_t n, const float* theta, float* logq, cudaStream_t s)
 {
     const size_t smem = fwd_smem(f);
     cudaError_t e = allow_smem(maf::logq_kernel<K>, smem);
     if (e != cudaSuccess) return e;
     const uint64_t tiles = (n + 15) / 16;
     const int grid = fill_grid(maf::logq_kernel<K>, 128, smem, (tiles + 3) / 4);
-    maf::logq_kernel<K><<<grid, 128, smem, s>>>(f->d_pub, f->H, f->box, theta, n, logq);
+    maf::logq_kernel<K><<<grid, 128, smem, s>>>(flow_pub(f, r), f->H, f->box, theta, n, logq);
     return cudaGetLastError();
 }
 
 template <int K>
-cudaError_t launch_sample(abc_maf f, uint64_t n, const float* u, const ModelParams& p, uint32_t ctr3, uint64_t first,
-                          float* theta, float* logq, cudaStream_t s)
+cudaError_t launch_sample(abc_maf f, int r, uint64_t n, const float* u, const ModelParams& p, uint32_t ctr3,
+                          uint64_t first, float* theta, float* logq, cudaStream_t s)
 {
     const size_t smem = fwd_smem(f);
     cudaError_t e = allow_smem(maf::sample_kernel<K>, smem);
     if (e != cudaSuccess) return e;
     const uint64_t tiles = (n + 15) / 16;
     const int grid = fill_grid(maf::sample_kernel<K>, 128, smem, (tiles + 3) / 4);
-    maf::sample_kernel<K><<<grid, 128, smem, s>>>(f->d_pub, f->H, f->box, u, p, ctr3, first, n, theta, logq);
+    maf::sample_kernel<K><<<grid, 128, smem, s>>>(flow_pub(f, r), f->H, f->box, u, p, ctr3, first, n, theta, logq);
     return cudaGetLastError();
 }
 
+// gradients of every flow's slot: with rows, `batch` rows per flow; else all
+// max_n points (the largest slot)
 template <int K>
-cudaError_t launch_grad(abc_maf f, uint64_t n_rows, const float* theta, const float* w, const uint32_t* rows,
-                        cudaStream_t s)
+cudaError_t launch_grad(abc_maf f, const uint32_t* rows, uint32_t batch, uint64_t max_n, cudaStream_t s)
 {
     const size_t smem = grad_smem(f);
     cudaError_t e = allow_smem(maf::grad_kernel<K>, smem);
     if (e != cudaSuccess) return e;
-    const uint64_t tiles = (n_rows + 15) / 16;
+    const uint64_t tiles = ((rows ? batch : max_n) + 15) / 16;
     const uint64_t want = (tiles + maf::kGradWarps - 1) / maf::kGradWarps;
     const int grid = (int)(want < (uint64_t)sm_count() ? (want > 0 ? want : 1) : (uint64_t)sm_count());
-    maf::grad_kernel<K><<<grid, maf::kGradWarps * 32, smem, s>>>(f->d_pub, f->H, f->box, theta, w, rows, n_rows,
-                                                                 f->d_grad, f->d_sums);
+    maf::grad_kernel<K><<<dim3(grid, f->R), maf::kGradWarps * 32, smem, s>>>(f->d_pub, f->H, f->box, f->d_slots, rows,
+                                                                             batch, f->d_grad, f->d_sums);
     return cudaGetLastError();
 }
 
@@ -807,30 +842,54 @@ cudaError_t launch_grad(abc_maf f, uint64_t n_rows, const float* theta, const fl
      : f->K == 3 ? fn<3>(__VA_ARGS__)              \
                  : fn<4>(__VA_ARGS__))
 
-cudaError_t full_gradient(abc_maf f, uint64_t n, const float* theta, const float* w, cudaStream_t s)
+// the slot table: theta[r], w[r], n[r] for every flow (n[r] = 0: no data)
+cudaError_t upload_slots(abc_maf f, const float* const* theta, const float* const* w, const uint64_t* n,
+                         cudaStream_t s)
 {
-    cudaError_t e = cudaMemsetAsync(f->d_grad, 0, sizeof(float) * f->n_params, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(f->d_sums, 0, 2 * sizeof(float), s);
-    if (e == cudaSuccess) e = MAF_DISPATCH(launch_grad, f, n, theta, w, nullptr, s);
+    for (int r = 0; r < f->R; ++r) {
+        f->h_slots[r].theta = n[r] ? theta[r] : nullptr;
+        f->h_slots[r].w = n[r] && w ? w[r] : nullptr;
+        f->h_slots[r].n = n[r];
+    }
+    return cudaMemcpyAsync(f->d_slots, f->h_slots, sizeof(maf::TrainSlot) * f->R, cudaMemcpyHostToDevice, s);
+}
+
+// full-data gradients of the flows described by the slot table
+cudaError_t full_gradient(abc_maf f, uint64_t max_n, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(f->d_grad, 0, sizeof(float) * f->n_params * f->R, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(f->d_sums, 0, 2 * sizeof(float) * f->R, s);
+    if (e == cudaSuccess) e = MAF_DISPATCH(launch_grad, f, nullptr, 0u, max_n, s);
     return e;
+}
+
+cudaError_t launch_adam(abc_maf f, float lr, float b1, float b2, float eps, cudaStream_t s)
+{
+    const int64_t n = f->n_params * f->R;
+    maf::adam_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(f->d_params, f->d_grad, f->d_m, f->d_v, f->d_sums,
+                                                                 f->d_step, f->n_params, n, lr, b1, b2, eps);
+    return cudaGetLastError();
 }
 
 }  // namespace
 
 extern "C" {
 
-abc_status abc_maf_create(int32_t n_blocks, int32_t hidden, const abc_prior_box* box, abc_maf* maf_out)
+abc_status abc_maf_create_multi(int32_t n_flows, int32_t n_blocks, int32_t hidden, const abc_prior_box* box,
+                                abc_maf* maf_out)
 {
     abc_status st;
     if (!maf_out) return plan_fail(ABC_ERR_INVALID_ARG, "maf_out is NULL");
     *maf_out = nullptr;
     if (!plan_check_prior(box, &st)) return st;
+    if (n_flows < 1 || n_flows > ABC_MAF_MAX_FLOWS) return plan_fail(ABC_ERR_INVALID_ARG, "n_flows must be in 1..64");
     if (n_blocks < 1 || n_blocks > maf::kKMax) return plan_fail(ABC_ERR_INVALID_ARG, "n_blocks must be in 1..4");
     if (hidden < 16 || hidden > maf::kHMax || hidden % 16)
         return plan_fail(ABC_ERR_INVALID_ARG, "hidden must be a multiple of 16 in 16..256");
     for (int j = 0; j < 8; ++j)
         if (!(box->hi[j] > box->lo[j])) return plan_fail(ABC_ERR_INVALID_ARG, "the flow needs lo < hi in every coordinate");
     abc_maf_s* f = new abc_maf_s();
+    f->R = n_flows;
     f->K = n_blocks;
     f->H = hidden;
     for (int j = 0; j < 8; ++j) {
@@ -844,38 +903,45 @@ abc_status abc_maf_create(int32_t n_blocks, int32_t hidden, const abc_prior_box*
         abc_maf_destroy(f);
         return e;
     };
+    const size_t np = sizeof(float) * f->n_params * f->R;
     cudaError_t e;
-    if ((e = cudaGetDevice(&f->device)) != cudaSuccess ||
-        (e = cudaMalloc(&f->d_params, sizeof(float) * f->n_params)) != cudaSuccess ||
-        (e = cudaMalloc(&f->d_m, sizeof(float) * f->n_params)) != cudaSuccess ||
-        (e = cudaMalloc(&f->d_v, sizeof(float) * f->n_params)) != cudaSuccess ||
-        (e = cudaMalloc(&f->d_grad, sizeof(float) * f->n_params)) != cudaSuccess ||
-        (e = cudaMalloc(&f->d_pub, sizeof(uint32_t) * (size_t)f->K * f->pub_words)) != cudaSuccess ||
-        (e = cudaMalloc(&f->d_sums, 2 * sizeof(float))) != cudaSuccess ||
-        (e = cudaMalloc(&f->d_step, sizeof(int))) != cudaSuccess)
+    if ((e = cudaGetDevice(&f->device)) != cudaSuccess || (e = cudaMalloc(&f->d_params, np)) != cudaSuccess ||
+        (e = cudaMalloc(&f->d_m, np)) != cudaSuccess || (e = cudaMalloc(&f->d_v, np)) != cudaSuccess ||
+        (e = cudaMalloc(&f->d_grad, np)) != cudaSuccess ||
+        (e = cudaMalloc(&f->d_pub, sizeof(uint32_t) * (size_t)f->R * f->K * f->pub_words)) != cudaSuccess ||
+        (e = cudaMalloc(&f->d_sums, 2 * sizeof(float) * f->R)) != cudaSuccess ||
+        (e = cudaMalloc(&f->d_step, sizeof(int))) != cudaSuccess ||
+        (e = cudaMalloc(&f->d_slots, sizeof(maf::TrainSlot) * f->R)) != cudaSuccess ||
+        (e = cudaMallocHost(&f->h_slots, sizeof(maf::TrainSlot) * f->R)) != cudaSuccess)
         return fail_free(plan_cuda_fail(e, "cudaMalloc(flow)"));
-    if ((e = cudaMemset(f->d_params, 0, sizeof(float) * f->n_params)) != cudaSuccess ||
-        (e = cudaMemset(f->d_m, 0, sizeof(float) * f->n_params)) != cudaSuccess ||
-        (e = cudaMemset(f->d_v, 0, sizeof(float) * f->n_params)) != cudaSuccess ||
-        (e = cudaMemset(f->d_step, 0, sizeof(int))) != cudaSuccess || (e = publish(f, nullptr)) != cudaSuccess ||
-        (e = cudaDeviceSynchronize()) != cudaSuccess)
+    if ((e = cudaMemset(f->d_params, 0, np)) != cudaSuccess || (e = cudaMemset(f->d_m, 0, np)) != cudaSuccess ||
+        (e = cudaMemset(f->d_v, 0, np)) != cudaSuccess || (e = cudaMemset(f->d_step, 0, sizeof(int))) != cudaSuccess ||
+        (e = cudaMemset(f->d_slots, 0, sizeof(maf::TrainSlot) * f->R)) != cudaSuccess ||
+        (e = publish(f, nullptr)) != cudaSuccess || (e = cudaDeviceSynchronize()) != cudaSuccess)
         return fail_free(plan_cuda_fail(e, "flow initialisation"));
     *maf_out = f;
     return plan_ok();
 }
 
+abc_status abc_maf_create(int32_t n_blocks, int32_t hidden, const abc_prior_box* box, abc_maf* maf_out)
+{
+    return abc_maf_create_multi(1, n_blocks, hidden, box, maf_out);
+}
+
 int64_t abc_maf_param_count(abc_maf f) { return f ? f->n_params : -1; }
+
+int32_t abc_maf_flow_count(abc_maf f) { return f ? f->R : -1; }
 
 abc_status abc_maf_init_random(abc_maf f, uint64_t seed, float scale)
 {
     abc_status st;
     if ((st = check(f)) != ABC_OK) return st;
     if (!(scale >= 0.f)) return plan_fail(ABC_ERR_INVALID_ARG, "scale must be >= 0");
-    std::vector<float> v((size_t)f->n_params, 0.f);
+    std::vector<float> v((size_t)f->n_params * f->R, 0.f);
     std::mt19937_64 gen(seed);
     std::normal_distribution<float> nd(0.f, 1.f);
     const int H = f->H, mb = maf::master_block(H);
-    for (int b = 0; b < f->K; ++b) {
+    for (int b = 0; b < f->K * f->R; ++b) {
         float* M = v.data() + (size_t)b * mb;
         for (int i = 0; i < 8 * H; ++i) M[i] = nd(gen) * scale / sqrtf(8.f);
         for (int i = 0; i < 16 * H; ++i) M[9 * H + i] = nd(gen) * scale / sqrtf((float)H);
@@ -888,9 +954,10 @@ abc_status abc_maf_set_params(abc_maf f, const float* params)
     abc_status st;
     if ((st = check(f)) != ABC_OK) return st;
     if (!params) return plan_fail(ABC_ERR_INVALID_ARG, "params is NULL");
-    MAF_TRY(cudaMemcpy(f->d_params, params, sizeof(float) * f->n_params, cudaMemcpyHostToDevice), "cudaMemcpy(params)");
-    MAF_TRY(cudaMemset(f->d_m, 0, sizeof(float) * f->n_params), "cudaMemset");
-    MAF_TRY(cudaMemset(f->d_v, 0, sizeof(float) * f->n_params), "cudaMemset");
+    const size_t np = sizeof(float) * f->n_params * f->R;
+    MAF_TRY(cudaMemcpy(f->d_params, params, np, cudaMemcpyHostToDevice), "cudaMemcpy(params)");
+    MAF_TRY(cudaMemset(f->d_m, 0, np), "cudaMemset");
+    MAF_TRY(cudaMemset(f->d_v, 0, np), "cudaMemset");
     MAF_TRY(cudaMemset(f->d_step, 0, sizeof(int)), "cudaMemset");
     MAF_TRY(publish(f, nullptr), "publish");
     MAF_TRY(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
@@ -903,33 +970,47 @@ abc_status abc_maf_get_params(abc_maf f, float* params)
     if ((st = check(f)) != ABC_OK) return st;
     if (!params) return plan_fail(ABC_ERR_INVALID_ARG, "params is NULL");
     MAF_TRY(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
-    MAF_TRY(cudaMemcpy(params, f->d_params, sizeof(float) * f->n_params, cudaMemcpyDeviceToHost), "cudaMemcpy(params)");
+    MAF_TRY(cudaMemcpy(params, f->d_params, sizeof(float) * f->n_params * f->R, cudaMemcpyDeviceToHost),
+            "cudaMemcpy(params)");
+    return plan_ok();
+}
+
+abc_status abc_maf_sample_at(abc_maf f, int32_t flow, uint64_t n, const float* base_normals, uint64_t seed,
+                             uint32_t stream, uint64_t first_index, float* theta_out, float* logq_out,
+                             void* cuda_stream)
+{
+    abc_status st;
+    if ((st = check_flow(f, flow)) != ABC_OK) return st;
+    if (n && !theta_out) return plan_fail(ABC_ERR_INVALID_ARG, "theta_out is NULL");
+    if (stream > ABC_STREAM_MAX) return plan_fail(ABC_ERR_INVALID_ARG, "stream above 2^30 - 1");
+    if (n == 0) return plan_ok();
+    const ModelParams p = plan_make_params(nullptr, 1, 1, seed, stream, nullptr);
+    MAF_TRY(MAF_DISPATCH(launch_sample, f, flow, n, base_normals, p, stream << 2, first_index, theta_out, logq_out,
+                         (cudaStream_t)cuda_stream),
+            "flow sample launch");
     return plan_ok();
 }
 
 abc_status abc_maf_sample(abc_maf f, uint64_t n, const float* base_normals, uint64_t seed, uint32_t stream,
                           uint64_t first_index, float* theta_out, float* logq_out, void* cuda_stream)
 {
+    return abc_maf_sample_at(f, 0, n, base_normals, seed, stream, first_index, theta_out, logq_out, cuda_stream);
+}
+
+abc_status abc_maf_log_q_at(abc_maf f, int32_t flow, uint64_t n, const float* theta, float* logq_out,
+                            void* cuda_stream)
+{
     abc_status st;
-    if ((st = check(f)) != ABC_OK) return st;
-    if (n && !theta_out) return plan_fail(ABC_ERR_INVALID_ARG, "theta_out is NULL");
-    if (stream > ABC_STREAM_MAX) return plan_fail(ABC_ERR_INVALID_ARG, "stream above 2^30 - 1");
+    if ((st = check_flow(f, flow)) != ABC_OK) return st;
+    if (n && (!theta || !logq_out)) return plan_fail(ABC_ERR_INVALID_ARG, "NULL device buffer");
     if (n == 0) return plan_ok();
-    const ModelParams p = plan_make_params(nullptr, 1, 1, seed, stream, nullptr);
-    MAF_TRY(MAF_DISPATCH(launch_sample, f, n, base_normals, p, stream << 2, first_index, theta_out, logq_out,
-                         (cudaStream_t)cuda_stream),
-            "flow sample launch");
+    MAF_TRY(MAF_DISPATCH(launch_logq, f, flow, n, theta, logq_out, (cudaStream_t)cuda_stream), "flow log_q launch");
     return plan_ok();
 }
 
 abc_status abc_maf_log_q(abc_maf f, uint64_t n, const float* theta, float* logq_out, void* cuda_stream)
 {
-    abc_status st;
-    if ((st = check(f)) != ABC_OK) return st;
-    if (n && (!theta || !logq_out)) return plan_fail(ABC_ERR_INVALID_ARG, "NULL device buffer");
-    if (n == 0) return plan_ok();
-    MAF_TRY(MAF_DISPATCH(launch_logq, f, n, theta, logq_out, (cudaStream_t)cuda_stream), "flow log_q launch");
-    return plan_ok();
+    return abc_maf_log_q_at(f, 0, n, theta, logq_out, cuda_stream);
 }
 
 abc_status abc_maf_gradient(abc_maf f, uint64_t n, const float* theta, const float* weights, float* loss_out,
@@ -939,7 +1020,14 @@ abc_status abc_maf_gradient(abc_maf f, uint64_t n, const float* theta, const flo
     if ((st = check(f)) != ABC_OK) return st;
     if (n == 0 || !theta) return plan_fail(ABC_ERR_INVALID_ARG, "need n > 0 points");
     cudaStream_t s = (cudaStream_t)cuda_stream;
-    MAF_TRY(full_gradient(f, n, theta, weights, s), "flow gradient");
+    // flow 0 only: the other flows get no points
+    std::vector<const float*> th((size_t)f->R, nullptr), w((size_t)f->R, nullptr);
+    std::vector<uint64_t> nn((size_t)f->R, 0);
+    th[0] = theta;
+    w[0] = weights;
+    nn[0] = n;
+    MAF_TRY(upload_slots(f, th.data(), w.data(), nn.data(), s), "cudaMemcpyAsync(slots)");
+    MAF_TRY(full_gradient(f, n, s), "flow gradient");
     float sums[2] = {0.f, 0.f};
     MAF_TRY(cudaMemcpyAsync(sums, f->d_sums, sizeof sums, cudaMemcpyDeviceToHost, s), "cudaMemcpyAsync(sums)");
     MAF_TRY(cudaStreamSynchronize(s), "cudaStreamSynchronize");
@@ -959,40 +1047,49 @@ abc_status abc_maf_adam_step(abc_maf f, float lr, float beta1, float beta2, floa
     if ((st = check(f)) != ABC_OK) return st;
     cudaStream_t s = (cudaStream_t)cuda_stream;
     maf::tick_kernel<<<1, 1, 0, s>>>(f->d_step);
-    maf::adam_kernel<<<(int)((f->n_params + 255) / 256), 256, 0, s>>>(f->d_params, f->d_grad, f->d_m, f->d_v, f->d_sums,
-                                                                      f->d_step, (int)f->n_params, lr, beta1, beta2, eps);
-    MAF_TRY(cudaGetLastError(), "adam launch");
+    MAF_TRY(launch_adam(f, lr, beta1, beta2, eps, s), "adam launch");
     MAF_TRY(publish(f, s), "publish");
     return plan_ok();
 }
 
-abc_status abc_maf_train(abc_maf f, uint64_t n, const float* theta, const float* weights, int32_t n_steps,
-                         int32_t batch, float lr, uint64_t seed, float* loss_out, void* cuda_stream)
+abc_status abc_maf_train_flows(abc_maf f, const float* const* theta, const float* const* weights, const uint64_t* n,
+                               int32_t n_steps, int32_t batch, float lr, uint64_t seed, float* loss_out,
+                               void* cuda_stream)
 {
     abc_status st;
     if ((st = check(f)) != ABC_OK) return st;
-    if (n == 0 || !theta || n_steps < 0 || batch < 16)
-        return plan_fail(ABC_ERR_INVALID_ARG, "need n > 0 points, n_steps >= 0 and batch >= 16");
+    if (!theta || !n || n_steps < 0 || batch < 16)
+        return plan_fail(ABC_ERR_INVALID_ARG, "need theta and n tables, n_steps >= 0 and batch >= 16");
+    uint64_t max_n = 0;
+    for (int r = 0; r < f->R; ++r) {
+        if (n[r] && !theta[r]) return plan_fail(ABC_ERR_INVALID_ARG, "a flow with points has theta NULL");
+        if (n[r] > 0xFFFFFFFFull) return plan_fail(ABC_ERR_INVALID_ARG, "more than 2^32 - 1 points for one flow");
+        max_n = n[r] > max_n ? n[r] : max_n;
+    }
+    if (max_n == 0) return plan_fail(ABC_ERR_INVALID_ARG, "no flow has points");
     cudaStream_t s = (cudaStream_t)cuda_stream;
     if (!s && n_steps > 0) return plan_fail(ABC_ERR_INVALID_ARG, "training needs a non-default stream");
     if ((uint32_t)batch > f->rows_cap) {
         cudaFree(f->d_rows);
         f->d_rows = nullptr;
         f->rows_cap = 0;
-        MAF_TRY(cudaMalloc(&f->d_rows, sizeof(uint32_t) * (size_t)batch), "cudaMalloc(rows)");
+        MAF_TRY(cudaMalloc(&f->d_rows, sizeof(uint32_t) * (size_t)batch * f->R), "cudaMalloc(rows)");
         f->rows_cap = (uint32_t)batch;
         if (f->graph) {
             cudaGraphExecDestroy(f->graph);
             f->graph = nullptr;
         }
     }
+    MAF_TRY(upload_slots(f, theta, weights, n, s), "cudaMemcpyAsync(slots)");
     // fresh Adam moments for this training run
-    MAF_TRY(cudaMemsetAsync(f->d_m, 0, sizeof(float) * f->n_params, s), "cudaMemsetAsync");
-    MAF_TRY(cudaMemsetAsync(f->d_v, 0, sizeof(float) * f->n_params, s), "cudaMemsetAsync");
+    const size_t np = sizeof(float) * f->n_params * f->R;
+    MAF_TRY(cudaMemsetAsync(f->d_m, 0, np, s), "cudaMemsetAsync");
+    MAF_TRY(cudaMemsetAsync(f->d_v, 0, np, s), "cudaMemsetAsync");
     MAF_TRY(cudaMemsetAsync(f->d_step, 0, sizeof(int), s), "cudaMemsetAsync");
     if (n_steps > 0) {
-        const bool same = f->graph && f->g_n == n && f->g_theta == theta && f->g_w == weights && f->g_batch == batch &&
-                          f->g_lr == lr && f->g_seed == seed && f->g_stream == s;
+        // the step reads its data through the slot table, so a graph captured
+        // for (batch, lr, seed, stream) serves every data set
+        const bool same = f->graph && f->g_batch == batch && f->g_lr == lr && f->g_seed == seed && f->g_stream == s;
         if (!same) {
             if (f->graph) {
                 cudaGraphExecDestroy(f->graph);
@@ -1001,13 +1098,13 @@ abc_status abc_maf_train(abc_maf f, uint64_t n, const float* theta, const float*
             const ModelParams p = plan_make_params(nullptr, 1, 1, seed, 0, nullptr);
             cudaGraph_t gph = nullptr;
             MAF_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
-            maf::batch_rows_kernel<<<(batch + 127) / 128, 128, 0, s>>>(p, f->d_step, n, (uint32_t)batch, f->d_rows);
-            cudaMemsetAsync(f->d_grad, 0, sizeof(float) * f->n_params, s);
-            cudaMemsetAsync(f->d_sums, 0, 2 * sizeof(float), s);
-            cudaError_t e = MAF_DISPATCH(launch_grad, f, (uint64_t)batch, theta, weights, f->d_rows, s);
+            maf::batch_rows_kernel<<<dim3((batch + 127) / 128, f->R), 128, 0, s>>>(p, f->d_step, f->d_slots,
+                                                                                 (uint32_t)batch, f->d_rows);
+            cudaMemsetAsync(f->d_grad, 0, np, s);
+            cudaMemsetAsync(f->d_sums, 0, 2 * sizeof(float) * f->R, s);
+            cudaError_t e = MAF_DISPATCH(launch_grad, f, f->d_rows, (uint32_t)batch, 0, s);
             maf::tick_kernel<<<1, 1, 0, s>>>(f->d_step);
-            maf::adam_kernel<<<(int)((f->n_params + 255) / 256), 256, 0, s>>>(
-                f->d_params, f->d_grad, f->d_m, f->d_v, f->d_sums, f->d_step, (int)f->n_params, lr, 0.9f, 0.999f, 1e-8f);
+            if (e == cudaSuccess) e = launch_adam(f, lr, 0.9f, 0.999f, 1e-8f, s);
             if (e == cudaSuccess) e = publish(f, s);
             cudaError_t ec = cudaStreamEndCapture(s, &gph);
             if (e != cudaSuccess || ec != cudaSuccess) {
@@ -1020,9 +1117,6 @@ abc_status abc_maf_train(abc_maf f, uint64_t n, const float* theta, const float*
                 f->graph = nullptr;
                 return plan_cuda_fail(e, "cudaGraphInstantiate(training step)");
             }
-            f->g_n = n;
-            f->g_theta = theta;
-            f->g_w = weights;
             f->g_batch = batch;
             f->g_lr = lr;
             f->g_seed = seed;
@@ -1031,15 +1125,35 @@ abc_status abc_maf_train(abc_maf f, uint64_t n, const float* theta, const float*
         for (int32_t i = 0; i < n_steps; ++i) MAF_TRY(cudaGraphLaunch(f->graph, s), "cudaGraphLaunch");
     }
     if (loss_out) {
-        MAF_TRY(full_gradient(f, n, theta, weights, s), "flow loss");
-        float sums[2] = {0.f, 0.f};
-        MAF_TRY(cudaMemcpyAsync(sums, f->d_sums, sizeof sums, cudaMemcpyDeviceToHost, s), "cudaMemcpyAsync(sums)");
+        MAF_TRY(full_gradient(f, max_n, s), "flow loss");
+        std::vector<float> sums(2 * (size_t)f->R);
+        MAF_TRY(cudaMemcpyAsync(sums.data(), f->d_sums, sizeof(float) * sums.size(), cudaMemcpyDeviceToHost, s),
+                "cudaMemcpyAsync(sums)");
         MAF_TRY(cudaStreamSynchronize(s), "cudaStreamSynchronize");
-        *loss_out = sums[1] > 0.f ? sums[0] / sums[1] : 0.f;
+        for (int r = 0; r < f->R; ++r) loss_out[r] = sums[2 * r + 1] > 0.f ? sums[2 * r] / sums[2 * r + 1] : 0.f;
     } else {
         MAF_TRY(cudaStreamSynchronize(s), "cudaStreamSynchronize");
     }
     return plan_ok();
+}
+
+abc_status abc_maf_train(abc_maf f, uint64_t n, const float* theta, const float* weights, int32_t n_steps,
+                         int32_t batch, float lr, uint64_t seed, float* loss_out, void* cuda_stream)
+{
+    abc_status st;
+    if ((st = check(f)) != ABC_OK) return st;
+    if (n == 0 || !theta) return plan_fail(ABC_ERR_INVALID_ARG, "need n > 0 points");
+    // flow 0 only: the other flows get no points and keep their parameters
+    std::vector<const float*> th((size_t)f->R, nullptr), w((size_t)f->R, nullptr);
+    std::vector<uint64_t> nn((size_t)f->R, 0);
+    std::vector<float> loss((size_t)f->R, 0.f);
+    th[0] = theta;
+    w[0] = weights;
+    nn[0] = n;
+    st = abc_maf_train_flows(f, th.data(), w.data(), nn.data(), n_steps, batch, lr, seed,
+                             loss_out ? loss.data() : nullptr, cuda_stream);
+    if (st == ABC_OK && loss_out) *loss_out = loss[0];
+    return st;
 }
 
 abc_status abc_maf_destroy(abc_maf f)
@@ -1054,6 +1168,8 @@ abc_status abc_maf_destroy(abc_maf f)
     cudaFree(f->d_sums);
     cudaFree(f->d_step);
     cudaFree(f->d_rows);
+    cudaFree(f->d_slots);
+    if (f->h_slots) cudaFreeHost(f->h_slots);
     delete f;
     return plan_ok();
 }

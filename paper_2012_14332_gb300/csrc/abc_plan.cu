@@ -2,6 +2,7 @@
 // device memory allocated up front, allocation-free asynchronous runs, CUDA
 // graph capture and replay of runs, and the launch-shape autotuner.
 #include <cmath>
+#include <cstddef>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -392,6 +393,22 @@ abc_status abc_plan_set_region(abc_plan plan, int32_t region, const float* theta
     PLAN_TRY(cudaMemcpy(plan->d_regions, cur.data(), sizeof(abcgb::RegionDev) * plan->n_regions,
                         cudaMemcpyHostToDevice),
              "cudaMemcpy(region table)");
+    return plan_ok();
+}
+
+abc_status abc_plan_set_eps(abc_plan plan, int32_t region, double eps)
+{
+    abc_status st;
+    if ((st = check_plan(plan)) != ABC_OK) return st;
+    if (region < 0 || region >= plan->n_regions) return plan_fail(ABC_ERR_INVALID_ARG, "region out of range");
+    if (!(eps >= 0.0)) return plan_fail(ABC_ERR_INVALID_ARG, "eps must be >= 0 and not NaN");
+    const uint64_t acc_max = abcgb::plan_acc_threshold(eps);
+    plan->regions[region].acc_max = acc_max;
+    // one field of the device table; the rest (first indices advanced by runs) stays
+    abcgb::RegionDev* d = plan->d_regions + region;
+    PLAN_TRY(cudaMemcpy(reinterpret_cast<char*>(d) + offsetof(abcgb::RegionDev, acc_max), &acc_max, sizeof acc_max,
+                        cudaMemcpyHostToDevice),
+             "cudaMemcpy(region eps)");
     return plan_ok();
 }
 

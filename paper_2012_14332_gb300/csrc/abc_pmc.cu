@@ -53,7 +53,7 @@ __global__ void propose_kernel(const __grid_constant__ abcgb::ModelParams p, uin
     abcgb::box_muller<abcgb::kFast>(b.x, b.y, z[4], z[5]);
     abcgb::box_muller<abcgb::kFast>(b.z, b.w, z[6], z[7]);
     // 53-bit uniform from two words, then the inverse CDF of the weights
-    const double u = ((double)(c.x >> 11) * 2097152.0 + (double)(c.y >> 11)) * 0x1p-53 * cumw[m - 1];
+    const double u = ((double)(c.x >> 5) * 67108864.0 + (double)(c.y >> 6)) * 0x1p-53 * cumw[m - 1];
     uint64_t lo = 0, hi = m - 1;
     while (lo < hi) {
         const uint64_t mid = (lo + hi) / 2;

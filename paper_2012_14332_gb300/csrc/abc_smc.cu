@@ -24,14 +24,6 @@ ModelParams plan_make_params(const abc_prior_box* prior, int32_t T, int64_t N_po
 
 namespace {
 
-// log q of each accepted sample, looked up by its index in the round's proposals.
-__global__ void gather_logq_kernel(const float* __restrict__ logq, const uint64_t* __restrict__ idx, uint64_t first,
-                                   uint64_t n, float* __restrict__ out)
-{
-    const uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j < n) out[j] = logq[idx[j] - first];
-}
-
 // prior draws of sample indices first .. first + n - 1 (stream 0, the words the
 // plain sampler would use for those indices)
 __global__ void prior_theta_kernel(const __grid_constant__ abcgb::ModelParams p, uint64_t first, uint64_t n,
@@ -54,6 +46,84 @@ __global__ void mixture_logq_kernel(float* __restrict__ logq, uint64_t n, float 
     const float a = log_1m_lam + logq[j], b = log_lam_prior;
     const float m = fmaxf(a, b);
     logq[j] = m + log1pf(expf(-fabsf(a - b)));
+}
+
+// Importance weights of a round's m accepted samples, on the device.
+// Pass 1: log w_j = log prior - log q_mix(theta_j) (0 for prior draws, logq
+// NULL), and the maximum (atomicMax over an order-preserving integer key).
+// Pass 2: v_j = exp(log w_j - max) in double; sum v and sum v^2 (for the ESS);
+// v_j as the float training weight, optionally v_j in double and the
+// unnormalised exp(log w_j) of the first pool_k samples in double.
+struct WeightScratch {
+    unsigned int max_key;
+    unsigned int pad;
+    double sums[2];
+};
+
+__device__ __forceinline__ unsigned int float_key(float f)
+{
+    const unsigned int u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+__device__ __forceinline__ float key_float(unsigned int k)
+{
+    return __uint_as_float((k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k);
+}
+
+__global__ void logw_kernel(const float* __restrict__ logq, const uint64_t* __restrict__ idx, uint64_t first, uint64_t m,
+                            float log_prior, float* __restrict__ lw, WeightScratch* ws)
+{
+    const uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    float v = -INFINITY;
+    if (j < m) {
+        v = logq ? log_prior - logq[idx[j] - first] : 0.f;
+        lw[j] = v;
+    }
+    for (int off = 16; off > 0; off >>= 1) v = fmaxf(v, __shfl_xor_sync(0xFFFFFFFFu, v, off));
+    if ((threadIdx.x & 31) == 0 && v > -INFINITY) atomicMax(&ws->max_key, float_key(v));
+}
+
+__global__ void weight_kernel(const float* __restrict__ lw, uint64_t m, WeightScratch* ws, float* __restrict__ w_train,
+                              double* __restrict__ w_exact, double* __restrict__ pool, uint64_t pool_k)
+{
+    __shared__ double part[2][8];
+    const uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const double top = (double)key_float(ws->max_key);
+    double v = 0.0;
+    if (j < m) {
+        const double l = (double)lw[j];
+        v = exp(l - top);
+        w_train[j] = (float)v;
+        if (w_exact) w_exact[j] = v;
+        if (pool && j < pool_k) pool[j] = exp(l);
+    }
+    double a = v, b = v * v;
+    for (int off = 16; off > 0; off >>= 1) {
+        a += __shfl_xor_sync(0xFFFFFFFFu, a, off);
+        b += __shfl_xor_sync(0xFFFFFFFFu, b, off);
+    }
+    const int warp = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        part[0][warp] = a;
+        part[1][warp] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double sa = 0.0, sb = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+            sa += part[0][k];
+            sb += part[1][k];
+        }
+        atomicAdd(&ws->sums[0], sa);
+        atomicAdd(&ws->sums[1], sb);
+    }
+}
+
+__global__ void scale_kernel(double* __restrict__ w, uint64_t m, double f)
+{
+    const uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < m) w[j] *= f;
 }
 
 struct Guard {
@@ -87,6 +157,27 @@ using abcgb::plan_fail;
         if (_s != ABC_OK) return _s;        \
     } while (0)
 
+// Weights of a round's m accepted samples (logq: the round's proposal log
+// densities, NULL for prior draws): float training weights v_j into w_train,
+// optionally v_j in double into w_exact and the unnormalised weights of the
+// first pool_k samples into pool; *sum_v, *sum_v2 for the ESS. Synchronizes s.
+static abc_status round_weights(const float* logq, const uint64_t* idx, uint64_t first, uint64_t m, double log_prior,
+                                float* d_lw, float* w_train, double* w_exact, double* pool, uint64_t pool_k,
+                                WeightScratch* d_ws, cudaStream_t s, double* sum_v, double* sum_v2)
+{
+    SMC_TRY(cudaMemsetAsync(d_ws, 0, sizeof(WeightScratch), s), "cudaMemsetAsync(weight scratch)");
+    const unsigned blocks = (unsigned)((m + 255) / 256);
+    logw_kernel<<<blocks, 256, 0, s>>>(logq, idx, first, m, (float)log_prior, d_lw, d_ws);
+    weight_kernel<<<blocks, 256, 0, s>>>(d_lw, m, d_ws, w_train, w_exact, pool, pool_k);
+    SMC_TRY(cudaGetLastError(), "weight launch");
+    WeightScratch h;
+    SMC_TRY(cudaMemcpyAsync(&h, d_ws, sizeof h, cudaMemcpyDeviceToHost, s), "cudaMemcpyAsync(weight sums)");
+    SMC_TRY(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+    *sum_v = h.sums[0];
+    *sum_v2 = h.sums[1];
+    return ABC_OK;
+}
+
 extern "C" abc_status abc_smc_run(const abc_prior_box* prior, const int32_t* observed, int32_t T, int64_t N_pop,
                                   const abc_smc_config* cfg, abc_smc_round* rounds_out, float* theta_out,
                                   double* weight_out, double* dist_out, uint64_t* n_out, void* cuda_stream)
@@ -112,10 +203,13 @@ extern "C" abc_status abc_smc_run(const abc_prior_box* prior, const int32_t* obs
     gd.dev.push_back(d_prop);
     SMC_TRY(cudaMalloc(&d_logq, sizeof(float) * N), "cudaMalloc(logq)");
     gd.dev.push_back(d_logq);
-    SMC_TRY(cudaMalloc(&d_acc_logq, sizeof(float) * cap), "cudaMalloc(accepted logq)");
+    SMC_TRY(cudaMalloc(&d_acc_logq, sizeof(float) * cap), "cudaMalloc(log weights)");
     gd.dev.push_back(d_acc_logq);
     SMC_TRY(cudaMalloc(&d_w, sizeof(float) * cap), "cudaMalloc(weights)");
     gd.dev.push_back(d_w);
+    WeightScratch* d_ws = nullptr;
+    SMC_TRY(cudaMalloc(&d_ws, sizeof(WeightScratch)), "cudaMalloc(weight scratch)");
+    gd.dev.push_back(d_ws);
     float* d_train = nullptr;
     SMC_TRY(cudaMalloc(&d_train, sizeof(float) * 8 * cap), "cudaMalloc(training set)");
     gd.dev.push_back(d_train);
@@ -123,8 +217,6 @@ extern "C" abc_status abc_smc_run(const abc_prior_box* prior, const int32_t* obs
 
     double eps = cfg->eps0;
     bool use_flow = false;
-    std::vector<float> h_logq(cap), h_w(cap);
-    std::vector<double> h_wd(cap);
     uint64_t last_n = 0;
     for (int32_t r = 0; r < cfg->rounds; ++r) {
         abc_smc_round& R = rounds_out[r];
@@ -180,33 +272,15 @@ extern "C" abc_status abc_smc_run(const abc_prior_box* prior, const int32_t* obs
         R.n_accepted = n_acc;
         R.simulated_days = days;
         const uint64_t m = std::min(n_acc, cap);
-        // importance weights prior / q of the kept accepted samples
+        const bool last = r + 1 == cfg->rounds;
+        // importance weights prior / q_mix of the kept accepted samples
+        double sw = 0.0, sw2 = 0.0;
         if (m > 0) {
-            if (use_flow) {
-                gather_logq_kernel<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(d_logq, acc_idx, first, m, d_acc_logq);
-                SMC_TRY(cudaGetLastError(), "gather launch");
-                SMC_TRY(cudaMemcpyAsync(h_logq.data(), d_acc_logq, sizeof(float) * m, cudaMemcpyDeviceToHost, s),
-                        "cudaMemcpyAsync(logq)");
-                SMC_TRY(cudaStreamSynchronize(s), "cudaStreamSynchronize");
-                double top = -INFINITY;
-                for (uint64_t j = 0; j < m; ++j) top = std::max(top, log_prior - (double)h_logq[j]);
-                for (uint64_t j = 0; j < m; ++j) h_wd[j] = std::exp(log_prior - (double)h_logq[j] - top);
-            } else {
-                for (uint64_t j = 0; j < m; ++j) h_wd[j] = 1.0;
-            }
-            double sw = 0.0, sw2 = 0.0;
-            for (uint64_t j = 0; j < m; ++j) {
-                sw += h_wd[j];
-                sw2 += h_wd[j] * h_wd[j];
-            }
+            SMC_ST(round_weights(use_flow ? d_logq : nullptr, acc_idx, first, m, log_prior, d_acc_logq, d_w,
+                                 last ? weight_out : nullptr, nullptr, 0, d_ws, s, &sw, &sw2));
             R.ess_fraction = sw2 > 0.0 ? sw * sw / sw2 / (double)m : 0.0;
-            for (uint64_t j = 0; j < m; ++j) {
-                h_wd[j] /= sw;
-                h_w[j] = (float)h_wd[j];
-            }
         }
         // the next round's proposal: train on this round's weighted accepts
-        const bool last = r + 1 == cfg->rounds;
         if (last) {
             last_n = m;
             if (m > 0) {
@@ -216,9 +290,10 @@ extern "C" abc_status abc_smc_run(const abc_prior_box* prior, const int32_t* obs
                 if (dist_out)
                     SMC_TRY(cudaMemcpyAsync(dist_out, acc_dist, sizeof(double) * m, cudaMemcpyDefault, s),
                             "cudaMemcpyAsync(dist)");
-                if (weight_out)
-                    SMC_TRY(cudaMemcpyAsync(weight_out, h_wd.data(), sizeof(double) * m, cudaMemcpyDefault, s),
-                            "cudaMemcpyAsync(weights)");
+                if (weight_out && sw > 0.0) {
+                    scale_kernel<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(weight_out, m, 1.0 / sw);
+                    SMC_TRY(cudaGetLastError(), "scale launch");
+                }
             }
             SMC_TRY(cudaEventRecord(gd.ev[3], s), "cudaEventRecord");
         } else {
@@ -226,8 +301,6 @@ extern "C" abc_status abc_smc_run(const abc_prior_box* prior, const int32_t* obs
             if (trainable) {
                 SMC_TRY(cudaMemcpyAsync(d_train, acc_theta, sizeof(float) * 8 * m, cudaMemcpyDeviceToDevice, s),
                         "cudaMemcpyAsync(training set)");
-                SMC_TRY(cudaMemcpyAsync(d_w, h_w.data(), sizeof(float) * m, cudaMemcpyHostToDevice, s),
-                        "cudaMemcpyAsync(weights)");
                 float loss = 0.f;
                 SMC_ST(abc_maf_train(gd.flow, m, d_train, d_w, cfg->train_steps, cfg->train_batch, cfg->train_lr,
                                      cfg->seed + 7919 * (uint64_t)r, &loss, s));
@@ -244,5 +317,206 @@ extern "C" abc_status abc_smc_run(const abc_prior_box* prior, const int32_t* obs
     }
     SMC_TRY(cudaStreamSynchronize(s), "cudaStreamSynchronize");
     *n_out = last_n;
+    return abcgb::plan_ok();
+}
+
+namespace {
+
+struct RegionsGuard {
+    std::vector<void*> dev;
+    abc_plan plan = nullptr;
+    abc_maf flows = nullptr;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    ~RegionsGuard()
+    {
+        for (void* p : dev) cudaFree(p);
+        if (plan) abc_plan_destroy(plan);
+        if (flows) abc_maf_destroy(flows);
+        for (cudaEvent_t e : ev)
+            if (e) cudaEventDestroy(e);
+    }
+};
+
+}  // namespace
+
+extern "C" abc_status abc_smc_run_regions(const abc_prior_box* prior, abc_smc_region* regions, int32_t n_regions,
+                                          const abc_smc_stream_config* scfg, abc_smc_round* rounds_out,
+                                          void* cuda_stream)
+{
+    abc_status st;
+    if (!abcgb::plan_check_prior(prior, &st)) return st;
+    if (!scfg || !rounds_out || !regions) return plan_fail(ABC_ERR_INVALID_ARG, "regions, cfg and rounds_out are required");
+    const abc_smc_config* cfg = &scfg->base;
+    const int32_t R = n_regions;
+    if (R < 1 || R > ABC_MAX_REGIONS) return plan_fail(ABC_ERR_INVALID_ARG, "n_regions must be in [1, ABC_MAX_REGIONS]");
+    if (cfg->rounds < 1 || cfg->sims_per_round == 0 || !(cfg->eps_factor > 0.0) || cfg->eps_factor > 1.0 ||
+        !(cfg->ess_min >= 0.0) || cfg->capacity == 0 || !(cfg->defensive >= 0.0) || cfg->defensive >= 1.0 ||
+        scfg->shrink_rounds < 1 || scfg->shrink_rounds > cfg->rounds || scfg->train_steps_warm < 0 ||
+        cfg->train_steps < 0)
+        return plan_fail(ABC_ERR_INVALID_ARG, "bad multi-region sequential ABC configuration");
+    for (int32_t g = 0; g < R; ++g) {
+        const abc_smc_region& G = regions[g];
+        if (!G.observed || !(G.eps >= 0.0)) return plan_fail(ABC_ERR_INVALID_ARG, "a region lacks observed data or eps");
+        if (G.capacity > 0 && (!G.theta_out || !G.weight_out || !G.dist_out))
+            return plan_fail(ABC_ERR_INVALID_ARG, "a region with capacity > 0 lacks output buffers");
+    }
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    if (!s) return plan_fail(ABC_ERR_INVALID_ARG, "sequential ABC needs a non-default stream");
+    const uint64_t N = cfg->sims_per_round, cap = cfg->capacity;
+    const int32_t S = scfg->shrink_rounds;
+    double log_prior = 0.0;
+    for (int j = 0; j < 8; ++j) log_prior -= std::log((double)prior->hi[j] - (double)prior->lo[j]);
+
+    RegionsGuard gd;
+    SMC_ST(abc_maf_create_multi(R, cfg->flow_blocks, cfg->flow_hidden, prior, &gd.flows));
+    SMC_ST(abc_maf_init_random(gd.flows, cfg->seed ^ 0x5EED5EEDull, 0.3f));
+    float *d_prop = nullptr, *d_logq = nullptr, *d_acc_logq = nullptr, *d_w = nullptr, *d_train = nullptr;
+    SMC_TRY(cudaMalloc(&d_prop, sizeof(float) * 8 * N * R), "cudaMalloc(proposals)");
+    gd.dev.push_back(d_prop);
+    SMC_TRY(cudaMalloc(&d_logq, sizeof(float) * N * R), "cudaMalloc(logq)");
+    gd.dev.push_back(d_logq);
+    SMC_TRY(cudaMalloc(&d_acc_logq, sizeof(float) * cap), "cudaMalloc(log weights)");
+    gd.dev.push_back(d_acc_logq);
+    WeightScratch* d_ws = nullptr;
+    SMC_TRY(cudaMalloc(&d_ws, sizeof(WeightScratch)), "cudaMalloc(weight scratch)");
+    gd.dev.push_back(d_ws);
+    SMC_TRY(cudaMalloc(&d_w, sizeof(float) * cap * R), "cudaMalloc(weights)");
+    gd.dev.push_back(d_w);
+    SMC_TRY(cudaMalloc(&d_train, sizeof(float) * 8 * cap * R), "cudaMalloc(training sets)");
+    gd.dev.push_back(d_train);
+    for (cudaEvent_t& e : gd.ev) SMC_TRY(cudaEventCreate(&e), "cudaEventCreate");
+
+    // one plan for every round: the regions' eps, proposals and first indices
+    // are set before each run
+    std::vector<abc_region> regs((size_t)R);
+    for (int32_t g = 0; g < R; ++g) {
+        abc_region& q = regs[g];
+        q = abc_region{};
+        q.observed = regions[g].observed;
+        q.T = regions[g].T;
+        q.N_pop = regions[g].N_pop;
+        q.eps = regions[g].eps;
+        q.n_samples = N;
+        q.first_index = 0;
+        q.stream = (uint32_t)g;
+        q.capacity = cap;
+        q.theta_in = nullptr;
+        regions[g].n_pooled = 0;
+        regions[g].n_out = 0;
+    }
+    SMC_ST(abc_plan_create(prior, regs.data(), R, cfg->seed, cfg->mode, &gd.plan));
+
+    std::vector<char> use_flow((size_t)R, 0), trainable((size_t)R, 0);
+    bool trained_once = false;
+    std::vector<float> losses((size_t)R, 0.f);
+    std::vector<const float*> tr_theta((size_t)R), tr_w((size_t)R);
+    std::vector<uint64_t> tr_n((size_t)R);
+    for (int32_t r = 0; r < cfg->rounds; ++r) {
+        const uint64_t first = (uint64_t)r * N;
+        abc_smc_round* Rr = rounds_out + (size_t)r * R;
+        SMC_TRY(cudaEventRecord(gd.ev[0], s), "cudaEventRecord");
+        for (int32_t g = 0; g < R; ++g) {
+            const double eps = r < S ? regions[g].eps / std::pow(cfg->eps_factor, (double)(S - 1 - r)) : regions[g].eps;
+            Rr[g] = abc_smc_round{};
+            Rr[g].eps = eps;
+            Rr[g].proposal = use_flow[g] ? 1 : 0;
+            Rr[g].n_sims = N;
+            if (use_flow[g]) {
+                const uint64_t n_prior = (uint64_t)std::floor(cfg->defensive * (double)N);
+                const uint64_t n_flow = N - n_prior;
+                float* prop = d_prop + (size_t)g * 8 * N;
+                float* lq = d_logq + (size_t)g * N;
+                if (n_flow)
+                    SMC_ST(abc_maf_sample_at(gd.flows, g, n_flow, nullptr, cfg->seed, (uint32_t)(R + g), first, prop, lq,
+                                             s));
+                if (n_prior) {
+                    const abcgb::ModelParams pp = abcgb::plan_make_params(prior, 1, 1, cfg->seed, (uint32_t)g, nullptr);
+                    prior_theta_kernel<<<(unsigned)((n_prior + 255) / 256), 256, 0, s>>>(pp, first + n_flow, n_prior,
+                                                                                       prop + 8 * n_flow);
+                    SMC_TRY(cudaGetLastError(), "prior draw launch");
+                    SMC_ST(abc_maf_log_q_at(gd.flows, g, n_prior, prop + 8 * n_flow, lq + n_flow, s));
+                }
+                if (cfg->defensive > 0.0) {
+                    mixture_logq_kernel<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(
+                        lq, N, (float)std::log1p(-cfg->defensive), (float)(std::log(cfg->defensive) + log_prior));
+                    SMC_TRY(cudaGetLastError(), "mixture launch");
+                }
+            }
+            SMC_ST(abc_plan_set_eps(gd.plan, g, eps));
+            SMC_ST(abc_plan_set_region(gd.plan, g, use_flow[g] ? d_prop + (size_t)g * 8 * N : nullptr, first));
+        }
+        SMC_TRY(cudaEventRecord(gd.ev[1], s), "cudaEventRecord");
+        SMC_ST(abc_plan_reset(gd.plan, s));
+        SMC_ST(abc_plan_run(gd.plan, s));
+        SMC_TRY(cudaEventRecord(gd.ev[2], s), "cudaEventRecord");
+        bool any_train = false;
+        for (int32_t g = 0; g < R; ++g) {
+            uint64_t n_acc = 0, days = 0;
+            float* acc_theta = nullptr;
+            double* acc_dist = nullptr;
+            uint64_t* acc_idx = nullptr;
+            SMC_ST(abc_plan_results(gd.plan, g, &n_acc, &days, &acc_theta, &acc_dist, &acc_idx, s));
+            Rr[g].n_accepted = n_acc;
+            Rr[g].simulated_days = days;
+            const uint64_t m = std::min(n_acc, cap);
+            trainable[g] = 0;
+            tr_n[g] = 0;
+            if (m == 0) continue;
+            // weights prior / q_mix (1 for prior draws); the samples accepted at
+            // the region's final eps are pooled with their unnormalised weights
+            abc_smc_region& G = regions[g];
+            const bool pool = r >= S - 1;
+            const uint64_t k = pool ? std::min(m, G.capacity - G.n_out) : 0;
+            float* tw = d_w + (size_t)g * cap;
+            double sw = 0.0, sw2 = 0.0;
+            SMC_ST(round_weights(use_flow[g] ? d_logq + (size_t)g * N : nullptr, acc_idx, first, m, log_prior,
+                                 d_acc_logq, tw, nullptr, k ? G.weight_out + G.n_out : nullptr, k, d_ws, s, &sw,
+                                 &sw2));
+            Rr[g].ess_fraction = sw2 > 0.0 ? sw * sw / sw2 / (double)m : 0.0;
+            if (pool) {
+                G.n_pooled += n_acc;
+                if (k > 0) {
+                    SMC_TRY(cudaMemcpyAsync(G.theta_out + 8 * G.n_out, acc_theta, sizeof(float) * 8 * k,
+                                            cudaMemcpyDefault, s),
+                            "cudaMemcpyAsync(pooled theta)");
+                    SMC_TRY(cudaMemcpyAsync(G.dist_out + G.n_out, acc_dist, sizeof(double) * k, cudaMemcpyDefault, s),
+                            "cudaMemcpyAsync(pooled dist)");
+                    G.n_out += k;
+                }
+            }
+            // this round's weighted accepts train the region's next proposal
+            if (r + 1 < cfg->rounds && m >= 64 && Rr[g].ess_fraction >= cfg->ess_min) {
+                float* tt = d_train + (size_t)g * 8 * cap;
+                SMC_TRY(cudaMemcpyAsync(tt, acc_theta, sizeof(float) * 8 * m, cudaMemcpyDeviceToDevice, s),
+                        "cudaMemcpyAsync(training set)");
+                trainable[g] = 1;
+                tr_theta[g] = tt;
+                tr_w[g] = tw;
+                tr_n[g] = m;
+                any_train = true;
+            }
+        }
+        if (any_train) {
+            const int32_t steps = trained_once ? scfg->train_steps_warm : cfg->train_steps;
+            SMC_ST(abc_maf_train_flows(gd.flows, tr_theta.data(), tr_w.data(), tr_n.data(), steps, cfg->train_batch,
+                                       cfg->train_lr, cfg->seed + 7919 * (uint64_t)r, losses.data(), s));
+            trained_once = true;
+            for (int32_t g = 0; g < R; ++g)
+                if (trainable[g]) Rr[g].train_loss = losses[g];
+        }
+        SMC_TRY(cudaEventRecord(gd.ev[3], s), "cudaEventRecord");
+        SMC_TRY(cudaEventSynchronize(gd.ev[3]), "cudaEventSynchronize");
+        float ms[3] = {0.f, 0.f, 0.f};
+        cudaEventElapsedTime(&ms[0], gd.ev[0], gd.ev[1]);
+        cudaEventElapsedTime(&ms[1], gd.ev[1], gd.ev[2]);
+        cudaEventElapsedTime(&ms[2], gd.ev[2], gd.ev[3]);
+        for (int32_t g = 0; g < R; ++g) {
+            Rr[g].ms_propose = ms[0];
+            Rr[g].ms_simulate = ms[1];
+            Rr[g].ms_train = ms[2];
+            use_flow[g] = trainable[g];
+        }
+    }
+    SMC_TRY(cudaStreamSynchronize(s), "cudaStreamSynchronize");
     return abcgb::plan_ok();
 }

@@ -173,3 +173,62 @@ def test_training_fits_a_known_density():
     assert np.allclose(ys.mean(0), m, atol=0.08)
     assert np.allclose(np.cov(ys.T), A @ A.T, atol=0.1)
     f.close()
+
+
+def test_flow_set_members_equal_single_flows():
+    """Flow r of a set evaluates and samples exactly like a one-flow object
+    holding the same parameters (the same kernels on flow r's copy)."""
+    K, H, R = 3, 64, 3
+    singles, vs = [], []
+    for r in range(R):
+        f, _ = _flow(K, H, 50 + r, 0.3)
+        singles.append(f)
+        vs.append(f.get_params())
+    fs = abc.Flow(K, H, n_flows=R)
+    fs.set_params(np.stack(vs))
+    assert np.array_equal(fs.get_params(), np.stack(vs))
+    th = torch.from_numpy(_thetas(1000, 3)).to(DEV)
+    u = torch.from_numpy(np.random.default_rng(4).normal(size=(777, 8)).astype(np.float32)).to(DEV)
+    for r in range(R):
+        assert torch.equal(fs.log_q(th, flow=r), singles[r].log_q(th))
+        a, la = fs.sample(777, base_normals=u, flow=r)
+        b, lb = singles[r].sample(777, base_normals=u)
+        assert torch.equal(a, b) and torch.equal(la, lb)
+        a, _ = fs.sample(2000, seed=9, stream=2, first_index=5, flow=r)
+        b, _ = singles[r].sample(2000, seed=9, stream=2, first_index=5)
+        assert torch.equal(a, b)
+    with pytest.raises(abc.AbcError):
+        fs.log_q(th, flow=R)
+    for f in singles:
+        f.close()
+    fs.close()
+
+
+def test_train_flows_fits_each_flow_to_its_own_data():
+    """One set trains three flows on three different Gaussians (in y space) in
+    the same launches; each reaches its own data's entropy, and a flow given no
+    data keeps its parameters bit for bit."""
+    rng = np.random.default_rng(21)
+    R = 4
+    fs = abc.Flow(3, 128, n_flows=R)
+    fs.init_random(seed=8, scale=0.3)
+    p0 = fs.get_params().copy()
+    data, ents, means = [], [], []
+    for r in range(3):
+        A = np.tril(rng.normal(size=(8, 8)) * 0.3) + np.eye(8) * (0.4 + 0.2 * r)
+        m = rng.normal(size=8) * 0.5
+        y = rng.normal(size=(20000 + 5000 * r, 8)) @ A.T + m
+        data.append(torch.from_numpy(mo.to_theta(y, LO, HI).astype(np.float32)).to(DEV))
+        ents.append(0.5 * np.linalg.slogdet(2 * np.pi * np.e * A @ A.T)[1])
+        means.append(m)
+    losses = fs.train_flows(data + [None], None, n_steps=1500, batch=1024, lr=2e-3, seed=1)
+    p1 = fs.get_params()
+    print("train_flows: losses %s, entropies %s" % (np.round(losses, 4), np.round(ents, 4)))
+    for r in range(3):
+        assert losses[r] < ents[r] + 0.1, r
+        ts, _ = fs.sample(20000, seed=2, flow=r)
+        ys = mo.to_y(ts.cpu().numpy().astype(np.float64), LO, HI)
+        assert np.allclose(ys.mean(0), means[r], atol=0.1), r
+    assert losses[3] == 0.0 and np.array_equal(p1[3], p0[3])
+    assert not np.array_equal(p1[0], p0[0])
+    fs.close()

@@ -42,6 +42,27 @@ def test_weights_match_oracle():
     assert np.median(rel) < 1e-5 and rel.max() < 1e-3
 
 
+def test_parents_match_the_oracle_exactly():
+    """With a negligible move, each proposal names its parent; the parent index
+    (integer work) equals the oracle's inverse-CDF choice from the same Philox
+    words: counter (i_lo, i_hi, 0, 4 * 2 + 2), key = seed."""
+    import oracle
+    m, n, seed, first = 700, 20000, 31, (1 << 32) - 5000
+    old, w = _population(m, 6)
+    old[:, 0] = 0.25 + 0.5 * np.arange(m) / m              # parent j is read off coordinate 0
+    w[::7] = 0.0                                           # zero-weight parents are never chosen
+    prop = abc.abc_pmc_propose(torch.from_numpy(old).to(DEV), torch.from_numpy(w).to(DEV),
+                               np.eye(8, dtype=np.float32) * 1e-7, n, seed=seed,
+                               first_index=first).cpu().numpy().astype(np.float64)
+    got = np.rint((prop[:, 0] - 0.25) * m / 0.5).astype(np.int64)
+    words = np.array([oracle.philox4x32_10([(first + j) & 0xFFFFFFFF, (first + j) >> 32, 0, 10],
+                                           [seed & 0xFFFFFFFF, seed >> 32]) for j in range(n)])
+    u = pmc.parent_uniform(words[:, 0], words[:, 1])
+    _, want = pmc.propose(old.astype(np.float64), w, np.eye(8) * 1e-7, u, np.zeros((n, 8)), LO, HI)
+    assert np.array_equal(got, want)
+    assert not np.isin(got, np.arange(0, m, 7)).any()
+
+
 def test_proposals_have_the_mixture_moments():
     old, w = _population(500, 3)
     L = (pmc.kernel_factor(old.astype(np.float64), w) * 0.01).astype(np.float32)

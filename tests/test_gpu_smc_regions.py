@@ -1,0 +1,70 @@
+"""Sequential ABC with one learned proposal per region, several regions in one
+batched launch per round (abc_smc_run_regions): each region's pooled,
+importance-weighted samples at its final tolerance estimate the same ABC
+posterior (Eq. 7) as plain rejection from the prior at that tolerance
+(weighted means within Monte-Carlo error, weighted KS per coordinate), and
+the learned proposals accept far more of their simulations than the prior."""
+import numpy as np
+import pytest
+
+from tests import inputs
+from tests.test_gpu_smc import weighted_ks
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_2012_14332_gb300 as abc  # noqa: E402
+from paper_2012_14332_gb300 import build as _build  # noqa: E402
+
+_build.build()
+NAMES = ["stream16_r11", "stream16_r15", "stream16_r04", "stream16_r12"]
+
+
+def test_per_region_flows_keep_each_posterior():
+    regs = []
+    for k, name in enumerate(NAMES):
+        w = inputs.workload(name)
+        pilot = abc.abc_distances(w["observed"], w["P"], 1 << 20, 300 + k, mode="fast")
+        eps = abc.abc_kth_smallest(pilot, 1 << 10)            # ~1e-3 prior acceptance
+        regs.append(dict(observed=w["observed"], N_pop=w["P"], eps=eps, pool=1 << 18))
+    rounds, shrink, n = 6, 3, 1 << 18
+    info, res = abc.abc_smc_run_regions(regs, rounds=rounds, shrink_rounds=shrink, sims_per_round=n, eps_factor=0.7,
+                                        flow_blocks=3, flow_hidden=128, train_steps=400, train_steps_warm=150,
+                                        train_batch=4096, train_lr=2e-3, seed=21, capacity=1 << 17, mode="fast")
+    for r in range(rounds):
+        print("round %d: %s" % (r, "  ".join("%d/%d ess %.2f" % (x["proposal"], x["n_accepted"], x["ess_fraction"])
+                                             for x in info[r])))
+    for g, reg in enumerate(regs):
+        th, wt, di, n_pooled = res[g]
+        assert n_pooled == sum(info[r][g]["n_accepted"] for r in range(shrink - 1, rounds))
+        assert 0 < th.shape[0] <= min(n_pooled, 1 << 18)
+        assert np.all(di.cpu().numpy() <= reg["eps"])
+        assert info[shrink - 1][g]["eps"] == reg["eps"] and info[0][g]["eps"] > reg["eps"]
+        used_flow = [info[r][g]["proposal"] for r in range(1, rounds)]
+        assert sum(used_flow) >= rounds - 2, (g, used_flow)
+        # plain prior ABC at the same final tolerance
+        n_plain = 1 << 24
+        th_p, _, _, n_acc_p = abc.abc_sample(reg["observed"], reg["N_pop"], reg["eps"], n_plain, 777 + g, mode="fast",
+                                             capacity=1 << 16)
+        assert n_acc_p > 2000
+        p_prior = n_acc_p / n_plain
+        last = info[rounds - 1][g]
+        p_flow = last["n_accepted"] / n
+        print("region %d: prior acceptance %.3e, flow acceptance %.3e, ESS fraction %.3f, pooled %d" % (
+            g, p_prior, p_flow, last["ess_fraction"], n_pooled))
+        if last["proposal"] == 1:
+            assert p_flow * last["ess_fraction"] > 3 * p_prior
+        a = th.cpu().numpy().astype(np.float64)
+        wa = wt.cpu().numpy()
+        wa = wa / wa.sum()
+        b = th_p.cpu().numpy().astype(np.float64)
+        ne = 1.0 / (wa ** 2).sum()
+        for j in range(8):
+            mw = (wa * a[:, j]).sum()
+            se = np.sqrt((wa * (a[:, j] - mw) ** 2).sum() / ne + b[:, j].var() / len(b))
+            assert abs(mw - b[:, j].mean()) < 5 * se + 1e-9, (g, j)
+            D, p = weighted_ks(a[:, j], wa, b[:, j])
+            assert p > 1e-3, (g, j, D, p)

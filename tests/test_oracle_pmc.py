@@ -55,3 +55,27 @@ def test_proposals_outside_the_box_are_marked():
     L = np.eye(8) * 100.0
     prop, _ = pmc.propose(old, w, L, np.linspace(0, 0.99, 50), np.ones((50, 8)), LO, HI)
     assert np.all(np.isnan(prop[:, 0]))
+
+
+def test_parent_uniform_spans_the_unit_interval():
+    """The 53-bit construction: zero words give 0, all-ones words give the
+    largest double below 1, and each bit of the kept fields lands at its own
+    power of two (so no field is dropped or overlapped)."""
+    assert pmc.parent_uniform(0, 0) == 0.0
+    assert pmc.parent_uniform(0xFFFFFFFF, 0xFFFFFFFF) == 1.0 - 2.0 ** -53
+    assert pmc.parent_uniform(0x80000000, 0) == 0.5
+    assert pmc.parent_uniform(0x20, 0) == 2.0 ** -27
+    assert pmc.parent_uniform(0, 0x40) == 2.0 ** -53
+    assert pmc.parent_uniform(0x1F, 0x3F) == 0.0                 # the dropped low bits
+    w = np.random.default_rng(0).integers(0, 1 << 32, size=(2, 200000), dtype=np.uint64)
+    u = pmc.parent_uniform(w[0], w[1])
+    assert abs(u.mean() - 0.5) < 5 * np.sqrt(1 / 12 / len(u))
+    assert u.min() >= 0 and u.max() < 1
+
+
+def test_parent_choice_is_the_inverse_cdf():
+    """Parents from evenly spaced uniforms land in proportion to the weights."""
+    w = np.array([1.0, 3.0, 0.0, 4.0])
+    u = (np.arange(8000) + 0.5) / 8000
+    _, j = pmc.propose(np.zeros((4, 8)), w, np.eye(8) * 1e-9, u, np.zeros((8000, 8)), -np.ones(8), np.ones(8))
+    assert np.array_equal(np.bincount(j, minlength=4), [1000, 3000, 0, 4000])
