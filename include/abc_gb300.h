@@ -274,9 +274,12 @@ abc_status abc_plan_destroy(abc_plan plan);
  *  - y = logit((theta - lo) / (hi - lo)) (support = the box);
  *  - n_blocks MADE blocks (one hidden ReLU layer of `hidden` units; output j
  *    depends on inputs < j), each x -> z = (x - mu(x)) exp(-alpha(x)) with
- *    alpha = 6 tanh(alpha_raw / 6), the order reversed between blocks; base
- *    N(0, I);
- *  - log q(theta) = log N(z) - sum alpha - sum_j log((hi_j - lo_j) s_j (1 - s_j)),
+ *    alpha = 6 tanh(alpha_raw / 6), the order reversed between blocks;
+ *  - base: independent standard logistic coordinates,
+ *    log p(z) = sum_j (-|z_j| - 2 log(1 + exp(-|z_j|))): the logit of a uniform
+ *    variable is standard logistic, so with zero parameters q is exactly the
+ *    uniform prior, and flat posterior directions keep the prior's tails;
+ *  - log q(theta) = log p(z) - sum alpha - sum_j log((hi_j - lo_j) s_j (1 - s_j)),
  *    s = sigmoid(y).
  * Weights live in FP32 (the master copy trained by Adam) and in masked BF16
  * copies used by tensor-core products (mma.sync m16n8k8 / m16n8k16 BF16 with
@@ -291,8 +294,8 @@ abc_status abc_plan_destroy(abc_plan plan);
 typedef struct abc_maf_s* abc_maf;
 
 /* Create a flow with n_blocks (1..4) blocks of `hidden` units (a multiple of
- * 16, 16..256) on the prior box, parameters zero (q = the box's logistic
- * image of N(0, I)). Allocates its device memory on the current device. */
+ * 16, 16..256) on the prior box, parameters zero (q = the uniform prior).
+ * Allocates its device memory on the current device. */
 abc_status abc_maf_create(int32_t n_blocks, int32_t hidden, const abc_prior_box* box, abc_maf* maf_out);
 
 /* A set of n_flows (1..ABC_MAF_MAX_FLOWS) independent flows of the same shape
@@ -320,13 +323,16 @@ int64_t abc_maf_param_count(abc_maf maf);
 abc_status abc_maf_set_params(abc_maf maf, const float* params);
 abc_status abc_maf_get_params(abc_maf maf, float* params);
 
-/* Draw n proposals: base normals u (DEVICE float [n][8], or NULL to draw them
- * with Philox from (seed, stream, first_index + j)), the sequential inverse of
- * the flow, theta = lo + (hi - lo) sigmoid(y). theta_out DEVICE float [n][8];
- * logq_out DEVICE float [n] (log q(theta)) or NULL. Async. */
-abc_status abc_maf_sample(abc_maf maf, uint64_t n, const float* base_normals, uint64_t seed, uint32_t stream,
+/* Draw n proposals: standard logistic base draws u (DEVICE float [n][8], or
+ * NULL to draw them with Philox from (seed, stream, i = first_index + j):
+ * coordinate c of sample j takes word c mod 4 of the block with counter
+ * (i_lo, i_hi, 0, 4 stream + c / 4), whose uniform (2m + 1) 2^-24 (m its low
+ * 23 bits) gives the draw log(u / (1 - u))), the sequential
+ * inverse of the flow, theta = lo + (hi - lo) sigmoid(y). theta_out DEVICE
+ * float [n][8]; logq_out DEVICE float [n] (log q(theta)) or NULL. Async. */
+abc_status abc_maf_sample(abc_maf maf, uint64_t n, const float* base_draws, uint64_t seed, uint32_t stream,
                           uint64_t first_index, float* theta_out, float* logq_out, void* cuda_stream);
-abc_status abc_maf_sample_at(abc_maf maf, int32_t flow, uint64_t n, const float* base_normals, uint64_t seed,
+abc_status abc_maf_sample_at(abc_maf maf, int32_t flow, uint64_t n, const float* base_draws, uint64_t seed,
                              uint32_t stream, uint64_t first_index, float* theta_out, float* logq_out,
                              void* cuda_stream);
 
@@ -363,11 +369,17 @@ abc_status abc_maf_train(abc_maf maf, uint64_t n, const float* theta, const floa
  * ([n[r]] or NULL; `weights` itself may be NULL for all ones) and of counts
  * n[r] < 2^32; a flow with n[r] = 0 is left as it is. Each step draws `batch`
  * rows per flow and updates all flows with one gradient launch (one CTA row of
- * the grid per flow) and one Adam launch. loss_out HOST float [n_flows] or
- * NULL. Synchronizes cuda_stream (non-default). */
+ * the grid per flow) and one Adam launch. With val_fraction in (0, 0.5], the
+ * last floor(val_fraction n[r]) points of each flow with n[r] >= 20 are held
+ * out: every 25 steps each flow's validation loss is measured, a flow keeps
+ * the parameters of its best validation loss and stops training after three
+ * checks without improvement (early stopping against overfitting a small
+ * round); n_steps is then an upper bound. loss_out HOST float [n_flows] or
+ * NULL: the kept validation loss (with validation) or the full-data loss.
+ * Synchronizes cuda_stream (non-default). */
 abc_status abc_maf_train_flows(abc_maf maf, const float* const* theta, const float* const* weights, const uint64_t* n,
-                               int32_t n_steps, int32_t batch, float lr, uint64_t seed, float* loss_out,
-                               void* cuda_stream);
+                               int32_t n_steps, int32_t batch, float lr, uint64_t seed, float val_fraction,
+                               float* loss_out, void* cuda_stream);
 
 abc_status abc_maf_destroy(abc_maf maf);
 
@@ -379,7 +391,8 @@ abc_status abc_maf_destroy(abc_maf maf);
  * prior draws), and the next round draws from the flow, unless the round's
  * effective sample size (sum w)^2 / sum w^2 fell below ess_min times its
  * accept count (or it accepted fewer than 64), in which case the next round
- * falls back to the prior. A flow round draws a fraction `defensive` of its
+ * falls back to the prior. Training holds out val_fraction of the round's
+ * accepts and stops early (abc_maf_train_flows). A flow round draws a fraction `defensive` of its
  * proposals from the prior and weights every proposal by the mixture density
  * q_mix = (1 - defensive) q + defensive * prior (defensive importance sampling,
  * Hesterberg 1995), so w = prior / q_mix <= 1 / defensive.
@@ -402,6 +415,7 @@ typedef struct {
     uint64_t capacity;        /* accepted samples kept per round */
     abc_mode mode;
     double defensive;         /* prior fraction of a flow round's proposals, in [0, 1) (e.g. 0.1) */
+    double val_fraction;      /* held-out fraction for early stopping of the training, in [0, 0.5] (e.g. 0.1) */
 } abc_smc_config;
 
 typedef struct {

@@ -13,13 +13,17 @@ weighted samples:
     with (theta - lo) / (hi - lo) held in [2^-24, 1 - 2^-24];
   * flow (Papamakarios, Pavlakou, Murray 2017): K MADE blocks (Germain, Gregor,
     Murray, Larochelle 2015), each x -> z = (x - mu(x)) exp(-alpha(x)) with
-    mu_j, alpha_j depending on x_{<j} only, the order reversed between blocks,
-    base N(0, I);
+    mu_j, alpha_j depending on x_{<j} only, the order reversed between blocks;
+  * base: independent standard logistic coordinates, log p(z) =
+    -|z| - 2 log(1 + exp(-|z|)). The logit of a uniform variable is standard
+    logistic, so the flow with zero parameters is exactly the uniform prior
+    on the box, and in a coordinate where the posterior stays flat up to the
+    box's edge the flow's tails can match it (a Gaussian base cannot);
   * MADE: h = relu(W1 x + b1) with mask M1[l, j] = [d_h(l) >= j + 1], outputs
     (mu, alpha_raw) = W2 h + b2 with mask M2[j, l] = [j + 1 > d_h(l)], hidden
     degrees d_h(l) = (l mod (D - 1)) + 1;
   * alpha = A tanh(alpha_raw / A), A = 6 (keeps exp(alpha) bounded);
-  * log q(theta) = log N(z_K) - sum_k sum_j alpha_kj - sum_j log((hi_j - lo_j) u_j (1 - u_j));
+  * log q(theta) = log p(z_K) - sum_k sum_j alpha_kj - sum_j log((hi_j - lo_j) u_j (1 - u_j));
   * importance weight of an accepted draw: w = prior(theta) / q(theta);
   * training: Adam (Kingma, Ba 2015) on the weighted mean of -log q_y(y).
 """
@@ -27,7 +31,17 @@ import numpy as np
 
 D = 8
 ALPHA_MAX = 6.0
-LOG_2PI = np.log(2.0 * np.pi)
+
+
+def log_base(z):
+    """Sum over coordinates of the standard logistic log density."""
+    a = np.abs(np.asarray(z, dtype=np.float64))
+    return (-a - 2.0 * np.log1p(np.exp(-a))).sum(axis=-1)
+
+
+def base_grad(z):
+    """d/dz of -log p(z) per coordinate: tanh(z / 2)."""
+    return np.tanh(0.5 * np.asarray(z, dtype=np.float64))
 
 
 def degrees(H, D=D):
@@ -90,16 +104,17 @@ def forward(y, params, bf16=False):
         logdet -= alpha.sum(axis=1)
         caches.append(dict(x=x, mu=mu, alpha=alpha, araw=araw, a1=a1, h=h, z=z))
         x = z[:, ::-1]
-    logq = -0.5 * (x ** 2).sum(axis=1) - 0.5 * D * LOG_2PI + logdet
+    logq = log_base(x) + logdet
     return x, logq, caches
 
 
 def inverse(u, params, bf16=False):
-    """Base normals u [N, D] -> (y [N, D], log q_y [N]) by the sequential inverse."""
+    """Base draws u [N, D] (standard logistic) -> (y [N, D], log q_y [N]) by the
+    sequential inverse."""
     H = params[0]["W1"].shape[0]
     M1, M2 = masks(H)
     x = np.asarray(u, dtype=np.float64)
-    logq = -0.5 * (x ** 2).sum(axis=1) - 0.5 * D * LOG_2PI
+    logq = log_base(x)
     for p in reversed(params):
         z = x[:, ::-1]
         xin = np.zeros_like(z)
@@ -147,7 +162,7 @@ def loss_and_grad(y, w, params):
     W = w.sum()
     zK, logq, caches = forward(y, params)
     loss = -(w * logq).sum() / W
-    g_x = (w / W)[:, None] * zK                    # d loss / d (final x)
+    g_x = (w / W)[:, None] * base_grad(zK)         # d loss / d (final x)
     grads = [None] * len(params)
     for k in reversed(range(len(params))):
         c, p = caches[k], params[k]

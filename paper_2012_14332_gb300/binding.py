@@ -52,7 +52,7 @@ class AbcSmcConfig(ctypes.Structure):
                 ("eps_factor", ctypes.c_double), ("ess_min", ctypes.c_double), ("flow_blocks", ctypes.c_int32),
                 ("flow_hidden", ctypes.c_int32), ("train_steps", ctypes.c_int32), ("train_batch", ctypes.c_int32),
                 ("train_lr", ctypes.c_float), ("seed", ctypes.c_uint64), ("capacity", ctypes.c_uint64),
-                ("mode", ctypes.c_int), ("defensive", ctypes.c_double)]
+                ("mode", ctypes.c_int), ("defensive", ctypes.c_double), ("val_fraction", ctypes.c_double)]
 
 
 class AbcSmcRound(ctypes.Structure):
@@ -164,7 +164,7 @@ def load(path=None):
         L.abc_maf_flow_count.restype = ctypes.c_int32
         L.abc_maf_sample_at.argtypes = [pp, i32, u64, vp, u64, u32, u64, vp, vp, vp]
         L.abc_maf_log_q_at.argtypes = [pp, i32, u64, vp, vp, vp]
-        L.abc_maf_train_flows.argtypes = [pp, vp, vp, vp, i32, i32, ctypes.c_float, u64, vp, vp]
+        L.abc_maf_train_flows.argtypes = [pp, vp, vp, vp, i32, i32, ctypes.c_float, u64, ctypes.c_float, vp, vp]
         for nm in ("abc_maf_create_multi", "abc_maf_sample_at", "abc_maf_log_q_at", "abc_maf_train_flows"):
             getattr(L, nm).restype = ctypes.c_int
         for nm in ("abc_maf_create", "abc_maf_set_params", "abc_maf_get_params", "abc_maf_sample", "abc_maf_log_q",
@@ -581,10 +581,13 @@ class Flow:
         _check(self._L, self._L.abc_maf_get_params(self._h, v.ctypes.data))
         return v if self.n_flows == 1 else v.reshape(self.n_flows, self.n_params)
 
-    def train_flows(self, thetas, weights=None, n_steps=500, batch=1024, lr=1e-3, seed=0, cuda_stream=None):
+    def train_flows(self, thetas, weights=None, n_steps=500, batch=1024, lr=1e-3, seed=0, val_fraction=0.0,
+                    cuda_stream=None):
         """Train every flow on its own data in the same launches: thetas is a
         list of n_flows CUDA f32 [n_r, 8] tensors (None or empty = leave that
-        flow as it is), weights a matching list or None. Returns the losses."""
+        flow as it is), weights a matching list or None; val_fraction > 0 holds
+        out that share of each flow's points for early stopping. Returns the
+        losses."""
         R = self.n_flows
         th = (ctypes.c_void_p * R)()
         wt = (ctypes.c_void_p * R)()
@@ -602,11 +605,11 @@ class Flow:
         _check(self._L, self._L.abc_maf_train_flows(self._h, ctypes.cast(th, ctypes.c_void_p),
                                                     ctypes.cast(wt, ctypes.c_void_p) if weights is not None else None,
                                                     ctypes.cast(nn, ctypes.c_void_p), int(n_steps), int(batch),
-                                                    float(lr), int(seed), ctypes.cast(loss, ctypes.c_void_p),
-                                                    _stream(s)))
+                                                    float(lr), int(seed), float(val_fraction),
+                                                    ctypes.cast(loss, ctypes.c_void_p), _stream(s)))
         return np.array(loss[:], dtype=np.float64)
 
-    def sample(self, n, seed=0, stream=0, first_index=0, base_normals=None, want_logq=True, out=None,
+    def sample(self, n, seed=0, stream=0, first_index=0, base=None, want_logq=True, out=None,
                cuda_stream=None, flow=0):
         dev = torch.device("cuda", torch.cuda.current_device())
         if out is None:
@@ -614,7 +617,7 @@ class Flow:
             logq = torch.empty((n,), dtype=torch.float32, device=dev) if want_logq else None
         else:
             theta, logq = out
-        u = base_normals.data_ptr() if base_normals is not None else None
+        u = base.data_ptr() if base is not None else None
         _check(self._L, self._L.abc_maf_sample_at(self._h, int(flow), int(n), u, int(seed), int(stream),
                                                   int(first_index), theta.data_ptr(),
                                                   logq.data_ptr() if logq is not None else None, _stream(cuda_stream)))
@@ -726,7 +729,8 @@ def abc_maf_train_flows(flow, thetas, weights=None, **kw):
 
 def abc_smc_run(observed, N_pop, eps0, rounds=5, sims_per_round=1 << 22, eps_factor=0.7, ess_min=0.1,
                 flow_blocks=3, flow_hidden=256, train_steps=500, train_batch=1024, train_lr=1e-3, seed=0,
-                capacity=1 << 16, mode="fast", defensive=0.1, lo=PAPER_LO, hi=PAPER_HI, cuda_stream=None):
+                capacity=1 << 16, mode="fast", defensive=0.1, val_fraction=0.1, lo=PAPER_LO, hi=PAPER_HI,
+                cuda_stream=None):
     """Sequential ABC with the learned flow proposal. Returns (rounds: list of
     dicts, theta [m, 8], weights [m] (f64, sum 1), dist [m]) of the last round."""
     L = load()
@@ -734,7 +738,7 @@ def abc_smc_run(observed, N_pop, eps0, rounds=5, sims_per_round=1 << 22, eps_fac
     T = obs.shape[1] - 1
     cfg = AbcSmcConfig(int(rounds), int(sims_per_round), float(eps0), float(eps_factor), float(ess_min),
                        int(flow_blocks), int(flow_hidden), int(train_steps), int(train_batch), float(train_lr),
-                       int(seed), int(capacity), _mode(mode), float(defensive))
+                       int(seed), int(capacity), _mode(mode), float(defensive), float(val_fraction))
     rr = (AbcSmcRound * int(rounds))()
     dev = torch.device("cuda", torch.cuda.current_device())
     theta = torch.empty((capacity, 8), dtype=torch.float32, device=dev)
@@ -754,8 +758,8 @@ def abc_smc_run(observed, N_pop, eps0, rounds=5, sims_per_round=1 << 22, eps_fac
 
 def abc_smc_run_regions(regions, rounds=16, shrink_rounds=4, sims_per_round=1 << 20, eps_factor=0.7, ess_min=0.1,
                         flow_blocks=3, flow_hidden=256, train_steps=500, train_steps_warm=100, train_batch=1024,
-                        train_lr=1e-3, seed=0, capacity=1 << 16, mode="fast", defensive=0.1, lo=PAPER_LO, hi=PAPER_HI,
-                        cuda_stream=None):
+                        train_lr=1e-3, seed=0, capacity=1 << 16, mode="fast", defensive=0.1, val_fraction=0.1,
+                        lo=PAPER_LO, hi=PAPER_HI, cuda_stream=None):
     """Sequential ABC with one flow proposal per region, all regions in one
     batched launch per round. regions: list of dicts with observed (host int32
     [3, T+1]), N_pop, eps (final) and pool (samples kept at the final eps).
@@ -778,7 +782,7 @@ def abc_smc_run_regions(regions, rounds=16, shrink_rounds=4, sims_per_round=1 <<
                               float(reg["eps"]), th.data_ptr(), w.data_ptr(), d.data_ptr(), pool, 0, 0)
     base = AbcSmcConfig(int(rounds), int(sims_per_round), 0.0, float(eps_factor), float(ess_min), int(flow_blocks),
                         int(flow_hidden), int(train_steps), int(train_batch), float(train_lr), int(seed),
-                        int(capacity), _mode(mode), float(defensive))
+                        int(capacity), _mode(mode), float(defensive), float(val_fraction))
     cfg = AbcSmcStreamConfig(base, int(shrink_rounds), int(train_steps_warm))
     rr = (AbcSmcRound * (int(rounds) * R))()
     s = cuda_stream if cuda_stream is not None else torch.cuda.Stream()

@@ -42,7 +42,6 @@ constexpr int kD = 8;
 constexpr int kHMax = 256;
 constexpr int kKMax = 4;
 constexpr float kAlphaMax = 6.0f;
-constexpr float kLog2Pi = 1.8378770664093453f;
 constexpr uint32_t kFull = 0xFFFFFFFFu;
 
 // Master (FP32) parameters of one block: W1 [H][8], b1 [H], W2 [16][H], b2 [16].
@@ -142,6 +141,23 @@ __device__ __forceinline__ void reverse_cols(float (&v)[4])
 }
 
 __device__ __forceinline__ float soft_alpha(float ar) { return kAlphaMax * tanhf(ar / kAlphaMax); }
+
+// The base density: independent standard logistic coordinates,
+// log p(z) = -|z| - 2 log(1 + exp(-|z|)); d(-log p)/dz = tanh(z / 2). The logit
+// of a uniform variable is standard logistic, so the flow with zero
+// parameters is the uniform prior on the box.
+__device__ __forceinline__ float log_base(float z)
+{
+    const float a = fabsf(z);
+    return -a - 2.f * log1pf(expf(-a));
+}
+
+// a standard logistic draw from one random word: logit of its uniform in (0, 1)
+__device__ __forceinline__ float logistic_draw(uint32_t w)
+{
+    const float u = uniform01(w);
+    return logf(u) - log1pf(-u);
+}
 
 // One MADE on the warp's 16 rows: mu and alpha_raw in the accumulator layout.
 __device__ __forceinline__ void made_fwd(const BlockView& v, int H, const float (&x)[4], float (&mu)[4],
@@ -301,17 +317,17 @@ __global__ void __launch_bounds__(128) logq_kernel(const uint32_t* __restrict__ 
             }
             reverse_cols(x);
         }
-        const float q0 = quad_sum(-0.5f * (x[0] * x[0] + x[1] * x[1]) + ld[0] + ld[1] - jac[0] - jac[1]);
-        const float q1 = quad_sum(-0.5f * (x[2] * x[2] + x[3] * x[3]) + ld[2] + ld[3] - jac[2] - jac[3]);
+        const float q0 = quad_sum(log_base(x[0]) + log_base(x[1]) + ld[0] + ld[1] - jac[0] - jac[1]);
+        const float q1 = quad_sum(log_base(x[2]) + log_base(x[3]) + ld[2] + ld[3] - jac[2] - jac[3]);
         if (t == 0) {
-            if (r0 < n) logq[r0] = q0 - 4.f * kLog2Pi;
-            if (r1 < n) logq[r1] = q1 - 4.f * kLog2Pi;
+            if (r0 < n) logq[r0] = q0;
+            if (r1 < n) logq[r1] = q1;
         }
     }
 }
 
 // ---------------------------------------------------------------------------
-// sampling: base normals -> sequential inverse -> theta, log q(theta)
+// sampling: base draws -> sequential inverse -> theta, log q(theta)
 // ---------------------------------------------------------------------------
 template <int K>
 __global__ void __launch_bounds__(128) sample_kernel(const uint32_t* __restrict__ pub, int H, Box box,
@@ -336,15 +352,17 @@ __global__ void __launch_bounds__(128) sample_kernel(const uint32_t* __restrict_
             x[0] = ua.x; x[1] = ua.y; x[2] = ub.x; x[3] = ub.y;
         } else {
             // row r: Philox block (t / 2) of sample first + r; lane t takes words
-            // (x, y) for even t and (z, w) for odd t: one Box-Muller pair per row
+            // (x, y) for even t and (z, w) for odd t, one word per column
             const uint4 wa = rng_block_s(p, first + r0, 0, ctr3, (uint32_t)(t >> 1));
             const uint4 wb = rng_block_s(p, first + r1, 0, ctr3, (uint32_t)(t >> 1));
-            box_muller<kFast>((t & 1) ? wa.z : wa.x, (t & 1) ? wa.w : wa.y, x[0], x[1]);
-            box_muller<kFast>((t & 1) ? wb.z : wb.x, (t & 1) ? wb.w : wb.y, x[2], x[3]);
+            x[0] = logistic_draw((t & 1) ? wa.z : wa.x);
+            x[1] = logistic_draw((t & 1) ? wa.w : wa.y);
+            x[2] = logistic_draw((t & 1) ? wb.z : wb.x);
+            x[3] = logistic_draw((t & 1) ? wb.w : wb.y);
         }
         float lq[4];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) lq[e] = -0.5f * x[e] * x[e];
+        for (int e = 0; e < 4; ++e) lq[e] = log_base(x[e]);
         // blocks and passes are runtime loops (a fully unrolled 3 x 8 inverse
         // overflows the instruction cache); passes go in pairs so every
         // register index stays static: pass 2p+1 fills column 2p+1 (lane t = p,
@@ -392,8 +410,8 @@ __global__ void __launch_bounds__(128) sample_kernel(const uint32_t* __restrict_
         to_theta(box, 2 * t + 1, x[1], th[1], jac[1]);
         to_theta(box, 2 * t, x[2], th[2], jac[2]);
         to_theta(box, 2 * t + 1, x[3], th[3], jac[3]);
-        const float q0 = quad_sum(lq[0] + lq[1] - jac[0] - jac[1]) - 4.f * kLog2Pi;
-        const float q1 = quad_sum(lq[2] + lq[3] - jac[2] - jac[3]) - 4.f * kLog2Pi;
+        const float q0 = quad_sum(lq[0] + lq[1] - jac[0] - jac[1]);
+        const float q1 = quad_sum(lq[2] + lq[3] - jac[2] - jac[3]);
         if (r0 < n) *reinterpret_cast<float2*>(theta_out + 8 * r0 + 2 * t) = make_float2(th[0], th[1]);
         if (r1 < n) *reinterpret_cast<float2*>(theta_out + 8 * r1 + 2 * t) = make_float2(th[2], th[3]);
         if (t == 0 && logq_out) {
@@ -493,9 +511,9 @@ __global__ void __launch_bounds__(kGradWarps * 32) grad_kernel(const uint32_t* _
             ld1 += as[b][2] + as[b][3];
             reverse_cols(x);
         }
-        // nll = 0.5 |z|^2 + sum alpha + 4 log 2 pi
-        const float n0 = quad_sum(0.5f * (x[0] * x[0] + x[1] * x[1]) + ld0) + 4.f * kLog2Pi;
-        const float n1 = quad_sum(0.5f * (x[2] * x[2] + x[3] * x[3]) + ld1) + 4.f * kLog2Pi;
+        // nll = -log p(z) + sum alpha
+        const float n0 = quad_sum(ld0 - log_base(x[0]) - log_base(x[1]));
+        const float n1 = quad_sum(ld1 - log_base(x[2]) - log_base(x[3]));
         float contrib = (t == 0) ? (w0 * n0 + w1 * n1) : 0.f;
         float wsum = (t == 0) ? (w0 + w1) : 0.f;
 #pragma unroll
@@ -507,8 +525,9 @@ __global__ void __launch_bounds__(kGradWarps * 32) grad_kernel(const uint32_t* _
             atomicAdd(&ssum[0], contrib);
             atomicAdd(&ssum[1], wsum);
         }
-        // d/dz_K of sum w (0.5 |z|^2)
-        float gx[4] = {w0 * x[0], w0 * x[1], w1 * x[2], w1 * x[3]};
+        // d/dz_K of sum w (-log p(z)) = w tanh(z / 2)
+        float gx[4] = {w0 * tanhf(0.5f * x[0]), w0 * tanhf(0.5f * x[1]), w1 * tanhf(0.5f * x[2]),
+                       w1 * tanhf(0.5f * x[3])};
         const float wr[4] = {w0, w0, w1, w1};
 #pragma unroll
         for (int b = K - 1; b >= 0; --b) {
@@ -718,7 +737,7 @@ struct abc_maf_s {
     uint32_t* d_rows = nullptr;
     uint32_t rows_cap = 0;     // batch rows per flow
     maf::TrainSlot* d_slots = nullptr;   // [R] training data of each flow
-    maf::TrainSlot* h_slots = nullptr;   // pinned host mirror
+    float* d_best = nullptr;   // [R][n_params] best parameters under validation (allocated on first use)
     cudaGraphExec_t graph = nullptr;
     // what the captured training step was built for
     int32_t g_batch = 0;
@@ -842,16 +861,19 @@ cudaError_t launch_grad(abc_maf f, const uint32_t* rows, uint32_t batch, uint64_
      : f->K == 3 ? fn<3>(__VA_ARGS__)              \
                  : fn<4>(__VA_ARGS__))
 
-// the slot table: theta[r], w[r], n[r] for every flow (n[r] = 0: no data)
+// the slot table: theta[r], w[r], n[r] for every flow (n[r] = 0: no data).
+// The copy is from pageable memory, which the runtime has consumed when the
+// call returns, so tables can be uploaded back to back without a wait.
 cudaError_t upload_slots(abc_maf f, const float* const* theta, const float* const* w, const uint64_t* n,
                          cudaStream_t s)
 {
+    std::vector<maf::TrainSlot> h((size_t)f->R);
     for (int r = 0; r < f->R; ++r) {
-        f->h_slots[r].theta = n[r] ? theta[r] : nullptr;
-        f->h_slots[r].w = n[r] && w ? w[r] : nullptr;
-        f->h_slots[r].n = n[r];
+        h[r].theta = n[r] ? theta[r] : nullptr;
+        h[r].w = n[r] && w ? w[r] : nullptr;
+        h[r].n = n[r];
     }
-    return cudaMemcpyAsync(f->d_slots, f->h_slots, sizeof(maf::TrainSlot) * f->R, cudaMemcpyHostToDevice, s);
+    return cudaMemcpyAsync(f->d_slots, h.data(), sizeof(maf::TrainSlot) * f->R, cudaMemcpyHostToDevice, s);
 }
 
 // full-data gradients of the flows described by the slot table
@@ -911,8 +933,7 @@ abc_status abc_maf_create_multi(int32_t n_flows, int32_t n_blocks, int32_t hidde
         (e = cudaMalloc(&f->d_pub, sizeof(uint32_t) * (size_t)f->R * f->K * f->pub_words)) != cudaSuccess ||
         (e = cudaMalloc(&f->d_sums, 2 * sizeof(float) * f->R)) != cudaSuccess ||
         (e = cudaMalloc(&f->d_step, sizeof(int))) != cudaSuccess ||
-        (e = cudaMalloc(&f->d_slots, sizeof(maf::TrainSlot) * f->R)) != cudaSuccess ||
-        (e = cudaMallocHost(&f->h_slots, sizeof(maf::TrainSlot) * f->R)) != cudaSuccess)
+        (e = cudaMalloc(&f->d_slots, sizeof(maf::TrainSlot) * f->R)) != cudaSuccess)
         return fail_free(plan_cuda_fail(e, "cudaMalloc(flow)"));
     if ((e = cudaMemset(f->d_params, 0, np)) != cudaSuccess || (e = cudaMemset(f->d_m, 0, np)) != cudaSuccess ||
         (e = cudaMemset(f->d_v, 0, np)) != cudaSuccess || (e = cudaMemset(f->d_step, 0, sizeof(int))) != cudaSuccess ||
@@ -975,7 +996,7 @@ abc_status abc_maf_get_params(abc_maf f, float* params)
     return plan_ok();
 }
 
-abc_status abc_maf_sample_at(abc_maf f, int32_t flow, uint64_t n, const float* base_normals, uint64_t seed,
+abc_status abc_maf_sample_at(abc_maf f, int32_t flow, uint64_t n, const float* base_draws, uint64_t seed,
                              uint32_t stream, uint64_t first_index, float* theta_out, float* logq_out,
                              void* cuda_stream)
 {
@@ -985,16 +1006,16 @@ abc_status abc_maf_sample_at(abc_maf f, int32_t flow, uint64_t n, const float* b
     if (stream > ABC_STREAM_MAX) return plan_fail(ABC_ERR_INVALID_ARG, "stream above 2^30 - 1");
     if (n == 0) return plan_ok();
     const ModelParams p = plan_make_params(nullptr, 1, 1, seed, stream, nullptr);
-    MAF_TRY(MAF_DISPATCH(launch_sample, f, flow, n, base_normals, p, stream << 2, first_index, theta_out, logq_out,
+    MAF_TRY(MAF_DISPATCH(launch_sample, f, flow, n, base_draws, p, stream << 2, first_index, theta_out, logq_out,
                          (cudaStream_t)cuda_stream),
             "flow sample launch");
     return plan_ok();
 }
 
-abc_status abc_maf_sample(abc_maf f, uint64_t n, const float* base_normals, uint64_t seed, uint32_t stream,
+abc_status abc_maf_sample(abc_maf f, uint64_t n, const float* base_draws, uint64_t seed, uint32_t stream,
                           uint64_t first_index, float* theta_out, float* logq_out, void* cuda_stream)
 {
-    return abc_maf_sample_at(f, 0, n, base_normals, seed, stream, first_index, theta_out, logq_out, cuda_stream);
+    return abc_maf_sample_at(f, 0, n, base_draws, seed, stream, first_index, theta_out, logq_out, cuda_stream);
 }
 
 abc_status abc_maf_log_q_at(abc_maf f, int32_t flow, uint64_t n, const float* theta, float* logq_out,
@@ -1053,13 +1074,15 @@ abc_status abc_maf_adam_step(abc_maf f, float lr, float beta1, float beta2, floa
 }
 
 abc_status abc_maf_train_flows(abc_maf f, const float* const* theta, const float* const* weights, const uint64_t* n,
-                               int32_t n_steps, int32_t batch, float lr, uint64_t seed, float* loss_out,
-                               void* cuda_stream)
+                               int32_t n_steps, int32_t batch, float lr, uint64_t seed, float val_fraction,
+                               float* loss_out, void* cuda_stream)
 {
     abc_status st;
     if ((st = check(f)) != ABC_OK) return st;
     if (!theta || !n || n_steps < 0 || batch < 16)
         return plan_fail(ABC_ERR_INVALID_ARG, "need theta and n tables, n_steps >= 0 and batch >= 16");
+    if (!(val_fraction >= 0.f) || val_fraction > 0.5f)
+        return plan_fail(ABC_ERR_INVALID_ARG, "val_fraction must be in [0, 0.5]");
     uint64_t max_n = 0;
     for (int r = 0; r < f->R; ++r) {
         if (n[r] && !theta[r]) return plan_fail(ABC_ERR_INVALID_ARG, "a flow with points has theta NULL");
@@ -1067,6 +1090,23 @@ abc_status abc_maf_train_flows(abc_maf f, const float* const* theta, const float
         max_n = n[r] > max_n ? n[r] : max_n;
     }
     if (max_n == 0) return plan_fail(ABC_ERR_INVALID_ARG, "no flow has points");
+    // the last floor(val_fraction n) points of a flow validate, the rest train
+    const int R = f->R;
+    std::vector<const float*> th_tr(theta, theta + R), w_tr((size_t)R, nullptr), th_va((size_t)R, nullptr),
+        w_va((size_t)R, nullptr);
+    std::vector<uint64_t> n_tr(n, n + R), n_va((size_t)R, 0);
+    bool validate = false;
+    for (int r = 0; r < R; ++r) {
+        w_tr[r] = weights ? weights[r] : nullptr;
+        const uint64_t v = val_fraction > 0.f && n[r] >= 20 ? (uint64_t)std::floor(val_fraction * (double)n[r]) : 0;
+        if (v > 0) {
+            n_va[r] = v;
+            n_tr[r] = n[r] - v;
+            th_va[r] = theta[r] + 8 * n_tr[r];
+            w_va[r] = w_tr[r] ? w_tr[r] + n_tr[r] : nullptr;
+            validate = true;
+        }
+    }
     cudaStream_t s = (cudaStream_t)cuda_stream;
     if (!s && n_steps > 0) return plan_fail(ABC_ERR_INVALID_ARG, "training needs a non-default stream");
     if ((uint32_t)batch > f->rows_cap) {
@@ -1080,7 +1120,7 @@ abc_status abc_maf_train_flows(abc_maf f, const float* const* theta, const float
             f->graph = nullptr;
         }
     }
-    MAF_TRY(upload_slots(f, theta, weights, n, s), "cudaMemcpyAsync(slots)");
+    MAF_TRY(upload_slots(f, th_tr.data(), w_tr.data(), n_tr.data(), s), "cudaMemcpyAsync(slots)");
     // fresh Adam moments for this training run
     const size_t np = sizeof(float) * f->n_params * f->R;
     MAF_TRY(cudaMemsetAsync(f->d_m, 0, np, s), "cudaMemsetAsync");
@@ -1122,8 +1162,64 @@ abc_status abc_maf_train_flows(abc_maf f, const float* const* theta, const float
             f->g_seed = seed;
             f->g_stream = s;
         }
-        for (int32_t i = 0; i < n_steps; ++i) MAF_TRY(cudaGraphLaunch(f->graph, s), "cudaGraphLaunch");
     }
+    if (validate) {
+        // early stopping: every kCheck steps the validation loss of each flow;
+        // a flow keeps its best parameters and stops after kPatience checks
+        // without improvement
+        constexpr int kCheck = 25, kPatience = 3;
+        const size_t npb = sizeof(float) * f->n_params;
+        if (!f->d_best) MAF_TRY(cudaMalloc(&f->d_best, npb * R), "cudaMalloc(best parameters)");
+        uint64_t max_va = 0;
+        for (int r = 0; r < R; ++r) max_va = n_va[r] > max_va ? n_va[r] : max_va;
+        std::vector<float> sums(2 * (size_t)R), best((size_t)R, INFINITY);
+        std::vector<int> bad((size_t)R, 0);
+        auto val_losses = [&]() -> abc_status {
+            MAF_TRY(upload_slots(f, th_va.data(), w_va.data(), n_va.data(), s), "cudaMemcpyAsync(slots)");
+            MAF_TRY(full_gradient(f, max_va, s), "validation loss");
+            MAF_TRY(cudaMemcpyAsync(sums.data(), f->d_sums, sizeof(float) * sums.size(), cudaMemcpyDeviceToHost, s),
+                    "cudaMemcpyAsync(sums)");
+            MAF_TRY(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+            for (int r = 0; r < R; ++r) {
+                if (n_va[r] == 0 || sums[2 * r + 1] <= 0.f) continue;
+                const float vl = sums[2 * r] / sums[2 * r + 1];
+                if (vl < best[r]) {
+                    best[r] = vl;
+                    bad[r] = 0;
+                    MAF_TRY(cudaMemcpyAsync(f->d_best + (size_t)r * f->n_params, f->d_params + (size_t)r * f->n_params,
+                                            npb, cudaMemcpyDeviceToDevice, s),
+                            "cudaMemcpyAsync(best parameters)");
+                } else if (++bad[r] >= kPatience && n_tr[r] > 0) {
+                    n_tr[r] = 0;   // this flow stops training
+                }
+            }
+            MAF_TRY(upload_slots(f, th_tr.data(), w_tr.data(), n_tr.data(), s), "cudaMemcpyAsync(slots)");
+            return ABC_OK;
+        };
+        if ((st = val_losses()) != ABC_OK) return st;
+        for (int32_t done = 0; done < n_steps;) {
+            bool active = false;
+            for (int r = 0; r < R; ++r) active = active || n_tr[r] > 0;
+            if (!active) break;
+            const int32_t k = n_steps - done < kCheck ? n_steps - done : kCheck;
+            for (int32_t i = 0; i < k; ++i) MAF_TRY(cudaGraphLaunch(f->graph, s), "cudaGraphLaunch");
+            done += k;
+            if ((st = val_losses()) != ABC_OK) return st;
+        }
+        // the kept parameters: each validated flow's best
+        for (int r = 0; r < R; ++r)
+            if (n_va[r] > 0)
+                MAF_TRY(cudaMemcpyAsync(f->d_params + (size_t)r * f->n_params, f->d_best + (size_t)r * f->n_params, npb,
+                                        cudaMemcpyDeviceToDevice, s),
+                        "cudaMemcpyAsync(restore parameters)");
+        MAF_TRY(publish(f, s), "publish");
+        MAF_TRY(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+        if (loss_out)
+            for (int r = 0; r < R; ++r) loss_out[r] = n_va[r] > 0 && best[r] < INFINITY ? best[r] : 0.f;
+        return plan_ok();
+    }
+    if (n_steps > 0)
+        for (int32_t i = 0; i < n_steps; ++i) MAF_TRY(cudaGraphLaunch(f->graph, s), "cudaGraphLaunch");
     if (loss_out) {
         MAF_TRY(full_gradient(f, max_n, s), "flow loss");
         std::vector<float> sums(2 * (size_t)f->R);
@@ -1150,7 +1246,7 @@ abc_status abc_maf_train(abc_maf f, uint64_t n, const float* theta, const float*
     th[0] = theta;
     w[0] = weights;
     nn[0] = n;
-    st = abc_maf_train_flows(f, th.data(), w.data(), nn.data(), n_steps, batch, lr, seed,
+    st = abc_maf_train_flows(f, th.data(), w.data(), nn.data(), n_steps, batch, lr, seed, 0.f,
                              loss_out ? loss.data() : nullptr, cuda_stream);
     if (st == ABC_OK && loss_out) *loss_out = loss[0];
     return st;
@@ -1169,7 +1265,7 @@ abc_status abc_maf_destroy(abc_maf f)
     cudaFree(f->d_step);
     cudaFree(f->d_rows);
     cudaFree(f->d_slots);
-    if (f->h_slots) cudaFreeHost(f->h_slots);
+    cudaFree(f->d_best);
     delete f;
     return plan_ok();
 }

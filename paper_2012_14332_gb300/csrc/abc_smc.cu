@@ -5,6 +5,7 @@
 // (abc_batch.cu) reading the proposals from device memory.
 #include <algorithm>
 #include <cmath>
+#include <numeric>
 #include <cstdint>
 #include <vector>
 
@@ -120,6 +121,22 @@ __global__ void weight_kernel(const float* __restrict__ lw, uint64_t m, WeightSc
     }
 }
 
+// training set of a round: dst[j] = src[(a j + b) mod m] for theta and weights
+// (a coprime to m, so a permutation): the held-out tail of the training set is
+// then a spread-out subset of the round, not its highest sample indices
+__global__ void permute_kernel(const float* __restrict__ theta, const float* __restrict__ w, uint64_t m, uint64_t a,
+                               uint64_t b, float* __restrict__ theta_dst, float* __restrict__ w_dst)
+{
+    const uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= m) return;
+    const uint64_t i = (a * j + b) % m;
+    const float4* src = reinterpret_cast<const float4*>(theta + 8 * i);
+    float4* dst = reinterpret_cast<float4*>(theta_dst + 8 * j);
+    dst[0] = src[0];
+    dst[1] = src[1];
+    w_dst[j] = w[i];
+}
+
 __global__ void scale_kernel(double* __restrict__ w, uint64_t m, double f)
 {
     const uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -157,6 +174,19 @@ using abcgb::plan_fail;
         if (_s != ABC_OK) return _s;        \
     } while (0)
 
+// Shuffle a round's m accepted samples and their training weights into a
+// training set (permute_kernel). m < 2^32.
+static abc_status shuffled_training_set(const float* theta, const float* w, uint64_t m, uint64_t salt,
+                                        float* theta_dst, float* w_dst, cudaStream_t s)
+{
+    uint64_t a = (uint64_t)(0.6180339887498949 * (double)m) | 1u;
+    while (std::gcd(a, m) != 1) a += 2;
+    const uint64_t b = (salt * 0x9E3779B97F4A7C15ull) % m;
+    permute_kernel<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(theta, w, m, a % m ? a % m : 1, b, theta_dst, w_dst);
+    SMC_TRY(cudaGetLastError(), "permute launch");
+    return ABC_OK;
+}
+
 // Weights of a round's m accepted samples (logq: the round's proposal log
 // densities, NULL for prior draws): float training weights v_j into w_train,
 // optionally v_j in double into w_exact and the unnormalised weights of the
@@ -187,7 +217,7 @@ extern "C" abc_status abc_smc_run(const abc_prior_box* prior, const int32_t* obs
     if (!cfg || !rounds_out || !n_out) return plan_fail(ABC_ERR_INVALID_ARG, "cfg, rounds_out and n_out are required");
     if (cfg->rounds < 1 || cfg->sims_per_round == 0 || !(cfg->eps0 >= 0.0) || !(cfg->eps_factor > 0.0) ||
         cfg->eps_factor > 1.0 || !(cfg->ess_min >= 0.0) || cfg->capacity == 0 || !(cfg->defensive >= 0.0) ||
-        cfg->defensive >= 1.0)
+        cfg->defensive >= 1.0 || !(cfg->val_fraction >= 0.0) || cfg->val_fraction > 0.5)
         return plan_fail(ABC_ERR_INVALID_ARG, "bad sequential ABC configuration");
     cudaStream_t s = (cudaStream_t)cuda_stream;
     if (!s) return plan_fail(ABC_ERR_INVALID_ARG, "sequential ABC needs a non-default stream");
@@ -210,6 +240,9 @@ extern "C" abc_status abc_smc_run(const abc_prior_box* prior, const int32_t* obs
     WeightScratch* d_ws = nullptr;
     SMC_TRY(cudaMalloc(&d_ws, sizeof(WeightScratch)), "cudaMalloc(weight scratch)");
     gd.dev.push_back(d_ws);
+    float* d_wround = nullptr;
+    SMC_TRY(cudaMalloc(&d_wround, sizeof(float) * cap), "cudaMalloc(round weights)");
+    gd.dev.push_back(d_wround);
     float* d_train = nullptr;
     SMC_TRY(cudaMalloc(&d_train, sizeof(float) * 8 * cap), "cudaMalloc(training set)");
     gd.dev.push_back(d_train);
@@ -276,7 +309,7 @@ extern "C" abc_status abc_smc_run(const abc_prior_box* prior, const int32_t* obs
         // importance weights prior / q_mix of the kept accepted samples
         double sw = 0.0, sw2 = 0.0;
         if (m > 0) {
-            SMC_ST(round_weights(use_flow ? d_logq : nullptr, acc_idx, first, m, log_prior, d_acc_logq, d_w,
+            SMC_ST(round_weights(use_flow ? d_logq : nullptr, acc_idx, first, m, log_prior, d_acc_logq, d_wround,
                                  last ? weight_out : nullptr, nullptr, 0, d_ws, s, &sw, &sw2));
             R.ess_fraction = sw2 > 0.0 ? sw * sw / sw2 / (double)m : 0.0;
         }
@@ -299,11 +332,13 @@ extern "C" abc_status abc_smc_run(const abc_prior_box* prior, const int32_t* obs
         } else {
             const bool trainable = m >= 64 && R.ess_fraction >= cfg->ess_min;
             if (trainable) {
-                SMC_TRY(cudaMemcpyAsync(d_train, acc_theta, sizeof(float) * 8 * m, cudaMemcpyDeviceToDevice, s),
-                        "cudaMemcpyAsync(training set)");
+                SMC_ST(shuffled_training_set(acc_theta, d_wround, m, cfg->seed + (uint64_t)r, d_train, d_w, s));
                 float loss = 0.f;
-                SMC_ST(abc_maf_train(gd.flow, m, d_train, d_w, cfg->train_steps, cfg->train_batch, cfg->train_lr,
-                                     cfg->seed + 7919 * (uint64_t)r, &loss, s));
+                const float* tt = d_train;
+                const float* tw = d_w;
+                const uint64_t tn = m;
+                SMC_ST(abc_maf_train_flows(gd.flow, &tt, &tw, &tn, cfg->train_steps, cfg->train_batch, cfg->train_lr,
+                                           cfg->seed + 7919 * (uint64_t)r, (float)cfg->val_fraction, &loss, s));
                 R.train_loss = loss;
             }
             SMC_TRY(cudaEventRecord(gd.ev[3], s), "cudaEventRecord");
@@ -351,7 +386,7 @@ extern "C" abc_status abc_smc_run_regions(const abc_prior_box* prior, abc_smc_re
     if (R < 1 || R > ABC_MAX_REGIONS) return plan_fail(ABC_ERR_INVALID_ARG, "n_regions must be in [1, ABC_MAX_REGIONS]");
     if (cfg->rounds < 1 || cfg->sims_per_round == 0 || !(cfg->eps_factor > 0.0) || cfg->eps_factor > 1.0 ||
         !(cfg->ess_min >= 0.0) || cfg->capacity == 0 || !(cfg->defensive >= 0.0) || cfg->defensive >= 1.0 ||
-        scfg->shrink_rounds < 1 || scfg->shrink_rounds > cfg->rounds || scfg->train_steps_warm < 0 ||
+        !(cfg->val_fraction >= 0.0) || cfg->val_fraction > 0.5 || scfg->shrink_rounds < 1 || scfg->shrink_rounds > cfg->rounds || scfg->train_steps_warm < 0 ||
         cfg->train_steps < 0)
         return plan_fail(ABC_ERR_INVALID_ARG, "bad multi-region sequential ABC configuration");
     for (int32_t g = 0; g < R; ++g) {
@@ -380,6 +415,9 @@ extern "C" abc_status abc_smc_run_regions(const abc_prior_box* prior, abc_smc_re
     WeightScratch* d_ws = nullptr;
     SMC_TRY(cudaMalloc(&d_ws, sizeof(WeightScratch)), "cudaMalloc(weight scratch)");
     gd.dev.push_back(d_ws);
+    float* d_wround = nullptr;
+    SMC_TRY(cudaMalloc(&d_wround, sizeof(float) * cap), "cudaMalloc(round weights)");
+    gd.dev.push_back(d_wround);
     SMC_TRY(cudaMalloc(&d_w, sizeof(float) * cap * R), "cudaMalloc(weights)");
     gd.dev.push_back(d_w);
     SMC_TRY(cudaMalloc(&d_train, sizeof(float) * 8 * cap * R), "cudaMalloc(training sets)");
@@ -470,7 +508,7 @@ extern "C" abc_status abc_smc_run_regions(const abc_prior_box* prior, abc_smc_re
             float* tw = d_w + (size_t)g * cap;
             double sw = 0.0, sw2 = 0.0;
             SMC_ST(round_weights(use_flow[g] ? d_logq + (size_t)g * N : nullptr, acc_idx, first, m, log_prior,
-                                 d_acc_logq, tw, nullptr, k ? G.weight_out + G.n_out : nullptr, k, d_ws, s, &sw,
+                                 d_acc_logq, d_wround, nullptr, k ? G.weight_out + G.n_out : nullptr, k, d_ws, s, &sw,
                                  &sw2));
             Rr[g].ess_fraction = sw2 > 0.0 ? sw * sw / sw2 / (double)m : 0.0;
             if (pool) {
@@ -487,8 +525,8 @@ extern "C" abc_status abc_smc_run_regions(const abc_prior_box* prior, abc_smc_re
             // this round's weighted accepts train the region's next proposal
             if (r + 1 < cfg->rounds && m >= 64 && Rr[g].ess_fraction >= cfg->ess_min) {
                 float* tt = d_train + (size_t)g * 8 * cap;
-                SMC_TRY(cudaMemcpyAsync(tt, acc_theta, sizeof(float) * 8 * m, cudaMemcpyDeviceToDevice, s),
-                        "cudaMemcpyAsync(training set)");
+                SMC_ST(shuffled_training_set(acc_theta, d_wround, m, cfg->seed + 131 * (uint64_t)r + (uint64_t)g, tt,
+                                             tw, s));
                 trainable[g] = 1;
                 tr_theta[g] = tt;
                 tr_w[g] = tw;
@@ -499,7 +537,8 @@ extern "C" abc_status abc_smc_run_regions(const abc_prior_box* prior, abc_smc_re
         if (any_train) {
             const int32_t steps = trained_once ? scfg->train_steps_warm : cfg->train_steps;
             SMC_ST(abc_maf_train_flows(gd.flows, tr_theta.data(), tr_w.data(), tr_n.data(), steps, cfg->train_batch,
-                                       cfg->train_lr, cfg->seed + 7919 * (uint64_t)r, losses.data(), s));
+                                       cfg->train_lr, cfg->seed + 7919 * (uint64_t)r, (float)cfg->val_fraction,
+                                       losses.data(), s));
             trained_once = true;
             for (int32_t g = 0; g < R; ++g)
                 if (trainable[g]) Rr[g].train_loss = losses[g];
