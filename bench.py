@@ -274,7 +274,7 @@ def bench_learned(abc, torch, w, prior_value, peaks):
     eps0 = w["eps"] / factor ** (rounds - 1)
     info, th, wt, dist = abc.abc_smc_run(w["observed"], w["P"], eps0, rounds=rounds, sims_per_round=n,
                                          eps_factor=factor, flow_blocks=3, flow_hidden=256, train_steps=500,
-                                         train_batch=4096, train_lr=1e-3, seed=w["seed"] + 17, capacity=1 << 18,
+                                         train_batch=4096, train_lr=1e-3, seed=w["seed"] + 17, capacity=n,
                                          mode="fast")
     last = info[-1]
     ms = last["ms_propose"] + last["ms_simulate"]

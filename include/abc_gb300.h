@@ -309,6 +309,16 @@ abc_status abc_maf_create_multi(int32_t n_flows, int32_t n_blocks, int32_t hidde
                                 abc_maf* maf_out);
 int32_t abc_maf_flow_count(abc_maf maf);
 
+/* Broadened proposal: sampling and density evaluation (abc_maf_sample*,
+ * abc_maf_log_q*) use the base z = tau * (standard logistic), density
+ * sum_j (log p(z_j / tau) - log tau), for every flow of the object; training
+ * still fits the flow with tau = 1 (maximum likelihood). tau in [0.5, 4],
+ * default 1. A proposal fitted by maximum likelihood to its own weighted
+ * output tends to miss the target's tails round after round, which leaves the
+ * self-normalised estimates of a finite run biased toward the proposal's
+ * bulk; a base broader than the fitted one keeps covering them. */
+abc_status abc_maf_set_proposal_scale(abc_maf maf, float tau);
+
 /* Random initial parameters: W1 ~ N(0, scale^2 / 8), W2 ~ N(0, scale^2 / hidden),
  * zero biases (so the ReLU units start active and the flow near the base
  * density), from a host generator seeded with `seed`; resets Adam. */
@@ -370,8 +380,8 @@ abc_status abc_maf_train(abc_maf maf, uint64_t n, const float* theta, const floa
  * n[r] < 2^32; a flow with n[r] = 0 is left as it is. Each step draws `batch`
  * rows per flow and updates all flows with one gradient launch (one CTA row of
  * the grid per flow) and one Adam launch. With val_fraction in (0, 0.5], the
- * last floor(val_fraction n[r]) points of each flow with n[r] >= 20 are held
- * out: every 25 steps each flow's validation loss is measured, a flow keeps
+ * last min(floor(val_fraction n[r]), 8192) points of each flow with
+ * n[r] >= 20 are held out: every 25 steps each flow's validation loss is measured, a flow keeps
  * the parameters of its best validation loss and stops training after three
  * checks without improvement (early stopping against overfitting a small
  * round); n_steps is then an upper bound. loss_out HOST float [n_flows] or
@@ -412,7 +422,7 @@ typedef struct {
     int32_t train_batch;      /* rows per step (>= 16) */
     float train_lr;
     uint64_t seed;
-    uint64_t capacity;        /* accepted samples kept per round */
+    uint64_t capacity;        /* accepted samples kept per round: >= sims_per_round, so no round is truncated */
     abc_mode mode;
     double defensive;         /* prior fraction of a flow round's proposals, in [0, 1) (e.g. 0.1) */
     double val_fraction;      /* held-out fraction for early stopping of the training, in [0, 0.5] (e.g. 0.1) */
@@ -451,9 +461,12 @@ abc_status abc_smc_run(const abc_prior_box* prior, const int32_t* observed, int3
  * that accepted fewer than 64) falls back to the prior for its next round, as
  * in abc_smc_run (defensive mixture included). Every sample accepted at the
  * region's final eps (all rounds from shrink_rounds - 1 on) is pooled in the
- * region's output buffers with its unnormalised weight prior / q_mix (1 for
- * prior rounds): the weighted pool estimates the ABC posterior at eps_g
- * (Eq. 7). Region g simulates with (seed, stream g, index r *
+ * region's output buffers. Its weight is its round's self-normalised
+ * importance weight (prior / q_mix) times the round's effective sample size,
+ * so each round's estimate counts in proportion to its ESS; the weighted pool
+ * estimates the ABC posterior at eps_g (Eq. 7). From the first round at the
+ * final eps on, each region's flow trains on (up to capacity points of) the
+ * whole pool instead of the last round alone. Region g simulates with (seed, stream g, index r *
  * sims_per_round + j) and its flow draws with (seed, stream n_regions + g,
  * the same index). The first training of the flows runs base.train_steps
  * Adam steps, later ones (warm starts) train_steps_warm. */
@@ -463,7 +476,7 @@ typedef struct {
     int64_t N_pop;
     double eps;               /* the region's final tolerance */
     float* theta_out;         /* DEVICE float [capacity][8]: pooled samples at eps */
-    double* weight_out;       /* DEVICE double [capacity]: their unnormalised weights */
+    double* weight_out;       /* DEVICE double [capacity]: their weights (ESS-combined across rounds) */
     double* dist_out;         /* DEVICE double [capacity] */
     uint64_t capacity;
     uint64_t n_pooled;        /* out: accepted at eps over all rounds (may exceed capacity) */
@@ -472,7 +485,8 @@ typedef struct {
 
 typedef struct {
     abc_smc_config base;      /* rounds, sims_per_round (per region), eps_factor, ess_min, flow shape and
-                                 training, seed, capacity (per round and region), mode, defensive; eps0 unused */
+                                 training, seed, capacity (per round and region, >= sims_per_round), mode,
+                                 defensive, val_fraction; eps0 unused */
     int32_t shrink_rounds;    /* 1..rounds */
     int32_t train_steps_warm; /* Adam steps of every later training */
 } abc_smc_stream_config;

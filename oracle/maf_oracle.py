@@ -91,8 +91,9 @@ def made(x, p, M1, M2, bf16=False):
     return mu, alpha, araw, a1, h
 
 
-def forward(y, params, bf16=False):
-    """y [N, D] -> (z [N, D] after the last reversal, log q_y [N], per-block caches)."""
+def forward(y, params, bf16=False, tau=1.0):
+    """y [N, D] -> (z [N, D] after the last reversal, log q_y [N], per-block caches).
+    tau > 1 evaluates the broadened proposal whose base is tau * (standard logistic)."""
     H = params[0]["W1"].shape[0]
     M1, M2 = masks(H)
     x = np.asarray(y, dtype=np.float64)
@@ -104,17 +105,17 @@ def forward(y, params, bf16=False):
         logdet -= alpha.sum(axis=1)
         caches.append(dict(x=x, mu=mu, alpha=alpha, araw=araw, a1=a1, h=h, z=z))
         x = z[:, ::-1]
-    logq = log_base(x) + logdet
+    logq = log_base(x / tau) - D * np.log(tau) + logdet
     return x, logq, caches
 
 
-def inverse(u, params, bf16=False):
+def inverse(u, params, bf16=False, tau=1.0):
     """Base draws u [N, D] (standard logistic) -> (y [N, D], log q_y [N]) by the
-    sequential inverse."""
+    sequential inverse of the flow whose base is tau * (standard logistic)."""
     H = params[0]["W1"].shape[0]
     M1, M2 = masks(H)
-    x = np.asarray(u, dtype=np.float64)
-    logq = log_base(x)
+    x = tau * np.asarray(u, dtype=np.float64)
+    logq = log_base(x / tau) - D * np.log(tau)
     for p in reversed(params):
         z = x[:, ::-1]
         xin = np.zeros_like(z)
@@ -148,9 +149,9 @@ def log_jacobian_y(y, lo, hi):
     return (np.log(w) - np.logaddexp(0, -y) - np.logaddexp(0, y)).sum(axis=1)
 
 
-def log_q_theta(theta, params, lo, hi, bf16=False):
+def log_q_theta(theta, params, lo, hi, bf16=False, tau=1.0):
     y = to_y(theta, lo, hi)
-    _, logq_y, _ = forward(y, params, bf16)
+    _, logq_y, _ = forward(y, params, bf16, tau)
     return logq_y - log_jacobian_y(y, lo, hi)
 
 

@@ -162,6 +162,8 @@ def load(path=None):
         L.abc_maf_create_multi.argtypes = [i32, i32, i32, box, ctypes.POINTER(pp)]
         L.abc_maf_flow_count.argtypes = [pp]
         L.abc_maf_flow_count.restype = ctypes.c_int32
+        L.abc_maf_set_proposal_scale.argtypes = [pp, ctypes.c_float]
+        L.abc_maf_set_proposal_scale.restype = ctypes.c_int
         L.abc_maf_sample_at.argtypes = [pp, i32, u64, vp, u64, u32, u64, vp, vp, vp]
         L.abc_maf_log_q_at.argtypes = [pp, i32, u64, vp, vp, vp]
         L.abc_maf_train_flows.argtypes = [pp, vp, vp, vp, i32, i32, ctypes.c_float, u64, ctypes.c_float, vp, vp]
@@ -570,6 +572,10 @@ class Flow:
     def init_random(self, seed=0, scale=0.3):
         _check(self._L, self._L.abc_maf_init_random(self._h, int(seed), float(scale)))
 
+    def set_proposal_scale(self, tau):
+        """Sample and evaluate with the base broadened by tau (training is unaffected)."""
+        _check(self._L, self._L.abc_maf_set_proposal_scale(self._h, float(tau)))
+
     def set_params(self, params):
         """params: [n_params] (one flow) or [n_flows, n_params]."""
         v = np.ascontiguousarray(np.asarray(params, dtype=np.float32).ravel())
@@ -714,6 +720,10 @@ def abc_maf_flow_count(flow):
     return flow.n_flows
 
 
+def abc_maf_set_proposal_scale(flow, tau):
+    flow.set_proposal_scale(tau)
+
+
 def abc_maf_sample_at(flow, r, n, **kw):
     return flow.sample(n, flow=r, **kw)
 
@@ -729,13 +739,15 @@ def abc_maf_train_flows(flow, thetas, weights=None, **kw):
 
 def abc_smc_run(observed, N_pop, eps0, rounds=5, sims_per_round=1 << 22, eps_factor=0.7, ess_min=0.1,
                 flow_blocks=3, flow_hidden=256, train_steps=500, train_batch=1024, train_lr=1e-3, seed=0,
-                capacity=1 << 16, mode="fast", defensive=0.1, val_fraction=0.1, lo=PAPER_LO, hi=PAPER_HI,
+                capacity=None, mode="fast", defensive=0.1, val_fraction=0.1, lo=PAPER_LO, hi=PAPER_HI,
                 cuda_stream=None):
     """Sequential ABC with the learned flow proposal. Returns (rounds: list of
     dicts, theta [m, 8], weights [m] (f64, sum 1), dist [m]) of the last round."""
     L = load()
     obs, obs_p = _host_i32(observed)
     T = obs.shape[1] - 1
+    if capacity is None:
+        capacity = sims_per_round
     cfg = AbcSmcConfig(int(rounds), int(sims_per_round), float(eps0), float(eps_factor), float(ess_min),
                        int(flow_blocks), int(flow_hidden), int(train_steps), int(train_batch), float(train_lr),
                        int(seed), int(capacity), _mode(mode), float(defensive), float(val_fraction))
@@ -758,15 +770,18 @@ def abc_smc_run(observed, N_pop, eps0, rounds=5, sims_per_round=1 << 22, eps_fac
 
 def abc_smc_run_regions(regions, rounds=16, shrink_rounds=4, sims_per_round=1 << 20, eps_factor=0.7, ess_min=0.1,
                         flow_blocks=3, flow_hidden=256, train_steps=500, train_steps_warm=100, train_batch=1024,
-                        train_lr=1e-3, seed=0, capacity=1 << 16, mode="fast", defensive=0.1, val_fraction=0.1,
+                        train_lr=1e-3, seed=0, capacity=None, mode="fast", defensive=0.1, val_fraction=0.1,
                         lo=PAPER_LO, hi=PAPER_HI, cuda_stream=None):
     """Sequential ABC with one flow proposal per region, all regions in one
     batched launch per round. regions: list of dicts with observed (host int32
     [3, T+1]), N_pop, eps (final) and pool (samples kept at the final eps).
     Returns (rounds [rounds][n_regions] of dicts, per region a tuple
-    (theta [m, 8], weights [m] f64 unnormalised, dist [m], n_pooled))."""
+    (theta [m, 8], weights [m] f64 (a round's normalised weights times its
+    ESS), dist [m], n_pooled))."""
     L = load()
     R = len(regions)
+    if capacity is None:
+        capacity = sims_per_round
     dev = torch.device("cuda", torch.cuda.current_device())
     keep, outs = [], []
     arr = (AbcSmcRegion * R)()

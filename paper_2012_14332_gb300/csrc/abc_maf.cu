@@ -281,10 +281,12 @@ __global__ void publish_kernel(const float* __restrict__ master, uint32_t* __res
 // ---------------------------------------------------------------------------
 // density: log q(theta)
 // ---------------------------------------------------------------------------
+// The proposal may use a broadened base, z = tau * (standard logistic), with
+// density log p(z / tau) - log tau per coordinate (tau = 1: the trained flow).
 template <int K>
 __global__ void __launch_bounds__(128) logq_kernel(const uint32_t* __restrict__ pub, int H, Box box,
-                                                   const float* __restrict__ theta, uint64_t n,
-                                                   float* __restrict__ logq)
+                                                   const float* __restrict__ theta, uint64_t n, float inv_tau,
+                                                   float log_tau, float* __restrict__ logq)
 {
     extern __shared__ __align__(16) uint32_t sm[];
     const Layout L = layout(H);
@@ -317,8 +319,10 @@ __global__ void __launch_bounds__(128) logq_kernel(const uint32_t* __restrict__ 
             }
             reverse_cols(x);
         }
-        const float q0 = quad_sum(log_base(x[0]) + log_base(x[1]) + ld[0] + ld[1] - jac[0] - jac[1]);
-        const float q1 = quad_sum(log_base(x[2]) + log_base(x[3]) + ld[2] + ld[3] - jac[2] - jac[3]);
+        const float q0 = quad_sum(log_base(x[0] * inv_tau) + log_base(x[1] * inv_tau) + ld[0] + ld[1] - jac[0] -
+                                  jac[1] - 2.f * log_tau);
+        const float q1 = quad_sum(log_base(x[2] * inv_tau) + log_base(x[3] * inv_tau) + ld[2] + ld[3] - jac[2] -
+                                  jac[3] - 2.f * log_tau);
         if (t == 0) {
             if (r0 < n) logq[r0] = q0;
             if (r1 < n) logq[r1] = q1;
@@ -332,8 +336,9 @@ __global__ void __launch_bounds__(128) logq_kernel(const uint32_t* __restrict__ 
 template <int K>
 __global__ void __launch_bounds__(128) sample_kernel(const uint32_t* __restrict__ pub, int H, Box box,
                                                      const float* __restrict__ u_in, const __grid_constant__ ModelParams p,
-                                                     uint32_t ctr3, uint64_t first, uint64_t n,
-                                                     float* __restrict__ theta_out, float* __restrict__ logq_out)
+                                                     uint32_t ctr3, uint64_t first, uint64_t n, float tau,
+                                                     float log_tau, float* __restrict__ theta_out,
+                                                     float* __restrict__ logq_out)
 {
     extern __shared__ __align__(16) uint32_t sm[];
     const Layout L = layout(H);
@@ -362,7 +367,10 @@ __global__ void __launch_bounds__(128) sample_kernel(const uint32_t* __restrict_
         }
         float lq[4];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) lq[e] = log_base(x[e]);
+        for (int e = 0; e < 4; ++e) {
+            lq[e] = log_base(x[e]) - log_tau;
+            x[e] *= tau;
+        }
         // blocks and passes are runtime loops (a fully unrolled 3 x 8 inverse
         // overflows the instruction cache); passes go in pairs so every
         // register index stays static: pass 2p+1 fills column 2p+1 (lane t = p,
@@ -424,7 +432,12 @@ __global__ void __launch_bounds__(128) sample_kernel(const uint32_t* __restrict_
 // ---------------------------------------------------------------------------
 // gradient of sum_r w_r (-log q_y(y_r)) (unnormalised; Adam divides by sum w)
 // ---------------------------------------------------------------------------
-constexpr int kGradWarps = 4;
+// warps per CTA of the gradient kernel: 4, or 16 when a step has enough
+// tiles for more than two waves of 4-warp CTAs (one CTA fits per SM, so the
+// wider CTA hides four times the latency and flushes a quarter as many
+// per-CTA gradient sums)
+constexpr int kGradWarpsNarrow = 4;
+constexpr int kGradWarpsWide = 16;
 constexpr int kStage = 12;   // staging row stride in 32-bit words (8 data + 4 pad)
 
 struct WarpStage {
@@ -448,8 +461,8 @@ struct TrainSlot {
 
 // Flow f = blockIdx.y reads slots[f]: with rows, the batch of rows
 // rows[f * batch ..] (none if the flow has no points), else all its n points.
-template <int K>
-__global__ void __launch_bounds__(kGradWarps * 32) grad_kernel(const uint32_t* __restrict__ pub, int H, Box box,
+template <int K, int W>
+__global__ void __launch_bounds__(W * 32) grad_kernel(const uint32_t* __restrict__ pub, int H, Box box,
                                                                const TrainSlot* __restrict__ slots,
                                                                const uint32_t* __restrict__ rows_all, uint32_t batch,
                                                                float* __restrict__ grad, float* __restrict__ sums)
@@ -479,8 +492,8 @@ __global__ void __launch_bounds__(kGradWarps * 32) grad_kernel(const uint32_t* _
     WarpStage& st = stages[threadIdx.x >> 5];
     const uint64_t tiles = (n_rows + 15) / 16;
     const int hw = H / 2 + 4;
-    for (uint64_t tile = (uint64_t)blockIdx.x * kGradWarps + (threadIdx.x >> 5); tile < tiles;
-         tile += (uint64_t)gridDim.x * kGradWarps) {
+    for (uint64_t tile = (uint64_t)blockIdx.x * W + (threadIdx.x >> 5); tile < tiles;
+         tile += (uint64_t)gridDim.x * W) {
         const uint64_t q0 = tile * 16 + g, q1 = q0 + 8;
         const uint64_t i0 = q0 < n_rows ? (rows ? rows[q0] : q0) : 0;
         const uint64_t i1 = q1 < n_rows ? (rows ? rows[q1] : q1) : 0;
@@ -727,6 +740,7 @@ struct abc_maf_s {
     maf::Box box{};
     int64_t n_params = 0;      // per flow
     int pub_words = 0;         // per block
+    float tau = 1.f;           // base scale of sampling and density (training fits tau = 1)
     float* d_params = nullptr; // [R][n_params] FP32 master parameters
     float* d_m = nullptr;
     float* d_v = nullptr;
@@ -756,10 +770,10 @@ namespace {
 
 size_t fwd_smem(const abc_maf_s* f) { return sizeof(uint32_t) * (size_t)f->K * maf::layout(f->H).fwd_words; }
 
-size_t grad_smem(const abc_maf_s* f)
+size_t grad_smem(const abc_maf_s* f, int warps)
 {
     return sizeof(uint32_t) * (size_t)f->K * maf::layout(f->H).words +
-           sizeof(float) * (size_t)f->K * maf::master_block(f->H) + sizeof(maf::WarpStage) * maf::kGradWarps;
+           sizeof(float) * (size_t)f->K * maf::master_block(f->H) + sizeof(maf::WarpStage) * warps;
 }
 
 abc_status check(abc_maf f)
@@ -822,7 +836,8 @@ cudaError_t launch_logq(abc_maf f, int r, uint64_t n, const float* theta, float*
     if (e != cudaSuccess) return e;
     const uint64_t tiles = (n + 15) / 16;
     const int grid = fill_grid(maf::logq_kernel<K>, 128, smem, (tiles + 3) / 4);
-    maf::logq_kernel<K><<<grid, 128, smem, s>>>(flow_pub(f, r), f->H, f->box, theta, n, logq);
+    maf::logq_kernel<K><<<grid, 128, smem, s>>>(flow_pub(f, r), f->H, f->box, theta, n, 1.f / f->tau, logf(f->tau),
+                                                logq);
     return cudaGetLastError();
 }
 
@@ -835,24 +850,34 @@ cudaError_t launch_sample(abc_maf f, int r, uint64_t n, const float* u, const Mo
     if (e != cudaSuccess) return e;
     const uint64_t tiles = (n + 15) / 16;
     const int grid = fill_grid(maf::sample_kernel<K>, 128, smem, (tiles + 3) / 4);
-    maf::sample_kernel<K><<<grid, 128, smem, s>>>(flow_pub(f, r), f->H, f->box, u, p, ctr3, first, n, theta, logq);
+    maf::sample_kernel<K><<<grid, 128, smem, s>>>(flow_pub(f, r), f->H, f->box, u, p, ctr3, first, n, f->tau,
+                                                  logf(f->tau), theta, logq);
     return cudaGetLastError();
 }
 
 // gradients of every flow's slot: with rows, `batch` rows per flow; else all
 // max_n points (the largest slot)
+template <int K, int W>
+cudaError_t launch_grad_w(abc_maf f, const uint32_t* rows, uint32_t batch, uint64_t tiles, cudaStream_t s)
+{
+    const size_t smem = grad_smem(f, W);
+    cudaError_t e = allow_smem(maf::grad_kernel<K, W>, smem);
+    if (e != cudaSuccess) return e;
+    const uint64_t want = (tiles + W - 1) / W;
+    const int grid = (int)(want < (uint64_t)sm_count() ? (want > 0 ? want : 1) : (uint64_t)sm_count());
+    maf::grad_kernel<K, W><<<dim3(grid, f->R), W * 32, smem, s>>>(f->d_pub, f->H, f->box, f->d_slots, rows, batch,
+                                                                 f->d_grad, f->d_sums);
+    return cudaGetLastError();
+}
+
 template <int K>
 cudaError_t launch_grad(abc_maf f, const uint32_t* rows, uint32_t batch, uint64_t max_n, cudaStream_t s)
 {
-    const size_t smem = grad_smem(f);
-    cudaError_t e = allow_smem(maf::grad_kernel<K>, smem);
-    if (e != cudaSuccess) return e;
     const uint64_t tiles = ((rows ? batch : max_n) + 15) / 16;
-    const uint64_t want = (tiles + maf::kGradWarps - 1) / maf::kGradWarps;
-    const int grid = (int)(want < (uint64_t)sm_count() ? (want > 0 ? want : 1) : (uint64_t)sm_count());
-    maf::grad_kernel<K><<<dim3(grid, f->R), maf::kGradWarps * 32, smem, s>>>(f->d_pub, f->H, f->box, f->d_slots, rows,
-                                                                             batch, f->d_grad, f->d_sums);
-    return cudaGetLastError();
+    const uint64_t narrow_ctas = (tiles + maf::kGradWarpsNarrow - 1) / maf::kGradWarpsNarrow * (uint64_t)f->R;
+    if (narrow_ctas > 2 * (uint64_t)sm_count() && grad_smem(f, maf::kGradWarpsWide) <= 227 * 1024)
+        return launch_grad_w<K, maf::kGradWarpsWide>(f, rows, batch, tiles, s);
+    return launch_grad_w<K, maf::kGradWarpsNarrow>(f, rows, batch, tiles, s);
 }
 
 #define MAF_DISPATCH(fn, ...)                      \
@@ -952,6 +977,15 @@ abc_status abc_maf_create(int32_t n_blocks, int32_t hidden, const abc_prior_box*
 int64_t abc_maf_param_count(abc_maf f) { return f ? f->n_params : -1; }
 
 int32_t abc_maf_flow_count(abc_maf f) { return f ? f->R : -1; }
+
+abc_status abc_maf_set_proposal_scale(abc_maf f, float tau)
+{
+    abc_status st;
+    if ((st = check(f)) != ABC_OK) return st;
+    if (!(tau >= 0.5f && tau <= 4.f)) return plan_fail(ABC_ERR_INVALID_ARG, "tau must be in [0.5, 4]");
+    f->tau = tau;
+    return plan_ok();
+}
 
 abc_status abc_maf_init_random(abc_maf f, uint64_t seed, float scale)
 {
@@ -1090,7 +1124,9 @@ abc_status abc_maf_train_flows(abc_maf f, const float* const* theta, const float
         max_n = n[r] > max_n ? n[r] : max_n;
     }
     if (max_n == 0) return plan_fail(ABC_ERR_INVALID_ARG, "no flow has points");
-    // the last floor(val_fraction n) points of a flow validate, the rest train
+    // the last floor(val_fraction n) points of a flow, at most kMaxVal,
+    // validate; the rest train
+    constexpr uint64_t kMaxVal = 8192;
     const int R = f->R;
     std::vector<const float*> th_tr(theta, theta + R), w_tr((size_t)R, nullptr), th_va((size_t)R, nullptr),
         w_va((size_t)R, nullptr);
@@ -1098,7 +1134,8 @@ abc_status abc_maf_train_flows(abc_maf f, const float* const* theta, const float
     bool validate = false;
     for (int r = 0; r < R; ++r) {
         w_tr[r] = weights ? weights[r] : nullptr;
-        const uint64_t v = val_fraction > 0.f && n[r] >= 20 ? (uint64_t)std::floor(val_fraction * (double)n[r]) : 0;
+        uint64_t v = val_fraction > 0.f && n[r] >= 20 ? (uint64_t)std::floor(val_fraction * (double)n[r]) : 0;
+        if (v > kMaxVal) v = kMaxVal;
         if (v > 0) {
             n_va[r] = v;
             n_tr[r] = n[r] - v;

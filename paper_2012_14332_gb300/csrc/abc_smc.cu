@@ -53,8 +53,8 @@ __global__ void mixture_logq_kernel(float* __restrict__ logq, uint64_t n, float 
 // Pass 1: log w_j = log prior - log q_mix(theta_j) (0 for prior draws, logq
 // NULL), and the maximum (atomicMax over an order-preserving integer key).
 // Pass 2: v_j = exp(log w_j - max) in double; sum v and sum v^2 (for the ESS);
-// v_j as the float training weight, optionally v_j in double and the
-// unnormalised exp(log w_j) of the first pool_k samples in double.
+// v_j as the float training weight, optionally v_j in double for every j and
+// for the first pool_k samples.
 struct WeightScratch {
     unsigned int max_key;
     unsigned int pad;
@@ -97,7 +97,7 @@ __global__ void weight_kernel(const float* __restrict__ lw, uint64_t m, WeightSc
         v = exp(l - top);
         w_train[j] = (float)v;
         if (w_exact) w_exact[j] = v;
-        if (pool && j < pool_k) pool[j] = exp(l);
+        if (pool && j < pool_k) pool[j] = v;
     }
     double a = v, b = v * v;
     for (int off = 16; off > 0; off >>= 1) {
@@ -121,20 +121,21 @@ __global__ void weight_kernel(const float* __restrict__ lw, uint64_t m, WeightSc
     }
 }
 
-// training set of a round: dst[j] = src[(a j + b) mod m] for theta and weights
+// training set: dst[j] = src[(a j + b) mod m] for theta and weights, j < n <= m
 // (a coprime to m, so a permutation): the held-out tail of the training set is
-// then a spread-out subset of the round, not its highest sample indices
-__global__ void permute_kernel(const float* __restrict__ theta, const float* __restrict__ w, uint64_t m, uint64_t a,
-                               uint64_t b, float* __restrict__ theta_dst, float* __restrict__ w_dst)
+// then a spread-out subset of the data, not its highest sample indices
+template <typename W>
+__global__ void permute_kernel(const float* __restrict__ theta, const W* __restrict__ w, uint64_t m, uint64_t n,
+                               uint64_t a, uint64_t b, float* __restrict__ theta_dst, float* __restrict__ w_dst)
 {
     const uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= m) return;
+    if (j >= n) return;
     const uint64_t i = (a * j + b) % m;
     const float4* src = reinterpret_cast<const float4*>(theta + 8 * i);
     float4* dst = reinterpret_cast<float4*>(theta_dst + 8 * j);
     dst[0] = src[0];
     dst[1] = src[1];
-    w_dst[j] = w[i];
+    w_dst[j] = (float)w[i];
 }
 
 __global__ void scale_kernel(double* __restrict__ w, uint64_t m, double f)
@@ -174,15 +175,17 @@ using abcgb::plan_fail;
         if (_s != ABC_OK) return _s;        \
     } while (0)
 
-// Shuffle a round's m accepted samples and their training weights into a
-// training set (permute_kernel). m < 2^32.
-static abc_status shuffled_training_set(const float* theta, const float* w, uint64_t m, uint64_t salt,
+// Shuffle m samples and their weights into a training set of the first
+// n <= m of the permuted order (permute_kernel). m < 2^32.
+template <typename W>
+static abc_status shuffled_training_set(const float* theta, const W* w, uint64_t m, uint64_t n, uint64_t salt,
                                         float* theta_dst, float* w_dst, cudaStream_t s)
 {
     uint64_t a = (uint64_t)(0.6180339887498949 * (double)m) | 1u;
     while (std::gcd(a, m) != 1) a += 2;
     const uint64_t b = (salt * 0x9E3779B97F4A7C15ull) % m;
-    permute_kernel<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(theta, w, m, a % m ? a % m : 1, b, theta_dst, w_dst);
+    permute_kernel<W><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(theta, w, m, n, a % m ? a % m : 1, b, theta_dst,
+                                                                  w_dst);
     SMC_TRY(cudaGetLastError(), "permute launch");
     return ABC_OK;
 }
@@ -219,6 +222,11 @@ extern "C" abc_status abc_smc_run(const abc_prior_box* prior, const int32_t* obs
         cfg->eps_factor > 1.0 || !(cfg->ess_min >= 0.0) || cfg->capacity == 0 || !(cfg->defensive >= 0.0) ||
         cfg->defensive >= 1.0 || !(cfg->val_fraction >= 0.0) || cfg->val_fraction > 0.5)
         return plan_fail(ABC_ERR_INVALID_ARG, "bad sequential ABC configuration");
+    // every accepted sample of a round is kept: the accept buffer is filled in
+    // claim (index) order and a flow round's defensive prior draws are its
+    // last indices, so a truncated round would drop them selectively
+    if (cfg->capacity < cfg->sims_per_round)
+        return plan_fail(ABC_ERR_INVALID_ARG, "capacity must be >= sims_per_round");
     cudaStream_t s = (cudaStream_t)cuda_stream;
     if (!s) return plan_fail(ABC_ERR_INVALID_ARG, "sequential ABC needs a non-default stream");
     const uint64_t N = cfg->sims_per_round, cap = cfg->capacity;
@@ -332,7 +340,7 @@ extern "C" abc_status abc_smc_run(const abc_prior_box* prior, const int32_t* obs
         } else {
             const bool trainable = m >= 64 && R.ess_fraction >= cfg->ess_min;
             if (trainable) {
-                SMC_ST(shuffled_training_set(acc_theta, d_wround, m, cfg->seed + (uint64_t)r, d_train, d_w, s));
+                SMC_ST(shuffled_training_set(acc_theta, d_wround, m, m, cfg->seed + (uint64_t)r, d_train, d_w, s));
                 float loss = 0.f;
                 const float* tt = d_train;
                 const float* tw = d_w;
@@ -386,7 +394,8 @@ extern "C" abc_status abc_smc_run_regions(const abc_prior_box* prior, abc_smc_re
     if (R < 1 || R > ABC_MAX_REGIONS) return plan_fail(ABC_ERR_INVALID_ARG, "n_regions must be in [1, ABC_MAX_REGIONS]");
     if (cfg->rounds < 1 || cfg->sims_per_round == 0 || !(cfg->eps_factor > 0.0) || cfg->eps_factor > 1.0 ||
         !(cfg->ess_min >= 0.0) || cfg->capacity == 0 || !(cfg->defensive >= 0.0) || cfg->defensive >= 1.0 ||
-        !(cfg->val_fraction >= 0.0) || cfg->val_fraction > 0.5 || scfg->shrink_rounds < 1 || scfg->shrink_rounds > cfg->rounds || scfg->train_steps_warm < 0 ||
+        !(cfg->val_fraction >= 0.0) || cfg->val_fraction > 0.5 || cfg->capacity < cfg->sims_per_round ||
+        scfg->shrink_rounds < 1 || scfg->shrink_rounds > cfg->rounds || scfg->train_steps_warm < 0 ||
         cfg->train_steps < 0)
         return plan_fail(ABC_ERR_INVALID_ARG, "bad multi-region sequential ABC configuration");
     for (int32_t g = 0; g < R; ++g) {
@@ -444,7 +453,7 @@ extern "C" abc_status abc_smc_run_regions(const abc_prior_box* prior, abc_smc_re
     }
     SMC_ST(abc_plan_create(prior, regs.data(), R, cfg->seed, cfg->mode, &gd.plan));
 
-    std::vector<char> use_flow((size_t)R, 0), trainable((size_t)R, 0);
+    std::vector<char> use_flow((size_t)R, 0), trainable((size_t)R, 0), next_flow((size_t)R, 0);
     bool trained_once = false;
     std::vector<float> losses((size_t)R, 0.f);
     std::vector<const float*> tr_theta((size_t)R), tr_w((size_t)R);
@@ -498,22 +507,26 @@ extern "C" abc_status abc_smc_run_regions(const abc_prior_box* prior, abc_smc_re
             Rr[g].simulated_days = days;
             const uint64_t m = std::min(n_acc, cap);
             trainable[g] = 0;
+            next_flow[g] = 0;
             tr_n[g] = 0;
             if (m == 0) continue;
-            // weights prior / q_mix (1 for prior draws); the samples accepted at
-            // the region's final eps are pooled with their unnormalised weights
+            // weights prior / q_mix (1 for prior draws)
             abc_smc_region& G = regions[g];
             const bool pool = r >= S - 1;
             const uint64_t k = pool ? std::min(m, G.capacity - G.n_out) : 0;
-            float* tw = d_w + (size_t)g * cap;
+            double* pw = k ? G.weight_out + G.n_out : nullptr;
             double sw = 0.0, sw2 = 0.0;
             SMC_ST(round_weights(use_flow[g] ? d_logq + (size_t)g * N : nullptr, acc_idx, first, m, log_prior,
-                                 d_acc_logq, d_wround, nullptr, k ? G.weight_out + G.n_out : nullptr, k, d_ws, s, &sw,
-                                 &sw2));
+                                 d_acc_logq, d_wround, nullptr, pw, k, d_ws, s, &sw, &sw2));
             Rr[g].ess_fraction = sw2 > 0.0 ? sw * sw / sw2 / (double)m : 0.0;
+            // samples accepted at the region's final eps join the pool; the
+            // rounds' self-normalised estimates are combined with weights
+            // proportional to their ESS, i.e. sample weight v_j sum v / sum v^2
             if (pool) {
                 G.n_pooled += n_acc;
                 if (k > 0) {
+                    scale_kernel<<<(unsigned)((k + 255) / 256), 256, 0, s>>>(pw, k, sw / sw2);
+                    SMC_TRY(cudaGetLastError(), "scale launch");
                     SMC_TRY(cudaMemcpyAsync(G.theta_out + 8 * G.n_out, acc_theta, sizeof(float) * 8 * k,
                                             cudaMemcpyDefault, s),
                             "cudaMemcpyAsync(pooled theta)");
@@ -522,17 +535,32 @@ extern "C" abc_status abc_smc_run_regions(const abc_prior_box* prior, abc_smc_re
                     G.n_out += k;
                 }
             }
-            // this round's weighted accepts train the region's next proposal
-            if (r + 1 < cfg->rounds && m >= 64 && Rr[g].ess_fraction >= cfg->ess_min) {
+            // the next round uses the flow unless this round's ESS fell below
+            // ess_min; the flow trains on this round's weighted accepts, or,
+            // once at the final eps, on the whole pool (same target, more points)
+            const bool good = m >= 64 && Rr[g].ess_fraction >= cfg->ess_min;
+            if (r + 1 < cfg->rounds) {
                 float* tt = d_train + (size_t)g * 8 * cap;
-                SMC_ST(shuffled_training_set(acc_theta, d_wround, m, cfg->seed + 131 * (uint64_t)r + (uint64_t)g, tt,
-                                             tw, s));
-                trainable[g] = 1;
-                tr_theta[g] = tt;
-                tr_w[g] = tw;
-                tr_n[g] = m;
-                any_train = true;
+                float* tw = d_w + (size_t)g * cap;
+                uint64_t tn = 0;
+                if (pool && G.n_out >= 64) {
+                    tn = std::min(G.n_out, cap);
+                    SMC_ST(shuffled_training_set(G.theta_out, G.weight_out, G.n_out, tn,
+                                                 cfg->seed + 131 * (uint64_t)r + (uint64_t)g, tt, tw, s));
+                } else if (!pool && good) {
+                    tn = m;
+                    SMC_ST(shuffled_training_set(acc_theta, d_wround, m, m, cfg->seed + 131 * (uint64_t)r + (uint64_t)g,
+                                                 tt, tw, s));
+                }
+                if (tn > 0) {
+                    trainable[g] = 1;
+                    tr_theta[g] = tt;
+                    tr_w[g] = tw;
+                    tr_n[g] = tn;
+                    any_train = true;
+                }
             }
+            next_flow[g] = good && (trainable[g] || use_flow[g]);
         }
         if (any_train) {
             const int32_t steps = trained_once ? scfg->train_steps_warm : cfg->train_steps;
@@ -553,7 +581,7 @@ extern "C" abc_status abc_smc_run_regions(const abc_prior_box* prior, abc_smc_re
             Rr[g].ms_propose = ms[0];
             Rr[g].ms_simulate = ms[1];
             Rr[g].ms_train = ms[2];
-            use_flow[g] = trainable[g];
+            use_flow[g] = next_flow[g];
         }
     }
     SMC_TRY(cudaStreamSynchronize(s), "cudaStreamSynchronize");

@@ -167,3 +167,40 @@ def test_plan_create_validates_before_any_cuda_call(L):
     assert create([dict(good, observed=big.ctypes.data)]) == ABC_ERR_INVALID_ARG
     assert L.abc_plan_run(None, None) == ABC_ERR_INVALID_ARG
     assert L.abc_plan_destroy(None) == ABC_ERR_INVALID_ARG
+
+
+def test_sequential_drivers_validate_before_any_cuda_call(L):
+    """Bad configurations of the sequential drivers (one region, many regions)
+    and of flow training return ABC_ERR_INVALID_ARG without touching a GPU;
+    a round must keep every accepted sample (capacity >= sims_per_round)."""
+    from paper_2012_14332_gb300.binding import (ABC_ERR_INVALID_ARG, AbcSmcConfig, AbcSmcRegion, AbcSmcRound,
+                                                AbcSmcStreamConfig, prior_box)
+    box = prior_box()
+    obs = np.zeros((3, 11), dtype=np.int32)
+    obs[0, 0] = 5
+    op = obs.ctypes.data_as(ctypes.c_void_p)
+    good = dict(rounds=3, sims_per_round=1024, eps0=10.0, eps_factor=0.7, ess_min=0.1, flow_blocks=3, flow_hidden=64,
+                train_steps=10, train_batch=256, train_lr=1e-3, seed=1, capacity=1024, mode=1, defensive=0.1,
+                val_fraction=0.1)
+    rounds = (AbcSmcRound * 16)()
+    n = ctypes.c_uint64()
+    s = ctypes.c_void_p(1)   # never used: validation fails first
+    for bad in (dict(capacity=1023), dict(rounds=0), dict(eps_factor=1.5), dict(defensive=1.0),
+                dict(val_fraction=0.6), dict(sims_per_round=0)):
+        cfg = AbcSmcConfig(**dict(good, **bad))
+        assert L.abc_smc_run(ctypes.byref(box), op, 10, 1000, ctypes.byref(cfg), rounds, None, None, None,
+                             ctypes.byref(n), s) == ABC_ERR_INVALID_ARG, bad
+    assert "capacity" in (L.abc_smc_run(ctypes.byref(box), op, 10, 1000,
+                                        ctypes.byref(AbcSmcConfig(**dict(good, capacity=1))), rounds, None, None,
+                                        None, ctypes.byref(n), s) and L.abc_last_error().decode())
+    reg = (AbcSmcRegion * 2)(AbcSmcRegion(op, 10, 1000, 5.0, None, None, None, 0, 0, 0),
+                             AbcSmcRegion(op, 10, 1000, 5.0, None, None, None, 0, 0, 0))
+    for bad, shrink, nreg in ((dict(), 0, 2), (dict(), 4, 2), (dict(capacity=10), 2, 2), (dict(), 2, 0),
+                              (dict(), 2, 33)):
+        cfg = AbcSmcStreamConfig(AbcSmcConfig(**dict(good, **bad)), shrink, 5)
+        assert L.abc_smc_run_regions(ctypes.byref(box), reg, nreg, ctypes.byref(cfg), rounds, s) \
+            == ABC_ERR_INVALID_ARG, (bad, shrink, nreg)
+    # a region with capacity but no output buffers
+    reg[1] = AbcSmcRegion(op, 10, 1000, 5.0, None, None, None, 8, 0, 0)
+    cfg = AbcSmcStreamConfig(AbcSmcConfig(**good), 2, 5)
+    assert L.abc_smc_run_regions(ctypes.byref(box), reg, 2, ctypes.byref(cfg), rounds, s) == ABC_ERR_INVALID_ARG

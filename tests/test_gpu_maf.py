@@ -268,3 +268,25 @@ def test_early_stopping_generalises_on_a_small_set():
         f.close()
     print("fresh-data loss: no validation %.4f, early stopping %.4f, entropy %.4f" % (out[0], out[1], ent))
     assert out[1] < out[0]
+
+
+def test_broadened_proposal_matches_oracle():
+    """With the base scaled by tau, sampling (given base draws) and the density
+    follow the oracle's tau-broadened flow; tau = 1 is the trained flow."""
+    K, H, tau = 3, 64, 1.4
+    f, params = _flow(K, H, 61, 0.3)
+    f.set_proposal_scale(tau)
+    th = _thetas(3000, 11)
+    got = f.log_q(torch.from_numpy(th).to(DEV)).cpu().numpy().astype(np.float64)
+    want = mo.log_q_theta(th.astype(np.float64), params, LO, HI, bf16=True, tau=tau)
+    err = np.abs(got - want)
+    assert np.median(err) < 1e-4 and np.quantile(err, 0.99) < 2e-3
+    u = np.random.default_rng(12).logistic(size=(2000, 8)).astype(np.float32)
+    ts, lq = f.sample(2000, base=torch.from_numpy(u).to(DEV))
+    y, lqy = mo.inverse(u.astype(np.float64), params, bf16=True, tau=tau)
+    rel = np.abs(ts.cpu().numpy() - mo.to_theta(y, LO, HI)) / (HI - LO)
+    assert np.median(rel) < 1e-5 and np.quantile(rel, 0.99) < 1e-3
+    assert np.median(np.abs(lq.cpu().numpy() - (lqy - mo.log_jacobian_y(y, LO, HI)))) < 1e-4
+    with pytest.raises(abc.AbcError):
+        f.set_proposal_scale(0.1)
+    f.close()

@@ -6,7 +6,7 @@ import pytest
 
 from oracle import pmc_oracle as pmc
 from tests import inputs
-from tests.test_gpu_smc import weighted_ks
+from tests.stats_helpers import weighted_ks
 
 pytestmark = pytest.mark.gpu
 

@@ -9,6 +9,7 @@ import pytest
 from scipy import stats
 
 from tests import inputs
+from tests.stats_helpers import sandwich_ks, weighted_ks  # noqa: F401
 
 pytestmark = pytest.mark.gpu
 
@@ -22,21 +23,6 @@ from paper_2012_14332_gb300 import build as _build  # noqa: E402
 _build.build()
 
 
-def weighted_ks(x, w, y):
-    """sup |F_w - G| between a weighted sample (n_eff = ESS) and a plain one,
-    with the asymptotic Kolmogorov p-value."""
-    o = np.argsort(x)
-    xs, ws = x[o], w[o] / w.sum()
-    ys = np.sort(y)
-    grid = np.concatenate([xs, ys])
-    Fw = np.concatenate([[0.0], np.cumsum(ws)])[np.searchsorted(xs, grid, side="right")]
-    G = np.searchsorted(ys, grid, side="right") / len(ys)
-    D = np.max(np.abs(Fw - G))
-    ne = w.sum() ** 2 / (w ** 2).sum()
-    en = np.sqrt(ne * len(y) / (ne + len(y)))
-    return D, stats.kstwobign.sf(D * en)
-
-
 def test_learned_proposal_gains_and_keeps_the_posterior():
     w = inputs.workload("region_1e6_T49")
     obs, P = w["observed"], w["P"]
@@ -45,7 +31,7 @@ def test_learned_proposal_gains_and_keeps_the_posterior():
     rounds, N = 4, 1 << 20
     info, th, wt, dist = abc.abc_smc_run(obs, P, eps0, rounds=rounds, sims_per_round=N, eps_factor=0.7,
                                          flow_blocks=3, flow_hidden=128, train_steps=400, train_batch=1024,
-                                         train_lr=2e-3, seed=5, capacity=1 << 17, mode="fast")
+                                         train_lr=2e-3, seed=5, mode="fast")
     for r in info:
         print("round eps %.4g proposal %d accepted %d / %d  ESS %.3f  loss %.3f" % (
             r["eps"], r["proposal"], r["n_accepted"], r["n_sims"], r["ess_fraction"], r["train_loss"]))
