@@ -68,3 +68,36 @@ def weighted_mean_z(x, w, y):
     wn = np.asarray(w, dtype=np.float64) / np.sum(w)
     mw = (wn * x).sum()
     return (mw - y.mean()) / np.sqrt((wn ** 2 * (x - mw) ** 2).sum() + y.var() / len(y))
+
+
+def posterior_error(x, w, y, probs=(0.1, 0.25, 0.5, 0.75, 0.9)):
+    """Accuracy of an importance-weighted sample x (weights w) against a plain
+    sample y of the target, one coordinate: (|mean difference| in units of the
+    plain standard deviation, its standard error in the same units, max
+    |F_w(t_p) - G(t_p)| over y's quantiles t_p, the standard error there),
+    standard errors from the sandwich variance and the plain sample's."""
+    wn = np.asarray(w, dtype=np.float64) / np.sum(w)
+    sd = y.std()
+    mw = (wn * x).sum()
+    dm = abs(mw - y.mean()) / sd
+    se_m = np.sqrt((wn ** 2 * (x - mw) ** 2).sum() + y.var() / len(y)) / sd
+    ys = np.sort(y)
+    dc, se_c = 0.0, 0.0
+    for p in probs:
+        t = ys[min(len(ys) - 1, int(p * len(ys)))]
+        below = x <= t
+        Fw = wn[below].sum()
+        G = np.searchsorted(ys, t, side="right") / len(ys)
+        se = np.sqrt((wn ** 2 * (below - Fw) ** 2).sum() + G * (1 - G) / len(ys))
+        if abs(Fw - G) - 4 * se > dc - 4 * se_c:
+            dc, se_c = abs(Fw - G), se
+    return dm, se_m, dc, se_c
+
+
+def assert_posterior_close(x, w, y, tol_mean=0.05, tol_cdf=0.02, k=4.0, tag=""):
+    """Every coordinate: |mean difference| <= tol_mean plain sd + k SE and
+    max CDF difference at five quantiles <= tol_cdf + k SE."""
+    for j in range(x.shape[1]):
+        dm, se_m, dc, se_c = posterior_error(x[:, j], w, y[:, j])
+        assert dm <= tol_mean + k * se_m, (tag, j, dm, se_m)
+        assert dc <= tol_cdf + k * se_c, (tag, j, dc, se_c)

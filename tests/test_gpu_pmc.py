@@ -6,7 +6,7 @@ import pytest
 
 from oracle import pmc_oracle as pmc
 from tests import inputs
-from tests.stats_helpers import weighted_ks
+from tests.stats_helpers import assert_posterior_close
 
 pytestmark = pytest.mark.gpu
 
@@ -104,10 +104,4 @@ def test_pmc_posterior_matches_plain_abc():
     a = th.cpu().numpy().astype(np.float64)
     wa = wt.cpu().numpy()
     b = th_p.cpu().numpy().astype(np.float64)
-    ne = 1.0 / (wa ** 2).sum()
-    for j in range(8):
-        mw = (wa * a[:, j]).sum()
-        se = np.sqrt((wa * (a[:, j] - mw) ** 2).sum() / ne + b[:, j].var() / len(b))
-        assert abs(mw - b[:, j].mean()) < 5 * se, j
-        D, p = weighted_ks(a[:, j], wa, b[:, j])
-        assert p > 0.01, (j, D, p)
+    assert_posterior_close(a, wa, b, tag="population Monte Carlo")

@@ -1,14 +1,15 @@
 """Sequential ABC with one learned proposal per region, several regions in one
 batched launch per round (abc_smc_run_regions): each region's pooled,
 importance-weighted samples at its final tolerance estimate the same ABC
-posterior (Eq. 7) as plain rejection from the prior at that tolerance
-(weighted means within Monte-Carlo error, weighted KS per coordinate), and
-the learned proposals accept far more of their simulations than the prior."""
+posterior (Eq. 7) as plain rejection from the prior at that tolerance (every
+coordinate's mean within 0.05 posterior sd and CDF at five quantiles within
+0.02, beyond Monte-Carlo error), and the learned proposals give far more
+effective samples per simulation than the prior."""
 import numpy as np
 import pytest
 
 from tests import inputs
-from tests.stats_helpers import weighted_ks
+from tests.stats_helpers import assert_posterior_close
 
 pytestmark = pytest.mark.gpu
 
@@ -46,9 +47,9 @@ def test_per_region_flows_keep_each_posterior():
         used_flow = [info[r][g]["proposal"] for r in range(1, rounds)]
         assert 2 * sum(used_flow) >= len(used_flow), (g, used_flow)
         # plain prior ABC at the same final tolerance
-        n_plain = 1 << 24
+        n_plain = 1 << 25
         th_p, _, _, n_acc_p = abc.abc_sample(reg["observed"], reg["N_pop"], reg["eps"], n_plain, 777 + g, mode="fast",
-                                             capacity=1 << 16)
+                                             capacity=1 << 17)
         assert n_acc_p > 2000
         p_prior = n_acc_p / n_plain
         a = th.cpu().numpy().astype(np.float64)
@@ -62,10 +63,4 @@ def test_per_region_flows_keep_each_posterior():
             g, p_prior, per_sim, n_pooled))
         assert per_sim > 3 * p_prior
         b = th_p.cpu().numpy().astype(np.float64)
-        ne = 1.0 / (wa ** 2).sum()
-        for j in range(8):
-            mw = (wa * a[:, j]).sum()
-            se = np.sqrt((wa * (a[:, j] - mw) ** 2).sum() / ne + b[:, j].var() / len(b))
-            assert abs(mw - b[:, j].mean()) < 5 * se + 1e-9, (g, j)
-            D, p = weighted_ks(a[:, j], wa, b[:, j])
-            assert p > 1e-3, (g, j, D, p)
+        assert_posterior_close(a, wa, b, tag="region %d" % g)

@@ -46,3 +46,19 @@ def test_sandwich_z_scores_detect_a_small_shift():
     rng = np.random.default_rng(2)
     hits = [np.abs(cdf_z_scores(*_draw(rng, 20000, 0.5, 0.7, 0.1))).max() > 4 for _ in range(40)]
     assert np.mean(hits) > 0.75
+
+
+def test_posterior_error_measures_a_known_shift():
+    """A plain sample against itself shifted by 0.1 sd: the mean error reads
+    0.1 sd and the CDF error about phi(0) 0.1; the accuracy check rejects a
+    0.1 sd shift and accepts 0.02 sd at these sizes."""
+    from tests.stats_helpers import assert_posterior_close, posterior_error
+    rng = np.random.default_rng(3)
+    y = rng.normal(size=(200000, 1))
+    x = rng.normal(size=(200000, 1))
+    dm, se_m, dc, se_c = posterior_error(x[:, 0] + 0.1, np.ones(len(x)), y[:, 0])
+    assert abs(dm - 0.1) < 5 * se_m and abs(dc - 0.1 * stats.norm.pdf(0)) < 0.01
+    import pytest
+    with pytest.raises(AssertionError):
+        assert_posterior_close(x + 0.1, np.ones(len(x)), y)
+    assert_posterior_close(x + 0.02, np.ones(len(x)), y)
