@@ -426,6 +426,9 @@ typedef struct {
     abc_mode mode;
     double defensive;         /* prior fraction of a flow round's proposals, in [0, 1) (e.g. 0.1) */
     double val_fraction;      /* held-out fraction for early stopping of the training, in [0, 0.5] (e.g. 0.1) */
+    double train_weight_power;/* training weights are (prior / q)^power, in (0, 1] (1: the importance weights;
+                                 below 1 the flow fits a broader density between proposal and target) */
+    int32_t fresh_init;       /* 1: re-initialise the flow (random, fresh seed) before each training; 0: continue */
 } abc_smc_config;
 
 typedef struct {

@@ -52,7 +52,8 @@ class AbcSmcConfig(ctypes.Structure):
                 ("eps_factor", ctypes.c_double), ("ess_min", ctypes.c_double), ("flow_blocks", ctypes.c_int32),
                 ("flow_hidden", ctypes.c_int32), ("train_steps", ctypes.c_int32), ("train_batch", ctypes.c_int32),
                 ("train_lr", ctypes.c_float), ("seed", ctypes.c_uint64), ("capacity", ctypes.c_uint64),
-                ("mode", ctypes.c_int), ("defensive", ctypes.c_double), ("val_fraction", ctypes.c_double)]
+                ("mode", ctypes.c_int), ("defensive", ctypes.c_double), ("val_fraction", ctypes.c_double),
+                ("train_weight_power", ctypes.c_double), ("fresh_init", ctypes.c_int32)]
 
 
 class AbcSmcRound(ctypes.Structure):
@@ -739,8 +740,8 @@ def abc_maf_train_flows(flow, thetas, weights=None, **kw):
 
 def abc_smc_run(observed, N_pop, eps0, rounds=5, sims_per_round=1 << 22, eps_factor=0.7, ess_min=0.1,
                 flow_blocks=3, flow_hidden=256, train_steps=500, train_batch=1024, train_lr=1e-3, seed=0,
-                capacity=None, mode="fast", defensive=0.1, val_fraction=0.1, lo=PAPER_LO, hi=PAPER_HI,
-                cuda_stream=None):
+                capacity=None, mode="fast", defensive=0.1, val_fraction=0.1, train_weight_power=1.0, fresh_init=False,
+                lo=PAPER_LO, hi=PAPER_HI, cuda_stream=None):
     """Sequential ABC with the learned flow proposal. Returns (rounds: list of
     dicts, theta [m, 8], weights [m] (f64, sum 1), dist [m]) of the last round."""
     L = load()
@@ -750,7 +751,8 @@ def abc_smc_run(observed, N_pop, eps0, rounds=5, sims_per_round=1 << 22, eps_fac
         capacity = sims_per_round
     cfg = AbcSmcConfig(int(rounds), int(sims_per_round), float(eps0), float(eps_factor), float(ess_min),
                        int(flow_blocks), int(flow_hidden), int(train_steps), int(train_batch), float(train_lr),
-                       int(seed), int(capacity), _mode(mode), float(defensive), float(val_fraction))
+                       int(seed), int(capacity), _mode(mode), float(defensive), float(val_fraction),
+                       float(train_weight_power), int(bool(fresh_init)))
     rr = (AbcSmcRound * int(rounds))()
     dev = torch.device("cuda", torch.cuda.current_device())
     theta = torch.empty((capacity, 8), dtype=torch.float32, device=dev)
@@ -771,7 +773,7 @@ def abc_smc_run(observed, N_pop, eps0, rounds=5, sims_per_round=1 << 22, eps_fac
 def abc_smc_run_regions(regions, rounds=16, shrink_rounds=4, sims_per_round=1 << 20, eps_factor=0.7, ess_min=0.1,
                         flow_blocks=3, flow_hidden=256, train_steps=500, train_steps_warm=100, train_batch=1024,
                         train_lr=1e-3, seed=0, capacity=None, mode="fast", defensive=0.1, val_fraction=0.1,
-                        lo=PAPER_LO, hi=PAPER_HI, cuda_stream=None):
+                        train_weight_power=1.0, lo=PAPER_LO, hi=PAPER_HI, cuda_stream=None):
     """Sequential ABC with one flow proposal per region, all regions in one
     batched launch per round. regions: list of dicts with observed (host int32
     [3, T+1]), N_pop, eps (final) and pool (samples kept at the final eps).
@@ -797,7 +799,8 @@ def abc_smc_run_regions(regions, rounds=16, shrink_rounds=4, sims_per_round=1 <<
                               float(reg["eps"]), th.data_ptr(), w.data_ptr(), d.data_ptr(), pool, 0, 0)
     base = AbcSmcConfig(int(rounds), int(sims_per_round), 0.0, float(eps_factor), float(ess_min), int(flow_blocks),
                         int(flow_hidden), int(train_steps), int(train_batch), float(train_lr), int(seed),
-                        int(capacity), _mode(mode), float(defensive), float(val_fraction))
+                        int(capacity), _mode(mode), float(defensive), float(val_fraction),
+                        float(train_weight_power), 0)
     cfg = AbcSmcStreamConfig(base, int(shrink_rounds), int(train_steps_warm))
     rr = (AbcSmcRound * (int(rounds) * R))()
     s = cuda_stream if cuda_stream is not None else torch.cuda.Stream()

@@ -49,12 +49,17 @@ __host__ __device__ inline int master_block(int H) { return 25 * H + 16; }
 
 // Published BF16 layout of one block, in 32-bit words (two bf16 per word).
 // The forward operands come first, so density and sampling kernels stage only
-// fwd_words per block; the gradient kernel stages all words.
-//   w1  [H][4]        B operand of x W1^T      (n = hidden l, k = input j)
-//   w2  [16][H/2+4]   B operand of h W2^T      (n = output o, k = l), padded rows
-//   b1 [H], b2 [16]   FP32 biases
-//   w1t [8][H/2+4]    B operand of g_a1 W1     (n = j, k = l)
-//   w2t [H][12]       B operand of g_out W2    (n = l, k = o)
+// fwd_words per block; the gradient kernel stages all words. The forward
+// operands are grouped by 16-unit hidden chunk s and lane (g = lane / 4,
+// t = lane % 4) so that one chunk's fragments are one vector load per lane:
+//   w1  [H/16][8][4][2]  B operands of x W1^T (k = input j = 2t, 2t+1) for
+//                        hidden units 16s + g and 16s + 8 + g
+//   w2  [H/16][8][4][4]  B operands of h W2^T (k = hidden 16s + 2t, +1 and
+//                        16s + 8 + 2t, +1) for outputs g and 8 + g
+//   b1  [H/16][4][4]     FP32: b1 of hidden 16s + 2t, +1, 16s + 8 + 2t, +1
+//   b2  [16]             FP32
+//   w1t [8][H/2+4]       B operand of g_a1 W1     (n = j, k = l)
+//   w2t [H][12]          B operand of g_out W2    (n = l, k = o)
 struct Layout {
     int w1, w2, b1, b2, w1t, w2t, fwd_words, words;
 };
@@ -63,7 +68,7 @@ __host__ __device__ inline Layout layout(int H)
     Layout L;
     int o = 0;
     L.w1 = o; o += H * 4;
-    L.w2 = o; o += 16 * (H / 2 + 4);
+    L.w2 = o; o += H * 8;
     L.b1 = o; o += H;
     L.b2 = o; o += 16;
     L.fwd_words = o;
@@ -86,6 +91,16 @@ __device__ __forceinline__ uint32_t pack2(float lo, float hi)
 {
     __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
     return *reinterpret_cast<uint32_t*>(&v);
+}
+
+// bf16x2 of (max(lo, 0), max(hi, 0)), round to nearest: the ReLU folded into
+// the conversion (for a negative input the rounded value is <= 0 and clamps
+// to 0, as clamping first would give)
+__device__ __forceinline__ uint32_t pack2_relu(float lo, float hi)
+{
+    uint32_t d;
+    asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+    return d;
 }
 
 __device__ __forceinline__ void mma_k8(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t b0)
@@ -159,31 +174,48 @@ __device__ __forceinline__ float logistic_draw(uint32_t w)
     return logf(u) - log1pf(-u);
 }
 
+// One 16-unit hidden chunk of a MADE on the warp's 16 rows: layer 1 (two
+// m16n8k8, accumulators starting at b1), ReLU and bf16 in one conversion,
+// then the chunk's layer-2 contribution (two m16n8k16) into o0 (mu) and o1
+// (alpha_raw).
+__device__ __forceinline__ void made_chunk(const BlockView& v, int s, int g, int t, uint32_t a0, uint32_t a1,
+                                           float (&o0)[4], float (&o1)[4])
+{
+    const uint2 wa = reinterpret_cast<const uint2*>(v.w1)[(s * 8 + g) * 4 + t];
+    const uint4 wb = reinterpret_cast<const uint4*>(v.w2)[(s * 8 + g) * 4 + t];
+    const float4 bb = reinterpret_cast<const float4*>(v.b1)[s * 4 + t];
+    float c0[4] = {bb.x, bb.y, bb.x, bb.y}, c1[4] = {bb.z, bb.w, bb.z, bb.w};
+    mma_k8(c0, a0, a1, wa.x);
+    mma_k8(c1, a0, a1, wa.y);
+    const uint32_t A0 = pack2_relu(c0[0], c0[1]), A1 = pack2_relu(c0[2], c0[3]);
+    const uint32_t A2 = pack2_relu(c1[0], c1[1]), A3 = pack2_relu(c1[2], c1[3]);
+    mma_k16(o0, A0, A1, A2, A3, wb.x, wb.y);
+    mma_k16(o1, A0, A1, A2, A3, wb.z, wb.w);
+}
+
 // One MADE on the warp's 16 rows: mu and alpha_raw in the accumulator layout.
+// Even and odd chunks accumulate separately (two independent tensor-core
+// chains), summed at the end.
 __device__ __forceinline__ void made_fwd(const BlockView& v, int H, const float (&x)[4], float (&mu)[4],
                                          float (&ar)[4])
 {
     const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
     const uint32_t a0 = pack2(x[0], x[1]), a1 = pack2(x[2], x[3]);
     float o0[4] = {0.f, 0.f, 0.f, 0.f}, o1[4] = {0.f, 0.f, 0.f, 0.f};
-    const int w2s = H / 2 + 4;
-    for (int s = 0; s < H / 16; ++s) {
-        float c0[4] = {0.f, 0.f, 0.f, 0.f}, c1[4] = {0.f, 0.f, 0.f, 0.f};
-        mma_k8(c0, a0, a1, v.w1[(16 * s + g) * 4 + t]);
-        mma_k8(c1, a0, a1, v.w1[(16 * s + 8 + g) * 4 + t]);
-        const float2 ba = *reinterpret_cast<const float2*>(v.b1 + 16 * s + 2 * t);
-        const float2 bb = *reinterpret_cast<const float2*>(v.b1 + 16 * s + 8 + 2 * t);
-        const uint32_t A0 = pack2(fmaxf(c0[0] + ba.x, 0.f), fmaxf(c0[1] + ba.y, 0.f));
-        const uint32_t A1 = pack2(fmaxf(c0[2] + ba.x, 0.f), fmaxf(c0[3] + ba.y, 0.f));
-        const uint32_t A2 = pack2(fmaxf(c1[0] + bb.x, 0.f), fmaxf(c1[1] + bb.y, 0.f));
-        const uint32_t A3 = pack2(fmaxf(c1[2] + bb.x, 0.f), fmaxf(c1[3] + bb.y, 0.f));
-        mma_k16(o0, A0, A1, A2, A3, v.w2[g * w2s + 8 * s + t], v.w2[g * w2s + 8 * s + 4 + t]);
-        mma_k16(o1, A0, A1, A2, A3, v.w2[(8 + g) * w2s + 8 * s + t], v.w2[(8 + g) * w2s + 8 * s + 4 + t]);
+    float p0[4] = {0.f, 0.f, 0.f, 0.f}, p1[4] = {0.f, 0.f, 0.f, 0.f};
+    const int chunks = H / 16;
+    int s = 0;
+    for (; s + 1 < chunks; s += 2) {
+        made_chunk(v, s, g, t, a0, a1, o0, o1);
+        made_chunk(v, s + 1, g, t, a0, a1, p0, p1);
     }
+    if (s < chunks) made_chunk(v, s, g, t, a0, a1, o0, o1);
     const float2 bm = *reinterpret_cast<const float2*>(v.b2 + 2 * t);
     const float2 bs = *reinterpret_cast<const float2*>(v.b2 + 8 + 2 * t);
-    mu[0] = o0[0] + bm.x; mu[1] = o0[1] + bm.y; mu[2] = o0[2] + bm.x; mu[3] = o0[3] + bm.y;
-    ar[0] = o1[0] + bs.x; ar[1] = o1[1] + bs.y; ar[2] = o1[2] + bs.x; ar[3] = o1[3] + bs.y;
+    mu[0] = (o0[0] + p0[0]) + bm.x; mu[1] = (o0[1] + p0[1]) + bm.y;
+    mu[2] = (o0[2] + p0[2]) + bm.x; mu[3] = (o0[3] + p0[3]) + bm.y;
+    ar[0] = (o1[0] + p1[0]) + bs.x; ar[1] = (o1[1] + p1[1]) + bs.y;
+    ar[2] = (o1[2] + p1[2]) + bs.x; ar[3] = (o1[3] + p1[3]) + bs.y;
 }
 
 // theta -> y = logit((theta - lo) / w) and the log-Jacobian term log(w u (1 - u)).
@@ -241,20 +273,23 @@ __global__ void publish_kernel(const float* __restrict__ master, uint32_t* __res
         const float* b2 = M + 25 * H;
         uint32_t out = 0;
         if (w < L.w2) {
-            const int r = w - L.w1, l = r / 4, j0 = 2 * (r % 4);
+            // r = ((s 8 + g) 4 + t) 2 + h: hidden l = 16 s + g + 8 h, inputs 2t, 2t+1
+            const int r = w - L.w1, h = r & 1, t = (r >> 1) & 3, g = (r >> 3) & 7, sc = r >> 6;
+            const int l = 16 * sc + g + 8 * h, j0 = 2 * t;
             __nv_bfloat162 v = __floats2bfloat162_rn(mask1(l, j0) ? W1[l * 8 + j0] : 0.f,
                                                      mask1(l, j0 + 1) ? W1[l * 8 + j0 + 1] : 0.f);
             out = *reinterpret_cast<uint32_t*>(&v);
         } else if (w < L.b1) {
-            const int r = w - L.w2, o = r / hw, c = r % hw;
-            if (c < H / 2) {
-                const int l0 = 2 * c;
-                __nv_bfloat162 v = __floats2bfloat162_rn(mask2(o, l0) ? W2[o * H + l0] : 0.f,
-                                                         mask2(o, l0 + 1) ? W2[o * H + l0 + 1] : 0.f);
-                out = *reinterpret_cast<uint32_t*>(&v);
-            }
+            // r = ((s 8 + g) 4 + t) 4 + q: output g + 8 (q / 2), hidden 16 s + 8 (q % 2) + 2t, +1
+            const int r = w - L.w2, q = r & 3, t = (r >> 2) & 3, g = (r >> 4) & 7, sc = r >> 7;
+            const int o = g + 8 * (q >> 1), l0 = 16 * sc + 8 * (q & 1) + 2 * t;
+            __nv_bfloat162 v = __floats2bfloat162_rn(mask2(o, l0) ? W2[o * H + l0] : 0.f,
+                                                     mask2(o, l0 + 1) ? W2[o * H + l0 + 1] : 0.f);
+            out = *reinterpret_cast<uint32_t*>(&v);
         } else if (w < L.b2) {
-            out = __float_as_uint(b1[w - L.b1]);
+            // r = (s 4 + t) 4 + q: b1 of hidden 16 s + 8 (q / 2) + 2t + q % 2
+            const int r = w - L.b1, q = r & 3, t = (r >> 2) & 3, sc = r >> 4;
+            out = __float_as_uint(b1[16 * sc + 8 * (q >> 1) + 2 * t + (q & 1)]);
         } else if (w < L.w1t) {
             out = __float_as_uint(b2[w - L.b2]);
         } else if (w < L.w2t) {
@@ -593,16 +628,18 @@ __global__ void __launch_bounds__(W * 32) grad_kernel(const uint32_t* __restrict
             const uint32_t A0 = pack2(gmu[0], gmu[1]), A1 = pack2(gmu[2], gmu[3]);
             const uint32_t A2 = pack2(gar[0], gar[1]), A3 = pack2(gar[2], gar[3]);
             const uint32_t xa0 = pack2(xs[b][0], xs[b][1]), xa1 = pack2(xs[b][2], xs[b][3]);
+            // g_out^T (A of dW2) and x^T (B of dW1) are the same for every chunk
+            const uint32_t go0 = st.goutT[g * kStage + t], go1 = st.goutT[(g + 8) * kStage + t];
+            const uint32_t go2 = st.goutT[g * kStage + 4 + t], go3 = st.goutT[(g + 8) * kStage + 4 + t];
+            const uint32_t xt0 = st.xT[g * kStage + t], xt1 = st.xT[g * kStage + 4 + t];
             float accx[4] = {0.f, 0.f, 0.f, 0.f};
             for (int s = 0; s < H / 16; ++s) {
                 // recompute the pre-activations of hidden units 16s .. 16s+15
-                float c0[4] = {0.f, 0.f, 0.f, 0.f}, c1[4] = {0.f, 0.f, 0.f, 0.f};
-                mma_k8(c0, xa0, xa1, v.w1[(16 * s + g) * 4 + t]);
-                mma_k8(c1, xa0, xa1, v.w1[(16 * s + 8 + g) * 4 + t]);
-                const float2 ba = *reinterpret_cast<const float2*>(v.b1 + 16 * s + 2 * t);
-                const float2 bb = *reinterpret_cast<const float2*>(v.b1 + 16 * s + 8 + 2 * t);
-                c0[0] += ba.x; c0[1] += ba.y; c0[2] += ba.x; c0[3] += ba.y;
-                c1[0] += bb.x; c1[1] += bb.y; c1[2] += bb.x; c1[3] += bb.y;
+                const uint2 wa = reinterpret_cast<const uint2*>(v.w1)[(s * 8 + g) * 4 + t];
+                const float4 bq = reinterpret_cast<const float4*>(v.b1)[s * 4 + t];
+                float c0[4] = {bq.x, bq.y, bq.x, bq.y}, c1[4] = {bq.z, bq.w, bq.z, bq.w};
+                mma_k8(c0, xa0, xa1, wa.x);
+                mma_k8(c1, xa0, xa1, wa.y);
                 // h^T [l][row]
                 put_bf16(st.hT, 2 * t, g, fmaxf(c0[0], 0.f));
                 put_bf16(st.hT, 2 * t + 1, g, fmaxf(c0[1], 0.f));
@@ -651,11 +688,9 @@ __global__ void __launch_bounds__(W * 32) grad_kernel(const uint32_t* __restrict
                 __syncwarp();
                 // dW2[o][l] += sum_rows g_out[row][o] h[row][l]
                 {
-                    const uint32_t a0 = st.goutT[g * kStage + t], a1 = st.goutT[(g + 8) * kStage + t];
-                    const uint32_t a2 = st.goutT[g * kStage + 4 + t], a3 = st.goutT[(g + 8) * kStage + 4 + t];
                     float e0[4] = {0.f, 0.f, 0.f, 0.f}, e1[4] = {0.f, 0.f, 0.f, 0.f};
-                    mma_k16(e0, a0, a1, a2, a3, st.hT[g * kStage + t], st.hT[g * kStage + 4 + t]);
-                    mma_k16(e1, a0, a1, a2, a3, st.hT[(8 + g) * kStage + t], st.hT[(8 + g) * kStage + 4 + t]);
+                    mma_k16(e0, go0, go1, go2, go3, st.hT[g * kStage + t], st.hT[g * kStage + 4 + t]);
+                    mma_k16(e1, go0, go1, go2, go3, st.hT[(8 + g) * kStage + t], st.hT[(8 + g) * kStage + 4 + t]);
                     const int la = 16 * s + 2 * t, lb = 16 * s + 8 + 2 * t;
                     if (mask2(g, la)) atomicAdd(&GW2[g * H + la], e0[0]);
                     if (mask2(g, la + 1)) atomicAdd(&GW2[g * H + la + 1], e0[1]);
@@ -671,7 +706,7 @@ __global__ void __launch_bounds__(W * 32) grad_kernel(const uint32_t* __restrict
                     const uint32_t a0 = st.gaT[g * kStage + t], a1 = st.gaT[(g + 8) * kStage + t];
                     const uint32_t a2 = st.gaT[g * kStage + 4 + t], a3 = st.gaT[(g + 8) * kStage + 4 + t];
                     float e0[4] = {0.f, 0.f, 0.f, 0.f};
-                    mma_k16(e0, a0, a1, a2, a3, st.xT[g * kStage + t], st.xT[g * kStage + 4 + t]);
+                    mma_k16(e0, a0, a1, a2, a3, xt0, xt1);
                     const int la = 16 * s + g, lb = la + 8;
                     if (mask1(la, 2 * t)) atomicAdd(&GW1[la * 8 + 2 * t], e0[0]);
                     if (mask1(la, 2 * t + 1)) atomicAdd(&GW1[la * 8 + 2 * t + 1], e0[1]);

@@ -86,7 +86,7 @@ __global__ void logw_kernel(const float* __restrict__ logq, const uint64_t* __re
 }
 
 __global__ void weight_kernel(const float* __restrict__ lw, uint64_t m, WeightScratch* ws, float* __restrict__ w_train,
-                              double* __restrict__ w_exact, double* __restrict__ pool, uint64_t pool_k)
+                              double* __restrict__ w_exact, double* __restrict__ pool, uint64_t pool_k, double power)
 {
     __shared__ double part[2][8];
     const uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -95,7 +95,7 @@ __global__ void weight_kernel(const float* __restrict__ lw, uint64_t m, WeightSc
     if (j < m) {
         const double l = (double)lw[j];
         v = exp(l - top);
-        w_train[j] = (float)v;
+        w_train[j] = (float)(power == 1.0 ? v : exp(power * (l - top)));
         if (w_exact) w_exact[j] = v;
         if (pool && j < pool_k) pool[j] = v;
     }
@@ -196,12 +196,13 @@ static abc_status shuffled_training_set(const float* theta, const W* w, uint64_t
 // first pool_k samples into pool; *sum_v, *sum_v2 for the ESS. Synchronizes s.
 static abc_status round_weights(const float* logq, const uint64_t* idx, uint64_t first, uint64_t m, double log_prior,
                                 float* d_lw, float* w_train, double* w_exact, double* pool, uint64_t pool_k,
-                                WeightScratch* d_ws, cudaStream_t s, double* sum_v, double* sum_v2)
+                                WeightScratch* d_ws, cudaStream_t s, double* sum_v, double* sum_v2,
+                                double power = 1.0)
 {
     SMC_TRY(cudaMemsetAsync(d_ws, 0, sizeof(WeightScratch), s), "cudaMemsetAsync(weight scratch)");
     const unsigned blocks = (unsigned)((m + 255) / 256);
     logw_kernel<<<blocks, 256, 0, s>>>(logq, idx, first, m, (float)log_prior, d_lw, d_ws);
-    weight_kernel<<<blocks, 256, 0, s>>>(d_lw, m, d_ws, w_train, w_exact, pool, pool_k);
+    weight_kernel<<<blocks, 256, 0, s>>>(d_lw, m, d_ws, w_train, w_exact, pool, pool_k, power);
     SMC_TRY(cudaGetLastError(), "weight launch");
     WeightScratch h;
     SMC_TRY(cudaMemcpyAsync(&h, d_ws, sizeof h, cudaMemcpyDeviceToHost, s), "cudaMemcpyAsync(weight sums)");
@@ -220,7 +221,8 @@ extern "C" abc_status abc_smc_run(const abc_prior_box* prior, const int32_t* obs
     if (!cfg || !rounds_out || !n_out) return plan_fail(ABC_ERR_INVALID_ARG, "cfg, rounds_out and n_out are required");
     if (cfg->rounds < 1 || cfg->sims_per_round == 0 || !(cfg->eps0 >= 0.0) || !(cfg->eps_factor > 0.0) ||
         cfg->eps_factor > 1.0 || !(cfg->ess_min >= 0.0) || cfg->capacity == 0 || !(cfg->defensive >= 0.0) ||
-        cfg->defensive >= 1.0 || !(cfg->val_fraction >= 0.0) || cfg->val_fraction > 0.5)
+        cfg->defensive >= 1.0 || !(cfg->val_fraction >= 0.0) || cfg->val_fraction > 0.5 ||
+        !(cfg->train_weight_power > 0.0) || cfg->train_weight_power > 1.0)
         return plan_fail(ABC_ERR_INVALID_ARG, "bad sequential ABC configuration");
     // every accepted sample of a round is kept: the accept buffer is filled in
     // claim (index) order and a flow round's defensive prior draws are its
@@ -318,7 +320,7 @@ extern "C" abc_status abc_smc_run(const abc_prior_box* prior, const int32_t* obs
         double sw = 0.0, sw2 = 0.0;
         if (m > 0) {
             SMC_ST(round_weights(use_flow ? d_logq : nullptr, acc_idx, first, m, log_prior, d_acc_logq, d_wround,
-                                 last ? weight_out : nullptr, nullptr, 0, d_ws, s, &sw, &sw2));
+                                 last ? weight_out : nullptr, nullptr, 0, d_ws, s, &sw, &sw2, cfg->train_weight_power));
             R.ess_fraction = sw2 > 0.0 ? sw * sw / sw2 / (double)m : 0.0;
         }
         // the next round's proposal: train on this round's weighted accepts
@@ -341,6 +343,8 @@ extern "C" abc_status abc_smc_run(const abc_prior_box* prior, const int32_t* obs
             const bool trainable = m >= 64 && R.ess_fraction >= cfg->ess_min;
             if (trainable) {
                 SMC_ST(shuffled_training_set(acc_theta, d_wround, m, m, cfg->seed + (uint64_t)r, d_train, d_w, s));
+                if (cfg->fresh_init)
+                    SMC_ST(abc_maf_init_random(gd.flow, (cfg->seed ^ 0x5EED5EEDull) + 7 * (uint64_t)(r + 1), 0.3f));
                 float loss = 0.f;
                 const float* tt = d_train;
                 const float* tw = d_w;
@@ -395,6 +399,7 @@ extern "C" abc_status abc_smc_run_regions(const abc_prior_box* prior, abc_smc_re
     if (cfg->rounds < 1 || cfg->sims_per_round == 0 || !(cfg->eps_factor > 0.0) || cfg->eps_factor > 1.0 ||
         !(cfg->ess_min >= 0.0) || cfg->capacity == 0 || !(cfg->defensive >= 0.0) || cfg->defensive >= 1.0 ||
         !(cfg->val_fraction >= 0.0) || cfg->val_fraction > 0.5 || cfg->capacity < cfg->sims_per_round ||
+        !(cfg->train_weight_power > 0.0) || cfg->train_weight_power > 1.0 ||
         scfg->shrink_rounds < 1 || scfg->shrink_rounds > cfg->rounds || scfg->train_steps_warm < 0 ||
         cfg->train_steps < 0)
         return plan_fail(ABC_ERR_INVALID_ARG, "bad multi-region sequential ABC configuration");
@@ -517,7 +522,7 @@ extern "C" abc_status abc_smc_run_regions(const abc_prior_box* prior, abc_smc_re
             double* pw = k ? G.weight_out + G.n_out : nullptr;
             double sw = 0.0, sw2 = 0.0;
             SMC_ST(round_weights(use_flow[g] ? d_logq + (size_t)g * N : nullptr, acc_idx, first, m, log_prior,
-                                 d_acc_logq, d_wround, nullptr, pw, k, d_ws, s, &sw, &sw2));
+                                 d_acc_logq, d_wround, nullptr, pw, k, d_ws, s, &sw, &sw2, cfg->train_weight_power));
             Rr[g].ess_fraction = sw2 > 0.0 ? sw * sw / sw2 / (double)m : 0.0;
             // samples accepted at the region's final eps join the pool; the
             // rounds' self-normalised estimates are combined with weights
