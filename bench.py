@@ -307,13 +307,16 @@ def bench_learned(abc, torch, w, prior_value, peaks, reps=5):
            "runs": runs}
     if flow_runs:
         ms_prop = float(np.median([r["ms_propose"] for r in flow_runs]))
-        flops = 3 * 8 * (16 * 256 + 32 * 256) * n      # per proposal: 3 blocks x 8 inverse passes x 2 products
+        # per proposal: 3 blocks x 7 inverse passes (column 0 of a block depends on
+        # the biases alone) x the two dense products, 2 (8 H + 16 H) FLOP
+        flops = 3 * 7 * (16 * 256 + 32 * 256) * int(0.9 * n)
         peak = (peaks or {}).get("bf16_tflops", 1900.0)
         achieved = flops / (ms_prop * 1e-3) / 1e12
         out["sampler_roofline"] = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                                    "frac": achieved / peak, "traffic": None,
-                                   "basis": "%d FLOP per proposal (3 blocks x 8 passes x (16 H + 32 H), H = 256), "
-                                            "peak = measured cuBLAS bf16 burst" % (flops // n)}
+                                   "basis": "%d FLOP per flow proposal (3 blocks x 7 passes x (16 H + 32 H), H = 256, "
+                                            "dense), %d flow proposals per round (the other 10 %% are prior draws), "
+                                            "peak = measured cuBLAS bf16 burst" % (flops // int(0.9 * n), int(0.9 * n))}
     return out
 
 

@@ -53,7 +53,16 @@ typedef struct {
     float hi[8];
 } abc_prior_box;
 
-typedef enum { ABC_EXACT = 0, ABC_FAST = 1 } abc_mode;
+/* Arithmetic mode. ABC_EXACT: the library's own fixed FP32 series for log2,
+ * exp2, sin and cos, every operation IEEE round-to-nearest and no FMA
+ * contraction, so results equal a plain CPU implementation bit for bit.
+ * ABC_FAST: the SFU approximations and FMA, judged statistically.
+ * ABC_VARIANCE_LITERAL may be OR-ed into either for the model variant that
+ * reads the transition variance of Sec. 2.1 literally (standard deviation
+ * h^(1/4) instead of sqrt(h)); it is accepted by abc_sample, abc_sample_async,
+ * abc_sample_noalloc, abc_distances, abc_simulate, abc_step and abc_project,
+ * and rejected (ABC_ERR_INVALID_ARG) by the batched and sequential calls. */
+typedef enum { ABC_EXACT = 0, ABC_FAST = 1, ABC_VARIANCE_LITERAL = 4 } abc_mode;
 
 typedef enum {
     ABC_OK = 0,
@@ -295,7 +304,11 @@ typedef struct abc_maf_s* abc_maf;
 
 /* Create a flow with n_blocks (1..4) blocks of `hidden` units (a multiple of
  * 16, 16..256) on the prior box, parameters zero (q = the uniform prior).
- * Allocates its device memory on the current device. */
+ * Allocates its device memory on the current device. The training kernel
+ * stages a CTA's operands and gradients in shared memory, about
+ * n_blocks (928 hidden + 2048) bytes: a shape beyond the device's per-block
+ * limit returns ABC_ERR_INVALID_ARG (on GB300, 227 KB: n_blocks = 4 allows
+ * hidden <= 224). */
 abc_status abc_maf_create(int32_t n_blocks, int32_t hidden, const abc_prior_box* box, abc_maf* maf_out);
 
 /* A set of n_flows (1..ABC_MAF_MAX_FLOWS) independent flows of the same shape

@@ -14,7 +14,7 @@ import torch
 
 from . import build as _build
 
-ABC_EXACT, ABC_FAST = 0, 1
+ABC_EXACT, ABC_FAST, ABC_VARIANCE_LITERAL = 0, 1, 4
 ABC_OK, ABC_ERR_INVALID_ARG, ABC_ERR_CAPACITY, ABC_ERR_CUDA, ABC_ERR_TIMEOUT, ABC_ERR_NOMEM = range(6)
 ABC_T_MAX = 4096
 
@@ -210,12 +210,17 @@ def _check(L, status, allow=()):
     return status
 
 
+_MODES = {"exact": 0, "fast": 1, "exact_literal": 4, "fast_literal": 5}
+
+
 def _mode(mode):
-    if mode in ("exact", ABC_EXACT):
-        return ABC_EXACT
-    if mode in ("fast", ABC_FAST):
-        return ABC_FAST
-    raise ValueError("mode must be 'exact' or 'fast'")
+    """'exact' or 'fast', with '_literal' for the literal-variance model
+    variant (ABC_VARIANCE_LITERAL), or the ABI's integer value."""
+    if isinstance(mode, str) and mode in _MODES:
+        return _MODES[mode]
+    if isinstance(mode, int) and mode in _MODES.values():
+        return mode
+    raise ValueError("mode must be one of %s" % ", ".join(_MODES))
 
 
 def prior_box(lo=PAPER_LO, hi=PAPER_HI):

@@ -122,6 +122,20 @@ abcgb::ModelParams make_params(const abc_prior_box* prior, int32_t T, int64_t N_
     return p;
 }
 
+// The public mode (ABC_EXACT or ABC_FAST, optionally | ABC_VARIANCE_LITERAL)
+// and the kernels' mode bits.
+bool valid_mode(abc_mode mode)
+{
+    const int base = (int)mode & ~(int)ABC_VARIANCE_LITERAL;
+    return base == ABC_EXACT || base == ABC_FAST;
+}
+
+int kernel_mode(abc_mode mode)
+{
+    return (((int)mode & ABC_FAST) ? abcgb::kFast : abcgb::kExact) |
+           (((int)mode & ABC_VARIANCE_LITERAL) ? abcgb::kLiteral : 0);
+}
+
 // Observed [3][T+1] rows A, R, D -> per-day int4 (A, R, D, 0).
 abc_status pack_observed(const int32_t* observed, int32_t T, int64_t N_pop, std::vector<int4>& out)
 {
@@ -291,7 +305,7 @@ abc_status abc_sample(const abc_prior_box* prior, const int32_t* observed, int32
     abc_status st;
     if ((st = check_prior(prior)) != ABC_OK) return st;
     if ((st = check_model(T, N_pop, stream)) != ABC_OK) return st;
-    if (mode != ABC_EXACT && mode != ABC_FAST) return fail(ABC_ERR_INVALID_ARG, "unknown mode %d", (int)mode);
+    if (!valid_mode(mode)) return fail(ABC_ERR_INVALID_ARG, "unknown mode %d", (int)mode);
     if (!(eps >= 0.0)) return fail(ABC_ERR_INVALID_ARG, "eps must be >= 0 and not NaN");
     if (!n_accepted) return fail(ABC_ERR_INVALID_ARG, "n_accepted is NULL");
     if (capacity > 0 && (!theta_out || !dist_out || !idx_out))
@@ -340,7 +354,7 @@ abc_status abc_sample(const abc_prior_box* prior, const int32_t* observed, int32
     a.theta_out = theta_out;
     a.dist_out = dist_out;
     a.idx_out = idx_out;
-    ce = abcgb::launch_reject(p, a, mode == ABC_FAST, s, nullptr);
+    ce = abcgb::launch_reject(p, a, kernel_mode(mode), s, nullptr);
     if (ce != cudaSuccess) return drain(cuda_fail(ce, "abc_reject_kernel launch"));
     ce = cudaMemcpyAsync(count_h, count_d, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
     if (ce != cudaSuccess) return drain(cuda_fail(ce, "cudaMemcpyAsync(counters)"));
@@ -398,7 +412,7 @@ abc_status abc_sample_async(const abc_prior_box* prior, abc_observed obs, double
     if ((st = check_prior(prior)) != ABC_OK) return st;
     if (!obs) return fail(ABC_ERR_INVALID_ARG, "observed handle is NULL");
     if ((st = check_model(obs->T, obs->N_pop, stream)) != ABC_OK) return st;
-    if (mode != ABC_EXACT && mode != ABC_FAST) return fail(ABC_ERR_INVALID_ARG, "unknown mode %d", (int)mode);
+    if (!valid_mode(mode)) return fail(ABC_ERR_INVALID_ARG, "unknown mode %d", (int)mode);
     if (!(eps >= 0.0)) return fail(ABC_ERR_INVALID_ARG, "eps must be >= 0 and not NaN");
     if (!counters_dev) return fail(ABC_ERR_INVALID_ARG, "counters_dev is NULL");
     if (capacity > 0 && (!theta_out || !dist_out || !idx_out))
@@ -426,7 +440,7 @@ abc_status abc_sample_async(const abc_prior_box* prior, abc_observed obs, double
     a.dist_out = dist_out;
     a.idx_out = idx_out;
     if (injected("launch")) return fail(ABC_ERR_CUDA, "kernel launch failed (injected)");
-    CUDA_TRY(abcgb::launch_reject(p, a, mode == ABC_FAST, s, nullptr), "abc_reject_kernel launch");
+    CUDA_TRY(abcgb::launch_reject(p, a, kernel_mode(mode), s, nullptr), "abc_reject_kernel launch");
     return ok();
 }
 
@@ -437,7 +451,7 @@ abc_status abc_distances(const abc_prior_box* prior, const int32_t* observed, in
     abc_status st;
     if ((st = check_prior(prior)) != ABC_OK) return st;
     if ((st = check_model(T, N_pop, stream)) != ABC_OK) return st;
-    if (mode != ABC_EXACT && mode != ABC_FAST) return fail(ABC_ERR_INVALID_ARG, "unknown mode %d", (int)mode);
+    if (!valid_mode(mode)) return fail(ABC_ERR_INVALID_ARG, "unknown mode %d", (int)mode);
     if (n_samples > 0 && !dist_out) return fail(ABC_ERR_INVALID_ARG, "dist_out is NULL");
     if (n_samples > ~(uint64_t)0 - first_index)
         return fail(ABC_ERR_INVALID_ARG, "first_index + n_samples overflows");
@@ -458,7 +472,7 @@ abc_status abc_distances(const abc_prior_box* prior, const int32_t* observed, in
     a.dist_out = dist_out;
     a.theta_out = theta_out;
     if (injected("launch")) return fail(ABC_ERR_CUDA, "kernel launch failed (injected)");
-    CUDA_TRY(abcgb::launch_distances(p, a, mode == ABC_FAST, s), "abc_distance_kernel launch");
+    CUDA_TRY(abcgb::launch_distances(p, a, kernel_mode(mode), s), "abc_distance_kernel launch");
     return ok();
 }
 
@@ -468,7 +482,7 @@ abc_status abc_simulate(const float* theta, const uint64_t* sample_index, uint64
 {
     abc_status st;
     if ((st = check_model(T, N_pop, stream)) != ABC_OK) return st;
-    if (mode != ABC_EXACT && mode != ABC_FAST) return fail(ABC_ERR_INVALID_ARG, "unknown mode %d", (int)mode);
+    if (!valid_mode(mode)) return fail(ABC_ERR_INVALID_ARG, "unknown mode %d", (int)mode);
     if ((st = check_initial(init_ard, N_pop)) != ABC_OK) return st;
     if (B > 0 && (!theta || !sample_index || !traj_out)) return fail(ABC_ERR_INVALID_ARG, "NULL device buffer");
     if (B == 0) return ok();
@@ -479,7 +493,7 @@ abc_status abc_simulate(const float* theta, const uint64_t* sample_index, uint64
     a.B = B;
     a.traj_out = traj_out;
     if (injected("launch")) return fail(ABC_ERR_CUDA, "kernel launch failed (injected)");
-    CUDA_TRY(abcgb::launch_simulate(p, a, mode == ABC_FAST, (cudaStream_t)cuda_stream), "abc_simulate_kernel launch");
+    CUDA_TRY(abcgb::launch_simulate(p, a, kernel_mode(mode), (cudaStream_t)cuda_stream), "abc_simulate_kernel launch");
     return ok();
 }
 
@@ -489,7 +503,7 @@ abc_status abc_step(const float* theta, const int32_t* state_in, const uint64_t*
 {
     abc_status st;
     if ((st = check_model(1, N_pop, stream)) != ABC_OK) return st;
-    if (mode != ABC_EXACT && mode != ABC_FAST) return fail(ABC_ERR_INVALID_ARG, "unknown mode %d", (int)mode);
+    if (!valid_mode(mode)) return fail(ABC_ERR_INVALID_ARG, "unknown mode %d", (int)mode);
     if (B > 0 && (!theta || !state_in || !sample_index || !day || !state_out))
         return fail(ABC_ERR_INVALID_ARG, "NULL device buffer");
     if (B == 0) return ok();
@@ -503,7 +517,7 @@ abc_status abc_step(const float* theta, const int32_t* state_in, const uint64_t*
     a.state_out = state_out;
     a.counts_out = counts_out;
     if (injected("launch")) return fail(ABC_ERR_CUDA, "kernel launch failed (injected)");
-    CUDA_TRY(abcgb::launch_step(p, a, mode == ABC_FAST, (cudaStream_t)cuda_stream), "abc_step_kernel launch");
+    CUDA_TRY(abcgb::launch_step(p, a, kernel_mode(mode), (cudaStream_t)cuda_stream), "abc_step_kernel launch");
     return ok();
 }
 
@@ -513,7 +527,7 @@ abc_status abc_project(const float* theta, const uint64_t* sample_index, uint64_
 {
     abc_status st;
     if ((st = check_model(T, N_pop, stream)) != ABC_OK) return st;
-    if (mode != ABC_EXACT && mode != ABC_FAST) return fail(ABC_ERR_INVALID_ARG, "unknown mode %d", (int)mode);
+    if (!valid_mode(mode)) return fail(ABC_ERR_INVALID_ARG, "unknown mode %d", (int)mode);
     if ((st = check_initial(init_ard, N_pop)) != ABC_OK) return st;
     if (B < 1 || B > ABC_PROJECT_MAX_B) return fail(ABC_ERR_INVALID_ARG, "B must be in [1, %d]", ABC_PROJECT_MAX_B);
     if (!theta || !sample_index || !bands_out || !quantiles || n_q < 1 || n_q > 1024)
@@ -537,7 +551,7 @@ abc_status abc_project(const float* theta, const uint64_t* sample_index, uint64_
     a.B = B;
     a.traj_out = traj;
     if (injected("launch")) return fail(ABC_ERR_CUDA, "kernel launch failed (injected)");
-    CUDA_TRY(abcgb::launch_simulate(p, a, mode == ABC_FAST, s), "abc_simulate_kernel launch");
+    CUDA_TRY(abcgb::launch_simulate(p, a, kernel_mode(mode), s), "abc_simulate_kernel launch");
     CUDA_TRY(abcgb::launch_bands(traj, (uint32_t)B, T, qd, n_q, bands_out, s), "band_kernel launch");
     // qpos (host) was staged synchronously enough: wait for the copy before it leaves scope
     CUDA_TRY(cudaStreamSynchronize(s), "cudaStreamSynchronize");
@@ -588,7 +602,7 @@ abc_status abc_sample_noalloc(const abc_prior_box* prior, const int32_t* observe
     if (T > ABC_NOALLOC_T_MAX)
         return fail(ABC_ERR_INVALID_ARG, "T = %d exceeds the no-alloc scratch limit of %d days", T,
                     ABC_NOALLOC_T_MAX);
-    if (mode != ABC_EXACT && mode != ABC_FAST) return fail(ABC_ERR_INVALID_ARG, "unknown mode %d", (int)mode);
+    if (!valid_mode(mode)) return fail(ABC_ERR_INVALID_ARG, "unknown mode %d", (int)mode);
     if (!(eps >= 0.0)) return fail(ABC_ERR_INVALID_ARG, "eps must be >= 0 and not NaN");
     if (!n_accepted) return fail(ABC_ERR_INVALID_ARG, "n_accepted is NULL");
     if (capacity > 0 && (!theta_out || !dist_out || !idx_out))
@@ -630,7 +644,7 @@ abc_status abc_sample_noalloc(const abc_prior_box* prior, const int32_t* observe
     a.theta_out = theta_out;
     a.dist_out = dist_out;
     a.idx_out = idx_out;
-    CUDA_TRY(abcgb::launch_reject(p, a, mode == ABC_FAST, s, nullptr), "abc_reject_kernel launch");
+    CUDA_TRY(abcgb::launch_reject(p, a, kernel_mode(mode), s, nullptr), "abc_reject_kernel launch");
     unsigned long long counters[3] = {0, 0, 0};
     CUDA_TRY(cudaMemcpyAsync(counters, count_d, sizeof counters, cudaMemcpyDeviceToHost, s),
              "cudaMemcpyAsync(counters)");

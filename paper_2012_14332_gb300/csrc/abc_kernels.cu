@@ -366,55 +366,72 @@ static cudaError_t launch_reject_t(const ModelParams& p, const RejectArgs& a, cu
     return cudaGetLastError();
 }
 
-cudaError_t launch_reject(const ModelParams& p, const RejectArgs& a, bool fast, cudaStream_t s, int* blocks_out)
+template <int MODE>
+static cudaError_t launch_reject_m(const ModelParams& p, const RejectArgs& a, cudaStream_t s, int* blocks_out)
 {
     const bool below62 = a.acc_max < 0x4000000000000000ull;
-    if (fast)
-        return below62 ? launch_reject_t<kFast, true>(p, a, s, blocks_out) : launch_reject_t<kFast, false>(p, a, s, blocks_out);
-    return below62 ? launch_reject_t<kExact, true>(p, a, s, blocks_out) : launch_reject_t<kExact, false>(p, a, s, blocks_out);
+    return below62 ? launch_reject_t<MODE, true>(p, a, s, blocks_out) : launch_reject_t<MODE, false>(p, a, s, blocks_out);
 }
 
-cudaError_t launch_distances(const ModelParams& p, const DistanceArgs& a, bool fast, cudaStream_t s)
+#define ABC_MODE_DISPATCH(fn, mode, ...)                        \
+    ((mode) == kFast ? fn<kFast>(__VA_ARGS__)                   \
+     : (mode) == kExact ? fn<kExact>(__VA_ARGS__)               \
+     : (mode) == (kFast | kLiteral) ? fn<kFast | kLiteral>(__VA_ARGS__) \
+                                  : fn<kExact | kLiteral>(__VA_ARGS__))
+
+cudaError_t launch_reject(const ModelParams& p, const RejectArgs& a, int mode, cudaStream_t s, int* blocks_out)
+{
+    return ABC_MODE_DISPATCH(launch_reject_m, mode, p, a, s, blocks_out);
+}
+
+template <int MODE>
+static cudaError_t launch_distances_m(const ModelParams& p, const DistanceArgs& a, cudaStream_t s)
 {
     const size_t smem = sizeof(int4) * (size_t)(p.T + 1);
     int grid = 0;
-    cudaError_t e = fast ? grid_for(abc_distance_kernel<kFast>, smem, &grid)
-                         : grid_for(abc_distance_kernel<kExact>, smem, &grid);
+    cudaError_t e = grid_for(abc_distance_kernel<MODE>, smem, &grid);
     if (e != cudaSuccess) return e;
     grid = blocks_for(a.n_samples, grid);
-    if (fast)
-        abc_distance_kernel<kFast><<<grid, kBlockThreads, smem, s>>>(p, a);
-    else
-        abc_distance_kernel<kExact><<<grid, kBlockThreads, smem, s>>>(p, a);
+    abc_distance_kernel<MODE><<<grid, kBlockThreads, smem, s>>>(p, a);
     return cudaGetLastError();
 }
 
-cudaError_t launch_simulate(const ModelParams& p, const SimulateArgs& a, bool fast, cudaStream_t s)
+cudaError_t launch_distances(const ModelParams& p, const DistanceArgs& a, int mode, cudaStream_t s)
+{
+    return ABC_MODE_DISPATCH(launch_distances_m, mode, p, a, s);
+}
+
+template <int MODE>
+static cudaError_t launch_simulate_m(const ModelParams& p, const SimulateArgs& a, cudaStream_t s)
 {
     const size_t smem = sizeof(int4) * (size_t)(p.T + 1);
     int grid = 0;
-    cudaError_t e = fast ? grid_for(abc_simulate_kernel<kFast>, smem, &grid)
-                         : grid_for(abc_simulate_kernel<kExact>, smem, &grid);
+    cudaError_t e = grid_for(abc_simulate_kernel<MODE>, smem, &grid);
     if (e != cudaSuccess) return e;
     grid = blocks_for(a.B, grid);
-    if (fast)
-        abc_simulate_kernel<kFast><<<grid, kBlockThreads, smem, s>>>(p, a);
-    else
-        abc_simulate_kernel<kExact><<<grid, kBlockThreads, smem, s>>>(p, a);
+    abc_simulate_kernel<MODE><<<grid, kBlockThreads, smem, s>>>(p, a);
     return cudaGetLastError();
 }
 
-cudaError_t launch_step(const ModelParams& p, const StepArgs& a, bool fast, cudaStream_t s)
+cudaError_t launch_simulate(const ModelParams& p, const SimulateArgs& a, int mode, cudaStream_t s)
+{
+    return ABC_MODE_DISPATCH(launch_simulate_m, mode, p, a, s);
+}
+
+template <int MODE>
+static cudaError_t launch_step_m(const ModelParams& p, const StepArgs& a, cudaStream_t s)
 {
     int grid = 0;
-    cudaError_t e = fast ? grid_for(abc_step_kernel<kFast>, 0, &grid) : grid_for(abc_step_kernel<kExact>, 0, &grid);
+    cudaError_t e = grid_for(abc_step_kernel<MODE>, 0, &grid);
     if (e != cudaSuccess) return e;
     grid = blocks_for(a.B, grid);
-    if (fast)
-        abc_step_kernel<kFast><<<grid, kBlockThreads, 0, s>>>(p, a);
-    else
-        abc_step_kernel<kExact><<<grid, kBlockThreads, 0, s>>>(p, a);
+    abc_step_kernel<MODE><<<grid, kBlockThreads, 0, s>>>(p, a);
     return cudaGetLastError();
+}
+
+cudaError_t launch_step(const ModelParams& p, const StepArgs& a, int mode, cudaStream_t s)
+{
+    return ABC_MODE_DISPATCH(launch_step_m, mode, p, a, s);
 }
 
 cudaError_t launch_bands(const int32_t* traj, uint32_t B, int32_t T, const float* qpos, int32_t n_q, float* bands,

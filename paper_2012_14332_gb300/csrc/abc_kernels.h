@@ -89,10 +89,11 @@ cudaError_t launch_advance(RegionDev* regions, int32_t n_regions, cudaStream_t s
 cudaError_t prepare_batch(bool fast, const BatchShape& shape);
 
 size_t reject_smem_bytes(int32_t T);
-cudaError_t launch_reject(const ModelParams& p, const RejectArgs& a, bool fast, cudaStream_t s, int* blocks_out);
-cudaError_t launch_distances(const ModelParams& p, const DistanceArgs& a, bool fast, cudaStream_t s);
-cudaError_t launch_simulate(const ModelParams& p, const SimulateArgs& a, bool fast, cudaStream_t s);
-cudaError_t launch_step(const ModelParams& p, const StepArgs& a, bool fast, cudaStream_t s);
+// mode: kExact or kFast, optionally | kLiteral (see abc_model.cuh)
+cudaError_t launch_reject(const ModelParams& p, const RejectArgs& a, int mode, cudaStream_t s, int* blocks_out);
+cudaError_t launch_distances(const ModelParams& p, const DistanceArgs& a, int mode, cudaStream_t s);
+cudaError_t launch_simulate(const ModelParams& p, const SimulateArgs& a, int mode, cudaStream_t s);
+cudaError_t launch_step(const ModelParams& p, const StepArgs& a, int mode, cudaStream_t s);
 cudaError_t launch_bands(const int32_t* traj, uint32_t B, int32_t T, const float* qpos, int32_t n_q, float* bands,
                          cudaStream_t s);
 cudaError_t launch_digit_histogram(const double* dist, uint64_t n, uint64_t prefix, uint64_t prefix_mask, int shift,

@@ -47,6 +47,14 @@ constexpr uint32_t kFull = 0xFFFFFFFFu;
 // Master (FP32) parameters of one block: W1 [H][8], b1 [H], W2 [16][H], b2 [16].
 __host__ __device__ inline int master_block(int H) { return 25 * H + 16; }
 
+// The gradient kernel's per-CTA accumulator of one block, in shared memory:
+// W1 [H][12], b1 [H], W2 [16][H + 4], b2 [16]. The padded row strides, with
+// odd row-groups writing their column pair in the opposite order, give the
+// warp's atomic adds 32 distinct banks (unpadded: W2 rows H apart share a
+// bank, 8-way conflicts).
+constexpr int kGW1Stride = 12;
+__host__ __device__ inline int grad_block(int H) { return 29 * H + 80; }
+
 // Published BF16 layout of one block, in 32-bit words (two bf16 per word).
 // The forward operands come first, so density and sampling kernels stage only
 // fwd_words per block; the gradient kernel stages all words. The forward
@@ -473,18 +481,34 @@ __global__ void __launch_bounds__(128) sample_kernel(const uint32_t* __restrict_
 // per-CTA gradient sums)
 constexpr int kGradWarpsNarrow = 4;
 constexpr int kGradWarpsWide = 16;
-constexpr int kStage = 12;   // staging row stride in 32-bit words (8 data + 4 pad)
+// Per-warp staging for the row-reducing weight-gradient products, row-major
+// [tile row][column] bf16 pairs as the accumulator layout produces them; the
+// transposed operands come back with ldmatrix .trans. Rows of 16 columns are
+// padded to 48 bytes (12 words) so that neither the stores (lane g, t writes
+// word 12 g + t) nor the 8-row ldmatrix reads meet a bank conflict; rows of
+// 8 columns are 16 bytes.
+constexpr int kStage = 12;
 
 struct WarpStage {
-    uint32_t goutT[16 * kStage];   // [o][row] bf16
-    uint32_t hT[16 * kStage];      // [l (16 of a chunk)][row]
-    uint32_t gaT[16 * kStage];     // [l][row]
-    uint32_t xT[8 * kStage];       // [j][row]
+    uint32_t gout[16 * kStage];    // g_out [row][o], o = 0..15
+    uint32_t h[16 * kStage];       // h [row][l], the chunk's 16 hidden units
+    uint32_t ga[16 * kStage];      // g_a1 [row][l]
+    uint32_t x[16 * 4];            // x [row][j], j = 0..7
 };
 
-__device__ __forceinline__ void put_bf16(uint32_t* base, int row, int col, float v)
+// four 8x8 bf16 matrices, transposed, one row address per lane (lanes 8m..8m+7: matrix m)
+__device__ __forceinline__ void ldsm_x4_trans(uint32_t (&r)[4], const uint32_t* row)
 {
-    reinterpret_cast<__nv_bfloat16*>(base)[row * 2 * kStage + col] = __float2bfloat16_rn(v);
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(row);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(a));
+}
+
+__device__ __forceinline__ void ldsm_x2_trans(uint32_t& r0, uint32_t& r1, const uint32_t* row)
+{
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(row);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0,%1}, [%2];\n" : "=r"(r0), "=r"(r1) : "r"(a));
 }
 
 // Training data of one flow: points theta [n][8], weights [n] (NULL = 1).
@@ -504,7 +528,7 @@ __global__ void __launch_bounds__(W * 32) grad_kernel(const uint32_t* __restrict
 {
     extern __shared__ __align__(16) uint32_t sm[];
     const Layout L = layout(H);
-    const int mb = master_block(H);
+    const int mb = master_block(H), gb = grad_block(H);
     const int f = blockIdx.y;
     const TrainSlot slot = slots[f];
     const uint64_t n_rows = rows_all ? (slot.n ? batch : 0) : slot.n;
@@ -517,9 +541,9 @@ __global__ void __launch_bounds__(W * 32) grad_kernel(const uint32_t* __restrict
     sums += 2 * f;
     uint32_t* wsm = sm;
     float* gsm = reinterpret_cast<float*>(sm + K * L.words);
-    WarpStage* stages = reinterpret_cast<WarpStage*>(gsm + K * mb);
+    WarpStage* stages = reinterpret_cast<WarpStage*>(gsm + K * gb);
     stage_weights(wsm, pub, K * L.words);
-    for (int i = threadIdx.x; i < K * mb; i += blockDim.x) gsm[i] = 0.f;
+    for (int i = threadIdx.x; i < K * gb; i += blockDim.x) gsm[i] = 0.f;
     __shared__ float ssum[2];
     if (threadIdx.x < 2) ssum[threadIdx.x] = 0.f;
     __syncthreads();
@@ -580,10 +604,11 @@ __global__ void __launch_bounds__(W * 32) grad_kernel(const uint32_t* __restrict
 #pragma unroll
         for (int b = K - 1; b >= 0; --b) {
             const BlockView v = view(wsm + b * L.words, L);
-            float* GW1 = gsm + b * mb;
-            float* GB1 = GW1 + 8 * H;
-            float* GW2 = GW1 + 9 * H;
-            float* GB2 = GW1 + 25 * H;
+            float* GW1 = gsm + b * gb;                // [H][kGW1Stride]
+            float* GB1 = GW1 + kGW1Stride * H;
+            float* GW2 = GB1 + H;                     // [16][H + 4]
+            float* GB2 = GW2 + 16 * (H + 4);
+            const int S2 = H + 4, sw = g & 1;
             reverse_cols(gx);   // gradient with respect to this block's output z
             float gmu[4], gar[4], gxd[4];
 #pragma unroll
@@ -595,19 +620,17 @@ __global__ void __launch_bounds__(W * 32) grad_kernel(const uint32_t* __restrict
                 const float r = as[b][e] / kAlphaMax;
                 gar[e] = ga * (1.f - r * r);
             }
-            // stage g_out^T [o][row] and x^T [j][row]
-            put_bf16(st.goutT, 2 * t, g, gmu[0]);
-            put_bf16(st.goutT, 2 * t + 1, g, gmu[1]);
-            put_bf16(st.goutT, 2 * t, g + 8, gmu[2]);
-            put_bf16(st.goutT, 2 * t + 1, g + 8, gmu[3]);
-            put_bf16(st.goutT, 8 + 2 * t, g, gar[0]);
-            put_bf16(st.goutT, 9 + 2 * t, g, gar[1]);
-            put_bf16(st.goutT, 8 + 2 * t, g + 8, gar[2]);
-            put_bf16(st.goutT, 9 + 2 * t, g + 8, gar[3]);
-            put_bf16(st.xT, 2 * t, g, xs[b][0]);
-            put_bf16(st.xT, 2 * t + 1, g, xs[b][1]);
-            put_bf16(st.xT, 2 * t, g + 8, xs[b][2]);
-            put_bf16(st.xT, 2 * t + 1, g + 8, xs[b][3]);
+            // g_out (A of g_h = g_out W2 and, transposed, of dW2) and x, packed
+            // in the accumulator layout and staged row-major
+            const uint32_t A0 = pack2(gmu[0], gmu[1]), A1 = pack2(gmu[2], gmu[3]);
+            const uint32_t A2 = pack2(gar[0], gar[1]), A3 = pack2(gar[2], gar[3]);
+            const uint32_t xa0 = pack2(xs[b][0], xs[b][1]), xa1 = pack2(xs[b][2], xs[b][3]);
+            st.gout[g * kStage + t] = A0;
+            st.gout[(g + 8) * kStage + t] = A1;
+            st.gout[g * kStage + 4 + t] = A2;
+            st.gout[(g + 8) * kStage + 4 + t] = A3;
+            st.x[g * 4 + t] = xa0;
+            st.x[(g + 8) * 4 + t] = xa1;
             // db2[o] = sum over rows of g_out
             {
                 float d[4] = {gmu[0] + gmu[2], gmu[1] + gmu[3], gar[0] + gar[2], gar[1] + gar[3]};
@@ -625,13 +648,18 @@ __global__ void __launch_bounds__(W * 32) grad_kernel(const uint32_t* __restrict
                 }
             }
             __syncwarp();
-            const uint32_t A0 = pack2(gmu[0], gmu[1]), A1 = pack2(gmu[2], gmu[3]);
-            const uint32_t A2 = pack2(gar[0], gar[1]), A3 = pack2(gar[2], gar[3]);
-            const uint32_t xa0 = pack2(xs[b][0], xs[b][1]), xa1 = pack2(xs[b][2], xs[b][3]);
+            // row addresses of the transposed loads: lane L feeds row L % 8 of
+            // matrix L / 8. For an A operand the matrices are the quadrants
+            // (rows 0-7 | 8-15) x (cols 0-7 | 8-15) in the order TL, TR, BL,
+            // BR; for a B operand TL, BL, TR, BR.
+            const int lm = lane >> 3, lr = lane & 7;
+            const int rowA = ((lm >> 1) << 3) + lr, colA = (lm & 1) << 2;
+            const int rowB = ((lm & 1) << 3) + lr, colB = (lm >> 1) << 2;
             // g_out^T (A of dW2) and x^T (B of dW1) are the same for every chunk
-            const uint32_t go0 = st.goutT[g * kStage + t], go1 = st.goutT[(g + 8) * kStage + t];
-            const uint32_t go2 = st.goutT[g * kStage + 4 + t], go3 = st.goutT[(g + 8) * kStage + 4 + t];
-            const uint32_t xt0 = st.xT[g * kStage + t], xt1 = st.xT[g * kStage + 4 + t];
+            uint32_t go[4];
+            ldsm_x4_trans(go, st.gout + rowA * kStage + colA);
+            uint32_t xt0, xt1;
+            ldsm_x2_trans(xt0, xt1, st.x + (((lane >> 3) & 1) * 8 + lr) * 4);
             float accx[4] = {0.f, 0.f, 0.f, 0.f};
             for (int s = 0; s < H / 16; ++s) {
                 // recompute the pre-activations of hidden units 16s .. 16s+15
@@ -640,15 +668,11 @@ __global__ void __launch_bounds__(W * 32) grad_kernel(const uint32_t* __restrict
                 float c0[4] = {bq.x, bq.y, bq.x, bq.y}, c1[4] = {bq.z, bq.w, bq.z, bq.w};
                 mma_k8(c0, xa0, xa1, wa.x);
                 mma_k8(c1, xa0, xa1, wa.y);
-                // h^T [l][row]
-                put_bf16(st.hT, 2 * t, g, fmaxf(c0[0], 0.f));
-                put_bf16(st.hT, 2 * t + 1, g, fmaxf(c0[1], 0.f));
-                put_bf16(st.hT, 2 * t, g + 8, fmaxf(c0[2], 0.f));
-                put_bf16(st.hT, 2 * t + 1, g + 8, fmaxf(c0[3], 0.f));
-                put_bf16(st.hT, 8 + 2 * t, g, fmaxf(c1[0], 0.f));
-                put_bf16(st.hT, 9 + 2 * t, g, fmaxf(c1[1], 0.f));
-                put_bf16(st.hT, 8 + 2 * t, g + 8, fmaxf(c1[2], 0.f));
-                put_bf16(st.hT, 9 + 2 * t, g + 8, fmaxf(c1[3], 0.f));
+                // h = relu(pre-activation), staged row-major
+                st.h[g * kStage + t] = pack2_relu(c0[0], c0[1]);
+                st.h[(g + 8) * kStage + t] = pack2_relu(c0[2], c0[3]);
+                st.h[g * kStage + 4 + t] = pack2_relu(c1[0], c1[1]);
+                st.h[(g + 8) * kStage + 4 + t] = pack2_relu(c1[2], c1[3]);
                 // g_h = g_out W2 for these units, then through the ReLU
                 float d0[4] = {0.f, 0.f, 0.f, 0.f}, d1[4] = {0.f, 0.f, 0.f, 0.f};
                 mma_k16(d0, A0, A1, A2, A3, v.w2t[(16 * s + g) * 12 + t], v.w2t[(16 * s + g) * 12 + 4 + t]);
@@ -658,14 +682,12 @@ __global__ void __launch_bounds__(W * 32) grad_kernel(const uint32_t* __restrict
                     d0[e] = c0[e] > 0.f ? d0[e] : 0.f;
                     d1[e] = c1[e] > 0.f ? d1[e] : 0.f;
                 }
-                put_bf16(st.gaT, 2 * t, g, d0[0]);
-                put_bf16(st.gaT, 2 * t + 1, g, d0[1]);
-                put_bf16(st.gaT, 2 * t, g + 8, d0[2]);
-                put_bf16(st.gaT, 2 * t + 1, g + 8, d0[3]);
-                put_bf16(st.gaT, 8 + 2 * t, g, d1[0]);
-                put_bf16(st.gaT, 9 + 2 * t, g, d1[1]);
-                put_bf16(st.gaT, 8 + 2 * t, g + 8, d1[2]);
-                put_bf16(st.gaT, 9 + 2 * t, g + 8, d1[3]);
+                const uint32_t P0 = pack2(d0[0], d0[1]), P1 = pack2(d0[2], d0[3]);
+                const uint32_t P2 = pack2(d1[0], d1[1]), P3 = pack2(d1[2], d1[3]);
+                st.ga[g * kStage + t] = P0;
+                st.ga[(g + 8) * kStage + t] = P1;
+                st.ga[g * kStage + 4 + t] = P2;
+                st.ga[(g + 8) * kStage + 4 + t] = P3;
                 // db1[l] = sum over rows of g_a1
                 {
                     float d[4] = {d0[0] + d0[2], d0[1] + d0[3], d1[0] + d1[2], d1[1] + d1[3]};
@@ -683,35 +705,45 @@ __global__ void __launch_bounds__(W * 32) grad_kernel(const uint32_t* __restrict
                     }
                 }
                 // g_x += g_a1 W1 (this chunk's 16 hidden units as k)
-                mma_k16(accx, pack2(d0[0], d0[1]), pack2(d0[2], d0[3]), pack2(d1[0], d1[1]), pack2(d1[2], d1[3]),
-                        v.w1t[g * hw + 8 * s + t], v.w1t[g * hw + 8 * s + 4 + t]);
+                mma_k16(accx, P0, P1, P2, P3, v.w1t[g * hw + 8 * s + t], v.w1t[g * hw + 8 * s + 4 + t]);
                 __syncwarp();
                 // dW2[o][l] += sum_rows g_out[row][o] h[row][l]
                 {
+                    uint32_t hb[4];   // B of e0: hb[0], hb[1]; of e1: hb[2], hb[3]
+                    ldsm_x4_trans(hb, st.h + rowB * kStage + colB);
                     float e0[4] = {0.f, 0.f, 0.f, 0.f}, e1[4] = {0.f, 0.f, 0.f, 0.f};
-                    mma_k16(e0, go0, go1, go2, go3, st.hT[g * kStage + t], st.hT[g * kStage + 4 + t]);
-                    mma_k16(e1, go0, go1, go2, go3, st.hT[(8 + g) * kStage + t], st.hT[(8 + g) * kStage + 4 + t]);
+                    mma_k16(e0, go[0], go[1], go[2], go[3], hb[0], hb[1]);
+                    mma_k16(e1, go[0], go[1], go[2], go[3], hb[2], hb[3]);
                     const int la = 16 * s + 2 * t, lb = 16 * s + 8 + 2 * t;
-                    if (mask2(g, la)) atomicAdd(&GW2[g * H + la], e0[0]);
-                    if (mask2(g, la + 1)) atomicAdd(&GW2[g * H + la + 1], e0[1]);
-                    if (mask2(g + 8, la)) atomicAdd(&GW2[(g + 8) * H + la], e0[2]);
-                    if (mask2(g + 8, la + 1)) atomicAdd(&GW2[(g + 8) * H + la + 1], e0[3]);
-                    if (mask2(g, lb)) atomicAdd(&GW2[g * H + lb], e1[0]);
-                    if (mask2(g, lb + 1)) atomicAdd(&GW2[g * H + lb + 1], e1[1]);
-                    if (mask2(g + 8, lb)) atomicAdd(&GW2[(g + 8) * H + lb], e1[2]);
-                    if (mask2(g + 8, lb + 1)) atomicAdd(&GW2[(g + 8) * H + lb + 1], e1[3]);
+                    // odd row-groups take their column pair in the other order
+                    const float e00 = sw ? e0[1] : e0[0], e01 = sw ? e0[0] : e0[1];
+                    const float e02 = sw ? e0[3] : e0[2], e03 = sw ? e0[2] : e0[3];
+                    const float e10 = sw ? e1[1] : e1[0], e11 = sw ? e1[0] : e1[1];
+                    const float e12 = sw ? e1[3] : e1[2], e13 = sw ? e1[2] : e1[3];
+                    const int pa = la + sw, qa = la + 1 - sw, pb = lb + sw, qb = lb + 1 - sw;
+                    if (mask2(g, pa)) atomicAdd(&GW2[g * S2 + pa], e00);
+                    if (mask2(g, qa)) atomicAdd(&GW2[g * S2 + qa], e01);
+                    if (mask2(g + 8, pa)) atomicAdd(&GW2[(g + 8) * S2 + pa], e02);
+                    if (mask2(g + 8, qa)) atomicAdd(&GW2[(g + 8) * S2 + qa], e03);
+                    if (mask2(g, pb)) atomicAdd(&GW2[g * S2 + pb], e10);
+                    if (mask2(g, qb)) atomicAdd(&GW2[g * S2 + qb], e11);
+                    if (mask2(g + 8, pb)) atomicAdd(&GW2[(g + 8) * S2 + pb], e12);
+                    if (mask2(g + 8, qb)) atomicAdd(&GW2[(g + 8) * S2 + qb], e13);
                 }
                 // dW1[l][j] += sum_rows g_a1[row][l] x[row][j]
                 {
-                    const uint32_t a0 = st.gaT[g * kStage + t], a1 = st.gaT[(g + 8) * kStage + t];
-                    const uint32_t a2 = st.gaT[g * kStage + 4 + t], a3 = st.gaT[(g + 8) * kStage + 4 + t];
+                    uint32_t ab[4];
+                    ldsm_x4_trans(ab, st.ga + rowA * kStage + colA);
                     float e0[4] = {0.f, 0.f, 0.f, 0.f};
-                    mma_k16(e0, a0, a1, a2, a3, xt0, xt1);
+                    mma_k16(e0, ab[0], ab[1], ab[2], ab[3], xt0, xt1);
                     const int la = 16 * s + g, lb = la + 8;
-                    if (mask1(la, 2 * t)) atomicAdd(&GW1[la * 8 + 2 * t], e0[0]);
-                    if (mask1(la, 2 * t + 1)) atomicAdd(&GW1[la * 8 + 2 * t + 1], e0[1]);
-                    if (mask1(lb, 2 * t)) atomicAdd(&GW1[lb * 8 + 2 * t], e0[2]);
-                    if (mask1(lb, 2 * t + 1)) atomicAdd(&GW1[lb * 8 + 2 * t + 1], e0[3]);
+                    const int ja = 2 * t + sw, jb = 2 * t + 1 - sw;
+                    const float f0 = sw ? e0[1] : e0[0], f1 = sw ? e0[0] : e0[1];
+                    const float f2 = sw ? e0[3] : e0[2], f3 = sw ? e0[2] : e0[3];
+                    if (mask1(la, ja)) atomicAdd(&GW1[la * kGW1Stride + ja], f0);
+                    if (mask1(la, jb)) atomicAdd(&GW1[la * kGW1Stride + jb], f1);
+                    if (mask1(lb, ja)) atomicAdd(&GW1[lb * kGW1Stride + ja], f2);
+                    if (mask1(lb, jb)) atomicAdd(&GW1[lb * kGW1Stride + jb], f3);
                 }
                 __syncwarp();
             }
@@ -720,9 +752,28 @@ __global__ void __launch_bounds__(W * 32) grad_kernel(const uint32_t* __restrict
         }
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < K * mb; i += blockDim.x) {
-        const float v = gsm[i];
-        if (v != 0.f) atomicAdd(&grad[i], v);
+    // flush in the parameter order: W1 [H][8], b1 [H], W2 [16][H], b2 [16]
+    for (int b = 0; b < K; ++b) {
+        const float* G = gsm + b * gb;
+        float* out = grad + b * mb;
+        for (int i = threadIdx.x; i < 8 * H; i += blockDim.x) {
+            const float v = G[(i >> 3) * kGW1Stride + (i & 7)];
+            if (v != 0.f) atomicAdd(&out[i], v);
+        }
+        for (int i = threadIdx.x; i < H; i += blockDim.x) {
+            const float v = G[kGW1Stride * H + i];
+            if (v != 0.f) atomicAdd(&out[8 * H + i], v);
+        }
+        const float* G2 = G + (kGW1Stride + 1) * H;
+        for (int o = 0; o < 16; ++o)
+            for (int l = threadIdx.x; l < H; l += blockDim.x) {
+                const float v = G2[o * (H + 4) + l];
+                if (v != 0.f) atomicAdd(&out[9 * H + o * H + l], v);
+            }
+        if (threadIdx.x < 16) {
+            const float v = G2[16 * (H + 4) + threadIdx.x];
+            if (v != 0.f) atomicAdd(&out[25 * H + threadIdx.x], v);
+        }
     }
     if (threadIdx.x < 2) atomicAdd(&sums[threadIdx.x], ssum[threadIdx.x]);
 }
@@ -808,7 +859,7 @@ size_t fwd_smem(const abc_maf_s* f) { return sizeof(uint32_t) * (size_t)f->K * m
 size_t grad_smem(const abc_maf_s* f, int warps)
 {
     return sizeof(uint32_t) * (size_t)f->K * maf::layout(f->H).words +
-           sizeof(float) * (size_t)f->K * maf::master_block(f->H) + sizeof(maf::WarpStage) * warps;
+           sizeof(float) * (size_t)f->K * maf::grad_block(f->H) + sizeof(maf::WarpStage) * warps;
 }
 
 abc_status check(abc_maf f)
@@ -826,6 +877,14 @@ abc_status check_flow(abc_maf f, int32_t r)
     if ((st = check(f)) != ABC_OK) return st;
     if (r < 0 || r >= f->R) return plan_fail(ABC_ERR_INVALID_ARG, "flow index out of range");
     return ABC_OK;
+}
+
+size_t max_smem_optin()
+{
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    return (size_t)v;
 }
 
 int sm_count()
@@ -910,7 +969,7 @@ cudaError_t launch_grad(abc_maf f, const uint32_t* rows, uint32_t batch, uint64_
 {
     const uint64_t tiles = ((rows ? batch : max_n) + 15) / 16;
     const uint64_t narrow_ctas = (tiles + maf::kGradWarpsNarrow - 1) / maf::kGradWarpsNarrow * (uint64_t)f->R;
-    if (narrow_ctas > 2 * (uint64_t)sm_count() && grad_smem(f, maf::kGradWarpsWide) <= 227 * 1024)
+    if (narrow_ctas > 2 * (uint64_t)sm_count() && grad_smem(f, maf::kGradWarpsWide) <= max_smem_optin())
         return launch_grad_w<K, maf::kGradWarpsWide>(f, rows, batch, tiles, s);
     return launch_grad_w<K, maf::kGradWarpsNarrow>(f, rows, batch, tiles, s);
 }
@@ -985,6 +1044,10 @@ abc_status abc_maf_create_multi(int32_t n_flows, int32_t n_blocks, int32_t hidde
         abc_maf_destroy(f);
         return e;
     };
+    if (grad_smem(f, maf::kGradWarpsNarrow) > max_smem_optin())
+        return fail_free(plan_fail(ABC_ERR_INVALID_ARG,
+                                   "the gradient kernel of this flow (blocks x hidden) needs more shared memory per "
+                                   "block than the device has; use fewer blocks or hidden units"));
     const size_t np = sizeof(float) * f->n_params * f->R;
     cudaError_t e;
     if ((e = cudaGetDevice(&f->device)) != cudaSuccess || (e = cudaMalloc(&f->d_params, np)) != cudaSuccess ||

@@ -31,7 +31,11 @@
 
 namespace abcgb {
 
-enum : int { kExact = 0, kFast = 1 };
+// Arithmetic mode of a kernel instance: bit 0 fast (else exact), bit 1 the
+// literal reading of the transition variance (std h^(1/4), else sqrt(h)).
+enum : int { kExact = 0, kFast = 1, kLiteral = 2 };
+__host__ __device__ constexpr bool is_fast(int mode) { return (mode & kFast) != 0; }
+__host__ __device__ constexpr bool is_literal(int mode) { return (mode & kLiteral) != 0; }
 
 // ---------------------------------------------------------------------------
 // Kernel parameters (passed by value; lives in the constant bank).
@@ -194,7 +198,7 @@ template <int MODE>
 __device__ __forceinline__ void box_muller(uint32_t w_radius, uint32_t w_angle, float& z0, float& z1)
 {
     const float u1 = uniform01(w_radius);
-    if (MODE == kExact) {
+    if (!is_fast(MODE)) {
         const float u2 = uniform01(w_angle);
         const float r = __fsqrt_rn(__fmul_rn(exact::kNeg2Ln2, exact::log2x(u1)));
         float s, c;
@@ -273,7 +277,7 @@ __device__ __forceinline__ Theta make_theta(const float th[8], float inv_p)
     t.a0 = th[0]; t.a = th[1]; t.n = th[2]; t.beta = th[3]; t.gamma = th[4]; t.delta = th[5];
     t.beta_eta = __fmul_rn(th[3], th[6]);
     t.kappa = th[7];
-    if (MODE == kFast) {
+    if (is_fast(MODE)) {
         t.a0 = th[0] * inv_p;
         t.a = th[1] * inv_p;
     }
@@ -301,7 +305,7 @@ __device__ __forceinline__ void model_day(State& x, const Theta& t, float inv_p,
     const float Sf = __int2float_rn(x.S), If = __int2float_rn(x.I), Af = __int2float_rn(x.A);
     const int32_t U = x.A + x.R + x.D;
     float h0, h1, h2, h3, h4, v0, v1, v2, v3, v4;
-    if (MODE == kExact) {
+    if (!is_fast(MODE)) {
         float pw = 0.0f;
         if (U != 0) pw = exact::exp2x(__fmul_rn(t.n, exact::log2x(__int2float_rn(U))));
         const float g = __fadd_rn(t.a0, __fdiv_rn(t.a, __fadd_rn(1.0f, pw)));
@@ -310,11 +314,13 @@ __device__ __forceinline__ void model_day(State& x, const Theta& t, float inv_p,
         h2 = __fmul_rn(t.beta, Af);
         h3 = __fmul_rn(t.delta, Af);
         h4 = __fmul_rn(t.beta_eta, If);
-        v0 = __fadd_rn(h0, __fmul_rn(__fsqrt_rn(h0), z[0]));
-        v1 = __fadd_rn(h1, __fmul_rn(__fsqrt_rn(h1), z[1]));
-        v2 = __fadd_rn(h2, __fmul_rn(__fsqrt_rn(h2), z[2]));
-        v3 = __fadd_rn(h3, __fmul_rn(__fsqrt_rn(h3), z[3]));
-        v4 = __fadd_rn(h4, __fmul_rn(__fsqrt_rn(h4), z[4]));
+        // standard deviation sqrt(h), or h^(1/4) = sqrt(sqrt(h)) under the literal reading
+        auto sd = [](float h) { return is_literal(MODE) ? __fsqrt_rn(__fsqrt_rn(h)) : __fsqrt_rn(h); };
+        v0 = __fadd_rn(h0, __fmul_rn(sd(h0), z[0]));
+        v1 = __fadd_rn(h1, __fmul_rn(sd(h1), z[1]));
+        v2 = __fadd_rn(h2, __fmul_rn(sd(h2), z[2]));
+        v3 = __fadd_rn(h3, __fmul_rn(sd(h3), z[3]));
+        v4 = __fadd_rn(h4, __fmul_rn(sd(h4), z[4]));
     } else {
         const float pw = (U != 0) ? fast::ex2(t.n * fast::lg2(__int2float_rn(U))) : 0.0f;
         const float g_over_p = __fmaf_rn(t.a, fast::rcp(1.0f + pw), t.a0);   // a0, a carry 1/P
@@ -323,11 +329,12 @@ __device__ __forceinline__ void model_day(State& x, const Theta& t, float inv_p,
         h2 = t.beta * Af;
         h3 = t.delta * Af;
         h4 = t.beta_eta * If;
-        v0 = __fmaf_rn(fast::sqrt_a(h0), z[0], h0);
-        v1 = __fmaf_rn(fast::sqrt_a(h1), z[1], h1);
-        v2 = __fmaf_rn(fast::sqrt_a(h2), z[2], h2);
-        v3 = __fmaf_rn(fast::sqrt_a(h3), z[3], h3);
-        v4 = __fmaf_rn(fast::sqrt_a(h4), z[4], h4);
+        auto sd = [](float h) { return is_literal(MODE) ? fast::sqrt_a(fast::sqrt_a(h)) : fast::sqrt_a(h); };
+        v0 = __fmaf_rn(sd(h0), z[0], h0);
+        v1 = __fmaf_rn(sd(h1), z[1], h1);
+        v2 = __fmaf_rn(sd(h2), z[2], h2);
+        v3 = __fmaf_rn(sd(h3), z[3], h3);
+        v4 = __fmaf_rn(sd(h4), z[4], h4);
     }
     // clamp against what is left of each source, in h order
     const int32_t n_si = clamp_count(v0, x.S);
