@@ -46,7 +46,10 @@ struct LaneRegion {
     float inv_p;
 };
 
-template <int MODE, int BLOCK, int PAIRS>
+// BELOW62: every region's acc_max < 2^62, so the running sum can be clamped at
+// 2^62 each day instead of saturating exactly at 2^63 (fewer instructions; the
+// accept sets and accepted distances are the same, as in abc_reject_kernel).
+template <int MODE, int BLOCK, int PAIRS, bool BELOW62>
 __global__ void __launch_bounds__(BLOCK) abc_batch_kernel(const __grid_constant__ ModelParams p,
                                                           const __grid_constant__ BatchArgs a)
 {
@@ -151,10 +154,11 @@ __global__ void __launch_bounds__(BLOCK) abc_batch_kernel(const __grid_constant_
                 const int32_t d1 = (int32_t)(2 * k - 1);
                 const int4* obs = a.obs + lr.obs_off;
                 model_day<MODE>(x, t, lr.inv_p, z);
-                acc = add_day_sq(acc, x, __ldg(obs + d1));
+                acc = BELOW62 ? add_day_sq_below62(acc, x, __ldg(obs + d1)) : add_day_sq(acc, x, __ldg(obs + d1));
                 if (d1 < lr.T) {
                     model_day<MODE>(x, t, lr.inv_p, z + 5);
-                    acc = add_day_sq(acc, x, __ldg(obs + d1 + 1));
+                    acc = BELOW62 ? add_day_sq_below62(acc, x, __ldg(obs + d1 + 1))
+                                  : add_day_sq(acc, x, __ldg(obs + d1 + 1));
                     days += 2;
                 } else {
                     days += 1;
@@ -201,10 +205,10 @@ static const BatchShape kShapes[] = {
 int batch_shape_count() { return (int)(sizeof kShapes / sizeof kShapes[0]); }
 BatchShape batch_shape(int index) { return kShapes[index]; }
 
-template <int MODE, int BLOCK, int PAIRS>
+template <int MODE, int BLOCK, int PAIRS, bool BELOW62>
 static cudaError_t launch_t(const ModelParams& p, const BatchArgs* a, int blocks_per_sm, cudaStream_t s)
 {
-    auto kernel = abc_batch_kernel<MODE, BLOCK, PAIRS>;
+    auto kernel = abc_batch_kernel<MODE, BLOCK, PAIRS, BELOW62>;
     const size_t smem = sizeof(BatchRing) * (BLOCK / 32);
     int dev = 0, sms = 0, fit = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -223,27 +227,36 @@ static cudaError_t launch_t(const ModelParams& p, const BatchArgs* a, int blocks
     return cudaGetLastError();
 }
 
-template <int MODE>
+template <int MODE, bool B62>
 static cudaError_t dispatch(const ModelParams& p, const BatchArgs* a, const BatchShape& sh, cudaStream_t s)
 {
-    if (sh.block_threads == 128 && sh.pairs == 1) return launch_t<MODE, 128, 1>(p, a, sh.blocks_per_sm, s);
-    if (sh.block_threads == 256 && sh.pairs == 1) return launch_t<MODE, 256, 1>(p, a, sh.blocks_per_sm, s);
-    if (sh.block_threads == 512 && sh.pairs == 1) return launch_t<MODE, 512, 1>(p, a, sh.blocks_per_sm, s);
-    if (sh.block_threads == 128 && sh.pairs == 2) return launch_t<MODE, 128, 2>(p, a, sh.blocks_per_sm, s);
-    if (sh.block_threads == 256 && sh.pairs == 2) return launch_t<MODE, 256, 2>(p, a, sh.blocks_per_sm, s);
-    if (sh.block_threads == 512 && sh.pairs == 2) return launch_t<MODE, 512, 2>(p, a, sh.blocks_per_sm, s);
+    if (sh.block_threads == 128 && sh.pairs == 1) return launch_t<MODE, 128, 1, B62>(p, a, sh.blocks_per_sm, s);
+    if (sh.block_threads == 256 && sh.pairs == 1) return launch_t<MODE, 256, 1, B62>(p, a, sh.blocks_per_sm, s);
+    if (sh.block_threads == 512 && sh.pairs == 1) return launch_t<MODE, 512, 1, B62>(p, a, sh.blocks_per_sm, s);
+    if (sh.block_threads == 128 && sh.pairs == 2) return launch_t<MODE, 128, 2, B62>(p, a, sh.blocks_per_sm, s);
+    if (sh.block_threads == 256 && sh.pairs == 2) return launch_t<MODE, 256, 2, B62>(p, a, sh.blocks_per_sm, s);
+    if (sh.block_threads == 512 && sh.pairs == 2) return launch_t<MODE, 512, 2, B62>(p, a, sh.blocks_per_sm, s);
     return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_batch(const ModelParams& p, const BatchArgs& a, bool fast, const BatchShape& shape, cudaStream_t s)
+template <bool B62>
+static cudaError_t dispatch_mode(const ModelParams& p, const BatchArgs* a, bool fast, const BatchShape& sh,
+                                 cudaStream_t s)
 {
-    return fast ? dispatch<kFast>(p, &a, shape, s) : dispatch<kExact>(p, &a, shape, s);
+    return fast ? dispatch<kFast, B62>(p, a, sh, s) : dispatch<kExact, B62>(p, a, sh, s);
 }
 
-cudaError_t prepare_batch(bool fast, const BatchShape& shape)
+cudaError_t launch_batch(const ModelParams& p, const BatchArgs& a, bool fast, bool below62, const BatchShape& shape,
+                         cudaStream_t s)
+{
+    return below62 ? dispatch_mode<true>(p, &a, fast, shape, s) : dispatch_mode<false>(p, &a, fast, shape, s);
+}
+
+cudaError_t prepare_batch(bool fast, bool below62, const BatchShape& shape)
 {
     ModelParams p{};
-    return fast ? dispatch<kFast>(p, nullptr, shape, nullptr) : dispatch<kExact>(p, nullptr, shape, nullptr);
+    return below62 ? dispatch_mode<true>(p, nullptr, fast, shape, nullptr)
+                   : dispatch_mode<false>(p, nullptr, fast, shape, nullptr);
 }
 
 cudaError_t launch_advance(RegionDev* regions, int32_t n_regions, cudaStream_t s)

@@ -84,9 +84,11 @@ struct BatchShape {
 int batch_shape_count();
 BatchShape batch_shape(int index);
 
-cudaError_t launch_batch(const ModelParams& p, const BatchArgs& a, bool fast, const BatchShape& shape, cudaStream_t s);
+// below62: every region's acc_max < 2^62 (the cheaper distance accumulation)
+cudaError_t launch_batch(const ModelParams& p, const BatchArgs& a, bool fast, bool below62, const BatchShape& shape,
+                         cudaStream_t s);
 cudaError_t launch_advance(RegionDev* regions, int32_t n_regions, cudaStream_t s);
-cudaError_t prepare_batch(bool fast, const BatchShape& shape);
+cudaError_t prepare_batch(bool fast, bool below62, const BatchShape& shape);
 
 size_t reject_smem_bytes(int32_t T);
 // mode: kExact or kFast, optionally | kLiteral (see abc_model.cuh)

@@ -165,6 +165,12 @@ __device__ __forceinline__ void reverse_cols(float (&v)[4])
 
 __device__ __forceinline__ float soft_alpha(float ar) { return kAlphaMax * tanhf(ar / kAlphaMax); }
 
+// Density and sampling CTAs: 8 warps share one staged copy of the forward
+// operands (about 41 KB at 3 x 256), at most 64 registers so that 4 CTAs
+// (32 warps) fit on an SM to hide the tensor-core chains' latency.
+constexpr int kFwdThreads = 256;
+constexpr int kFwdMinBlocks = 4;
+
 // The base density: independent standard logistic coordinates,
 // log p(z) = -|z| - 2 log(1 + exp(-|z|)); d(-log p)/dz = tanh(z / 2). The logit
 // of a uniform variable is standard logistic, so the flow with zero
@@ -327,7 +333,7 @@ __global__ void publish_kernel(const float* __restrict__ master, uint32_t* __res
 // The proposal may use a broadened base, z = tau * (standard logistic), with
 // density log p(z / tau) - log tau per coordinate (tau = 1: the trained flow).
 template <int K>
-__global__ void __launch_bounds__(128) logq_kernel(const uint32_t* __restrict__ pub, int H, Box box,
+__global__ void __launch_bounds__(kFwdThreads, kFwdMinBlocks) logq_kernel(const uint32_t* __restrict__ pub, int H, Box box,
                                                    const float* __restrict__ theta, uint64_t n, float inv_tau,
                                                    float log_tau, float* __restrict__ logq)
 {
@@ -377,7 +383,7 @@ __global__ void __launch_bounds__(128) logq_kernel(const uint32_t* __restrict__ 
 // sampling: base draws -> sequential inverse -> theta, log q(theta)
 // ---------------------------------------------------------------------------
 template <int K>
-__global__ void __launch_bounds__(128) sample_kernel(const uint32_t* __restrict__ pub, int H, Box box,
+__global__ void __launch_bounds__(kFwdThreads, kFwdMinBlocks) sample_kernel(const uint32_t* __restrict__ pub, int H, Box box,
                                                      const float* __restrict__ u_in, const __grid_constant__ ModelParams p,
                                                      uint32_t ctr3, uint64_t first, uint64_t n, float tau,
                                                      float log_tau, float* __restrict__ theta_out,
@@ -929,8 +935,8 @@ cudaError_t launch_logq(abc_maf f, int r, uint64_t n, const float* theta, float*
     cudaError_t e = allow_smem(maf::logq_kernel<K>, smem);
     if (e != cudaSuccess) return e;
     const uint64_t tiles = (n + 15) / 16;
-    const int grid = fill_grid(maf::logq_kernel<K>, 128, smem, (tiles + 3) / 4);
-    maf::logq_kernel<K><<<grid, 128, smem, s>>>(flow_pub(f, r), f->H, f->box, theta, n, 1.f / f->tau, logf(f->tau),
+    const int grid = fill_grid(maf::logq_kernel<K>, maf::kFwdThreads, smem, (tiles + 7) / 8);
+    maf::logq_kernel<K><<<grid, maf::kFwdThreads, smem, s>>>(flow_pub(f, r), f->H, f->box, theta, n, 1.f / f->tau, logf(f->tau),
                                                 logq);
     return cudaGetLastError();
 }
@@ -943,8 +949,8 @@ cudaError_t launch_sample(abc_maf f, int r, uint64_t n, const float* u, const Mo
     cudaError_t e = allow_smem(maf::sample_kernel<K>, smem);
     if (e != cudaSuccess) return e;
     const uint64_t tiles = (n + 15) / 16;
-    const int grid = fill_grid(maf::sample_kernel<K>, 128, smem, (tiles + 3) / 4);
-    maf::sample_kernel<K><<<grid, 128, smem, s>>>(flow_pub(f, r), f->H, f->box, u, p, ctr3, first, n, f->tau,
+    const int grid = fill_grid(maf::sample_kernel<K>, maf::kFwdThreads, smem, (tiles + 7) / 8);
+    maf::sample_kernel<K><<<grid, maf::kFwdThreads, smem, s>>>(flow_pub(f, r), f->H, f->box, u, p, ctr3, first, n, f->tau,
                                                   logf(f->tau), theta, logq);
     return cudaGetLastError();
 }

@@ -41,6 +41,7 @@ struct abc_plan_s {
     abcgb::BatchShape shape{256, 1, 0};
     cudaGraphExec_t graph = nullptr;
     int32_t graph_runs = 0;
+    bool graph_below62 = false;   // the kernel variant the graph was captured with
 };
 
 namespace {
@@ -85,6 +86,14 @@ abc_status upload_table(abc_plan plan)
     return ABC_OK;
 }
 
+// every region's threshold below 2^62: the batched kernel's cheaper variant
+bool below62(const abc_plan_s* plan)
+{
+    for (int32_t r = 0; r < plan->n_regions; ++r)
+        if (plan->regions[r].acc_max >= 0x4000000000000000ull) return false;
+    return true;
+}
+
 abc_status run_once(abc_plan plan, cudaStream_t s)
 {
     PLAN_TRY(cudaMemsetAsync(plan->d_next, 0, sizeof(unsigned long long), s), "cudaMemsetAsync(claims)");
@@ -94,7 +103,7 @@ abc_status run_once(abc_plan plan, cudaStream_t s)
     a.total_chunks = plan->total_chunks;
     a.obs = plan->d_obs;
     a.next = plan->d_next;
-    PLAN_TRY(abcgb::launch_batch(plan->p, a, plan->fast, plan->shape, s), "abc_batch_kernel launch");
+    PLAN_TRY(abcgb::launch_batch(plan->p, a, plan->fast, below62(plan), plan->shape, s), "abc_batch_kernel launch");
     PLAN_TRY(abcgb::launch_advance(plan->d_regions, plan->n_regions, s), "advance launch");
     return ABC_OK;
 }
@@ -202,7 +211,9 @@ abc_status abc_plan_create(const abc_prior_box* prior, const abc_region* regions
         (e = cudaMemset(pl->d_counters, 0, 2 * sizeof(unsigned long long) * n_regions)) != cudaSuccess)
         return cleanup(plan_cuda_fail(e, "plan upload"));
     if ((st = upload_table(pl)) != ABC_OK) return cleanup(st);
-    if ((e = abcgb::prepare_batch(pl->fast, pl->shape)) != cudaSuccess)
+    // both distance-accumulation variants: either may be launched (or captured) later
+    if ((e = abcgb::prepare_batch(pl->fast, true, pl->shape)) != cudaSuccess ||
+        (e = abcgb::prepare_batch(pl->fast, false, pl->shape)) != cudaSuccess)
         return cleanup(plan_cuda_fail(e, "prepare_batch"));
     *plan_out = pl;
     return plan_ok();
@@ -232,7 +243,7 @@ abc_status abc_plan_run_graph(abc_plan plan, int32_t n_runs, void* cuda_stream)
     if ((st = check_plan(plan)) != ABC_OK) return st;
     if (n_runs < 1) return plan_fail(ABC_ERR_INVALID_ARG, "n_runs must be >= 1");
     cudaStream_t s = (cudaStream_t)cuda_stream;
-    if (!plan->graph || plan->graph_runs != n_runs) {
+    if (!plan->graph || plan->graph_runs != n_runs || plan->graph_below62 != below62(plan)) {
         if (!s) return plan_fail(ABC_ERR_INVALID_ARG, "graph capture needs a non-default stream");
         if (plan->graph) {
             cudaGraphExecDestroy(plan->graph);
@@ -255,6 +266,7 @@ abc_status abc_plan_run_graph(abc_plan plan, int32_t n_runs, void* cuda_stream)
             return plan_cuda_fail(e, "cudaGraphInstantiate");
         }
         plan->graph_runs = n_runs;
+        plan->graph_below62 = below62(plan);
     }
     PLAN_TRY(cudaGraphLaunch(plan->graph, s), "cudaGraphLaunch");
     return plan_ok();
@@ -287,7 +299,7 @@ abc_status abc_plan_tune(abc_plan plan, void* cuda_stream, abc_launch_shape* sha
     abc_status result = ABC_OK;
     for (int c = 0; c < n && result == ABC_OK; ++c) {
         plan->shape = abcgb::batch_shape(c);
-        cudaError_t e = abcgb::prepare_batch(plan->fast, plan->shape);
+        cudaError_t e = abcgb::prepare_batch(plan->fast, below62(plan), plan->shape);
         if (e != cudaSuccess) { result = plan_cuda_fail(e, "prepare_batch"); break; }
         float ms = 0.0f;
         // one untimed run to warm up, one timed run; both on tuning sample ranges

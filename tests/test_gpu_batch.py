@@ -156,3 +156,30 @@ def test_nan_proposals_are_skipped():
     assert n_acc == len(keep) and np.array_equal(ix, keep + first) and np.array_equal(tt, th[keep])
     assert days == len(keep) * w["T"]
     plan.close()
+
+
+def test_graph_follows_an_eps_change_across_2_to_the_62():
+    """The batched kernel has a cheaper distance accumulation for thresholds
+    below 2^62; a graph captured with it is recaptured when set_eps moves a
+    region's threshold past 2^62 (eps >= 2^31), so replays stay exact."""
+    w = inputs.workload("region_1e6_T49")
+    n = 4096
+    reg = dict(observed=w["observed"], N_pop=w["P"], eps=1e4, n_samples=n, first_index=0, stream=2, capacity=n)
+    a = abc.Plan([reg], SEED, mode="exact")
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        a.run_graph(1, cuda_stream=s)
+        s.synchronize()
+        a.reset(s)
+        a.set_region(0, None, 0)
+        a.set_eps(0, 2.0 ** 40)
+        a.run_graph(1, cuda_stream=s)
+        s.synchronize()
+    b = abc.Plan([dict(reg, eps=2.0 ** 40)], SEED, mode="exact")
+    b.run()
+    ra, rb = a.results(0), b.results(0)
+    assert ra[3] == rb[3] == n
+    for x, y in zip(_sorted(*ra[:3]), _sorted(*rb[:3])):
+        assert np.array_equal(x, y)
+    a.close()
+    b.close()
