@@ -115,7 +115,12 @@ def measured_peaks():
     return None
 
 
-def roofline(sim_days_per_launch, launch_ms, sm_count, sm_max_mhz):
+# dram__bytes_read.sum + dram__bytes_write.sum of one headline launch after an
+# L2 flush, from ncu (profiles/abc_reject_kernel_traffic_region_6e7_T100.md)
+REJECT_TRAFFIC_BYTES = 267008
+
+
+def roofline(sim_days_per_launch, launch_ms, sm_count, sm_max_mhz, traffic=None):
     """ALU roofline: the fastest a launch could run if the tighter of issue
     slots and SFU throughput for the method's instructions (OPS_PER_SIM_DAY)
     were saturated on every SM at the maximum SM clock. In simulated days/s,
@@ -125,7 +130,7 @@ def roofline(sim_days_per_launch, launch_ms, sm_count, sm_max_mhz):
     peak = sm_count * sm_max_mhz * 1e6 / clk_per_sim_day
     achieved = sim_days_per_launch / (launch_ms * 1e-3)
     return {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Gsim*days/s",
-            "frac": achieved / peak, "traffic": None, "pipe": bound_pipe,
+            "frac": achieved / peak, "traffic": traffic, "pipe": bound_pipe,
             "peak_basis": "%d SMs x %.0f MHz (max SM clock) / %.3f clk per sim-day on the %s pipe" % (
                 sm_count, sm_max_mhz, clk_per_sim_day, bound_pipe)}
 
@@ -521,7 +526,8 @@ def main():
         props = torch.cuda.get_device_properties(dev)
         peaks = measured_peaks() or {}
         sm_max = clocks.get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2070.0
-        rf = roofline(sim_days[0] / args.steps, float(np.mean(launch_ms)), props.multi_processor_count, sm_max)
+        rf = roofline(sim_days[0] / args.steps, float(np.mean(launch_ms)), props.multi_processor_count, sm_max,
+                      traffic=REJECT_TRAFFIC_BYTES if w["n_samples"] == 1 << 24 else None)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
