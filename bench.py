@@ -227,6 +227,10 @@ def ess(w):
     return float(w.sum() ** 2 / (w ** 2).sum()) if len(w) else 0.0
 
 
+# learned proposals: flow base broadened by 1.25, training weights w^0.8
+LEARNED_TAU, LEARNED_POWER = 1.25, 0.8
+
+
 def bench_learned_stream(abc, torch, prior_stream=None):
     """Sixteen regions (the streamed leg's), one flow proposal per region:
     16 rounds, each one batched launch of 2^20 simulations per region (2^24
@@ -234,7 +238,8 @@ def bench_learned_stream(abc, torch, prior_stream=None):
     final eps over the first 4 rounds, then stays there while the samples
     accepted at the final eps pool in device buffers with their importance
     weights; the 16 flows (3 x 256, BF16) train together after every round,
-    a region falling back to the prior whenever its ESS drops below 10 %."""
+    a region falling back to the prior whenever its flow round gave fewer
+    effective samples per simulation than its defensive prior draws' acceptance."""
     with open(os.path.join(ROOT, "tests", "golden", "workloads.json")) as f:
         wl = json.load(f)
     names = sorted(k for k in wl if k.startswith("stream16_"))
@@ -246,7 +251,8 @@ def bench_learned_stream(abc, torch, prior_stream=None):
     info, res = abc.abc_smc_run_regions(regs, rounds=rounds, shrink_rounds=shrink, sims_per_round=n, eps_factor=0.7,
                                         flow_blocks=3, flow_hidden=256, train_steps=500, train_steps_warm=100,
                                         train_batch=4096, train_lr=1e-3, seed=wl[names[0]]["seed"] + 29,
-                                        capacity=1 << 20, mode="fast")
+                                        capacity=1 << 20, mode="fast", proposal_scale=LEARNED_TAU,
+                                        train_weight_power=LEARNED_POWER)
     wall = time.perf_counter() - t0
     pooled = sum(r[3] for r in res)
     eff = sum(ess(r[1].cpu().numpy()) for r in res)
@@ -274,10 +280,11 @@ def bench_learned(abc, torch, w, prior_value, peaks, reps=5):
     """Sequential ABC with the learned flow proposal on the P = 6e7, T = 100
     region: 5 rounds of 2^22 simulations, eps shrinking by 0.7 per round to the
     headline eps, flow of 3 MADE blocks x 256 hidden units (BF16 weights, FP32
-    accumulation). Compared with plain prior ABC at the same (final) eps. The
-    flow's training is stochastic and a round whose ESS drops below 10 % falls
-    back to the prior, so `reps` independent runs (own seeds) are made and the
-    median is the reported figure, with every run listed."""
+    accumulation), proposals from the flow broadened by LEARNED_TAU. Compared
+    with plain prior ABC at the same (final) eps. The flow's training is
+    stochastic (and a flow doing worse than the prior falls back to it), so
+    `reps` independent runs (own seeds) are made and the median is the
+    reported figure, with every run listed."""
     rounds, n, factor = 5, 1 << 22, 0.7
     eps0 = w["eps"] / factor ** (rounds - 1)
     runs = []
@@ -285,7 +292,8 @@ def bench_learned(abc, torch, w, prior_value, peaks, reps=5):
         info, th, wt, dist = abc.abc_smc_run(w["observed"], w["P"], eps0, rounds=rounds, sims_per_round=n,
                                              eps_factor=factor, flow_blocks=3, flow_hidden=256, train_steps=500,
                                              train_batch=4096, train_lr=1e-3, seed=w["seed"] + 17 + 1000 * rep,
-                                             capacity=n, mode="fast")
+                                             capacity=n, mode="fast", proposal_scale=LEARNED_TAU,
+                                             train_weight_power=LEARNED_POWER)
         last = info[-1]
         ms = last["ms_propose"] + last["ms_simulate"]
         runs.append({"seed": w["seed"] + 17 + 1000 * rep,
@@ -312,16 +320,26 @@ def bench_learned(abc, torch, w, prior_value, peaks, reps=5):
            "runs": runs}
     if flow_runs:
         ms_prop = float(np.median([r["ms_propose"] for r in flow_runs]))
-        # per proposal: 3 blocks x 7 inverse passes (column 0 of a block depends on
-        # the biases alone) x the two dense products, 2 (8 H + 16 H) FLOP
-        flops = 3 * 7 * (16 * 256 + 32 * 256) * int(0.9 * n)
+        # algorithmic work per proposal: every hidden unit once per block (the
+        # sampler adds each unit's contribution when its inputs are final), the
+        # masked MADE's nonzero multiply-adds: unit l of degree d = l mod 7 + 1
+        # reads d inputs and feeds 8 - d means and 8 - d log-scales
+        H, blocks = 256, 3
+        macs = sum(16 - (l % 7 + 1) for l in range(H))
+        n_flow = int(0.9 * n)
+        flops = 2 * macs * blocks * n_flow
+        dense = 3 * 7 * (16 * H + 32 * H) * n_flow     # 7 full dense passes per block
         peak = (peaks or {}).get("bf16_tflops", 1900.0)
         achieved = flops / (ms_prop * 1e-3) / 1e12
         out["sampler_roofline"] = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                                    "frac": achieved / peak, "traffic": None,
-                                   "basis": "%d FLOP per flow proposal (3 blocks x 7 passes x (16 H + 32 H), H = 256, "
-                                            "dense), %d flow proposals per round (the other 10 %% are prior draws), "
-                                            "peak = measured cuBLAS bf16 burst" % (flops // int(0.9 * n), int(0.9 * n))}
+                                   "dense_equivalent_tflops": dense / (ms_prop * 1e-3) / 1e12,
+                                   "basis": "%d FLOP per flow proposal (3 blocks x the masked MADE's %d nonzero "
+                                            "multiply-adds, H = 256), %d flow proposals per round (the other 10 %% "
+                                            "are prior draws), time = the round's proposal stage; dense_equivalent "
+                                            "counts 7 full dense passes per block (%d FLOP per proposal); peak = "
+                                            "measured cuBLAS bf16 burst" % (flops // n_flow, macs, n_flow,
+                                                                             dense // n_flow)}
     return out
 
 

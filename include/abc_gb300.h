@@ -411,10 +411,14 @@ abc_status abc_maf_destroy(abc_maf maf);
  * eps_r = eps0 * eps_factor^r. Round 0 draws from the prior. After each round
  * the flow is trained (weighted maximum likelihood) on that round's accepted
  * samples with importance weights w = prior(theta) / q(theta) (w = 1 for
- * prior draws), and the next round draws from the flow, unless the round's
- * effective sample size (sum w)^2 / sum w^2 fell below ess_min times its
- * accept count (or it accepted fewer than 64), in which case the next round
- * falls back to the prior. Training holds out val_fraction of the round's
+ * prior draws), and the next round draws from the flow unless the prior
+ * would do better, in which case it falls back to the prior: a flow round
+ * with defensive draws falls back when its effective samples per simulation,
+ * ESS / sims_per_round with ESS = (sum w)^2 / sum w^2, fall below the prior's
+ * acceptance rate measured on those defensive draws (n_defensive_accepted /
+ * n_defensive); a prior round, or a flow round without defensive draws, when
+ * its ESS fraction ESS / n_accepted is below ess_min; any round with fewer
+ * than 64 accepted samples. Training holds out val_fraction of the round's
  * accepts and stops early (abc_maf_train_flows). A flow round draws a fraction `defensive` of its
  * proposals from the prior and weights every proposal by the mixture density
  * q_mix = (1 - defensive) q + defensive * prior (defensive importance sampling,
@@ -442,6 +446,9 @@ typedef struct {
     double train_weight_power;/* training weights are (prior / q)^power, in (0, 1] (1: the importance weights;
                                  below 1 the flow fits a broader density between proposal and target) */
     int32_t fresh_init;       /* 1: re-initialise the flow (random, fresh seed) before each training; 0: continue */
+    double proposal_scale;    /* base scale tau of the flow proposals (abc_maf_set_proposal_scale), in [0.5, 4]:
+                                 1 samples the trained flow; above 1 a broader proposal with heavier coverage
+                                 of the tails, weighted by its own density */
 } abc_smc_config;
 
 typedef struct {
@@ -453,6 +460,8 @@ typedef struct {
     double ess_fraction;      /* ESS / n_accepted of this round's weights */
     float train_loss;         /* flow loss after training on this round (0 if not trained) */
     float ms_propose, ms_simulate, ms_train;
+    uint64_t n_defensive;     /* a flow round's proposals drawn from the prior (0 in a prior round) */
+    uint64_t n_defensive_accepted; /* how many of them were accepted */
 } abc_smc_round;
 
 /* Run cfg->rounds rounds on one region (observed HOST [3][T+1], population
@@ -473,9 +482,8 @@ abc_status abc_smc_run(const abc_prior_box* prior, const int32_t* observed, int3
  * afterwards. Each region has its own flow (one set, abc_maf_create_multi);
  * after every round the flows of all regions whose round was good enough are
  * trained together (abc_maf_train_flows) on that round's weighted accepts, and
- * a region whose effective sample size fell below ess_min of its accepts (or
- * that accepted fewer than 64) falls back to the prior for its next round, as
- * in abc_smc_run (defensive mixture included). Every sample accepted at the
+ * a region falls back to the prior for its next round by the rule of
+ * abc_smc_run (defensive mixture included). Every sample accepted at the
  * region's final eps (all rounds from shrink_rounds - 1 on) is pooled in the
  * region's output buffers. Its weight is its round's self-normalised
  * importance weight (prior / q_mix) times the round's effective sample size,

@@ -53,14 +53,16 @@ class AbcSmcConfig(ctypes.Structure):
                 ("flow_hidden", ctypes.c_int32), ("train_steps", ctypes.c_int32), ("train_batch", ctypes.c_int32),
                 ("train_lr", ctypes.c_float), ("seed", ctypes.c_uint64), ("capacity", ctypes.c_uint64),
                 ("mode", ctypes.c_int), ("defensive", ctypes.c_double), ("val_fraction", ctypes.c_double),
-                ("train_weight_power", ctypes.c_double), ("fresh_init", ctypes.c_int32)]
+                ("train_weight_power", ctypes.c_double), ("fresh_init", ctypes.c_int32),
+                ("proposal_scale", ctypes.c_double)]
 
 
 class AbcSmcRound(ctypes.Structure):
     _fields_ = [("eps", ctypes.c_double), ("proposal", ctypes.c_int32), ("n_sims", ctypes.c_uint64),
                 ("n_accepted", ctypes.c_uint64), ("simulated_days", ctypes.c_uint64),
                 ("ess_fraction", ctypes.c_double), ("train_loss", ctypes.c_float), ("ms_propose", ctypes.c_float),
-                ("ms_simulate", ctypes.c_float), ("ms_train", ctypes.c_float)]
+                ("ms_simulate", ctypes.c_float), ("ms_train", ctypes.c_float), ("n_defensive", ctypes.c_uint64),
+                ("n_defensive_accepted", ctypes.c_uint64)]
 
 
 class AbcSmcRegion(ctypes.Structure):
@@ -745,10 +747,16 @@ def abc_maf_train_flows(flow, thetas, weights=None, **kw):
 
 def abc_smc_run(observed, N_pop, eps0, rounds=5, sims_per_round=1 << 22, eps_factor=0.7, ess_min=0.1,
                 flow_blocks=3, flow_hidden=256, train_steps=500, train_batch=1024, train_lr=1e-3, seed=0,
-                capacity=None, mode="fast", defensive=0.1, val_fraction=0.1, train_weight_power=1.0, fresh_init=False,
-                lo=PAPER_LO, hi=PAPER_HI, cuda_stream=None):
+                capacity=None, mode="fast", defensive=0.1, val_fraction=0.1, train_weight_power=0.8, fresh_init=False,
+                proposal_scale=1.25, lo=PAPER_LO, hi=PAPER_HI, cuda_stream=None):
     """Sequential ABC with the learned flow proposal. Returns (rounds: list of
-    dicts, theta [m, 8], weights [m] (f64, sum 1), dist [m]) of the last round."""
+    dicts, theta [m, 8], weights [m] (f64, sum 1), dist [m]) of the last round.
+    The defaults proposal_scale=1.25 (proposals from the flow with its base
+    broadened by 1.25) and train_weight_power=0.8 (training weights w^0.8)
+    trade some acceptance for proposals that cover the posterior's tails: on
+    the P = 6e7, T = 100 workload they gave the highest median and worst-case
+    effective samples per second over six seeds among the settings tried
+    (scale 1 to 1.7, power 0.7 to 1)."""
     L = load()
     obs, obs_p = _host_i32(observed)
     T = obs.shape[1] - 1
@@ -757,7 +765,7 @@ def abc_smc_run(observed, N_pop, eps0, rounds=5, sims_per_round=1 << 22, eps_fac
     cfg = AbcSmcConfig(int(rounds), int(sims_per_round), float(eps0), float(eps_factor), float(ess_min),
                        int(flow_blocks), int(flow_hidden), int(train_steps), int(train_batch), float(train_lr),
                        int(seed), int(capacity), _mode(mode), float(defensive), float(val_fraction),
-                       float(train_weight_power), int(bool(fresh_init)))
+                       float(train_weight_power), int(bool(fresh_init)), float(proposal_scale))
     rr = (AbcSmcRound * int(rounds))()
     dev = torch.device("cuda", torch.cuda.current_device())
     theta = torch.empty((capacity, 8), dtype=torch.float32, device=dev)
@@ -778,7 +786,7 @@ def abc_smc_run(observed, N_pop, eps0, rounds=5, sims_per_round=1 << 22, eps_fac
 def abc_smc_run_regions(regions, rounds=16, shrink_rounds=4, sims_per_round=1 << 20, eps_factor=0.7, ess_min=0.1,
                         flow_blocks=3, flow_hidden=256, train_steps=500, train_steps_warm=100, train_batch=1024,
                         train_lr=1e-3, seed=0, capacity=None, mode="fast", defensive=0.1, val_fraction=0.1,
-                        train_weight_power=1.0, lo=PAPER_LO, hi=PAPER_HI, cuda_stream=None):
+                        train_weight_power=0.8, proposal_scale=1.25, lo=PAPER_LO, hi=PAPER_HI, cuda_stream=None):
     """Sequential ABC with one flow proposal per region, all regions in one
     batched launch per round. regions: list of dicts with observed (host int32
     [3, T+1]), N_pop, eps (final) and pool (samples kept at the final eps).
@@ -805,7 +813,7 @@ def abc_smc_run_regions(regions, rounds=16, shrink_rounds=4, sims_per_round=1 <<
     base = AbcSmcConfig(int(rounds), int(sims_per_round), 0.0, float(eps_factor), float(ess_min), int(flow_blocks),
                         int(flow_hidden), int(train_steps), int(train_batch), float(train_lr), int(seed),
                         int(capacity), _mode(mode), float(defensive), float(val_fraction),
-                        float(train_weight_power), 0)
+                        float(train_weight_power), 0, float(proposal_scale))
     cfg = AbcSmcStreamConfig(base, int(shrink_rounds), int(train_steps_warm))
     rr = (AbcSmcRound * (int(rounds) * R))()
     s = cuda_stream if cuda_stream is not None else torch.cuda.Stream()

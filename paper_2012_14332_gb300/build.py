@@ -16,6 +16,12 @@ NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", 
               "-Xcompiler", "-fPIC", "-Xcompiler", "-O2", "-shared"]
 
 
+# The flow kernels are accurate to a tolerance (BF16 products), not bit for
+# bit, and include no exact-mode model arithmetic: FMA contraction is allowed
+# there.
+FMAD_SOURCES = {"abc_maf.cu"}
+
+
 def nvcc():
     for cand in (os.environ.get("NVCC"), "/usr/local/cuda/bin/nvcc", "nvcc"):
         if cand and (os.path.sep not in cand or os.path.exists(cand)):
@@ -41,7 +47,10 @@ def build(force=False, verbose=False):
     procs = []
     for f in SOURCES:
         obj = os.path.join(objdir, f.replace(".cu", ".o"))
-        cmd = [nvcc()] + [x for x in NVCC_FLAGS if x != "-shared"] + (["-Xptxas", "-v"] if verbose else []) + \
+        flags = [x for x in NVCC_FLAGS if x != "-shared"]
+        if f in FMAD_SOURCES:
+            flags = ["-fmad=true" if x == "-fmad=false" else x for x in flags]
+        cmd = [nvcc()] + flags + (["-Xptxas", "-v"] if verbose else []) + \
             ["-c", "-o", obj, os.path.join(CSRC, f)]
         procs.append((f, obj, subprocess.Popen(cmd, cwd=CSRC)))
     objs = []

@@ -68,9 +68,43 @@ __host__ __device__ inline int grad_block(int H) { return 29 * H + 80; }
 //   b2  [16]             FP32
 //   w1t [8][H/2+4]       B operand of g_a1 W1     (n = j, k = l)
 //   w2t [H][12]          B operand of g_out W2    (n = l, k = o)
+// then the sampler's copy of the forward operands (sw1, sw2, sb1 in the w1,
+// w2, b1 layouts, and sb2 = b2), whose 16-unit chunks hold the hidden units
+// grouped by degree: the chunks of degree d = 1..7 hold units d - 1, d + 6,
+// d + 13, ... in order, the last chunk of each degree padded with zero units.
 struct Layout {
-    int w1, w2, b1, b2, w1t, w2t, fwd_words, words;
+    int w1, w2, b1, b2, w1t, w2t, fwd_words, grad_words;
+    int sw1, sw2, sb1, sb2, samp_words, words;
 };
+
+// MADE masks (Germain et al.): hidden degree (l mod 7) + 1; input j and output
+// j (mu_j and alpha_j, o = j and o = 8 + j) have degree j + 1.
+__host__ __device__ inline bool mask1(int l, int j) { return (l % 7) + 1 >= j + 1; }
+__host__ __device__ inline bool mask2(int o, int l) { return (o % 8) + 1 > (l % 7) + 1; }
+
+// hidden units of degree d (1..7) among H, and the 16-unit chunks they fill
+__host__ __device__ inline int degree_units(int H, int d) { return (H - d) / 7 + 1; }
+__host__ __device__ inline int degree_chunks(int H, int d) { return (degree_units(H, d) + 15) / 16; }
+__host__ __device__ inline int sampler_chunks(int H)
+{
+    int c = 0;
+    for (int d = 1; d <= 7; ++d) c += degree_chunks(H, d);
+    return c;
+}
+// hidden unit at position u (0..15) of sampler chunk s, or -1 for padding
+__host__ __device__ inline int sampler_unit(int H, int s, int u)
+{
+    for (int d = 1; d <= 7; ++d) {
+        const int c = degree_chunks(H, d);
+        if (s < c) {
+            const int i = 16 * s + u;
+            return i < degree_units(H, d) ? d - 1 + 7 * i : -1;
+        }
+        s -= c;
+    }
+    return -1;
+}
+
 __host__ __device__ inline Layout layout(int H)
 {
     Layout L;
@@ -82,14 +116,16 @@ __host__ __device__ inline Layout layout(int H)
     L.fwd_words = o;
     L.w1t = o; o += 8 * (H / 2 + 4);
     L.w2t = o; o += H * 12;
+    L.grad_words = o;
+    const int C = sampler_chunks(H);
+    L.sw1 = o; o += C * 64;
+    L.sw2 = o; o += C * 128;
+    L.sb1 = o; o += C * 16;
+    L.sb2 = o; o += 16;
+    L.samp_words = o - L.sw1;
     L.words = o;
     return L;
 }
-
-// MADE masks (Germain et al.): hidden degree (l mod 7) + 1; input j and output
-// j (mu_j and alpha_j, o = j and o = 8 + j) have degree j + 1.
-__host__ __device__ inline bool mask1(int l, int j) { return (l % 7) + 1 >= j + 1; }
-__host__ __device__ inline bool mask2(int o, int l) { return (o % 8) + 1 > (l % 7) + 1; }
 
 struct Box {
     float lo[8], w[8], logw[8];
@@ -163,7 +199,14 @@ __device__ __forceinline__ void reverse_cols(float (&v)[4])
     v[0] = n0; v[1] = n1; v[2] = n2; v[3] = n3;
 }
 
-__device__ __forceinline__ float soft_alpha(float ar) { return kAlphaMax * tanhf(ar / kAlphaMax); }
+// alpha = A tanh(ar / A) from one exponential: tanh|y| = (1 - e) / (1 + e) with
+// e = exp(-2 |y|) in (0, 1], so nothing overflows; the fast exponential and
+// division leave an absolute error of a few 1e-7 in alpha
+__device__ __forceinline__ float soft_alpha(float ar)
+{
+    const float e = __expf((-2.f / kAlphaMax) * fabsf(ar));
+    return copysignf(kAlphaMax * __fdividef(1.f - e, 1.f + e), ar);
+}
 
 // Density and sampling CTAs: 8 warps share one staged copy of the forward
 // operands (about 41 KB at 3 x 256), at most 64 registers so that 4 CTAs
@@ -254,19 +297,17 @@ __device__ __forceinline__ void to_theta(const Box& b, int j, float y, float& th
     jac = b.logw[j] + ls + l1s;
 }
 
-// the forward words of each of K blocks, packed block after block (stride fwd_words)
-__device__ __forceinline__ void stage_forward(uint32_t* sm, const uint32_t* pub, int K, const Layout& L)
+// words [off, off + n) of each of K published blocks, packed block after
+// block in shared memory (stride n). Every offset and length is a multiple of
+// 4 words (H is a multiple of 16), so the copy moves 16-byte vectors.
+__device__ __forceinline__ void stage_blocks(uint32_t* sm, const uint32_t* pub, int K, int off, int n,
+                                             const Layout& L)
 {
-    for (int b = 0; b < K; ++b)
-        for (int i = threadIdx.x; i < L.fwd_words; i += blockDim.x) sm[b * L.fwd_words + i] = pub[b * L.words + i];
-}
-
-__device__ __forceinline__ void stage_weights(uint32_t* sm, const uint32_t* pub, int words)
-{
-    const uint4* src = reinterpret_cast<const uint4*>(pub);
-    uint4* dst = reinterpret_cast<uint4*>(sm);
-    for (int i = threadIdx.x; i < words / 4; i += blockDim.x) dst[i] = src[i];
-    for (int i = (words / 4) * 4 + threadIdx.x; i < words; i += blockDim.x) sm[i] = pub[i];
+    const int n4 = n / 4;
+    for (int i = threadIdx.x; i < K * n4; i += blockDim.x) {
+        const int b = i / n4, r = i - b * n4;
+        reinterpret_cast<uint4*>(sm)[i] = reinterpret_cast<const uint4*>(pub + (size_t)b * L.words + off)[r];
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -314,7 +355,7 @@ __global__ void publish_kernel(const float* __restrict__ master, uint32_t* __res
                                                          mask1(l0 + 1, j) ? W1[(l0 + 1) * 8 + j] : 0.f);
                 out = *reinterpret_cast<uint32_t*>(&v);
             }
-        } else {
+        } else if (w < L.grad_words) {
             const int r = w - L.w2t, l = r / 12, c = r % 12;
             if (c < 8) {
                 const int o0 = 2 * c;
@@ -322,6 +363,26 @@ __global__ void publish_kernel(const float* __restrict__ master, uint32_t* __res
                                                          mask2(o0 + 1, l) ? W2[(o0 + 1) * H + l] : 0.f);
                 out = *reinterpret_cast<uint32_t*>(&v);
             }
+        } else if (w < L.sw2) {
+            // as w1, over the degree-grouped chunks: unit at position g + 8 h of chunk s
+            const int r = w - L.sw1, h = r & 1, t = (r >> 1) & 3, g = (r >> 3) & 7, sc = r >> 6;
+            const int l = sampler_unit(H, sc, g + 8 * h), j0 = 2 * t;
+            __nv_bfloat162 v = __floats2bfloat162_rn(l >= 0 && mask1(l, j0) ? W1[l * 8 + j0] : 0.f,
+                                                     l >= 0 && mask1(l, j0 + 1) ? W1[l * 8 + j0 + 1] : 0.f);
+            out = *reinterpret_cast<uint32_t*>(&v);
+        } else if (w < L.sb1) {
+            const int r = w - L.sw2, q = r & 3, t = (r >> 2) & 3, g = (r >> 4) & 7, sc = r >> 7;
+            const int o = g + 8 * (q >> 1), u0 = 8 * (q & 1) + 2 * t;
+            const int l0 = sampler_unit(H, sc, u0), l1 = sampler_unit(H, sc, u0 + 1);
+            __nv_bfloat162 v = __floats2bfloat162_rn(l0 >= 0 && mask2(o, l0) ? W2[o * H + l0] : 0.f,
+                                                     l1 >= 0 && mask2(o, l1) ? W2[o * H + l1] : 0.f);
+            out = *reinterpret_cast<uint32_t*>(&v);
+        } else if (w < L.sb2) {
+            const int r = w - L.sb1, q = r & 3, t = (r >> 2) & 3, sc = r >> 4;
+            const int l = sampler_unit(H, sc, 8 * (q >> 1) + 2 * t + (q & 1));
+            out = __float_as_uint(l >= 0 ? b1[l] : 0.f);
+        } else {
+            out = __float_as_uint(b2[w - L.sb2]);
         }
         pub[idx] = out;
     }
@@ -339,7 +400,7 @@ __global__ void __launch_bounds__(kFwdThreads, kFwdMinBlocks) logq_kernel(const 
 {
     extern __shared__ __align__(16) uint32_t sm[];
     const Layout L = layout(H);
-    stage_forward(sm, pub, K, L);
+    stage_blocks(sm, pub, K, 0, L.fwd_words, L);
     __syncthreads();
     const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
     const uint64_t tiles = (n + 15) / 16;
@@ -363,7 +424,7 @@ __global__ void __launch_bounds__(kFwdThreads, kFwdMinBlocks) logq_kernel(const 
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
                 const float al = soft_alpha(ar[e]);
-                x[e] = (x[e] - mu[e]) * expf(-al);
+                x[e] = (x[e] - mu[e]) * __expf(-al);
                 ld[e] -= al;
             }
             reverse_cols(x);
@@ -382,6 +443,26 @@ __global__ void __launch_bounds__(kFwdThreads, kFwdMinBlocks) logq_kernel(const 
 // ---------------------------------------------------------------------------
 // sampling: base draws -> sequential inverse -> theta, log q(theta)
 // ---------------------------------------------------------------------------
+// One pass of the sequential inverse: the chunks of the hidden units of one
+// degree, from chunk s0 on. Their inputs (columns below the degree) are all
+// final, so each unit's activation is computed once, and its layer-2
+// contribution to every output is added to the running accumulators (even
+// chunks into o, odd into p). Returns the next degree's first chunk.
+__device__ __forceinline__ int inverse_pass(const BlockView& v, int H, int d, int s0, int g, int t,
+                                            const float (&xin)[4], float (&o0)[4], float (&o1)[4],
+                                            float (&p0)[4], float (&p1)[4])
+{
+    const uint32_t a0 = pack2(xin[0], xin[1]), a1 = pack2(xin[2], xin[3]);
+    const int s1 = s0 + degree_chunks(H, d);
+    int s = s0;
+    for (; s + 1 < s1; s += 2) {
+        made_chunk(v, s, g, t, a0, a1, o0, o1);
+        made_chunk(v, s + 1, g, t, a0, a1, p0, p1);
+    }
+    if (s < s1) made_chunk(v, s, g, t, a0, a1, o0, o1);
+    return s1;
+}
+
 template <int K>
 __global__ void __launch_bounds__(kFwdThreads, kFwdMinBlocks) sample_kernel(const uint32_t* __restrict__ pub, int H, Box box,
                                                      const float* __restrict__ u_in, const __grid_constant__ ModelParams p,
@@ -391,7 +472,7 @@ __global__ void __launch_bounds__(kFwdThreads, kFwdMinBlocks) sample_kernel(cons
 {
     extern __shared__ __align__(16) uint32_t sm[];
     const Layout L = layout(H);
-    stage_forward(sm, pub, K, L);
+    stage_blocks(sm, pub, K, L.sw1, L.samp_words, L);
     __syncthreads();
     const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
     const uint64_t tiles = (n + 15) / 16;
@@ -423,38 +504,50 @@ __global__ void __launch_bounds__(kFwdThreads, kFwdMinBlocks) sample_kernel(cons
         // blocks and passes are runtime loops (a fully unrolled 3 x 8 inverse
         // overflows the instruction cache); passes go in pairs so every
         // register index stays static: pass 2p+1 fills column 2p+1 (lane t = p,
-        // element 1), pass 2p+2 fills column 2p+2 (lane t = p+1, element 0)
+        // element 1), pass 2p+2 fills column 2p+2 (lane t = p+1, element 0).
+        // Column j depends on the hidden units of degree <= j alone, which
+        // passes 1..j have added to the accumulators by then.
 #pragma unroll 1
         for (int bb = K - 1; bb >= 0; --bb) {
-            const BlockView v = view(sm + bb * L.fwd_words, L);
+            const uint32_t* base = sm + bb * L.samp_words;
+            BlockView v;
+            v.w1 = base;
+            v.w2 = base + (L.sw2 - L.sw1);
+            v.b1 = reinterpret_cast<const float*>(base + (L.sb1 - L.sw1));
+            v.b2 = reinterpret_cast<const float*>(base + (L.sb2 - L.sw1));
+            v.w1t = v.w2t = nullptr;
             float z[4] = {x[0], x[1], x[2], x[3]};
             reverse_cols(z);
             float xin[4] = {0.f, 0.f, 0.f, 0.f};
+            const float2 bm = *reinterpret_cast<const float2*>(v.b2 + 2 * t);
+            const float2 bs = *reinterpret_cast<const float2*>(v.b2 + 8 + 2 * t);
+            float o0[4] = {bm.x, bm.y, bm.x, bm.y}, o1[4] = {bs.x, bs.y, bs.x, bs.y};
+            float p0[4] = {0.f, 0.f, 0.f, 0.f}, p1[4] = {0.f, 0.f, 0.f, 0.f};
             if (t == 0) {
                 // column 0 has degree 1: every weight into mu_0, alpha_0 is masked
-                const float al0 = soft_alpha(v.b2[8]);
-                xin[0] = z[0] * expf(al0) + v.b2[0];
-                xin[2] = z[2] * expf(al0) + v.b2[0];
+                const float al0 = soft_alpha(bs.x);
+                xin[0] = z[0] * __expf(al0) + bm.x;
+                xin[2] = z[2] * __expf(al0) + bm.x;
                 lq[0] -= al0;
                 lq[2] -= al0;
             }
+            int s0 = 0;
 #pragma unroll 1
             for (int pj = 0; pj < kD / 2; ++pj) {
-                float mu[4], ar[4];
-                made_fwd(v, H, xin, mu, ar);
+                s0 = inverse_pass(v, H, 2 * pj + 1, s0, g, t, xin, o0, o1, p0, p1);
                 if (t == pj) {
-                    const float al0 = soft_alpha(ar[1]), al1 = soft_alpha(ar[3]);
-                    xin[1] = z[1] * expf(al0) + mu[1];
-                    xin[3] = z[3] * expf(al1) + mu[3];
+                    const float al0 = soft_alpha(o1[1] + p1[1]), al1 = soft_alpha(o1[3] + p1[3]);
+                    xin[1] = z[1] * __expf(al0) + (o0[1] + p0[1]);
+                    xin[3] = z[3] * __expf(al1) + (o0[3] + p0[3]);
                     lq[1] -= al0;
                     lq[3] -= al1;
                 }
                 if (pj < kD / 2 - 1) {
-                    made_fwd(v, H, xin, mu, ar);
+                    s0 = inverse_pass(v, H, 2 * pj + 2, s0, g, t, xin, o0, o1, p0, p1);
                     if (t == pj + 1) {
-                        const float al0 = soft_alpha(ar[0]), al1 = soft_alpha(ar[2]);
-                        xin[0] = z[0] * expf(al0) + mu[0];
-                        xin[2] = z[2] * expf(al1) + mu[2];
+                        const float al0 = soft_alpha(o1[0] + p1[0]), al1 = soft_alpha(o1[2] + p1[2]);
+                        xin[0] = z[0] * __expf(al0) + (o0[0] + p0[0]);
+                        xin[2] = z[2] * __expf(al1) + (o0[2] + p0[2]);
                         lq[0] -= al0;
                         lq[2] -= al1;
                     }
@@ -546,9 +639,9 @@ __global__ void __launch_bounds__(W * 32) grad_kernel(const uint32_t* __restrict
     grad += (size_t)f * K * mb;
     sums += 2 * f;
     uint32_t* wsm = sm;
-    float* gsm = reinterpret_cast<float*>(sm + K * L.words);
+    float* gsm = reinterpret_cast<float*>(sm + K * L.grad_words);
     WarpStage* stages = reinterpret_cast<WarpStage*>(gsm + K * gb);
-    stage_weights(wsm, pub, K * L.words);
+    stage_blocks(wsm, pub, K, 0, L.grad_words, L);
     for (int i = threadIdx.x; i < K * gb; i += blockDim.x) gsm[i] = 0.f;
     __shared__ float ssum[2];
     if (threadIdx.x < 2) ssum[threadIdx.x] = 0.f;
@@ -576,13 +669,13 @@ __global__ void __launch_bounds__(W * 32) grad_kernel(const uint32_t* __restrict
 #pragma unroll
         for (int b = 0; b < K; ++b) {
             float mu[4], ar[4];
-            made_fwd(view(wsm + b * L.words, L), H, x, mu, ar);
+            made_fwd(view(wsm + b * L.grad_words, L), H, x, mu, ar);
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
                 xs[b][e] = x[e];
                 ms[b][e] = mu[e];
                 as[b][e] = soft_alpha(ar[e]);
-                zs[b][e] = (x[e] - mu[e]) * expf(-as[b][e]);
+                zs[b][e] = (x[e] - mu[e]) * __expf(-as[b][e]);
                 x[e] = zs[b][e];
             }
             ld0 += as[b][0] + as[b][1];
@@ -609,7 +702,7 @@ __global__ void __launch_bounds__(W * 32) grad_kernel(const uint32_t* __restrict
         const float wr[4] = {w0, w0, w1, w1};
 #pragma unroll
         for (int b = K - 1; b >= 0; --b) {
-            const BlockView v = view(wsm + b * L.words, L);
+            const BlockView v = view(wsm + b * L.grad_words, L);
             float* GW1 = gsm + b * gb;                // [H][kGW1Stride]
             float* GB1 = GW1 + kGW1Stride * H;
             float* GW2 = GB1 + H;                     // [16][H + 4]
@@ -619,7 +712,7 @@ __global__ void __launch_bounds__(W * 32) grad_kernel(const uint32_t* __restrict
             float gmu[4], gar[4], gxd[4];
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
-                const float ex = expf(-as[b][e]);
+                const float ex = __expf(-as[b][e]);
                 gxd[e] = gx[e] * ex;
                 gmu[e] = -gx[e] * ex;
                 const float ga = -gx[e] * zs[b][e] + wr[e];
@@ -861,10 +954,11 @@ namespace {
     } while (0)
 
 size_t fwd_smem(const abc_maf_s* f) { return sizeof(uint32_t) * (size_t)f->K * maf::layout(f->H).fwd_words; }
+size_t samp_smem(const abc_maf_s* f) { return sizeof(uint32_t) * (size_t)f->K * maf::layout(f->H).samp_words; }
 
 size_t grad_smem(const abc_maf_s* f, int warps)
 {
-    return sizeof(uint32_t) * (size_t)f->K * maf::layout(f->H).words +
+    return sizeof(uint32_t) * (size_t)f->K * maf::layout(f->H).grad_words +
            sizeof(float) * (size_t)f->K * maf::grad_block(f->H) + sizeof(maf::WarpStage) * warps;
 }
 
@@ -945,7 +1039,7 @@ template <int K>
 cudaError_t launch_sample(abc_maf f, int r, uint64_t n, const float* u, const ModelParams& p, uint32_t ctr3,
                           uint64_t first, float* theta, float* logq, cudaStream_t s)
 {
-    const size_t smem = fwd_smem(f);
+    const size_t smem = samp_smem(f);
     cudaError_t e = allow_smem(maf::sample_kernel<K>, smem);
     if (e != cudaSuccess) return e;
     const uint64_t tiles = (n + 15) / 16;

@@ -59,6 +59,7 @@ struct WeightScratch {
     unsigned int max_key;
     unsigned int pad;
     double sums[2];
+    unsigned long long n_tail;   // accepted samples with index >= tail_first (the defensive prior draws)
 };
 
 __device__ __forceinline__ unsigned int float_key(float f)
@@ -73,16 +74,22 @@ __device__ __forceinline__ float key_float(unsigned int k)
 }
 
 __global__ void logw_kernel(const float* __restrict__ logq, const uint64_t* __restrict__ idx, uint64_t first, uint64_t m,
-                            float log_prior, float* __restrict__ lw, WeightScratch* ws)
+                            uint64_t tail_first, float log_prior, float* __restrict__ lw, WeightScratch* ws)
 {
     const uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     float v = -INFINITY;
+    bool tail = false;
     if (j < m) {
         v = logq ? log_prior - logq[idx[j] - first] : 0.f;
         lw[j] = v;
+        tail = idx[j] >= tail_first;
     }
+    const unsigned int n_tail = __popc(__ballot_sync(0xFFFFFFFFu, tail));
     for (int off = 16; off > 0; off >>= 1) v = fmaxf(v, __shfl_xor_sync(0xFFFFFFFFu, v, off));
-    if ((threadIdx.x & 31) == 0 && v > -INFINITY) atomicMax(&ws->max_key, float_key(v));
+    if ((threadIdx.x & 31) == 0) {
+        if (v > -INFINITY) atomicMax(&ws->max_key, float_key(v));
+        if (n_tail) atomicAdd(&ws->n_tail, (unsigned long long)n_tail);
+    }
 }
 
 __global__ void weight_kernel(const float* __restrict__ lw, uint64_t m, WeightScratch* ws, float* __restrict__ w_train,
@@ -197,11 +204,11 @@ static abc_status shuffled_training_set(const float* theta, const W* w, uint64_t
 static abc_status round_weights(const float* logq, const uint64_t* idx, uint64_t first, uint64_t m, double log_prior,
                                 float* d_lw, float* w_train, double* w_exact, double* pool, uint64_t pool_k,
                                 WeightScratch* d_ws, cudaStream_t s, double* sum_v, double* sum_v2,
-                                double power = 1.0)
+                                double power, uint64_t tail_first, uint64_t* n_tail)
 {
     SMC_TRY(cudaMemsetAsync(d_ws, 0, sizeof(WeightScratch), s), "cudaMemsetAsync(weight scratch)");
     const unsigned blocks = (unsigned)((m + 255) / 256);
-    logw_kernel<<<blocks, 256, 0, s>>>(logq, idx, first, m, (float)log_prior, d_lw, d_ws);
+    logw_kernel<<<blocks, 256, 0, s>>>(logq, idx, first, m, tail_first, (float)log_prior, d_lw, d_ws);
     weight_kernel<<<blocks, 256, 0, s>>>(d_lw, m, d_ws, w_train, w_exact, pool, pool_k, power);
     SMC_TRY(cudaGetLastError(), "weight launch");
     WeightScratch h;
@@ -209,7 +216,22 @@ static abc_status round_weights(const float* logq, const uint64_t* idx, uint64_t
     SMC_TRY(cudaStreamSynchronize(s), "cudaStreamSynchronize");
     *sum_v = h.sums[0];
     *sum_v2 = h.sums[1];
+    *n_tail = h.n_tail;
     return ABC_OK;
+}
+
+// Whether the next round should draw from the flow. A flow round keeps the
+// flow when it gave at least as many effective samples per simulation,
+// ESS / N with ESS = (sum w)^2 / sum w^2, as rejection from the prior accepts
+// per simulation at the same eps, that rate measured on the round's own
+// defensive prior draws. A prior round, or a flow round without defensive
+// draws, keeps or switches to the flow when its ESS fraction reaches ess_min.
+// Fewer than 64 accepted samples always means the prior.
+static bool next_uses_flow(const abc_smc_round& R, double sw, double sw2, double ess_min)
+{
+    if (R.n_accepted < 64 || !(sw2 > 0.0)) return false;
+    if (R.proposal == 0 || R.n_defensive == 0) return R.ess_fraction >= ess_min;
+    return sw * sw / sw2 / (double)R.n_sims >= (double)R.n_defensive_accepted / (double)R.n_defensive;
 }
 
 extern "C" abc_status abc_smc_run(const abc_prior_box* prior, const int32_t* observed, int32_t T, int64_t N_pop,
@@ -222,7 +244,8 @@ extern "C" abc_status abc_smc_run(const abc_prior_box* prior, const int32_t* obs
     if (cfg->rounds < 1 || cfg->sims_per_round == 0 || !(cfg->eps0 >= 0.0) || !(cfg->eps_factor > 0.0) ||
         cfg->eps_factor > 1.0 || !(cfg->ess_min >= 0.0) || cfg->capacity == 0 || !(cfg->defensive >= 0.0) ||
         cfg->defensive >= 1.0 || !(cfg->val_fraction >= 0.0) || cfg->val_fraction > 0.5 ||
-        !(cfg->train_weight_power > 0.0) || cfg->train_weight_power > 1.0)
+        !(cfg->train_weight_power > 0.0) || cfg->train_weight_power > 1.0 || !(cfg->proposal_scale >= 0.5) ||
+        cfg->proposal_scale > 4.0)
         return plan_fail(ABC_ERR_INVALID_ARG, "bad sequential ABC configuration");
     // every accepted sample of a round is kept: the accept buffer is filled in
     // claim (index) order and a flow round's defensive prior draws are its
@@ -237,6 +260,7 @@ extern "C" abc_status abc_smc_run(const abc_prior_box* prior, const int32_t* obs
 
     Guard gd;
     SMC_ST(abc_maf_create(cfg->flow_blocks, cfg->flow_hidden, prior, &gd.flow));
+    SMC_ST(abc_maf_set_proposal_scale(gd.flow, (float)cfg->proposal_scale));
     SMC_ST(abc_maf_init_random(gd.flow, cfg->seed ^ 0x5EED5EEDull, 0.3f));
     float *d_prop = nullptr, *d_logq = nullptr, *d_acc_logq = nullptr, *d_w = nullptr;
     SMC_TRY(cudaMalloc(&d_prop, sizeof(float) * 8 * N), "cudaMalloc(proposals)");
@@ -273,6 +297,7 @@ extern "C" abc_status abc_smc_run(const abc_prior_box* prior, const int32_t* obs
             // (1 - defensive) N flow draws, the rest prior draws, all weighted by the mixture density
             const uint64_t n_prior = (uint64_t)std::floor(cfg->defensive * (double)N);
             const uint64_t n_flow = N - n_prior;
+            R.n_defensive = n_prior;
             // flow draws carry the sampler's log q (exact for the drawn point); the
             // prior draws get the flow's density evaluated at them
             if (n_flow) SMC_ST(abc_maf_sample(gd.flow, n_flow, nullptr, cfg->seed, 1, first, d_prop, d_logq, s));
@@ -319,9 +344,14 @@ extern "C" abc_status abc_smc_run(const abc_prior_box* prior, const int32_t* obs
         // importance weights prior / q_mix of the kept accepted samples
         double sw = 0.0, sw2 = 0.0;
         if (m > 0) {
+            // a flow round's defensive prior draws are its last n_defensive indices
+            const uint64_t tail_first = use_flow ? first + N - R.n_defensive : UINT64_MAX;
+            uint64_t n_tail = 0;
             SMC_ST(round_weights(use_flow ? d_logq : nullptr, acc_idx, first, m, log_prior, d_acc_logq, d_wround,
-                                 last ? weight_out : nullptr, nullptr, 0, d_ws, s, &sw, &sw2, cfg->train_weight_power));
+                                 last ? weight_out : nullptr, nullptr, 0, d_ws, s, &sw, &sw2, cfg->train_weight_power,
+                                 tail_first, &n_tail));
             R.ess_fraction = sw2 > 0.0 ? sw * sw / sw2 / (double)m : 0.0;
+            R.n_defensive_accepted = n_tail;
         }
         // the next round's proposal: train on this round's weighted accepts
         if (last) {
@@ -340,7 +370,7 @@ extern "C" abc_status abc_smc_run(const abc_prior_box* prior, const int32_t* obs
             }
             SMC_TRY(cudaEventRecord(gd.ev[3], s), "cudaEventRecord");
         } else {
-            const bool trainable = m >= 64 && R.ess_fraction >= cfg->ess_min;
+            const bool trainable = next_uses_flow(R, sw, sw2, cfg->ess_min);
             if (trainable) {
                 SMC_ST(shuffled_training_set(acc_theta, d_wround, m, m, cfg->seed + (uint64_t)r, d_train, d_w, s));
                 if (cfg->fresh_init)
@@ -399,8 +429,8 @@ extern "C" abc_status abc_smc_run_regions(const abc_prior_box* prior, abc_smc_re
     if (cfg->rounds < 1 || cfg->sims_per_round == 0 || !(cfg->eps_factor > 0.0) || cfg->eps_factor > 1.0 ||
         !(cfg->ess_min >= 0.0) || cfg->capacity == 0 || !(cfg->defensive >= 0.0) || cfg->defensive >= 1.0 ||
         !(cfg->val_fraction >= 0.0) || cfg->val_fraction > 0.5 || cfg->capacity < cfg->sims_per_round ||
-        !(cfg->train_weight_power > 0.0) || cfg->train_weight_power > 1.0 ||
-        scfg->shrink_rounds < 1 || scfg->shrink_rounds > cfg->rounds || scfg->train_steps_warm < 0 ||
+        !(cfg->train_weight_power > 0.0) || cfg->train_weight_power > 1.0 || !(cfg->proposal_scale >= 0.5) ||
+        cfg->proposal_scale > 4.0 || scfg->shrink_rounds < 1 || scfg->shrink_rounds > cfg->rounds || scfg->train_steps_warm < 0 ||
         cfg->train_steps < 0)
         return plan_fail(ABC_ERR_INVALID_ARG, "bad multi-region sequential ABC configuration");
     for (int32_t g = 0; g < R; ++g) {
@@ -418,6 +448,7 @@ extern "C" abc_status abc_smc_run_regions(const abc_prior_box* prior, abc_smc_re
 
     RegionsGuard gd;
     SMC_ST(abc_maf_create_multi(R, cfg->flow_blocks, cfg->flow_hidden, prior, &gd.flows));
+    SMC_ST(abc_maf_set_proposal_scale(gd.flows, (float)cfg->proposal_scale));
     SMC_ST(abc_maf_init_random(gd.flows, cfg->seed ^ 0x5EED5EEDull, 0.3f));
     float *d_prop = nullptr, *d_logq = nullptr, *d_acc_logq = nullptr, *d_w = nullptr, *d_train = nullptr;
     SMC_TRY(cudaMalloc(&d_prop, sizeof(float) * 8 * N * R), "cudaMalloc(proposals)");
@@ -476,6 +507,7 @@ extern "C" abc_status abc_smc_run_regions(const abc_prior_box* prior, abc_smc_re
             if (use_flow[g]) {
                 const uint64_t n_prior = (uint64_t)std::floor(cfg->defensive * (double)N);
                 const uint64_t n_flow = N - n_prior;
+                Rr[g].n_defensive = n_prior;
                 float* prop = d_prop + (size_t)g * 8 * N;
                 float* lq = d_logq + (size_t)g * N;
                 if (n_flow)
@@ -521,9 +553,12 @@ extern "C" abc_status abc_smc_run_regions(const abc_prior_box* prior, abc_smc_re
             const uint64_t k = pool ? std::min(m, G.capacity - G.n_out) : 0;
             double* pw = k ? G.weight_out + G.n_out : nullptr;
             double sw = 0.0, sw2 = 0.0;
+            uint64_t n_tail = 0;
             SMC_ST(round_weights(use_flow[g] ? d_logq + (size_t)g * N : nullptr, acc_idx, first, m, log_prior,
-                                 d_acc_logq, d_wround, nullptr, pw, k, d_ws, s, &sw, &sw2, cfg->train_weight_power));
+                                 d_acc_logq, d_wround, nullptr, pw, k, d_ws, s, &sw, &sw2, cfg->train_weight_power,
+                                 use_flow[g] ? first + N - Rr[g].n_defensive : UINT64_MAX, &n_tail));
             Rr[g].ess_fraction = sw2 > 0.0 ? sw * sw / sw2 / (double)m : 0.0;
+            Rr[g].n_defensive_accepted = n_tail;
             // samples accepted at the region's final eps join the pool; the
             // rounds' self-normalised estimates are combined with weights
             // proportional to their ESS, i.e. sample weight v_j sum v / sum v^2
@@ -540,10 +575,11 @@ extern "C" abc_status abc_smc_run_regions(const abc_prior_box* prior, abc_smc_re
                     G.n_out += k;
                 }
             }
-            // the next round uses the flow unless this round's ESS fell below
-            // ess_min; the flow trains on this round's weighted accepts, or,
-            // once at the final eps, on the whole pool (same target, more points)
-            const bool good = m >= 64 && Rr[g].ess_fraction >= cfg->ess_min;
+            // the next round uses the flow unless the prior does better
+            // (next_uses_flow); the flow trains on this round's weighted
+            // accepts, or, once at the final eps, on the whole pool (same
+            // target, more points)
+            const bool good = next_uses_flow(Rr[g], sw, sw2, cfg->ess_min);
             if (r + 1 < cfg->rounds) {
                 float* tt = d_train + (size_t)g * 8 * cap;
                 float* tw = d_w + (size_t)g * cap;

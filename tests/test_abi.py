@@ -44,6 +44,38 @@ def test_binding_names_match_header():
             assert hasattr(b, name), name
 
 
+def test_binding_structs_match_the_header_layout(tmp_path):
+    """Every ctypes mirror of a header struct has the C compiler's size and
+    field offsets (gcc on the header itself), so no field is dropped,
+    reordered or mistyped on either side of the boundary."""
+    import shutil
+    import subprocess
+    import paper_2012_14332_gb300.binding as b
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    pairs = {"abc_prior_box": b.AbcPriorBox, "abc_region": b.AbcRegion, "abc_launch_shape": b.AbcLaunchShape,
+             "abc_smc_config": b.AbcSmcConfig, "abc_smc_round": b.AbcSmcRound, "abc_smc_region": b.AbcSmcRegion,
+             "abc_smc_stream_config": b.AbcSmcStreamConfig, "abc_pmc_config": b.AbcPmcConfig,
+             "abc_pmc_round": b.AbcPmcRound}
+    src = open(HEADER).read()
+    lines, want = [], []
+    for cname, cls in pairs.items():
+        assert re.search(r"\}\s*%s\s*;" % cname, src), cname
+        lines.append('printf("%%zu\\n", sizeof(%s));' % cname)
+        want.append(ctypes.sizeof(cls))
+        for f in cls._fields_:
+            lines.append('printf("%%zu\\n", offsetof(%s, %s));' % (cname, f[0]))
+            want.append(getattr(cls, f[0]).offset)
+    prog = tmp_path / "layout.c"
+    prog.write_text('#include <stddef.h>\n#include <stdio.h>\n#include "abc_gb300.h"\nint main(void) {\n%s\nreturn 0;\n}\n'
+                    % "\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.check_call([cc, "-std=c11", "-I", os.path.dirname(HEADER), "-o", str(exe), str(prog)])
+    got = [int(x) for x in subprocess.check_output([str(exe)]).split()]
+    assert got == want
+
+
 def test_strerror_and_version(L):
     from paper_2012_14332_gb300 import binding as b
     for st in range(6):
@@ -181,13 +213,13 @@ def test_sequential_drivers_validate_before_any_cuda_call(L):
     op = obs.ctypes.data_as(ctypes.c_void_p)
     good = dict(rounds=3, sims_per_round=1024, eps0=10.0, eps_factor=0.7, ess_min=0.1, flow_blocks=3, flow_hidden=64,
                 train_steps=10, train_batch=256, train_lr=1e-3, seed=1, capacity=1024, mode=1, defensive=0.1,
-                val_fraction=0.1, train_weight_power=1.0, fresh_init=0)
+                val_fraction=0.1, train_weight_power=1.0, fresh_init=0, proposal_scale=1.0)
     rounds = (AbcSmcRound * 16)()
     n = ctypes.c_uint64()
     s = ctypes.c_void_p(1)   # never used: validation fails first
     for bad in (dict(capacity=1023), dict(rounds=0), dict(eps_factor=1.5), dict(defensive=1.0),
                 dict(val_fraction=0.6), dict(sims_per_round=0), dict(train_weight_power=0.0),
-                dict(train_weight_power=1.5)):
+                dict(train_weight_power=1.5), dict(proposal_scale=0.4), dict(proposal_scale=4.5)):
         cfg = AbcSmcConfig(**dict(good, **bad))
         assert L.abc_smc_run(ctypes.byref(box), op, 10, 1000, ctypes.byref(cfg), rounds, None, None, None,
                              ctypes.byref(n), s) == ABC_ERR_INVALID_ARG, bad
@@ -197,7 +229,7 @@ def test_sequential_drivers_validate_before_any_cuda_call(L):
     reg = (AbcSmcRegion * 2)(AbcSmcRegion(op, 10, 1000, 5.0, None, None, None, 0, 0, 0),
                              AbcSmcRegion(op, 10, 1000, 5.0, None, None, None, 0, 0, 0))
     for bad, shrink, nreg in ((dict(), 0, 2), (dict(), 4, 2), (dict(capacity=10), 2, 2), (dict(), 2, 0),
-                              (dict(), 2, 33)):
+                              (dict(), 2, 33), (dict(proposal_scale=0.0), 2, 2)):
         cfg = AbcSmcStreamConfig(AbcSmcConfig(**dict(good, **bad)), shrink, 5)
         assert L.abc_smc_run_regions(ctypes.byref(box), reg, nreg, ctypes.byref(cfg), rounds, s) \
             == ABC_ERR_INVALID_ARG, (bad, shrink, nreg)

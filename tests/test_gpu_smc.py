@@ -9,6 +9,7 @@ import numpy as np
 import pytest
 
 from tests import inputs
+from tests.smc_rules import flow_is_kept
 from tests.stats_helpers import assert_posterior_close
 
 pytestmark = pytest.mark.gpu
@@ -37,6 +38,8 @@ def test_learned_proposal_gains_and_keeps_the_posterior():
             r["eps"], r["proposal"], r["n_accepted"], r["n_sims"], r["ess_fraction"], r["train_loss"]))
     eps_f = info[-1]["eps"]
     assert info[0]["proposal"] == 0 and info[-1]["proposal"] == 1
+    for r in range(rounds - 1):
+        assert info[r + 1]["proposal"] == flow_is_kept(info[r], 0.1), r
     assert all(r["ess_fraction"] > 0.1 for r in info)
     # plain prior ABC at the final tolerance
     n_plain = 1 << 26

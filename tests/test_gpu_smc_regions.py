@@ -9,6 +9,7 @@ import numpy as np
 import pytest
 
 from tests import inputs
+from tests.smc_rules import flow_is_kept
 from tests.stats_helpers import assert_posterior_close
 
 pytestmark = pytest.mark.gpu
@@ -44,6 +45,9 @@ def test_per_region_flows_keep_each_posterior():
         assert 0 < th.shape[0] <= min(n_pooled, 1 << 18)
         assert np.all(di.cpu().numpy() <= reg["eps"])
         assert info[shrink - 1][g]["eps"] == reg["eps"] and info[0][g]["eps"] > reg["eps"]
+        for r in range(rounds - 1):
+            # a region may also stay on the prior for want of training points
+            assert info[r + 1][g]["proposal"] <= flow_is_kept(info[r][g], 0.1), (g, r)
         used_flow = [info[r][g]["proposal"] for r in range(1, rounds)]
         assert 2 * sum(used_flow) >= len(used_flow), (g, used_flow)
         # plain prior ABC at the same final tolerance
