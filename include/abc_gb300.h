@@ -126,6 +126,27 @@ abc_status abc_sample_async(const abc_prior_box* prior, abc_observed obs, double
                             float* theta_out, double* dist_out, uint64_t* idx_out, uint64_t capacity,
                             uint64_t* counters_dev, void* cuda_stream);
 
+/* Rejection sampling until a target number of accepts (Sec. 2.2: draws are
+ * repeated until the target number of posterior samples is accepted; Sec. 3.1:
+ * each iteration is one vectorised batch). Runs batches of `batch` consecutive
+ * sample indices from first_index on, one launch of abc_sample's kernel each
+ * on the resident observed series, until at least n_target samples are
+ * accepted or max_samples indices are used. The accepted set is every sample
+ * accepted among [first_index, first_index + *n_used): the batches are whole
+ * (only max_samples may cut the last one), so the set depends on the inputs
+ * alone, not on timing. Outputs as abc_sample (DEVICE buffers of `capacity`
+ * rows, order unspecified); *n_accepted (HOST) may exceed n_target by the last
+ * batch's accepts, and falls short of it only when max_samples ran out.
+ * Returns ABC_ERR_CAPACITY as soon as the accepts exceed capacity
+ * (*n_accepted, *n_used: the true counts so far; output contents then
+ * unspecified). n_target = 0 or max_samples = 0 runs nothing. Synchronises
+ * cuda_stream after every batch (one 24-byte read of the counters);
+ * abc_last_simulated_days reports the days of all batches. */
+abc_status abc_sample_until(const abc_prior_box* prior, abc_observed obs, double eps, uint64_t n_target,
+                            uint64_t batch, uint64_t max_samples, uint64_t seed, uint32_t stream, abc_mode mode,
+                            uint64_t first_index, float* theta_out, double* dist_out, uint64_t* idx_out,
+                            uint64_t capacity, uint64_t* n_accepted, uint64_t* n_used, void* cuda_stream);
+
 /* The distance of every sample in [first_index, first_index + n_samples)
  * (Sec. 2.2): dist_out DEVICE double [n_samples], dist_out[j] the distance of
  * sample first_index + j. theta_out, when not NULL, is DEVICE float

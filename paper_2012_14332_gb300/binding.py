@@ -125,8 +125,11 @@ def load(path=None):
         L.abc_observed_destroy.argtypes = [vp]
         L.abc_sample_async.argtypes = [box, vp, ctypes.c_double, u64, u64, u32, ctypes.c_int, u64, vp, vp, vp, u64,
                                        vp, vp]
+        L.abc_sample_until.argtypes = [box, vp, ctypes.c_double, u64, u64, u64, u64, u32, ctypes.c_int, u64, vp, vp,
+                                       vp, u64, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64), vp]
         for nm in ("abc_sample", "abc_sample_noalloc", "abc_distances", "abc_simulate", "abc_step",
-                   "abc_kth_smallest", "abc_observed_create", "abc_observed_destroy", "abc_sample_async"):
+                   "abc_kth_smallest", "abc_observed_create", "abc_observed_destroy", "abc_sample_async",
+                   "abc_sample_until"):
             getattr(L, nm).restype = ctypes.c_int
         L.abc_strerror.argtypes = [ctypes.c_int]
         L.abc_strerror.restype = ctypes.c_char_p
@@ -343,6 +346,38 @@ def abc_sample_async(obs, eps, n_samples, seed, out, counters, stream=0, mode="f
                                  _mode(mode), int(first_index), _dev(theta, torch.float32, (capacity, 8)),
                                  _dev(dist, torch.float64, (capacity,)), _dev(idx, torch.int64, (capacity,)),
                                  int(capacity), counters.data_ptr(), _stream(cuda_stream)))
+
+
+def abc_sample_until(obs, eps, n_target, seed, batch=1 << 22, max_samples=1 << 40, stream=0, mode="fast",
+                     first_index=0, capacity=None, out=None, lo=PAPER_LO, hi=PAPER_HI, cuda_stream=None,
+                     allow_overflow=False):
+    """ABC rejection in batches of `batch` indices from first_index on until
+    n_target samples are accepted (or max_samples indices are used). obs is an
+    Observed. Returns (theta [m, 8] f32, dist [m] f64, idx [m] int64,
+    n_accepted, n_used) as CUDA tensors, m = min(n_accepted, capacity): every
+    sample accepted among [first_index, first_index + n_used)."""
+    L = load()
+    if capacity is None:
+        capacity = max(4 * int(n_target), 1024)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    if out is None:
+        theta = torch.empty((capacity, 8), dtype=torch.float32, device=dev)
+        dist = torch.empty((capacity,), dtype=torch.float64, device=dev)
+        idx = torch.empty((capacity,), dtype=torch.int64, device=dev)
+    else:
+        theta, dist, idx = out
+        capacity = theta.shape[0]
+    nacc, used = ctypes.c_uint64(0), ctypes.c_uint64(0)
+    b = prior_box(lo, hi)
+    st = L.abc_sample_until(ctypes.byref(b), obs.handle, float(eps), int(n_target), int(batch), int(max_samples),
+                            int(seed), int(stream), _mode(mode), int(first_index),
+                            _dev(theta, torch.float32, (capacity, 8)), _dev(dist, torch.float64, (capacity,)),
+                            _dev(idx, torch.int64, (capacity,)), int(capacity), ctypes.byref(nacc), ctypes.byref(used),
+                            _stream(cuda_stream))
+    _check(L, st, allow=(ABC_ERR_CAPACITY,) if allow_overflow else ())
+    n = int(nacc.value)
+    m = min(n, capacity)
+    return theta[:m], dist[:m], idx[:m], n, int(used.value)
 
 
 def abc_sample_noalloc(observed, N_pop, eps, n_samples, seed, out, stream=0, mode="fast", first_index=0,

@@ -1,5 +1,6 @@
 // abc_api.cu -- the C ABI declared in include/abc_gb300.h: argument checks,
 // kernel parameters, stream-ordered scratch memory and error reporting.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -441,6 +442,82 @@ abc_status abc_sample_async(const abc_prior_box* prior, abc_observed obs, double
     a.idx_out = idx_out;
     if (injected("launch")) return fail(ABC_ERR_CUDA, "kernel launch failed (injected)");
     CUDA_TRY(abcgb::launch_reject(p, a, kernel_mode(mode), s, nullptr), "abc_reject_kernel launch");
+    return ok();
+}
+
+abc_status abc_sample_until(const abc_prior_box* prior, abc_observed obs, double eps, uint64_t n_target,
+                            uint64_t batch, uint64_t max_samples, uint64_t seed, uint32_t stream, abc_mode mode,
+                            uint64_t first_index, float* theta_out, double* dist_out, uint64_t* idx_out,
+                            uint64_t capacity, uint64_t* n_accepted, uint64_t* n_used, void* cuda_stream)
+{
+    abc_status st;
+    if ((st = check_prior(prior)) != ABC_OK) return st;
+    if (!obs) return fail(ABC_ERR_INVALID_ARG, "observed handle is NULL");
+    if ((st = check_model(obs->T, obs->N_pop, stream)) != ABC_OK) return st;
+    if (!valid_mode(mode)) return fail(ABC_ERR_INVALID_ARG, "unknown mode %d", (int)mode);
+    if (!(eps >= 0.0)) return fail(ABC_ERR_INVALID_ARG, "eps must be >= 0 and not NaN");
+    if (!n_accepted || !n_used) return fail(ABC_ERR_INVALID_ARG, "n_accepted and n_used are required");
+    if (batch == 0) return fail(ABC_ERR_INVALID_ARG, "batch must be >= 1");
+    if (capacity > 0 && (!theta_out || !dist_out || !idx_out))
+        return fail(ABC_ERR_INVALID_ARG, "output buffers are NULL");
+    if (max_samples > ~(uint64_t)0 - first_index)
+        return fail(ABC_ERR_INVALID_ARG, "first_index + max_samples overflows");
+    int dev = -1;
+    CUDA_TRY(cudaGetDevice(&dev), "cudaGetDevice");
+    if (dev != obs->device) return fail(ABC_ERR_INVALID_ARG, "the observed handle belongs to another device");
+    *n_accepted = 0;
+    *n_used = 0;
+    g_last_sim_days = 0;
+    if (n_target == 0 || max_samples == 0) return ok();
+
+    const abcgb::ModelParams p = make_params(prior, obs->T, obs->N_pop, seed, stream, obs->ard0);
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    SampleScratch* sc = nullptr;
+    if ((st = sample_scratch(256, &sc)) != ABC_OK) return st;
+    unsigned long long* count_h = (unsigned long long*)sc->host;
+    unsigned long long* count_d = (unsigned long long*)sc->dev;
+    auto drain = [s](abc_status e) {
+        cudaStreamSynchronize(s);
+        return e;
+    };
+    // accepts and simulated days accumulate over the batches; each batch
+    // starts its own index claims at 0
+    cudaError_t ce = cudaMemsetAsync(count_d, 0, 3 * sizeof(unsigned long long), s);
+    if (ce != cudaSuccess) return drain(cuda_fail(ce, "cudaMemsetAsync(counters)"));
+    abcgb::RejectArgs a;
+    a.obs = (const int4*)obs->dev;
+    a.acc_max = acc_threshold(eps);
+    a.count = count_d;
+    a.next = count_d + 1;
+    a.sim_days = count_d + 2;
+    a.capacity = capacity;
+    a.theta_out = theta_out;
+    a.dist_out = dist_out;
+    a.idx_out = idx_out;
+    uint64_t used = 0;
+    unsigned long long count = 0;
+    while (used < max_samples && count < n_target && count <= capacity) {
+        const uint64_t nb = std::min(batch, max_samples - used);
+        if (used > 0) {
+            ce = cudaMemsetAsync(count_d + 1, 0, sizeof(unsigned long long), s);
+            if (ce != cudaSuccess) return drain(cuda_fail(ce, "cudaMemsetAsync(claim counter)"));
+        }
+        a.first_index = first_index + used;
+        a.n_samples = nb;
+        if (injected("launch")) return drain(fail(ABC_ERR_CUDA, "kernel launch failed (injected)"));
+        ce = abcgb::launch_reject(p, a, kernel_mode(mode), s, nullptr);
+        if (ce != cudaSuccess) return drain(cuda_fail(ce, "abc_reject_kernel launch"));
+        ce = cudaMemcpyAsync(count_h, count_d, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
+        if (ce != cudaSuccess) return drain(cuda_fail(ce, "cudaMemcpyAsync(counters)"));
+        CUDA_TRY(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+        used += nb;
+        count = count_h[0];
+        g_last_sim_days = count_h[2];
+    }
+    *n_accepted = count;
+    *n_used = used;
+    if (count > capacity)
+        return fail(ABC_ERR_CAPACITY, "%llu samples accepted, capacity %llu", count, (unsigned long long)capacity);
     return ok();
 }
 

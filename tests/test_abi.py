@@ -157,6 +157,13 @@ def test_other_entry_points_validate(L):
     obs = np.zeros((3, 11), dtype=np.int32)
     assert L.abc_distances(ctypes.byref(box), obs.ctypes.data_as(ctypes.c_void_p), 10, 1000, 5, 1, 0, 1, 0, None,
                            None, None) == ABC_ERR_INVALID_ARG
+    n1, n2 = ctypes.c_uint64(7), ctypes.c_uint64(7)
+    assert L.abc_sample_until(ctypes.byref(box), None, 1.0, 5, 10, 100, 1, 0, 1, 0, None, None, None, 0,
+                              ctypes.byref(n1), ctypes.byref(n2), None) == ABC_ERR_INVALID_ARG
+    assert "observed" in L.abc_last_error().decode()
+    bad = prior_box(hi=[0.0] * 8)
+    assert L.abc_sample_until(ctypes.byref(bad), None, 1.0, 5, 10, 100, 1, 0, 1, 0, None, None, None, 0,
+                              ctypes.byref(n1), ctypes.byref(n2), None) == ABC_ERR_INVALID_ARG
 
 
 def test_zero_samples_is_a_no_op(L):
