@@ -238,8 +238,8 @@ def bench_learned_stream(abc, torch, prior_stream=None):
     final eps over the first 4 rounds, then stays there while the samples
     accepted at the final eps pool in device buffers with their importance
     weights; the 16 flows (3 x 256, BF16) train together after every round,
-    a region falling back to the prior whenever its flow round gave fewer
-    effective samples per simulation than its defensive prior draws' acceptance."""
+    a region falling back to the prior whenever its ESS fraction drops below
+    10 %."""
     with open(os.path.join(ROOT, "tests", "golden", "workloads.json")) as f:
         wl = json.load(f)
     names = sorted(k for k in wl if k.startswith("stream16_"))
@@ -252,14 +252,15 @@ def bench_learned_stream(abc, torch, prior_stream=None):
                                         flow_blocks=3, flow_hidden=256, train_steps=500, train_steps_warm=100,
                                         train_batch=4096, train_lr=1e-3, seed=wl[names[0]]["seed"] + 29,
                                         capacity=1 << 20, mode="fast", proposal_scale=LEARNED_TAU,
-                                        train_weight_power=LEARNED_POWER)
+                                        train_weight_power=LEARNED_POWER, fallback="ess")
     wall = time.perf_counter() - t0
     pooled = sum(r[3] for r in res)
     eff = sum(ess(r[1].cpu().numpy()) for r in res)
     dev_s = sum(info[r][0]["ms_propose"] + info[r][0]["ms_simulate"] + info[r][0]["ms_train"] for r in range(rounds))
     out = {"workload": "16 regions (P log-uniform 1e6..3e8, T uniform 30..180, own final eps each), one flow "
                        "proposal per region (3 x 256 BF16), %d rounds x 2^20 simulations per region (2^24 per "
-                       "chunk, 2^28 in all), eps x0.7 per round over the first %d rounds, fast mode" % (rounds, shrink),
+                       "chunk, 2^28 in all), eps x0.7 per round over the first %d rounds, prior fallback when a "
+                       "region's ESS fraction drops below 10 %%, fast mode" % (rounds, shrink),
            "seconds": wall, "device_seconds_by_round_events": dev_s * 1e-3,
            "propose_seconds": sum(info[r][0]["ms_propose"] for r in range(rounds)) * 1e-3,
            "simulate_seconds": sum(info[r][0]["ms_simulate"] for r in range(rounds)) * 1e-3,

@@ -432,14 +432,11 @@ abc_status abc_maf_destroy(abc_maf maf);
  * eps_r = eps0 * eps_factor^r. Round 0 draws from the prior. After each round
  * the flow is trained (weighted maximum likelihood) on that round's accepted
  * samples with importance weights w = prior(theta) / q(theta) (w = 1 for
- * prior draws), and the next round draws from the flow unless the prior
- * would do better, in which case it falls back to the prior: a flow round
- * with defensive draws falls back when its effective samples per simulation,
- * ESS / sims_per_round with ESS = (sum w)^2 / sum w^2, fall below the prior's
- * acceptance rate measured on those defensive draws (n_defensive_accepted /
- * n_defensive); a prior round, or a flow round without defensive draws, when
- * its ESS fraction ESS / n_accepted is below ess_min; any round with fewer
- * than 64 accepted samples. Training holds out val_fraction of the round's
+ * prior draws), and the next round draws from the flow unless fallback_rule
+ * sends it back to the prior (ESS = (sum w)^2 / sum w^2; by default when the
+ * flow gave fewer effective samples per simulation than the prior's
+ * acceptance rate, measured on the round's defensive draws as
+ * n_defensive_accepted / n_defensive). Training holds out val_fraction of the round's
  * accepts and stops early (abc_maf_train_flows). A flow round draws a fraction `defensive` of its
  * proposals from the prior and weights every proposal by the mixture density
  * q_mix = (1 - defensive) q + defensive * prior (defensive importance sampling,
@@ -470,7 +467,17 @@ typedef struct {
     double proposal_scale;    /* base scale tau of the flow proposals (abc_maf_set_proposal_scale), in [0.5, 4]:
                                  1 samples the trained flow; above 1 a broader proposal with heavier coverage
                                  of the tails, weighted by its own density */
+    int32_t fallback_rule;    /* ABC_FALLBACK_EFFICIENCY (0) or ABC_FALLBACK_ESS (1), see below */
 } abc_smc_config;
+
+/* When a round sends the next one back to the prior (fewer than 64 accepts
+ * always does). ABC_FALLBACK_EFFICIENCY: a flow round with defensive draws
+ * keeps the flow while ESS / sims_per_round reaches the prior's acceptance
+ * rate measured on those draws; a prior round, or a flow round without
+ * defensive draws, uses the flow next when its ESS fraction reaches ess_min.
+ * ABC_FALLBACK_ESS: every round uses the flow next when its ESS fraction
+ * ESS / n_accepted reaches ess_min, and the prior otherwise. */
+enum { ABC_FALLBACK_EFFICIENCY = 0, ABC_FALLBACK_ESS = 1 };
 
 typedef struct {
     double eps;

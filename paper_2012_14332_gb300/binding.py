@@ -54,7 +54,7 @@ class AbcSmcConfig(ctypes.Structure):
                 ("train_lr", ctypes.c_float), ("seed", ctypes.c_uint64), ("capacity", ctypes.c_uint64),
                 ("mode", ctypes.c_int), ("defensive", ctypes.c_double), ("val_fraction", ctypes.c_double),
                 ("train_weight_power", ctypes.c_double), ("fresh_init", ctypes.c_int32),
-                ("proposal_scale", ctypes.c_double)]
+                ("proposal_scale", ctypes.c_double), ("fallback_rule", ctypes.c_int32)]
 
 
 class AbcSmcRound(ctypes.Structure):
@@ -780,10 +780,20 @@ def abc_maf_train_flows(flow, thetas, weights=None, **kw):
 
 
 
+ABC_FALLBACK_EFFICIENCY, ABC_FALLBACK_ESS = 0, 1
+_FALLBACK = {"efficiency": ABC_FALLBACK_EFFICIENCY, "ess": ABC_FALLBACK_ESS}
+
+
+def _fallback(rule):
+    if rule not in _FALLBACK:
+        raise ValueError("fallback must be one of %s" % sorted(_FALLBACK))
+    return _FALLBACK[rule]
+
+
 def abc_smc_run(observed, N_pop, eps0, rounds=5, sims_per_round=1 << 22, eps_factor=0.7, ess_min=0.1,
                 flow_blocks=3, flow_hidden=256, train_steps=500, train_batch=1024, train_lr=1e-3, seed=0,
                 capacity=None, mode="fast", defensive=0.1, val_fraction=0.1, train_weight_power=0.8, fresh_init=False,
-                proposal_scale=1.25, lo=PAPER_LO, hi=PAPER_HI, cuda_stream=None):
+                proposal_scale=1.25, fallback="efficiency", lo=PAPER_LO, hi=PAPER_HI, cuda_stream=None):
     """Sequential ABC with the learned flow proposal. Returns (rounds: list of
     dicts, theta [m, 8], weights [m] (f64, sum 1), dist [m]) of the last round.
     The defaults proposal_scale=1.25 (proposals from the flow with its base
@@ -800,7 +810,7 @@ def abc_smc_run(observed, N_pop, eps0, rounds=5, sims_per_round=1 << 22, eps_fac
     cfg = AbcSmcConfig(int(rounds), int(sims_per_round), float(eps0), float(eps_factor), float(ess_min),
                        int(flow_blocks), int(flow_hidden), int(train_steps), int(train_batch), float(train_lr),
                        int(seed), int(capacity), _mode(mode), float(defensive), float(val_fraction),
-                       float(train_weight_power), int(bool(fresh_init)), float(proposal_scale))
+                       float(train_weight_power), int(bool(fresh_init)), float(proposal_scale), _fallback(fallback))
     rr = (AbcSmcRound * int(rounds))()
     dev = torch.device("cuda", torch.cuda.current_device())
     theta = torch.empty((capacity, 8), dtype=torch.float32, device=dev)
@@ -821,7 +831,8 @@ def abc_smc_run(observed, N_pop, eps0, rounds=5, sims_per_round=1 << 22, eps_fac
 def abc_smc_run_regions(regions, rounds=16, shrink_rounds=4, sims_per_round=1 << 20, eps_factor=0.7, ess_min=0.1,
                         flow_blocks=3, flow_hidden=256, train_steps=500, train_steps_warm=100, train_batch=1024,
                         train_lr=1e-3, seed=0, capacity=None, mode="fast", defensive=0.1, val_fraction=0.1,
-                        train_weight_power=0.8, proposal_scale=1.25, lo=PAPER_LO, hi=PAPER_HI, cuda_stream=None):
+                        train_weight_power=0.8, proposal_scale=1.25, fallback="efficiency", lo=PAPER_LO, hi=PAPER_HI,
+                        cuda_stream=None):
     """Sequential ABC with one flow proposal per region, all regions in one
     batched launch per round. regions: list of dicts with observed (host int32
     [3, T+1]), N_pop, eps (final) and pool (samples kept at the final eps).
@@ -848,7 +859,7 @@ def abc_smc_run_regions(regions, rounds=16, shrink_rounds=4, sims_per_round=1 <<
     base = AbcSmcConfig(int(rounds), int(sims_per_round), 0.0, float(eps_factor), float(ess_min), int(flow_blocks),
                         int(flow_hidden), int(train_steps), int(train_batch), float(train_lr), int(seed),
                         int(capacity), _mode(mode), float(defensive), float(val_fraction),
-                        float(train_weight_power), 0, float(proposal_scale))
+                        float(train_weight_power), 0, float(proposal_scale), _fallback(fallback))
     cfg = AbcSmcStreamConfig(base, int(shrink_rounds), int(train_steps_warm))
     rr = (AbcSmcRound * (int(rounds) * R))()
     s = cuda_stream if cuda_stream is not None else torch.cuda.Stream()

@@ -220,17 +220,19 @@ static abc_status round_weights(const float* logq, const uint64_t* idx, uint64_t
     return ABC_OK;
 }
 
-// Whether the next round should draw from the flow. A flow round keeps the
-// flow when it gave at least as many effective samples per simulation,
-// ESS / N with ESS = (sum w)^2 / sum w^2, as rejection from the prior accepts
-// per simulation at the same eps, that rate measured on the round's own
-// defensive prior draws. A prior round, or a flow round without defensive
-// draws, keeps or switches to the flow when its ESS fraction reaches ess_min.
-// Fewer than 64 accepted samples always means the prior.
-static bool next_uses_flow(const abc_smc_round& R, double sw, double sw2, double ess_min)
+// Whether the next round should draw from the flow. By efficiency: a flow
+// round keeps the flow when it gave at least as many effective samples per
+// simulation, ESS / N with ESS = (sum w)^2 / sum w^2, as rejection from the
+// prior accepts per simulation at the same eps, that rate measured on the
+// round's own defensive prior draws; a prior round, or a flow round without
+// defensive draws, keeps or switches to the flow when its ESS fraction
+// reaches ess_min. By ESS: every round by its ESS fraction. Fewer than 64
+// accepted samples always means the prior.
+static bool next_uses_flow(const abc_smc_round& R, double sw, double sw2, const abc_smc_config& cfg)
 {
     if (R.n_accepted < 64 || !(sw2 > 0.0)) return false;
-    if (R.proposal == 0 || R.n_defensive == 0) return R.ess_fraction >= ess_min;
+    if (cfg.fallback_rule == ABC_FALLBACK_ESS || R.proposal == 0 || R.n_defensive == 0)
+        return R.ess_fraction >= cfg.ess_min;
     return sw * sw / sw2 / (double)R.n_sims >= (double)R.n_defensive_accepted / (double)R.n_defensive;
 }
 
@@ -245,7 +247,7 @@ extern "C" abc_status abc_smc_run(const abc_prior_box* prior, const int32_t* obs
         cfg->eps_factor > 1.0 || !(cfg->ess_min >= 0.0) || cfg->capacity == 0 || !(cfg->defensive >= 0.0) ||
         cfg->defensive >= 1.0 || !(cfg->val_fraction >= 0.0) || cfg->val_fraction > 0.5 ||
         !(cfg->train_weight_power > 0.0) || cfg->train_weight_power > 1.0 || !(cfg->proposal_scale >= 0.5) ||
-        cfg->proposal_scale > 4.0)
+        cfg->proposal_scale > 4.0 || (cfg->fallback_rule != ABC_FALLBACK_EFFICIENCY && cfg->fallback_rule != ABC_FALLBACK_ESS))
         return plan_fail(ABC_ERR_INVALID_ARG, "bad sequential ABC configuration");
     // every accepted sample of a round is kept: the accept buffer is filled in
     // claim (index) order and a flow round's defensive prior draws are its
@@ -370,7 +372,7 @@ extern "C" abc_status abc_smc_run(const abc_prior_box* prior, const int32_t* obs
             }
             SMC_TRY(cudaEventRecord(gd.ev[3], s), "cudaEventRecord");
         } else {
-            const bool trainable = next_uses_flow(R, sw, sw2, cfg->ess_min);
+            const bool trainable = next_uses_flow(R, sw, sw2, *cfg);
             if (trainable) {
                 SMC_ST(shuffled_training_set(acc_theta, d_wround, m, m, cfg->seed + (uint64_t)r, d_train, d_w, s));
                 if (cfg->fresh_init)
@@ -430,7 +432,8 @@ extern "C" abc_status abc_smc_run_regions(const abc_prior_box* prior, abc_smc_re
         !(cfg->ess_min >= 0.0) || cfg->capacity == 0 || !(cfg->defensive >= 0.0) || cfg->defensive >= 1.0 ||
         !(cfg->val_fraction >= 0.0) || cfg->val_fraction > 0.5 || cfg->capacity < cfg->sims_per_round ||
         !(cfg->train_weight_power > 0.0) || cfg->train_weight_power > 1.0 || !(cfg->proposal_scale >= 0.5) ||
-        cfg->proposal_scale > 4.0 || scfg->shrink_rounds < 1 || scfg->shrink_rounds > cfg->rounds || scfg->train_steps_warm < 0 ||
+        cfg->proposal_scale > 4.0 ||
+        (cfg->fallback_rule != ABC_FALLBACK_EFFICIENCY && cfg->fallback_rule != ABC_FALLBACK_ESS) || scfg->shrink_rounds < 1 || scfg->shrink_rounds > cfg->rounds || scfg->train_steps_warm < 0 ||
         cfg->train_steps < 0)
         return plan_fail(ABC_ERR_INVALID_ARG, "bad multi-region sequential ABC configuration");
     for (int32_t g = 0; g < R; ++g) {
@@ -579,7 +582,7 @@ extern "C" abc_status abc_smc_run_regions(const abc_prior_box* prior, abc_smc_re
             // (next_uses_flow); the flow trains on this round's weighted
             // accepts, or, once at the final eps, on the whole pool (same
             // target, more points)
-            const bool good = next_uses_flow(Rr[g], sw, sw2, cfg->ess_min);
+            const bool good = next_uses_flow(Rr[g], sw, sw2, *cfg);
             if (r + 1 < cfg->rounds) {
                 float* tt = d_train + (size_t)g * 8 * cap;
                 float* tw = d_w + (size_t)g * cap;

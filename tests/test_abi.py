@@ -220,13 +220,14 @@ def test_sequential_drivers_validate_before_any_cuda_call(L):
     op = obs.ctypes.data_as(ctypes.c_void_p)
     good = dict(rounds=3, sims_per_round=1024, eps0=10.0, eps_factor=0.7, ess_min=0.1, flow_blocks=3, flow_hidden=64,
                 train_steps=10, train_batch=256, train_lr=1e-3, seed=1, capacity=1024, mode=1, defensive=0.1,
-                val_fraction=0.1, train_weight_power=1.0, fresh_init=0, proposal_scale=1.0)
+                val_fraction=0.1, train_weight_power=1.0, fresh_init=0, proposal_scale=1.0, fallback_rule=0)
     rounds = (AbcSmcRound * 16)()
     n = ctypes.c_uint64()
     s = ctypes.c_void_p(1)   # never used: validation fails first
     for bad in (dict(capacity=1023), dict(rounds=0), dict(eps_factor=1.5), dict(defensive=1.0),
                 dict(val_fraction=0.6), dict(sims_per_round=0), dict(train_weight_power=0.0),
-                dict(train_weight_power=1.5), dict(proposal_scale=0.4), dict(proposal_scale=4.5)):
+                dict(train_weight_power=1.5), dict(proposal_scale=0.4), dict(proposal_scale=4.5),
+                dict(fallback_rule=2)):
         cfg = AbcSmcConfig(**dict(good, **bad))
         assert L.abc_smc_run(ctypes.byref(box), op, 10, 1000, ctypes.byref(cfg), rounds, None, None, None,
                              ctypes.byref(n), s) == ABC_ERR_INVALID_ARG, bad

@@ -4,7 +4,9 @@ importance-weighted samples at its final tolerance estimate the same ABC
 posterior (Eq. 7) as plain rejection from the prior at that tolerance (every
 coordinate's mean within 0.05 posterior sd and CDF at five quantiles within
 0.02, beyond Monte-Carlo error), and the learned proposals give far more
-effective samples per simulation than the prior."""
+effective samples per simulation than the prior. Both fallback rules: by ESS
+fraction below 10 % (the 16-region stream's stated rule) and by efficiency
+against the prior."""
 import numpy as np
 import pytest
 
@@ -25,7 +27,8 @@ _build.build()
 NAMES = ["stream16_r11", "stream16_r15", "stream16_r04", "stream16_r12"]
 
 
-def test_per_region_flows_keep_each_posterior():
+@pytest.mark.parametrize("rule", ["ess", "efficiency"])
+def test_per_region_flows_keep_each_posterior(rule):
     regs = []
     for k, name in enumerate(NAMES):
         w = inputs.workload(name)
@@ -35,7 +38,7 @@ def test_per_region_flows_keep_each_posterior():
     rounds, shrink, n = 6, 3, 1 << 18
     info, res = abc.abc_smc_run_regions(regs, rounds=rounds, shrink_rounds=shrink, sims_per_round=n, eps_factor=0.7,
                                         flow_blocks=3, flow_hidden=128, train_steps=400, train_steps_warm=150,
-                                        train_batch=4096, train_lr=2e-3, seed=21, mode="fast")
+                                        train_batch=4096, train_lr=2e-3, seed=21, mode="fast", fallback=rule)
     for r in range(rounds):
         print("round %d: %s" % (r, "  ".join("%d/%d ess %.2f" % (x["proposal"], x["n_accepted"], x["ess_fraction"])
                                              for x in info[r])))
@@ -47,7 +50,7 @@ def test_per_region_flows_keep_each_posterior():
         assert info[shrink - 1][g]["eps"] == reg["eps"] and info[0][g]["eps"] > reg["eps"]
         for r in range(rounds - 1):
             # a region may also stay on the prior for want of training points
-            assert info[r + 1][g]["proposal"] <= flow_is_kept(info[r][g], 0.1), (g, r)
+            assert info[r + 1][g]["proposal"] <= flow_is_kept(info[r][g], 0.1, rule), (g, r)
         used_flow = [info[r][g]["proposal"] for r in range(1, rounds)]
         assert 2 * sum(used_flow) >= len(used_flow), (g, used_flow)
         # plain prior ABC at the same final tolerance
