@@ -222,6 +222,42 @@ def bench_streamed(abc, torch, dev, flush, sm_count, sm_max, chunks=16):
             "roofline": roofline(days, ms, sm_count, sm_max)}
 
 
+def bench_exact(abc, torch, w, dev, flush, fast_days_per_s, steps=5, warmup=3, n=1 << 22):
+    """The headline workload in exact mode (the project's own FP32 series, no
+    FMA contraction: bit-exact against the CPU oracle), 2^22 samples per
+    launch on fresh indices, L2 flushed between launches; the cost of exactness
+    as simulated days per second against fast mode."""
+    obs_dev = abc.Observed(w["observed"], w["P"])
+    cap = 1 << 14
+    outs = (torch.empty((cap, 8), dtype=torch.float32, device=dev), torch.empty((cap,), dtype=torch.float64, device=dev),
+            torch.empty((cap,), dtype=torch.int64, device=dev))
+    cnt = torch.zeros((warmup + steps, 4), dtype=torch.int64, device=dev)
+    s = torch.cuda.current_stream(dev)
+    first = 1 << 40
+    for k in range(warmup):
+        abc.abc_sample_async(obs_dev, w["eps"], n, w["seed"], outs, cnt[k], mode="exact", first_index=first + k * n,
+                             cuda_stream=s)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for k in range(steps):
+        flush.fill_(k & 0xFF)
+        ev[k][0].record(s)
+        abc.abc_sample_async(obs_dev, w["eps"], n, w["seed"], outs, cnt[warmup + k], mode="exact",
+                             first_index=first + (warmup + k) * n, cuda_stream=s)
+        ev[k][1].record(s)
+    torch.cuda.synchronize()
+    obs_dev.close()
+    ms = float(sum(a.elapsed_time(b) for a, b in ev))
+    c = cnt[warmup:].cpu().numpy()
+    acc, days = int(c[:, 0].sum()), int(c[:, 2].sum())
+    dps = days / (ms * 1e-3)
+    return {"workload": "region_6e7_T100 in exact mode, %d prior samples per launch, %d launches, eps=%g" % (
+                n, steps, w["eps"]),
+            "accepted_per_s": acc / (ms * 1e-3), "unit": UNIT, "ms_per_launch": ms / steps,
+            "simulated_days_per_s": dps, "fast_simulated_days_per_s": fast_days_per_s,
+            "exact_over_fast": dps / fast_days_per_s}
+
+
 def ess(w):
     w = np.asarray(w, dtype=np.float64)
     return float(w.sum() ** 2 / (w ** 2).sum()) if len(w) else 0.0
@@ -403,8 +439,9 @@ def main():
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--no-streamed", action="store_true")
     ap.add_argument("--no-learned-stream", action="store_true")
+    ap.add_argument("--no-exact", action="store_true")
     ap.add_argument("--leg", default="all", choices=["all", "headline", "batched", "learned", "streamed",
-                                                     "learned_stream"],
+                                                     "learned_stream", "exact"],
                     help="run one leg only (profiling); 'all' is the benchmark")
     ap.add_argument("--samples", type=int, default=0,
                     help="samples per launch (profiling runs on a smaller case; not a benchmark value)")
@@ -454,7 +491,7 @@ def main():
         abc.abc_sample_async(obs_dev, eps, n, seed, outs, counters[s], mode=w["mode"], first_index=first_index(s),
                              cuda_stream=stream)
 
-    if args.leg in ("batched", "learned", "streamed", "learned_stream"):
+    if args.leg in ("batched", "learned", "streamed", "learned_stream", "exact"):
         props = torch.cuda.get_device_properties(dev)
         peaks = measured_peaks() or {}
         if args.leg == "batched":
@@ -464,6 +501,8 @@ def main():
             out = bench_streamed(abc, torch, dev, flush, props.multi_processor_count, peaks.get("sm_max_mhz", 2070.0))
         elif args.leg == "learned_stream":
             out = bench_learned_stream(abc, torch)
+        elif args.leg == "exact":
+            out = bench_exact(abc, torch, w, dev, flush, float("nan"))
         else:
             out = bench_learned(abc, torch, w, float("nan"), peaks)
         print(json.dumps({"leg": args.leg, **out}), flush=True)
@@ -573,7 +612,9 @@ def main():
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(w)
         if args.leg == "headline":
-            args.no_learned = args.no_batched = args.no_streamed = args.no_learned_stream = True
+            args.no_learned = args.no_batched = args.no_streamed = args.no_learned_stream = args.no_exact = True
+        if not args.no_exact and world == 1:
+            line["exact_mode"] = bench_exact(abc, torch, w, dev, flush, sim_days[0] / (float(np.sum(launch_ms)) * 1e-3))
         if not args.no_learned and world == 1:
             line["learned_proposal"] = bench_learned(abc, torch, w, value, peaks)
         if not args.no_batched and world == 1:
