@@ -22,6 +22,9 @@ namespace abcgb {
 namespace {
 
 constexpr int kRingB = 64;
+// idle lanes get new samples once at least this many are idle, as in
+// abc_reject_kernel (all 32 always qualify)
+constexpr uint32_t kRefillMinIdleB = 2;
 
 struct BatchRing {
     float4 lo[kRingB];
@@ -74,8 +77,8 @@ __global__ void __launch_bounds__(BLOCK) abc_batch_kernel(const __grid_constant_
 
     while (true) {
         const uint32_t idle = __ballot_sync(0xFFFFFFFFu, !active);
-        if (idle) {
-            const uint32_t need = __popc(idle);
+        const uint32_t need = __popc(idle);
+        if (need >= kRefillMinIdleB) {
             if (tail - head < need && !exhausted) {
                 unsigned long long c = 0;
                 if (lane == 0) c = atomicAdd(a.next, 1ull);
@@ -113,6 +116,10 @@ __global__ void __launch_bounds__(BLOCK) abc_batch_kernel(const __grid_constant_
                 }
             }
             const uint32_t avail = tail - head;
+            // every lane idle and nothing left to hand out: the chunks are
+            // exhausted (a claim adds at least one entry otherwise, since a
+            // chunk of only skipped proposals is followed by another claim)
+            if (need == 32 && avail == 0 && exhausted) break;
             if (!active) {
                 const uint32_t rank = __popc(idle & lt_mask);
                 if (rank < avail) {
@@ -143,7 +150,6 @@ __global__ void __launch_bounds__(BLOCK) abc_batch_kernel(const __grid_constant_
             head += need < avail ? need : avail;
             __syncwarp();
         }
-        if (__ballot_sync(0xFFFFFFFFu, active) == 0) break;
 
         bool accept = false;
 #pragma unroll

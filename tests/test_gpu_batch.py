@@ -158,6 +158,26 @@ def test_nan_proposals_are_skipped():
     plan.close()
 
 
+def test_chunks_of_skipped_proposals_do_not_end_the_run():
+    """A warp that claims a chunk of 32 skipped (NaN) proposals while all its
+    lanes are idle must claim again rather than stop: here every chunk but
+    the last is skipped, and there are more chunks than resident warps, so
+    each warp's first claims find nothing to run."""
+    w = inputs.workload("region_1e6_T49")
+    n, first, stream = 32 * 60000, 77, 4
+    th = inputs.random_thetas(14, n)
+    th_nan = th.copy()
+    th_nan[:-32, 0] = np.nan
+    plan = abc.Plan([dict(observed=w["observed"], N_pop=w["P"], eps=1e12, n_samples=n, first_index=first,
+                          stream=stream, capacity=64, theta_in=torch.from_numpy(th_nan).to(DEV))], SEED, mode="fast")
+    plan.run()
+    tt, di, ix, n_acc, days = plan.results(0)
+    tt, di, ix = _sorted(tt, di, ix)
+    assert n_acc == 32 and days == 32 * w["T"]
+    assert np.array_equal(ix, np.arange(n - 32, n, dtype=np.uint64) + first) and np.array_equal(tt, th[-32:])
+    plan.close()
+
+
 def test_graph_follows_an_eps_change_across_2_to_the_62():
     """The batched kernel has a cheaper distance accumulation for thresholds
     below 2^62; a graph captured with it is recaptured when set_eps moves a
