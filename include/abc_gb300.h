@@ -327,9 +327,10 @@ typedef struct abc_maf_s* abc_maf;
  * 16, 16..256) on the prior box, parameters zero (q = the uniform prior).
  * Allocates its device memory on the current device. The training kernel
  * stages a CTA's operands and gradients in shared memory, about
- * n_blocks (928 hidden + 2048) bytes: a shape beyond the device's per-block
- * limit returns ABC_ERR_INVALID_ARG (on GB300, 227 KB: n_blocks = 4 allows
- * hidden <= 224). */
+ * n_blocks (232 hidden + 512) + 10240 bytes (published BF16 operands and FP32
+ * gradient sums per block, staging of four warps): a shape beyond the
+ * device's per-block limit returns ABC_ERR_INVALID_ARG (on GB300, 227 KB:
+ * n_blocks = 4 allows hidden <= 224). */
 abc_status abc_maf_create(int32_t n_blocks, int32_t hidden, const abc_prior_box* box, abc_maf* maf_out);
 
 /* A set of n_flows (1..ABC_MAF_MAX_FLOWS) independent flows of the same shape
