@@ -313,7 +313,7 @@ def bench_learned_stream(abc, torch, prior_stream=None):
     return out
 
 
-def bench_learned(abc, torch, w, prior_value, peaks, reps=5):
+def bench_learned(abc, torch, w, prior_value, peaks, sm_count, sm_max, reps=5):
     """Sequential ABC with the learned flow proposal on the P = 6e7, T = 100
     region: 5 rounds of 2^22 simulations, eps shrinking by 0.7 per round to the
     headline eps, flow of 3 MADE blocks x 256 hidden units (BF16 weights, FP32
@@ -341,6 +341,7 @@ def bench_learned(abc, torch, w, prior_value, peaks, reps=5):
                      "final_round_ess_fraction": last["ess_fraction"],
                      "all_rounds_seconds": sum(r["ms_propose"] + r["ms_simulate"] + r["ms_train"] for r in info) * 1e-3,
                      "ms_propose": last["ms_propose"], "ms_simulate": last["ms_simulate"],
+                     "final_round_simulated_days": last["simulated_days"],
                      "rounds": [{k: (round(v, 4) if isinstance(v, float) else v) for k, v in r.items()} for r in info]})
     med = lambda key: float(np.median([r[key] for r in runs]))
     flow_runs = [r for r in runs if r["final_round_proposal"] == "flow"]
@@ -356,6 +357,11 @@ def bench_learned(abc, torch, w, prior_value, peaks, reps=5):
            "all_rounds_seconds": med("all_rounds_seconds"),
            "runs": runs}
     if flow_runs:
+        # the final round's simulations of flow proposals (batched kernel with a
+        # proposal buffer) against the same ALU roofline as the headline
+        sims = sorted(flow_runs, key=lambda r: r["final_round_simulated_days"] / r["ms_simulate"])
+        mid = sims[len(sims) // 2]
+        out["simulate_roofline"] = roofline(mid["final_round_simulated_days"], mid["ms_simulate"], sm_count, sm_max)
         ms_prop = float(np.median([r["ms_propose"] for r in flow_runs]))
         # algorithmic work per proposal: every hidden unit once per block (the
         # sampler adds each unit's contribution when its inputs are final), the
@@ -504,7 +510,8 @@ def main():
         elif args.leg == "exact":
             out = bench_exact(abc, torch, w, dev, flush, float("nan"))
         else:
-            out = bench_learned(abc, torch, w, float("nan"), peaks)
+            out = bench_learned(abc, torch, w, float("nan"), peaks, props.multi_processor_count,
+                                peaks.get("sm_max_mhz", 2070.0))
         print(json.dumps({"leg": args.leg, **out}), flush=True)
         return
     for s in range(args.warmup):
@@ -616,7 +623,7 @@ def main():
         if not args.no_exact and world == 1:
             line["exact_mode"] = bench_exact(abc, torch, w, dev, flush, sim_days[0] / (float(np.sum(launch_ms)) * 1e-3))
         if not args.no_learned and world == 1:
-            line["learned_proposal"] = bench_learned(abc, torch, w, value, peaks)
+            line["learned_proposal"] = bench_learned(abc, torch, w, value, peaks, props.multi_processor_count, sm_max)
         if not args.no_batched and world == 1:
             line["batched_regions"] = bench_batched(abc, torch, args.steps, args.warmup, dev, flush,
                                                     props.multi_processor_count, sm_max)

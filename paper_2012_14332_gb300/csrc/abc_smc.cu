@@ -287,6 +287,21 @@ extern "C" abc_status abc_smc_run(const abc_prior_box* prior, const int32_t* obs
     double eps = cfg->eps0;
     bool use_flow = false;
     uint64_t last_n = 0;
+    // one plan for every round, made before the first; each round sets its
+    // eps, proposals and first index before its timed stages
+    {
+        abc_region reg{};
+        reg.observed = observed;
+        reg.T = T;
+        reg.N_pop = N_pop;
+        reg.eps = eps;
+        reg.n_samples = N;
+        reg.first_index = 0;
+        reg.stream = 0;
+        reg.capacity = cap;
+        reg.theta_in = nullptr;
+        SMC_ST(abc_plan_create(prior, &reg, 1, cfg->seed, cfg->mode, &gd.plan));
+    }
     for (int32_t r = 0; r < cfg->rounds; ++r) {
         abc_smc_round& R = rounds_out[r];
         R = abc_smc_round{};
@@ -294,6 +309,8 @@ extern "C" abc_status abc_smc_run(const abc_prior_box* prior, const int32_t* obs
         R.proposal = use_flow ? 1 : 0;
         R.n_sims = N;
         const uint64_t first = (uint64_t)r * N;
+        SMC_ST(abc_plan_set_eps(gd.plan, 0, eps));
+        SMC_ST(abc_plan_set_region(gd.plan, 0, use_flow ? d_prop : nullptr, first));
         SMC_TRY(cudaEventRecord(gd.ev[0], s), "cudaEventRecord");
         if (use_flow) {
             // (1 - defensive) N flow draws, the rest prior draws, all weighted by the mixture density
@@ -317,21 +334,7 @@ extern "C" abc_status abc_smc_run(const abc_prior_box* prior, const int32_t* obs
             }
         }
         SMC_TRY(cudaEventRecord(gd.ev[1], s), "cudaEventRecord");
-        abc_region reg{};
-        reg.observed = observed;
-        reg.T = T;
-        reg.N_pop = N_pop;
-        reg.eps = eps;
-        reg.n_samples = N;
-        reg.first_index = first;
-        reg.stream = 0;
-        reg.capacity = cap;
-        reg.theta_in = use_flow ? d_prop : nullptr;
-        if (gd.plan) {
-            abc_plan_destroy(gd.plan);
-            gd.plan = nullptr;
-        }
-        SMC_ST(abc_plan_create(prior, &reg, 1, cfg->seed, cfg->mode, &gd.plan));
+        SMC_ST(abc_plan_reset(gd.plan, s));
         SMC_ST(abc_plan_run(gd.plan, s));
         SMC_TRY(cudaEventRecord(gd.ev[2], s), "cudaEventRecord");
         uint64_t n_acc = 0, days = 0;
