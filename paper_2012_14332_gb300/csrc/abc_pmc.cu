@@ -351,21 +351,24 @@ abc_status abc_pmc_run(const abc_prior_box* prior, const int32_t* observed, int3
             PMC_TRY(cudaMemcpyAsync(d_w, h_w.data(), sizeof(double) * m, cudaMemcpyHostToDevice, s), "upload");
             PMC_ST(upload_cumw(h_w, d_cumw, s, h_tmp));
         }
-        abc_region reg{};
-        reg.observed = observed;
-        reg.T = T;
-        reg.N_pop = N_pop;
-        reg.eps = eps;
-        reg.n_samples = B;
-        reg.first_index = base;
-        reg.stream = 0;
-        reg.capacity = cap;
-        reg.theta_in = r > 0 ? d_prop : nullptr;
-        if (guard.plan) {
-            abc_plan_destroy(guard.plan);
-            guard.plan = nullptr;
+        // one plan for every round, made in the first; a round sets its eps,
+        // proposal buffer and first index and clears the accepted samples
+        if (!guard.plan) {
+            abc_region reg{};
+            reg.observed = observed;
+            reg.T = T;
+            reg.N_pop = N_pop;
+            reg.eps = eps;
+            reg.n_samples = B;
+            reg.first_index = base;
+            reg.stream = 0;
+            reg.capacity = cap;
+            reg.theta_in = nullptr;
+            PMC_ST(abc_plan_create(prior, &reg, 1, cfg->seed, cfg->mode, &guard.plan));
         }
-        PMC_ST(abc_plan_create(prior, &reg, 1, cfg->seed, cfg->mode, &guard.plan));
+        PMC_ST(abc_plan_set_eps(guard.plan, 0, eps));
+        PMC_ST(abc_plan_set_region(guard.plan, 0, r > 0 ? d_prop : nullptr, base));
+        PMC_ST(abc_plan_reset(guard.plan, s));
         uint64_t n_acc = 0, batches = 0;
         while (n_acc < cfg->n_particles && batches < (uint64_t)cfg->max_batches) {
             if (r > 0)
