@@ -273,7 +273,8 @@ def bench_learned_stream(abc, torch, prior_stream=None):
     per chunk, 2^28 in all); eps shrinks by 0.7 per round to each region's
     final eps over the first 4 rounds, then stays there while the samples
     accepted at the final eps pool in device buffers with their importance
-    weights; the 16 flows (3 x 256, BF16) train together after every round,
+    weights; the 16 flows (3 x 256, BF16) train together after every round
+    on batches of 2048 rows each,
     a region falling back to the prior whenever its ESS fraction drops below
     10 %."""
     with open(os.path.join(ROOT, "tests", "golden", "workloads.json")) as f:
@@ -286,7 +287,7 @@ def bench_learned_stream(abc, torch, prior_stream=None):
     t0 = time.perf_counter()
     info, res = abc.abc_smc_run_regions(regs, rounds=rounds, shrink_rounds=shrink, sims_per_round=n, eps_factor=0.7,
                                         flow_blocks=3, flow_hidden=256, train_steps=500, train_steps_warm=100,
-                                        train_batch=4096, train_lr=1e-3, seed=wl[names[0]]["seed"] + 29,
+                                        train_batch=2048, train_lr=1e-3, seed=wl[names[0]]["seed"] + 29,
                                         capacity=1 << 20, mode="fast", proposal_scale=LEARNED_TAU,
                                         train_weight_power=LEARNED_POWER, fallback="ess")
     wall = time.perf_counter() - t0
