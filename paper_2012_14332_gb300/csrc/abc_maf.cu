@@ -218,17 +218,22 @@ constexpr int kFwdMinBlocks = 4;
 // log p(z) = -|z| - 2 log(1 + exp(-|z|)); d(-log p)/dz = tanh(z / 2). The logit
 // of a uniform variable is standard logistic, so the flow with zero
 // parameters is the uniform prior on the box.
+// The flow's transcendentals outside the products use the SFU forms
+// (__expf, __logf, __fdividef): their absolute errors of about 1e-7 are far
+// inside the flow's BF16 accuracy, and the density is always evaluated at
+// the point actually produced, so the proposal stays self-consistent.
 __device__ __forceinline__ float log_base(float z)
 {
     const float a = fabsf(z);
-    return -a - 2.f * log1pf(expf(-a));
+    return -a - 2.f * __logf(1.f + __expf(-a));
 }
 
-// a standard logistic draw from one random word: logit of its uniform in (0, 1)
+// a standard logistic draw from one random word: logit of its uniform u in
+// (0, 1); u = (2m + 1) 2^-24, so 1 - u is exact
 __device__ __forceinline__ float logistic_draw(uint32_t w)
 {
     const float u = uniform01(w);
-    return logf(u) - log1pf(-u);
+    return __logf(u) - __logf(1.f - u);
 }
 
 // One 16-unit hidden chunk of a MADE on the warp's 16 rows: layer 1 (two
@@ -281,7 +286,7 @@ __device__ __forceinline__ void made_fwd(const BlockView& v, int H, const float 
 __device__ __forceinline__ void to_y(const Box& b, int j, float th, float& y, float& jac)
 {
     const float u = fminf(fmaxf((th - b.lo[j]) / b.w[j], 0x1p-24f), 0x1.fffffep-1f);
-    const float lu = logf(u), l1u = log1pf(-u);
+    const float lu = __logf(u), l1u = __logf(1.f - u);
     y = lu - l1u;
     jac = b.logw[j] + lu + l1u;
 }
@@ -289,10 +294,10 @@ __device__ __forceinline__ void to_y(const Box& b, int j, float th, float& y, fl
 // y -> theta = lo + w sigmoid(y) and log(w s (1 - s)).
 __device__ __forceinline__ void to_theta(const Box& b, int j, float y, float& th, float& jac)
 {
-    const float e = expf(-fabsf(y));
-    const float l = log1pf(e);
+    const float e = __expf(-fabsf(y));
+    const float l = __logf(1.f + e);
     const float ls = fminf(y, 0.f) - l, l1s = fminf(-y, 0.f) - l;
-    const float s = y >= 0.f ? 1.f / (1.f + e) : e / (1.f + e);
+    const float s = __fdividef(y >= 0.f ? 1.f : e, 1.f + e);
     th = b.lo[j] + b.w[j] * s;
     jac = b.logw[j] + ls + l1s;
 }
