@@ -7,8 +7,9 @@
 // each 32-sample chunk belongs to one region, and a lane that takes a sample
 // also takes its region's T, eps threshold, stream, 1/P and observed-series
 // offset from the region table staged in shared memory. The observed series
-// are read through the read-only data cache (all regions together can exceed
-// shared memory). Chunks are claimed from one counter across all regions, so
+// are staged in shared memory too when all regions' series fit (OBS_S), and
+// read through the read-only data cache otherwise. Chunks are claimed from
+// one counter across all regions, so
 // uneven regions balance across the whole GPU. Accepted samples go to their
 // region's buffers (one atomicAdd per accept: accepts are rare).
 #include <cstdint>
@@ -52,13 +53,16 @@ struct LaneRegion {
 // BELOW62: every region's acc_max < 2^62, so the running sum can be clamped at
 // 2^62 each day instead of saturating exactly at 2^63 (fewer instructions; the
 // accept sets and accepted distances are the same, as in abc_reject_kernel).
-template <int MODE, int BLOCK, int PAIRS, bool BELOW62>
+template <int MODE, int BLOCK, int PAIRS, bool BELOW62, bool OBS_S>
 __global__ void __launch_bounds__(BLOCK) abc_batch_kernel(const __grid_constant__ ModelParams p,
                                                           const __grid_constant__ BatchArgs a)
 {
     __shared__ RegionDev reg_s[kMaxRegions];
-    extern __shared__ BatchRing rings[];
+    extern __shared__ BatchRing rings[];   // one per warp, then (OBS_S) the observed series
+    int4* obs_s = reinterpret_cast<int4*>(rings + BLOCK / 32);
     for (int r = threadIdx.x; r < a.n_regions; r += BLOCK) reg_s[r] = a.regions[r];
+    if (OBS_S)
+        for (int q = threadIdx.x; q < a.n_obs_smem; q += BLOCK) obs_s[q] = a.obs[q];
     __syncthreads();
     const uint32_t lane = threadIdx.x & 31u;
     BatchRing& ring = rings[threadIdx.x >> 5];
@@ -158,13 +162,14 @@ __global__ void __launch_bounds__(BLOCK) abc_batch_kernel(const __grid_constant_
                 float z[10];
                 day_pair_normals_s<MODE>(p, i, k, lr.ctr3, z);
                 const int32_t d1 = (int32_t)(2 * k - 1);
-                const int4* obs = a.obs + lr.obs_off;
+                const int4* obs = (OBS_S ? obs_s : a.obs) + lr.obs_off;
                 model_day<MODE>(x, t, lr.inv_p, z);
-                acc = BELOW62 ? add_day_sq_below62(acc, x, __ldg(obs + d1)) : add_day_sq(acc, x, __ldg(obs + d1));
+                const int4 o1 = OBS_S ? obs[d1] : __ldg(obs + d1);
+                acc = BELOW62 ? add_day_sq_below62(acc, x, o1) : add_day_sq(acc, x, o1);
                 if (d1 < lr.T) {
                     model_day<MODE>(x, t, lr.inv_p, z + 5);
-                    acc = BELOW62 ? add_day_sq_below62(acc, x, __ldg(obs + d1 + 1))
-                                  : add_day_sq(acc, x, __ldg(obs + d1 + 1));
+                    const int4 o2 = OBS_S ? obs[d1 + 1] : __ldg(obs + d1 + 1);
+                    acc = BELOW62 ? add_day_sq_below62(acc, x, o2) : add_day_sq(acc, x, o2);
                     days += 2;
                 } else {
                     days += 1;
@@ -211,21 +216,32 @@ static const BatchShape kShapes[] = {
 int batch_shape_count() { return (int)(sizeof kShapes / sizeof kShapes[0]); }
 BatchShape batch_shape(int index) { return kShapes[index]; }
 
-template <int MODE, int BLOCK, int PAIRS, bool BELOW62>
-static cudaError_t launch_t(const ModelParams& p, const BatchArgs* a, int blocks_per_sm, cudaStream_t s)
+// With a == NULL only prepares: sets the kernel's dynamic shared-memory limit
+// (the rings, and the observed series with OBS_S) and resolves its occupancy,
+// so that a launch, or a graph capture of one, makes no attribute calls.
+template <int MODE, int BLOCK, int PAIRS, bool BELOW62, bool OBS_S>
+static cudaError_t launch_t(const ModelParams& p, const BatchArgs* a, int32_t n_obs_smem, int blocks_per_sm,
+                            cudaStream_t s)
 {
-    auto kernel = abc_batch_kernel<MODE, BLOCK, PAIRS, BELOW62>;
-    const size_t smem = sizeof(BatchRing) * (BLOCK / 32);
+    auto kernel = abc_batch_kernel<MODE, BLOCK, PAIRS, BELOW62, OBS_S>;
+    const size_t smem = sizeof(BatchRing) * (BLOCK / 32) + (OBS_S ? sizeof(int4) * (size_t)n_obs_smem : 0);
     int dev = 0, sms = 0, fit = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
+    if (!a) {
+        // the limit is the kernel's, shared by every plan: set the largest
+        // this instantiation can need, so no plan lowers another's
+        const size_t most = sizeof(BatchRing) * (BLOCK / 32) + (OBS_S ? sizeof(int4) * (size_t)kBatchObsSmemMax : 0);
+        e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most);
+        if (e != cudaSuccess) return e;
+    }
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, kernel, BLOCK, smem);
     if (e != cudaSuccess) return e;
     if (fit < 1) fit = 1;
     const int per_sm = (blocks_per_sm > 0 && blocks_per_sm < fit) ? blocks_per_sm : fit;
-    if (!a) return cudaSuccess;   // preparation only: attributes and occupancy resolved
+    if (!a) return cudaSuccess;
     uint64_t want = (a->total_chunks + BLOCK / 32 - 1) / (BLOCK / 32);
     int grid = sms * per_sm;
     if (want < (uint64_t)grid) grid = (int)(want > 0 ? want : 1);
@@ -233,36 +249,47 @@ static cudaError_t launch_t(const ModelParams& p, const BatchArgs* a, int blocks
     return cudaGetLastError();
 }
 
-template <int MODE, bool B62>
-static cudaError_t dispatch(const ModelParams& p, const BatchArgs* a, const BatchShape& sh, cudaStream_t s)
+template <int MODE, bool B62, bool OS>
+static cudaError_t dispatch(const ModelParams& p, const BatchArgs* a, int32_t n_obs_smem, const BatchShape& sh,
+                            cudaStream_t s)
 {
-    if (sh.block_threads == 128 && sh.pairs == 1) return launch_t<MODE, 128, 1, B62>(p, a, sh.blocks_per_sm, s);
-    if (sh.block_threads == 256 && sh.pairs == 1) return launch_t<MODE, 256, 1, B62>(p, a, sh.blocks_per_sm, s);
-    if (sh.block_threads == 512 && sh.pairs == 1) return launch_t<MODE, 512, 1, B62>(p, a, sh.blocks_per_sm, s);
-    if (sh.block_threads == 128 && sh.pairs == 2) return launch_t<MODE, 128, 2, B62>(p, a, sh.blocks_per_sm, s);
-    if (sh.block_threads == 256 && sh.pairs == 2) return launch_t<MODE, 256, 2, B62>(p, a, sh.blocks_per_sm, s);
-    if (sh.block_threads == 512 && sh.pairs == 2) return launch_t<MODE, 512, 2, B62>(p, a, sh.blocks_per_sm, s);
+    const int bps = sh.blocks_per_sm;
+    if (sh.block_threads == 128 && sh.pairs == 1) return launch_t<MODE, 128, 1, B62, OS>(p, a, n_obs_smem, bps, s);
+    if (sh.block_threads == 256 && sh.pairs == 1) return launch_t<MODE, 256, 1, B62, OS>(p, a, n_obs_smem, bps, s);
+    if (sh.block_threads == 512 && sh.pairs == 1) return launch_t<MODE, 512, 1, B62, OS>(p, a, n_obs_smem, bps, s);
+    if (sh.block_threads == 128 && sh.pairs == 2) return launch_t<MODE, 128, 2, B62, OS>(p, a, n_obs_smem, bps, s);
+    if (sh.block_threads == 256 && sh.pairs == 2) return launch_t<MODE, 256, 2, B62, OS>(p, a, n_obs_smem, bps, s);
+    if (sh.block_threads == 512 && sh.pairs == 2) return launch_t<MODE, 512, 2, B62, OS>(p, a, n_obs_smem, bps, s);
     return cudaErrorInvalidValue;
 }
 
-template <bool B62>
-static cudaError_t dispatch_mode(const ModelParams& p, const BatchArgs* a, bool fast, const BatchShape& sh,
-                                 cudaStream_t s)
+template <bool B62, bool OS>
+static cudaError_t dispatch_mode(const ModelParams& p, const BatchArgs* a, bool fast, int32_t n_obs_smem,
+                                 const BatchShape& sh, cudaStream_t s)
 {
-    return fast ? dispatch<kFast, B62>(p, a, sh, s) : dispatch<kExact, B62>(p, a, sh, s);
+    return fast ? dispatch<kFast, B62, OS>(p, a, n_obs_smem, sh, s) : dispatch<kExact, B62, OS>(p, a, n_obs_smem, sh, s);
+}
+
+static cudaError_t dispatch_all(const ModelParams& p, const BatchArgs* a, bool fast, bool below62, int32_t n_obs_smem,
+                                const BatchShape& sh, cudaStream_t s)
+{
+    if (n_obs_smem < 0 || n_obs_smem > kBatchObsSmemMax) return cudaErrorInvalidValue;
+    if (n_obs_smem > 0)
+        return below62 ? dispatch_mode<true, true>(p, a, fast, n_obs_smem, sh, s)
+                       : dispatch_mode<false, true>(p, a, fast, n_obs_smem, sh, s);
+    return below62 ? dispatch_mode<true, false>(p, a, fast, 0, sh, s) : dispatch_mode<false, false>(p, a, fast, 0, sh, s);
 }
 
 cudaError_t launch_batch(const ModelParams& p, const BatchArgs& a, bool fast, bool below62, const BatchShape& shape,
                          cudaStream_t s)
 {
-    return below62 ? dispatch_mode<true>(p, &a, fast, shape, s) : dispatch_mode<false>(p, &a, fast, shape, s);
+    return dispatch_all(p, &a, fast, below62, a.n_obs_smem, shape, s);
 }
 
-cudaError_t prepare_batch(bool fast, bool below62, const BatchShape& shape)
+cudaError_t prepare_batch(bool fast, bool below62, int32_t n_obs_smem, const BatchShape& shape)
 {
     ModelParams p{};
-    return below62 ? dispatch_mode<true>(p, nullptr, fast, shape, nullptr)
-                   : dispatch_mode<false>(p, nullptr, fast, shape, nullptr);
+    return dispatch_all(p, nullptr, fast, below62, n_obs_smem, shape, nullptr);
 }
 
 cudaError_t launch_advance(RegionDev* regions, int32_t n_regions, cudaStream_t s)

@@ -72,8 +72,14 @@ struct BatchArgs {
     int32_t n_regions;
     uint64_t total_chunks;
     const int4* obs;               // device, concatenated (A, R, D, 0) per day of every region
+    int32_t n_obs_smem;            // > 0: all n_obs_smem entries of obs are staged in shared memory
     unsigned long long* next;      // claimed chunks, zeroed before each run
 };
+
+// The batched kernel stages every region's observed series in shared memory
+// when together they hold at most this many days (32 KB), and reads them
+// through the read-only data cache otherwise.
+constexpr int32_t kBatchObsSmemMax = 2048;
 
 // Launch shapes the batched kernel is compiled for (the autotuner's space).
 struct BatchShape {
@@ -88,7 +94,7 @@ BatchShape batch_shape(int index);
 cudaError_t launch_batch(const ModelParams& p, const BatchArgs& a, bool fast, bool below62, const BatchShape& shape,
                          cudaStream_t s);
 cudaError_t launch_advance(RegionDev* regions, int32_t n_regions, cudaStream_t s);
-cudaError_t prepare_batch(bool fast, bool below62, const BatchShape& shape);
+cudaError_t prepare_batch(bool fast, bool below62, int32_t n_obs_smem, const BatchShape& shape);
 
 size_t reject_smem_bytes(int32_t T);
 // mode: kExact or kFast, optionally | kLiteral (see abc_model.cuh)

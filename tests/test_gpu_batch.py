@@ -178,6 +178,36 @@ def test_chunks_of_skipped_proposals_do_not_end_the_run():
     plan.close()
 
 
+@pytest.mark.parametrize("mode", ["exact", "fast"])
+def test_long_series_read_through_the_cache_equal_abc_sample(mode):
+    """Regions whose observed series together exceed what the kernel stages in
+    shared memory (2048 days) are read through the read-only cache; each
+    region's accept set still equals abc_sample's. The series are the
+    oracle's trajectories of seeded draws over 1100 days."""
+    regs = []
+    for r, (P, seed) in enumerate([(10 ** 6, 31), (5 * 10 ** 6, 32)]):
+        T = 1100
+        th = inputs.random_thetas(seed, 1)[0]
+        traj = oracle.simulate(th, [100, 0, 0], T, P, seed, 1, 0)
+        obs = np.ascontiguousarray(traj[:, 2:5].T).astype(np.int32)
+        regs.append(dict(observed=obs, N_pop=P, eps=0.0, n_samples=3000, first_index=17, stream=20 + r,
+                         capacity=3000))
+    for g in regs:
+        d = abc.abc_distances(g["observed"], g["N_pop"], g["n_samples"], SEED, stream=g["stream"], mode=mode,
+                              first_index=g["first_index"]).cpu().numpy()
+        g["eps"] = float(np.sort(d)[60])
+    plan = abc.Plan(regs, SEED, mode=mode)
+    plan.run()
+    for r, g in enumerate(regs):
+        ref = abc.abc_sample(g["observed"], g["N_pop"], g["eps"], g["n_samples"], SEED, stream=g["stream"], mode=mode,
+                             first_index=g["first_index"], capacity=3000)
+        res = plan.results(r)
+        assert res[3] == ref[3] >= 61
+        for x, y in zip(_sorted(*res[:3]), _sorted(*ref[:3])):
+            assert np.array_equal(x, y)
+    plan.close()
+
+
 def test_graph_follows_an_eps_change_across_2_to_the_62():
     """The batched kernel has a cheaper distance accumulation for thresholds
     below 2^62; a graph captured with it is recaptured when set_eps moves a
