@@ -615,6 +615,38 @@ __device__ __forceinline__ void ldsm_x2_trans(uint32_t& r0, uint32_t& r1, const 
     asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0,%1}, [%2];\n" : "=r"(r0), "=r"(r1) : "r"(a));
 }
 
+// Adds a CTA's gradient sums (layout of grad_block) and its loss and weight
+// sums into the flow's global gradient, in the parameter order W1 [H][8],
+// b1 [H], W2 [16][H], b2 [16] per block. Called by every thread after a
+// barrier.
+__device__ __forceinline__ void flush_grad(const float* gsm, float* grad, float* sums, const float* ssum, int K, int H)
+{
+    const int mb = master_block(H), gb = grad_block(H);
+    for (int b = 0; b < K; ++b) {
+        const float* G = gsm + b * gb;
+        float* out = grad + b * mb;
+        for (int i = threadIdx.x; i < 8 * H; i += blockDim.x) {
+            const float v = G[(i >> 3) * kGW1Stride + (i & 7)];
+            if (v != 0.f) atomicAdd(&out[i], v);
+        }
+        for (int i = threadIdx.x; i < H; i += blockDim.x) {
+            const float v = G[kGW1Stride * H + i];
+            if (v != 0.f) atomicAdd(&out[8 * H + i], v);
+        }
+        const float* G2 = G + (kGW1Stride + 1) * H;
+        for (int o = 0; o < 16; ++o)
+            for (int l = threadIdx.x; l < H; l += blockDim.x) {
+                const float v = G2[o * (H + 4) + l];
+                if (v != 0.f) atomicAdd(&out[9 * H + o * H + l], v);
+            }
+        if (threadIdx.x < 16) {
+            const float v = G2[16 * (H + 4) + threadIdx.x];
+            if (v != 0.f) atomicAdd(&out[25 * H + threadIdx.x], v);
+        }
+    }
+    if (threadIdx.x < 2) atomicAdd(&sums[threadIdx.x], ssum[threadIdx.x]);
+}
+
 // Training data of one flow: points theta [n][8], weights [n] (NULL = 1).
 struct TrainSlot {
     const float* theta;
@@ -856,30 +888,7 @@ __global__ void __launch_bounds__(W * 32) grad_kernel(const uint32_t* __restrict
         }
     }
     __syncthreads();
-    // flush in the parameter order: W1 [H][8], b1 [H], W2 [16][H], b2 [16]
-    for (int b = 0; b < K; ++b) {
-        const float* G = gsm + b * gb;
-        float* out = grad + b * mb;
-        for (int i = threadIdx.x; i < 8 * H; i += blockDim.x) {
-            const float v = G[(i >> 3) * kGW1Stride + (i & 7)];
-            if (v != 0.f) atomicAdd(&out[i], v);
-        }
-        for (int i = threadIdx.x; i < H; i += blockDim.x) {
-            const float v = G[kGW1Stride * H + i];
-            if (v != 0.f) atomicAdd(&out[8 * H + i], v);
-        }
-        const float* G2 = G + (kGW1Stride + 1) * H;
-        for (int o = 0; o < 16; ++o)
-            for (int l = threadIdx.x; l < H; l += blockDim.x) {
-                const float v = G2[o * (H + 4) + l];
-                if (v != 0.f) atomicAdd(&out[9 * H + o * H + l], v);
-            }
-        if (threadIdx.x < 16) {
-            const float v = G2[16 * (H + 4) + threadIdx.x];
-            if (v != 0.f) atomicAdd(&out[25 * H + threadIdx.x], v);
-        }
-    }
-    if (threadIdx.x < 2) atomicAdd(&sums[threadIdx.x], ssum[threadIdx.x]);
+    flush_grad(gsm, grad, sums, ssum, K, H);
 }
 
 // batch rows for one training step: uniform indices with replacement

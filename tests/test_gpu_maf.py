@@ -132,6 +132,40 @@ def test_gradient_matches_oracle():
     f.close()
 
 
+@pytest.mark.parametrize("n", [2055, 2069])
+def test_wide_gradient_form_matches_the_narrow_one_and_the_oracle(n):
+    """A set of 16 flows takes the wide (16-warp) gradient kernel, chosen when
+    4-warp CTAs would run more than two waves; flow 0's gradient there equals
+    a one-flow object's (the 4-warp kernel) up to float summation order, and
+    the oracle's. Both point counts end in a partial tile."""
+    K, H, R = 3, 256, 16
+    f1, params = _flow(K, H, 71, 0.5)
+    fs = abc.Flow(K, H, n_flows=R)
+    fs.set_params(np.stack([f1.get_params()] * R))
+    th = _thetas(n, 5)
+    w = np.random.default_rng(6).uniform(0.2, 2.0, size=n).astype(np.float32)
+    thd, wd = torch.from_numpy(th).to(DEV), torch.from_numpy(w).to(DEV)
+    loss_w, g_w = fs.gradient(thd, wd)
+    loss_n, g_n = f1.gradient(thd, wd)
+    rel = np.linalg.norm(g_w - g_n) / np.linalg.norm(g_n)
+    print("wide vs narrow gradient (n=%d): loss %.7f vs %.7f, relative difference %.2e" % (n, loss_w, loss_n, rel))
+    assert abs(loss_w - loss_n) < 1e-5 * abs(loss_n) and rel < 1e-4
+    y = mo.to_y(th.astype(np.float64), LO, HI)
+    bfp = [dict(W1=mo.round_bf16(p["W1"] * mo.masks(H)[0]), b1=p["b1"],
+                W2=mo.round_bf16(p["W2"] * mo.masks(H)[1]), b2=p["b2"]) for p in params]
+    loss_ref, grads = mo.loss_and_grad(y, w.astype(np.float64), bfp)
+    gref = mo.flat(grads)
+    rel_o = np.linalg.norm(g_w - gref) / np.linalg.norm(gref)
+    cos = g_w @ gref / (np.linalg.norm(g_w) * np.linalg.norm(gref))
+    assert abs(loss_w - loss_ref) < 2e-3 * abs(loss_ref) + 1e-3
+    assert rel_o < 3e-2 and cos > 0.9995
+    M1, M2 = mo.masks(H)
+    zero = mo.flat([dict(W1=1 - M1, b1=np.zeros(H), W2=1 - M2, b2=np.zeros(16))] * K) > 0
+    assert np.all(g_w[zero] == 0)
+    f1.close()
+    fs.close()
+
+
 def test_adam_step_matches_oracle():
     K, H = 2, 32
     f, params = _flow(K, H, 41, 0.5)
