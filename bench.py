@@ -257,6 +257,94 @@ def bench_exact(abc, torch, w, dev, flush, fast_days_per_s, steps=5, warmup=3, n
             "exact_over_fast": dps / fast_days_per_s}
 
 
+def bench_projection(abc, torch, w, B=8192, T=120, reps=10):
+    """Posterior-predictive projection (Sec. 5: accepted samples simulated 120
+    days forward, 5th-95th percentile bands): B accepted samples of the
+    headline workload re-simulated from its initial condition for T days,
+    with bands at the 5, 50 and 95 % quantiles of every (day, compartment)."""
+    th, _, idx, n = abc.abc_sample(w["observed"], w["P"], w["eps"], 6 << 24, w["seed"], first_index=1 << 36,
+                                   capacity=1 << 15)
+    m = min(B, th.shape[0])
+    th, idx = th[:m].contiguous(), idx[:m].contiguous()
+    s = torch.cuda.Stream()
+
+    def timed(fn):
+        with torch.cuda.stream(s):
+            for _ in range(3):
+                fn()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            for _ in range(reps):
+                fn()
+            e1.record(s)
+        s.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    ms = timed(lambda: abc.abc_project(th, idx, w["observed"][:, 0], T, w["P"], w["seed"], cuda_stream=s))
+    ms_sim = timed(lambda: abc.abc_simulate(th, idx, w["observed"][:, 0], T, w["P"], w["seed"], mode="fast",
+                                            cuda_stream=s))
+    # one thread per trajectory: 8192 trajectories are 1.7 warps per SM, so the
+    # call is latency-bound by its size (Sec. 5 projects 100 samples)
+    return {"workload": "%d accepted samples of region_6e7_T100 simulated %d days from its initial condition, "
+                        "bands at the 5, 50, 95 %% quantiles, fast mode" % (m, T),
+            "ms_per_projection": ms, "ms_trajectories": ms_sim, "ms_bands": ms - ms_sim,
+            "trajectories_per_s": m / (ms * 1e-3), "simulated_days_per_s": m * T / (ms * 1e-3)}
+
+
+def bench_pmc(abc, torch, w, prior_value, rounds=4, factor=0.7):
+    """Population Monte Carlo ABC (Beaumont et al. 2009, the SMC-ABC of
+    Sec. 2.2) on the headline region, 4 rounds of 4096 particles ending at the
+    headline eps, proposals in batches of 2^22."""
+    eps0 = w["eps"] / factor ** (rounds - 1)
+    info, th, wt, dist = abc.abc_pmc_run(w["observed"], w["P"], eps0, rounds=rounds, n_particles=4096,
+                                         batch=1 << 22, max_batches=64, eps_factor=factor, seed=w["seed"] + 5,
+                                         capacity=1 << 17, mode="fast")
+    last = info[-1]
+    ms = last["ms"]
+    eff = ess(wt.cpu().numpy())
+    return {"workload": "population Monte Carlo ABC, region_6e7_T100, %d rounds of 4096 particles, eps0=%g, "
+                        "factor %g, final eps=%g (the headline eps), batches of 2^22" % (rounds, eps0, factor, w["eps"]),
+            "final_round_accepted_per_s": last["n_accepted"] / (ms * 1e-3),
+            "final_round_effective_accepted_per_s": eff / (ms * 1e-3),
+            "final_round_simulations": last["n_sims"], "final_round_ess_fraction": last["ess_fraction"],
+            "prior_accepted_per_s_same_eps": prior_value,
+            "gain_effective_vs_prior": eff / (ms * 1e-3) / prior_value,
+            "all_rounds_seconds": sum(r["ms"] for r in info) * 1e-3}
+
+
+def bench_literal(abc, torch, w, dev, flush, fast_days_per_s, steps=5, warmup=3, n=1 << 24):
+    """The literal-variance model variant (transition draws with standard
+    deviation h^(1/4)) on the headline workload and eps, fast mode."""
+    obs_dev = abc.Observed(w["observed"], w["P"])
+    cap = 1 << 20
+    outs = (torch.empty((cap, 8), dtype=torch.float32, device=dev), torch.empty((cap,), dtype=torch.float64, device=dev),
+            torch.empty((cap,), dtype=torch.int64, device=dev))
+    cnt = torch.zeros((warmup + steps, 4), dtype=torch.int64, device=dev)
+    s = torch.cuda.current_stream(dev)
+    first = 1 << 41
+    for k in range(warmup):
+        abc.abc_sample_async(obs_dev, w["eps"], n, w["seed"], outs, cnt[k], mode="fast_literal",
+                             first_index=first + k * n, cuda_stream=s)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for k in range(steps):
+        flush.fill_(k & 0xFF)
+        ev[k][0].record(s)
+        abc.abc_sample_async(obs_dev, w["eps"], n, w["seed"], outs, cnt[warmup + k], mode="fast_literal",
+                             first_index=first + (warmup + k) * n, cuda_stream=s)
+        ev[k][1].record(s)
+    torch.cuda.synchronize()
+    obs_dev.close()
+    ms = float(sum(a.elapsed_time(b) for a, b in ev))
+    c = cnt[warmup:].cpu().numpy()
+    acc, days = int(c[:, 0].sum()), int(c[:, 2].sum())
+    return {"workload": "region_6e7_T100, literal-variance model, %d prior samples per launch, %d launches, eps=%g"
+                        % (n, steps, w["eps"]),
+            "accepted_per_s": acc / (ms * 1e-3), "unit": UNIT, "ms_per_launch": ms / steps,
+            "simulated_days_per_s": days / (ms * 1e-3), "standard_model_simulated_days_per_s": fast_days_per_s,
+            "acceptance": acc / (steps * n)}
+
+
 def ess(w):
     w = np.asarray(w, dtype=np.float64)
     return float(w.sum() ** 2 / (w ** 2).sum()) if len(w) else 0.0
@@ -446,8 +534,9 @@ def main():
     ap.add_argument("--no-streamed", action="store_true")
     ap.add_argument("--no-learned-stream", action="store_true")
     ap.add_argument("--no-exact", action="store_true")
+    ap.add_argument("--no-next", action="store_true", help="skip the projection, PMC and literal-model legs")
     ap.add_argument("--leg", default="all", choices=["all", "headline", "batched", "learned", "streamed",
-                                                     "learned_stream", "exact"],
+                                                     "learned_stream", "exact", "projection", "pmc", "literal"],
                     help="run one leg only (profiling); 'all' is the benchmark")
     ap.add_argument("--samples", type=int, default=0,
                     help="samples per launch (profiling runs on a smaller case; not a benchmark value)")
@@ -497,7 +586,7 @@ def main():
         abc.abc_sample_async(obs_dev, eps, n, seed, outs, counters[s], mode=w["mode"], first_index=first_index(s),
                              cuda_stream=stream)
 
-    if args.leg in ("batched", "learned", "streamed", "learned_stream", "exact"):
+    if args.leg in ("batched", "learned", "streamed", "learned_stream", "exact", "projection", "pmc", "literal"):
         props = torch.cuda.get_device_properties(dev)
         peaks = measured_peaks() or {}
         if args.leg == "batched":
@@ -509,6 +598,12 @@ def main():
             out = bench_learned_stream(abc, torch)
         elif args.leg == "exact":
             out = bench_exact(abc, torch, w, dev, flush, float("nan"))
+        elif args.leg == "projection":
+            out = bench_projection(abc, torch, w)
+        elif args.leg == "pmc":
+            out = bench_pmc(abc, torch, w, float("nan"))
+        elif args.leg == "literal":
+            out = bench_literal(abc, torch, w, dev, flush, float("nan"))
         else:
             out = bench_learned(abc, torch, w, float("nan"), peaks, props.multi_processor_count,
                                 peaks.get("sm_max_mhz", 2070.0))
@@ -620,6 +715,7 @@ def main():
             line["cpu_baseline"] = cpu_baseline(w)
         if args.leg == "headline":
             args.no_learned = args.no_batched = args.no_streamed = args.no_learned_stream = args.no_exact = True
+            args.no_next = True
         if not args.no_exact and world == 1:
             line["exact_mode"] = bench_exact(abc, torch, w, dev, flush, sim_days[0] / (float(np.sum(launch_ms)) * 1e-3))
         if not args.no_learned and world == 1:
@@ -631,6 +727,11 @@ def main():
             line["streamed_regions"] = bench_streamed(abc, torch, dev, flush, props.multi_processor_count, sm_max)
         if not args.no_learned_stream and world == 1:
             line["learned_stream"] = bench_learned_stream(abc, torch, line.get("streamed_regions"))
+        if not args.no_next and world == 1:
+            fast_dps = sim_days[0] / (float(np.sum(launch_ms)) * 1e-3)
+            line["projection"] = bench_projection(abc, torch, w)
+            line["pmc"] = bench_pmc(abc, torch, w, value)
+            line["literal_model"] = bench_literal(abc, torch, w, dev, flush, fast_dps)
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.barrier()

@@ -259,7 +259,9 @@ __global__ void __launch_bounds__(kBlockThreads) abc_step_kernel(const __grid_co
 // the B values sorted in shared memory by a bitonic network (padded to a power
 // of two with INT_MAX), then order statistics floor(q (B - 1)).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kBlockThreads) band_kernel(const int32_t* __restrict__ traj, uint32_t B, int32_t T,
+constexpr int kBandThreads = 1024;
+
+__global__ void __launch_bounds__(kBandThreads) band_kernel(const int32_t* __restrict__ traj, uint32_t B, int32_t T,
                                                              const float* __restrict__ qpos, int32_t n_q,
                                                              float* __restrict__ bands)
 {
@@ -270,17 +272,17 @@ __global__ void __launch_bounds__(kBlockThreads) band_kernel(const int32_t* __re
     for (uint32_t b = threadIdx.x; b < n2; b += blockDim.x)
         v[b] = b < B ? traj[((size_t)b * (T + 1) + d) * 6 + 2 + c] : 0x7FFFFFFF;
     __syncthreads();
+    // bitonic sort; each stage visits its n2 / 2 compare-exchange pairs
+    // (i, i + j), i with bit j clear, rather than all n2 positions
     for (uint32_t k = 2; k <= n2; k <<= 1) {
         for (uint32_t j = k >> 1; j > 0; j >>= 1) {
-            for (uint32_t i = threadIdx.x; i < n2; i += blockDim.x) {
-                const uint32_t p = i ^ j;
-                if (p > i) {
-                    const bool up = (i & k) == 0;
-                    const int32_t a = v[i], b2 = v[p];
-                    if ((a > b2) == up) {
-                        v[i] = b2;
-                        v[p] = a;
-                    }
+            for (uint32_t q = threadIdx.x; q < n2 / 2; q += blockDim.x) {
+                const uint32_t i = ((q & ~(j - 1)) << 1) | (q & (j - 1)), p = i | j;
+                const bool up = (i & k) == 0;
+                const int32_t a = v[i], b2 = v[p];
+                if ((a > b2) == up) {
+                    v[i] = b2;
+                    v[p] = a;
                 }
             }
             __syncthreads();
@@ -454,7 +456,7 @@ cudaError_t launch_bands(const int32_t* traj, uint32_t B, int32_t T, const float
         cudaError_t e = cudaFuncSetAttribute(band_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    band_kernel<<<3 * (T + 1), kBlockThreads, smem, s>>>(traj, B, T, qpos, n_q, bands);
+    band_kernel<<<3 * (T + 1), kBandThreads, smem, s>>>(traj, B, T, qpos, n_q, bands);
     return cudaGetLastError();
 }
 
