@@ -283,11 +283,14 @@ abc_status abc_plan_copy_results(abc_plan plan, int32_t region, float* theta_dst
                                  uint64_t* idx_dst, uint64_t count, uint64_t* copied, void* cuda_stream);
 
 /* Point a region at a new proposal buffer (DEVICE [n_samples][8]) or NULL for
- * prior draws, and/or set its next first_index. Synchronous (cudaMemcpy). */
+ * prior draws, and/or set its next first_index. Synchronous (cudaMemcpy of the
+ * region table, which is not ordered with the plan's stream): no run of the
+ * plan may be in flight, so synchronize its stream first. */
 abc_status abc_plan_set_region(abc_plan plan, int32_t region, const float* theta_in, uint64_t first_index);
 
 /* Set a region's tolerance for the following runs (eps >= 0, not NaN).
- * Synchronous (cudaMemcpy of the one table field). */
+ * Synchronous (cudaMemcpy of the one table field); as for
+ * abc_plan_set_region, no run of the plan may be in flight. */
 abc_status abc_plan_set_eps(abc_plan plan, int32_t region, double eps);
 
 /* Release the plan's device memory and graph. */
