@@ -120,6 +120,36 @@ def test_plan_with_proposal_buffer():
     plan.close()
 
 
+def test_several_regions_with_proposal_buffers_match_oracle():
+    """Three regions, each with its own proposal buffer, in one plan (their
+    series staged in shared memory): each region's accept set equals the
+    oracle's over its proposals, bit for bit in exact mode."""
+    names = ["region_1e6_T49", "region_1e7_T60", "region_6e7_T90"]
+    regs, want = [], []
+    for r, name in enumerate(names):
+        w = inputs.workload(name)
+        n, first, stream = 1500 + 37 * r, 1000 * r + 5, 30 + r
+        th = inputs.random_thetas(40 + r, n)
+        th[:, 2] *= 0.5                                 # proposals away from the prior
+        d = np.array([oracle.distance_from_sq(oracle.sq_distance(
+            oracle.simulate(th[j], w["observed"][:, 0], w["T"], w["P"], SEED, stream, first + j), w["observed"]))
+            for j in range(n)])
+        eps = float(np.sort(d)[40 + 10 * r])
+        regs.append(dict(observed=w["observed"], N_pop=w["P"], eps=eps, n_samples=n, first_index=first,
+                         stream=stream, capacity=n, theta_in=torch.from_numpy(th).to(DEV)))
+        want.append((th, d, eps, first))
+    plan = abc.Plan(regs, SEED, mode="exact")
+    plan.run()
+    for r, (th, d, eps, first) in enumerate(want):
+        tt, di, ix, n_acc, _ = plan.results(r)
+        tt, di, ix = _sorted(tt, di, ix)
+        keep = np.nonzero(d <= eps)[0]
+        assert n_acc == len(keep), r
+        assert np.array_equal(ix, keep.astype(np.uint64) + first) and np.array_equal(di, d[keep])
+        assert np.array_equal(tt, th[keep])
+    plan.close()
+
+
 def test_tune_keeps_state_and_picks_a_shape():
     n = 1 << 18
     regs = _regions([n, n, n], [0, 0, 0])
