@@ -464,6 +464,9 @@ def bench_learned(abc, torch, w, prior_value, peaks, sm_count, sm_max, reps=5):
         achieved = flops / (ms_prop * 1e-3) / 1e12
         out["sampler_roofline"] = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                                    "frac": achieved / peak, "traffic": None,
+                                   "limit": "instruction issue (71 % of issue slots active, tensor pipe 30 %, in "
+                                            "the ncu capture of this kernel): the sequential inverse leaves 16 x 8 x 16 "
+                                            "products between dependent passes",
                                    "dense_equivalent_tflops": dense / (ms_prop * 1e-3) / 1e12,
                                    "basis": "%d FLOP per flow proposal (3 blocks x the masked MADE's %d nonzero "
                                             "multiply-adds, H = 256), %d flow proposals per round (the other 10 %% "
