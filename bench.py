@@ -116,7 +116,7 @@ def measured_peaks():
 
 # dram__bytes_read.sum + dram__bytes_write.sum of one headline launch after an
 # L2 flush, from ncu (profiles/abc_reject_kernel_traffic_region_6e7_T100.md)
-REJECT_TRAFFIC_BYTES = 243968
+REJECT_TRAFFIC_BYTES = 167168
 
 
 def roofline(sim_days_per_launch, launch_ms, sm_count, sm_max_mhz, traffic=None):
