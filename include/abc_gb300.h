@@ -329,11 +329,11 @@ typedef struct abc_maf_s* abc_maf;
 /* Create a flow with n_blocks (1..4) blocks of `hidden` units (a multiple of
  * 16, 16..256) on the prior box, parameters zero (q = the uniform prior).
  * Allocates its device memory on the current device. The training kernel
- * stages a CTA's operands and gradients in shared memory, about
- * n_blocks (232 hidden + 512) + 10240 bytes (published BF16 operands and FP32
- * gradient sums per block, staging of four warps): a shape beyond the
+ * stages a CTA's operands in shared memory, n_blocks (116 hidden + 192) +
+ * 40960 bytes (published BF16 operands per block, tensor-core operand slots
+ * of four warps), and its gradient sums in tensor memory: a shape beyond the
  * device's per-block limit returns ABC_ERR_INVALID_ARG (on GB300, 227 KB:
- * n_blocks = 4 allows hidden <= 224). */
+ * every shape up to 4 blocks of 256 fits). */
 abc_status abc_maf_create(int32_t n_blocks, int32_t hidden, const abc_prior_box* box, abc_maf* maf_out);
 
 /* A set of n_flows (1..ABC_MAF_MAX_FLOWS) independent flows of the same shape
@@ -394,7 +394,9 @@ abc_status abc_maf_log_q_at(abc_maf maf, int32_t flow, uint64_t n, const float* 
  * DEVICE [n][8], weights DEVICE [n] >= 0 or NULL for all ones) into the flow's
  * gradient buffer; *loss_out (HOST, may be NULL) gets the loss. Synchronizes
  * cuda_stream. grads_out (HOST, may be NULL) receives the gradient in the
- * parameter order. */
+ * parameter order. The gradient kernel's waits between its warps and the
+ * thread that issues its tensor-core products are bounded (2 s each);
+ * ABC_ERR_TIMEOUT reports one that ran out, here and in the training calls. */
 abc_status abc_maf_gradient(abc_maf maf, uint64_t n, const float* theta, const float* weights, float* loss_out,
                             float* grads_out, void* cuda_stream);
 

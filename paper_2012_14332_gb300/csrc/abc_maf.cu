@@ -1,7 +1,8 @@
 // abc_maf.cu -- masked autoregressive flow proposal for sequential ABC:
 // density, sampling (sequential inverse), weighted maximum-likelihood
 // gradient and Adam, with BF16 tensor-core products (mma.sync m16n8k8 and
-// m16n8k16, FP32 accumulation).
+// m16n8k16 per warp tile; tcgen05.mma with TMEM accumulators for the weight
+// gradients; FP32 accumulation).
 //
 // A warp owns 16 rows (samples). A row's eight coordinates sit in the
 // accumulator layout of an m16n8 tile: lane (g = lane / 4, t = lane % 4) holds
@@ -13,8 +14,8 @@
 //            never leaves registers (16 units at a time).
 // The order reversal between blocks (column j <-> 7 - j) is a shuffle with
 // lane ^ 3; row sums are shuffles over the 4 lanes of a row.
-// Weight gradients reduce over rows, so their products take operands staged
-// transposed in shared memory and accumulate in shared memory per CTA.
+// Weight gradients reduce over rows: their products take the warps' operands
+// from shared memory on tcgen05 and accumulate in tensor memory per CTA.
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -46,14 +47,6 @@ constexpr uint32_t kFull = 0xFFFFFFFFu;
 
 // Master (FP32) parameters of one block: W1 [H][8], b1 [H], W2 [16][H], b2 [16].
 __host__ __device__ inline int master_block(int H) { return 25 * H + 16; }
-
-// The gradient kernel's per-CTA accumulator of one block, in shared memory:
-// W1 [H][12], b1 [H], W2 [16][H + 4], b2 [16]. The padded row strides, with
-// odd row-groups writing their column pair in the opposite order, give the
-// warp's atomic adds 32 distinct banks (unpadded: W2 rows H apart share a
-// bank, 8-way conflicts).
-constexpr int kGW1Stride = 12;
-__host__ __device__ inline int grad_block(int H) { return 29 * H + 80; }
 
 // Published BF16 layout of one block, in 32-bit words (two bf16 per word).
 // The forward operands come first, so density and sampling kernels stage only
@@ -579,72 +572,140 @@ __global__ void __launch_bounds__(kFwdThreads, kFwdMinBlocks) sample_kernel(cons
 // ---------------------------------------------------------------------------
 // gradient of sum_r w_r (-log q_y(y_r)) (unnormalised; Adam divides by sum w)
 // ---------------------------------------------------------------------------
-// warps per CTA of the gradient kernel: 4, or 16 when a step has enough
-// tiles for more than two waves of 4-warp CTAs (one CTA fits per SM, so the
-// wider CTA hides four times the latency and flushes a quarter as many
-// per-CTA gradient sums)
+// The forward pass and the backward products of each row (g_h = g_out W2,
+// g_x = g_a1 W1) run in the warp's registers on mma.sync, as in the density
+// kernel. The weight gradients reduce over rows:
+//   dW2^T [l][o]       = sum over rows of h[row][l] g_out[row][o]
+//   [dW1 | db1] [l][j] = sum over rows of g_a1[row][l] [x | 1][row][j]
+// (j < 8: dW1, j = 8: db1). Per warp tile both are products of M = 128 hidden
+// units x N = 16 x K = 16 rows. They run on the tensor cores (tcgen05.mma,
+// BF16 operands from shared memory, FP32 accumulators in tensor memory) and
+// accumulate over every tile the CTA processes: TMEM lane = hidden unit within
+// a 128-unit half, 16 columns per product and (block, half). The CTA adds its
+// sums to the flow's gradient once, at the end.
+//
+// Warps 0..W-1 compute; one lane of warp W issues the products. A compute
+// warp's job is one (block, half) of one tile: it stores h and g_a1 of 128
+// hidden units (eight 16-unit chunks) into its A slot, having stored g_out and
+// x into one of its two B slots at the start of the block, and arrives on
+// full[w]. The issuing thread polls the full barriers, issues the job's two
+// products and commits them to empty[w]. A warp waits on empty[w] before it
+// overwrites its A slot with the next job. A commit tracks every product the
+// thread issued before it, so that wait also frees the B slot the warp
+// rewrites two blocks later. All products come from one thread in issue
+// order, so accumulations into the same TMEM columns never race.
+//
+// Operands in shared memory are MN-major (hidden unit, output or input
+// contiguous), without swizzle: a core matrix is 8 rows of k (tile rows) x 16
+// bytes (8 bf16 along m or n); core matrices 128 bytes apart along K (the
+// descriptor's leading byte offset) and 256 bytes apart along M or N (stride
+// byte offset). Lane (g, t) of the accumulator layout holds columns 2t, 2t+1
+// of rows g and g + 8: one 32-bit word at byte 16 g + 4 t of a core matrix,
+// so a warp's 32 stores meet 32 distinct banks.
+//
+// Every wait is bounded in time (kTcWaitNs). A wait that runs out sets the
+// flow's error word; the kernel still runs to its end and frees its TMEM.
+
+// compute warps per CTA: 4, or 12 when a step has enough tiles for more than
+// two waves of 4-warp CTAs (one CTA fits per SM)
 constexpr int kGradWarpsNarrow = 4;
-constexpr int kGradWarpsWide = 16;
-// Per-warp staging for the row-reducing weight-gradient products, row-major
-// [tile row][column] bf16 pairs as the accumulator layout produces them; the
-// transposed operands come back with ldmatrix .trans. Rows of 16 columns are
-// padded to 48 bytes (12 words) so that neither the stores (lane g, t writes
-// word 12 g + t) nor the 8-row ldmatrix reads meet a bank conflict; rows of
-// 8 columns are 16 bytes.
-constexpr int kStage = 12;
+constexpr int kGradWarpsWide = 12;
+constexpr int kTcM = 128;                          // hidden units per product
+constexpr int kTcHalf = 4096;                      // one A operand: 128 units x 16 rows, bf16
+constexpr int kTcB = 1024;                         // one B slot: g_out (512 B), [x | 1] (512 B)
+constexpr int kTcSlot = 2 * kTcHalf + 2 * kTcB;    // shared memory per compute warp
+constexpr uint32_t kTcLBO = 128, kTcSBO = 256;
+// instruction descriptor of kind::f16: FP32 accumulator (bits 4-5), BF16 A
+// and B (bits 7-9, 10-12), both MN-major (bits 15, 16), N >> 3 (bits 17-22),
+// M >> 4 (bits 24-28)
+constexpr uint32_t kTcIdesc = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) | ((16u >> 3) << 17) |
+                              ((uint32_t)(kTcM >> 4) << 24);
+constexpr unsigned long long kTcWaitNs = 2000000000ull;
 
-struct WarpStage {
-    uint32_t gout[16 * kStage];    // g_out [row][o], o = 0..15
-    uint32_t h[16 * kStage];       // h [row][l], the chunk's 16 hidden units
-    uint32_t ga[16 * kStage];      // g_a1 [row][l]
-    uint32_t x[16 * 4];            // x [row][j], j = 0..7
-};
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-// four 8x8 bf16 matrices, transposed, one row address per lane (lanes 8m..8m+7: matrix m)
-__device__ __forceinline__ void ldsm_x4_trans(uint32_t (&r)[4], const uint32_t* row)
+__device__ __forceinline__ void st_u32(unsigned char* p, uint32_t v) { *reinterpret_cast<uint32_t*>(p) = v; }
+
+__device__ __forceinline__ unsigned long long global_ns()
 {
-    const uint32_t a = (uint32_t)__cvta_generic_to_shared(row);
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-                 : "r"(a));
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
 }
 
-__device__ __forceinline__ void ldsm_x2_trans(uint32_t& r0, uint32_t& r1, const uint32_t* row)
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
 {
-    const uint32_t a = (uint32_t)__cvta_generic_to_shared(row);
-    asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0,%1}, [%2];\n" : "=r"(r0), "=r"(r1) : "r"(a));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
 }
 
-// Adds a CTA's gradient sums (layout of grad_block) and its loss and weight
-// sums into the flow's global gradient, in the parameter order W1 [H][8],
-// b1 [H], W2 [16][H], b2 [16] per block. Called by every thread after a
-// barrier.
-__device__ __forceinline__ void flush_grad(const float* gsm, float* grad, float* sums, const float* ssum, int K, int H)
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
 {
-    const int mb = master_block(H), gb = grad_block(H);
-    for (int b = 0; b < K; ++b) {
-        const float* G = gsm + b * gb;
-        float* out = grad + b * mb;
-        for (int i = threadIdx.x; i < 8 * H; i += blockDim.x) {
-            const float v = G[(i >> 3) * kGW1Stride + (i & 7)];
-            if (v != 0.f) atomicAdd(&out[i], v);
-        }
-        for (int i = threadIdx.x; i < H; i += blockDim.x) {
-            const float v = G[kGW1Stride * H + i];
-            if (v != 0.f) atomicAdd(&out[8 * H + i], v);
-        }
-        const float* G2 = G + (kGW1Stride + 1) * H;
-        for (int o = 0; o < 16; ++o)
-            for (int l = threadIdx.x; l < H; l += blockDim.x) {
-                const float v = G2[o * (H + 4) + l];
-                if (v != 0.f) atomicAdd(&out[9 * H + o * H + l], v);
-            }
-        if (threadIdx.x < 16) {
-            const float v = G2[16 * (H + 4) + threadIdx.x];
-            if (v != 0.f) atomicAdd(&out[25 * H + threadIdx.x], v);
-        }
+    asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.shared::cta.b64 st, [%0];\n}" ::"r"(bar) : "memory");
+}
+
+// has the phase of this parity completed (no waiting)
+__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile("{\n.reg .pred p;\nmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(ok)
+                 : "r"(bar), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+
+// waits for the phase of this parity to complete, for at most kTcWaitNs
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
+{
+    const unsigned long long t0 = global_ns();
+    while (true) {
+        uint32_t ok;
+        asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
+                     : "=r"(ok)
+                     : "r"(bar), "r"(parity)
+                     : "memory");
+        if (ok) return true;
+        if (global_ns() - t0 > kTcWaitNs) return false;
     }
-    if (threadIdx.x < 2) atomicAdd(&sums[threadIdx.x], ssum[threadIdx.x]);
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+// this thread's shared-memory stores become visible to the tensor cores
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// shared-memory matrix descriptor: start address, leading and stride byte
+// offsets (all >> 4), descriptor version 1 (bit 46), no swizzle
+__device__ __forceinline__ uint64_t tc_desc(uint32_t addr)
+{
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)(kTcLBO >> 4) << 16) | ((uint64_t)(kTcSBO >> 4) << 32) |
+           (1ull << 46);
+}
+
+// D (TMEM) = A B + (accumulate ? D : 0)
+__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t accumulate)
+{
+    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}"
+                 ::"r"(d), "l"(a), "l"(b), "r"(kTcIdesc), "r"(accumulate)
+                 : "memory");
+}
+
+// arrives on the barrier once every product this thread issued has completed
+__device__ __forceinline__ void tc_commit(uint32_t bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+// 16 consecutive 32-bit columns of this warp's 32 TMEM lanes (lane i: thread i)
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, uint32_t (&v)[16])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+                 "tcgen05.wait::ld.sync.aligned;"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                   "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                   "=r"(v[15])
+                 : "r"(taddr)
+                 : "memory");
 }
 
 // Training data of one flow: points theta [n][8], weights [n] (NULL = 1).
@@ -656,15 +717,23 @@ struct TrainSlot {
 
 // Flow f = blockIdx.y reads slots[f]: with rows, the batch of rows
 // rows[f * batch ..] (none if the flow has no points), else all its n points.
+// Dynamic shared memory: W slots of kTcSlot bytes, then the K blocks' published
+// operands.
 template <int K, int W>
-__global__ void __launch_bounds__(W * 32) grad_kernel(const uint32_t* __restrict__ pub, int H, Box box,
+__global__ void __launch_bounds__((W + 1) * 32, 1) grad_kernel(const uint32_t* __restrict__ pub, int H, Box box,
                                                                const TrainSlot* __restrict__ slots,
                                                                const uint32_t* __restrict__ rows_all, uint32_t batch,
-                                                               float* __restrict__ grad, float* __restrict__ sums)
+                                                               float* __restrict__ grad, float* __restrict__ sums,
+                                                               int* __restrict__ err)
 {
-    extern __shared__ __align__(16) uint32_t sm[];
+    static_assert(W % 4 == 0 && W <= 16, "compute warps come in groups of 4 (the TMEM lane quarters)");
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bar_full[W], bar_empty[W], bar_done;
+    __shared__ uint32_t tmem_s, init_s;
+    __shared__ float ssum[2];
+    __shared__ float gb2[K * 16];   // the CTA's db2 sums
     const Layout L = layout(H);
-    const int mb = master_block(H), gb = grad_block(H);
+    const int mb = master_block(H);
     const int f = blockIdx.y;
     const TrainSlot slot = slots[f];
     const uint64_t n_rows = rows_all ? (slot.n ? batch : 0) : slot.n;
@@ -675,158 +744,125 @@ __global__ void __launch_bounds__(W * 32) grad_kernel(const uint32_t* __restrict
     pub += (size_t)f * K * L.words;
     grad += (size_t)f * K * mb;
     sums += 2 * f;
-    uint32_t* wsm = sm;
-    float* gsm = reinterpret_cast<float*>(sm + K * L.grad_words);
-    WarpStage* stages = reinterpret_cast<WarpStage*>(gsm + K * gb);
+    uint32_t* wsm = reinterpret_cast<uint32_t*>(smem + W * kTcSlot);
     stage_blocks(wsm, pub, K, 0, L.grad_words, L);
-    for (int i = threadIdx.x; i < K * gb; i += blockDim.x) gsm[i] = 0.f;
-    __shared__ float ssum[2];
-    if (threadIdx.x < 2) ssum[threadIdx.x] = 0.f;
-    __syncthreads();
-    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    WarpStage& st = stages[threadIdx.x >> 5];
-    const uint64_t tiles = (n_rows + 15) / 16;
-    const int hw = H / 2 + 4;
-    for (uint64_t tile = (uint64_t)blockIdx.x * W + (threadIdx.x >> 5); tile < tiles;
-         tile += (uint64_t)gridDim.x * W) {
-        const uint64_t q0 = tile * 16 + g, q1 = q0 + 8;
-        const uint64_t i0 = q0 < n_rows ? (rows ? rows[q0] : q0) : 0;
-        const uint64_t i1 = q1 < n_rows ? (rows ? rows[q1] : q1) : 0;
-        const float w0 = q0 < n_rows ? (weights ? weights[i0] : 1.f) : 0.f;
-        const float w1 = q1 < n_rows ? (weights ? weights[i1] : 1.f) : 0.f;
-        const float2 ta = *reinterpret_cast<const float2*>(theta + 8 * i0 + 2 * t);
-        const float2 tb = *reinterpret_cast<const float2*>(theta + 8 * i1 + 2 * t);
-        float x[4], jac;
-        to_y(box, 2 * t, ta.x, x[0], jac);
-        to_y(box, 2 * t + 1, ta.y, x[1], jac);
-        to_y(box, 2 * t, tb.x, x[2], jac);
-        to_y(box, 2 * t + 1, tb.y, x[3], jac);
-        float xs[K][4], ms[K][4], as[K][4], zs[K][4];
-        float ld0 = 0.f, ld1 = 0.f;
-#pragma unroll
-        for (int b = 0; b < K; ++b) {
-            float mu[4], ar[4];
-            made_fwd(view(wsm + b * L.grad_words, L), H, x, mu, ar);
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                xs[b][e] = x[e];
-                ms[b][e] = mu[e];
-                as[b][e] = soft_alpha(ar[e]);
-                zs[b][e] = (x[e] - mu[e]) * __expf(-as[b][e]);
-                x[e] = zs[b][e];
-            }
-            ld0 += as[b][0] + as[b][1];
-            ld1 += as[b][2] + as[b][3];
-            reverse_cols(x);
-        }
-        // nll = -log p(z) + sum alpha
-        const float n0 = quad_sum(ld0 - log_base(x[0]) - log_base(x[1]));
-        const float n1 = quad_sum(ld1 - log_base(x[2]) - log_base(x[3]));
-        float contrib = (t == 0) ? (w0 * n0 + w1 * n1) : 0.f;
-        float wsum = (t == 0) ? (w0 + w1) : 0.f;
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            contrib += __shfl_xor_sync(kFull, contrib, off);
-            wsum += __shfl_xor_sync(kFull, wsum, off);
-        }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int C = (H + kTcM - 1) / kTcM;   // jobs (128-unit halves) per block
+    const int D = K * C;                   // (block, half) accumulator pairs, 32 columns each
+    const uint32_t ncols = D <= 1 ? 32u : D <= 2 ? 64u : D <= 4 ? 128u : 256u;
+    if (warp < W) {
+        // columns 8..15 of [x | 1] in both B slots: 1 in column 8, 0 after it
+        unsigned char* sb = smem + warp * kTcSlot + 2 * kTcHalf + 512 + 256;
+        for (int i = lane; i < 128; i += 32) st_u32(sb + (i >> 6) * kTcB + 4 * (i & 63), (i & 3) == 0 ? 0x3F80u : 0u);
+        fence_async_smem();
+    } else {
         if (lane == 0) {
-            atomicAdd(&ssum[0], contrib);
-            atomicAdd(&ssum[1], wsum);
+            for (int i = 0; i < W; ++i) {
+                mbar_init(smem_addr(&bar_full[i]), 1);
+                mbar_init(smem_addr(&bar_empty[i]), 1);
+            }
+            mbar_init(smem_addr(&bar_done), 1);
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         }
-        // d/dz_K of sum w (-log p(z)) = w tanh(z / 2)
-        float gx[4] = {w0 * tanhf(0.5f * x[0]), w0 * tanhf(0.5f * x[1]), w1 * tanhf(0.5f * x[2]),
-                       w1 * tanhf(0.5f * x[3])};
-        const float wr[4] = {w0, w0, w1, w1};
+        __syncwarp();
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_s)),
+                     "r"(ncols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    for (int i = threadIdx.x; i < K * 16; i += blockDim.x) gb2[i] = 0.f;
+    if (threadIdx.x < 2) ssum[threadIdx.x] = 0.f;
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_s;
+    const uint64_t tiles = (n_rows + 15) / 16;
+    const uint64_t tstride = (uint64_t)gridDim.x * W;
+    if (warp < W) {
+        const int g = lane >> 2, t = lane & 3, rg = 16 * g + 4 * t;
+        unsigned char* sA = smem + warp * kTcSlot;   // h at 0, g_a1 at kTcHalf, B slots after
+        const uint32_t full = smem_addr(&bar_full[warp]), empty = smem_addr(&bar_empty[warp]);
+        uint32_t job = 0, blk = 0;
+        bool ok = true;
+        const int hw = H / 2 + 4, chunks = H / 16;
+        for (uint64_t tile = (uint64_t)blockIdx.x * W + warp; tile < tiles; tile += tstride) {
+            const uint64_t q0 = tile * 16 + g, q1 = q0 + 8;
+            const uint64_t i0 = q0 < n_rows ? (rows ? rows[q0] : q0) : 0;
+            const uint64_t i1 = q1 < n_rows ? (rows ? rows[q1] : q1) : 0;
+            const float w0 = q0 < n_rows ? (weights ? weights[i0] : 1.f) : 0.f;
+            const float w1 = q1 < n_rows ? (weights ? weights[i1] : 1.f) : 0.f;
+            const float2 ta = *reinterpret_cast<const float2*>(theta + 8 * i0 + 2 * t);
+            const float2 tb = *reinterpret_cast<const float2*>(theta + 8 * i1 + 2 * t);
+            float x[4], jac;
+            to_y(box, 2 * t, ta.x, x[0], jac);
+            to_y(box, 2 * t + 1, ta.y, x[1], jac);
+            to_y(box, 2 * t, tb.x, x[2], jac);
+            to_y(box, 2 * t + 1, tb.y, x[3], jac);
+            float xs[K][4], as[K][4], zs[K][4];
+            float ld0 = 0.f, ld1 = 0.f;
 #pragma unroll
-        for (int b = K - 1; b >= 0; --b) {
-            const BlockView v = view(wsm + b * L.grad_words, L);
-            float* GW1 = gsm + b * gb;                // [H][kGW1Stride]
-            float* GB1 = GW1 + kGW1Stride * H;
-            float* GW2 = GB1 + H;                     // [16][H + 4]
-            float* GB2 = GW2 + 16 * (H + 4);
-            const int S2 = H + 4, sw = g & 1;
-            reverse_cols(gx);   // gradient with respect to this block's output z
-            float gmu[4], gar[4], gxd[4];
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const float ex = __expf(-as[b][e]);
-                gxd[e] = gx[e] * ex;
-                gmu[e] = -gx[e] * ex;
-                const float ga = -gx[e] * zs[b][e] + wr[e];
-                const float r = as[b][e] / kAlphaMax;
-                gar[e] = ga * (1.f - r * r);
-            }
-            // g_out (A of g_h = g_out W2 and, transposed, of dW2) and x, packed
-            // in the accumulator layout and staged row-major
-            const uint32_t A0 = pack2(gmu[0], gmu[1]), A1 = pack2(gmu[2], gmu[3]);
-            const uint32_t A2 = pack2(gar[0], gar[1]), A3 = pack2(gar[2], gar[3]);
-            const uint32_t xa0 = pack2(xs[b][0], xs[b][1]), xa1 = pack2(xs[b][2], xs[b][3]);
-            st.gout[g * kStage + t] = A0;
-            st.gout[(g + 8) * kStage + t] = A1;
-            st.gout[g * kStage + 4 + t] = A2;
-            st.gout[(g + 8) * kStage + 4 + t] = A3;
-            st.x[g * 4 + t] = xa0;
-            st.x[(g + 8) * 4 + t] = xa1;
-            // db2[o] = sum over rows of g_out
-            {
-                float d[4] = {gmu[0] + gmu[2], gmu[1] + gmu[3], gar[0] + gar[2], gar[1] + gar[3]};
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    d[e] += __shfl_xor_sync(kFull, d[e], 4);
-                    d[e] += __shfl_xor_sync(kFull, d[e], 8);
-                    d[e] += __shfl_xor_sync(kFull, d[e], 16);
-                }
-                if (g == 0) {
-                    atomicAdd(&GB2[2 * t], d[0]);
-                    atomicAdd(&GB2[2 * t + 1], d[1]);
-                    atomicAdd(&GB2[8 + 2 * t], d[2]);
-                    atomicAdd(&GB2[9 + 2 * t], d[3]);
-                }
-            }
-            __syncwarp();
-            // row addresses of the transposed loads: lane L feeds row L % 8 of
-            // matrix L / 8. For an A operand the matrices are the quadrants
-            // (rows 0-7 | 8-15) x (cols 0-7 | 8-15) in the order TL, TR, BL,
-            // BR; for a B operand TL, BL, TR, BR.
-            const int lm = lane >> 3, lr = lane & 7;
-            const int rowA = ((lm >> 1) << 3) + lr, colA = (lm & 1) << 2;
-            const int rowB = ((lm & 1) << 3) + lr, colB = (lm >> 1) << 2;
-            // g_out^T (A of dW2) and x^T (B of dW1) are the same for every chunk
-            uint32_t go[4];
-            ldsm_x4_trans(go, st.gout + rowA * kStage + colA);
-            uint32_t xt0, xt1;
-            ldsm_x2_trans(xt0, xt1, st.x + (((lane >> 3) & 1) * 8 + lr) * 4);
-            float accx[4] = {0.f, 0.f, 0.f, 0.f};
-            for (int s = 0; s < H / 16; ++s) {
-                // recompute the pre-activations of hidden units 16s .. 16s+15
-                const uint2 wa = reinterpret_cast<const uint2*>(v.w1)[(s * 8 + g) * 4 + t];
-                const float4 bq = reinterpret_cast<const float4*>(v.b1)[s * 4 + t];
-                float c0[4] = {bq.x, bq.y, bq.x, bq.y}, c1[4] = {bq.z, bq.w, bq.z, bq.w};
-                mma_k8(c0, xa0, xa1, wa.x);
-                mma_k8(c1, xa0, xa1, wa.y);
-                // h = relu(pre-activation), staged row-major
-                st.h[g * kStage + t] = pack2_relu(c0[0], c0[1]);
-                st.h[(g + 8) * kStage + t] = pack2_relu(c0[2], c0[3]);
-                st.h[g * kStage + 4 + t] = pack2_relu(c1[0], c1[1]);
-                st.h[(g + 8) * kStage + 4 + t] = pack2_relu(c1[2], c1[3]);
-                // g_h = g_out W2 for these units, then through the ReLU
-                float d0[4] = {0.f, 0.f, 0.f, 0.f}, d1[4] = {0.f, 0.f, 0.f, 0.f};
-                mma_k16(d0, A0, A1, A2, A3, v.w2t[(16 * s + g) * 12 + t], v.w2t[(16 * s + g) * 12 + 4 + t]);
-                mma_k16(d1, A0, A1, A2, A3, v.w2t[(16 * s + 8 + g) * 12 + t], v.w2t[(16 * s + 8 + g) * 12 + 4 + t]);
+            for (int b = 0; b < K; ++b) {
+                float mu[4], ar[4];
+                made_fwd(view(wsm + b * L.grad_words, L), H, x, mu, ar);
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
-                    d0[e] = c0[e] > 0.f ? d0[e] : 0.f;
-                    d1[e] = c1[e] > 0.f ? d1[e] : 0.f;
+                    xs[b][e] = x[e];
+                    as[b][e] = soft_alpha(ar[e]);
+                    zs[b][e] = (x[e] - mu[e]) * __expf(-as[b][e]);
+                    x[e] = zs[b][e];
                 }
-                const uint32_t P0 = pack2(d0[0], d0[1]), P1 = pack2(d0[2], d0[3]);
-                const uint32_t P2 = pack2(d1[0], d1[1]), P3 = pack2(d1[2], d1[3]);
-                st.ga[g * kStage + t] = P0;
-                st.ga[(g + 8) * kStage + t] = P1;
-                st.ga[g * kStage + 4 + t] = P2;
-                st.ga[(g + 8) * kStage + 4 + t] = P3;
-                // db1[l] = sum over rows of g_a1
+                ld0 += as[b][0] + as[b][1];
+                ld1 += as[b][2] + as[b][3];
+                reverse_cols(x);
+            }
+            // nll = -log p(z) + sum alpha
+            const float n0 = quad_sum(ld0 - log_base(x[0]) - log_base(x[1]));
+            const float n1 = quad_sum(ld1 - log_base(x[2]) - log_base(x[3]));
+            float contrib = (t == 0) ? (w0 * n0 + w1 * n1) : 0.f;
+            float wsum = (t == 0) ? (w0 + w1) : 0.f;
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                contrib += __shfl_xor_sync(kFull, contrib, off);
+                wsum += __shfl_xor_sync(kFull, wsum, off);
+            }
+            if (lane == 0) {
+                atomicAdd(&ssum[0], contrib);
+                atomicAdd(&ssum[1], wsum);
+            }
+            // d/dz_K of sum w (-log p(z)) = w tanh(z / 2)
+            float gx[4] = {w0 * tanhf(0.5f * x[0]), w0 * tanhf(0.5f * x[1]), w1 * tanhf(0.5f * x[2]),
+                           w1 * tanhf(0.5f * x[3])};
+            const float wr[4] = {w0, w0, w1, w1};
+#pragma unroll
+            for (int b = K - 1; b >= 0; --b) {
+                const BlockView v = view(wsm + b * L.grad_words, L);
+                reverse_cols(gx);   // gradient with respect to this block's output z
+                float gmu[4], gar[4], gxd[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const float ex = __expf(-as[b][e]);
+                    gxd[e] = gx[e] * ex;
+                    gmu[e] = -gx[e] * ex;
+                    const float ga = -gx[e] * zs[b][e] + wr[e];
+                    const float r = as[b][e] / kAlphaMax;
+                    gar[e] = ga * (1.f - r * r);
+                }
+                // g_out: the A fragment of g_h = g_out W2, and this block's B
+                // operands g_out [row][o] and x [row][j] in the B slot
+                const uint32_t A0 = pack2(gmu[0], gmu[1]), A1 = pack2(gmu[2], gmu[3]);
+                const uint32_t A2 = pack2(gar[0], gar[1]), A3 = pack2(gar[2], gar[3]);
+                unsigned char* sB = sA + 2 * kTcHalf + (blk & 1) * kTcB;
+                ++blk;
+                st_u32(sB + rg, A0);
+                st_u32(sB + 128 + rg, A1);
+                st_u32(sB + 256 + rg, A2);
+                st_u32(sB + 384 + rg, A3);
+                const uint32_t xa0 = pack2(xs[b][0], xs[b][1]), xa1 = pack2(xs[b][2], xs[b][3]);
+                st_u32(sB + 512 + rg, xa0);
+                st_u32(sB + 640 + rg, xa1);
+                // db2[o] = sum over rows of g_out
                 {
-                    float d[4] = {d0[0] + d0[2], d0[1] + d0[3], d1[0] + d1[2], d1[1] + d1[3]};
+                    float d[4] = {gmu[0] + gmu[2], gmu[1] + gmu[3], gar[0] + gar[2], gar[1] + gar[3]};
 #pragma unroll
                     for (int e = 0; e < 4; ++e) {
                         d[e] += __shfl_xor_sync(kFull, d[e], 4);
@@ -834,61 +870,146 @@ __global__ void __launch_bounds__(W * 32) grad_kernel(const uint32_t* __restrict
                         d[e] += __shfl_xor_sync(kFull, d[e], 16);
                     }
                     if (g == 0) {
-                        atomicAdd(&GB1[16 * s + 2 * t], d[0]);
-                        atomicAdd(&GB1[16 * s + 2 * t + 1], d[1]);
-                        atomicAdd(&GB1[16 * s + 8 + 2 * t], d[2]);
-                        atomicAdd(&GB1[16 * s + 9 + 2 * t], d[3]);
+                        atomicAdd(&gb2[16 * b + 2 * t], d[0]);
+                        atomicAdd(&gb2[16 * b + 2 * t + 1], d[1]);
+                        atomicAdd(&gb2[16 * b + 8 + 2 * t], d[2]);
+                        atomicAdd(&gb2[16 * b + 9 + 2 * t], d[3]);
                     }
                 }
-                // g_x += g_a1 W1 (this chunk's 16 hidden units as k)
-                mma_k16(accx, P0, P1, P2, P3, v.w1t[g * hw + 8 * s + t], v.w1t[g * hw + 8 * s + 4 + t]);
-                __syncwarp();
-                // dW2[o][l] += sum_rows g_out[row][o] h[row][l]
-                {
-                    uint32_t hb[4];   // B of e0: hb[0], hb[1]; of e1: hb[2], hb[3]
-                    ldsm_x4_trans(hb, st.h + rowB * kStage + colB);
-                    float e0[4] = {0.f, 0.f, 0.f, 0.f}, e1[4] = {0.f, 0.f, 0.f, 0.f};
-                    mma_k16(e0, go[0], go[1], go[2], go[3], hb[0], hb[1]);
-                    mma_k16(e1, go[0], go[1], go[2], go[3], hb[2], hb[3]);
-                    const int la = 16 * s + 2 * t, lb = 16 * s + 8 + 2 * t;
-                    // odd row-groups take their column pair in the other order
-                    const float e00 = sw ? e0[1] : e0[0], e01 = sw ? e0[0] : e0[1];
-                    const float e02 = sw ? e0[3] : e0[2], e03 = sw ? e0[2] : e0[3];
-                    const float e10 = sw ? e1[1] : e1[0], e11 = sw ? e1[0] : e1[1];
-                    const float e12 = sw ? e1[3] : e1[2], e13 = sw ? e1[2] : e1[3];
-                    const int pa = la + sw, qa = la + 1 - sw, pb = lb + sw, qb = lb + 1 - sw;
-                    if (mask2(g, pa)) atomicAdd(&GW2[g * S2 + pa], e00);
-                    if (mask2(g, qa)) atomicAdd(&GW2[g * S2 + qa], e01);
-                    if (mask2(g + 8, pa)) atomicAdd(&GW2[(g + 8) * S2 + pa], e02);
-                    if (mask2(g + 8, qa)) atomicAdd(&GW2[(g + 8) * S2 + qa], e03);
-                    if (mask2(g, pb)) atomicAdd(&GW2[g * S2 + pb], e10);
-                    if (mask2(g, qb)) atomicAdd(&GW2[g * S2 + qb], e11);
-                    if (mask2(g + 8, pb)) atomicAdd(&GW2[(g + 8) * S2 + pb], e12);
-                    if (mask2(g + 8, qb)) atomicAdd(&GW2[(g + 8) * S2 + qb], e13);
-                }
-                // dW1[l][j] += sum_rows g_a1[row][l] x[row][j]
-                {
-                    uint32_t ab[4];
-                    ldsm_x4_trans(ab, st.ga + rowA * kStage + colA);
-                    float e0[4] = {0.f, 0.f, 0.f, 0.f};
-                    mma_k16(e0, ab[0], ab[1], ab[2], ab[3], xt0, xt1);
-                    const int la = 16 * s + g, lb = la + 8;
-                    const int ja = 2 * t + sw, jb = 2 * t + 1 - sw;
-                    const float f0 = sw ? e0[1] : e0[0], f1 = sw ? e0[0] : e0[1];
-                    const float f2 = sw ? e0[3] : e0[2], f3 = sw ? e0[2] : e0[3];
-                    if (mask1(la, ja)) atomicAdd(&GW1[la * kGW1Stride + ja], f0);
-                    if (mask1(la, jb)) atomicAdd(&GW1[la * kGW1Stride + jb], f1);
-                    if (mask1(lb, ja)) atomicAdd(&GW1[lb * kGW1Stride + ja], f2);
-                    if (mask1(lb, jb)) atomicAdd(&GW1[lb * kGW1Stride + jb], f3);
-                }
-                __syncwarp();
-            }
+                float accx[4] = {0.f, 0.f, 0.f, 0.f};
+                for (int s = 0; s < chunks; ++s) {
+                    const int q = s & 7;   // chunk within the 128-unit half
+                    // recompute the pre-activations of hidden units 16s .. 16s+15
+                    const uint2 wa = reinterpret_cast<const uint2*>(v.w1)[(s * 8 + g) * 4 + t];
+                    const float4 bq = reinterpret_cast<const float4*>(v.b1)[s * 4 + t];
+                    float c0[4] = {bq.x, bq.y, bq.x, bq.y}, c1[4] = {bq.z, bq.w, bq.z, bq.w};
+                    mma_k8(c0, xa0, xa1, wa.x);
+                    mma_k8(c1, xa0, xa1, wa.y);
+                    // g_h = g_out W2 for these units, then through the ReLU
+                    float d0[4] = {0.f, 0.f, 0.f, 0.f}, d1[4] = {0.f, 0.f, 0.f, 0.f};
+                    mma_k16(d0, A0, A1, A2, A3, v.w2t[(16 * s + g) * 12 + t], v.w2t[(16 * s + g) * 12 + 4 + t]);
+                    mma_k16(d1, A0, A1, A2, A3, v.w2t[(16 * s + 8 + g) * 12 + t], v.w2t[(16 * s + 8 + g) * 12 + 4 + t]);
 #pragma unroll
-            for (int e = 0; e < 4; ++e) gx[e] = gxd[e] + accx[e];
+                    for (int e = 0; e < 4; ++e) {
+                        d0[e] = c0[e] > 0.f ? d0[e] : 0.f;
+                        d1[e] = c1[e] > 0.f ? d1[e] : 0.f;
+                    }
+                    const uint32_t P0 = pack2(d0[0], d0[1]), P1 = pack2(d0[2], d0[3]);
+                    const uint32_t P2 = pack2(d1[0], d1[1]), P3 = pack2(d1[2], d1[3]);
+                    // g_x += g_a1 W1 (this chunk's 16 hidden units as k)
+                    mma_k16(accx, P0, P1, P2, P3, v.w1t[g * hw + 8 * s + t], v.w1t[g * hw + 8 * s + 4 + t]);
+                    // h and g_a1 of these units into the A slot (core matrices
+                    // 2q and 2q + 1 along M); a job's first chunk waits until the
+                    // products of the warp's previous job have read the slot
+                    if (q == 0 && job > 0) ok = mbar_wait(empty, (job - 1) & 1u) && ok;
+                    unsigned char* a = sA + 512 * q + rg;
+                    st_u32(a, pack2_relu(c0[0], c0[1]));
+                    st_u32(a + 128, pack2_relu(c0[2], c0[3]));
+                    st_u32(a + 256, pack2_relu(c1[0], c1[1]));
+                    st_u32(a + 384, pack2_relu(c1[2], c1[3]));
+                    st_u32(a + kTcHalf, P0);
+                    st_u32(a + kTcHalf + 128, P1);
+                    st_u32(a + kTcHalf + 256, P2);
+                    st_u32(a + kTcHalf + 384, P3);
+                    if (q == 7 || s == chunks - 1) {
+                        fence_async_smem();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(full);
+                        ++job;
+                    }
+                }
+#pragma unroll
+                for (int e = 0; e < 4; ++e) gx[e] = gxd[e] + accx[e];
+            }
         }
+        if (!ok && lane == 0) atomicExch(err, 1);
+    } else if (lane == 0) {
+        // the issuing thread: jobs of warp w in its order (tile, block K-1..0, half)
+        uint32_t next[W], total[W], remaining = 0;
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+            const uint64_t t0 = (uint64_t)blockIdx.x * W + w;
+            total[w] = t0 < tiles ? (uint32_t)((tiles - 1 - t0) / tstride + 1) * (uint32_t)D : 0u;
+            next[w] = 0;
+            remaining += total[w];
+        }
+        uint32_t init = 0;   // accumulator pairs written at least once
+        unsigned long long t_last = global_ns();
+        while (remaining > 0) {
+            bool progress = false;
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                const uint32_t n = next[w];
+                if (n == total[w] || !mbar_test(smem_addr(&bar_full[w]), n & 1u)) continue;
+                tc_fence_after();
+                const uint32_t bi = n / (uint32_t)C;   // block index in the warp's sequence
+                const int c = (int)(n - bi * (uint32_t)C), b = K - 1 - (int)(bi % K);
+                const int d = b * C + c;
+                const uint32_t sa = smem_addr(smem + w * kTcSlot);
+                const uint32_t sb = sa + 2 * kTcHalf + (bi & 1u) * kTcB;
+                const uint32_t acc = (init >> d) & 1u;
+                init |= 1u << d;
+                tc_mma(tmem + 32 * d, tc_desc(sa), tc_desc(sb), acc);
+                tc_mma(tmem + 32 * d + 16, tc_desc(sa + kTcHalf), tc_desc(sb + 512), acc);
+                tc_commit(smem_addr(&bar_empty[w]));
+                next[w] = n + 1;
+                --remaining;
+                progress = true;
+            }
+            if (progress) {
+                t_last = global_ns();
+            } else if (global_ns() - t_last > kTcWaitNs) {
+                atomicExch(err, 1);
+                break;
+            }
+        }
+        init_s = init;
+        tc_commit(smem_addr(&bar_done));
     }
     __syncthreads();
-    flush_grad(gsm, grad, sums, ssum, K, H);
+    // bar_done's first phase completes once every product of the CTA has
+    const bool done = __all_sync(kFull, mbar_wait(smem_addr(&bar_done), 0));   // uniform over the warp
+    if (!done && threadIdx.x == 0) atomicExch(err, 1);
+    tc_fence_after();
+    const uint32_t init = init_s;
+    if (warp < W && done) {
+        // warp w reads TMEM lanes 32 (w mod 4) .. + 31; the warps of a lane
+        // quarter share its 2 D column groups
+        const int quarter = warp & 3;
+        for (int cc = warp >> 2; cc < 2 * D; cc += W / 4) {
+            const int d = cc >> 1;
+            if (!((init >> d) & 1u)) continue;   // uniform over the warp
+            uint32_t v[16];
+            tc_ld16(tmem + ((uint32_t)(32 * quarter) << 16) + 16 * cc, v);
+            const int b = d / C, c = d - b * C;
+            const int l = kTcM * c + 32 * quarter + lane;
+            if (l >= H) continue;
+            float* out = grad + (size_t)b * mb;
+            if ((cc & 1) == 0) {
+#pragma unroll
+                for (int o = 0; o < 16; ++o) {
+                    const float val = __uint_as_float(v[o]);
+                    if (mask2(o, l) && val != 0.f) atomicAdd(&out[9 * H + o * H + l], val);
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const float val = __uint_as_float(v[j]);
+                    if (mask1(l, j) && val != 0.f) atomicAdd(&out[l * 8 + j], val);
+                }
+                const float val = __uint_as_float(v[8]);
+                if (val != 0.f) atomicAdd(&out[8 * H + l], val);
+            }
+        }
+    }
+    for (int i = threadIdx.x; i < K * 16; i += blockDim.x)
+        if (gb2[i] != 0.f) atomicAdd(&grad[(size_t)(i >> 4) * mb + 25 * H + (i & 15)], gb2[i]);
+    if (threadIdx.x < 2) atomicAdd(&sums[threadIdx.x], ssum[threadIdx.x]);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == W)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
 }
 
 // batch rows for one training step: uniform indices with replacement
@@ -946,6 +1067,7 @@ struct abc_maf_s {
     float* d_grad = nullptr;
     uint32_t* d_pub = nullptr; // [R][K][pub_words] published BF16 operands
     float* d_sums = nullptr;   // [R][2] (weighted loss sum, weight sum)
+    int* d_err = nullptr;      // set by a gradient kernel whose bounded wait ran out
     int* d_step = nullptr;
     uint32_t* d_rows = nullptr;
     uint32_t rows_cap = 0;     // batch rows per flow
@@ -967,13 +1089,26 @@ namespace {
         if (_e != cudaSuccess) return plan_cuda_fail(_e, what); \
     } while (0)
 
+// After the stream has been synchronised: ABC_ERR_TIMEOUT if a gradient
+// kernel's bounded wait for its tensor-core products ran out (the word is
+// then cleared for the next call).
+abc_status take_err(abc_maf f)
+{
+    int h = 0;
+    MAF_TRY(cudaMemcpy(&h, f->d_err, sizeof h, cudaMemcpyDeviceToHost), "cudaMemcpy(error word)");
+    if (h) {
+        MAF_TRY(cudaMemset(f->d_err, 0, sizeof h), "cudaMemset(error word)");
+        return plan_fail(ABC_ERR_TIMEOUT, "a flow gradient kernel's wait for its tensor-core products ran out of time");
+    }
+    return ABC_OK;
+}
+
 size_t fwd_smem(const abc_maf_s* f) { return sizeof(uint32_t) * (size_t)f->K * maf::layout(f->H).fwd_words; }
 size_t samp_smem(const abc_maf_s* f) { return sizeof(uint32_t) * (size_t)f->K * maf::layout(f->H).samp_words; }
 
 size_t grad_smem(const abc_maf_s* f, int warps)
 {
-    return sizeof(uint32_t) * (size_t)f->K * maf::layout(f->H).grad_words +
-           sizeof(float) * (size_t)f->K * maf::grad_block(f->H) + sizeof(maf::WarpStage) * warps;
+    return sizeof(uint32_t) * (size_t)f->K * maf::layout(f->H).grad_words + (size_t)maf::kTcSlot * warps;
 }
 
 abc_status check(abc_maf f)
@@ -1073,8 +1208,8 @@ cudaError_t launch_grad_w(abc_maf f, const uint32_t* rows, uint32_t batch, uint6
     if (e != cudaSuccess) return e;
     const uint64_t want = (tiles + W - 1) / W;
     const int grid = (int)(want < (uint64_t)sm_count() ? (want > 0 ? want : 1) : (uint64_t)sm_count());
-    maf::grad_kernel<K, W><<<dim3(grid, f->R), W * 32, smem, s>>>(f->d_pub, f->H, f->box, f->d_slots, rows, batch,
-                                                                 f->d_grad, f->d_sums);
+    maf::grad_kernel<K, W><<<dim3(grid, f->R), (W + 1) * 32, smem, s>>>(f->d_pub, f->H, f->box, f->d_slots, rows,
+                                                                       batch, f->d_grad, f->d_sums, f->d_err);
     return cudaGetLastError();
 }
 
@@ -1170,11 +1305,13 @@ abc_status abc_maf_create_multi(int32_t n_flows, int32_t n_blocks, int32_t hidde
         (e = cudaMalloc(&f->d_pub, sizeof(uint32_t) * (size_t)f->R * f->K * f->pub_words)) != cudaSuccess ||
         (e = cudaMalloc(&f->d_sums, 2 * sizeof(float) * f->R)) != cudaSuccess ||
         (e = cudaMalloc(&f->d_step, sizeof(int))) != cudaSuccess ||
-        (e = cudaMalloc(&f->d_slots, sizeof(maf::TrainSlot) * f->R)) != cudaSuccess)
+        (e = cudaMalloc(&f->d_slots, sizeof(maf::TrainSlot) * f->R)) != cudaSuccess ||
+        (e = cudaMalloc(&f->d_err, sizeof(int))) != cudaSuccess)
         return fail_free(plan_cuda_fail(e, "cudaMalloc(flow)"));
     if ((e = cudaMemset(f->d_params, 0, np)) != cudaSuccess || (e = cudaMemset(f->d_m, 0, np)) != cudaSuccess ||
         (e = cudaMemset(f->d_v, 0, np)) != cudaSuccess || (e = cudaMemset(f->d_step, 0, sizeof(int))) != cudaSuccess ||
         (e = cudaMemset(f->d_slots, 0, sizeof(maf::TrainSlot) * f->R)) != cudaSuccess ||
+        (e = cudaMemset(f->d_err, 0, sizeof(int))) != cudaSuccess ||
         (e = publish(f, nullptr)) != cudaSuccess || (e = cudaDeviceSynchronize()) != cudaSuccess)
         return fail_free(plan_cuda_fail(e, "flow initialisation"));
     *maf_out = f;
@@ -1298,6 +1435,10 @@ abc_status abc_maf_gradient(abc_maf f, uint64_t n, const float* theta, const flo
     float sums[2] = {0.f, 0.f};
     MAF_TRY(cudaMemcpyAsync(sums, f->d_sums, sizeof sums, cudaMemcpyDeviceToHost, s), "cudaMemcpyAsync(sums)");
     MAF_TRY(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+    {
+        const abc_status es = take_err(f);
+        if (es != ABC_OK) return es;
+    }
     if (loss_out) *loss_out = sums[1] > 0.f ? sums[0] / sums[1] : 0.f;
     if (grads_out) {
         MAF_TRY(cudaMemcpy(grads_out, f->d_grad, sizeof(float) * f->n_params, cudaMemcpyDeviceToHost),
@@ -1429,6 +1570,10 @@ abc_status abc_maf_train_flows(abc_maf f, const float* const* theta, const float
             MAF_TRY(cudaMemcpyAsync(sums.data(), f->d_sums, sizeof(float) * sums.size(), cudaMemcpyDeviceToHost, s),
                     "cudaMemcpyAsync(sums)");
             MAF_TRY(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+            {
+                const abc_status es = take_err(f);
+                if (es != ABC_OK) return es;
+            }
             for (int r = 0; r < R; ++r) {
                 if (n_va[r] == 0 || sums[2 * r + 1] <= 0.f) continue;
                 const float vl = sums[2 * r] / sums[2 * r + 1];
@@ -1463,6 +1608,10 @@ abc_status abc_maf_train_flows(abc_maf f, const float* const* theta, const float
                         "cudaMemcpyAsync(restore parameters)");
         MAF_TRY(publish(f, s), "publish");
         MAF_TRY(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+        {
+            const abc_status es = take_err(f);
+            if (es != ABC_OK) return es;
+        }
         if (loss_out)
             for (int r = 0; r < R; ++r) loss_out[r] = n_va[r] > 0 && best[r] < INFINITY ? best[r] : 0.f;
         return plan_ok();
@@ -1475,9 +1624,17 @@ abc_status abc_maf_train_flows(abc_maf f, const float* const* theta, const float
         MAF_TRY(cudaMemcpyAsync(sums.data(), f->d_sums, sizeof(float) * sums.size(), cudaMemcpyDeviceToHost, s),
                 "cudaMemcpyAsync(sums)");
         MAF_TRY(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+        {
+            const abc_status es = take_err(f);
+            if (es != ABC_OK) return es;
+        }
         for (int r = 0; r < f->R; ++r) loss_out[r] = sums[2 * r + 1] > 0.f ? sums[2 * r] / sums[2 * r + 1] : 0.f;
     } else {
         MAF_TRY(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+        {
+            const abc_status es = take_err(f);
+            if (es != ABC_OK) return es;
+        }
     }
     return plan_ok();
 }
@@ -1514,6 +1671,7 @@ abc_status abc_maf_destroy(abc_maf f)
     cudaFree(f->d_step);
     cudaFree(f->d_rows);
     cudaFree(f->d_slots);
+    cudaFree(f->d_err);
     cudaFree(f->d_best);
     delete f;
     return plan_ok();
