@@ -329,8 +329,8 @@ typedef struct abc_maf_s* abc_maf;
 /* Create a flow with n_blocks (1..4) blocks of `hidden` units (a multiple of
  * 16, 16..256) on the prior box, parameters zero (q = the uniform prior).
  * Allocates its device memory on the current device. The training kernel
- * stages a CTA's operands in shared memory, n_blocks (116 hidden + 192) +
- * 40960 bytes (published BF16 operands per block, tensor-core operand slots
+ * stages a CTA's operands in shared memory, n_blocks (100 hidden + 192) +
+ * 36864 bytes (published BF16 operands per block, tensor-core operand slots
  * of four warps), and its gradient sums in tensor memory: a shape beyond the
  * device's per-block limit returns ABC_ERR_INVALID_ARG (on GB300, 227 KB:
  * every shape up to 4 blocks of 256 fits). */

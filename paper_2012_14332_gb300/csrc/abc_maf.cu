@@ -60,7 +60,9 @@ __host__ __device__ inline int master_block(int H) { return 25 * H + 16; }
 //   b1  [H/16][4][4]     FP32: b1 of hidden 16s + 2t, +1, 16s + 8 + 2t, +1
 //   b2  [16]             FP32
 //   w1t [8][H/2+4]       B operand of g_a1 W1     (n = j, k = l)
-//   w2t [H][12]          B operand of g_out W2    (n = l, k = o)
+//   w2t [H][8]           B operand of g_out W2    (n = l, k = o); rows l with
+//                        l & 4 hold their two 4-word halves swapped, so the
+//                        warp's fragment loads meet 32 distinct banks
 // then the sampler's copy of the forward operands (sw1, sw2, sb1 in the w1,
 // w2, b1 layouts, and sb2 = b2), whose 16-unit chunks hold the hidden units
 // grouped by degree: the chunks of degree d = 1..7 hold units d - 1, d + 6,
@@ -108,7 +110,7 @@ __host__ __device__ inline Layout layout(int H)
     L.b2 = o; o += 16;
     L.fwd_words = o;
     L.w1t = o; o += 8 * (H / 2 + 4);
-    L.w2t = o; o += H * 12;
+    L.w2t = o; o += H * 8;
     L.grad_words = o;
     const int C = sampler_chunks(H);
     L.sw1 = o; o += C * 64;
@@ -354,13 +356,10 @@ __global__ void publish_kernel(const float* __restrict__ master, uint32_t* __res
                 out = *reinterpret_cast<uint32_t*>(&v);
             }
         } else if (w < L.grad_words) {
-            const int r = w - L.w2t, l = r / 12, c = r % 12;
-            if (c < 8) {
-                const int o0 = 2 * c;
-                __nv_bfloat162 v = __floats2bfloat162_rn(mask2(o0, l) ? W2[o0 * H + l] : 0.f,
-                                                         mask2(o0 + 1, l) ? W2[(o0 + 1) * H + l] : 0.f);
-                out = *reinterpret_cast<uint32_t*>(&v);
-            }
+            const int r = w - L.w2t, l = r / 8, o0 = 2 * ((r % 8) ^ (l & 4));
+            __nv_bfloat162 v = __floats2bfloat162_rn(mask2(o0, l) ? W2[o0 * H + l] : 0.f,
+                                                     mask2(o0 + 1, l) ? W2[(o0 + 1) * H + l] : 0.f);
+            out = *reinterpret_cast<uint32_t*>(&v);
         } else if (w < L.sw2) {
             // as w1, over the degree-grouped chunks: unit at position g + 8 h of chunk s
             const int r = w - L.sw1, h = r & 1, t = (r >> 1) & 3, g = (r >> 3) & 7, sc = r >> 6;
@@ -586,14 +585,14 @@ __global__ void __launch_bounds__(kFwdThreads, kFwdMinBlocks) sample_kernel(cons
 //
 // Warps 0..W-1 compute; one lane of warp W issues the products. A compute
 // warp's job is one (block, half) of one tile: it stores h and g_a1 of 128
-// hidden units (eight 16-unit chunks) into its A slot, having stored g_out and
-// x into one of its two B slots at the start of the block, and arrives on
-// full[w]. The issuing thread polls the full barriers, issues the job's two
-// products and commits them to empty[w]. A warp waits on empty[w] before it
-// overwrites its A slot with the next job. A commit tracks every product the
-// thread issued before it, so that wait also frees the B slot the warp
-// rewrites two blocks later. All products come from one thread in issue
-// order, so accumulations into the same TMEM columns never race.
+// hidden units (eight 16-unit chunks) into its A slot (and, in a block's
+// first job, g_out and x into its B slot), then arrives on full[w]. The
+// issuing thread polls the full barriers, issues the job's two products and
+// commits them to empty[w]. A warp waits on empty[w] before the first store
+// of its next job; a commit tracks every product the thread issued before
+// it, so the previous block's products are done when the B slot is
+// rewritten. All products come from one thread in issue order, so
+// accumulations into the same TMEM columns never race.
 //
 // Operands in shared memory are MN-major (hidden unit, output or input
 // contiguous), without swizzle: a core matrix is 8 rows of k (tile rows) x 16
@@ -606,14 +605,15 @@ __global__ void __launch_bounds__(kFwdThreads, kFwdMinBlocks) sample_kernel(cons
 // Every wait is bounded in time (kTcWaitNs). A wait that runs out sets the
 // flow's error word; the kernel still runs to its end and frees its TMEM.
 
-// compute warps per CTA: 4, or 12 when a step has enough tiles for more than
-// two waves of 4-warp CTAs (one CTA fits per SM)
+// compute warps per CTA: 4, or 15 when a step has enough tiles for more than
+// two waves of 4-warp CTAs (one CTA fits per SM; 16 warps in all keep 128
+// registers per thread)
 constexpr int kGradWarpsNarrow = 4;
-constexpr int kGradWarpsWide = 12;
+constexpr int kGradWarpsWide = 15;
 constexpr int kTcM = 128;                          // hidden units per product
 constexpr int kTcHalf = 4096;                      // one A operand: 128 units x 16 rows, bf16
-constexpr int kTcB = 1024;                         // one B slot: g_out (512 B), [x | 1] (512 B)
-constexpr int kTcSlot = 2 * kTcHalf + 2 * kTcB;    // shared memory per compute warp
+constexpr int kTcB = 1024;                         // the B slot: g_out (512 B), [x | 1] (512 B)
+constexpr int kTcSlot = 2 * kTcHalf + kTcB;        // shared memory per compute warp
 constexpr uint32_t kTcLBO = 128, kTcSBO = 256;
 // instruction descriptor of kind::f16: FP32 accumulator (bits 4-5), BF16 A
 // and B (bits 7-9, 10-12), both MN-major (bits 15, 16), N >> 3 (bits 17-22),
@@ -726,7 +726,7 @@ __global__ void __launch_bounds__((W + 1) * 32, 1) grad_kernel(const uint32_t* _
                                                                float* __restrict__ grad, float* __restrict__ sums,
                                                                int* __restrict__ err)
 {
-    static_assert(W % 4 == 0 && W <= 16, "compute warps come in groups of 4 (the TMEM lane quarters)");
+    static_assert(W >= 4 && W <= 15, "at least one compute warp per TMEM lane quarter; 16 warps in all at most");
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ __align__(8) uint64_t bar_full[W], bar_empty[W], bar_done;
     __shared__ uint32_t tmem_s, init_s;
@@ -751,9 +751,9 @@ __global__ void __launch_bounds__((W + 1) * 32, 1) grad_kernel(const uint32_t* _
     const int D = K * C;                   // (block, half) accumulator pairs, 32 columns each
     const uint32_t ncols = D <= 1 ? 32u : D <= 2 ? 64u : D <= 4 ? 128u : 256u;
     if (warp < W) {
-        // columns 8..15 of [x | 1] in both B slots: 1 in column 8, 0 after it
+        // columns 8..15 of [x | 1] in the B slot: 1 in column 8, 0 after it
         unsigned char* sb = smem + warp * kTcSlot + 2 * kTcHalf + 512 + 256;
-        for (int i = lane; i < 128; i += 32) st_u32(sb + (i >> 6) * kTcB + 4 * (i & 63), (i & 3) == 0 ? 0x3F80u : 0u);
+        for (int i = lane; i < 64; i += 32) st_u32(sb + 4 * i, (i & 3) == 0 ? 0x3F80u : 0u);
         fence_async_smem();
     } else {
         if (lane == 0) {
@@ -779,10 +779,11 @@ __global__ void __launch_bounds__((W + 1) * 32, 1) grad_kernel(const uint32_t* _
     const uint64_t tiles = (n_rows + 15) / 16;
     const uint64_t tstride = (uint64_t)gridDim.x * W;
     if (warp < W) {
-        const int g = lane >> 2, t = lane & 3, rg = 16 * g + 4 * t;
-        unsigned char* sA = smem + warp * kTcSlot;   // h at 0, g_a1 at kTcHalf, B slots after
+        const int g = lane >> 2, t = lane & 3, rg = 16 * g + 4 * t, sw = g & 4;
+        unsigned char* sA = smem + warp * kTcSlot;   // h at 0, g_a1 at kTcHalf, the B slot after
+        unsigned char* sB = sA + 2 * kTcHalf;
         const uint32_t full = smem_addr(&bar_full[warp]), empty = smem_addr(&bar_empty[warp]);
-        uint32_t job = 0, blk = 0;
+        uint32_t job = 0;
         bool ok = true;
         const int hw = H / 2 + 4, chunks = H / 16;
         for (uint64_t tile = (uint64_t)blockIdx.x * W + warp; tile < tiles; tile += tstride) {
@@ -847,19 +848,11 @@ __global__ void __launch_bounds__((W + 1) * 32, 1) grad_kernel(const uint32_t* _
                     const float r = as[b][e] / kAlphaMax;
                     gar[e] = ga * (1.f - r * r);
                 }
-                // g_out: the A fragment of g_h = g_out W2, and this block's B
-                // operands g_out [row][o] and x [row][j] in the B slot
+                // g_out: the A fragment of g_h = g_out W2 and, with x, this
+                // block's B operands g_out [row][o] and x [row][j]
                 const uint32_t A0 = pack2(gmu[0], gmu[1]), A1 = pack2(gmu[2], gmu[3]);
                 const uint32_t A2 = pack2(gar[0], gar[1]), A3 = pack2(gar[2], gar[3]);
-                unsigned char* sB = sA + 2 * kTcHalf + (blk & 1) * kTcB;
-                ++blk;
-                st_u32(sB + rg, A0);
-                st_u32(sB + 128 + rg, A1);
-                st_u32(sB + 256 + rg, A2);
-                st_u32(sB + 384 + rg, A3);
                 const uint32_t xa0 = pack2(xs[b][0], xs[b][1]), xa1 = pack2(xs[b][2], xs[b][3]);
-                st_u32(sB + 512 + rg, xa0);
-                st_u32(sB + 640 + rg, xa1);
                 // db2[o] = sum over rows of g_out
                 {
                     float d[4] = {gmu[0] + gmu[2], gmu[1] + gmu[3], gar[0] + gar[2], gar[1] + gar[3]};
@@ -887,8 +880,9 @@ __global__ void __launch_bounds__((W + 1) * 32, 1) grad_kernel(const uint32_t* _
                     mma_k8(c1, xa0, xa1, wa.y);
                     // g_h = g_out W2 for these units, then through the ReLU
                     float d0[4] = {0.f, 0.f, 0.f, 0.f}, d1[4] = {0.f, 0.f, 0.f, 0.f};
-                    mma_k16(d0, A0, A1, A2, A3, v.w2t[(16 * s + g) * 12 + t], v.w2t[(16 * s + g) * 12 + 4 + t]);
-                    mma_k16(d1, A0, A1, A2, A3, v.w2t[(16 * s + 8 + g) * 12 + t], v.w2t[(16 * s + 8 + g) * 12 + 4 + t]);
+                    mma_k16(d0, A0, A1, A2, A3, v.w2t[(16 * s + g) * 8 + (t ^ sw)], v.w2t[(16 * s + g) * 8 + (4 ^ sw) + t]);
+                    mma_k16(d1, A0, A1, A2, A3, v.w2t[(16 * s + 8 + g) * 8 + (t ^ sw)],
+                            v.w2t[(16 * s + 8 + g) * 8 + (4 ^ sw) + t]);
 #pragma unroll
                     for (int e = 0; e < 4; ++e) {
                         d0[e] = c0[e] > 0.f ? d0[e] : 0.f;
@@ -902,6 +896,15 @@ __global__ void __launch_bounds__((W + 1) * 32, 1) grad_kernel(const uint32_t* _
                     // 2q and 2q + 1 along M); a job's first chunk waits until the
                     // products of the warp's previous job have read the slot
                     if (q == 0 && job > 0) ok = mbar_wait(empty, (job - 1) & 1u) && ok;
+                    if (s == 0) {
+                        // the previous job was the previous block's last: the B slot is free
+                        st_u32(sB + rg, A0);
+                        st_u32(sB + 128 + rg, A1);
+                        st_u32(sB + 256 + rg, A2);
+                        st_u32(sB + 384 + rg, A3);
+                        st_u32(sB + 512 + rg, xa0);
+                        st_u32(sB + 640 + rg, xa1);
+                    }
                     unsigned char* a = sA + 512 * q + rg;
                     st_u32(a, pack2_relu(c0[0], c0[1]));
                     st_u32(a + 128, pack2_relu(c0[2], c0[3]));
@@ -946,7 +949,7 @@ __global__ void __launch_bounds__((W + 1) * 32, 1) grad_kernel(const uint32_t* _
                 const int c = (int)(n - bi * (uint32_t)C), b = K - 1 - (int)(bi % K);
                 const int d = b * C + c;
                 const uint32_t sa = smem_addr(smem + w * kTcSlot);
-                const uint32_t sb = sa + 2 * kTcHalf + (bi & 1u) * kTcB;
+                const uint32_t sb = sa + 2 * kTcHalf;
                 const uint32_t acc = (init >> d) & 1u;
                 init |= 1u << d;
                 tc_mma(tmem + 32 * d, tc_desc(sa), tc_desc(sb), acc);
@@ -975,8 +978,8 @@ __global__ void __launch_bounds__((W + 1) * 32, 1) grad_kernel(const uint32_t* _
     if (warp < W && done) {
         // warp w reads TMEM lanes 32 (w mod 4) .. + 31; the warps of a lane
         // quarter share its 2 D column groups
-        const int quarter = warp & 3;
-        for (int cc = warp >> 2; cc < 2 * D; cc += W / 4) {
+        const int quarter = warp & 3, per_quarter = (W - quarter + 3) / 4;
+        for (int cc = warp >> 2; cc < 2 * D; cc += per_quarter) {
             const int d = cc >> 1;
             if (!((init >> d) & 1u)) continue;   // uniform over the warp
             uint32_t v[16];
@@ -1218,7 +1221,8 @@ cudaError_t launch_grad(abc_maf f, const uint32_t* rows, uint32_t batch, uint64_
 {
     const uint64_t tiles = ((rows ? batch : max_n) + 15) / 16;
     const uint64_t narrow_ctas = (tiles + maf::kGradWarpsNarrow - 1) / maf::kGradWarpsNarrow * (uint64_t)f->R;
-    if (narrow_ctas > 2 * (uint64_t)sm_count() && grad_smem(f, maf::kGradWarpsWide) <= max_smem_optin())
+    // the wide form's dynamic shared memory, with 1 KB left for its static part
+    if (narrow_ctas > 2 * (uint64_t)sm_count() && grad_smem(f, maf::kGradWarpsWide) + 1024 <= max_smem_optin())
         return launch_grad_w<K, maf::kGradWarpsWide>(f, rows, batch, tiles, s);
     return launch_grad_w<K, maf::kGradWarpsNarrow>(f, rows, batch, tiles, s);
 }
