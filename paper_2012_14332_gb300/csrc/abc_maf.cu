@@ -158,6 +158,24 @@ __device__ __forceinline__ void mma_k16(float (&d)[4], uint32_t a0, uint32_t a1,
         : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
 
+// The same products as plain asm (no side effects): the compiler may
+// interleave independent chains, which the gradient kernel's backward pass
+// uses to overlap neighbouring chunks.
+__device__ __forceinline__ void mma_k8_p(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t b0)
+{
+    asm("mma.sync.aligned.m16n8k8.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5}, {%6}, {%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a0), "r"(a1), "r"(b0));
+}
+
+__device__ __forceinline__ void mma_k16_p(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                          uint32_t b0, uint32_t b1)
+{
+    asm("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
 struct BlockView {
     const uint32_t* w1;
     const uint32_t* w2;
@@ -461,7 +479,10 @@ __device__ __forceinline__ int inverse_pass(const BlockView& v, int H, int d, in
 }
 
 template <int K>
-__global__ void __launch_bounds__(kFwdThreads, kFwdMinBlocks) sample_kernel(const uint32_t* __restrict__ pub, int H, Box box,
+// box: read in place from the parameter space (indexing a by-value copy by
+// the lane's column put it in local memory)
+__global__ void __launch_bounds__(kFwdThreads, kFwdMinBlocks) sample_kernel(const uint32_t* __restrict__ pub, int H,
+                                                     const __grid_constant__ Box box,
                                                      const float* __restrict__ u_in, const __grid_constant__ ModelParams p,
                                                      uint32_t ctr3, uint64_t first, uint64_t n, float tau,
                                                      float log_tau, float* __restrict__ theta_out,
@@ -720,7 +741,8 @@ struct TrainSlot {
 // Dynamic shared memory: W slots of kTcSlot bytes, then the K blocks' published
 // operands.
 template <int K, int W>
-__global__ void __launch_bounds__((W + 1) * 32, 1) grad_kernel(const uint32_t* __restrict__ pub, int H, Box box,
+__global__ void __launch_bounds__((W + 1) * 32, 1) grad_kernel(const uint32_t* __restrict__ pub, int H,
+                                                               const __grid_constant__ Box box,
                                                                const TrainSlot* __restrict__ slots,
                                                                const uint32_t* __restrict__ rows_all, uint32_t batch,
                                                                float* __restrict__ grad, float* __restrict__ sums,
@@ -869,20 +891,22 @@ __global__ void __launch_bounds__((W + 1) * 32, 1) grad_kernel(const uint32_t* _
                         atomicAdd(&gb2[16 * b + 9 + 2 * t], d[3]);
                     }
                 }
-                float accx[4] = {0.f, 0.f, 0.f, 0.f};
-                for (int s = 0; s < chunks; ++s) {
+                // one 16-unit chunk; even and odd chunks keep separate g_x sums
+                // (independent chains the compiler can interleave)
+                auto chunk = [&](int s, float (&accx)[4]) {
                     const int q = s & 7;   // chunk within the 128-unit half
                     // recompute the pre-activations of hidden units 16s .. 16s+15
                     const uint2 wa = reinterpret_cast<const uint2*>(v.w1)[(s * 8 + g) * 4 + t];
                     const float4 bq = reinterpret_cast<const float4*>(v.b1)[s * 4 + t];
                     float c0[4] = {bq.x, bq.y, bq.x, bq.y}, c1[4] = {bq.z, bq.w, bq.z, bq.w};
-                    mma_k8(c0, xa0, xa1, wa.x);
-                    mma_k8(c1, xa0, xa1, wa.y);
+                    mma_k8_p(c0, xa0, xa1, wa.x);
+                    mma_k8_p(c1, xa0, xa1, wa.y);
                     // g_h = g_out W2 for these units, then through the ReLU
+                    const uint32_t* w2r0 = v.w2t + (16 * s + g) * 8;
+                    const uint32_t* w2r1 = w2r0 + 64;
                     float d0[4] = {0.f, 0.f, 0.f, 0.f}, d1[4] = {0.f, 0.f, 0.f, 0.f};
-                    mma_k16(d0, A0, A1, A2, A3, v.w2t[(16 * s + g) * 8 + (t ^ sw)], v.w2t[(16 * s + g) * 8 + (4 ^ sw) + t]);
-                    mma_k16(d1, A0, A1, A2, A3, v.w2t[(16 * s + 8 + g) * 8 + (t ^ sw)],
-                            v.w2t[(16 * s + 8 + g) * 8 + (4 ^ sw) + t]);
+                    mma_k16_p(d0, A0, A1, A2, A3, w2r0[t ^ sw], w2r0[(4 ^ sw) + t]);
+                    mma_k16_p(d1, A0, A1, A2, A3, w2r1[t ^ sw], w2r1[(4 ^ sw) + t]);
 #pragma unroll
                     for (int e = 0; e < 4; ++e) {
                         d0[e] = c0[e] > 0.f ? d0[e] : 0.f;
@@ -891,7 +915,7 @@ __global__ void __launch_bounds__((W + 1) * 32, 1) grad_kernel(const uint32_t* _
                     const uint32_t P0 = pack2(d0[0], d0[1]), P1 = pack2(d0[2], d0[3]);
                     const uint32_t P2 = pack2(d1[0], d1[1]), P3 = pack2(d1[2], d1[3]);
                     // g_x += g_a1 W1 (this chunk's 16 hidden units as k)
-                    mma_k16(accx, P0, P1, P2, P3, v.w1t[g * hw + 8 * s + t], v.w1t[g * hw + 8 * s + 4 + t]);
+                    mma_k16_p(accx, P0, P1, P2, P3, v.w1t[g * hw + 8 * s + t], v.w1t[g * hw + 8 * s + 4 + t]);
                     // h and g_a1 of these units into the A slot (core matrices
                     // 2q and 2q + 1 along M); a job's first chunk waits until the
                     // products of the warp's previous job have read the slot
@@ -920,9 +944,16 @@ __global__ void __launch_bounds__((W + 1) * 32, 1) grad_kernel(const uint32_t* _
                         if (lane == 0) mbar_arrive(full);
                         ++job;
                     }
+                };
+                float ax0[4] = {0.f, 0.f, 0.f, 0.f}, ax1[4] = {0.f, 0.f, 0.f, 0.f};
+                int s = 0;
+                for (; s + 1 < chunks; s += 2) {
+                    chunk(s, ax0);
+                    chunk(s + 1, ax1);
                 }
+                if (s < chunks) chunk(s, ax0);
 #pragma unroll
-                for (int e = 0; e < 4; ++e) gx[e] = gxd[e] + accx[e];
+                for (int e = 0; e < 4; ++e) gx[e] = gxd[e] + (ax0[e] + ax1[e]);
             }
         }
         if (!ok && lane == 0) atomicExch(err, 1);
