@@ -357,6 +357,15 @@ int32_t abc_maf_flow_count(abc_maf maf);
  * bulk; a base broader than the fitted one keeps covering them. */
 abc_status abc_maf_set_proposal_scale(abc_maf maf, float tau);
 
+/* Testing hook for the gradient kernel's bounded waits. With hold != 0 the
+ * thread that issues the kernel's tensor-core products issues none, so the
+ * kernel's final wait for them runs out (after 2 s): abc_maf_gradient and the
+ * training calls then return ABC_ERR_TIMEOUT and leave the flow's gradient
+ * unspecified. hold = 0 (the default) restores normal operation; the CUDA
+ * context stays usable throughout. Applies to launches after the call (a
+ * captured training step is rebuilt). */
+abc_status abc_maf_test_hold_products(abc_maf maf, int32_t hold);
+
 /* Random initial parameters: W1 ~ N(0, scale^2 / 8), W2 ~ N(0, scale^2 / hidden),
  * zero biases (so the ReLU units start active and the flow near the base
  * density), from a host generator seeded with `seed`; resets Adam. */

@@ -170,6 +170,8 @@ def load(path=None):
         L.abc_maf_flow_count.restype = ctypes.c_int32
         L.abc_maf_set_proposal_scale.argtypes = [pp, ctypes.c_float]
         L.abc_maf_set_proposal_scale.restype = ctypes.c_int
+        L.abc_maf_test_hold_products.argtypes = [pp, ctypes.c_int32]
+        L.abc_maf_test_hold_products.restype = ctypes.c_int
         L.abc_maf_sample_at.argtypes = [pp, i32, u64, vp, u64, u32, u64, vp, vp, vp]
         L.abc_maf_log_q_at.argtypes = [pp, i32, u64, vp, vp, vp]
         L.abc_maf_train_flows.argtypes = [pp, vp, vp, vp, i32, i32, ctypes.c_float, u64, ctypes.c_float, vp, vp]
@@ -619,6 +621,11 @@ class Flow:
         """Sample and evaluate with the base broadened by tau (training is unaffected)."""
         _check(self._L, self._L.abc_maf_set_proposal_scale(self._h, float(tau)))
 
+    def test_hold_products(self, hold):
+        """Testing hook: the gradient kernel issues no tensor-core products, so
+        its bounded wait runs out and gradient/training raise ABC_ERR_TIMEOUT."""
+        _check(self._L, self._L.abc_maf_test_hold_products(self._h, int(bool(hold))))
+
     def set_params(self, params):
         """params: [n_params] (one flow) or [n_flows, n_params]."""
         v = np.ascontiguousarray(np.asarray(params, dtype=np.float32).ravel())
@@ -765,6 +772,10 @@ def abc_maf_flow_count(flow):
 
 def abc_maf_set_proposal_scale(flow, tau):
     flow.set_proposal_scale(tau)
+
+
+def abc_maf_test_hold_products(flow, hold):
+    flow.test_hold_products(hold)
 
 
 def abc_maf_sample_at(flow, r, n, **kw):

@@ -746,7 +746,7 @@ __global__ void __launch_bounds__((W + 1) * 32, 1) grad_kernel(const uint32_t* _
                                                                const TrainSlot* __restrict__ slots,
                                                                const uint32_t* __restrict__ rows_all, uint32_t batch,
                                                                float* __restrict__ grad, float* __restrict__ sums,
-                                                               int* __restrict__ err)
+                                                               int* __restrict__ err, int hold)
 {
     static_assert(W >= 4 && W <= 15, "at least one compute warp per TMEM lane quarter; 16 warps in all at most");
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -957,6 +957,9 @@ __global__ void __launch_bounds__((W + 1) * 32, 1) grad_kernel(const uint32_t* _
             }
         }
         if (!ok && lane == 0) atomicExch(err, 1);
+    } else if (lane == 0 && hold) {
+        // testing: no products, so the wait for bar_done below runs out
+        init_s = 0;
     } else if (lane == 0) {
         // the issuing thread: jobs of warp w in its order (tile, block K-1..0, half)
         uint32_t next[W], total[W], remaining = 0;
@@ -1102,6 +1105,7 @@ struct abc_maf_s {
     uint32_t* d_pub = nullptr; // [R][K][pub_words] published BF16 operands
     float* d_sums = nullptr;   // [R][2] (weighted loss sum, weight sum)
     int* d_err = nullptr;      // set by a gradient kernel whose bounded wait ran out
+    int hold = 0;              // testing: the gradient kernel issues no products
     int* d_step = nullptr;
     uint32_t* d_rows = nullptr;
     uint32_t rows_cap = 0;     // batch rows per flow
@@ -1243,7 +1247,7 @@ cudaError_t launch_grad_w(abc_maf f, const uint32_t* rows, uint32_t batch, uint6
     const uint64_t want = (tiles + W - 1) / W;
     const int grid = (int)(want < (uint64_t)sm_count() ? (want > 0 ? want : 1) : (uint64_t)sm_count());
     maf::grad_kernel<K, W><<<dim3(grid, f->R), (W + 1) * 32, smem, s>>>(f->d_pub, f->H, f->box, f->d_slots, rows,
-                                                                       batch, f->d_grad, f->d_sums, f->d_err);
+                                                                       batch, f->d_grad, f->d_sums, f->d_err, f->hold);
     return cudaGetLastError();
 }
 
@@ -1361,6 +1365,18 @@ abc_status abc_maf_create(int32_t n_blocks, int32_t hidden, const abc_prior_box*
 int64_t abc_maf_param_count(abc_maf f) { return f ? f->n_params : -1; }
 
 int32_t abc_maf_flow_count(abc_maf f) { return f ? f->R : -1; }
+
+abc_status abc_maf_test_hold_products(abc_maf f, int32_t hold)
+{
+    abc_status st;
+    if ((st = check(f)) != ABC_OK) return st;
+    f->hold = hold != 0;
+    if (f->graph) {
+        cudaGraphExecDestroy(f->graph);
+        f->graph = nullptr;
+    }
+    return plan_ok();
+}
 
 abc_status abc_maf_set_proposal_scale(abc_maf f, float tau)
 {

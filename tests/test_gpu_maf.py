@@ -108,10 +108,16 @@ def test_zero_flow_draws_the_prior_from_the_documented_words():
     f.close()
 
 
-def test_gradient_matches_oracle():
-    K, H = 3, 64
-    f, params = _flow(K, H, 31, 0.7)
-    n = 4096
+@pytest.mark.parametrize("K,H,n,scale", [(3, 64, 4096, 0.7), (2, 208, 3000, 0.7), (4, 256, 2069, 0.5),
+                                         (1, 144, 1000, 0.7)])
+def test_gradient_matches_oracle(K, H, n, scale):
+    """The weight gradients accumulate in tensor memory per 128-unit half:
+    H = 64 and 144 and 208 leave the last half partly filled (its padding
+    lanes must be skipped), K = 4 x 256 uses all 256 allocated columns. Four
+    blocks initialised at scale 0.7 compound their exp(-alpha) factors into a
+    loss near 10^3 per point, where FP32 against FP64 differs by percents; at
+    0.5 the loss is about 19, like the other shapes'."""
+    f, params = _flow(K, H, 31, scale)
     th = _thetas(n, 7)
     w = np.random.default_rng(8).uniform(0.2, 2.0, size=n).astype(np.float32)
     loss, g = f.gradient(torch.from_numpy(th).to(DEV), torch.from_numpy(w).to(DEV))
@@ -132,13 +138,14 @@ def test_gradient_matches_oracle():
     f.close()
 
 
-@pytest.mark.parametrize("n", [2055, 2069])
-def test_wide_gradient_form_matches_the_narrow_one_and_the_oracle(n):
-    """A set of 16 flows takes the wide (16-warp) gradient kernel, chosen when
-    4-warp CTAs would run more than two waves; flow 0's gradient there equals
-    a one-flow object's (the 4-warp kernel) up to float summation order, and
-    the oracle's. Both point counts end in a partial tile."""
-    K, H, R = 3, 256, 16
+@pytest.mark.parametrize("K,H,n", [(3, 256, 2055), (3, 256, 2069), (2, 208, 2055)])
+def test_wide_gradient_form_matches_the_narrow_one_and_the_oracle(K, H, n):
+    """A set of 16 flows takes the wide (15 compute warps) gradient kernel,
+    chosen when 4-warp CTAs would run more than two waves; flow 0's gradient
+    there equals a one-flow object's (the 4-warp kernel) up to float summation
+    order, and the oracle's. The point counts end in a partial tile; H = 208
+    leaves the second 128-unit half partly filled."""
+    R = 16
     f1, params = _flow(K, H, 71, 0.5)
     fs = abc.Flow(K, H, n_flows=R)
     fs.set_params(np.stack([f1.get_params()] * R))
@@ -164,6 +171,24 @@ def test_wide_gradient_form_matches_the_narrow_one_and_the_oracle(n):
     assert np.all(g_w[zero] == 0)
     f1.close()
     fs.close()
+
+
+def test_gradient_wait_that_runs_out_reports_timeout_and_recovers():
+    """The gradient kernel's waits are bounded. With the issuing thread held
+    (no tensor-core products), its wait for them runs out after 2 s, the call
+    returns ABC_ERR_TIMEOUT, and the next call on the same flow gives the
+    same gradient as before."""
+    f, _ = _flow(1, 16, 41, 0.5)
+    th = torch.from_numpy(_thetas(16, 3)).to(DEV)
+    loss0, g0 = f.gradient(th)
+    f.test_hold_products(True)
+    with pytest.raises(abc.AbcError) as e:
+        f.gradient(th)
+    assert e.value.status == abc.binding.ABC_ERR_TIMEOUT
+    f.test_hold_products(False)
+    loss1, g1 = f.gradient(th)
+    assert loss1 == loss0 and np.array_equal(g1, g0)
+    f.close()
 
 
 def test_adam_step_matches_oracle():
