@@ -44,7 +44,7 @@ def _thetas(n, seed):
     return (LO + (HI - LO) * u).astype(np.float32)
 
 
-@pytest.mark.parametrize("K,H", [(3, 256), (1, 16), (2, 64), (4, 128)])
+@pytest.mark.parametrize("K,H", [(3, 256), (1, 16), (2, 64), (4, 128), (4, 256)])
 def test_log_q_matches_oracle(K, H):
     f, params = _flow(K, H, 10 + K, 0.3)
     th = _thetas(5003, K)
@@ -56,7 +56,7 @@ def test_log_q_matches_oracle(K, H):
     f.close()
 
 
-@pytest.mark.parametrize("K,H", [(3, 256), (2, 32)])
+@pytest.mark.parametrize("K,H", [(3, 256), (2, 32), (4, 256)])
 def test_sample_matches_oracle_inverse(K, H):
     f, params = _flow(K, H, 20 + K, 0.3)
     n = 3001
