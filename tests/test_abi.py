@@ -164,6 +164,9 @@ def test_other_entry_points_validate(L):
     bad = prior_box(hi=[0.0] * 8)
     assert L.abc_sample_until(ctypes.byref(bad), None, 1.0, 5, 10, 100, 1, 0, 1, 0, None, None, None, 0,
                               ctypes.byref(n1), ctypes.byref(n2), None) == ABC_ERR_INVALID_ARG
+    # flow calls on a NULL flow return before any CUDA call
+    assert L.abc_maf_test_hold_products(None, 1) == ABC_ERR_INVALID_ARG
+    assert "NULL" in L.abc_last_error().decode()
 
 
 def test_zero_samples_is_a_no_op(L):
