@@ -155,36 +155,63 @@ def log_q_theta(theta, params, lo, hi, bf16=False, tau=1.0):
     return logq_y - log_jacobian_y(y, lo, hi)
 
 
-def loss_and_grad(y, w, params):
-    """Weighted mean of -log q_y(y) and its gradient with respect to every parameter."""
+def loss_and_grad(y, w, params, bf16=False, with_scale=False):
+    """Weighted mean of -log q_y(y) and its gradient with respect to every parameter.
+
+    bf16=True follows the precision of a BF16 tensor-core backward pass with
+    FP32 sums: the forward pass as made(bf16=True); every operand entering a
+    backward matrix product is rounded to bfloat16 (g_out = (g_mu, g_alpha_raw)
+    and the masked W2 for g_h = g_out W2; g_a1 and the masked W1 for
+    g_x = g_a1 W1; h, g_out, g_a1 and x for the weight gradients; g_a1 for
+    db1 = sum of g_a1 over rows), db2 stays the sum of the unrounded g_out.
+    The per-row weights enter unnormalised (w, not w / sum w), as they do on
+    a device that sums w (-log q) over the rows, and the gradient is divided
+    by sum w at the end: rounding to bfloat16 commutes with a power-of-two
+    scale only, so the scale must be applied where the device applies it.
+
+    with_scale=True also returns, per gradient entry, the sum over rows of the
+    absolute values of its terms (each product's |a| |b|, divided by sum w):
+    the natural scale of that entry's rounding error."""
     H = params[0]["W1"].shape[0]
     M1, M2 = masks(H)
     w = np.asarray(w, dtype=np.float64)
     W = w.sum()
-    zK, logq, caches = forward(y, params)
+    rb = round_bf16 if bf16 else (lambda a: a)
+    wr = w if bf16 else w / W                      # row weights in the backward pass
+    zK, logq, caches = forward(y, params, bf16=bf16)
     loss = -(w * logq).sum() / W
-    g_x = (w / W)[:, None] * base_grad(zK)         # d loss / d (final x)
+    g_x = wr[:, None] * base_grad(zK)              # d loss / d (final x)
     grads = [None] * len(params)
+    scales = [None] * len(params)
     for k in reversed(range(len(params))):
         c, p = caches[k], params[k]
         g_z = g_x[:, ::-1]                         # undo the reversal after block k
         e = np.exp(-c["alpha"])
         g_xdirect = g_z * e
         g_mu = -g_z * e
-        # d loss / d alpha: -g_z z (through z = (x - mu) e^-alpha) + w/W (log-det term)
-        g_alpha = -g_z * c["z"] + (w / W)[:, None]
+        # d loss / d alpha: -g_z z (through z = (x - mu) e^-alpha) + w (log-det term)
+        g_alpha = -g_z * c["z"] + wr[:, None]
         g_araw = g_alpha * (1.0 - (c["alpha"] / ALPHA_MAX) ** 2)
         g_out = np.concatenate([g_mu, g_araw], axis=1)          # [N, 2D]
-        W2m = p["W2"] * M2
-        gW2 = (g_out.T @ c["h"]) * M2
+        gob, hb, xb = rb(g_out), rb(c["h"]), rb(c["x"])
+        W2m, W1m = rb(p["W2"] * M2), rb(p["W1"] * M1)
+        gW2 = (gob.T @ hb) * M2
         gb2 = g_out.sum(axis=0)
-        g_h = g_out @ W2m
-        g_a1 = g_h * (c["a1"] > 0)
-        W1m = p["W1"] * M1
-        gW1 = (g_a1.T @ c["x"]) * M1
+        g_h = gob @ W2m
+        g_a1 = rb(g_h * (c["a1"] > 0))
+        gW1 = (g_a1.T @ xb) * M1
         gb1 = g_a1.sum(axis=0)
         g_x = g_xdirect + g_a1 @ W1m
         grads[k] = dict(W1=gW1, b1=gb1, W2=gW2, b2=gb2)
+        if with_scale:
+            scales[k] = dict(W1=(np.abs(g_a1).T @ np.abs(xb)) * M1, b1=np.abs(g_a1).sum(axis=0),
+                             W2=(np.abs(gob).T @ np.abs(hb)) * M2, b2=np.abs(g_out).sum(axis=0))
+    if bf16:
+        grads = [{key: v / W for key, v in g.items()} for g in grads]
+    if with_scale:
+        sw = W if bf16 else 1.0
+        scales = [{key: v / sw for key, v in g.items()} for g in scales]
+        return loss, grads, scales
     return loss, grads
 
 

@@ -19,7 +19,10 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <random>
+#include <utility>
 #include <vector>
 
 #include <cuda_bf16.h>
@@ -922,8 +925,10 @@ __global__ void __launch_bounds__((W + 1) * 32, 1) grad_kernel(const uint32_t* _
                     mma_k16_p(accx, P0, P1, P2, P3, v.w1t[g * hw + 8 * s + t], v.w1t[g * hw + 8 * s + 4 + t]);
                     // h and g_a1 of these units into the A slot (core matrices
                     // 2q and 2q + 1 along M); a job's first chunk waits until the
-                    // products of the warp's previous job have read the slot
-                    if (q == 0 && job > 0) ok = mbar_wait(empty, (job - 1) & 1u) && ok;
+                    // products of the warp's previous job have read the slot;
+                    // after one wait has run out the warp skips the rest, so a
+                    // failed call returns within about one wait limit
+                    if (q == 0 && job > 0 && ok) ok = mbar_wait(empty, (job - 1) & 1u);
                     if (s == 0) {
                         // the previous job was the previous block's last: the B slot is free
                         st_u32(sB + rg, A0);
@@ -1198,10 +1203,23 @@ int fill_grid(Kern k, int threads, size_t smem, uint64_t want)
 }
 
 
+// The kernel's dynamic shared-memory limit (one value per kernel and device)
+// is only ever raised, so flows of different sizes used from several host
+// threads never lower it under a launch that needs more.
 template <typename Kern>
 cudaError_t allow_smem(Kern k, size_t bytes)
 {
-    return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    static std::mutex mu;
+    static std::map<std::pair<const void*, int>, size_t> limit;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    size_t& lim = limit[std::make_pair((const void*)k, dev)];
+    if (lim >= bytes) return cudaSuccess;
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) lim = bytes;
+    return e;
 }
 
 const uint32_t* flow_pub(abc_maf f, int r) { return f->d_pub + (size_t)r * f->K * f->pub_words; }

@@ -214,3 +214,118 @@ def test_edge_points_are_clamped_inside():
                  np.array([1, 100, 2, 1, 1, 1, 1, 2.0]))
     assert np.all(np.isfinite(y))
     assert np.isclose(y[0, 0], np.log(2.0**-24) - np.log1p(-2.0**-24))
+
+
+# --------------------------------------------------------------------------
+# the bf16 mode of the backward pass (what the device's gradient is held to)
+# --------------------------------------------------------------------------
+def test_bf16_gradient_is_the_float64_gradient_with_rounded_operands(params, monkeypatch):
+    """With the rounding made the identity, the bf16-mode backward pass is the
+    float64 one (pinned against finite differences above) up to where the
+    row weights are normalised; with rounding it stays within bfloat16's
+    relative precision of it."""
+    rng = np.random.default_rng(21)
+    y = rng.normal(size=(300, 8))
+    w = rng.uniform(0.2, 2.0, size=300)
+    loss, grads, scales = maf.loss_and_grad(y, w, params, with_scale=True)
+    lb, gb, sb = maf.loss_and_grad(y, w, params, bf16=True, with_scale=True)
+    g, g_b = maf.flat(grads), maf.flat(gb)
+    assert np.linalg.norm(g_b - g) < 1e-2 * np.linalg.norm(g) and abs(lb - loss) < 1e-2 * abs(loss)
+    monkeypatch.setattr(maf, "round_bf16", lambda a: np.asarray(a, dtype=np.float64))
+    li, gi, si = maf.loss_and_grad(y, w, params, bf16=True, with_scale=True)
+    assert abs(li - loss) <= 1e-12 * abs(loss)
+    assert np.allclose(maf.flat(gi), g, rtol=1e-10, atol=1e-14 * np.abs(g).max())
+    assert np.allclose(maf.flat(si), maf.flat(scales), rtol=1e-10, atol=0)
+    # the scale bounds the value: |sum of terms| <= sum of |terms|
+    assert np.all(np.abs(g) <= maf.flat(scales) * (1 + 1e-12) + 1e-300)
+
+
+def _device_like_gradient(y, w, params):
+    """The gradient in the device's arithmetic, emulated on the CPU: float32
+    everywhere, bfloat16 operands at every product, the row weights
+    unnormalised until the end (an independent restatement of the backward
+    pass, used to size the element-wise tolerance)."""
+    f32 = np.float32
+
+    def rb(a):
+        return maf.round_bf16(a).astype(f32)
+
+    H = params[0]["W1"].shape[0]
+    M1, M2 = maf.masks(H)
+    x, w = y.astype(f32), w.astype(f32)
+    caches = []
+    for p in params:
+        W1, W2 = rb(p["W1"] * M1), rb(p["W2"] * M2)
+        xb = rb(x)
+        a1 = (xb @ W1.T).astype(f32) + p["b1"].astype(f32)
+        hb = rb(np.maximum(a1, 0))
+        out = (hb @ W2.T).astype(f32) + p["b2"].astype(f32)
+        mu, al = out[:, :8], (6 * np.tanh(out[:, 8:] / 6)).astype(f32)
+        z = ((x - mu) * np.exp(-al)).astype(f32)
+        caches.append(dict(xb=xb, a1=a1, hb=hb, al=al, z=z, W1=W1, W2=W2))
+        x = z[:, ::-1]
+    gx = (w[:, None] * np.tanh(0.5 * x)).astype(f32)
+    out = [None] * len(params)
+    for k in reversed(range(len(params))):
+        c = caches[k]
+        gz = gx[:, ::-1]
+        ex = np.exp(-c["al"]).astype(f32)
+        r = c["al"] / f32(6)
+        gout = np.concatenate([-gz * ex, (-gz * c["z"] + w[:, None]) * (f32(1) - r * r)], 1).astype(f32)
+        gob = rb(gout)
+        ga1 = rb(np.where(c["a1"] > 0, (gob @ c["W2"]).astype(f32), 0))
+        out[k] = dict(W1=(ga1.T @ c["xb"]).astype(f32) * M1, b1=ga1.sum(0), W2=(gob.T @ c["hb"]).astype(f32) * M2,
+                      b2=gout.sum(0))
+        gx = (gz * ex + (ga1 @ c["W1"]).astype(f32)).astype(f32)
+    return maf.flat(out).astype(np.float64) / float(w.sum())
+
+
+@pytest.mark.parametrize("K,H,n", [(3, 64, 2000), (2, 208, 1500), (4, 256, 1100)])
+def test_elementwise_gradient_bound_passes_device_arithmetic_and_fails_planted_mistakes(K, H, n):
+    """The element-wise bound of tests/grad_check.py holds for the float32
+    emulation of the device's arithmetic and fails for plausible mistakes:
+    a sign on one block's db1, a factor of two on one 16-column group of one
+    block's dW2 (one tensor-memory column group: 16 outputs x one 128-unit
+    half), one input column of dW1 dropped, and the W1 gradients of two
+    blocks exchanged."""
+    from tests import grad_check
+    rng = np.random.default_rng(K * 1000 + H)
+    ps = maf.init_params(rng, K=K, H=H, scale=0.5)
+    for p in ps:
+        p["b1"] = rng.normal(0, 0.2, H)
+        p["b2"] = rng.normal(0, 0.2, 16)
+    ps = maf.unflat(maf.flat(ps).astype(np.float32).astype(np.float64), K, H)
+    y = maf.to_y(rng.uniform(0.02, 0.98, size=(n, 8)), np.zeros(8), np.ones(8))
+    w = rng.uniform(0.2, 2.0, size=n).astype(np.float32).astype(np.float64)
+    _, gr, sc = maf.loss_and_grad(y, w, ps, bf16=True, with_scale=True)
+    gref, scale = maf.flat(gr), maf.flat(sc)
+    g = _device_like_gradient(y, w, ps)
+    err, stray = grad_check.gradient_errors(g, gref, scale)
+    assert stray == 0 and grad_check.gradient_close(g, gref, scale), grad_check.summary(err)
+    # the layout of one block in the flat vector: W1 [H][8], b1 [H], W2 [16][H], b2 [16]
+    size = 8 * H + H + 16 * H + 16
+
+    def planted(fn):
+        bad = [dict((key, v.copy()) for key, v in blk.items()) for blk in maf.unflat(g, K, H)]
+        fn(bad)
+        return maf.flat(bad)
+
+    def flip_db1(b):
+        b[0]["b1"] *= -1
+
+    def double_w2_group(b):
+        b[K - 1]["W2"][8:, :min(H, 128)] *= 2
+
+    def drop_w1_column(b):
+        b[0]["W1"][:, 3] = 0
+
+    def swap_w1(b):
+        if K > 1:
+            b[0]["W1"], b[1]["W1"] = b[1]["W1"], b[0]["W1"]
+        else:
+            b[0]["W1"] = b[0]["W1"][::-1]
+
+    for fn in (flip_db1, double_w2_group, drop_w1_column, swap_w1):
+        bad = planted(fn)
+        assert len(bad) == K * size
+        assert not grad_check.gradient_close(bad, gref, scale), fn.__name__
