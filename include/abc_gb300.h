@@ -183,8 +183,10 @@ abc_status abc_step(const float* theta, const int32_t* state_in, const uint64_t*
 
 /* The k-th smallest (1-based, 1 <= k <= n) of n non-negative distances
  * (DEVICE double [n], e.g. from abc_distances), returned in *eps_out (HOST).
- * Used to set eps to a distance quantile. Synchronizes cuda_stream. Uses device
- * scratch (a histogram) allocated stream-ordered and freed before returning. */
+ * Used to set eps to a distance quantile. +infinity is allowed; any NaN,
+ * negative value or -0 returns ABC_ERR_INVALID_ARG (their bit patterns do not
+ * order like values). Synchronizes cuda_stream. Uses device scratch (a
+ * histogram) allocated stream-ordered and freed before returning. */
 abc_status abc_kth_smallest(const double* dist, uint64_t n, uint64_t k, double* eps_out,
                             void* cuda_stream);
 
@@ -625,7 +627,8 @@ abc_status abc_pmc_weights(const float* theta_new, uint64_t n, const float* thet
  * scope in this library, so every GPU that loads the library holds it until the
  * process exits. The first call on each device looks up that array's device
  * address with the device current (a one-time set-up done by that call); make
- * the first call on a device before any stream capture. All calls share the one
+ * the first call on a device before any stream capture. If that lookup fails,
+ * the call returns ABC_ERR_CUDA and the next call on the device tries again. All calls share the one
  * array and each call zeroes the counters it uses: calls that overlap on the GPU
  * (different streams or host threads) race on it and must be serialized by the
  * caller. Calls no cudaMalloc, cudaMallocAsync or cudaFree. */

@@ -254,23 +254,27 @@ namespace {
 constexpr int kNoallocMaxDevices = 256;
 
 struct NoallocDevice {
-    std::once_flag once;
-    void* ptr = nullptr;
-    cudaError_t err = cudaSuccess;
+    std::mutex mu;
+    void* ptr = nullptr;   // set once a lookup on this device has succeeded
 };
 
 NoallocDevice g_noalloc_devices[kNoallocMaxDevices];
 
-// Device address of abc_noalloc_scratch on the current device, looked up once
-// per device (with that device current) and kept for the life of the process.
+// Device address of abc_noalloc_scratch on the current device, looked up with
+// that device current. A successful lookup is kept for the life of the
+// process; a failed one is not, so a later call retries it.
 abc_status noalloc_scratch(void** out)
 {
     int dev = 0;
     CUDA_TRY(cudaGetDevice(&dev), "cudaGetDevice");
     if (dev < 0 || dev >= kNoallocMaxDevices) return fail(ABC_ERR_INVALID_ARG, "device ordinal %d too large", dev);
     NoallocDevice& d = g_noalloc_devices[dev];
-    std::call_once(d.once, [&d]() { d.err = cudaGetSymbolAddress(&d.ptr, abc_noalloc_scratch); });
-    if (d.err != cudaSuccess) return cuda_fail(d.err, "cudaGetSymbolAddress(abc_noalloc_scratch)");
+    std::lock_guard<std::mutex> lock(d.mu);
+    if (!d.ptr) {
+        void* p = nullptr;
+        CUDA_TRY(cudaGetSymbolAddress(&p, abc_noalloc_scratch), "cudaGetSymbolAddress(abc_noalloc_scratch)");
+        d.ptr = p;
+    }
     *out = d.ptr;
     return ABC_OK;
 }
@@ -643,9 +647,9 @@ abc_status abc_kth_smallest(const double* dist, uint64_t n, uint64_t k, double* 
     cudaStream_t s = (cudaStream_t)cuda_stream;
     abc_status st;
     Scratch sc;
-    if ((st = alloc_scratch(sc, 256 * sizeof(unsigned long long), s)) != ABC_OK) return st;
+    if ((st = alloc_scratch(sc, 257 * sizeof(unsigned long long), s)) != ABC_OK) return st;
     unsigned long long* hist_d = (unsigned long long*)sc.ptr;
-    unsigned long long hist[256];
+    unsigned long long hist[257];
     uint64_t prefix = 0, mask = 0, rank = k;   // rank: 1-based rank within the current prefix
     for (int shift = 56; shift >= 0; shift -= 8) {
         CUDA_TRY(cudaMemsetAsync(hist_d, 0, sizeof hist, s), "cudaMemsetAsync(hist)");
@@ -653,13 +657,15 @@ abc_status abc_kth_smallest(const double* dist, uint64_t n, uint64_t k, double* 
         CUDA_TRY(abcgb::launch_digit_histogram(dist, n, prefix, mask, shift, hist_d, s), "digit_histogram launch");
         CUDA_TRY(cudaMemcpyAsync(hist, hist_d, sizeof hist, cudaMemcpyDeviceToHost, s), "cudaMemcpyAsync(hist)");
         CUDA_TRY(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+        // first pass: keys that are NaN or carry the sign bit do not order like values
+        if (shift == 56 && hist[256] != 0)
+            return fail(ABC_ERR_INVALID_ARG, "%llu distances are negative, -0 or NaN", hist[256]);
         uint64_t below = 0;
         int digit = 0;
         for (; digit < 256; ++digit) {
             if (below + hist[digit] >= rank) break;
             below += hist[digit];
         }
-        if (digit == 256) return fail(ABC_ERR_INVALID_ARG, "distances contain negative values or NaN");
         rank -= below;
         prefix |= (uint64_t)digit << shift;
         mask |= (uint64_t)0xFF << shift;

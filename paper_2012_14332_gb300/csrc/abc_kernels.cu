@@ -6,6 +6,7 @@
 #include <map>
 #include <mutex>
 #include <tuple>
+#include <utility>
 #include <cuda_runtime.h>
 
 #include "abc_kernels.h"
@@ -265,6 +266,7 @@ __global__ void __launch_bounds__(kBlockThreads) abc_step_kernel(const __grid_co
 // of two with INT_MAX), then order statistics floor(q (B - 1)).
 // ---------------------------------------------------------------------------
 constexpr int kBandThreads = 1024;
+constexpr uint32_t kBandMaxB = 8192;   // the largest B the C ABI accepts (power of two)
 
 __global__ void __launch_bounds__(kBandThreads) band_kernel(const int32_t* __restrict__ traj, uint32_t B, int32_t T,
                                                              const float* __restrict__ qpos, int32_t n_q,
@@ -302,22 +304,27 @@ __global__ void __launch_bounds__(kBandThreads) band_kernel(const int32_t* __res
 // ---------------------------------------------------------------------------
 // Radix select of the k-th smallest distance: histogram of one 8-bit digit of
 // the keys (the bit patterns of non-negative doubles order like the values)
-// among the keys whose higher digits equal `prefix`.
+// among the keys whose higher digits equal `prefix`. On the first pass
+// (prefix_mask == 0) hist[256] counts the keys above +infinity's pattern:
+// NaN and anything with the sign bit set (negative values and -0), which
+// would not order like their values.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kBlockThreads) digit_histogram_kernel(const double* __restrict__ dist, uint64_t n,
                                                                         uint64_t prefix, uint64_t prefix_mask,
                                                                         int shift, unsigned long long* __restrict__ hist)
 {
-    __shared__ unsigned int h[256];
-    for (int b = threadIdx.x; b < 256; b += blockDim.x) h[b] = 0;
+    __shared__ unsigned int h[257];
+    for (int b = threadIdx.x; b < 257; b += blockDim.x) h[b] = 0;
     __syncthreads();
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const bool first = prefix_mask == 0;
     for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
         const uint64_t key = (uint64_t)__double_as_longlong(dist[j]);
         if ((key & prefix_mask) == prefix) atomicAdd(&h[(key >> shift) & 0xFFu], 1u);
+        if (first && key > 0x7FF0000000000000ull) atomicAdd(&h[256], 1u);
     }
     __syncthreads();
-    for (int b = threadIdx.x; b < 256; b += blockDim.x)
+    for (int b = threadIdx.x; b < 257; b += blockDim.x)
         if (h[b]) atomicAdd(&hist[b], (unsigned long long)h[b]);
 }
 
@@ -326,35 +333,40 @@ __global__ void __launch_bounds__(kBlockThreads) digit_histogram_kernel(const do
 // ---------------------------------------------------------------------------
 // Resident blocks per SM times the SM count, for a kernel, dynamic shared
 // memory size and device; looked up once and cached (the launch path then
-// makes no attribute or occupancy query).
+// makes no occupancy query). The kernel's dynamic shared-memory limit is one
+// value per kernel and device: it is only ever raised, to the largest size
+// launched so far, so a call with a shorter horizon never lowers it below
+// what a cached longer one needs.
 template <typename K>
 static cudaError_t grid_for(K kernel, size_t smem, int* grid)
 {
     static std::mutex mu;
     static std::map<std::tuple<const void*, int, size_t>, int> cache;
+    static std::map<std::pair<const void*, int>, size_t> limit;   // largest limit set per kernel and device
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    const auto key = std::make_tuple((const void*)kernel, dev, smem);
-    {
-        std::lock_guard<std::mutex> lock(mu);
-        auto it = cache.find(key);
-        if (it != cache.end()) {
-            *grid = it->second;
-            return cudaSuccess;
+    std::lock_guard<std::mutex> lock(mu);
+    if (smem > 48 * 1024) {
+        size_t& lim = limit[std::make_pair((const void*)kernel, dev)];
+        if (lim < smem) {
+            e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            lim = smem;
         }
+    }
+    const auto key = std::make_tuple((const void*)kernel, dev, smem);
+    auto it = cache.find(key);
+    if (it != cache.end()) {
+        *grid = it->second;
+        return cudaSuccess;
     }
     int sms = 0, per_sm = 0;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    if (smem > 48 * 1024) {
-        e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kBlockThreads, smem);
     if (e != cudaSuccess) return e;
     *grid = sms * (per_sm > 0 ? per_sm : 1);
-    std::lock_guard<std::mutex> lock(mu);
     cache[key] = *grid;
     return cudaSuccess;
 }
@@ -454,12 +466,24 @@ cudaError_t launch_step(const ModelParams& p, const StepArgs& a, int mode, cudaS
 cudaError_t launch_bands(const int32_t* traj, uint32_t B, int32_t T, const float* qpos, int32_t n_q, float* bands,
                          cudaStream_t s)
 {
+    if (B < 1 || B > kBandMaxB) return cudaErrorInvalidValue;
     uint32_t n2 = 1;
     while (n2 < B) n2 <<= 1;
     const size_t smem = sizeof(int32_t) * n2;
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(band_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        // set once per device to the largest size B <= ABC_PROJECT_MAX_B can need
+        static std::mutex mu;
+        static std::map<int, bool> done;
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
         if (e != cudaSuccess) return e;
+        std::lock_guard<std::mutex> lock(mu);
+        if (!done[dev]) {
+            e = cudaFuncSetAttribute(band_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)(sizeof(int32_t) * kBandMaxB));
+            if (e != cudaSuccess) return e;
+            done[dev] = true;
+        }
     }
     band_kernel<<<3 * (T + 1), kBandThreads, smem, s>>>(traj, B, T, qpos, n_q, bands);
     return cudaGetLastError();

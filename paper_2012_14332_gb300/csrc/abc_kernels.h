@@ -104,6 +104,8 @@ cudaError_t launch_simulate(const ModelParams& p, const SimulateArgs& a, int mod
 cudaError_t launch_step(const ModelParams& p, const StepArgs& a, int mode, cudaStream_t s);
 cudaError_t launch_bands(const int32_t* traj, uint32_t B, int32_t T, const float* qpos, int32_t n_q, float* bands,
                          cudaStream_t s);
+// hist: 257 counters, zeroed by the caller; [256] counts invalid keys on the
+// first pass (prefix_mask == 0)
 cudaError_t launch_digit_histogram(const double* dist, uint64_t n, uint64_t prefix, uint64_t prefix_mask, int shift,
                                    unsigned long long* hist, cudaStream_t s);
 

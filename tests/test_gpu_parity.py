@@ -223,6 +223,93 @@ def test_edge_cases():
     assert np.all(th.cpu().numpy() == lo)
 
 
+# P = 2^31 - 1 with 10^9 initially active: the daily differences reach 2^31,
+# so sums of squares cross 2^62 and 2^63. Series "mixed" puts about half the
+# samples between 2^62 and 2^63 and some past 2^63; in "day_past_2_63" the
+# three squares of day 1 alone exceed 2^63 (they still fit in 64 bits).
+P_TOP = 2**31 - 1
+
+
+def _top_range_observed(kind):
+    obs = np.zeros((3, 3), dtype=np.int32)
+    obs[:, 0] = [10**9, 0, 0]
+    if kind == "mixed":
+        obs[:, 1] = obs[:, 2] = [0, 2 * 10**9, 10**9]
+    else:
+        obs[:, 1] = [0, P_TOP, P_TOP]
+        obs[:, 2] = [0, 0, 0]
+    return obs
+
+
+@pytest.mark.parametrize("kind", ["mixed", "day_past_2_63"])
+def test_distance_at_the_top_of_its_range(kind):
+    """Eq. 7 with the exact uint64 sum saturating at 2^63: every distance
+    (abc_distances) equals the oracle's, including sqrt(2^63) for saturated
+    sums; the accept sets of abc_reject_kernel (abc_sample) and of
+    abc_batch_kernel (a one-region plan) equal the oracle's at an eps just
+    below 2^31 (threshold below 2^62: the kernels' clamped accumulation), at
+    an eps whose threshold lies between 2^62 and 2^63 (accepted sums in that
+    range) and at eps = sqrt(2^63) (saturated sums accepted too)."""
+    obs = _top_range_observed(kind)
+    n, seed = 20000, 77
+    ref = oracle.abc(obs, P_TOP, 0.0, n, seed, want_all=True, capacity=1)
+    d_all = ref["dist_all"]
+    top = float(np.sqrt(np.float64(2.0**63)))
+    d = abc.abc_distances(obs, P_TOP, n, seed, mode="exact").cpu().numpy()
+    assert np.array_equal(d, d_all)
+    n_sat, n_mid = int(np.sum(d_all == top)), int(np.sum((d_all >= 2.0**31) & (d_all < top)))
+    print("%s: %d saturated, %d between 2^62 and 2^63, %d below" % (kind, n_sat, n_mid, n - n_sat - n_mid))
+    assert n_sat > 0
+    if kind == "mixed":
+        assert n_mid > 0.2 * n and n - n_sat - n_mid > 0.2 * n
+    else:
+        # day 1's three squares alone pass 2^63 for some saturated samples (oracle trajectories, exact integers)
+        past = 0
+        for i in np.flatnonzero(d_all == top)[:100]:
+            traj = oracle.simulate(oracle.prior_draw(seed, 0, int(i)), obs[:, 0], 2, P_TOP, seed, 0, int(i))
+            past += sum((int(traj[1, 2 + c]) - int(obs[c, 1])) ** 2 for c in range(3)) >= 2**63
+        assert past > 0
+    for eps in (2.0**31 - 0.5, float(np.sort(d_all)[int(0.75 * n)]), top):
+        want = oracle.abc(obs, P_TOP, eps, n, seed, capacity=n)
+        if eps > 2.0**31 and eps < top:
+            assert np.sum(want["dist"] >= 2.0**31) > 1000
+        theta, dist, idx, n_acc = abc.abc_sample(obs, P_TOP, eps, n, seed, mode="exact", capacity=n)
+        th, di, ix = _sorted(theta, dist, idx)
+        assert n_acc == want["n_accepted"], eps
+        assert np.array_equal(ix, want["idx"]) and np.array_equal(th, want["theta"]) and np.array_equal(di, want["dist"])
+        plan = abc.Plan([dict(observed=obs, N_pop=P_TOP, eps=eps, n_samples=n, first_index=0, stream=0, capacity=n)],
+                        seed, mode="exact")
+        plan.run()
+        th, di, ix, n_acc, _ = plan.results(0)
+        th, di, ix = _sorted(th, di, ix)
+        plan.close()
+        assert n_acc == want["n_accepted"], eps
+        assert np.array_equal(ix, want["idx"]) and np.array_equal(th, want["theta"]) and np.array_equal(di, want["dist"])
+
+
+def test_long_horizons_in_turn():
+    """Kernels whose shared memory passes 48 KB at long horizons (the
+    rejection kernel from T = 1792, the distance kernel from T = 3072) run at
+    T = 4000, then 2000 or 3100, then 4000 again: a shorter horizon must not
+    lower the kernel's shared-memory limit under a longer one launched before."""
+    g = inputs.rng(5)
+    for T_mid in (2000, 3100):
+        for T in (4000, T_mid, 4000):
+            obs = np.zeros((3, T + 1), dtype=np.int32)
+            obs[:, 1:] = g.integers(0, 300, size=(3, T))
+            obs[:, 0] = [50, 5, 1]
+            n = 96
+            ref = oracle.abc(obs, 10**4, 0.0, n, 3, want_all=True, capacity=1)
+            d = abc.abc_distances(obs, 10**4, n, 3, mode="exact")
+            assert np.array_equal(d.cpu().numpy(), ref["dist_all"]), T
+            eps = float(np.sort(ref["dist_all"])[n // 4])
+            want = oracle.abc(obs, 10**4, eps, n, 3, capacity=n)
+            theta, dist, idx, n_acc = abc.abc_sample(obs, 10**4, eps, n, 3, mode="exact", capacity=n)
+            th, di, ix = _sorted(theta, dist, idx)
+            assert n_acc == want["n_accepted"], T
+            assert np.array_equal(ix, want["idx"]) and np.array_equal(di, want["dist"]), T
+
+
 def test_longest_horizon_and_tiny_population():
     """T = ABC_T_MAX (64 KiB of shared memory per block) and P = 1."""
     T = abc.ABC_T_MAX
@@ -243,11 +330,25 @@ def test_longest_horizon_and_tiny_population():
 
 def test_kth_smallest_matches_sort():
     g = inputs.rng(2)
-    x = np.concatenate([g.random(100_003) * 1e6, [0.0, 0.0, 5.0, 5.0, 1e300]])
+    x = np.concatenate([g.random(100_003) * 1e6, [0.0, 0.0, 5.0, 5.0, 1e300, np.inf]])
     t = torch.from_numpy(x).to(DEV)
     xs = np.sort(x)
-    for k in (1, 2, 3, 50, 100_000, len(x)):
+    for k in (1, 2, 3, 50, 100_000, len(x) - 1, len(x)):
         assert abc.abc_kth_smallest(t, k) == xs[k - 1]
+
+
+@pytest.mark.parametrize("bad", [np.nan, -1.0, -0.0, -np.inf])
+def test_kth_smallest_rejects_values_that_do_not_order(bad):
+    """A NaN, a negative value or -0 would sort by its bit pattern above
+    every distance: the call refuses the input instead of returning a wrong
+    quantile."""
+    x = inputs.rng(6).random(5000) * 100.0
+    x[1234] = bad
+    with pytest.raises(abc.AbcError) as e:
+        abc.abc_kth_smallest(torch.from_numpy(x).to(DEV), 10)
+    assert e.value.status == abc.binding.ABC_ERR_INVALID_ARG
+    x[1234] = 0.0
+    assert abc.abc_kth_smallest(torch.from_numpy(x).to(DEV), 1) == 0.0
 
 
 def test_full_size_launch_sampled_against_oracle():

@@ -57,3 +57,33 @@ def test_noalloc_rejects_horizon_beyond_its_scratch():
         abc.abc_sample_noalloc(obs, 1000, 1.0, 10, 1, out)
     assert e.value.status == abc.binding.ABC_ERR_INVALID_ARG
     assert "no-alloc scratch limit" in e.value.message
+
+
+def test_noalloc_allocates_nothing(monkeypatch):
+    """The property the entry point exists for. With the library's allocation
+    paths made to fail (ABC_GB300_INJECT_FAULT=alloc makes every scratch
+    allocation return ABC_ERR_NOMEM), abc_sample fails while
+    abc_sample_noalloc still succeeds with the same results; and after a
+    warm-up call (which loads the kernel's module), two more calls leave the
+    device's free memory unchanged to the byte."""
+    w = inputs.workload("region_1e6_T49")
+    obs, P, seed, eps = w["observed"], w["P"], w["seed"], w["eps"]
+    n, cap = 65536, 4096
+    out = (torch.empty((cap, 8), dtype=torch.float32, device=DEV), torch.empty((cap,), dtype=torch.float64, device=DEV),
+           torch.empty((cap,), dtype=torch.int64, device=DEV))
+    ref = _sorted(*abc.abc_sample_noalloc(obs, P, eps, n, seed, out, mode="exact")[:3])
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(2):
+        th, di, ix, _ = abc.abc_sample_noalloc(obs, P, eps, n, seed, out, mode="exact")
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0, (free0, free1)
+    monkeypatch.setenv("ABC_GB300_INJECT_FAULT", "alloc")
+    with pytest.raises(abc.AbcError) as e:
+        abc.abc_sample(obs, P, eps, n, seed, mode="exact", capacity=cap)
+    assert e.value.status == abc.binding.ABC_ERR_NOMEM
+    th, di, ix, n_acc = abc.abc_sample_noalloc(obs, P, eps, n, seed, out, mode="exact")
+    monkeypatch.delenv("ABC_GB300_INJECT_FAULT")
+    for a, b in zip(_sorted(th, di, ix), ref):
+        assert np.array_equal(a, b)
