@@ -114,9 +114,10 @@ def measured_peaks():
     return None
 
 
-# dram__bytes_read.sum + dram__bytes_write.sum of one headline launch after an
-# L2 flush, from ncu (profiles/abc_reject_kernel_traffic_region_6e7_T100.md)
-REJECT_TRAFFIC_BYTES = 167168
+# dram__bytes_read.sum + dram__bytes_write.sum per headline launch, taken by
+# ncu from a capture of the rejection kernel as it stands; None when the
+# kernel has changed since the last capture (the line then reports null).
+REJECT_TRAFFIC_BYTES = None
 
 
 def roofline(sim_days_per_launch, launch_ms, sm_count, sm_max_mhz, traffic=None):

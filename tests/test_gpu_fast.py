@@ -4,8 +4,12 @@ and the oracle:
   * teacher-forced steps: the fast day applied to exact states (from the
     oracle) with the same random numbers gives every transition count within
     one count plus 1e-6 relative of the exact count (a floor of two reals that
-    agree to 1e-6 relative can differ by one);
-  * distances: at least 98 % of samples within 1e-6 relative of exact mode;
+    agree to 1e-6 relative can differ by one), and the fraction of counts off
+    by one stays within 1.5x of what was measured on a GB300 per workload
+    (1.77e-3, 4.28e-3 and 9.5e-5 of 150,000, 180,000 and 73,500 counts);
+  * distances: at least 98.5 % of samples within 1e-6 relative of exact mode
+    (measured 98.58 % of 2^20, p99 1.44e-6, p99.9 1.34e-5): a sample whose
+    trajectory took a different floor on some day differs by more;
   * acceptance rate within binomial error of exact mode at the same eps;
   * posterior: accepted theta of fast mode vs exact mode on independent seeds,
     per coordinate two-sample KS p > 0.01, means and quantiles within Monte
@@ -28,6 +32,12 @@ from paper_2012_14332_gb300 import build as _build  # noqa: E402
 
 _build.build()
 DEV = torch.device("cuda", 0)
+
+
+# fraction of fast-mode counts off by one from exact mode, measured on a GB300
+# with these inputs (300 samples x T days x 5 transitions), times 1.5
+OFF_BY_ONE_MAX = {"region_6e7_T100": 1.5 * 1.77e-3, "region_3p3e8_T120": 1.5 * 4.29e-3,
+                  "region_1e6_T49": 1.5 * 9.6e-5}
 
 
 @pytest.mark.parametrize("name", ["region_6e7_T100", "region_3p3e8_T120", "region_1e6_T49"])
@@ -53,8 +63,11 @@ def test_teacher_forced_step_disagreement(name):
     nf = nf.cpu().numpy().astype(np.int64)
     diff = np.abs(nf - ne)
     beyond = diff > 1 + 1e-6 * ne
-    assert beyond.mean() < 1e-6, (beyond.sum(), diff.size)
-    assert (diff > 0).mean() < 1e-2
+    off = (diff > 0).mean()
+    print("%s: %d transitions, %d beyond one count + 1e-6 relative, fraction off by one %.3e" % (
+        name, diff.size, int(beyond.sum()), off))
+    assert beyond.sum() == 0, (beyond.sum(), diff.size)
+    assert off <= OFF_BY_ONE_MAX[name], off
     Yf = Yf.cpu().numpy().astype(np.int64)
     assert np.all(Yf.sum(axis=1) == P) and np.all(Yf >= 0)
 
@@ -66,7 +79,11 @@ def test_fast_distances_relative_error():
     de = abc.abc_distances(obs, P, n, seed, mode="exact").cpu().numpy()
     df = abc.abc_distances(obs, P, n, seed, mode="fast").cpu().numpy()
     rel = np.abs(df - de) / np.maximum(de, 1.0)
-    assert np.mean(rel <= 1e-6) >= 0.98
+    within = np.mean(rel <= 1e-6)
+    print("distances: %.5f within 1e-6 relative, p99 %.2e, p99.9 %.2e, max %.2e" % (
+        within, np.quantile(rel, 0.99), np.quantile(rel, 0.999), rel.max()))
+    assert within >= 0.985
+    assert np.quantile(rel, 0.99) <= 2e-6 and np.quantile(rel, 0.999) <= 2e-5
     assert np.median(rel) == 0.0
     for q in (1e-4, 1e-3, 1e-2):
         k = int(q * n)
