@@ -236,6 +236,9 @@ typedef struct {
     int32_t block_threads;        /* 128, 256 or 512 */
     int32_t pairs_per_iteration;  /* day pairs per loop iteration: 1 or 2 */
     int32_t blocks_per_sm;        /* resident blocks per SM requested (0 = all that fit) */
+    int32_t lean;                 /* 1: the kernel form that reads each region's constants from
+                                     shared memory where it uses them (64 registers, four
+                                     256-thread blocks per SM; fast mode only) */
     float ms;                     /* measured time of one run with this shape */
 } abc_launch_shape;
 
@@ -289,6 +292,13 @@ abc_status abc_plan_copy_results(abc_plan plan, int32_t region, float* theta_dst
  * region table, which is not ordered with the plan's stream): no run of the
  * plan may be in flight, so synchronize its stream first. */
 abc_status abc_plan_set_region(abc_plan plan, int32_t region, const float* theta_in, uint64_t first_index);
+
+/* Use one of the compiled launch shapes (as abc_plan_tune reports them; ms is
+ * ignored) for the following runs, without tuning. Returns ABC_ERR_INVALID_ARG
+ * for a shape the library is not compiled for, or a lean shape in exact mode.
+ * Every shape gives the same accepted samples and day counts. As for
+ * abc_plan_set_region, no run of the plan may be in flight. */
+abc_status abc_plan_set_shape(abc_plan plan, const abc_launch_shape* shape);
 
 /* Set a region's tolerance for the following runs (eps >= 0, not NaN).
  * Synchronous (cudaMemcpy of the one table field); as for

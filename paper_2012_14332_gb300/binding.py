@@ -24,7 +24,7 @@ PAPER_HI = (1.0, 100.0, 2.0, 1.0, 1.0, 1.0, 1.0, 2.0)   # Sec. 2.1, Eq. 2
 EXPORTED = ("abc_sample", "abc_distances", "abc_simulate", "abc_step", "abc_kth_smallest", "abc_strerror",
             "abc_last_error", "abc_version", "abc_last_simulated_days", "abc_sample_noalloc", "abc_plan_create",
             "abc_plan_reset", "abc_plan_run", "abc_plan_run_graph", "abc_plan_tune", "abc_plan_results",
-            "abc_plan_copy_results", "abc_plan_set_region", "abc_plan_destroy", "abc_maf_create",
+            "abc_plan_copy_results", "abc_plan_set_region", "abc_plan_set_shape", "abc_plan_destroy", "abc_maf_create",
             "abc_maf_init_random", "abc_maf_param_count", "abc_maf_set_params", "abc_maf_get_params", "abc_maf_sample", "abc_maf_log_q",
             "abc_maf_gradient", "abc_maf_adam_step", "abc_maf_train", "abc_maf_destroy", "abc_smc_run", "abc_project", "abc_pmc_run", "abc_pmc_propose",
             "abc_pmc_weights")
@@ -44,7 +44,7 @@ class AbcRegion(ctypes.Structure):
 
 class AbcLaunchShape(ctypes.Structure):
     _fields_ = [("block_threads", ctypes.c_int32), ("pairs_per_iteration", ctypes.c_int32),
-                ("blocks_per_sm", ctypes.c_int32), ("ms", ctypes.c_float)]
+                ("blocks_per_sm", ctypes.c_int32), ("lean", ctypes.c_int32), ("ms", ctypes.c_float)]
 
 
 class AbcSmcConfig(ctypes.Structure):
@@ -197,6 +197,8 @@ def load(path=None):
         L.abc_smc_run_regions.restype = ctypes.c_int
         L.abc_plan_set_eps.argtypes = [pp, i32, ctypes.c_double]
         L.abc_plan_set_eps.restype = ctypes.c_int
+        L.abc_plan_set_shape.argtypes = [pp, ctypes.POINTER(AbcLaunchShape)]
+        L.abc_plan_set_shape.restype = ctypes.c_int
         L.abc_last_simulated_days.argtypes = []
         L.abc_last_simulated_days.restype = ctypes.c_uint64
         if path is None:
@@ -517,8 +519,14 @@ class Plan:
         _check(self._L, self._L.abc_plan_tune(self._h, _stream(cuda_stream), shapes, 32, ctypes.byref(n),
                                               ctypes.byref(best)))
         as_dict = lambda s: dict(block_threads=s.block_threads, pairs_per_iteration=s.pairs_per_iteration,
-                                 blocks_per_sm=s.blocks_per_sm, ms=s.ms)
+                                 blocks_per_sm=s.blocks_per_sm, lean=s.lean, ms=s.ms)
         return as_dict(best), [as_dict(shapes[j]) for j in range(n.value)]
+
+    def set_shape(self, shape):
+        """Pin a compiled launch shape (a dict as tune() returns) without tuning."""
+        sh = AbcLaunchShape(int(shape["block_threads"]), int(shape["pairs_per_iteration"]),
+                            int(shape["blocks_per_sm"]), int(shape.get("lean", 0)), 0.0)
+        _check(self._L, self._L.abc_plan_set_shape(self._h, ctypes.byref(sh)))
 
     def counts(self, region, cuda_stream=None):
         n, d = ctypes.c_uint64(), ctypes.c_uint64()

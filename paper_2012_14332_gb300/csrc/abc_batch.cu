@@ -27,9 +27,12 @@ constexpr int kRingB = 64;
 // abc_reject_kernel (all 32 always qualify)
 constexpr uint32_t kRefillMinIdleB = 2;
 
+// A ring entry holds the sample's parameters as the day loop uses them and its
+// initial I0 (worked out when the ring is refilled, one sample per lane), so
+// handing a sample to an idle lane is a few shared-memory reads.
 struct BatchRing {
-    float4 lo[kRingB];
-    float4 hi[kRingB];
+    float4 lo[kRingB];      // Theta a0, a, n, beta
+    float4 hi[kRingB];      // Theta gamma, delta, beta_eta; I0 (int32 bits)
     uint64_t idx[kRingB];
     int32_t region[kRingB];
 };
@@ -53,14 +56,27 @@ struct LaneRegion {
 // BELOW62: every region's acc_max < 2^62, so the running sum can be clamped at
 // 2^62 each day instead of saturating exactly at 2^63 (fewer instructions; the
 // accept sets and accepted distances are the same, as in abc_reject_kernel).
-template <int MODE, int BLOCK, int PAIRS, bool BELOW62, bool OBS_S>
+//
+// LEAN: a lane keeps only its region's index and reads the region's constants
+// from the shared table where it uses them, and a sample that ends adds its
+// simulated days to a shared per-region count; this fits 64 registers (four
+// 256-thread blocks per SM instead of three) for a few shared-memory reads per
+// day pair. The autotuner chooses between the two forms: on the 16-region
+// stream the lean form ran 53.1 ms against 56.4 ms, on the three-region
+// workload 2.25 ms against 2.18 ms (128-thread blocks, where it gains no
+// occupancy).
+template <int MODE, int BLOCK, int PAIRS, bool BELOW62, bool OBS_S, bool LEAN>
 __global__ void __launch_bounds__(BLOCK) abc_batch_kernel(const __grid_constant__ ModelParams p,
                                                           const __grid_constant__ BatchArgs a)
 {
     __shared__ RegionDev reg_s[kMaxRegions];
+    __shared__ unsigned long long days_s[LEAN ? kMaxRegions : 1];   // LEAN: simulated days per region
     extern __shared__ BatchRing rings[];   // one per warp, then (OBS_S) the observed series
     int4* obs_s = reinterpret_cast<int4*>(rings + BLOCK / 32);
-    for (int r = threadIdx.x; r < a.n_regions; r += BLOCK) reg_s[r] = a.regions[r];
+    for (int r = threadIdx.x; r < a.n_regions; r += BLOCK) {
+        reg_s[r] = a.regions[r];
+        if (LEAN) days_s[r] = 0;
+    }
     if (OBS_S)
         for (int q = threadIdx.x; q < a.n_obs_smem; q += BLOCK) obs_s[q] = a.obs[q];
     __syncthreads();
@@ -71,7 +87,7 @@ __global__ void __launch_bounds__(BLOCK) abc_batch_kernel(const __grid_constant_
     bool active = false;
     uint64_t i = 0, acc = 0;
     uint32_t k = 0;
-    Theta t;
+    Theta t{};
     State x;
     LaneRegion lr{0, 1, 0, 0, 0, 0.0f};
     int32_t days_region = -1;
@@ -116,8 +132,10 @@ __global__ void __launch_bounds__(BLOCK) abc_batch_kernel(const __grid_constant_
                     const uint32_t kept = __ballot_sync(0xFFFFFFFFu, keep);
                     if (keep) {
                         const uint32_t slot = (tail + __popc(kept & lt_mask)) & (kRingB - 1);
-                        ring.lo[slot] = make_float4(th[0], th[1], th[2], th[3]);
-                        ring.hi[slot] = make_float4(th[4], th[5], th[6], th[7]);
+                        const Theta tt = make_theta<MODE>(th, R.inv_p);
+                        const int32_t I0 = initial_infected(tt, R.A0, R.room0);
+                        ring.lo[slot] = make_float4(tt.a0, tt.a, tt.n, tt.beta);
+                        ring.hi[slot] = make_float4(tt.gamma, tt.delta, tt.beta_eta, __int_as_float(I0));
                         ring.idx[slot] = R.first_index + j0 + lane;
                         ring.region[slot] = r;
                     }
@@ -135,23 +153,25 @@ __global__ void __launch_bounds__(BLOCK) abc_batch_kernel(const __grid_constant_
                 if (rank < avail) {
                     const uint32_t slot = (head + rank) & (kRingB - 1);
                     const float4 l = ring.lo[slot], h = ring.hi[slot];
-                    const float th[8] = {l.x, l.y, l.z, l.w, h.x, h.y, h.z, h.w};
                     i = ring.idx[slot];
                     const int32_t r = ring.region[slot];
                     const RegionDev& R = reg_s[r];
-                    if (r != days_region) {
-                        if (days_region >= 0 && days) atomicAdd(reg_s[days_region].counters + 1, days);
-                        days = 0;
-                        days_region = r;
-                    }
                     lr.r = r;
-                    lr.T = R.T;
-                    lr.ctr3 = R.ctr3_base;
-                    lr.obs_off = R.obs_off;
-                    lr.acc_max = R.acc_max;
-                    lr.inv_p = R.inv_p;
-                    t = make_theta<MODE>(th, R.inv_p);
-                    x = init_state(t, R.A0, R.R0, R.D0, R.room0);
+                    if (!LEAN) {
+                        if (r != days_region) {
+                            if (days_region >= 0 && days) atomicAdd(reg_s[days_region].counters + 1, days);
+                            days = 0;
+                            days_region = r;
+                        }
+                        lr.T = R.T;
+                        lr.ctr3 = R.ctr3_base;
+                        lr.obs_off = R.obs_off;
+                        lr.acc_max = R.acc_max;
+                        lr.inv_p = R.inv_p;
+                    }
+                    t.a0 = l.x; t.a = l.y; t.n = l.z; t.beta = l.w;
+                    t.gamma = h.x; t.delta = h.y; t.beta_eta = h.z;
+                    x = state_from(__float_as_int(h.w), R.A0, R.R0, R.D0, R.room0);
                     acc = 0;
                     k = 1;
                     active = true;
@@ -165,25 +185,31 @@ __global__ void __launch_bounds__(BLOCK) abc_batch_kernel(const __grid_constant_
 #pragma unroll
         for (int rep = 0; rep < PAIRS; ++rep) {
             if (active) {
+                const RegionDev& R = reg_s[lr.r];
                 float z[10];
-                day_pair_normals_s<MODE>(p, i, k, lr.ctr3, z);
+                day_pair_normals_s<MODE>(p, i, k, LEAN ? R.ctr3_base : lr.ctr3, z);
                 const int32_t d1 = (int32_t)(2 * k - 1);
-                const int4* obs = (OBS_S ? obs_s : a.obs) + lr.obs_off;
-                model_day<MODE>(x, t, lr.inv_p, z);
+                const int4* obs = (OBS_S ? obs_s : a.obs) + (LEAN ? R.obs_off : lr.obs_off);
+                // fast mode folds 1/P into theta at the hand-out; only exact mode reads it per day
+                const float inv_p = is_fast(MODE) ? 0.0f : (LEAN ? R.inv_p : lr.inv_p);
+                model_day<MODE>(x, t, inv_p, z);
                 const int4 o1 = OBS_S ? obs[d1] : __ldg(obs + d1);
                 acc = BELOW62 ? add_day_sq_below62(acc, x, o1) : add_day_sq(acc, x, o1);
-                if (d1 < lr.T) {
-                    model_day<MODE>(x, t, lr.inv_p, z + 5);
+                const int32_t T = LEAN ? R.T : lr.T;
+                if (d1 < T) {
+                    model_day<MODE>(x, t, inv_p, z + 5);
                     const int4 o2 = OBS_S ? obs[d1 + 1] : __ldg(obs + d1 + 1);
                     acc = BELOW62 ? add_day_sq_below62(acc, x, o2) : add_day_sq(acc, x, o2);
-                    days += 2;
-                } else {
+                    if (!LEAN) days += 2;
+                } else if (!LEAN) {
                     days += 1;
                 }
-                const bool over = acc > lr.acc_max;
-                const bool last = d1 + 1 >= lr.T;
+                const bool over = acc > (LEAN ? R.acc_max : lr.acc_max);
+                const bool last = d1 + 1 >= T;
                 accept = !over && last;
                 active = !(over || last);
+                // LEAN: a sample that ends adds the days it simulated to its region's count
+                if (LEAN && !active) atomicAdd(&days_s[lr.r], (unsigned long long)(d1 < T ? d1 + 1 : T));
                 ++k;
             }
         }
@@ -195,7 +221,7 @@ __global__ void __launch_bounds__(BLOCK) abc_batch_kernel(const __grid_constant_
                 if (R.theta_in)
                     load_theta(R.theta_in + 8 * (i - R.first_index), th);
                 else
-                    prior_draw_s(p, i, lr.ctr3, th);
+                    prior_draw_s(p, i, R.ctr3_base, th);
                 R.idx_out[slot] = i;
                 R.dist_out[slot] = __dsqrt_rn(__ull2double_rn(acc));
                 float4* to = reinterpret_cast<float4*>(R.theta_out + 8 * slot);
@@ -204,7 +230,13 @@ __global__ void __launch_bounds__(BLOCK) abc_batch_kernel(const __grid_constant_
             }
         }
     }
-    if (days_region >= 0 && days) atomicAdd(reg_s[days_region].counters + 1, days);
+    if (LEAN) {
+        __syncthreads();
+        for (int r = threadIdx.x; r < a.n_regions; r += BLOCK)
+            if (days_s[r]) atomicAdd(reg_s[r].counters + 1, days_s[r]);
+    } else if (days_region >= 0 && days) {
+        atomicAdd(reg_s[days_region].counters + 1, days);
+    }
 }
 
 __global__ void advance_kernel(RegionDev* regions, int32_t n)
@@ -216,20 +248,22 @@ __global__ void advance_kernel(RegionDev* regions, int32_t n)
 }  // namespace
 
 static const BatchShape kShapes[] = {
-    {256, 1, 0}, {128, 1, 0}, {512, 1, 0}, {256, 2, 0}, {128, 2, 0}, {512, 2, 0}, {256, 1, 2}, {256, 1, 3},
+    {256, 1, 0, 0}, {128, 1, 0, 0}, {512, 1, 0, 0}, {256, 2, 0, 0}, {128, 2, 0, 0}, {512, 2, 0, 0},
+    {256, 1, 2, 0}, {256, 1, 3, 0}, {256, 1, 0, 1}, {256, 2, 0, 1},
 };
 
 int batch_shape_count() { return (int)(sizeof kShapes / sizeof kShapes[0]); }
 BatchShape batch_shape(int index) { return kShapes[index]; }
+bool batch_shape_supported(const BatchShape& shape, bool fast) { return fast || !shape.lean; }
 
 // With a == NULL only prepares: sets the kernel's dynamic shared-memory limit
 // (the rings, and the observed series with OBS_S) and resolves its occupancy,
 // so that a launch, or a graph capture of one, makes no attribute calls.
-template <int MODE, int BLOCK, int PAIRS, bool BELOW62, bool OBS_S>
+template <int MODE, int BLOCK, int PAIRS, bool BELOW62, bool OBS_S, bool LEAN = false>
 static cudaError_t launch_t(const ModelParams& p, const BatchArgs* a, int32_t n_obs_smem, int blocks_per_sm,
                             cudaStream_t s)
 {
-    auto kernel = abc_batch_kernel<MODE, BLOCK, PAIRS, BELOW62, OBS_S>;
+    auto kernel = abc_batch_kernel<MODE, BLOCK, PAIRS, BELOW62, OBS_S, LEAN>;
     const size_t smem = sizeof(BatchRing) * (BLOCK / 32) + (OBS_S ? sizeof(int4) * (size_t)n_obs_smem : 0);
     int dev = 0, sms = 0, fit = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -260,6 +294,14 @@ static cudaError_t dispatch(const ModelParams& p, const BatchArgs* a, int32_t n_
                             cudaStream_t s)
 {
     const int bps = sh.blocks_per_sm;
+    // the lean form is compiled for fast mode at 256 threads, where it raises occupancy
+    if (sh.lean) {
+        if constexpr (MODE == kFast) {
+            if (sh.block_threads == 256 && sh.pairs == 1) return launch_t<MODE, 256, 1, B62, OS, true>(p, a, n_obs_smem, bps, s);
+            if (sh.block_threads == 256 && sh.pairs == 2) return launch_t<MODE, 256, 2, B62, OS, true>(p, a, n_obs_smem, bps, s);
+        }
+        return cudaErrorInvalidValue;
+    }
     if (sh.block_threads == 128 && sh.pairs == 1) return launch_t<MODE, 128, 1, B62, OS>(p, a, n_obs_smem, bps, s);
     if (sh.block_threads == 256 && sh.pairs == 1) return launch_t<MODE, 256, 1, B62, OS>(p, a, n_obs_smem, bps, s);
     if (sh.block_threads == 512 && sh.pairs == 1) return launch_t<MODE, 512, 1, B62, OS>(p, a, n_obs_smem, bps, s);

@@ -32,7 +32,10 @@ __device__ __forceinline__ void stage_observed(int4* obs_s, const int4* __restri
 // whole warp (sample indices claimed with one atomicAdd per 32), so the theta
 // draw of a new sample costs one shared-memory read for the lane that needs
 // it. The loop advances every active lane by one day pair; all ring
-// bookkeeping is warp-uniform. Accepted samples are compacted with a ballot
+// bookkeeping is warp-uniform. A ring entry holds the sample's parameters as
+// the day loop uses them and its initial I0, worked out when the ring is
+// refilled (32 samples, one per lane), so handing a sample to an idle lane
+// is a few shared-memory reads. Accepted samples are compacted with a ballot
 // and one atomicAdd per warp; their theta is re-drawn from the index.
 // ---------------------------------------------------------------------------
 constexpr int kRing = 64;
@@ -46,10 +49,22 @@ constexpr int kWarpsPerBlock = kBlockThreads / 32;
 constexpr uint32_t kRefillMinIdle = 2;
 
 struct WarpRing {
-    float4 lo[kRing];     // theta0..3
-    float4 hi[kRing];     // theta4..7
+    float4 lo[kRing];     // Theta a0, a, n, beta
+    float4 hi[kRing];     // Theta gamma, delta, beta_eta; I0 (int32 bits)
     uint64_t idx[kRing];  // sample index
 };
+
+// Ring entry of sample ii: its Theta (kappa folded into I0) and I0.
+template <int MODE>
+__device__ __forceinline__ void ring_put(WarpRing& ring, uint32_t slot, const ModelParams& p, uint64_t ii,
+                                         const float th[8], int32_t A0, int32_t room)
+{
+    const Theta t = make_theta<MODE>(th, p.inv_p);
+    const int32_t I0 = initial_infected(t, A0, room);
+    ring.lo[slot] = make_float4(t.a0, t.a, t.n, t.beta);
+    ring.hi[slot] = make_float4(t.gamma, t.delta, t.beta_eta, __int_as_float(I0));
+    ring.idx[slot] = ii;
+}
 
 template <int MODE, bool BELOW62>
 __global__ void __launch_bounds__(kBlockThreads) abc_reject_kernel(const __grid_constant__ ModelParams p,
@@ -66,7 +81,7 @@ __global__ void __launch_bounds__(kBlockThreads) abc_reject_kernel(const __grid_
     bool active = false;
     uint64_t i = 0, acc = 0;
     uint32_t k = 0, days = 0;
-    Theta t;
+    Theta t{};
     State x;
     uint32_t head = 0, tail = 0;     // ring entries consumed / produced (warp-uniform)
     bool exhausted = false;          // no indices left to claim (warp-uniform)
@@ -88,10 +103,7 @@ __global__ void __launch_bounds__(kBlockThreads) abc_reject_kernel(const __grid_
                         const uint64_t ii = a.first_index + base + lane;
                         float th[8];
                         prior_draw(p, ii, th);
-                        const uint32_t slot = (tail + lane) & (kRing - 1);
-                        ring.lo[slot] = make_float4(th[0], th[1], th[2], th[3]);
-                        ring.hi[slot] = make_float4(th[4], th[5], th[6], th[7]);
-                        ring.idx[slot] = ii;
+                        ring_put<MODE>(ring, (tail + lane) & (kRing - 1), p, ii, th, p.A0, p.room0);
                     }
                     tail += made;
                     if (made < 32 || base + 32 >= a.n_samples) exhausted = true;
@@ -108,10 +120,10 @@ __global__ void __launch_bounds__(kBlockThreads) abc_reject_kernel(const __grid_
                 if (rank < avail) {
                     const uint32_t slot = (head + rank) & (kRing - 1);
                     const float4 l = ring.lo[slot], h = ring.hi[slot];
-                    const float th[8] = {l.x, l.y, l.z, l.w, h.x, h.y, h.z, h.w};
                     i = ring.idx[slot];
-                    t = make_theta<MODE>(th, p.inv_p);
-                    x = init_state(t, p.A0, p.R0, p.D0, p.room0);
+                    t.a0 = l.x; t.a = l.y; t.n = l.z; t.beta = l.w;
+                    t.gamma = h.x; t.delta = h.y; t.beta_eta = h.z;
+                    x = state_from(__float_as_int(h.w), p.A0, p.R0, p.D0, p.room0);
                     acc = 0;
                     k = 1;
                     active = true;

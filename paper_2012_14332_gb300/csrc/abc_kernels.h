@@ -86,9 +86,11 @@ struct BatchShape {
     int block_threads;   // 128, 256 or 512
     int pairs;           // day pairs per loop iteration (1 or 2)
     int blocks_per_sm;   // resident blocks requested per SM (0 = as many as fit)
+    int lean;            // 1: region constants read from shared memory (fast mode, 256 threads)
 };
 int batch_shape_count();
 BatchShape batch_shape(int index);
+bool batch_shape_supported(const BatchShape& shape, bool fast);   // the lean form is fast mode only
 
 // below62: every region's acc_max < 2^62 (the cheaper distance accumulation)
 cudaError_t launch_batch(const ModelParams& p, const BatchArgs& a, bool fast, bool below62, const BatchShape& shape,

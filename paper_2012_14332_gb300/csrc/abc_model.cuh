@@ -288,14 +288,24 @@ struct State {
     int32_t S, I, A, R, D, Ru;
 };
 
-// Sec. 2.1 first step: Ru = 0, I0 = kappa A0 (floored, limited by the room
-// left after A0 + R0 + D0), S = P - (A0 + R0 + D0 + I0).
-__device__ __forceinline__ State init_state(const Theta& t, int32_t A0, int32_t R0, int32_t D0, int32_t room)
+// Sec. 2.1 first step: I0 = kappa A0, floored and limited by the room left
+// after A0 + R0 + D0.
+__device__ __forceinline__ int32_t initial_infected(const Theta& t, int32_t A0, int32_t room)
+{
+    return clamp_count(__fmul_rn(t.kappa, __int2float_rn(A0)), room);
+}
+
+// The initial state for a given I0: Ru = 0, S = P - (A0 + R0 + D0 + I0).
+__device__ __forceinline__ State state_from(int32_t I0, int32_t A0, int32_t R0, int32_t D0, int32_t room)
 {
     State x;
-    const int32_t I0 = clamp_count(__fmul_rn(t.kappa, __int2float_rn(A0)), room);
     x.S = room - I0; x.I = I0; x.A = A0; x.R = R0; x.D = D0; x.Ru = 0;
     return x;
+}
+
+__device__ __forceinline__ State init_state(const Theta& t, int32_t A0, int32_t R0, int32_t D0, int32_t room)
+{
+    return state_from(initial_infected(t, A0, room), A0, R0, D0, room);
 }
 
 // One day (Sec. 2.1 second to fourth step) with normals z[0..4] in h order.
@@ -322,7 +332,9 @@ __device__ __forceinline__ void model_day(State& x, const Theta& t, float inv_p,
         v3 = __fadd_rn(h3, __fmul_rn(sd(h3), z[3]));
         v4 = __fadd_rn(h4, __fmul_rn(sd(h4), z[4]));
     } else {
-        const float pw = (U != 0) ? fast::ex2(t.n * fast::lg2(__int2float_rn(U))) : 0.0f;
+        // U = 0: lg2 gives -inf and n (-inf) = -inf for n > 0; the clamp at -200
+        // also turns n = 0 (NaN) into 2^-200 = 0, so 0^n = 0 without a branch
+        const float pw = fast::ex2(fmaxf(t.n * fast::lg2(__int2float_rn(U)), -200.0f));
         const float g_over_p = __fmaf_rn(t.a, fast::rcp(1.0f + pw), t.a0);   // a0, a carry 1/P
         h0 = (g_over_p * Sf) * If;
         h1 = t.gamma * If;
@@ -354,13 +366,18 @@ __device__ __forceinline__ void model_day(State& x, const Theta& t, float inv_p,
 }
 
 // Distance^2 accumulation of one day when only "acc <= acc_max < 2^62" and the
-// exact value of accepted samples matter: clamp the running sum at 2^62 before
-// adding the three squares (each < 2^62, so no wrap). Every partial sum of an
-// accepted sample is <= acc_max < 2^62, so its sum is never clamped.
+// exact value of accepted samples matter. Before the day's three squares are
+// added, the high word of the running sum is clamped at 2^30 (one
+// instruction): the sum is then at most 2^62 + 2^32 - 1, and with three
+// squares of at most (2^31 - 1)^2 each it stays below 2^64 - 2^33 + 3, so it
+// never wraps. A sum that reached 2^62 keeps a high word of 2^30, so it stays
+// >= 2^62 > acc_max; every partial sum of an accepted sample is <= acc_max,
+// so its sum is never clamped and is exact.
 __device__ __forceinline__ uint64_t add_day_sq_below62(uint64_t acc, const State& x, int4 obs)
 {
     const int32_t dA = x.A - obs.x, dR = x.R - obs.y, dD = x.D - obs.z;
-    acc = acc < 0x4000000000000000ull ? acc : 0x4000000000000000ull;
+    const uint32_t hi = min((uint32_t)(acc >> 32), 0x40000000u);
+    acc = ((uint64_t)hi << 32) | (uint32_t)acc;
     acc += (uint64_t)((int64_t)dA * dA);
     acc += (uint64_t)((int64_t)dR * dR);
     acc += (uint64_t)((int64_t)dD * dD);

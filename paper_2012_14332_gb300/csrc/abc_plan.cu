@@ -39,7 +39,7 @@ struct abc_plan_s {
     uint64_t* d_idx = nullptr;
     uint64_t total_chunks = 0;
     int32_t n_obs_smem = 0;   // observed days staged in shared memory by the kernel (0: read through the cache)
-    abcgb::BatchShape shape{256, 1, 0};
+    abcgb::BatchShape shape{256, 1, 0, 0};
     cudaGraphExec_t graph = nullptr;
     int32_t graph_runs = 0;
     bool graph_below62 = false;   // the kernel variant the graph was captured with
@@ -303,6 +303,7 @@ abc_status abc_plan_tune(abc_plan plan, void* cuda_stream, abc_launch_shape* sha
     int written = 0;
     abc_status result = ABC_OK;
     for (int c = 0; c < n && result == ABC_OK; ++c) {
+        if (!abcgb::batch_shape_supported(abcgb::batch_shape(c), plan->fast)) continue;
         plan->shape = abcgb::batch_shape(c);
         // both distance variants: a later abc_plan_set_eps may switch to the other
         cudaError_t e = abcgb::prepare_batch(plan->fast, true, plan->n_obs_smem, plan->shape);
@@ -320,7 +321,7 @@ abc_status abc_plan_tune(abc_plan plan, void* cuda_stream, abc_launch_shape* sha
         if (result != ABC_OK) break;
         if (shapes_out && written < max_shapes) {
             shapes_out[written] = abc_launch_shape{plan->shape.block_threads, plan->shape.pairs,
-                                                   plan->shape.blocks_per_sm, ms};
+                                                   plan->shape.blocks_per_sm, plan->shape.lean, ms};
             ++written;
         }
         if (best < 0 || ms < best_ms) {
@@ -346,7 +347,8 @@ abc_status abc_plan_tune(abc_plan plan, void* cuda_stream, abc_launch_shape* sha
     }
     if (n_shapes_out) *n_shapes_out = written;
     if (best_out)
-        *best_out = abc_launch_shape{plan->shape.block_threads, plan->shape.pairs, plan->shape.blocks_per_sm, best_ms};
+        *best_out = abc_launch_shape{plan->shape.block_threads, plan->shape.pairs, plan->shape.blocks_per_sm,
+                                     plan->shape.lean, best_ms};
     return plan_ok();
 }
 
@@ -413,6 +415,30 @@ abc_status abc_plan_set_region(abc_plan plan, int32_t region, const float* theta
                         cudaMemcpyHostToDevice),
              "cudaMemcpy(region table)");
     return plan_ok();
+}
+
+abc_status abc_plan_set_shape(abc_plan plan, const abc_launch_shape* shape)
+{
+    abc_status st;
+    if ((st = check_plan(plan)) != ABC_OK) return st;
+    if (!shape) return plan_fail(ABC_ERR_INVALID_ARG, "shape is NULL");
+    for (int c = 0; c < abcgb::batch_shape_count(); ++c) {
+        const abcgb::BatchShape b = abcgb::batch_shape(c);
+        if (b.block_threads != shape->block_threads || b.pairs != shape->pairs_per_iteration ||
+            b.blocks_per_sm != shape->blocks_per_sm || b.lean != shape->lean)
+            continue;
+        if (!abcgb::batch_shape_supported(b, plan->fast))
+            return plan_fail(ABC_ERR_INVALID_ARG, "the lean kernel form is compiled for fast mode only");
+        PLAN_TRY(abcgb::prepare_batch(plan->fast, true, plan->n_obs_smem, b), "prepare_batch");
+        PLAN_TRY(abcgb::prepare_batch(plan->fast, false, plan->n_obs_smem, b), "prepare_batch");
+        plan->shape = b;
+        if (plan->graph) {
+            cudaGraphExecDestroy(plan->graph);
+            plan->graph = nullptr;
+        }
+        return plan_ok();
+    }
+    return plan_fail(ABC_ERR_INVALID_ARG, "the library is not compiled for this launch shape");
 }
 
 abc_status abc_plan_set_eps(abc_plan plan, int32_t region, double eps)

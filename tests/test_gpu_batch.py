@@ -263,3 +263,40 @@ def test_graph_follows_an_eps_change_across_2_to_the_62():
         assert np.array_equal(x, y)
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("mode", ["fast", "exact"])
+def test_every_launch_shape_gives_the_same_results(mode):
+    """Each compiled launch shape, the register-lean form included (fast mode
+    only; refused in exact mode), run on the same sample ranges gives the
+    same accepted samples per region and the same simulated-day counts."""
+    n = 20000
+    regs = _regions([n, n + 7, n - 5], [3, 10**9, (1 << 32) - 100], quantile=0.05)
+    plan = abc.Plan(regs, SEED, mode=mode)
+    _, shapes = plan.tune()
+    assert any(s["lean"] for s in shapes) == (mode == "fast")
+    ref = None
+    for sh in shapes:
+        plan.set_shape(sh)
+        plan.reset()
+        for r, g in enumerate(regs):
+            plan.set_region(r, None, g["first_index"])
+        plan.run()
+        got = []
+        for r in range(len(regs)):
+            th, di, ix, n_acc, days = plan.results(r)
+            got.append((n_acc, days) + _sorted(th, di, ix))
+        if ref is None:
+            ref = got
+            assert all(g[0] > 0 for g in got)
+            continue
+        for a, b in zip(got, ref):
+            assert a[:2] == b[:2], sh
+            for x, y in zip(a[2:], b[2:]):
+                assert np.array_equal(x, y), sh
+    if mode == "exact":
+        with pytest.raises(abc.AbcError):
+            plan.set_shape(dict(block_threads=256, pairs_per_iteration=2, blocks_per_sm=0, lean=1))
+    with pytest.raises(abc.AbcError):
+        plan.set_shape(dict(block_threads=96, pairs_per_iteration=1, blocks_per_sm=0, lean=0))
+    plan.close()
