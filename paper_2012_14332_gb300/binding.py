@@ -603,6 +603,10 @@ def abc_plan_set_eps(plan, region, eps):
     plan.set_eps(region, eps)
 
 
+def abc_plan_set_shape(plan, shape):
+    plan.set_shape(shape)
+
+
 def abc_plan_destroy(plan):
     plan.close()
 
