@@ -39,6 +39,12 @@ UNIT = "accepted samples/s"
 # SFU: 16 per clock per SM.
 OPS_PER_SIM_DAY = {"issue": 144.0, "sfu": 18.0}
 PIPE_RATE_PER_SM_CLK = {"issue": 128.0, "sfu": 16.0}
+# Algorithmic work of one sample besides its days (fast mode): the prior draw,
+# two Philox blocks of 10 rounds less the products their shared counter words
+# share (73), eight uniforms (16) and the prior's affine map (8); the derived
+# rates alpha0/P, alpha/P, beta*eta (3); I0 = floor(kappa A0) clamped and S0 (4).
+# 104 issue slots, no SFU transcendental: 104/144 of a simulated day's issue.
+OPS_PER_SAMPLE = {"issue": 104.0, "sfu": 0.0}
 
 
 def load_workload():
@@ -120,19 +126,23 @@ def measured_peaks():
 REJECT_TRAFFIC_BYTES = None
 
 
-def roofline(sim_days_per_launch, launch_ms, sm_count, sm_max_mhz, traffic=None):
+def roofline(sim_days_per_launch, launch_ms, sm_count, sm_max_mhz, traffic=None, samples_per_launch=0):
     """ALU roofline: the fastest a launch could run if the tighter of issue
-    slots and SFU throughput for the method's instructions (OPS_PER_SIM_DAY)
-    were saturated on every SM at the maximum SM clock. In simulated days/s,
-    counting the days the launch actually simulated."""
+    slots and SFU throughput for the method's instructions were saturated on
+    every SM at the maximum SM clock. In simulated days/s: the days the launch
+    actually simulated, plus each sample's own work (OPS_PER_SAMPLE) counted
+    in days of the bound pipe. days_only_frac leaves the per-sample work out."""
     clk_per_sim_day = max(OPS_PER_SIM_DAY[k] / PIPE_RATE_PER_SM_CLK[k] for k in OPS_PER_SIM_DAY)
     bound_pipe = max(OPS_PER_SIM_DAY, key=lambda k: OPS_PER_SIM_DAY[k] / PIPE_RATE_PER_SM_CLK[k])
     peak = sm_count * sm_max_mhz * 1e6 / clk_per_sim_day
-    achieved = sim_days_per_launch / (launch_ms * 1e-3)
+    day_equiv = OPS_PER_SAMPLE[bound_pipe] / OPS_PER_SIM_DAY[bound_pipe]
+    days = sim_days_per_launch + day_equiv * samples_per_launch
+    achieved = days / (launch_ms * 1e-3)
     return {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Gsim*days/s",
             "frac": achieved / peak, "traffic": traffic, "pipe": bound_pipe,
-            "peak_basis": "%d SMs x %.0f MHz (max SM clock) / %.3f clk per sim-day on the %s pipe" % (
-                sm_count, sm_max_mhz, clk_per_sim_day, bound_pipe)}
+            "days_only_frac": sim_days_per_launch / (launch_ms * 1e-3) / peak,
+            "peak_basis": "%d SMs x %.0f MHz / %.3f clk per sim-day (%s); a sample's own work = %.3f day" % (
+                sm_count, sm_max_mhz, clk_per_sim_day, bound_pipe, day_equiv)}
 
 
 BATCH_REGIONS = ["region_1e7_T60", "region_6e7_T90", "region_3p3e8_T120"]
@@ -182,7 +192,8 @@ def bench_batched(abc, torch, steps, warmup, dev, flush, sm_count, sm_max):
             "launch_ms_mean": launch_ms, "sims_days_per_s": nominal * steps / (region_ms * 1e-3),
             "simulated_days_per_step": days / steps, "accepted_per_step": acc / steps,
             "tuned_shape": best, "shapes_tried": shapes,
-            "roofline": roofline(days / steps, launch_ms, sm_count, sm_max)}
+            "roofline": roofline(days / steps, launch_ms, sm_count, sm_max,
+                                 samples_per_launch=sum(g["n_samples"] for g in regs))}
 
 
 def bench_streamed(abc, torch, dev, flush, sm_count, sm_max, chunks=16):
@@ -219,7 +230,71 @@ def bench_streamed(abc, torch, dev, flush, sm_count, sm_max, chunks=16):
                         "streamed in %d chunks of 2^24 in one CUDA-graph replay, fast mode" % chunks,
             "value": acc / (ms * 1e-3), "unit": UNIT, "ms_total": ms, "accepted": acc,
             "sims_days_per_s": nominal / (ms * 1e-3), "simulated_days": days, "tuned_shape": best,
-            "roofline": roofline(days, ms, sm_count, sm_max)}
+            "roofline": roofline(days, ms, sm_count, sm_max,
+                                 samples_per_launch=chunks * sum(g["n_samples"] for g in regs))}
+
+
+def bench_config1(abc, torch, dev, reps=20, warmup=3):
+    """Plain ABC on region_1e6_T49 (P = 1e6, T = 49): 65,536 prior samples,
+    exact mode, eps at the 0.1 % distance quantile. One run is the whole
+    pipeline through the public calls: every distance (abc_distances), eps as
+    the k-th smallest, k = ceil(0.001 n) = 66 (abc_kth_smallest, radix select
+    on the device), then the rejection launch at that eps (abc_sample). The
+    observed series comes from host memory in each call; eps and the accepted
+    count are checked against the workload's own (written by the oracle)."""
+    with open(os.path.join(ROOT, "tests", "golden", "workloads.json")) as f:
+        w = json.load(f)["region_1e6_T49"]
+    obs, P, T, n, seed = np.array(w["observed"], dtype=np.int32), w["P"], w["T"], w["n_samples"], w["seed"]
+    k = int(np.ceil(0.001 * n))
+    cap = 1024
+    outs = (torch.empty((cap, 8), dtype=torch.float32, device=dev), torch.empty((cap,), dtype=torch.float64, device=dev),
+            torch.empty((cap,), dtype=torch.int64, device=dev))
+    dbuf = torch.empty((n,), dtype=torch.float64, device=dev)
+    stage = {"distances": [], "kth_smallest": [], "sample": []}
+    walls, eps, n_acc = [], None, None
+    for rep in range(warmup + reps):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ev[0].record()
+        d = abc.abc_distances(obs, P, n, seed, mode="exact", out=(dbuf, None))
+        ev[1].record()
+        eps = abc.abc_kth_smallest(d, k)
+        ev[2].record()
+        _, _, _, n_acc = abc.abc_sample(obs, P, eps, n, seed, mode="exact", capacity=cap, out=outs)
+        ev[3].record()
+        torch.cuda.synchronize()
+        if rep >= warmup:
+            walls.append(time.perf_counter() - t0)
+            for j, key in enumerate(stage):
+                stage[key].append(ev[j].elapsed_time(ev[j + 1]))
+    ms = float(np.median(walls)) * 1e3
+    out = {"workload": "region_1e6_T49: P=1e6, T=49, %d prior samples, exact mode, eps = %d-th smallest distance "
+                       "(0.1 %% quantile)" % (n, k),
+           "accepted": int(n_acc), "eps": eps, "eps_equals_workload": bool(eps == w["eps"]),
+           "ms_per_run": ms, "accepted_per_s": n_acc / (ms * 1e-3),
+           "sims_days_per_s": n * T / (ms * 1e-3),
+           "ms_by_stage": {key: float(np.median(v)) for key, v in stage.items()}, "runs": reps}
+    return out
+
+
+def cpu_baseline_config1():
+    """The oracle on the same pipeline on the host cores: every distance of
+    region_1e6_T49's 65,536 samples (all cores), eps as the 66-th smallest, and
+    the accepted samples at that eps."""
+    import oracle
+    with open(os.path.join(ROOT, "tests", "golden", "workloads.json")) as f:
+        w = json.load(f)["region_1e6_T49"]
+    obs, n = np.array(w["observed"], dtype=np.int32), w["n_samples"]
+    k = int(np.ceil(0.001 * n))
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    d = oracle.abc(obs, w["P"], 0.0, n, w["seed"], want_all=True, capacity=1, n_threads=cores)["dist_all"]
+    eps = float(np.partition(d, k - 1)[k - 1])
+    acc = int(np.count_nonzero(d <= eps))
+    dt = time.perf_counter() - t0
+    return {"value": acc / dt, "unit": UNIT, "cores": cores, "kind": "oracle", "seconds": dt, "accepted": acc,
+            "sample": "the whole workload (%d samples), distances on %d threads" % (n, cores)}
 
 
 def bench_exact(abc, torch, w, dev, flush, fast_days_per_s, steps=5, warmup=3, n=1 << 22):
@@ -402,55 +477,72 @@ def bench_learned_stream(abc, torch, prior_stream=None):
     return out
 
 
-def bench_learned(abc, torch, w, prior_value, peaks, sm_count, sm_max, reps=5):
+def bench_learned(abc, torch, w, prior_value, peaks, sm_count, sm_max, reps=5, verbose=False):
     """Sequential ABC with the learned flow proposal on the P = 6e7, T = 100
     region: 5 rounds of 2^22 simulations, eps shrinking by 0.7 per round to the
     headline eps, flow of 3 MADE blocks x 256 hidden units (BF16 weights, FP32
     accumulation), proposals from the flow broadened by LEARNED_TAU. Compared
-    with plain prior ABC at the same (final) eps. The flow's training is
-    stochastic (and a flow doing worse than the prior falls back to it), so
-    `reps` independent runs (own seeds) are made and the median is the
-    reported figure, with every run listed."""
+    with plain prior ABC at the same (final) eps.
+
+    The headline figure is the whole run: effective samples accepted at the
+    final eps (accepted x ESS fraction of the final round, the only round at
+    that eps) per second of the whole abc_smc_run call, all five rounds with
+    their proposals, simulations, weights and training. The final round alone
+    (proposals and simulations) is reported beside it. The flow's training is
+    stochastic, so `reps` independent runs (own seeds) are made; medians are
+    reported, with every run listed."""
     rounds, n, factor = 5, 1 << 22, 0.7
     eps0 = w["eps"] / factor ** (rounds - 1)
     runs = []
     for rep in range(reps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
         info, th, wt, dist = abc.abc_smc_run(w["observed"], w["P"], eps0, rounds=rounds, sims_per_round=n,
                                              eps_factor=factor, flow_blocks=3, flow_hidden=256, train_steps=500,
                                              train_batch=4096, train_lr=1e-3, seed=w["seed"] + 17 + 1000 * rep,
                                              capacity=n, mode="fast", proposal_scale=LEARNED_TAU,
                                              train_weight_power=LEARNED_POWER)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
         last = info[-1]
         ms = last["ms_propose"] + last["ms_simulate"]
-        runs.append({"seed": w["seed"] + 17 + 1000 * rep,
-                     "final_round_proposal": "flow" if last["proposal"] == 1 else "prior (fallback)",
-                     "final_round_accepted_per_s": last["n_accepted"] / (ms * 1e-3),
-                     "final_round_effective_accepted_per_s": last["n_accepted"] * last["ess_fraction"] / (ms * 1e-3),
-                     "final_round_acceptance": last["n_accepted"] / n,
-                     "final_round_ess_fraction": last["ess_fraction"],
-                     "all_rounds_seconds": sum(r["ms_propose"] + r["ms_simulate"] + r["ms_train"] for r in info) * 1e-3,
-                     "ms_propose": last["ms_propose"], "ms_simulate": last["ms_simulate"],
-                     "final_round_simulated_days": last["simulated_days"],
-                     "rounds": [{k: (round(v, 4) if isinstance(v, float) else v) for k, v in r.items()} for r in info]})
+        eff = last["n_accepted"] * last["ess_fraction"]
+        run = {"seed": w["seed"] + 17 + 1000 * rep,
+               "final_round_proposal": "flow" if last["proposal"] == 1 else "prior (fallback)",
+               "whole_run_seconds": wall,
+               "whole_run_effective_accepted_per_s": eff / wall,
+               "final_round_accepted_per_s": last["n_accepted"] / (ms * 1e-3),
+               "final_round_effective_accepted_per_s": eff / (ms * 1e-3),
+               "final_round_acceptance": last["n_accepted"] / n,
+               "final_round_ess_fraction": last["ess_fraction"],
+               "device_seconds": sum(r["ms_propose"] + r["ms_simulate"] + r["ms_train"] for r in info) * 1e-3,
+               "ms_propose": last["ms_propose"], "ms_simulate": last["ms_simulate"],
+               "final_round_simulated_days": last["simulated_days"]}
+        if verbose:
+            run["rounds"] = [{k: (round(v, 4) if isinstance(v, float) else v) for k, v in r.items()} for r in info]
+        runs.append(run)
     med = lambda key: float(np.median([r[key] for r in runs]))
     flow_runs = [r for r in runs if r["final_round_proposal"] == "flow"]
-    out = {"workload": "sequential ABC, region_6e7_T100, %d rounds x %d simulations, eps0=%g, factor %g, final "
-                       "eps=%g (the headline eps), flow 3 x 256 BF16; %d independent runs, medians reported"
-                       % (rounds, n, eps0, factor, w["eps"], reps),
+    out = {"workload": "sequential ABC, region_6e7_T100, %d rounds x 2^22, eps x%g per round to the headline eps, "
+                       "flow 3 x 256 BF16, %d runs (medians)" % (rounds, factor, reps),
+           "whole_run_effective_accepted_per_s": med("whole_run_effective_accepted_per_s"),
+           "whole_run_gain_effective_vs_prior": med("whole_run_effective_accepted_per_s") / prior_value,
+           "whole_run_seconds": med("whole_run_seconds"),
            "final_round_accepted_per_s": med("final_round_accepted_per_s"),
            "final_round_effective_accepted_per_s": med("final_round_effective_accepted_per_s"),
+           "final_round_gain_effective_vs_prior": med("final_round_effective_accepted_per_s") / prior_value,
            "final_round_acceptance": med("final_round_acceptance"),
            "runs_ending_on_prior_fallback": reps - len(flow_runs),
            "prior_accepted_per_s_same_eps": prior_value,
-           "gain_effective_vs_prior": med("final_round_effective_accepted_per_s") / prior_value,
-           "all_rounds_seconds": med("all_rounds_seconds"),
+           "whole_run_effective_per_s_by_run": [round(r["whole_run_effective_accepted_per_s"], -3) for r in runs],
            "runs": runs}
     if flow_runs:
         # the final round's simulations of flow proposals (batched kernel with a
         # proposal buffer) against the same ALU roofline as the headline
         sims = sorted(flow_runs, key=lambda r: r["final_round_simulated_days"] / r["ms_simulate"])
         mid = sims[len(sims) // 2]
-        out["simulate_roofline"] = roofline(mid["final_round_simulated_days"], mid["ms_simulate"], sm_count, sm_max)
+        out["simulate_roofline"] = roofline(mid["final_round_simulated_days"], mid["ms_simulate"], sm_count, sm_max,
+                                            samples_per_launch=n)
         ms_prop = float(np.median([r["ms_propose"] for r in flow_runs]))
         # algorithmic work per proposal: every hidden unit once per block (the
         # sampler adds each unit's contribution when its inputs are final), the
@@ -460,21 +552,47 @@ def bench_learned(abc, torch, w, prior_value, peaks, sm_count, sm_max, reps=5):
         macs = sum(16 - (l % 7 + 1) for l in range(H))
         n_flow = int(0.9 * n)
         flops = 2 * macs * blocks * n_flow
-        dense = 3 * 7 * (16 * H + 32 * H) * n_flow     # 7 full dense passes per block
         peak = (peaks or {}).get("bf16_tflops", 1900.0)
         achieved = flops / (ms_prop * 1e-3) / 1e12
         out["sampler_roofline"] = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                                   "frac": achieved / peak, "traffic": None,
-                                   "limit": "instruction issue (71 % of issue slots active, tensor pipe 30 %, in "
-                                            "the ncu capture of this kernel): the sequential inverse leaves 16 x 8 x 16 "
-                                            "products between dependent passes",
-                                   "dense_equivalent_tflops": dense / (ms_prop * 1e-3) / 1e12,
-                                   "basis": "%d FLOP per flow proposal (3 blocks x the masked MADE's %d nonzero "
-                                            "multiply-adds, H = 256), %d flow proposals per round (the other 10 %% "
-                                            "are prior draws), time = the round's proposal stage; dense_equivalent "
-                                            "counts 7 full dense passes per block (%d FLOP per proposal); peak = "
-                                            "measured cuBLAS bf16 burst" % (flops // n_flow, macs, n_flow,
-                                                                             dense // n_flow)}
+                                   "frac": achieved / peak, "traffic": None, "ms_propose": ms_prop,
+                                   "basis": "%d FLOP per flow proposal (masked MADE nonzero multiply-adds), %d flow "
+                                            "proposals per round; peak = measured cuBLAS bf16 burst"
+                                            % (flops // n_flow, n_flow)}
+    return out
+
+
+def summary(line):
+    """The workloads' figures in one short object, last on the line."""
+    def r4(x):
+        return float("%.4g" % x) if isinstance(x, float) else x
+    out = {"c2_headline": {"accepted_per_s": r4(line["value"]), "frac": r4(line["roofline"]["frac"]),
+                           "days_only_frac": r4(line["roofline"]["days_only_frac"]),
+                           "e2e_accepted_per_s": r4((line.get("e2e") or {}).get("value"))}}
+    c1 = line.get("config1")
+    if c1:
+        out["c1_exact_quantile"] = {"accepted": c1["accepted"], "ms_per_run": r4(c1["ms_per_run"]),
+                                    "accepted_per_s": r4(c1["accepted_per_s"]), "eps_ok": c1["eps_equals_workload"],
+                                    "oracle_s": r4((c1.get("cpu_baseline") or {}).get("seconds"))}
+    b = line.get("batched_regions")
+    if b:
+        out["c3_batched"] = {"accepted_per_s": r4(b["value"]), "frac": r4(b["roofline"]["frac"]),
+                             "days_only_frac": r4(b["roofline"]["days_only_frac"])}
+    lp = line.get("learned_proposal")
+    if lp:
+        out["c4_learned"] = {"whole_run_gain": r4(lp["whole_run_gain_effective_vs_prior"]),
+                             "whole_run_effective_per_s": r4(lp["whole_run_effective_accepted_per_s"]),
+                             "final_round_gain": r4(lp["final_round_gain_effective_vs_prior"]),
+                             "whole_run_s": r4(lp["whole_run_seconds"])}
+    st = line.get("streamed_regions")
+    if st:
+        out["c5_prior_stream"] = {"accepted_per_s": r4(st["value"]), "frac": r4(st["roofline"]["frac"]),
+                                  "days_only_frac": r4(st["roofline"]["days_only_frac"])}
+    ls = line.get("learned_stream")
+    if ls:
+        out["c5_learned_stream"] = {"effective_per_s": r4(ls["effective_accepted_per_s"]),
+                                    "gain_vs_prior_stream": r4(ls.get("gain_effective_vs_prior_stream", float("nan"))),
+                                    "seconds": r4(ls["seconds"])}
     return out
 
 
@@ -539,8 +657,11 @@ def main():
     ap.add_argument("--no-learned-stream", action="store_true")
     ap.add_argument("--no-exact", action="store_true")
     ap.add_argument("--no-next", action="store_true", help="skip the projection, PMC and literal-model legs")
+    ap.add_argument("--no-config1", action="store_true")
+    ap.add_argument("--verbose", action="store_true", help="per-round detail of the learned runs")
     ap.add_argument("--leg", default="all", choices=["all", "headline", "batched", "learned", "streamed",
-                                                     "learned_stream", "exact", "projection", "pmc", "literal"],
+                                                     "learned_stream", "exact", "projection", "pmc", "literal",
+                                                     "config1"],
                     help="run one leg only (profiling); 'all' is the benchmark")
     ap.add_argument("--samples", type=int, default=0,
                     help="samples per launch (profiling runs on a smaller case; not a benchmark value)")
@@ -590,10 +711,13 @@ def main():
         abc.abc_sample_async(obs_dev, eps, n, seed, outs, counters[s], mode=w["mode"], first_index=first_index(s),
                              cuda_stream=stream)
 
-    if args.leg in ("batched", "learned", "streamed", "learned_stream", "exact", "projection", "pmc", "literal"):
+    if args.leg in ("batched", "learned", "streamed", "learned_stream", "exact", "projection", "pmc", "literal",
+                    "config1"):
         props = torch.cuda.get_device_properties(dev)
         peaks = measured_peaks() or {}
-        if args.leg == "batched":
+        if args.leg == "config1":
+            out = bench_config1(abc, torch, dev)
+        elif args.leg == "batched":
             out = bench_batched(abc, torch, args.steps, args.warmup, dev, flush, props.multi_processor_count,
                                 peaks.get("sm_max_mhz", 2070.0))
         elif args.leg == "streamed":
@@ -610,7 +734,7 @@ def main():
             out = bench_literal(abc, torch, w, dev, flush, float("nan"))
         else:
             out = bench_learned(abc, torch, w, float("nan"), peaks, props.multi_processor_count,
-                                peaks.get("sm_max_mhz", 2070.0))
+                                peaks.get("sm_max_mhz", 2070.0), verbose=args.verbose)
         print(json.dumps({"leg": args.leg, **out}), flush=True)
         return
     for s in range(args.warmup):
@@ -691,7 +815,7 @@ def main():
         peaks = measured_peaks() or {}
         sm_max = clocks.get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2070.0
         rf = roofline(sim_days[0] / args.steps, float(np.mean(launch_ms)), props.multi_processor_count, sm_max,
-                      traffic=REJECT_TRAFFIC_BYTES if w["n_samples"] == 1 << 24 else None)
+                      traffic=REJECT_TRAFFIC_BYTES if w["n_samples"] == 1 << 24 else None, samples_per_launch=n)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -719,11 +843,16 @@ def main():
             line["cpu_baseline"] = cpu_baseline(w)
         if args.leg == "headline":
             args.no_learned = args.no_batched = args.no_streamed = args.no_learned_stream = args.no_exact = True
-            args.no_next = True
+            args.no_next = args.no_config1 = True
+        if not args.no_config1 and world == 1:
+            line["config1"] = bench_config1(abc, torch, dev)
+            if not args.no_cpu_baseline:
+                line["config1"]["cpu_baseline"] = cpu_baseline_config1()
         if not args.no_exact and world == 1:
             line["exact_mode"] = bench_exact(abc, torch, w, dev, flush, sim_days[0] / (float(np.sum(launch_ms)) * 1e-3))
         if not args.no_learned and world == 1:
-            line["learned_proposal"] = bench_learned(abc, torch, w, value, peaks, props.multi_processor_count, sm_max)
+            line["learned_proposal"] = bench_learned(abc, torch, w, value, peaks, props.multi_processor_count, sm_max,
+                                                     verbose=args.verbose)
         if not args.no_batched and world == 1:
             line["batched_regions"] = bench_batched(abc, torch, args.steps, args.warmup, dev, flush,
                                                     props.multi_processor_count, sm_max)
@@ -736,6 +865,7 @@ def main():
             line["projection"] = bench_projection(abc, torch, w)
             line["pmc"] = bench_pmc(abc, torch, w, value)
             line["literal_model"] = bench_literal(abc, torch, w, dev, flush, fast_dps)
+        line["summary"] = summary(line)
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.barrier()

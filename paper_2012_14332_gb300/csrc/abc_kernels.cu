@@ -133,12 +133,14 @@ __global__ void __launch_bounds__(kBlockThreads) abc_reject_kernel(const __grid_
             __syncwarp();
         }
 
-        // fast mode takes two day pairs per pass between hand-outs, halving
-        // the refill and accept checks (5.586 -> 5.560 ms per 2^24 samples of
-        // P = 6e7, T = 100); exact mode's longer day ran 13 % slower that way
+        // fast mode takes three day pairs per pass between hand-outs, cutting
+        // the refill and accept checks; per 2^24 samples of P = 6e7, T = 100
+        // (interleaved, three repeats): 1 pair 5.462 ms, 2 pairs 5.474, 3 pairs
+        // 5.424, 4 pairs 5.438, 5 pairs 5.503. Exact mode's longer day ran
+        // 13 % slower with two pairs.
         bool accept = false;
 #pragma unroll
-        for (int rep = 0; rep < ((MODE & kFast) ? 2 : 1); ++rep)
+        for (int rep = 0; rep < ((MODE & kFast) ? 3 : 1); ++rep)
         if (active) {
             float z[10];
             day_pair_normals<MODE>(p, i, k, z);

@@ -49,3 +49,18 @@ def test_alu_roofline_arithmetic():
     assert r["frac"] == pytest.approx(2.8e11 / peak)
     # the SFU bound (18 transcendentals per day at 16 per clock) ties with issue
     assert 18.0 / 16.0 == pytest.approx(144.0 / 128.0)
+
+
+def test_roofline_counts_each_samples_own_work():
+    """A sample's prior draw and initial state (104 issue slots) count as
+    104/144 of a simulated day on the issue pipe; days_only_frac leaves them
+    out."""
+    if ROOT not in sys.path:
+        sys.path.insert(0, ROOT)
+    import bench
+    peak = 152 * 2070e6 / (144.0 / 128.0)
+    r = bench.roofline(2.8e8, 1.0, 152, 2070.0, samples_per_launch=1.44e6)
+    assert r["achieved"] == pytest.approx((2.8e8 + 1.04e6) / 1e-3 / 1e9)
+    assert r["frac"] == pytest.approx((2.8e11 + 1.04e9) / peak)
+    assert r["days_only_frac"] == pytest.approx(2.8e11 / peak)
+    assert bench.OPS_PER_SAMPLE["sfu"] == 0.0
