@@ -305,7 +305,7 @@ abc_status abc_plan_set_shape(abc_plan plan, const abc_launch_shape* shape);
  * abc_plan_set_region, no run of the plan may be in flight. */
 abc_status abc_plan_set_eps(abc_plan plan, int32_t region, double eps);
 
-/* Release the plan's device memory and graph. */
+/* Release the plan's device memory and graph. Leaves abc_last_error() as it was. */
 abc_status abc_plan_destroy(abc_plan plan);
 
 /* ------------------------------------------------------------------------
@@ -452,6 +452,8 @@ abc_status abc_maf_train_flows(abc_maf maf, const float* const* theta, const flo
                                int32_t n_steps, int32_t batch, float lr, uint64_t seed, float val_fraction,
                                float* loss_out, void* cuda_stream);
 
+/* Release the flow's device memory and captured training step. Leaves
+ * abc_last_error() as it was. */
 abc_status abc_maf_destroy(abc_maf maf);
 
 /* Sequential ABC with the learned proposal (the SMC-ABC idea of Sec. 2.2):

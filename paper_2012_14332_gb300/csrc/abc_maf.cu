@@ -16,6 +16,7 @@
 // lane ^ 3; row sums are shuffles over the 4 lanes of a row.
 // Weight gradients reduce over rows: their products take the warps' operands
 // from shared memory on tcgen05 and accumulate in tensor memory per CTA.
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -632,6 +633,14 @@ __global__ void __launch_bounds__(kFwdThreads, kSampMinBlocks) sample_kernel(con
 //
 // Every wait is bounded in time (kTcWaitNs). A wait that runs out sets the
 // flow's error word; the kernel still runs to its end and frees its TMEM.
+//
+// The gradient is reproducible bit for bit: the issuing thread takes the
+// compute warps' jobs in a fixed order (job n of warp 0, 1, ..., W-1, then job
+// n + 1), so the tensor-memory accumulations into each column group happen in
+// the same order in every run; db2 and the loss sums collect per warp and add
+// up in warp order; and each CTA writes its whole partial gradient to its own
+// slot of a buffer that grad_reduce_kernel sums in CTA order (no float atomics
+// anywhere).
 
 // compute warps per CTA: 4, or 15 when a step has enough tiles for more than
 // two waves of 4-warp CTAs (one CTA fits per SM; 16 warps in all keep 128
@@ -752,15 +761,15 @@ __global__ void __launch_bounds__((W + 1) * 32, 1) grad_kernel(const uint32_t* _
                                                                const __grid_constant__ Box box,
                                                                const TrainSlot* __restrict__ slots,
                                                                const uint32_t* __restrict__ rows_all, uint32_t batch,
-                                                               float* __restrict__ grad, float* __restrict__ sums,
+                                                               float* __restrict__ part, uint32_t part_stride,
                                                                int* __restrict__ err, int hold)
 {
     static_assert(W >= 4 && W <= 15, "at least one compute warp per TMEM lane quarter; 16 warps in all at most");
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ __align__(8) uint64_t bar_full[W], bar_empty[W], bar_done;
     __shared__ uint32_t tmem_s, init_s;
-    __shared__ float ssum[2];
-    __shared__ float gb2[K * 16];   // the CTA's db2 sums
+    __shared__ float ssum_w[W][2];       // per compute warp: weighted loss sum, weight sum
+    __shared__ float gb2_w[W][K * 16];   // per compute warp: db2 sums
     const Layout L = layout(H);
     const int mb = master_block(H);
     const int f = blockIdx.y;
@@ -771,8 +780,8 @@ __global__ void __launch_bounds__((W + 1) * 32, 1) grad_kernel(const uint32_t* _
     const float* __restrict__ weights = slot.w;
     const uint32_t* __restrict__ rows = rows_all ? rows_all + (size_t)f * batch : nullptr;
     pub += (size_t)f * K * L.words;
-    grad += (size_t)f * K * mb;
-    sums += 2 * f;
+    // this CTA's partial: K blocks of mb parameters, then the two loss sums
+    float* __restrict__ out_part = part + ((size_t)f * gridDim.x + blockIdx.x) * part_stride;
     uint32_t* wsm = reinterpret_cast<uint32_t*>(smem + W * kTcSlot);
     stage_blocks(wsm, pub, K, 0, L.grad_words, L);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -799,8 +808,8 @@ __global__ void __launch_bounds__((W + 1) * 32, 1) grad_kernel(const uint32_t* _
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    for (int i = threadIdx.x; i < K * 16; i += blockDim.x) gb2[i] = 0.f;
-    if (threadIdx.x < 2) ssum[threadIdx.x] = 0.f;
+    for (int i = threadIdx.x; i < W * K * 16; i += blockDim.x) (&gb2_w[0][0])[i] = 0.f;
+    for (int i = threadIdx.x; i < W * 2; i += blockDim.x) (&ssum_w[0][0])[i] = 0.f;
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -856,8 +865,8 @@ __global__ void __launch_bounds__((W + 1) * 32, 1) grad_kernel(const uint32_t* _
                 wsum += __shfl_xor_sync(kFull, wsum, off);
             }
             if (lane == 0) {
-                atomicAdd(&ssum[0], contrib);
-                atomicAdd(&ssum[1], wsum);
+                ssum_w[warp][0] += contrib;
+                ssum_w[warp][1] += wsum;
             }
             // d/dz_K of sum w (-log p(z)) = w tanh(z / 2)
             float gx[4] = {w0 * tanhf(0.5f * x[0]), w0 * tanhf(0.5f * x[1]), w1 * tanhf(0.5f * x[2]),
@@ -892,10 +901,10 @@ __global__ void __launch_bounds__((W + 1) * 32, 1) grad_kernel(const uint32_t* _
                         d[e] += __shfl_xor_sync(kFull, d[e], 16);
                     }
                     if (g == 0) {
-                        atomicAdd(&gb2[16 * b + 2 * t], d[0]);
-                        atomicAdd(&gb2[16 * b + 2 * t + 1], d[1]);
-                        atomicAdd(&gb2[16 * b + 8 + 2 * t], d[2]);
-                        atomicAdd(&gb2[16 * b + 9 + 2 * t], d[3]);
+                        gb2_w[warp][16 * b + 2 * t] += d[0];
+                        gb2_w[warp][16 * b + 2 * t + 1] += d[1];
+                        gb2_w[warp][16 * b + 8 + 2 * t] += d[2];
+                        gb2_w[warp][16 * b + 9 + 2 * t] += d[3];
                     }
                 }
                 // one 16-unit chunk; even and odd chunks keep separate g_x sums
@@ -970,23 +979,27 @@ __global__ void __launch_bounds__((W + 1) * 32, 1) grad_kernel(const uint32_t* _
         // testing: no products, so the wait for bar_done below runs out
         init_s = 0;
     } else if (lane == 0) {
-        // the issuing thread: jobs of warp w in its order (tile, block K-1..0, half)
-        uint32_t next[W], total[W], remaining = 0;
+        // the issuing thread: job n of every warp in warp order, then job n + 1
+        // (a warp's jobs: tile, block K-1..0, half), so each column group
+        // accumulates in the same order in every run
+        uint32_t total[W], most = 0;
 #pragma unroll
         for (int w = 0; w < W; ++w) {
             const uint64_t t0 = (uint64_t)blockIdx.x * W + w;
             total[w] = t0 < tiles ? (uint32_t)((tiles - 1 - t0) / tstride + 1) * (uint32_t)D : 0u;
-            next[w] = 0;
-            remaining += total[w];
+            most = total[w] > most ? total[w] : most;
         }
         uint32_t init = 0;   // accumulator pairs written at least once
-        unsigned long long t_last = global_ns();
-        while (remaining > 0) {
-            bool progress = false;
+        bool ok = true;
+        for (uint32_t n = 0; n < most && ok; ++n) {
 #pragma unroll
             for (int w = 0; w < W; ++w) {
-                const uint32_t n = next[w];
-                if (n == total[w] || !mbar_test(smem_addr(&bar_full[w]), n & 1u)) continue;
+                if (n >= total[w] || !ok) continue;
+                if (!mbar_wait(smem_addr(&bar_full[w]), n & 1u)) {
+                    atomicExch(err, 1);
+                    ok = false;
+                    continue;
+                }
                 tc_fence_after();
                 const uint32_t bi = n / (uint32_t)C;   // block index in the warp's sequence
                 const int c = (int)(n - bi * (uint32_t)C), b = K - 1 - (int)(bi % K);
@@ -998,15 +1011,6 @@ __global__ void __launch_bounds__((W + 1) * 32, 1) grad_kernel(const uint32_t* _
                 tc_mma(tmem + 32 * d, tc_desc(sa), tc_desc(sb), acc);
                 tc_mma(tmem + 32 * d + 16, tc_desc(sa + kTcHalf), tc_desc(sb + 512), acc);
                 tc_commit(smem_addr(&bar_empty[w]));
-                next[w] = n + 1;
-                --remaining;
-                progress = true;
-            }
-            if (progress) {
-                t_last = global_ns();
-            } else if (global_ns() - t_last > kTcWaitNs) {
-                atomicExch(err, 1);
-                break;
             }
         }
         init_s = init;
@@ -1020,42 +1024,72 @@ __global__ void __launch_bounds__((W + 1) * 32, 1) grad_kernel(const uint32_t* _
     const uint32_t init = init_s;
     if (warp < W && done) {
         // warp w reads TMEM lanes 32 (w mod 4) .. + 31; the warps of a lane
-        // quarter share its 2 D column groups
+        // quarter share its 2 D column groups. Every parameter of the CTA's
+        // partial is written: masked entries and column groups this CTA never
+        // accumulated (no tile) as 0.
         const int quarter = warp & 3, per_quarter = (W - quarter + 3) / 4;
         for (int cc = warp >> 2; cc < 2 * D; cc += per_quarter) {
             const int d = cc >> 1;
-            if (!((init >> d) & 1u)) continue;   // uniform over the warp
             uint32_t v[16];
-            tc_ld16(tmem + ((uint32_t)(32 * quarter) << 16) + 16 * cc, v);
+            if ((init >> d) & 1u) {   // uniform over the warp
+                tc_ld16(tmem + ((uint32_t)(32 * quarter) << 16) + 16 * cc, v);
+            } else {
+#pragma unroll
+                for (int o = 0; o < 16; ++o) v[o] = 0u;
+            }
             const int b = d / C, c = d - b * C;
             const int l = kTcM * c + 32 * quarter + lane;
             if (l >= H) continue;
-            float* out = grad + (size_t)b * mb;
+            float* out = out_part + (size_t)b * mb;
             if ((cc & 1) == 0) {
 #pragma unroll
-                for (int o = 0; o < 16; ++o) {
-                    const float val = __uint_as_float(v[o]);
-                    if (mask2(o, l) && val != 0.f) atomicAdd(&out[9 * H + o * H + l], val);
-                }
+                for (int o = 0; o < 16; ++o) out[9 * H + o * H + l] = mask2(o, l) ? __uint_as_float(v[o]) : 0.f;
             } else {
 #pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const float val = __uint_as_float(v[j]);
-                    if (mask1(l, j) && val != 0.f) atomicAdd(&out[l * 8 + j], val);
-                }
-                const float val = __uint_as_float(v[8]);
-                if (val != 0.f) atomicAdd(&out[8 * H + l], val);
+                for (int j = 0; j < 8; ++j) out[l * 8 + j] = mask1(l, j) ? __uint_as_float(v[j]) : 0.f;
+                out[8 * H + l] = __uint_as_float(v[8]);
             }
         }
     }
-    for (int i = threadIdx.x; i < K * 16; i += blockDim.x)
-        if (gb2[i] != 0.f) atomicAdd(&grad[(size_t)(i >> 4) * mb + 25 * H + (i & 15)], gb2[i]);
-    if (threadIdx.x < 2) atomicAdd(&sums[threadIdx.x], ssum[threadIdx.x]);
+    // db2 and the loss sums: the compute warps' parts added in warp order
+    for (int i = threadIdx.x; i < K * 16; i += blockDim.x) {
+        float a = 0.f;
+        for (int w = 0; w < W; ++w) a += gb2_w[w][i];
+        out_part[(size_t)(i >> 4) * mb + 25 * H + (i & 15)] = a;
+    }
+    if (threadIdx.x < 2) {
+        float a = 0.f;
+        for (int w = 0; w < W; ++w) a += ssum_w[w][threadIdx.x];
+        out_part[(size_t)K * mb + threadIdx.x] = a;
+    }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     if (warp == W)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+}
+
+// The flows' gradients and loss sums from the CTAs' partials, added in CTA
+// order: grad[f][p] = sum over c < nblk of part[f][c][p] (p < np), the two
+// loss sums after them. A flow without rows gets zeros (its CTAs returned
+// before writing).
+__global__ void grad_reduce_kernel(const float* __restrict__ part, int nblk, uint32_t part_stride, int np,
+                                   const TrainSlot* __restrict__ slots, const uint32_t* __restrict__ rows_all,
+                                   uint32_t batch, float* __restrict__ grad, float* __restrict__ sums)
+{
+    const int f = blockIdx.y;
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= np + 2) return;
+    const uint64_t n_rows = rows_all ? (slots[f].n ? batch : 0) : slots[f].n;
+    float a = 0.f;
+    if (n_rows) {
+        const float* q = part + (size_t)f * nblk * part_stride + p;
+        for (int c = 0; c < nblk; ++c) a += q[(size_t)c * part_stride];
+    }
+    if (p < np)
+        grad[(size_t)f * np + p] = a;
+    else
+        sums[2 * f + (p - np)] = a;
 }
 
 // batch rows for one training step: uniform indices with replacement
@@ -1111,6 +1145,8 @@ struct abc_maf_s {
     float* d_m = nullptr;
     float* d_v = nullptr;
     float* d_grad = nullptr;
+    float* d_part = nullptr;   // [R][CTAs][part_stride] the gradient kernel's per-CTA partials
+    size_t part_floats = 0;    // allocated size of d_part
     uint32_t* d_pub = nullptr; // [R][K][pub_words] published BF16 operands
     float* d_sums = nullptr;   // [R][2] (weighted loss sum, weight sum)
     int* d_err = nullptr;      // set by a gradient kernel whose bounded wait ran out
@@ -1258,18 +1294,64 @@ cudaError_t launch_sample(abc_maf f, int r, uint64_t n, const float* u, const Mo
     return cudaGetLastError();
 }
 
+// floats per CTA partial: K blocks of parameters and the two loss sums, padded to 16 bytes
+uint32_t part_stride(const abc_maf_s* f) { return (uint32_t)((f->K * maf::master_block(f->H) + 2 + 3) & ~3); }
+
+// compute warps per CTA and CTAs per flow for a gradient over `tiles` 16-row tiles:
+// the wide form when 4-warp CTAs would run more than two waves and it fits
+int grad_form(abc_maf f, uint64_t tiles, int* grid_out)
+{
+    const uint64_t narrow_ctas = (tiles + maf::kGradWarpsNarrow - 1) / maf::kGradWarpsNarrow * (uint64_t)f->R;
+    // the wide form's dynamic shared memory, with 5 KB left for its static part
+    const int W = (narrow_ctas > 2 * (uint64_t)sm_count() && grad_smem(f, maf::kGradWarpsWide) + 5120 <= max_smem_optin())
+                      ? maf::kGradWarpsWide
+                      : maf::kGradWarpsNarrow;
+    const uint64_t want = (tiles + W - 1) / W;
+    *grid_out = (int)(want < (uint64_t)sm_count() ? (want > 0 ? want : 1) : (uint64_t)sm_count());
+    return W;
+}
+
+// the partial buffer for any gradient over at most `tiles` tiles per flow:
+// sized for the 4-warp form's CTAs, which are never fewer than the 15-warp
+// form's and grow with the tiles; allocates, so it is called before a training
+// step is captured
+cudaError_t ensure_part(abc_maf f, uint64_t tiles)
+{
+    const uint64_t want = (tiles + maf::kGradWarpsNarrow - 1) / maf::kGradWarpsNarrow;
+    const uint64_t grid = want < (uint64_t)sm_count() ? (want > 0 ? want : 1) : (uint64_t)sm_count();
+    const size_t need = (size_t)f->R * grid * part_stride(f);
+    if (need <= f->part_floats) return cudaSuccess;
+    // a captured training step holds the old buffer's address
+    if (f->graph) {
+        cudaGraphExecDestroy(f->graph);
+        f->graph = nullptr;
+    }
+    cudaFree(f->d_part);
+    f->d_part = nullptr;
+    f->part_floats = 0;
+    cudaError_t e = cudaMalloc(&f->d_part, sizeof(float) * need);
+    if (e == cudaSuccess) f->part_floats = need;
+    return e;
+}
+
 // gradients of every flow's slot: with rows, `batch` rows per flow; else all
-// max_n points (the largest slot)
+// max_n points (the largest slot). The kernel writes per-CTA partials, the
+// reduction adds them in CTA order into d_grad and d_sums.
 template <int K, int W>
-cudaError_t launch_grad_w(abc_maf f, const uint32_t* rows, uint32_t batch, uint64_t tiles, cudaStream_t s)
+cudaError_t launch_grad_w(abc_maf f, const uint32_t* rows, uint32_t batch, int grid, cudaStream_t s)
 {
     const size_t smem = grad_smem(f, W);
     cudaError_t e = allow_smem(maf::grad_kernel<K, W>, smem);
     if (e != cudaSuccess) return e;
-    const uint64_t want = (tiles + W - 1) / W;
-    const int grid = (int)(want < (uint64_t)sm_count() ? (want > 0 ? want : 1) : (uint64_t)sm_count());
+    const uint32_t stride = part_stride(f);
+    if ((size_t)f->R * grid * stride > f->part_floats) return cudaErrorInvalidValue;   // ensure_part first
     maf::grad_kernel<K, W><<<dim3(grid, f->R), (W + 1) * 32, smem, s>>>(f->d_pub, f->H, f->box, f->d_slots, rows,
-                                                                       batch, f->d_grad, f->d_sums, f->d_err, f->hold);
+                                                                       batch, f->d_part, stride, f->d_err, f->hold);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int np = (int)f->n_params;
+    maf::grad_reduce_kernel<<<dim3((np + 2 + 255) / 256, f->R), 256, 0, s>>>(f->d_part, grid, stride, np, f->d_slots,
+                                                                          rows, batch, f->d_grad, f->d_sums);
     return cudaGetLastError();
 }
 
@@ -1277,11 +1359,10 @@ template <int K>
 cudaError_t launch_grad(abc_maf f, const uint32_t* rows, uint32_t batch, uint64_t max_n, cudaStream_t s)
 {
     const uint64_t tiles = ((rows ? batch : max_n) + 15) / 16;
-    const uint64_t narrow_ctas = (tiles + maf::kGradWarpsNarrow - 1) / maf::kGradWarpsNarrow * (uint64_t)f->R;
-    // the wide form's dynamic shared memory, with 1 KB left for its static part
-    if (narrow_ctas > 2 * (uint64_t)sm_count() && grad_smem(f, maf::kGradWarpsWide) + 1024 <= max_smem_optin())
-        return launch_grad_w<K, maf::kGradWarpsWide>(f, rows, batch, tiles, s);
-    return launch_grad_w<K, maf::kGradWarpsNarrow>(f, rows, batch, tiles, s);
+    int grid = 0;
+    if (grad_form(f, tiles, &grid) == maf::kGradWarpsWide)
+        return launch_grad_w<K, maf::kGradWarpsWide>(f, rows, batch, grid, s);
+    return launch_grad_w<K, maf::kGradWarpsNarrow>(f, rows, batch, grid, s);
 }
 
 #define MAF_DISPATCH(fn, ...)                      \
@@ -1308,8 +1389,7 @@ cudaError_t upload_slots(abc_maf f, const float* const* theta, const float* cons
 // full-data gradients of the flows described by the slot table
 cudaError_t full_gradient(abc_maf f, uint64_t max_n, cudaStream_t s)
 {
-    cudaError_t e = cudaMemsetAsync(f->d_grad, 0, sizeof(float) * f->n_params * f->R, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(f->d_sums, 0, 2 * sizeof(float) * f->R, s);
+    cudaError_t e = ensure_part(f, (max_n + 15) / 16);
     if (e == cudaSuccess) e = MAF_DISPATCH(launch_grad, f, nullptr, 0u, max_n, s);
     return e;
 }
@@ -1584,6 +1664,15 @@ abc_status abc_maf_train_flows(abc_maf f, const float* const* theta, const float
         }
     }
     MAF_TRY(upload_slots(f, th_tr.data(), w_tr.data(), n_tr.data(), s), "cudaMemcpyAsync(slots)");
+    // the gradient partials for both the training batches and the validation
+    // sets, allocated before the step is captured (a later reallocation would
+    // drop the captured step)
+    {
+        uint64_t max_va = 0;
+        for (int r = 0; r < R; ++r) max_va = n_va[r] > max_va ? n_va[r] : max_va;
+        const uint64_t rows = std::max<uint64_t>((uint64_t)batch, max_va);
+        MAF_TRY(ensure_part(f, (rows + 15) / 16), "cudaMalloc(gradient partials)");
+    }
     // fresh Adam moments for this training run
     const size_t np = sizeof(float) * f->n_params * f->R;
     MAF_TRY(cudaMemsetAsync(f->d_m, 0, np, s), "cudaMemsetAsync");
@@ -1603,8 +1692,6 @@ abc_status abc_maf_train_flows(abc_maf f, const float* const* theta, const float
             MAF_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
             maf::batch_rows_kernel<<<dim3((batch + 127) / 128, f->R), 128, 0, s>>>(p, f->d_step, f->d_slots,
                                                                                  (uint32_t)batch, f->d_rows);
-            cudaMemsetAsync(f->d_grad, 0, np, s);
-            cudaMemsetAsync(f->d_sums, 0, 2 * sizeof(float) * f->R, s);
             cudaError_t e = MAF_DISPATCH(launch_grad, f, f->d_rows, (uint32_t)batch, 0, s);
             maf::tick_kernel<<<1, 1, 0, s>>>(f->d_step);
             if (e == cudaSuccess) e = launch_adam(f, lr, 0.9f, 0.999f, 1e-8f, s);
@@ -1739,6 +1826,7 @@ abc_status abc_maf_destroy(abc_maf f)
     cudaFree(f->d_m);
     cudaFree(f->d_v);
     cudaFree(f->d_grad);
+    cudaFree(f->d_part);
     cudaFree(f->d_pub);
     cudaFree(f->d_sums);
     cudaFree(f->d_step);
@@ -1747,7 +1835,9 @@ abc_status abc_maf_destroy(abc_maf f)
     cudaFree(f->d_err);
     cudaFree(f->d_best);
     delete f;
-    return plan_ok();
+    // leaves the thread's last error as it was: drivers destroy their flows
+    // on the way out of a failed call
+    return ABC_OK;
 }
 
 }  // extern "C"

@@ -461,7 +461,9 @@ abc_status abc_plan_destroy(abc_plan plan)
 {
     if (!plan) return plan_fail(ABC_ERR_INVALID_ARG, "plan is NULL");
     free_plan(plan);
-    return plan_ok();
+    // leaves the thread's last error as it was: drivers destroy their plans on
+    // the way out of a failed call
+    return ABC_OK;
 }
 
 }  // extern "C"

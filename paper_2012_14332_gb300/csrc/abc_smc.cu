@@ -93,7 +93,8 @@ __global__ void logw_kernel(const float* __restrict__ logq, const uint64_t* __re
 }
 
 __global__ void weight_kernel(const float* __restrict__ lw, uint64_t m, WeightScratch* ws, float* __restrict__ w_train,
-                              double* __restrict__ w_exact, double* __restrict__ pool, uint64_t pool_k, double power)
+                              double* __restrict__ w_exact, double* __restrict__ pool, uint64_t pool_k, double power,
+                              double* __restrict__ block_sums)
 {
     __shared__ double part[2][8];
     const uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -123,8 +124,132 @@ __global__ void weight_kernel(const float* __restrict__ lw, uint64_t m, WeightSc
             sa += part[0][k];
             sb += part[1][k];
         }
-        atomicAdd(&ws->sums[0], sa);
-        atomicAdd(&ws->sums[1], sb);
+        block_sums[2 * blockIdx.x] = sa;
+        block_sums[2 * blockIdx.x + 1] = sb;
+    }
+}
+
+// sum v and sum v^2 from the blocks' sums in block order (one block of 256):
+// thread t adds blocks t, t + 256, ... in turn, thread 0 adds the threads' sums
+// in turn, so the sums are the same in every run
+__global__ void weight_sums_kernel(const double* __restrict__ block_sums, unsigned nblk, WeightScratch* ws)
+{
+    __shared__ double part[2][256];
+    double a = 0.0, b = 0.0;
+    for (unsigned k = threadIdx.x; k < nblk; k += blockDim.x) {
+        a += block_sums[2 * k];
+        b += block_sums[2 * k + 1];
+    }
+    part[0][threadIdx.x] = a;
+    part[1][threadIdx.x] = b;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double sa = 0.0, sb = 0.0;
+        for (int t = 0; t < (int)blockDim.x; ++t) {
+            sa += part[0][t];
+            sb += part[1][t];
+        }
+        ws->sums[0] = sa;
+        ws->sums[1] = sb;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// The accepted samples of a run in ascending sample index. The batched kernel
+// hands out accept slots with atomicAdd, so its buffers' order changes from
+// run to run; the drivers build the weights, the pools and the training sets
+// from this sorted copy, which makes every later step (training-set split,
+// batch rows, hence the trained flows) the same in every run with one seed.
+// A run's indices lie in [first, first + n): pos[i - first] takes the accept
+// slot of index i (all ones for none), a scan over 1024-index blocks gives
+// each accepted index its rank, and the gather writes the samples by rank.
+// ---------------------------------------------------------------------------
+constexpr uint32_t kNoSlot = 0xFFFFFFFFu;
+constexpr int kSortBlock = 1024;   // indices per scan block (256 threads x 4)
+
+__global__ void scatter_slots_kernel(const uint64_t* __restrict__ idx, uint64_t m, uint64_t first,
+                                     uint32_t* __restrict__ pos)
+{
+    const uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < m) pos[idx[j] - first] = (uint32_t)j;
+}
+
+// exclusive scan of the 256 threads' counts; returns this thread's offset, *total the block's sum
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* total)
+{
+    __shared__ uint32_t warp_sums[8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, off);
+        if (lane >= off) x += y;
+    }
+    if (lane == 31) warp_sums[warp] = x;
+    __syncthreads();
+    uint32_t before = 0, all = 0;
+    for (int w = 0; w < 8; ++w) {
+        if (w < warp) before += warp_sums[w];
+        all += warp_sums[w];
+    }
+    __syncthreads();
+    *total = all;
+    return before + x - v;
+}
+
+__global__ void __launch_bounds__(256) count_slots_kernel(const uint32_t* __restrict__ pos, uint64_t n,
+                                                          uint32_t* __restrict__ block_count)
+{
+    const uint64_t base = (uint64_t)blockIdx.x * kSortBlock + 4 * threadIdx.x;
+    uint32_t c = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) c += (base + q < n && pos[base + q] != kNoSlot) ? 1u : 0u;
+    uint32_t total = 0;
+    block_exclusive_scan(c, &total);
+    if (threadIdx.x == 0) block_count[blockIdx.x] = total;
+}
+
+// in-place exclusive scan of nb block counts, one block of 256 threads, in order
+__global__ void __launch_bounds__(256) scan_counts_kernel(uint32_t* __restrict__ count, uint32_t nb)
+{
+    uint32_t carry = 0;
+    for (uint32_t b0 = 0; b0 < nb; b0 += 256) {
+        const uint32_t b = b0 + threadIdx.x;
+        const uint32_t v = b < nb ? count[b] : 0u;
+        uint32_t total = 0;
+        const uint32_t off = block_exclusive_scan(v, &total);
+        if (b < nb) count[b] = carry + off;
+        carry += total;
+    }
+}
+
+__global__ void __launch_bounds__(256) gather_sorted_kernel(const uint32_t* __restrict__ pos, uint64_t n,
+                                                            const uint32_t* __restrict__ block_off,
+                                                            const float* __restrict__ theta,
+                                                            const double* __restrict__ dist,
+                                                            const uint64_t* __restrict__ idx,
+                                                            float* __restrict__ theta_o, double* __restrict__ dist_o,
+                                                            uint64_t* __restrict__ idx_o)
+{
+    const uint64_t base = (uint64_t)blockIdx.x * kSortBlock + 4 * threadIdx.x;
+    uint32_t slot[4], c = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        slot[q] = base + q < n ? pos[base + q] : kNoSlot;
+        c += slot[q] != kNoSlot ? 1u : 0u;
+    }
+    uint32_t total = 0;
+    uint32_t r = block_off[blockIdx.x] + block_exclusive_scan(c, &total);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        if (slot[q] == kNoSlot) continue;
+        const float4* src = reinterpret_cast<const float4*>(theta + 8 * (size_t)slot[q]);
+        float4* dst = reinterpret_cast<float4*>(theta_o + 8 * (size_t)r);
+        dst[0] = src[0];
+        dst[1] = src[1];
+        dist_o[r] = dist[slot[q]];
+        idx_o[r] = idx[slot[q]];
+        ++r;
     }
 }
 
@@ -201,15 +326,17 @@ static abc_status shuffled_training_set(const float* theta, const W* w, uint64_t
 // densities, NULL for prior draws): float training weights v_j into w_train,
 // optionally v_j in double into w_exact and the unnormalised weights of the
 // first pool_k samples into pool; *sum_v, *sum_v2 for the ESS. Synchronizes s.
+// d_block_sums: 2 doubles per 256 samples (the sums are added in block order).
 static abc_status round_weights(const float* logq, const uint64_t* idx, uint64_t first, uint64_t m, double log_prior,
                                 float* d_lw, float* w_train, double* w_exact, double* pool, uint64_t pool_k,
-                                WeightScratch* d_ws, cudaStream_t s, double* sum_v, double* sum_v2,
-                                double power, uint64_t tail_first, uint64_t* n_tail)
+                                WeightScratch* d_ws, double* d_block_sums, cudaStream_t s, double* sum_v,
+                                double* sum_v2, double power, uint64_t tail_first, uint64_t* n_tail)
 {
     SMC_TRY(cudaMemsetAsync(d_ws, 0, sizeof(WeightScratch), s), "cudaMemsetAsync(weight scratch)");
     const unsigned blocks = (unsigned)((m + 255) / 256);
     logw_kernel<<<blocks, 256, 0, s>>>(logq, idx, first, m, tail_first, (float)log_prior, d_lw, d_ws);
-    weight_kernel<<<blocks, 256, 0, s>>>(d_lw, m, d_ws, w_train, w_exact, pool, pool_k, power);
+    weight_kernel<<<blocks, 256, 0, s>>>(d_lw, m, d_ws, w_train, w_exact, pool, pool_k, power, d_block_sums);
+    weight_sums_kernel<<<1, 256, 0, s>>>(d_block_sums, blocks, d_ws);
     SMC_TRY(cudaGetLastError(), "weight launch");
     WeightScratch h;
     SMC_TRY(cudaMemcpyAsync(&h, d_ws, sizeof h, cudaMemcpyDeviceToHost, s), "cudaMemcpyAsync(weight sums)");
@@ -217,6 +344,51 @@ static abc_status round_weights(const float* logq, const uint64_t* idx, uint64_t
     *sum_v = h.sums[0];
     *sum_v2 = h.sums[1];
     *n_tail = h.n_tail;
+    return ABC_OK;
+}
+
+// Device scratch of sort_accepted for runs of n sample indices and up to cap
+// accepted samples, and of round_weights' block sums.
+struct SortScratch {
+    uint32_t* pos = nullptr;     // [n]
+    uint32_t* count = nullptr;   // [n / 1024 + 1]
+    float* theta = nullptr;      // [cap][8], the sorted samples
+    double* dist = nullptr;      // [cap]
+    uint64_t* idx = nullptr;     // [cap]
+    double* block_sums = nullptr;   // [2 (cap / 256 + 1)]
+};
+
+static abc_status alloc_sort_scratch(SortScratch& sc, uint64_t n, uint64_t cap, std::vector<void*>& owned)
+{
+    const uint64_t nb = (n + kSortBlock - 1) / kSortBlock + 1;
+    SMC_TRY(cudaMalloc(&sc.pos, sizeof(uint32_t) * n), "cudaMalloc(sort positions)");
+    owned.push_back(sc.pos);
+    SMC_TRY(cudaMalloc(&sc.count, sizeof(uint32_t) * nb), "cudaMalloc(sort counts)");
+    owned.push_back(sc.count);
+    SMC_TRY(cudaMalloc(&sc.theta, sizeof(float) * 8 * cap), "cudaMalloc(sorted theta)");
+    owned.push_back(sc.theta);
+    SMC_TRY(cudaMalloc(&sc.dist, sizeof(double) * cap), "cudaMalloc(sorted dist)");
+    owned.push_back(sc.dist);
+    SMC_TRY(cudaMalloc(&sc.idx, sizeof(uint64_t) * cap), "cudaMalloc(sorted idx)");
+    owned.push_back(sc.idx);
+    SMC_TRY(cudaMalloc(&sc.block_sums, sizeof(double) * 2 * (cap / 256 + 1)), "cudaMalloc(weight block sums)");
+    owned.push_back(sc.block_sums);
+    return ABC_OK;
+}
+
+// The m accepted samples of a run over indices [first, first + n) into
+// sc.theta, sc.dist, sc.idx in ascending index (the kernels above). Async.
+static abc_status sort_accepted(const float* theta, const double* dist, const uint64_t* idx, uint64_t m, uint64_t first,
+                                uint64_t n, SortScratch& sc, cudaStream_t s)
+{
+    if (m == 0) return ABC_OK;
+    const uint32_t nb = (uint32_t)((n + kSortBlock - 1) / kSortBlock);
+    SMC_TRY(cudaMemsetAsync(sc.pos, 0xFF, sizeof(uint32_t) * n, s), "cudaMemsetAsync(sort positions)");
+    scatter_slots_kernel<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(idx, m, first, sc.pos);
+    count_slots_kernel<<<nb, 256, 0, s>>>(sc.pos, n, sc.count);
+    scan_counts_kernel<<<1, 256, 0, s>>>(sc.count, nb);
+    gather_sorted_kernel<<<nb, 256, 0, s>>>(sc.pos, n, sc.count, theta, dist, idx, sc.theta, sc.dist, sc.idx);
+    SMC_TRY(cudaGetLastError(), "sort launch");
     return ABC_OK;
 }
 
@@ -282,6 +454,8 @@ extern "C" abc_status abc_smc_run(const abc_prior_box* prior, const int32_t* obs
     float* d_train = nullptr;
     SMC_TRY(cudaMalloc(&d_train, sizeof(float) * 8 * cap), "cudaMalloc(training set)");
     gd.dev.push_back(d_train);
+    SortScratch ss;
+    SMC_ST(alloc_sort_scratch(ss, N, cap, gd.dev));
     for (cudaEvent_t& e : gd.ev) SMC_TRY(cudaEventCreate(&e), "cudaEventCreate");
 
     double eps = cfg->eps0;
@@ -345,6 +519,11 @@ extern "C" abc_status abc_smc_run(const abc_prior_box* prior, const int32_t* obs
         R.n_accepted = n_acc;
         R.simulated_days = days;
         const uint64_t m = std::min(n_acc, cap);
+        // the accepted samples in index order, the same in every run
+        SMC_ST(sort_accepted(acc_theta, acc_dist, acc_idx, m, first, N, ss, s));
+        acc_theta = ss.theta;
+        acc_dist = ss.dist;
+        acc_idx = ss.idx;
         const bool last = r + 1 == cfg->rounds;
         // importance weights prior / q_mix of the kept accepted samples
         double sw = 0.0, sw2 = 0.0;
@@ -353,8 +532,8 @@ extern "C" abc_status abc_smc_run(const abc_prior_box* prior, const int32_t* obs
             const uint64_t tail_first = use_flow ? first + N - R.n_defensive : UINT64_MAX;
             uint64_t n_tail = 0;
             SMC_ST(round_weights(use_flow ? d_logq : nullptr, acc_idx, first, m, log_prior, d_acc_logq, d_wround,
-                                 last ? weight_out : nullptr, nullptr, 0, d_ws, s, &sw, &sw2, cfg->train_weight_power,
-                                 tail_first, &n_tail));
+                                 last ? weight_out : nullptr, nullptr, 0, d_ws, ss.block_sums, s, &sw, &sw2,
+                                 cfg->train_weight_power, tail_first, &n_tail));
             R.ess_fraction = sw2 > 0.0 ? sw * sw / sw2 / (double)m : 0.0;
             R.n_defensive_accepted = n_tail;
         }
@@ -473,6 +652,8 @@ extern "C" abc_status abc_smc_run_regions(const abc_prior_box* prior, abc_smc_re
     gd.dev.push_back(d_w);
     SMC_TRY(cudaMalloc(&d_train, sizeof(float) * 8 * cap * R), "cudaMalloc(training sets)");
     gd.dev.push_back(d_train);
+    SortScratch ss;
+    SMC_ST(alloc_sort_scratch(ss, N, cap, gd.dev));
     for (cudaEvent_t& e : gd.ev) SMC_TRY(cudaEventCreate(&e), "cudaEventCreate");
 
     // one plan for every round: the regions' eps, proposals and first indices
@@ -549,6 +730,12 @@ extern "C" abc_status abc_smc_run_regions(const abc_prior_box* prior, abc_smc_re
             Rr[g].n_accepted = n_acc;
             Rr[g].simulated_days = days;
             const uint64_t m = std::min(n_acc, cap);
+            // the accepted samples in index order, the same in every run (the
+            // sorted copy is used up by this region's copies before the next)
+            SMC_ST(sort_accepted(acc_theta, acc_dist, acc_idx, m, first, N, ss, s));
+            acc_theta = ss.theta;
+            acc_dist = ss.dist;
+            acc_idx = ss.idx;
             trainable[g] = 0;
             next_flow[g] = 0;
             tr_n[g] = 0;
@@ -561,8 +748,9 @@ extern "C" abc_status abc_smc_run_regions(const abc_prior_box* prior, abc_smc_re
             double sw = 0.0, sw2 = 0.0;
             uint64_t n_tail = 0;
             SMC_ST(round_weights(use_flow[g] ? d_logq + (size_t)g * N : nullptr, acc_idx, first, m, log_prior,
-                                 d_acc_logq, d_wround, nullptr, pw, k, d_ws, s, &sw, &sw2, cfg->train_weight_power,
-                                 use_flow[g] ? first + N - Rr[g].n_defensive : UINT64_MAX, &n_tail));
+                                 d_acc_logq, d_wround, nullptr, pw, k, d_ws, ss.block_sums, s, &sw, &sw2,
+                                 cfg->train_weight_power, use_flow[g] ? first + N - Rr[g].n_defensive : UINT64_MAX,
+                                 &n_tail));
             Rr[g].ess_fraction = sw2 > 0.0 ? sw * sw / sw2 / (double)m : 0.0;
             Rr[g].n_defensive_accepted = n_tail;
             // samples accepted at the region's final eps join the pool; the
