@@ -339,14 +339,20 @@ __device__ __forceinline__ void stage_blocks(uint32_t* sm, const uint32_t* pub, 
 // ---------------------------------------------------------------------------
 // publish: masked BF16 copies (and biases) from the FP32 master parameters
 // ---------------------------------------------------------------------------
-__global__ void publish_kernel(const float* __restrict__ master, uint32_t* __restrict__ pub, int K, int H)
+// Words [0, limit) of each block's published operands (limit = L.words: all;
+// L.grad_words: what the density and gradient kernels read, enough between
+// training steps). step, if not NULL, is advanced by one once the launch's
+// blocks have read nothing from it (the training step's tick).
+__global__ void publish_kernel(const float* __restrict__ master, uint32_t* __restrict__ pub, int K, int H, int limit,
+                               int* __restrict__ step)
 {
     const Layout L = layout(H);
     const int per = L.words, mb = master_block(H), hw = H / 2 + 4;
+    if (step && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *step += 1;
     master += (size_t)blockIdx.y * K * mb;   // flow blockIdx.y
     pub += (size_t)blockIdx.y * K * per;
-    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < K * per; idx += gridDim.x * blockDim.x) {
-        const int b = idx / per, w = idx % per;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < K * limit; i += gridDim.x * blockDim.x) {
+        const int b = i / limit, w = i % limit, idx = b * per + w;
         const float* M = master + (size_t)b * mb;
         const float* W1 = M;
         const float* b1 = M + 8 * H;
@@ -1069,6 +1075,23 @@ __global__ void __launch_bounds__((W + 1) * 32, 1) grad_kernel(const uint32_t* _
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
 }
 
+// q[0] + q[stride] + ... + q[(nblk - 1) stride], added in that order; the
+// loads go out eight at a time so their latencies overlap
+__device__ __forceinline__ float sum_in_order(const float* __restrict__ q, int nblk, uint32_t stride)
+{
+    float a = 0.f;
+    int c = 0;
+    for (; c + 8 <= nblk; c += 8) {
+        float x[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) x[k] = q[(size_t)(c + k) * stride];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) a += x[k];
+    }
+    for (; c < nblk; ++c) a += q[(size_t)c * stride];
+    return a;
+}
+
 // The flows' gradients and loss sums from the CTAs' partials, added in CTA
 // order: grad[f][p] = sum over c < nblk of part[f][c][p] (p < np), the two
 // loss sums after them. A flow without rows gets zeros (its CTAs returned
@@ -1081,11 +1104,7 @@ __global__ void grad_reduce_kernel(const float* __restrict__ part, int nblk, uin
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= np + 2) return;
     const uint64_t n_rows = rows_all ? (slots[f].n ? batch : 0) : slots[f].n;
-    float a = 0.f;
-    if (n_rows) {
-        const float* q = part + (size_t)f * nblk * part_stride + p;
-        for (int c = 0; c < nblk; ++c) a += q[(size_t)c * part_stride];
-    }
+    const float a = n_rows ? sum_in_order(part + (size_t)f * nblk * part_stride + p, nblk, part_stride) : 0.f;
     if (p < np)
         grad[(size_t)f * np + p] = a;
     else
@@ -1105,7 +1124,46 @@ __global__ void batch_rows_kernel(const __grid_constant__ ModelParams p, const i
     rows[(size_t)f * batch + b] = (uint32_t)r;
 }
 
+// One Adam update (Kingma, Ba 2015) of a parameter with gradient gr at step
+// t >= 1; the fused multiply-adds are written out, so both Adam kernels round
+// alike.
+__device__ __forceinline__ void adam_update(float& param, float& m, float& v, float gr, int t, float lr, float b1,
+                                            float b2, float eps)
+{
+    const float mi = __fmaf_rn(b1, m, __fmul_rn(1.f - b1, gr));
+    const float vi = __fmaf_rn(b2, v, __fmul_rn(__fmul_rn(1.f - b2, gr), gr));
+    m = mi;
+    v = vi;
+    const float mh = __fdiv_rn(mi, 1.f - powf(b1, (float)t));
+    const float vh = __fdiv_rn(vi, 1.f - powf(b2, (float)t));
+    param = __fmaf_rn(-lr, __fdiv_rn(mh, __fadd_rn(sqrtf(vh), eps)), param);
+}
+
 __global__ void tick_kernel(int* step) { *step += 1; }
+
+// adam_kernel on the gradient kernel's per-CTA partials, added here in CTA
+// order (the training step's reduction), at step *step + 1 (the publish
+// launch after it advances the counter). A flow without rows this step keeps
+// its parameters and moments.
+__global__ void adam_partials_kernel(float* __restrict__ params, const float* __restrict__ part, int nblk,
+                                     uint32_t part_stride, const TrainSlot* __restrict__ slots, float* __restrict__ m,
+                                     float* __restrict__ v, const int* __restrict__ step, int64_t n_params, int64_t n,
+                                     float lr, float b1, float b2, float eps)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t f = i / n_params, p = i - f * n_params;
+    if (slots[f].n == 0) return;
+    const float* q = part + (size_t)f * nblk * part_stride;
+    const float W = sum_in_order(q + n_params + 1, nblk, part_stride);
+    if (!(W > 0.f)) return;
+    const float g = sum_in_order(q + p, nblk, part_stride);
+    float pi = params[i], mi = m[i], vi = v[i];
+    adam_update(pi, mi, vi, __fdiv_rn(g, W), *step + 1, lr, b1, b2, eps);
+    params[i] = pi;
+    m[i] = mi;
+    v[i] = vi;
+}
 
 // n_params per flow; flows one after another. A flow whose weight sum is 0
 // (no points this step) keeps its parameters and moments.
@@ -1117,15 +1175,11 @@ __global__ void adam_kernel(float* __restrict__ params, const float* __restrict_
     if (i >= n) return;
     const float W = sums[2 * (i / n_params) + 1];
     if (!(W > 0.f)) return;
-    const int t = *step;
-    const float gr = grad[i] / W;
-    const float mi = b1 * m[i] + (1.f - b1) * gr;
-    const float vi = b2 * v[i] + (1.f - b2) * gr * gr;
+    float pi = params[i], mi = m[i], vi = v[i];
+    adam_update(pi, mi, vi, __fdiv_rn(grad[i], W), *step, lr, b1, b2, eps);
+    params[i] = pi;
     m[i] = mi;
     v[i] = vi;
-    const float mh = mi / (1.f - powf(b1, (float)t));
-    const float vh = vi / (1.f - powf(b2, (float)t));
-    params[i] -= lr * mh / (sqrtf(vh) + eps);
 }
 
 }  // namespace maf
@@ -1263,7 +1317,17 @@ const uint32_t* flow_pub(abc_maf f, int r) { return f->d_pub + (size_t)r * f->K 
 cudaError_t publish(abc_maf f, cudaStream_t s)
 {
     const int n = f->K * f->pub_words;
-    maf::publish_kernel<<<dim3((n + 255) / 256, f->R), 256, 0, s>>>(f->d_params, f->d_pub, f->K, f->H);
+    maf::publish_kernel<<<dim3((n + 255) / 256, f->R), 256, 0, s>>>(f->d_params, f->d_pub, f->K, f->H, f->pub_words,
+                                                                    nullptr);
+    return cudaGetLastError();
+}
+
+// a training step's publish: the words the gradient kernel reads, and the tick
+cudaError_t publish_step(abc_maf f, cudaStream_t s)
+{
+    const int limit = maf::layout(f->H).grad_words, n = f->K * limit;
+    maf::publish_kernel<<<dim3((n + 255) / 256, f->R), 256, 0, s>>>(f->d_params, f->d_pub, f->K, f->H, limit,
+                                                                    f->d_step);
     return cudaGetLastError();
 }
 
@@ -1338,7 +1402,7 @@ cudaError_t ensure_part(abc_maf f, uint64_t tiles)
 // max_n points (the largest slot). The kernel writes per-CTA partials, the
 // reduction adds them in CTA order into d_grad and d_sums.
 template <int K, int W>
-cudaError_t launch_grad_w(abc_maf f, const uint32_t* rows, uint32_t batch, int grid, cudaStream_t s)
+cudaError_t launch_grad_w(abc_maf f, const uint32_t* rows, uint32_t batch, int grid, bool reduce, cudaStream_t s)
 {
     const size_t smem = grad_smem(f, W);
     cudaError_t e = allow_smem(maf::grad_kernel<K, W>, smem);
@@ -1348,21 +1412,23 @@ cudaError_t launch_grad_w(abc_maf f, const uint32_t* rows, uint32_t batch, int g
     maf::grad_kernel<K, W><<<dim3(grid, f->R), (W + 1) * 32, smem, s>>>(f->d_pub, f->H, f->box, f->d_slots, rows,
                                                                        batch, f->d_part, stride, f->d_err, f->hold);
     e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    if (e != cudaSuccess || !reduce) return e;
     const int np = (int)f->n_params;
     maf::grad_reduce_kernel<<<dim3((np + 2 + 255) / 256, f->R), 256, 0, s>>>(f->d_part, grid, stride, np, f->d_slots,
                                                                           rows, batch, f->d_grad, f->d_sums);
     return cudaGetLastError();
 }
 
+// reduce: add the partials into d_grad and d_sums (a training step's Adam adds
+// them itself instead)
 template <int K>
-cudaError_t launch_grad(abc_maf f, const uint32_t* rows, uint32_t batch, uint64_t max_n, cudaStream_t s)
+cudaError_t launch_grad(abc_maf f, const uint32_t* rows, uint32_t batch, uint64_t max_n, bool reduce, cudaStream_t s)
 {
     const uint64_t tiles = ((rows ? batch : max_n) + 15) / 16;
     int grid = 0;
     if (grad_form(f, tiles, &grid) == maf::kGradWarpsWide)
-        return launch_grad_w<K, maf::kGradWarpsWide>(f, rows, batch, grid, s);
-    return launch_grad_w<K, maf::kGradWarpsNarrow>(f, rows, batch, grid, s);
+        return launch_grad_w<K, maf::kGradWarpsWide>(f, rows, batch, grid, reduce, s);
+    return launch_grad_w<K, maf::kGradWarpsNarrow>(f, rows, batch, grid, reduce, s);
 }
 
 #define MAF_DISPATCH(fn, ...)                      \
@@ -1390,7 +1456,7 @@ cudaError_t upload_slots(abc_maf f, const float* const* theta, const float* cons
 cudaError_t full_gradient(abc_maf f, uint64_t max_n, cudaStream_t s)
 {
     cudaError_t e = ensure_part(f, (max_n + 15) / 16);
-    if (e == cudaSuccess) e = MAF_DISPATCH(launch_grad, f, nullptr, 0u, max_n, s);
+    if (e == cudaSuccess) e = MAF_DISPATCH(launch_grad, f, nullptr, 0u, max_n, true, s);
     return e;
 }
 
@@ -1400,6 +1466,25 @@ cudaError_t launch_adam(abc_maf f, float lr, float b1, float b2, float eps, cuda
     maf::adam_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(f->d_params, f->d_grad, f->d_m, f->d_v, f->d_sums,
                                                                  f->d_step, f->n_params, n, lr, b1, b2, eps);
     return cudaGetLastError();
+}
+
+// one training step on `batch` drawn rows per flow: batch rows, per-CTA
+// gradient partials, Adam adding the partials in CTA order, publish with the
+// tick (captured once and replayed)
+cudaError_t launch_train_step(abc_maf f, uint32_t batch, const ModelParams& p, float lr, cudaStream_t s)
+{
+    maf::batch_rows_kernel<<<dim3((batch + 127) / 128, f->R), 128, 0, s>>>(p, f->d_step, f->d_slots, batch, f->d_rows);
+    cudaError_t e = MAF_DISPATCH(launch_grad, f, f->d_rows, batch, 0, false, s);
+    if (e != cudaSuccess) return e;
+    int grid = 0;
+    grad_form(f, ((uint64_t)batch + 15) / 16, &grid);
+    const int64_t n = f->n_params * f->R;
+    maf::adam_partials_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(
+        f->d_params, f->d_part, grid, part_stride(f), f->d_slots, f->d_m, f->d_v, f->d_step, f->n_params, n, lr, 0.9f,
+        0.999f, 1e-8f);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = publish_step(f, s);
+    return e;
 }
 
 }  // namespace
@@ -1690,12 +1775,7 @@ abc_status abc_maf_train_flows(abc_maf f, const float* const* theta, const float
             const ModelParams p = plan_make_params(nullptr, 1, 1, seed, 0, nullptr);
             cudaGraph_t gph = nullptr;
             MAF_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
-            maf::batch_rows_kernel<<<dim3((batch + 127) / 128, f->R), 128, 0, s>>>(p, f->d_step, f->d_slots,
-                                                                                 (uint32_t)batch, f->d_rows);
-            cudaError_t e = MAF_DISPATCH(launch_grad, f, f->d_rows, (uint32_t)batch, 0, s);
-            maf::tick_kernel<<<1, 1, 0, s>>>(f->d_step);
-            if (e == cudaSuccess) e = launch_adam(f, lr, 0.9f, 0.999f, 1e-8f, s);
-            if (e == cudaSuccess) e = publish(f, s);
+            cudaError_t e = launch_train_step(f, (uint32_t)batch, p, lr, s);
             cudaError_t ec = cudaStreamEndCapture(s, &gph);
             if (e != cudaSuccess || ec != cudaSuccess) {
                 if (gph) cudaGraphDestroy(gph);
@@ -1776,8 +1856,11 @@ abc_status abc_maf_train_flows(abc_maf f, const float* const* theta, const float
             for (int r = 0; r < R; ++r) loss_out[r] = n_va[r] > 0 && best[r] < INFINITY ? best[r] : 0.f;
         return plan_ok();
     }
-    if (n_steps > 0)
+    if (n_steps > 0) {
         for (int32_t i = 0; i < n_steps; ++i) MAF_TRY(cudaGraphLaunch(f->graph, s), "cudaGraphLaunch");
+        // the steps publish what the gradient reads; the sampler's operands now
+        MAF_TRY(publish(f, s), "publish");
+    }
     if (loss_out) {
         MAF_TRY(full_gradient(f, max_n, s), "flow loss");
         std::vector<float> sums(2 * (size_t)f->R);
