@@ -69,8 +69,9 @@ __host__ __device__ inline int master_block(int H) { return 25 * H + 16; }
 //                        warp's fragment loads meet 32 distinct banks
 // then the sampler's copy of the forward operands (sw1, sw2, sb1 in the w1,
 // w2, b1 layouts, and sb2 = b2), whose 16-unit chunks hold the hidden units
-// grouped by degree: the chunks of degree d = 1..7 hold units d - 1, d + 6,
-// d + 13, ... in order, the last chunk of each degree padded with zero units.
+// grouped by degree: every degree d = 1..7 has the same number of chunks,
+// sampler_cpd(H) (the chunks degree 1, which has the most units, needs),
+// holding units d - 1, d + 6, d + 13, ... in order, padded with zero units.
 struct Layout {
     int w1, w2, b1, b2, w1t, w2t, fwd_words, grad_words;
     int sw1, sw2, sb1, sb2, samp_words, words;
@@ -84,24 +85,14 @@ __host__ __device__ inline bool mask2(int o, int l) { return (o % 8) + 1 > (l % 
 // hidden units of degree d (1..7) among H, and the 16-unit chunks they fill
 __host__ __device__ inline int degree_units(int H, int d) { return (H - d) / 7 + 1; }
 __host__ __device__ inline int degree_chunks(int H, int d) { return (degree_units(H, d) + 15) / 16; }
-__host__ __device__ inline int sampler_chunks(int H)
-{
-    int c = 0;
-    for (int d = 1; d <= 7; ++d) c += degree_chunks(H, d);
-    return c;
-}
+// chunks per degree in the sampler's copy (1 up to H = 112, 2 up to 224, 3 up to 256)
+__host__ __device__ inline int sampler_cpd(int H) { return degree_chunks(H, 1); }
+__host__ __device__ inline int sampler_chunks(int H) { return 7 * sampler_cpd(H); }
 // hidden unit at position u (0..15) of sampler chunk s, or -1 for padding
 __host__ __device__ inline int sampler_unit(int H, int s, int u)
 {
-    for (int d = 1; d <= 7; ++d) {
-        const int c = degree_chunks(H, d);
-        if (s < c) {
-            const int i = 16 * s + u;
-            return i < degree_units(H, d) ? d - 1 + 7 * i : -1;
-        }
-        s -= c;
-    }
-    return -1;
+    const int cpd = sampler_cpd(H), d = s / cpd + 1, i = 16 * (s % cpd) + u;
+    return i < degree_units(H, d) ? d - 1 + 7 * i : -1;
 }
 
 __host__ __device__ inline Layout layout(int H)
@@ -469,30 +460,57 @@ __global__ void __launch_bounds__(kFwdThreads, kFwdMinBlocks) logq_kernel(const 
     }
 }
 
-// ---------------------------------------------------------------------------
-// sampling: base draws -> sequential inverse -> theta, log q(theta)
-// ---------------------------------------------------------------------------
-// One pass of the sequential inverse: the chunks of the hidden units of one
-// degree, from chunk s0 on. Their inputs (columns below the degree) are all
-// final, so each unit's activation is computed once, and its layer-2
-// contribution to every output is added to the running accumulators (even
-// chunks into o, odd into p). Returns the next degree's first chunk.
-__device__ __forceinline__ int inverse_pass(const BlockView& v, int H, int d, int s0, int g, int t,
-                                            const float (&xin)[4], float (&o0)[4], float (&o1)[4],
-                                            float (&p0)[4], float (&p1)[4])
+// One pass of the sequential inverse: the CPD chunks of degree-D hidden units
+// (chunks (D-1) CPD .. D CPD - 1 of the sampler's copy). Their inputs (columns
+// below D) are all final, so each unit's activation is computed once, and its
+// layer-2 contribution to every output is added to the running accumulators
+// (even chunks into o, odd into p). D and CPD are compile-time, so every
+// operand load is a fixed offset from the lane's base in the block's copy.
+template <int D, int CPD>
+__device__ __forceinline__ void inverse_pass(const BlockView& v, int g, int t, const float (&xin)[4], float (&o0)[4],
+                                             float (&o1)[4], float (&p0)[4], float (&p1)[4])
 {
     const uint32_t a0 = pack2(xin[0], xin[1]), a1 = pack2(xin[2], xin[3]);
-    const int s1 = s0 + degree_chunks(H, d);
-    int s = s0;
-    for (; s + 1 < s1; s += 2) {
-        made_chunk(v, s, g, t, a0, a1, o0, o1);
-        made_chunk(v, s + 1, g, t, a0, a1, p0, p1);
+#pragma unroll
+    for (int c = 0; c < CPD; ++c) {
+        const int s = (D - 1) * CPD + c;
+        if (s & 1)
+            made_chunk(v, s, g, t, a0, a1, p0, p1);
+        else
+            made_chunk(v, s, g, t, a0, a1, o0, o1);
     }
-    if (s < s1) made_chunk(v, s, g, t, a0, a1, o0, o1);
-    return s1;
 }
 
-template <int K>
+// Column D of the block's inverse, once pass D has added every unit of degree
+// <= D: lane t = D / 2 holds it, element D % 2 for row g and 2 + D % 2 for row g + 8.
+template <int D>
+__device__ __forceinline__ void inverse_column(int t, const float (&z)[4], float (&xin)[4], float (&lq)[4],
+                                               const float (&o0)[4], const float (&o1)[4], const float (&p0)[4],
+                                               const float (&p1)[4])
+{
+    constexpr int e = D & 1;
+    if (t == D / 2) {
+        const float al0 = soft_alpha(o1[e] + p1[e]), al1 = soft_alpha(o1[2 + e] + p1[2 + e]);
+        xin[e] = z[e] * __expf(al0) + (o0[e] + p0[e]);
+        xin[2 + e] = z[2 + e] * __expf(al1) + (o0[2 + e] + p0[2 + e]);
+        lq[e] -= al0;
+        lq[2 + e] -= al1;
+    }
+}
+
+template <int D, int CPD>
+__device__ __forceinline__ void inverse_passes(const BlockView& v, int g, int t, const float (&z)[4], float (&xin)[4],
+                                               float (&lq)[4], float (&o0)[4], float (&o1)[4], float (&p0)[4],
+                                               float (&p1)[4])
+{
+    if constexpr (D <= 7) {
+        inverse_pass<D, CPD>(v, g, t, xin, o0, o1, p0, p1);
+        inverse_column<D>(t, z, xin, lq, o0, o1, p0, p1);
+        inverse_passes<D + 1, CPD>(v, g, t, z, xin, lq, o0, o1, p0, p1);
+    }
+}
+
+template <int K, int CPD>
 // box: read in place from the parameter space (indexing a by-value copy by
 // the lane's column put it in local memory)
 __global__ void __launch_bounds__(kFwdThreads, kSampMinBlocks) sample_kernel(const uint32_t* __restrict__ pub, int H,
@@ -533,12 +551,11 @@ __global__ void __launch_bounds__(kFwdThreads, kSampMinBlocks) sample_kernel(con
             lq[e] = log_base(x[e]) - log_tau;
             x[e] *= tau;
         }
-        // blocks and passes are runtime loops (a fully unrolled 3 x 8 inverse
-        // overflows the instruction cache); passes go in pairs so every
-        // register index stays static: pass 2p+1 fills column 2p+1 (lane t = p,
-        // element 1), pass 2p+2 fills column 2p+2 (lane t = p+1, element 0).
-        // Column j depends on the hidden units of degree <= j alone, which
-        // passes 1..j have added to the accumulators by then.
+        // blocks are a runtime loop (a fully unrolled 3 x 7 inverse overflows
+        // the instruction cache); a block's seven passes are unrolled, so
+        // every operand offset and register index is static. Column j
+        // depends on the hidden units of degree <= j alone, which passes
+        // 1..j have added to the accumulators by then.
 #pragma unroll 1
         for (int bb = K - 1; bb >= 0; --bb) {
             const uint32_t* base = sm + bb * L.samp_words;
@@ -563,28 +580,7 @@ __global__ void __launch_bounds__(kFwdThreads, kSampMinBlocks) sample_kernel(con
                 lq[0] -= al0;
                 lq[2] -= al0;
             }
-            int s0 = 0;
-#pragma unroll 1
-            for (int pj = 0; pj < kD / 2; ++pj) {
-                s0 = inverse_pass(v, H, 2 * pj + 1, s0, g, t, xin, o0, o1, p0, p1);
-                if (t == pj) {
-                    const float al0 = soft_alpha(o1[1] + p1[1]), al1 = soft_alpha(o1[3] + p1[3]);
-                    xin[1] = z[1] * __expf(al0) + (o0[1] + p0[1]);
-                    xin[3] = z[3] * __expf(al1) + (o0[3] + p0[3]);
-                    lq[1] -= al0;
-                    lq[3] -= al1;
-                }
-                if (pj < kD / 2 - 1) {
-                    s0 = inverse_pass(v, H, 2 * pj + 2, s0, g, t, xin, o0, o1, p0, p1);
-                    if (t == pj + 1) {
-                        const float al0 = soft_alpha(o1[0] + p1[0]), al1 = soft_alpha(o1[2] + p1[2]);
-                        xin[0] = z[0] * __expf(al0) + (o0[0] + p0[0]);
-                        xin[2] = z[2] * __expf(al1) + (o0[2] + p0[2]);
-                        lq[0] -= al0;
-                        lq[2] -= al1;
-                    }
-                }
-            }
+            inverse_passes<1, CPD>(v, g, t, z, xin, lq, o0, o1, p0, p1);
             x[0] = xin[0]; x[1] = xin[1]; x[2] = xin[2]; x[3] = xin[3];
         }
         float th[4], jac[4];
@@ -1344,18 +1340,30 @@ cudaError_t launch_logq(abc_maf f, int r, uint64_t n, const float* theta, float*
     return cudaGetLastError();
 }
 
+template <int K, int CPD>
+cudaError_t launch_sample_c(abc_maf f, int r, uint64_t n, const float* u, const ModelParams& p, uint32_t ctr3,
+                            uint64_t first, float* theta, float* logq, cudaStream_t s)
+{
+    const size_t smem = samp_smem(f);
+    cudaError_t e = allow_smem(maf::sample_kernel<K, CPD>, smem);
+    if (e != cudaSuccess) return e;
+    const uint64_t tiles = (n + 15) / 16;
+    const int grid = fill_grid(maf::sample_kernel<K, CPD>, maf::kFwdThreads, smem, (tiles + 7) / 8);
+    maf::sample_kernel<K, CPD><<<grid, maf::kFwdThreads, smem, s>>>(flow_pub(f, r), f->H, f->box, u, p, ctr3, first, n, f->tau,
+                                                  logf(f->tau), theta, logq);
+    return cudaGetLastError();
+}
+
 template <int K>
 cudaError_t launch_sample(abc_maf f, int r, uint64_t n, const float* u, const ModelParams& p, uint32_t ctr3,
                           uint64_t first, float* theta, float* logq, cudaStream_t s)
 {
-    const size_t smem = samp_smem(f);
-    cudaError_t e = allow_smem(maf::sample_kernel<K>, smem);
-    if (e != cudaSuccess) return e;
-    const uint64_t tiles = (n + 15) / 16;
-    const int grid = fill_grid(maf::sample_kernel<K>, maf::kFwdThreads, smem, (tiles + 7) / 8);
-    maf::sample_kernel<K><<<grid, maf::kFwdThreads, smem, s>>>(flow_pub(f, r), f->H, f->box, u, p, ctr3, first, n, f->tau,
-                                                  logf(f->tau), theta, logq);
-    return cudaGetLastError();
+    switch (maf::sampler_cpd(f->H)) {
+    case 1: return launch_sample_c<K, 1>(f, r, n, u, p, ctr3, first, theta, logq, s);
+    case 2: return launch_sample_c<K, 2>(f, r, n, u, p, ctr3, first, theta, logq, s);
+    case 3: return launch_sample_c<K, 3>(f, r, n, u, p, ctr3, first, theta, logq, s);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 // floats per CTA partial: K blocks of parameters and the two loss sums, padded to 16 bytes

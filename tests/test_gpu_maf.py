@@ -57,8 +57,10 @@ def test_log_q_matches_oracle(K, H):
     f.close()
 
 
-@pytest.mark.parametrize("K,H", [(3, 256), (2, 32), (4, 256)])
+@pytest.mark.parametrize("K,H", [(3, 256), (2, 32), (4, 256), (3, 144)])
 def test_sample_matches_oracle_inverse(K, H):
+    """The sampler is compiled per number of 16-unit chunks per degree: one
+    (H = 32), two (H = 144) and three (H = 256)."""
     f, params = _flow(K, H, 20 + K, 0.3)
     n = 3001
     u = np.random.default_rng(3).logistic(size=(n, 8)).astype(np.float32)
