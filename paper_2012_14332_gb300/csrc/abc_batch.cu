@@ -86,7 +86,9 @@ __global__ void __launch_bounds__(BLOCK) abc_batch_kernel(const __grid_constant_
 
     bool active = false;
     uint64_t i = 0, acc = 0;
-    uint32_t k = 0;
+    // k: the next day pair of the lane's sample (1 with no sample); a sample's
+    // simulated days, min(2 (k - 1), T), are counted when its lane takes the next
+    uint32_t k = 1;
     Theta t{};
     State x;
     LaneRegion lr{0, 1, 0, 0, 0, 0.0f};
@@ -156,6 +158,12 @@ __global__ void __launch_bounds__(BLOCK) abc_batch_kernel(const __grid_constant_
                     i = ring.idx[slot];
                     const int32_t r = ring.region[slot];
                     const RegionDev& R = reg_s[r];
+                    // the days of the lane's previous sample (k = 1: none)
+                    if (LEAN) {
+                        if (k > 1) atomicAdd(&days_s[lr.r], (unsigned long long)min(2 * k - 2, (uint32_t)reg_s[lr.r].T));
+                    } else {
+                        days += min(2 * k - 2, (uint32_t)lr.T);
+                    }
                     lr.r = r;
                     if (!LEAN) {
                         if (r != days_region) {
@@ -200,16 +208,11 @@ __global__ void __launch_bounds__(BLOCK) abc_batch_kernel(const __grid_constant_
                     model_day<MODE>(x, t, inv_p, z + 5);
                     const int4 o2 = OBS_S ? obs[d1 + 1] : __ldg(obs + d1 + 1);
                     acc = BELOW62 ? add_day_sq_below62(acc, x, o2) : add_day_sq(acc, x, o2);
-                    if (!LEAN) days += 2;
-                } else if (!LEAN) {
-                    days += 1;
                 }
                 const bool over = acc > (LEAN ? R.acc_max : lr.acc_max);
                 const bool last = d1 + 1 >= T;
                 accept = !over && last;
                 active = !(over || last);
-                // LEAN: a sample that ends adds the days it simulated to its region's count
-                if (LEAN && !active) atomicAdd(&days_s[lr.r], (unsigned long long)(d1 < T ? d1 + 1 : T));
                 ++k;
             }
         }
@@ -230,12 +233,15 @@ __global__ void __launch_bounds__(BLOCK) abc_batch_kernel(const __grid_constant_
             }
         }
     }
+    // the days of each lane's last sample
     if (LEAN) {
+        if (k > 1) atomicAdd(&days_s[lr.r], (unsigned long long)min(2 * k - 2, (uint32_t)reg_s[lr.r].T));
         __syncthreads();
         for (int r = threadIdx.x; r < a.n_regions; r += BLOCK)
             if (days_s[r]) atomicAdd(reg_s[r].counters + 1, days_s[r]);
-    } else if (days_region >= 0 && days) {
-        atomicAdd(reg_s[days_region].counters + 1, days);
+    } else {
+        days += min(2 * k - 2, (uint32_t)lr.T);
+        if (days_region >= 0 && days) atomicAdd(reg_s[days_region].counters + 1, days);
     }
 }
 

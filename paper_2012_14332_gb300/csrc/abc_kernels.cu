@@ -80,7 +80,9 @@ __global__ void __launch_bounds__(kBlockThreads) abc_reject_kernel(const __grid_
 
     bool active = false;
     uint64_t i = 0, acc = 0;
-    uint32_t k = 0, days = 0;
+    // k: the next day pair of the lane's sample (1 with no sample); a sample's
+    // simulated days, min(2 (k - 1), T), are counted when its lane takes the next
+    uint32_t k = 1, days = 0;
     Theta t{};
     State x;
     uint32_t head = 0, tail = 0;     // ring entries consumed / produced (warp-uniform)
@@ -124,6 +126,7 @@ __global__ void __launch_bounds__(kBlockThreads) abc_reject_kernel(const __grid_
                     t.a0 = l.x; t.a = l.y; t.n = l.z; t.beta = l.w;
                     t.gamma = h.x; t.delta = h.y; t.beta_eta = h.z;
                     x = state_from(__float_as_int(h.w), p.A0, p.R0, p.D0, p.room0);
+                    days += min(2 * k - 2, (uint32_t)T);
                     acc = 0;
                     k = 1;
                     active = true;
@@ -150,9 +153,6 @@ __global__ void __launch_bounds__(kBlockThreads) abc_reject_kernel(const __grid_
             if (d1 < T) {
                 model_day<MODE>(x, t, p.inv_p, z + 5);
                 acc = BELOW62 ? add_day_sq_below62(acc, x, obs_s[d1 + 1]) : add_day_sq(acc, x, obs_s[d1 + 1]);
-                days += 2;
-            } else {
-                days += 1;
             }
             const bool over = acc > a.acc_max;
             const bool last = d1 + 1 >= T;
@@ -180,7 +180,9 @@ __global__ void __launch_bounds__(kBlockThreads) abc_reject_kernel(const __grid_
             }
         }
     }
-    // simulated model days of this warp (for throughput accounting)
+    // simulated model days of this warp (for throughput accounting), the
+    // lane's last sample included
+    days += min(2 * k - 2, (uint32_t)T);
     unsigned long long d = days;
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) d += __shfl_down_sync(0xFFFFFFFFu, d, off);
