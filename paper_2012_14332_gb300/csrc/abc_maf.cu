@@ -292,6 +292,29 @@ __device__ __forceinline__ void made_fwd(const BlockView& v, int H, const float 
     ar[2] = (o1[2] + p1[2]) + bs.x; ar[3] = (o1[3] + p1[3]) + bs.y;
 }
 
+// The partial MADE outputs (without b2) of hidden chunks [s0, s1) on the
+// warp's 16 rows: the contributions to mu and alpha_raw, even and odd chunks in
+// separate chains added at the end.
+__device__ __forceinline__ void made_part(const BlockView& v, int s0, int s1, const float (&x)[4], float (&pm)[4],
+                                          float (&pa)[4])
+{
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const uint32_t a0 = pack2(x[0], x[1]), a1 = pack2(x[2], x[3]);
+    float o0[4] = {0.f, 0.f, 0.f, 0.f}, o1[4] = {0.f, 0.f, 0.f, 0.f};
+    float p0[4] = {0.f, 0.f, 0.f, 0.f}, p1[4] = {0.f, 0.f, 0.f, 0.f};
+    int s = s0;
+    for (; s + 1 < s1; s += 2) {
+        made_chunk(v, s, g, t, a0, a1, o0, o1);
+        made_chunk(v, s + 1, g, t, a0, a1, p0, p1);
+    }
+    if (s < s1) made_chunk(v, s, g, t, a0, a1, o0, o1);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        pm[e] = o0[e] + p0[e];
+        pa[e] = o1[e] + p1[e];
+    }
+}
+
 // theta -> y = logit((theta - lo) / w) and the log-Jacobian term log(w u (1 - u)).
 // u is held in [2^-24, 1 - 2^-24]: a point on the box's edge (a flow draw whose
 // sigmoid rounded to 0 or 1) is read as lying 2^-24 of the width inside.
@@ -633,6 +656,14 @@ __global__ void __launch_bounds__(kFwdThreads, kSampMinBlocks) sample_kernel(con
 // of rows g and g + 8: one 32-bit word at byte 16 g + 4 t of a core matrix,
 // so a warp's 32 stores meet 32 distinct banks.
 //
+// In the paired form (PAIR, two 128-unit halves) warps 2p and 2p + 1 share a
+// tile: member m recomputes and differentiates only the hidden units of half
+// m, so its job per block is the (block, m) pair, and the two add their
+// partial layer-2 outputs (forward) and partial g_x (backward) through shared
+// memory once per block. A tile's dependent chain is then half as long, and a
+// CTA holds two tiles instead of four, so a small batch spreads over twice
+// as many SMs.
+//
 // Every wait is bounded in time (kTcWaitNs). A wait that runs out sets the
 // flow's error word; the kernel still runs to its end and frees its TMEM.
 //
@@ -640,8 +671,10 @@ __global__ void __launch_bounds__(kFwdThreads, kSampMinBlocks) sample_kernel(con
 // compute warps' jobs in a fixed order (job n of warp 0, 1, ..., W-1, then job
 // n + 1), so the tensor-memory accumulations into each column group happen in
 // the same order in every run; db2 and the loss sums collect per warp and add
-// up in warp order; and each CTA writes its whole partial gradient to its own
-// slot of a buffer that grad_reduce_kernel sums in CTA order (no float atomics
+// up in warp order; in the paired form the two members add their partial
+// sums commutatively, so both hold the same values; and each CTA writes its
+// whole partial gradient to its own slot of a buffer whose slots are added in
+// a fixed tree (grad_reduce_kernel, adam_partials_kernel; no float atomics
 // anywhere).
 
 // compute warps per CTA: 4, or 15 when a step has enough tiles for more than
@@ -747,6 +780,26 @@ __device__ __forceinline__ void tc_ld16(uint32_t taddr, uint32_t (&v)[16])
                  : "memory");
 }
 
+// The two warps of a pair add their partial sums: each stores its N values per
+// lane in its half of the exchange buffer for this parity, waits on the pair's
+// named barrier (64 threads), and adds the other warp's values. Float addition
+// is commutative, so both warps end with the same sums bit for bit. Two
+// parities: a warp rewrites a buffer only after the next exchange's barrier,
+// which the other warp reaches after it read the buffer.
+template <int N>
+__device__ __forceinline__ void pair_add(float* __restrict__ buf, uint32_t& xc, int member, int bar_id, int lane,
+                                         float (&v)[N])
+{
+    float* mine = buf + ((xc & 1u) * 2 + member) * (8 * 32);
+    const float* other = buf + ((xc & 1u) * 2 + (member ^ 1)) * (8 * 32);
+#pragma unroll
+    for (int e = 0; e < N; ++e) mine[32 * e + lane] = v[e];
+    asm volatile("bar.sync %0, 64;" ::"r"(bar_id) : "memory");
+#pragma unroll
+    for (int e = 0; e < N; ++e) v[e] += other[32 * e + lane];
+    ++xc;
+}
+
 // Training data of one flow: points theta [n][8], weights [n] (NULL = 1).
 struct TrainSlot {
     const float* theta;
@@ -758,7 +811,7 @@ struct TrainSlot {
 // rows[f * batch ..] (none if the flow has no points), else all its n points.
 // Dynamic shared memory: W slots of kTcSlot bytes, then the K blocks' published
 // operands.
-template <int K, int W>
+template <int K, int W, bool PAIR>
 __global__ void __launch_bounds__((W + 1) * 32, 1) grad_kernel(const uint32_t* __restrict__ pub, int H,
                                                                const __grid_constant__ Box box,
                                                                const TrainSlot* __restrict__ slots,
@@ -767,11 +820,14 @@ __global__ void __launch_bounds__((W + 1) * 32, 1) grad_kernel(const uint32_t* _
                                                                int* __restrict__ err, int hold)
 {
     static_assert(W >= 4 && W <= 15, "at least one compute warp per TMEM lane quarter; 16 warps in all at most");
+    static_assert(!PAIR || W % 2 == 0, "whole pairs");
+    constexpr int TPC = PAIR ? W / 2 : W;   // tiles a CTA works on at once
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ __align__(8) uint64_t bar_full[W], bar_empty[W], bar_done;
     __shared__ uint32_t tmem_s, init_s;
     __shared__ float ssum_w[W][2];       // per compute warp: weighted loss sum, weight sum
     __shared__ float gb2_w[W][K * 16];   // per compute warp: db2 sums
+    __shared__ float xch[PAIR ? W / 2 : 1][2 * 2 * 8 * 32];   // per pair: parity, member, value, lane
     const Layout L = layout(H);
     const int mb = master_block(H);
     const int f = blockIdx.y;
@@ -817,7 +873,7 @@ __global__ void __launch_bounds__((W + 1) * 32, 1) grad_kernel(const uint32_t* _
     tc_fence_after();
     const uint32_t tmem = tmem_s;
     const uint64_t tiles = (n_rows + 15) / 16;
-    const uint64_t tstride = (uint64_t)gridDim.x * W;
+    const uint64_t tstride = (uint64_t)gridDim.x * TPC;
     if (warp < W) {
         const int g = lane >> 2, t = lane & 3, rg = 16 * g + 4 * t, sw = g & 4;
         unsigned char* sA = smem + warp * kTcSlot;   // h at 0, g_a1 at kTcHalf, the B slot after
@@ -826,7 +882,12 @@ __global__ void __launch_bounds__((W + 1) * 32, 1) grad_kernel(const uint32_t* _
         uint32_t job = 0;
         bool ok = true;
         const int hw = H / 2 + 4, chunks = H / 16;
-        for (uint64_t tile = (uint64_t)blockIdx.x * W + warp; tile < tiles; tile += tstride) {
+        // a pair's member m takes the hidden units of half m (chunks 8m ..)
+        const int pair = PAIR ? warp >> 1 : warp, member = PAIR ? warp & 1 : 0;
+        const int s_lo = PAIR ? 8 * member : 0, s_hi = PAIR ? min(s_lo + 8, chunks) : chunks;
+        float* xbuf = xch[PAIR ? pair : 0];
+        uint32_t xc = 0;   // the pair's exchanges so far
+        for (uint64_t tile = (uint64_t)blockIdx.x * TPC + pair; tile < tiles; tile += tstride) {
             const uint64_t q0 = tile * 16 + g, q1 = q0 + 8;
             const uint64_t i0 = q0 < n_rows ? (rows ? rows[q0] : q0) : 0;
             const uint64_t i1 = q1 < n_rows ? (rows ? rows[q1] : q1) : 0;
@@ -844,7 +905,19 @@ __global__ void __launch_bounds__((W + 1) * 32, 1) grad_kernel(const uint32_t* _
 #pragma unroll
             for (int b = 0; b < K; ++b) {
                 float mu[4], ar[4];
-                made_fwd(view(wsm + b * L.grad_words, L), H, x, mu, ar);
+                if constexpr (PAIR) {
+                    const BlockView v = view(wsm + b * L.grad_words, L);
+                    float pm[4], pa[4];
+                    made_part(v, s_lo, s_hi, x, pm, pa);
+                    float o[8] = {pm[0], pm[1], pm[2], pm[3], pa[0], pa[1], pa[2], pa[3]};
+                    pair_add<8>(xbuf, xc, member, 1 + pair, lane, o);
+                    const float2 bm = *reinterpret_cast<const float2*>(v.b2 + 2 * t);
+                    const float2 bs = *reinterpret_cast<const float2*>(v.b2 + 8 + 2 * t);
+                    mu[0] = o[0] + bm.x; mu[1] = o[1] + bm.y; mu[2] = o[2] + bm.x; mu[3] = o[3] + bm.y;
+                    ar[0] = o[4] + bs.x; ar[1] = o[5] + bs.y; ar[2] = o[6] + bs.x; ar[3] = o[7] + bs.y;
+                } else {
+                    made_fwd(view(wsm + b * L.grad_words, L), H, x, mu, ar);
+                }
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
                     xs[b][e] = x[e];
@@ -866,7 +939,7 @@ __global__ void __launch_bounds__((W + 1) * 32, 1) grad_kernel(const uint32_t* _
                 contrib += __shfl_xor_sync(kFull, contrib, off);
                 wsum += __shfl_xor_sync(kFull, wsum, off);
             }
-            if (lane == 0) {
+            if (lane == 0 && member == 0) {
                 ssum_w[warp][0] += contrib;
                 ssum_w[warp][1] += wsum;
             }
@@ -902,7 +975,7 @@ __global__ void __launch_bounds__((W + 1) * 32, 1) grad_kernel(const uint32_t* _
                         d[e] += __shfl_xor_sync(kFull, d[e], 8);
                         d[e] += __shfl_xor_sync(kFull, d[e], 16);
                     }
-                    if (g == 0) {
+                    if (g == 0 && member == 0) {
                         gb2_w[warp][16 * b + 2 * t] += d[0];
                         gb2_w[warp][16 * b + 2 * t + 1] += d[1];
                         gb2_w[warp][16 * b + 8 + 2 * t] += d[2];
@@ -940,7 +1013,7 @@ __global__ void __launch_bounds__((W + 1) * 32, 1) grad_kernel(const uint32_t* _
                     // after one wait has run out the warp skips the rest, so a
                     // failed call returns within about one wait limit
                     if (q == 0 && job > 0 && ok) ok = mbar_wait(empty, (job - 1) & 1u);
-                    if (s == 0) {
+                    if (s == s_lo) {
                         // the previous job was the previous block's last: the B slot is free
                         st_u32(sB + rg, A0);
                         st_u32(sB + 128 + rg, A1);
@@ -966,14 +1039,17 @@ __global__ void __launch_bounds__((W + 1) * 32, 1) grad_kernel(const uint32_t* _
                     }
                 };
                 float ax0[4] = {0.f, 0.f, 0.f, 0.f}, ax1[4] = {0.f, 0.f, 0.f, 0.f};
-                int s = 0;
-                for (; s + 1 < chunks; s += 2) {
+                int s = s_lo;
+                for (; s + 1 < s_hi; s += 2) {
                     chunk(s, ax0);
                     chunk(s + 1, ax1);
                 }
-                if (s < chunks) chunk(s, ax0);
+                if (s < s_hi) chunk(s, ax0);
 #pragma unroll
-                for (int e = 0; e < 4; ++e) gx[e] = gxd[e] + (ax0[e] + ax1[e]);
+                for (int e = 0; e < 4; ++e) ax0[e] += ax1[e];
+                if constexpr (PAIR) pair_add<4>(xbuf, xc, member, 1 + pair, lane, ax0);
+#pragma unroll
+                for (int e = 0; e < 4; ++e) gx[e] = gxd[e] + ax0[e];
             }
         }
         if (!ok && lane == 0) atomicExch(err, 1);
@@ -982,13 +1058,15 @@ __global__ void __launch_bounds__((W + 1) * 32, 1) grad_kernel(const uint32_t* _
         init_s = 0;
     } else if (lane == 0) {
         // the issuing thread: job n of every warp in warp order, then job n + 1
-        // (a warp's jobs: tile, block K-1..0, half), so each column group
-        // accumulates in the same order in every run
+        // (a warp's jobs: tile, block K-1..0, half; a pair member's: tile,
+        // block K-1..0, with its own half), so each column group accumulates
+        // in the same order in every run
+        const uint32_t per_tile = PAIR ? (uint32_t)K : (uint32_t)D;
         uint32_t total[W], most = 0;
 #pragma unroll
         for (int w = 0; w < W; ++w) {
-            const uint64_t t0 = (uint64_t)blockIdx.x * W + w;
-            total[w] = t0 < tiles ? (uint32_t)((tiles - 1 - t0) / tstride + 1) * (uint32_t)D : 0u;
+            const uint64_t t0 = (uint64_t)blockIdx.x * TPC + (PAIR ? w >> 1 : w);
+            total[w] = t0 < tiles ? (uint32_t)((tiles - 1 - t0) / tstride + 1) * per_tile : 0u;
             most = total[w] > most ? total[w] : most;
         }
         uint32_t init = 0;   // accumulator pairs written at least once
@@ -1003,8 +1081,8 @@ __global__ void __launch_bounds__((W + 1) * 32, 1) grad_kernel(const uint32_t* _
                     continue;
                 }
                 tc_fence_after();
-                const uint32_t bi = n / (uint32_t)C;   // block index in the warp's sequence
-                const int c = (int)(n - bi * (uint32_t)C), b = K - 1 - (int)(bi % K);
+                const uint32_t bi = PAIR ? n : n / (uint32_t)C;   // block index in the warp's sequence
+                const int c = PAIR ? (w & 1) : (int)(n - bi * (uint32_t)C), b = K - 1 - (int)(bi % K);
                 const int d = b * C + c;
                 const uint32_t sa = smem_addr(smem + w * kTcSlot);
                 const uint32_t sb = sa + 2 * kTcHalf;
@@ -1071,43 +1149,76 @@ __global__ void __launch_bounds__((W + 1) * 32, 1) grad_kernel(const uint32_t* _
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
 }
 
-// q[0] + q[stride] + ... + q[(nblk - 1) stride], added in that order; the
-// loads go out eight at a time so their latencies overlap
-__device__ __forceinline__ float sum_in_order(const float* __restrict__ q, int nblk, uint32_t stride)
+// The CTAs' partials are added in a fixed tree. A 256-thread block covers
+// E = 256 / G consecutive entries in G groups: thread (q, e) adds the partials
+// of CTAs q, q + G, q + 2G, ... of entry e in that order, with a chunk's loads
+// all in flight at once, and the G group sums are then added in group order.
+// G is the smallest of 1, 2, 4, 8 that leaves at most kRedUnroll partials per
+// thread (red_groups), so a few CTAs cost one pass of loads and many CTAs
+// still take about one round trip. A warp covers 32 consecutive entries: every
+// load is a coalesced 128-byte row.
+constexpr int kRedUnroll = 20;
+
+template <int G>
+__device__ __forceinline__ float group_sum(const float* __restrict__ q, int nblk, uint32_t stride, int grp)
 {
     float a = 0.f;
-    int c = 0;
-    for (; c + 8 <= nblk; c += 8) {
-        float x[8];
+    for (int c0 = grp; c0 < nblk; c0 += G * kRedUnroll) {
+        float x[kRedUnroll];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) x[k] = q[(size_t)(c + k) * stride];
+        for (int k = 0; k < kRedUnroll; ++k) {
+            const int c = c0 + G * k;
+            x[k] = c < nblk ? q[(size_t)c * stride] : 0.f;
+        }
 #pragma unroll
-        for (int k = 0; k < 8; ++k) a += x[k];
+        for (int k = 0; k < kRedUnroll; ++k) a += x[k];
     }
-    for (; c < nblk; ++c) a += q[(size_t)c * stride];
     return a;
 }
 
-// The flows' gradients and loss sums from the CTAs' partials, added in CTA
-// order: grad[f][p] = sum over c < nblk of part[f][c][p] (p < np), the two
-// loss sums after them. A flow without rows gets zeros (its CTAs returned
-// before writing).
-__global__ void grad_reduce_kernel(const float* __restrict__ part, int nblk, uint32_t part_stride, int np,
-                                   const TrainSlot* __restrict__ slots, const uint32_t* __restrict__ rows_all,
-                                   uint32_t batch, float* __restrict__ grad, float* __restrict__ sums)
+// entry e's total over the block's G groups (group 0's sum first), valid in
+// group 0's threads; every thread of the block calls it
+template <int G>
+__device__ __forceinline__ float block_groups_total(float (*gs)[256 / G], float mine, int q, int e)
 {
-    const int f = blockIdx.y;
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= np + 2) return;
+    if constexpr (G == 1) {
+        return mine;
+    } else {
+        gs[q][e] = mine;
+        __syncthreads();
+        float a = 0.f;
+        if (q == 0)
+#pragma unroll
+            for (int k = 0; k < G; ++k) a += gs[k][e];
+        return a;
+    }
+}
+
+// The flows' gradients and loss sums from the CTAs' partials, in the fixed
+// tree above: grad[f][p] (p < np), then the two loss sums. A flow without
+// rows gets zeros (its CTAs returned before writing).
+template <int G>
+__global__ void __launch_bounds__(256) grad_reduce_kernel(const float* __restrict__ part, int nblk,
+                                                          uint32_t part_stride, int np,
+                                                          const TrainSlot* __restrict__ slots,
+                                                          const uint32_t* __restrict__ rows_all, uint32_t batch,
+                                                          float* __restrict__ grad, float* __restrict__ sums)
+{
+    constexpr int E = 256 / G;
+    __shared__ float gs[G][E];
+    const int f = blockIdx.y, e = threadIdx.x % E, q = threadIdx.x / E;
+    const int p = blockIdx.x * E + e;
     const uint64_t n_rows = rows_all ? (slots[f].n ? batch : 0) : slots[f].n;
-    const float a = n_rows ? sum_in_order(part + (size_t)f * nblk * part_stride + p, nblk, part_stride) : 0.f;
+    const float mine =
+        n_rows && p < np + 2 ? group_sum<G>(part + (size_t)f * nblk * part_stride + p, nblk, part_stride, q) : 0.f;
+    const float a = block_groups_total<G>(gs, mine, q, e);
+    if (q != 0 || p >= np + 2) return;
     if (p < np)
         grad[(size_t)f * np + p] = a;
     else
         sums[2 * f + (p - np)] = a;
 }
 
-// batch rows for one training step: uniform indices with replacement
 __global__ void batch_rows_kernel(const __grid_constant__ ModelParams p, const int* __restrict__ step,
                                   const TrainSlot* __restrict__ slots, uint32_t batch, uint32_t* __restrict__ rows)
 {
@@ -1137,23 +1248,40 @@ __device__ __forceinline__ void adam_update(float& param, float& m, float& v, fl
 
 __global__ void tick_kernel(int* step) { *step += 1; }
 
-// adam_kernel on the gradient kernel's per-CTA partials, added here in CTA
-// order (the training step's reduction), at step *step + 1 (the publish
-// launch after it advances the counter). A flow without rows this step keeps
+// adam_kernel on the gradient kernel's per-CTA partials, added here in the
+// fixed tree of group_sum (the training step's reduction), at step *step + 1
+// (the publish launch after it advances the counter). A block updates
+// 256 / G parameters of flow blockIdx.y. A flow without rows this step keeps
 // its parameters and moments.
-__global__ void adam_partials_kernel(float* __restrict__ params, const float* __restrict__ part, int nblk,
-                                     uint32_t part_stride, const TrainSlot* __restrict__ slots, float* __restrict__ m,
-                                     float* __restrict__ v, const int* __restrict__ step, int64_t n_params, int64_t n,
-                                     float lr, float b1, float b2, float eps)
+template <int G>
+__global__ void __launch_bounds__(256) adam_partials_kernel(float* __restrict__ params, const float* __restrict__ part,
+                                                            int nblk, uint32_t part_stride,
+                                                            const TrainSlot* __restrict__ slots, float* __restrict__ m,
+                                                            float* __restrict__ v, const int* __restrict__ step,
+                                                            int64_t n_params, float lr, float b1, float b2, float eps)
 {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int64_t f = i / n_params, p = i - f * n_params;
-    if (slots[f].n == 0) return;
-    const float* q = part + (size_t)f * nblk * part_stride;
-    const float W = sum_in_order(q + n_params + 1, nblk, part_stride);
-    if (!(W > 0.f)) return;
-    const float g = sum_in_order(q + p, nblk, part_stride);
+    constexpr int E = 256 / G;
+    __shared__ float gs[G][E];
+    __shared__ float w_s;
+    const int f = blockIdx.y, e = threadIdx.x % E, q = threadIdx.x / E;
+    const int64_t p = (int64_t)blockIdx.x * E + e;
+    if (slots[f].n == 0) return;   // uniform over the block
+    const float* base = part + (size_t)f * nblk * part_stride;
+    if (threadIdx.x < 32) {
+        // the weight sum: lane j adds CTAs j, j + 32, ...; the lanes' sums
+        // meet in lane 0 along a fixed butterfly
+        float w = 0.f;
+        for (int c = threadIdx.x; c < nblk; c += 32) w += base[(size_t)c * part_stride + n_params + 1];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) w += __shfl_xor_sync(kFull, w, off);
+        if (threadIdx.x == 0) w_s = w;
+    }
+    const float mine = p < n_params ? group_sum<G>(base + p, nblk, part_stride, q) : 0.f;
+    const float g = block_groups_total<G>(gs, mine, q, e);
+    __syncthreads();
+    const float W = w_s;
+    if (q != 0 || p >= n_params || !(W > 0.f)) return;
+    const int64_t i = (int64_t)f * n_params + p;
     float pi = params[i], mi = m[i], vi = v[i];
     adam_update(pi, mi, vi, __fdiv_rn(g, W), *step + 1, lr, b1, b2, eps);
     params[i] = pi;
@@ -1369,28 +1497,44 @@ cudaError_t launch_sample(abc_maf f, int r, uint64_t n, const float* u, const Mo
 // floats per CTA partial: K blocks of parameters and the two loss sums, padded to 16 bytes
 uint32_t part_stride(const abc_maf_s* f) { return (uint32_t)((f->K * maf::master_block(f->H) + 2 + 3) & ~3); }
 
-// compute warps per CTA and CTAs per flow for a gradient over `tiles` 16-row tiles:
-// the wide form when 4-warp CTAs would run more than two waves and it fits
-int grad_form(abc_maf f, uint64_t tiles, int* grid_out)
+// The CTA form of a gradient over `tiles` 16-row tiles per flow: compute
+// warps per CTA, whether they work in pairs (one tile per pair, each member
+// one 128-unit half: half the dependent chain per tile, twice the CTAs), and
+// CTAs per flow. The 15-warp form when 4-warp CTAs would run more than two
+// waves and it fits; the 4-warp form pairs its warps when the hidden layer has
+// two halves.
+struct GradForm {
+    int W;
+    bool pair;
+    int grid;
+};
+
+int grad_grid(uint64_t tiles, int tiles_per_cta)
+{
+    const uint64_t want = (tiles + tiles_per_cta - 1) / tiles_per_cta;
+    return (int)(want < (uint64_t)sm_count() ? (want > 0 ? want : 1) : (uint64_t)sm_count());
+}
+
+GradForm grad_form(abc_maf f, uint64_t tiles)
 {
     const uint64_t narrow_ctas = (tiles + maf::kGradWarpsNarrow - 1) / maf::kGradWarpsNarrow * (uint64_t)f->R;
     // the wide form's dynamic shared memory, with 5 KB left for its static part
-    const int W = (narrow_ctas > 2 * (uint64_t)sm_count() && grad_smem(f, maf::kGradWarpsWide) + 5120 <= max_smem_optin())
-                      ? maf::kGradWarpsWide
-                      : maf::kGradWarpsNarrow;
-    const uint64_t want = (tiles + W - 1) / W;
-    *grid_out = (int)(want < (uint64_t)sm_count() ? (want > 0 ? want : 1) : (uint64_t)sm_count());
-    return W;
+    GradForm g;
+    g.W = (narrow_ctas > 2 * (uint64_t)sm_count() && grad_smem(f, maf::kGradWarpsWide) + 5120 <= max_smem_optin())
+              ? maf::kGradWarpsWide
+              : maf::kGradWarpsNarrow;
+    g.pair = g.W == maf::kGradWarpsNarrow && (f->H + maf::kTcM - 1) / maf::kTcM == 2;
+    g.grid = grad_grid(tiles, g.pair ? g.W / 2 : g.W);
+    return g;
 }
 
 // the partial buffer for any gradient over at most `tiles` tiles per flow:
-// sized for the 4-warp form's CTAs, which are never fewer than the 15-warp
-// form's and grow with the tiles; allocates, so it is called before a training
-// step is captured
+// sized for the paired 4-warp form's CTAs (two tiles each), never fewer than
+// the other forms' and growing with the tiles; allocates, so it is called
+// before a training step is captured
 cudaError_t ensure_part(abc_maf f, uint64_t tiles)
 {
-    const uint64_t want = (tiles + maf::kGradWarpsNarrow - 1) / maf::kGradWarpsNarrow;
-    const uint64_t grid = want < (uint64_t)sm_count() ? (want > 0 ? want : 1) : (uint64_t)sm_count();
+    const uint64_t grid = (uint64_t)grad_grid(tiles, maf::kGradWarpsNarrow / 2);
     const size_t need = (size_t)f->R * grid * part_stride(f);
     if (need <= f->part_floats) return cudaSuccess;
     // a captured training step holds the old buffer's address
@@ -1406,24 +1550,53 @@ cudaError_t ensure_part(abc_maf f, uint64_t tiles)
     return e;
 }
 
+// groups per entry of the partial reductions over nblk CTAs: the smallest of
+// 1, 2, 4, 8 leaving at most kRedUnroll partials per thread
+int red_groups(int nblk)
+{
+    int g = 1;
+    while (g < 8 && nblk > g * maf::kRedUnroll) g *= 2;
+    return g;
+}
+
+template <int G>
+void launch_reduce(abc_maf f, const uint32_t* rows, uint32_t batch, int nblk, uint32_t stride, cudaStream_t s)
+{
+    const int np = (int)f->n_params;
+    maf::grad_reduce_kernel<G><<<dim3((np + 2 + 256 / G - 1) / (256 / G), f->R), 256, 0, s>>>(
+        f->d_part, nblk, stride, np, f->d_slots, rows, batch, f->d_grad, f->d_sums);
+}
+
+template <int G>
+void launch_adam_partials(abc_maf f, int nblk, float lr, cudaStream_t s)
+{
+    maf::adam_partials_kernel<G><<<dim3((unsigned)((f->n_params + 256 / G - 1) / (256 / G)), f->R), 256, 0, s>>>(
+        f->d_params, f->d_part, nblk, part_stride(f), f->d_slots, f->d_m, f->d_v, f->d_step, f->n_params, lr, 0.9f,
+        0.999f, 1e-8f);
+}
+
 // gradients of every flow's slot: with rows, `batch` rows per flow; else all
 // max_n points (the largest slot). The kernel writes per-CTA partials, the
-// reduction adds them in CTA order into d_grad and d_sums.
-template <int K, int W>
+// reduction adds them in a fixed tree into d_grad and d_sums.
+template <int K, int W, bool PAIR>
 cudaError_t launch_grad_w(abc_maf f, const uint32_t* rows, uint32_t batch, int grid, bool reduce, cudaStream_t s)
 {
     const size_t smem = grad_smem(f, W);
-    cudaError_t e = allow_smem(maf::grad_kernel<K, W>, smem);
+    cudaError_t e = allow_smem(maf::grad_kernel<K, W, PAIR>, smem);
     if (e != cudaSuccess) return e;
     const uint32_t stride = part_stride(f);
     if ((size_t)f->R * grid * stride > f->part_floats) return cudaErrorInvalidValue;   // ensure_part first
-    maf::grad_kernel<K, W><<<dim3(grid, f->R), (W + 1) * 32, smem, s>>>(f->d_pub, f->H, f->box, f->d_slots, rows,
-                                                                       batch, f->d_part, stride, f->d_err, f->hold);
+    if (PAIR && (f->H + maf::kTcM - 1) / maf::kTcM != 2) return cudaErrorInvalidValue;
+    maf::grad_kernel<K, W, PAIR><<<dim3(grid, f->R), (W + 1) * 32, smem, s>>>(
+        f->d_pub, f->H, f->box, f->d_slots, rows, batch, f->d_part, stride, f->d_err, f->hold);
     e = cudaGetLastError();
     if (e != cudaSuccess || !reduce) return e;
-    const int np = (int)f->n_params;
-    maf::grad_reduce_kernel<<<dim3((np + 2 + 255) / 256, f->R), 256, 0, s>>>(f->d_part, grid, stride, np, f->d_slots,
-                                                                          rows, batch, f->d_grad, f->d_sums);
+    switch (red_groups(grid)) {
+    case 1: launch_reduce<1>(f, rows, batch, grid, stride, s); break;
+    case 2: launch_reduce<2>(f, rows, batch, grid, stride, s); break;
+    case 4: launch_reduce<4>(f, rows, batch, grid, stride, s); break;
+    default: launch_reduce<8>(f, rows, batch, grid, stride, s); break;
+    }
     return cudaGetLastError();
 }
 
@@ -1433,10 +1606,10 @@ template <int K>
 cudaError_t launch_grad(abc_maf f, const uint32_t* rows, uint32_t batch, uint64_t max_n, bool reduce, cudaStream_t s)
 {
     const uint64_t tiles = ((rows ? batch : max_n) + 15) / 16;
-    int grid = 0;
-    if (grad_form(f, tiles, &grid) == maf::kGradWarpsWide)
-        return launch_grad_w<K, maf::kGradWarpsWide>(f, rows, batch, grid, reduce, s);
-    return launch_grad_w<K, maf::kGradWarpsNarrow>(f, rows, batch, grid, reduce, s);
+    const GradForm g = grad_form(f, tiles);
+    if (g.W == maf::kGradWarpsWide) return launch_grad_w<K, maf::kGradWarpsWide, false>(f, rows, batch, g.grid, reduce, s);
+    if (g.pair) return launch_grad_w<K, maf::kGradWarpsNarrow, true>(f, rows, batch, g.grid, reduce, s);
+    return launch_grad_w<K, maf::kGradWarpsNarrow, false>(f, rows, batch, g.grid, reduce, s);
 }
 
 #define MAF_DISPATCH(fn, ...)                      \
@@ -1477,19 +1650,20 @@ cudaError_t launch_adam(abc_maf f, float lr, float b1, float b2, float eps, cuda
 }
 
 // one training step on `batch` drawn rows per flow: batch rows, per-CTA
-// gradient partials, Adam adding the partials in CTA order, publish with the
-// tick (captured once and replayed)
+// gradient partials, Adam adding the partials in a fixed order, publish with
+// the tick (captured once and replayed)
 cudaError_t launch_train_step(abc_maf f, uint32_t batch, const ModelParams& p, float lr, cudaStream_t s)
 {
     maf::batch_rows_kernel<<<dim3((batch + 127) / 128, f->R), 128, 0, s>>>(p, f->d_step, f->d_slots, batch, f->d_rows);
     cudaError_t e = MAF_DISPATCH(launch_grad, f, f->d_rows, batch, 0, false, s);
     if (e != cudaSuccess) return e;
-    int grid = 0;
-    grad_form(f, ((uint64_t)batch + 15) / 16, &grid);
-    const int64_t n = f->n_params * f->R;
-    maf::adam_partials_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(
-        f->d_params, f->d_part, grid, part_stride(f), f->d_slots, f->d_m, f->d_v, f->d_step, f->n_params, n, lr, 0.9f,
-        0.999f, 1e-8f);
+    const int grid = grad_form(f, ((uint64_t)batch + 15) / 16).grid;
+    switch (red_groups(grid)) {
+    case 1: launch_adam_partials<1>(f, grid, lr, s); break;
+    case 2: launch_adam_partials<2>(f, grid, lr, s); break;
+    case 4: launch_adam_partials<4>(f, grid, lr, s); break;
+    default: launch_adam_partials<8>(f, grid, lr, s); break;
+    }
     e = cudaGetLastError();
     if (e == cudaSuccess) e = publish_step(f, s);
     return e;

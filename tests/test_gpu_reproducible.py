@@ -1,7 +1,7 @@
 """Reproducible learned proposals: a seed fixes the trained flows.
 
 The flow gradient takes no float atomics (the tensor-memory accumulations run
-in a fixed job order, each CTA's partial is added in CTA order), and the
+in a fixed job order, the CTAs' partials are added in a fixed tree), and the
 sequential drivers put each run's accepted samples in sample-index order
 before weighting, pooling and training. So a gradient computed twice is the
 same bit for bit, in both CTA forms, and two sequential-ABC runs with one seed
@@ -34,8 +34,9 @@ def _thetas(n, seed):
 
 @pytest.mark.parametrize("n_flows,n", [(1, 5000), (1, 1 << 16), (16, 2055)])
 def test_gradient_is_the_same_on_every_call(n_flows, n):
-    """One flow over 5,000 and 65,536 rows (4-warp CTAs; the second fills
-    every SM) and a set of 16 flows (15-warp CTAs): three calls, one result."""
+    """One flow over 5,000 and 65,536 rows (4-warp CTAs, paired at 256 hidden
+    units; the second fills every SM) and a set of 16 flows (15-warp CTAs):
+    three calls, one result."""
     f = abc.Flow(3, 256, n_flows=n_flows)
     f.init_random(seed=3, scale=0.5)
     th = _thetas(n, 11)
