@@ -58,15 +58,19 @@ struct LaneRegion {
 // accept sets and accepted distances are the same, as in abc_reject_kernel).
 //
 // LEAN: a lane keeps only its region's index and reads the region's constants
-// from the shared table where it uses them, and a sample that ends adds its
-// simulated days to a shared per-region count; this fits 64 registers (four
+// from the shared table where it uses them; this fits 64 registers (four
 // 256-thread blocks per SM instead of three) for a few shared-memory reads per
-// day pair. The autotuner chooses between the two forms: on the 16-region
-// stream the lean form ran 53.1 ms against 56.4 ms, on the three-region
-// workload 2.25 ms against 2.18 ms (128-thread blocks, where it gains no
-// occupancy).
+// day pair. A lane adds its samples' simulated days in a 32-bit register and
+// moves them to the block's 64-bit per-region count when its region changes
+// (chunks are laid out region by region, so rarely) or the register passes
+// 2^31, and at the end. Adding each sample's days to the shared count with a
+// 64-bit shared-memory atomic cost 5 % of the 16-region stream (52.5 -> 49.7
+// ms) and 3 % of the three-region workload. The autotuner chooses between the
+// two forms; with the register count it takes the lean form on both
+// workloads (16-region stream 49.1 ms, three-region workload 2.12 ms, against
+// 56.4 and 2.18 ms for the standard form).
 template <int MODE, int BLOCK, int PAIRS, bool BELOW62, bool OBS_S, bool LEAN>
-__global__ void __launch_bounds__(BLOCK) abc_batch_kernel(const __grid_constant__ ModelParams p,
+__global__ void __launch_bounds__(BLOCK, LEAN ? 4 : 1) abc_batch_kernel(const __grid_constant__ ModelParams p,
                                                           const __grid_constant__ BatchArgs a)
 {
     __shared__ RegionDev reg_s[kMaxRegions];
@@ -94,6 +98,7 @@ __global__ void __launch_bounds__(BLOCK) abc_batch_kernel(const __grid_constant_
     LaneRegion lr{0, 1, 0, 0, 0, 0.0f};
     int32_t days_region = -1;
     unsigned long long days = 0;
+    uint32_t days32 = 0;   // LEAN: days of the lane's samples in region lr.r not yet added
     uint32_t head = 0, tail = 0;
     bool exhausted = false;
     // Chunks are claimed one refill ahead (lane 0 holds the claim), so the
@@ -103,6 +108,9 @@ __global__ void __launch_bounds__(BLOCK) abc_batch_kernel(const __grid_constant_
     // kernel, whose samples run longer between refills, gains nothing).
     unsigned long long claim = 0;
     if (lane == 0) claim = atomicAdd(a.next, 1ull);
+    // region of the warp's last claim: a warp's claims only grow and regions
+    // occupy consecutive chunk ranges, so the region index only moves forward
+    int32_t claim_r = 0;
 
     while (true) {
         const uint32_t idle = __ballot_sync(0xFFFFFFFFu, !active);
@@ -114,9 +122,9 @@ __global__ void __launch_bounds__(BLOCK) abc_batch_kernel(const __grid_constant_
                     exhausted = true;
                 } else {
                     if (lane == 0) claim = atomicAdd(a.next, 1ull);
-                    int32_t r = 0;
-                    for (int32_t q = 1; q < a.n_regions; ++q)
-                        if (reg_s[q].chunk_begin <= c) r = q;
+                    int32_t r = claim_r;
+                    while (r + 1 < a.n_regions && reg_s[r + 1].chunk_begin <= c) ++r;
+                    claim_r = r;
                     const RegionDev& R = reg_s[r];
                     const uint64_t j0 = (c - R.chunk_begin) * 32;
                     const uint64_t left = R.n_samples - j0;
@@ -160,7 +168,11 @@ __global__ void __launch_bounds__(BLOCK) abc_batch_kernel(const __grid_constant_
                     const RegionDev& R = reg_s[r];
                     // the days of the lane's previous sample (k = 1: none)
                     if (LEAN) {
-                        if (k > 1) atomicAdd(&days_s[lr.r], (unsigned long long)min(2 * k - 2, (uint32_t)reg_s[lr.r].T));
+                        days32 += min(2 * k - 2, (uint32_t)reg_s[lr.r].T);
+                        if (r != lr.r || days32 >= 0x80000000u) {
+                            if (days32) atomicAdd(&days_s[lr.r], (unsigned long long)days32);
+                            days32 = 0;
+                        }
                     } else {
                         days += min(2 * k - 2, (uint32_t)lr.T);
                     }
@@ -235,7 +247,8 @@ __global__ void __launch_bounds__(BLOCK) abc_batch_kernel(const __grid_constant_
     }
     // the days of each lane's last sample
     if (LEAN) {
-        if (k > 1) atomicAdd(&days_s[lr.r], (unsigned long long)min(2 * k - 2, (uint32_t)reg_s[lr.r].T));
+        days32 += min(2 * k - 2, (uint32_t)reg_s[lr.r].T);
+        if (days32) atomicAdd(&days_s[lr.r], (unsigned long long)days32);
         __syncthreads();
         for (int r = threadIdx.x; r < a.n_regions; r += BLOCK)
             if (days_s[r]) atomicAdd(reg_s[r].counters + 1, days_s[r]);

@@ -780,6 +780,38 @@ __device__ __forceinline__ void tc_ld16(uint32_t taddr, uint32_t (&v)[16])
                  : "memory");
 }
 
+// mbarrier arrival that also adds `bytes` to the transaction count of the
+// current phase (the bytes bulk copies will complete on it)
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+
+// bulk copy (no tensor map) of `bytes` from global to this CTA's shared
+// memory, completing on the mbarrier; both addresses and the size are
+// multiples of 16 bytes
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
+// The K blocks' words [off, off + n) of the published operands, copied into
+// sm (K x n words, packed) by the bulk-copy engine: thread 0 sets the
+// barrier's transaction count and issues one copy per block. The barrier was
+// initialised (count 1) and that made visible to the CTA before the call.
+// Offsets and sizes are multiples of 4 words (16 bytes), as the bulk copy
+// requires: every section of the layout is, since H is a multiple of 16.
+__device__ __forceinline__ void stage_blocks_bulk(uint32_t* sm, const uint32_t* pub, int K, int off, int n,
+                                                  const Layout& L, uint32_t bar)
+{
+    if (threadIdx.x != 0) return;
+    mbar_arrive_expect_tx(bar, (uint32_t)(K * n) * 4u);
+    for (int b = 0; b < K; ++b) bulk_g2s(smem_addr(sm + b * n), pub + (size_t)b * L.words + off, (uint32_t)n * 4u, bar);
+}
+
 // The two warps of a pair add their partial sums: each stores its N values per
 // lane in its half of the exchange buffer for this parity, waits on the pair's
 // named barrier (64 threads), and adds the other warp's values. Float addition
@@ -823,7 +855,7 @@ __global__ void __launch_bounds__((W + 1) * 32, 1) grad_kernel(const uint32_t* _
     static_assert(!PAIR || W % 2 == 0, "whole pairs");
     constexpr int TPC = PAIR ? W / 2 : W;   // tiles a CTA works on at once
     extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ __align__(8) uint64_t bar_full[W], bar_empty[W], bar_done;
+    __shared__ __align__(8) uint64_t bar_full[W], bar_empty[W], bar_done, bar_stage;
     __shared__ uint32_t tmem_s, init_s;
     __shared__ float ssum_w[W][2];       // per compute warp: weighted loss sum, weight sum
     __shared__ float gb2_w[W][K * 16];   // per compute warp: db2 sums
@@ -841,7 +873,13 @@ __global__ void __launch_bounds__((W + 1) * 32, 1) grad_kernel(const uint32_t* _
     // this CTA's partial: K blocks of mb parameters, then the two loss sums
     float* __restrict__ out_part = part + ((size_t)f * gridDim.x + blockIdx.x) * part_stride;
     uint32_t* wsm = reinterpret_cast<uint32_t*>(smem + W * kTcSlot);
-    stage_blocks(wsm, pub, K, 0, L.grad_words, L);
+    // the published operands arrive by bulk copy while the CTA sets up
+    if (threadIdx.x == 0) {
+        mbar_init(smem_addr(&bar_stage), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    stage_blocks_bulk(wsm, pub, K, 0, L.grad_words, L, smem_addr(&bar_stage));
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int C = (H + kTcM - 1) / kTcM;   // jobs (128-unit halves) per block
     const int D = K * C;                   // (block, half) accumulator pairs, 32 columns each
@@ -871,6 +909,9 @@ __global__ void __launch_bounds__((W + 1) * 32, 1) grad_kernel(const uint32_t* _
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
+    // the operands staged (a wait that runs out sets the error word; the
+    // CTA's result is then not used, but it still runs to its end)
+    if (!mbar_wait(smem_addr(&bar_stage), 0) && lane == 0) atomicExch(err, 1);
     const uint32_t tmem = tmem_s;
     const uint64_t tiles = (n_rows + 15) / 16;
     const uint64_t tstride = (uint64_t)gridDim.x * TPC;
