@@ -353,16 +353,13 @@ __device__ __forceinline__ void stage_blocks(uint32_t* sm, const uint32_t* pub, 
 // ---------------------------------------------------------------------------
 // publish: masked BF16 copies (and biases) from the FP32 master parameters
 // ---------------------------------------------------------------------------
-// Words [0, limit) of each block's published operands (limit = L.words: all;
-// L.grad_words: what the density and gradient kernels read, enough between
-// training steps). step, if not NULL, is advanced by one once the launch's
-// blocks have read nothing from it (the training step's tick).
-__global__ void publish_kernel(const float* __restrict__ master, uint32_t* __restrict__ pub, int K, int H, int limit,
-                               int* __restrict__ step)
+// Every word of each block's published operands, padding included (a
+// training step's Adam launch republishes the parameters it updates, one
+// parameter per thread, and never writes the padding).
+__global__ void publish_kernel(const float* __restrict__ master, uint32_t* __restrict__ pub, int K, int H)
 {
     const Layout L = layout(H);
-    const int per = L.words, mb = master_block(H), hw = H / 2 + 4;
-    if (step && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *step += 1;
+    const int per = L.words, limit = L.words, mb = master_block(H), hw = H / 2 + 4;
     master += (size_t)blockIdx.y * K * mb;   // flow blockIdx.y
     pub += (size_t)blockIdx.y * K * per;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < K * limit; i += gridDim.x * blockDim.x) {
@@ -832,6 +829,14 @@ __device__ __forceinline__ void pair_add(float* __restrict__ buf, uint32_t& xc, 
     ++xc;
 }
 
+// Row b of flow f's training batch at step `step`: a uniform draw, with
+// replacement, from the flow's n points (one Philox block per row).
+__device__ __forceinline__ uint32_t batch_row(const ModelParams& p, uint32_t b, uint32_t step, int f, uint64_t n)
+{
+    const uint4 w = philox10(make_uint4(b, step, 0xB47C4u, 0x5EEDu + ((uint32_t)f << 16)), p);
+    return (uint32_t)((((uint64_t)w.y << 32) | w.x) % n);
+}
+
 // Training data of one flow: points theta [n][8], weights [n] (NULL = 1).
 struct TrainSlot {
     const float* theta;
@@ -839,15 +844,17 @@ struct TrainSlot {
     uint64_t n;
 };
 
-// Flow f = blockIdx.y reads slots[f]: with rows, the batch of rows
-// rows[f * batch ..] (none if the flow has no points), else all its n points.
+// Flow f = blockIdx.y reads slots[f]: with draw_step, `batch` rows drawn for
+// training step *draw_step (batch_row; none if the flow has no points), else
+// all its n points.
 // Dynamic shared memory: W slots of kTcSlot bytes, then the K blocks' published
 // operands.
 template <int K, int W, bool PAIR>
 __global__ void __launch_bounds__((W + 1) * 32, 1) grad_kernel(const uint32_t* __restrict__ pub, int H,
                                                                const __grid_constant__ Box box,
                                                                const TrainSlot* __restrict__ slots,
-                                                               const uint32_t* __restrict__ rows_all, uint32_t batch,
+                                                               const int* __restrict__ draw_step,
+                                                               const __grid_constant__ ModelParams rp, uint32_t batch,
                                                                float* __restrict__ part, uint32_t part_stride,
                                                                int* __restrict__ err, int hold)
 {
@@ -864,11 +871,11 @@ __global__ void __launch_bounds__((W + 1) * 32, 1) grad_kernel(const uint32_t* _
     const int mb = master_block(H);
     const int f = blockIdx.y;
     const TrainSlot slot = slots[f];
-    const uint64_t n_rows = rows_all ? (slot.n ? batch : 0) : slot.n;
+    const uint64_t n_rows = draw_step ? (slot.n ? batch : 0) : slot.n;
     if (n_rows == 0) return;   // uniform over the block
+    const uint32_t step_now = draw_step ? (uint32_t)*draw_step : 0u;
     const float* __restrict__ theta = slot.theta;
     const float* __restrict__ weights = slot.w;
-    const uint32_t* __restrict__ rows = rows_all ? rows_all + (size_t)f * batch : nullptr;
     pub += (size_t)f * K * L.words;
     // this CTA's partial: K blocks of mb parameters, then the two loss sums
     float* __restrict__ out_part = part + ((size_t)f * gridDim.x + blockIdx.x) * part_stride;
@@ -930,8 +937,14 @@ __global__ void __launch_bounds__((W + 1) * 32, 1) grad_kernel(const uint32_t* _
         uint32_t xc = 0;   // the pair's exchanges so far
         for (uint64_t tile = (uint64_t)blockIdx.x * TPC + pair; tile < tiles; tile += tstride) {
             const uint64_t q0 = tile * 16 + g, q1 = q0 + 8;
-            const uint64_t i0 = q0 < n_rows ? (rows ? rows[q0] : q0) : 0;
-            const uint64_t i1 = q1 < n_rows ? (rows ? rows[q1] : q1) : 0;
+            uint64_t i0 = q0 < n_rows ? q0 : 0, i1 = q1 < n_rows ? q1 : 0;
+            if (draw_step) {
+                // lanes t = 0 and 1 of the row group draw rows q0 and q1
+                const uint64_t qm = t ? q1 : q0;
+                const uint32_t mine = t < 2 && qm < n_rows ? batch_row(rp, (uint32_t)qm, step_now, f, slot.n) : 0u;
+                i0 = __shfl_sync(kFull, mine, lane & ~3);
+                i1 = __shfl_sync(kFull, mine, (lane & ~3) | 1);
+            }
             const float w0 = q0 < n_rows ? (weights ? weights[i0] : 1.f) : 0.f;
             const float w1 = q1 < n_rows ? (weights ? weights[i1] : 1.f) : 0.f;
             const float2 ta = *reinterpret_cast<const float2*>(theta + 8 * i0 + 2 * t);
@@ -1237,19 +1250,20 @@ __device__ __forceinline__ float block_groups_total(float (*gs)[256 / G], float 
 
 // The flows' gradients and loss sums from the CTAs' partials, in the fixed
 // tree above: grad[f][p] (p < np), then the two loss sums. A flow without
-// rows gets zeros (its CTAs returned before writing).
+// rows gets zeros (its CTAs returned before writing). drawn: the gradient was
+// over `batch` drawn rows per flow, else over all of each flow's points.
 template <int G>
 __global__ void __launch_bounds__(256) grad_reduce_kernel(const float* __restrict__ part, int nblk,
                                                           uint32_t part_stride, int np,
                                                           const TrainSlot* __restrict__ slots,
-                                                          const uint32_t* __restrict__ rows_all, uint32_t batch,
-                                                          float* __restrict__ grad, float* __restrict__ sums)
+                                                          int drawn, uint32_t batch, float* __restrict__ grad,
+                                                          float* __restrict__ sums)
 {
     constexpr int E = 256 / G;
     __shared__ float gs[G][E];
     const int f = blockIdx.y, e = threadIdx.x % E, q = threadIdx.x / E;
     const int p = blockIdx.x * E + e;
-    const uint64_t n_rows = rows_all ? (slots[f].n ? batch : 0) : slots[f].n;
+    const uint64_t n_rows = drawn ? (slots[f].n ? batch : 0) : slots[f].n;
     const float mine =
         n_rows && p < np + 2 ? group_sum<G>(part + (size_t)f * nblk * part_stride + p, nblk, part_stride, q) : 0.f;
     const float a = block_groups_total<G>(gs, mine, q, e);
@@ -1260,17 +1274,6 @@ __global__ void __launch_bounds__(256) grad_reduce_kernel(const float* __restric
         sums[2 * f + (p - np)] = a;
 }
 
-__global__ void batch_rows_kernel(const __grid_constant__ ModelParams p, const int* __restrict__ step,
-                                  const TrainSlot* __restrict__ slots, uint32_t batch, uint32_t* __restrict__ rows)
-{
-    const uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
-    const uint32_t f = blockIdx.y;
-    const uint64_t n = slots[f].n;
-    if (b >= batch || n == 0) return;
-    const uint4 w = philox10(make_uint4(b, (uint32_t)*step, 0xB47C4u, 0x5EEDu + (f << 16)), p);
-    const uint64_t r = (((uint64_t)w.y << 32) | w.x) % n;
-    rows[(size_t)f * batch + b] = (uint32_t)r;
-}
 
 // One Adam update (Kingma, Ba 2015) of a parameter with gradient gr at step
 // t >= 1; the fused multiply-adds are written out, so both Adam kernels round
@@ -1289,45 +1292,121 @@ __device__ __forceinline__ void adam_update(float& param, float& m, float& v, fl
 
 __global__ void tick_kernel(int* step) { *step += 1; }
 
-// adam_kernel on the gradient kernel's per-CTA partials, added here in the
-// fixed tree of group_sum (the training step's reduction), at step *step + 1
-// (the publish launch after it advances the counter). A block updates
-// 256 / G parameters of flow blockIdx.y. A flow without rows this step keeps
-// its parameters and moments.
+// Master parameter r of one block (W1 [H][8], b1 [H], W2 [16][H], b2 [16]),
+// value val, written to every place the published layout holds it: the
+// forward and backward operands and the sampler's copy, as BF16 halves of
+// their words (masked weights as 0) or whole FP32 words. The words of a layout
+// hold two parameters each; storing each half separately lets one thread per
+// parameter publish without the other. The layout's padding is never written
+// here (a full publish zeroes it).
+__device__ __forceinline__ void publish_param(uint32_t* __restrict__ pb, int H, const Layout& L, int r, float val)
+{
+    unsigned short* h16 = reinterpret_cast<unsigned short*>(pb);
+    const int cpd = sampler_cpd(H);
+    if (r < 8 * H) {
+        const int l = r >> 3, j = r & 7;
+        const unsigned short bf = mask1(l, j) ? __bfloat16_as_ushort(__float2bfloat16_rn(val)) : (unsigned short)0;
+        const int t = j >> 1;
+        // w1: word ((s 8 + g) 4 + t) 2 + h for hidden l = 16 s + g + 8 h
+        h16[2 * (L.w1 + (((l >> 4) * 8 + (l & 7)) * 4 + t) * 2 + ((l >> 3) & 1)) + (j & 1)] = bf;
+        // w1t: word [j][l / 2]
+        h16[2 * (L.w1t + j * (H / 2 + 4) + (l >> 1)) + (l & 1)] = bf;
+        // sampler copy: unit l sits at position u of chunk sc
+        const int i = l / 7, sc = (l % 7) * cpd + (i >> 4), u = i & 15;
+        h16[2 * (L.sw1 + ((sc * 8 + (u & 7)) * 4 + t) * 2 + (u >> 3)) + (j & 1)] = bf;
+    } else if (r < 9 * H) {
+        const int l = r - 8 * H, rem = l & 15;
+        // b1: word (s 4 + t) 4 + q for hidden 16 s + 8 (q / 2) + 2 t + q % 2
+        pb[L.b1 + ((l >> 4) * 4 + ((rem & 7) >> 1)) * 4 + ((rem >> 3) << 1 | (rem & 1))] = __float_as_uint(val);
+        const int i = l / 7, sc = (l % 7) * cpd + (i >> 4), u = i & 15;
+        pb[L.sb1 + (sc * 4 + ((u & 7) >> 1)) * 4 + ((u >> 3) << 1 | (u & 1))] = __float_as_uint(val);
+    } else if (r < 25 * H) {
+        const int o = (r - 9 * H) / H, l = (r - 9 * H) - o * H, rem = l & 15;
+        const unsigned short bf = mask2(o, l) ? __bfloat16_as_ushort(__float2bfloat16_rn(val)) : (unsigned short)0;
+        // w2: word ((s 8 + g) 4 + t) 4 + q for output g + 8 (q / 2) and hidden
+        // 16 s + 8 (q % 2) + 2 t (+1 in the high half)
+        h16[2 * (L.w2 + (((l >> 4) * 8 + (o & 7)) * 4 + ((rem & 7) >> 1)) * 4 + ((o >> 3) << 1 | (rem >> 3))) +
+            (l & 1)] = bf;
+        // w2t: word l 8 + ((o / 2) ^ (l & 4)), output o / 2 * 2 low, +1 high
+        h16[2 * (L.w2t + l * 8 + ((o >> 1) ^ (l & 4))) + (o & 1)] = bf;
+        const int i = l / 7, sc = (l % 7) * cpd + (i >> 4), u = i & 15;
+        h16[2 * (L.sw2 + ((sc * 8 + (o & 7)) * 4 + ((u & 7) >> 1)) * 4 + ((o >> 3) << 1 | (u >> 3))) + (u & 1)] = bf;
+    } else {
+        const int o = r - 25 * H;
+        pb[L.b2 + o] = __float_as_uint(val);
+        pb[L.sb2 + o] = __float_as_uint(val);
+    }
+}
+
+// A training step's Adam and publish in one launch: adam_kernel on the
+// gradient kernel's per-CTA partials, added here in the fixed tree of
+// group_sum, at step *step + 1; each updated parameter is published at once
+// (publish_param). A block updates 256 / G parameters of flow blockIdx.y; a
+// flow without rows this step keeps its parameters, moments and published
+// words. The last block to finish advances *step (done[0] counts finished
+// blocks and is back at 0 afterwards): every block has read the step by then.
 template <int G>
-__global__ void __launch_bounds__(256) adam_partials_kernel(float* __restrict__ params, const float* __restrict__ part,
-                                                            int nblk, uint32_t part_stride,
-                                                            const TrainSlot* __restrict__ slots, float* __restrict__ m,
-                                                            float* __restrict__ v, const int* __restrict__ step,
-                                                            int64_t n_params, float lr, float b1, float b2, float eps)
+__global__ void __launch_bounds__(256) adam_publish_kernel(float* __restrict__ params, const float* __restrict__ part,
+                                                           int nblk, uint32_t part_stride,
+                                                           const TrainSlot* __restrict__ slots, float* __restrict__ m,
+                                                           float* __restrict__ v, int* __restrict__ step,
+                                                           unsigned* __restrict__ done, uint32_t* __restrict__ pub,
+                                                           int K, int H, int64_t n_params, float lr, float b1,
+                                                           float b2, float eps)
 {
     constexpr int E = 256 / G;
     __shared__ float gs[G][E];
     __shared__ float w_s;
     const int f = blockIdx.y, e = threadIdx.x % E, q = threadIdx.x / E;
     const int64_t p = (int64_t)blockIdx.x * E + e;
-    if (slots[f].n == 0) return;   // uniform over the block
+    const int t_step = *step + 1;
+    const bool has_rows = slots[f].n != 0;   // uniform over the block
     const float* base = part + (size_t)f * nblk * part_stride;
     if (threadIdx.x < 32) {
-        // the weight sum: lane j adds CTAs j, j + 32, ...; the lanes' sums
-        // meet in lane 0 along a fixed butterfly
+        // the weight sum: lane j adds CTAs j, j + 32, ... (all loads of a
+        // chunk in flight); the lanes' sums meet in lane 0 along a fixed
+        // butterfly
         float w = 0.f;
-        for (int c = threadIdx.x; c < nblk; c += 32) w += base[(size_t)c * part_stride + n_params + 1];
+        if (has_rows)
+            for (int c0 = threadIdx.x; c0 < nblk; c0 += 32 * 8) {
+                float x[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const int c = c0 + 32 * k;
+                    x[k] = c < nblk ? base[(size_t)c * part_stride + n_params + 1] : 0.f;
+                }
+#pragma unroll
+                for (int k = 0; k < 8; ++k) w += x[k];
+            }
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) w += __shfl_xor_sync(kFull, w, off);
         if (threadIdx.x == 0) w_s = w;
     }
-    const float mine = p < n_params ? group_sum<G>(base + p, nblk, part_stride, q) : 0.f;
+    const float mine = has_rows && p < n_params ? group_sum<G>(base + p, nblk, part_stride, q) : 0.f;
     const float g = block_groups_total<G>(gs, mine, q, e);
     __syncthreads();
     const float W = w_s;
-    if (q != 0 || p >= n_params || !(W > 0.f)) return;
-    const int64_t i = (int64_t)f * n_params + p;
-    float pi = params[i], mi = m[i], vi = v[i];
-    adam_update(pi, mi, vi, __fdiv_rn(g, W), *step + 1, lr, b1, b2, eps);
-    params[i] = pi;
-    m[i] = mi;
-    v[i] = vi;
+    if (has_rows && q == 0 && p < n_params && W > 0.f) {
+        const int64_t i = (int64_t)f * n_params + p;
+        float pi = params[i], mi = m[i], vi = v[i];
+        adam_update(pi, mi, vi, __fdiv_rn(g, W), t_step, lr, b1, b2, eps);
+        params[i] = pi;
+        m[i] = mi;
+        v[i] = vi;
+        const Layout L = layout(H);
+        const int mb = master_block(H), b = (int)(p / mb);
+        publish_param(pub + ((size_t)f * K + b) * L.words, H, L, (int)(p - (int64_t)b * mb), pi);
+    }
+    // the tick: this block has read the step (the barrier), so the last
+    // block's increment comes after every read
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(done, 1u) == gridDim.x * gridDim.y - 1) {
+            *step = t_step;
+            *done = 0u;
+        }
+    }
 }
 
 // n_params per flow; flows one after another. A flow whose weight sum is 0
@@ -1370,9 +1449,7 @@ struct abc_maf_s {
     float* d_sums = nullptr;   // [R][2] (weighted loss sum, weight sum)
     int* d_err = nullptr;      // set by a gradient kernel whose bounded wait ran out
     int hold = 0;              // testing: the gradient kernel issues no products
-    int* d_step = nullptr;
-    uint32_t* d_rows = nullptr;
-    uint32_t rows_cap = 0;     // batch rows per flow
+    int* d_step = nullptr;     // [0] the training step, [1] a training step's finished Adam blocks
     maf::TrainSlot* d_slots = nullptr;   // [R] training data of each flow
     float* d_best = nullptr;   // [R][n_params] best parameters under validation (allocated on first use)
     cudaGraphExec_t graph = nullptr;
@@ -1482,17 +1559,7 @@ const uint32_t* flow_pub(abc_maf f, int r) { return f->d_pub + (size_t)r * f->K 
 cudaError_t publish(abc_maf f, cudaStream_t s)
 {
     const int n = f->K * f->pub_words;
-    maf::publish_kernel<<<dim3((n + 255) / 256, f->R), 256, 0, s>>>(f->d_params, f->d_pub, f->K, f->H, f->pub_words,
-                                                                    nullptr);
-    return cudaGetLastError();
-}
-
-// a training step's publish: the words the gradient kernel reads, and the tick
-cudaError_t publish_step(abc_maf f, cudaStream_t s)
-{
-    const int limit = maf::layout(f->H).grad_words, n = f->K * limit;
-    maf::publish_kernel<<<dim3((n + 255) / 256, f->R), 256, 0, s>>>(f->d_params, f->d_pub, f->K, f->H, limit,
-                                                                    f->d_step);
+    maf::publish_kernel<<<dim3((n + 255) / 256, f->R), 256, 0, s>>>(f->d_params, f->d_pub, f->K, f->H);
     return cudaGetLastError();
 }
 
@@ -1601,26 +1668,29 @@ int red_groups(int nblk)
 }
 
 template <int G>
-void launch_reduce(abc_maf f, const uint32_t* rows, uint32_t batch, int nblk, uint32_t stride, cudaStream_t s)
+void launch_reduce(abc_maf f, bool drawn, uint32_t batch, int nblk, uint32_t stride, cudaStream_t s)
 {
     const int np = (int)f->n_params;
     maf::grad_reduce_kernel<G><<<dim3((np + 2 + 256 / G - 1) / (256 / G), f->R), 256, 0, s>>>(
-        f->d_part, nblk, stride, np, f->d_slots, rows, batch, f->d_grad, f->d_sums);
+        f->d_part, nblk, stride, np, f->d_slots, drawn ? 1 : 0, batch, f->d_grad, f->d_sums);
 }
 
+// d_step[0]: the training step; d_step[1]: the Adam launch's finished blocks
 template <int G>
-void launch_adam_partials(abc_maf f, int nblk, float lr, cudaStream_t s)
+void launch_adam_publish(abc_maf f, int nblk, float lr, cudaStream_t s)
 {
-    maf::adam_partials_kernel<G><<<dim3((unsigned)((f->n_params + 256 / G - 1) / (256 / G)), f->R), 256, 0, s>>>(
-        f->d_params, f->d_part, nblk, part_stride(f), f->d_slots, f->d_m, f->d_v, f->d_step, f->n_params, lr, 0.9f,
-        0.999f, 1e-8f);
+    maf::adam_publish_kernel<G><<<dim3((unsigned)((f->n_params + 256 / G - 1) / (256 / G)), f->R), 256, 0, s>>>(
+        f->d_params, f->d_part, nblk, part_stride(f), f->d_slots, f->d_m, f->d_v, f->d_step,
+        reinterpret_cast<unsigned*>(f->d_step + 1), f->d_pub, f->K, f->H, f->n_params, lr, 0.9f, 0.999f, 1e-8f);
 }
 
-// gradients of every flow's slot: with rows, `batch` rows per flow; else all
-// max_n points (the largest slot). The kernel writes per-CTA partials, the
-// reduction adds them in a fixed tree into d_grad and d_sums.
+// gradients of every flow's slot: with draw_step, `batch` rows per flow drawn
+// for step *draw_step with rp's Philox key; else all max_n points (the
+// largest slot). The kernel writes per-CTA partials, the reduction adds them
+// in a fixed tree into d_grad and d_sums.
 template <int K, int W, bool PAIR>
-cudaError_t launch_grad_w(abc_maf f, const uint32_t* rows, uint32_t batch, int grid, bool reduce, cudaStream_t s)
+cudaError_t launch_grad_w(abc_maf f, const int* draw_step, const ModelParams& rp, uint32_t batch, int grid, bool reduce,
+                          cudaStream_t s)
 {
     const size_t smem = grad_smem(f, W);
     cudaError_t e = allow_smem(maf::grad_kernel<K, W, PAIR>, smem);
@@ -1629,14 +1699,14 @@ cudaError_t launch_grad_w(abc_maf f, const uint32_t* rows, uint32_t batch, int g
     if ((size_t)f->R * grid * stride > f->part_floats) return cudaErrorInvalidValue;   // ensure_part first
     if (PAIR && (f->H + maf::kTcM - 1) / maf::kTcM != 2) return cudaErrorInvalidValue;
     maf::grad_kernel<K, W, PAIR><<<dim3(grid, f->R), (W + 1) * 32, smem, s>>>(
-        f->d_pub, f->H, f->box, f->d_slots, rows, batch, f->d_part, stride, f->d_err, f->hold);
+        f->d_pub, f->H, f->box, f->d_slots, draw_step, rp, batch, f->d_part, stride, f->d_err, f->hold);
     e = cudaGetLastError();
     if (e != cudaSuccess || !reduce) return e;
     switch (red_groups(grid)) {
-    case 1: launch_reduce<1>(f, rows, batch, grid, stride, s); break;
-    case 2: launch_reduce<2>(f, rows, batch, grid, stride, s); break;
-    case 4: launch_reduce<4>(f, rows, batch, grid, stride, s); break;
-    default: launch_reduce<8>(f, rows, batch, grid, stride, s); break;
+    case 1: launch_reduce<1>(f, draw_step != nullptr, batch, grid, stride, s); break;
+    case 2: launch_reduce<2>(f, draw_step != nullptr, batch, grid, stride, s); break;
+    case 4: launch_reduce<4>(f, draw_step != nullptr, batch, grid, stride, s); break;
+    default: launch_reduce<8>(f, draw_step != nullptr, batch, grid, stride, s); break;
     }
     return cudaGetLastError();
 }
@@ -1644,13 +1714,15 @@ cudaError_t launch_grad_w(abc_maf f, const uint32_t* rows, uint32_t batch, int g
 // reduce: add the partials into d_grad and d_sums (a training step's Adam adds
 // them itself instead)
 template <int K>
-cudaError_t launch_grad(abc_maf f, const uint32_t* rows, uint32_t batch, uint64_t max_n, bool reduce, cudaStream_t s)
+cudaError_t launch_grad(abc_maf f, const int* draw_step, const ModelParams& rp, uint32_t batch, uint64_t max_n, bool reduce,
+                        cudaStream_t s)
 {
-    const uint64_t tiles = ((rows ? batch : max_n) + 15) / 16;
+    const uint64_t tiles = ((draw_step ? batch : max_n) + 15) / 16;
     const GradForm g = grad_form(f, tiles);
-    if (g.W == maf::kGradWarpsWide) return launch_grad_w<K, maf::kGradWarpsWide, false>(f, rows, batch, g.grid, reduce, s);
-    if (g.pair) return launch_grad_w<K, maf::kGradWarpsNarrow, true>(f, rows, batch, g.grid, reduce, s);
-    return launch_grad_w<K, maf::kGradWarpsNarrow, false>(f, rows, batch, g.grid, reduce, s);
+    if (g.W == maf::kGradWarpsWide)
+        return launch_grad_w<K, maf::kGradWarpsWide, false>(f, draw_step, rp, batch, g.grid, reduce, s);
+    if (g.pair) return launch_grad_w<K, maf::kGradWarpsNarrow, true>(f, draw_step, rp, batch, g.grid, reduce, s);
+    return launch_grad_w<K, maf::kGradWarpsNarrow, false>(f, draw_step, rp, batch, g.grid, reduce, s);
 }
 
 #define MAF_DISPATCH(fn, ...)                      \
@@ -1678,7 +1750,7 @@ cudaError_t upload_slots(abc_maf f, const float* const* theta, const float* cons
 cudaError_t full_gradient(abc_maf f, uint64_t max_n, cudaStream_t s)
 {
     cudaError_t e = ensure_part(f, (max_n + 15) / 16);
-    if (e == cudaSuccess) e = MAF_DISPATCH(launch_grad, f, nullptr, 0u, max_n, true, s);
+    if (e == cudaSuccess) e = MAF_DISPATCH(launch_grad, f, nullptr, ModelParams{}, 0u, max_n, true, s);
     return e;
 }
 
@@ -1690,24 +1762,22 @@ cudaError_t launch_adam(abc_maf f, float lr, float b1, float b2, float eps, cuda
     return cudaGetLastError();
 }
 
-// one training step on `batch` drawn rows per flow: batch rows, per-CTA
-// gradient partials, Adam adding the partials in a fixed order, publish with
-// the tick (captured once and replayed)
+// one training step on `batch` drawn rows per flow, two launches (captured
+// once and replayed): the gradient kernel draws its rows for the current step
+// and writes per-CTA partials; Adam adds the partials in a fixed order,
+// publishes every updated parameter and advances the step
 cudaError_t launch_train_step(abc_maf f, uint32_t batch, const ModelParams& p, float lr, cudaStream_t s)
 {
-    maf::batch_rows_kernel<<<dim3((batch + 127) / 128, f->R), 128, 0, s>>>(p, f->d_step, f->d_slots, batch, f->d_rows);
-    cudaError_t e = MAF_DISPATCH(launch_grad, f, f->d_rows, batch, 0, false, s);
+    cudaError_t e = MAF_DISPATCH(launch_grad, f, f->d_step, p, batch, 0, false, s);
     if (e != cudaSuccess) return e;
     const int grid = grad_form(f, ((uint64_t)batch + 15) / 16).grid;
     switch (red_groups(grid)) {
-    case 1: launch_adam_partials<1>(f, grid, lr, s); break;
-    case 2: launch_adam_partials<2>(f, grid, lr, s); break;
-    case 4: launch_adam_partials<4>(f, grid, lr, s); break;
-    default: launch_adam_partials<8>(f, grid, lr, s); break;
+    case 1: launch_adam_publish<1>(f, grid, lr, s); break;
+    case 2: launch_adam_publish<2>(f, grid, lr, s); break;
+    case 4: launch_adam_publish<4>(f, grid, lr, s); break;
+    default: launch_adam_publish<8>(f, grid, lr, s); break;
     }
-    e = cudaGetLastError();
-    if (e == cudaSuccess) e = publish_step(f, s);
-    return e;
+    return cudaGetLastError();
 }
 
 }  // namespace
@@ -1753,12 +1823,12 @@ abc_status abc_maf_create_multi(int32_t n_flows, int32_t n_blocks, int32_t hidde
         (e = cudaMalloc(&f->d_grad, np)) != cudaSuccess ||
         (e = cudaMalloc(&f->d_pub, sizeof(uint32_t) * (size_t)f->R * f->K * f->pub_words)) != cudaSuccess ||
         (e = cudaMalloc(&f->d_sums, 2 * sizeof(float) * f->R)) != cudaSuccess ||
-        (e = cudaMalloc(&f->d_step, sizeof(int))) != cudaSuccess ||
+        (e = cudaMalloc(&f->d_step, 2 * sizeof(int))) != cudaSuccess ||
         (e = cudaMalloc(&f->d_slots, sizeof(maf::TrainSlot) * f->R)) != cudaSuccess ||
         (e = cudaMalloc(&f->d_err, sizeof(int))) != cudaSuccess)
         return fail_free(plan_cuda_fail(e, "cudaMalloc(flow)"));
     if ((e = cudaMemset(f->d_params, 0, np)) != cudaSuccess || (e = cudaMemset(f->d_m, 0, np)) != cudaSuccess ||
-        (e = cudaMemset(f->d_v, 0, np)) != cudaSuccess || (e = cudaMemset(f->d_step, 0, sizeof(int))) != cudaSuccess ||
+        (e = cudaMemset(f->d_v, 0, np)) != cudaSuccess || (e = cudaMemset(f->d_step, 0, 2 * sizeof(int))) != cudaSuccess ||
         (e = cudaMemset(f->d_slots, 0, sizeof(maf::TrainSlot) * f->R)) != cudaSuccess ||
         (e = cudaMemset(f->d_err, 0, sizeof(int))) != cudaSuccess ||
         (e = publish(f, nullptr)) != cudaSuccess || (e = cudaDeviceSynchronize()) != cudaSuccess)
@@ -1823,7 +1893,7 @@ abc_status abc_maf_set_params(abc_maf f, const float* params)
     MAF_TRY(cudaMemcpy(f->d_params, params, np, cudaMemcpyHostToDevice), "cudaMemcpy(params)");
     MAF_TRY(cudaMemset(f->d_m, 0, np), "cudaMemset");
     MAF_TRY(cudaMemset(f->d_v, 0, np), "cudaMemset");
-    MAF_TRY(cudaMemset(f->d_step, 0, sizeof(int)), "cudaMemset");
+    MAF_TRY(cudaMemset(f->d_step, 0, 2 * sizeof(int)), "cudaMemset");
     MAF_TRY(publish(f, nullptr), "publish");
     MAF_TRY(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
     return plan_ok();
@@ -1960,17 +2030,6 @@ abc_status abc_maf_train_flows(abc_maf f, const float* const* theta, const float
     }
     cudaStream_t s = (cudaStream_t)cuda_stream;
     if (!s && n_steps > 0) return plan_fail(ABC_ERR_INVALID_ARG, "training needs a non-default stream");
-    if ((uint32_t)batch > f->rows_cap) {
-        cudaFree(f->d_rows);
-        f->d_rows = nullptr;
-        f->rows_cap = 0;
-        MAF_TRY(cudaMalloc(&f->d_rows, sizeof(uint32_t) * (size_t)batch * f->R), "cudaMalloc(rows)");
-        f->rows_cap = (uint32_t)batch;
-        if (f->graph) {
-            cudaGraphExecDestroy(f->graph);
-            f->graph = nullptr;
-        }
-    }
     MAF_TRY(upload_slots(f, th_tr.data(), w_tr.data(), n_tr.data(), s), "cudaMemcpyAsync(slots)");
     // the gradient partials for both the training batches and the validation
     // sets, allocated before the step is captured (a later reallocation would
@@ -1985,7 +2044,7 @@ abc_status abc_maf_train_flows(abc_maf f, const float* const* theta, const float
     const size_t np = sizeof(float) * f->n_params * f->R;
     MAF_TRY(cudaMemsetAsync(f->d_m, 0, np, s), "cudaMemsetAsync");
     MAF_TRY(cudaMemsetAsync(f->d_v, 0, np, s), "cudaMemsetAsync");
-    MAF_TRY(cudaMemsetAsync(f->d_step, 0, sizeof(int), s), "cudaMemsetAsync");
+    MAF_TRY(cudaMemsetAsync(f->d_step, 0, 2 * sizeof(int), s), "cudaMemsetAsync");
     if (n_steps > 0) {
         // the step reads its data through the slot table, so a graph captured
         // for (batch, lr, seed, stream) serves every data set
@@ -2080,9 +2139,9 @@ abc_status abc_maf_train_flows(abc_maf f, const float* const* theta, const float
         return plan_ok();
     }
     if (n_steps > 0) {
+        // each step publishes every parameter it updates, the sampler's
+        // operands included
         for (int32_t i = 0; i < n_steps; ++i) MAF_TRY(cudaGraphLaunch(f->graph, s), "cudaGraphLaunch");
-        // the steps publish what the gradient reads; the sampler's operands now
-        MAF_TRY(publish(f, s), "publish");
     }
     if (loss_out) {
         MAF_TRY(full_gradient(f, max_n, s), "flow loss");
@@ -2136,7 +2195,6 @@ abc_status abc_maf_destroy(abc_maf f)
     cudaFree(f->d_pub);
     cudaFree(f->d_sums);
     cudaFree(f->d_step);
-    cudaFree(f->d_rows);
     cudaFree(f->d_slots);
     cudaFree(f->d_err);
     cudaFree(f->d_best);

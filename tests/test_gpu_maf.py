@@ -310,6 +310,42 @@ def test_flow_set_members_equal_single_flows():
     fs.close()
 
 
+@pytest.mark.parametrize("K,H,R", [(3, 256, 1), (2, 64, 1), (3, 112, 3), (4, 256, 2), (1, 208, 1)])
+def test_training_steps_publish_what_a_full_publish_writes(K, H, R):
+    """A training step's Adam launch republishes each parameter it updates, one
+    thread per parameter, into every layout the kernels read (density,
+    gradient and the sampler's degree-grouped copy), and training without
+    validation ends on that. The densities, draws and gradient after training
+    then equal those after a full republish of the same parameters, bit for
+    bit: a parameter written to a wrong place, or not at all, would change
+    them. Shapes: the paired and unpaired gradient forms, a set of flows, and
+    one, two and three sampler chunks per degree."""
+    fs = abc.Flow(K, H, n_flows=R)
+    fs.init_random(seed=4, scale=0.3)
+    p0 = fs.get_params().copy()
+    data = [torch.from_numpy(_thetas(3000 + 500 * r, 30 + r)).to(DEV) for r in range(R)]
+    fs.train_flows(data, None, n_steps=7, batch=512, lr=5e-3, seed=2)
+    th = torch.from_numpy(_thetas(1500, 40)).to(DEV)
+
+    def outputs():
+        out = []
+        for r in range(R):
+            out.append(fs.log_q(th, flow=r).cpu().numpy())
+            t, lq = fs.sample(999, seed=5, flow=r)
+            out += [t.cpu().numpy(), lq.cpu().numpy()]
+        loss, g = fs.gradient(th)
+        return out + [np.array([loss]), g]
+
+    p1 = fs.get_params()
+    assert not np.array_equal(p1, p0)
+    a = outputs()
+    fs.set_params(p1)
+    b = outputs()
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+    fs.close()
+
+
 def test_train_flows_fits_each_flow_to_its_own_data():
     """One set trains three flows on three different densities (y = A l + m in
     y space, l iid standard logistic) in the same launches; each reaches its own
