@@ -723,18 +723,28 @@ __device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity)
     return ok != 0;
 }
 
-// waits for the phase of this parity to complete, for at most kTcWaitNs
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(ok)
+                 : "r"(bar), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+
+// waits for the phase of this parity to complete, for at most kTcWaitNs. The
+// clock (a long-latency read of the global timer) starts only once a first
+// try has failed, and is read every 8th try after that: the issuing thread
+// meets mostly completed phases, and a timer read per wait had cost it
+// hundreds of cycles per job.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
 {
+    if (mbar_try(bar, parity)) return true;
     const unsigned long long t0 = global_ns();
-    while (true) {
-        uint32_t ok;
-        asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
-                     : "=r"(ok)
-                     : "r"(bar), "r"(parity)
-                     : "memory");
-        if (ok) return true;
-        if (global_ns() - t0 > kTcWaitNs) return false;
+    for (uint32_t i = 1;; ++i) {
+        if (mbar_try(bar, parity)) return true;
+        if ((i & 7u) == 0 && global_ns() - t0 > kTcWaitNs) return false;
     }
 }
 
