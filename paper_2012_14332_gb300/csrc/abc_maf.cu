@@ -638,10 +638,11 @@ __global__ void __launch_bounds__(kFwdThreads, kSampMinBlocks) sample_kernel(con
 // warp's job is one (block, half) of one tile: it stores h and g_a1 of 128
 // hidden units (eight 16-unit chunks) into its A slot (and, in a block's
 // first job, g_out and x into its B slot), then arrives on full[w]. The
-// issuing thread polls the full barriers, issues the job's two products and
-// commits them to empty[w]. A warp waits on empty[w] before the first store
-// of its next job; a commit tracks every product the thread issued before
-// it, so the previous block's products are done when the B slot is
+// issuing thread takes round n (job n of every warp) in warp order, issues
+// each job's two products and commits the round to one round barrier. A
+// warp waits for its previous round's phase of that barrier before the first
+// store of its next job; a commit tracks every product the thread issued
+// before it, so the previous block's products are done when the B slot is
 // rewritten. All products come from one thread in issue order, so
 // accumulations into the same TMEM columns never race.
 //
@@ -872,7 +873,7 @@ __global__ void __launch_bounds__((W + 1) * 32, 1) grad_kernel(const uint32_t* _
     static_assert(!PAIR || W % 2 == 0, "whole pairs");
     constexpr int TPC = PAIR ? W / 2 : W;   // tiles a CTA works on at once
     extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ __align__(8) uint64_t bar_full[W], bar_empty[W], bar_done, bar_stage;
+    __shared__ __align__(8) uint64_t bar_full[W], bar_round, bar_done, bar_stage;
     __shared__ uint32_t tmem_s, init_s;
     __shared__ float ssum_w[W][2];       // per compute warp: weighted loss sum, weight sum
     __shared__ float gb2_w[W][K * 16];   // per compute warp: db2 sums
@@ -910,8 +911,8 @@ __global__ void __launch_bounds__((W + 1) * 32, 1) grad_kernel(const uint32_t* _
         if (lane == 0) {
             for (int i = 0; i < W; ++i) {
                 mbar_init(smem_addr(&bar_full[i]), 1);
-                mbar_init(smem_addr(&bar_empty[i]), 1);
             }
+            mbar_init(smem_addr(&bar_round), 1);
             mbar_init(smem_addr(&bar_done), 1);
             asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         }
@@ -936,7 +937,7 @@ __global__ void __launch_bounds__((W + 1) * 32, 1) grad_kernel(const uint32_t* _
         const int g = lane >> 2, t = lane & 3, rg = 16 * g + 4 * t, sw = g & 4;
         unsigned char* sA = smem + warp * kTcSlot;   // h at 0, g_a1 at kTcHalf, the B slot after
         unsigned char* sB = sA + 2 * kTcHalf;
-        const uint32_t full = smem_addr(&bar_full[warp]), empty = smem_addr(&bar_empty[warp]);
+        const uint32_t full = smem_addr(&bar_full[warp]), empty = smem_addr(&bar_round);
         uint32_t job = 0;
         bool ok = true;
         const int hw = H / 2 + 4, chunks = H / 16;
@@ -1121,10 +1122,14 @@ __global__ void __launch_bounds__((W + 1) * 32, 1) grad_kernel(const uint32_t* _
         // testing: no products, so the wait for bar_done below runs out
         init_s = 0;
     } else if (lane == 0) {
-        // the issuing thread: job n of every warp in warp order, then job n + 1
-        // (a warp's jobs: tile, block K-1..0, half; a pair member's: tile,
-        // block K-1..0, with its own half), so each column group accumulates
-        // in the same order in every run
+        // the issuing thread: round n is job n of every warp, issued in warp
+        // order (a warp's jobs: tile, block K-1..0, half; a pair member's:
+        // tile, block K-1..0, with its own half), so each column group
+        // accumulates in the same order in every run. Warps whose stores are
+        // already in are gathered and issued under one tensor-core fence; the
+        // thread waits only on a warp that is not ready yet. One commit ends
+        // the round: its products complete within about a hundred cycles,
+        // and every warp waits on that round barrier before reusing its slot.
         const uint32_t per_tile = PAIR ? (uint32_t)K : (uint32_t)D;
         uint32_t total[W], most = 0;
 #pragma unroll
@@ -1136,26 +1141,40 @@ __global__ void __launch_bounds__((W + 1) * 32, 1) grad_kernel(const uint32_t* _
         uint32_t init = 0;   // accumulator pairs written at least once
         bool ok = true;
         for (uint32_t n = 0; n < most && ok; ++n) {
+            const uint32_t bi = PAIR ? n : n / (uint32_t)C;   // block index in a warp's sequence
+            const int b = K - 1 - (int)(bi % K), cn = PAIR ? 0 : (int)(n - bi * (uint32_t)C);
+            uint32_t pending = 0;   // warps gathered, not yet issued
+            auto issue = [&]() {
+                tc_fence_after();
+#pragma unroll
+                for (int w = 0; w < W; ++w) {
+                    if (!((pending >> w) & 1u)) continue;
+                    const int d = b * C + (PAIR ? (w & 1) : cn);
+                    const uint32_t sa = smem_addr(smem + w * kTcSlot);
+                    const uint32_t sb = sa + 2 * kTcHalf;
+                    const uint32_t acc = (init >> d) & 1u;
+                    init |= 1u << d;
+                    tc_mma(tmem + 32 * d, tc_desc(sa), tc_desc(sb), acc);
+                    tc_mma(tmem + 32 * d + 16, tc_desc(sa + kTcHalf), tc_desc(sb + 512), acc);
+                }
+                pending = 0;
+            };
 #pragma unroll
             for (int w = 0; w < W; ++w) {
                 if (n >= total[w] || !ok) continue;
-                if (!mbar_wait(smem_addr(&bar_full[w]), n & 1u)) {
-                    atomicExch(err, 1);
-                    ok = false;
-                    continue;
+                const uint32_t fb = smem_addr(&bar_full[w]);
+                if (!mbar_test(fb, n & 1u)) {
+                    if (pending) issue();
+                    if (!mbar_wait(fb, n & 1u)) {
+                        atomicExch(err, 1);
+                        ok = false;
+                        continue;
+                    }
                 }
-                tc_fence_after();
-                const uint32_t bi = PAIR ? n : n / (uint32_t)C;   // block index in the warp's sequence
-                const int c = PAIR ? (w & 1) : (int)(n - bi * (uint32_t)C), b = K - 1 - (int)(bi % K);
-                const int d = b * C + c;
-                const uint32_t sa = smem_addr(smem + w * kTcSlot);
-                const uint32_t sb = sa + 2 * kTcHalf;
-                const uint32_t acc = (init >> d) & 1u;
-                init |= 1u << d;
-                tc_mma(tmem + 32 * d, tc_desc(sa), tc_desc(sb), acc);
-                tc_mma(tmem + 32 * d + 16, tc_desc(sa + kTcHalf), tc_desc(sb + 512), acc);
-                tc_commit(smem_addr(&bar_empty[w]));
+                pending |= 1u << w;
             }
+            if (pending) issue();
+            tc_commit(smem_addr(&bar_round));
         }
         init_s = init;
         tc_commit(smem_addr(&bar_done));
