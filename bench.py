@@ -237,11 +237,13 @@ def bench_streamed(abc, torch, dev, flush, sm_count, sm_max, chunks=16):
 def bench_config1(abc, torch, dev, reps=20, warmup=3):
     """Plain ABC on region_1e6_T49 (P = 1e6, T = 49): 65,536 prior samples,
     exact mode, eps at the 0.1 % distance quantile. One run is the whole
-    pipeline through the public calls: every distance (abc_distances), eps as
-    the k-th smallest, k = ceil(0.001 n) = 66 (abc_kth_smallest, radix select
-    on the device), then the rejection launch at that eps (abc_sample). The
-    observed series comes from host memory in each call; eps and the accepted
-    count are checked against the workload's own (written by the oracle)."""
+    pipeline through the public calls: every distance and prior draw
+    (abc_distances), eps as the k-th smallest, k = ceil(0.001 n) = 66
+    (abc_kth_smallest, radix select on the device), then the accept step at
+    that eps on those distances (abc_select_below: the same accepted set as a
+    rejection launch at eps, without simulating again). The observed series
+    comes from host memory in each call; eps and the accepted count are
+    checked against the workload's own (written by the oracle)."""
     with open(os.path.join(ROOT, "tests", "golden", "workloads.json")) as f:
         w = json.load(f)["region_1e6_T49"]
     obs, P, T, n, seed = np.array(w["observed"], dtype=np.int32), w["P"], w["T"], w["n_samples"], w["seed"]
@@ -250,18 +252,19 @@ def bench_config1(abc, torch, dev, reps=20, warmup=3):
     outs = (torch.empty((cap, 8), dtype=torch.float32, device=dev), torch.empty((cap,), dtype=torch.float64, device=dev),
             torch.empty((cap,), dtype=torch.int64, device=dev))
     dbuf = torch.empty((n,), dtype=torch.float64, device=dev)
-    stage = {"distances": [], "kth_smallest": [], "sample": []}
+    tbuf = torch.empty((n, 8), dtype=torch.float32, device=dev)
+    stage = {"distances": [], "kth_smallest": [], "select": []}
     walls, eps, n_acc = [], None, None
     for rep in range(warmup + reps):
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         ev[0].record()
-        d = abc.abc_distances(obs, P, n, seed, mode="exact", out=(dbuf, None))
+        d, th = abc.abc_distances(obs, P, n, seed, mode="exact", want_theta=True, out=(dbuf, tbuf))
         ev[1].record()
         eps = abc.abc_kth_smallest(d, k)
         ev[2].record()
-        _, _, _, n_acc = abc.abc_sample(obs, P, eps, n, seed, mode="exact", capacity=cap, out=outs)
+        _, _, _, n_acc = abc.abc_select_below(d, eps, theta=th, out=outs)
         ev[3].record()
         torch.cuda.synchronize()
         if rep >= warmup:

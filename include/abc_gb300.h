@@ -190,6 +190,30 @@ abc_status abc_step(const float* theta, const int32_t* state_in, const uint64_t*
 abc_status abc_kth_smallest(const double* dist, uint64_t n, uint64_t k, double* eps_out,
                             void* cuda_stream);
 
+/* The accept step of ABC rejection (Sec. 2.2: accept when the distance is at
+ * most eps) on distances already computed, e.g. by abc_distances over the
+ * sample indices [first_index, first_index + n): sample j is accepted iff
+ * dist[j] <= eps, and its index first_index + j, its distance and, if theta is
+ * not NULL, its theta are written out. With dist and theta from abc_distances
+ * the accepted set is exactly that of abc_sample with the same arguments and
+ * eps; choosing eps as a distance quantile (abc_kth_smallest) and selecting
+ * below it costs no second simulation.
+ *
+ *  dist       DEVICE double [n]             distances of samples 0..n-1
+ *  theta      DEVICE float  [n][8] or NULL  their parameters
+ *  theta_out  DEVICE float  [capacity][8]   accepted theta (ignored when theta is NULL)
+ *  dist_out   DEVICE double [capacity]      accepted distances
+ *  idx_out    DEVICE uint64 [capacity]      accepted sample indices
+ *  n_selected HOST   uint64                 number of accepted samples
+ *
+ * Order of the outputs, capacity overflow (ABC_ERR_CAPACITY with the true
+ * count in *n_selected) and eps (>= 0, not NaN) as in abc_sample. A NaN
+ * distance is never accepted. Uses one stream-ordered scratch counter and
+ * synchronises cuda_stream before it returns. */
+abc_status abc_select_below(const double* dist, const float* theta, uint64_t n, double eps, uint64_t first_index,
+                            float* theta_out, double* dist_out, uint64_t* idx_out, uint64_t capacity,
+                            uint64_t* n_selected, void* cuda_stream);
+
 /* Posterior-predictive projection (Sec. 5: accepted samples simulated forward
  * for 120 days, plotted as 5th to 95th percentile bands). For b < B simulate
  * theta[b] (DEVICE float [B][8]) with the random numbers of sample_index[b]

@@ -21,7 +21,8 @@ ABC_T_MAX = 4096
 PAPER_LO = (0.0,) * 8
 PAPER_HI = (1.0, 100.0, 2.0, 1.0, 1.0, 1.0, 1.0, 2.0)   # Sec. 2.1, Eq. 2
 
-EXPORTED = ("abc_sample", "abc_distances", "abc_simulate", "abc_step", "abc_kth_smallest", "abc_strerror",
+EXPORTED = ("abc_sample", "abc_distances", "abc_simulate", "abc_step", "abc_kth_smallest", "abc_select_below",
+            "abc_strerror",
             "abc_last_error", "abc_version", "abc_last_simulated_days", "abc_sample_noalloc", "abc_plan_create",
             "abc_plan_reset", "abc_plan_run", "abc_plan_run_graph", "abc_plan_tune", "abc_plan_results",
             "abc_plan_copy_results", "abc_plan_set_region", "abc_plan_set_shape", "abc_plan_destroy", "abc_maf_create",
@@ -121,6 +122,8 @@ def load(path=None):
         L.abc_simulate.argtypes = [vp, vp, u64, vp, i32, i64, u64, u32, ctypes.c_int, vp, vp]
         L.abc_step.argtypes = [vp, vp, vp, vp, u64, i64, u64, u32, ctypes.c_int, vp, vp, vp]
         L.abc_kth_smallest.argtypes = [vp, u64, u64, ctypes.POINTER(ctypes.c_double), vp]
+        L.abc_select_below.argtypes = [vp, vp, u64, ctypes.c_double, u64, vp, vp, vp, u64,
+                                       ctypes.POINTER(ctypes.c_uint64), vp]
         L.abc_observed_create.argtypes = [vp, i32, i64, ctypes.POINTER(ctypes.c_void_p)]
         L.abc_observed_destroy.argtypes = [vp]
         L.abc_sample_async.argtypes = [box, vp, ctypes.c_double, u64, u64, u32, ctypes.c_int, u64, vp, vp, vp, u64,
@@ -128,7 +131,7 @@ def load(path=None):
         L.abc_sample_until.argtypes = [box, vp, ctypes.c_double, u64, u64, u64, u64, u32, ctypes.c_int, u64, vp, vp,
                                        vp, u64, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64), vp]
         for nm in ("abc_sample", "abc_sample_noalloc", "abc_distances", "abc_simulate", "abc_step",
-                   "abc_kth_smallest", "abc_observed_create", "abc_observed_destroy", "abc_sample_async",
+                   "abc_kth_smallest", "abc_select_below", "abc_observed_create", "abc_observed_destroy", "abc_sample_async",
                    "abc_sample_until"):
             getattr(L, nm).restype = ctypes.c_int
         L.abc_strerror.argtypes = [ctypes.c_int]
@@ -465,6 +468,32 @@ def abc_kth_smallest(dist, k, cuda_stream=None):
                             _stream(cuda_stream))
     _check(L, st)
     return out.value
+
+
+def abc_select_below(dist, eps, first_index=0, theta=None, capacity=1 << 16, out=None, cuda_stream=None):
+    """Samples accepted at eps from distances already computed (dist: CUDA f64
+    [n], theta: CUDA f32 [n, 8] or None, sample j has index first_index + j):
+    (theta [m, 8] or None, dist [m], idx [m], m), unsorted, m = the number
+    with dist <= eps. Raises AbcError when m > capacity."""
+    L = load()
+    n = dist.numel()
+    dev = dist.device
+    if out is None:
+        outs = (torch.empty((capacity, 8), dtype=torch.float32, device=dev) if theta is not None else None,
+                torch.empty((capacity,), dtype=torch.float64, device=dev),
+                torch.empty((capacity,), dtype=torch.int64, device=dev))
+    else:
+        outs = out
+        capacity = outs[1].shape[0]
+    m = ctypes.c_uint64(0)
+    st = L.abc_select_below(_dev(dist, torch.float64, (n,)), _dev(theta, torch.float32, (n, 8)) if theta is not None
+                            else None, n, float(eps), int(first_index),
+                            _dev(outs[0], torch.float32, (capacity, 8)) if theta is not None else None,
+                            _dev(outs[1], torch.float64, (capacity,)), _dev(outs[2], torch.int64, (capacity,)),
+                            capacity, ctypes.byref(m), _stream(cuda_stream))
+    _check(L, st)
+    k = int(m.value)
+    return (outs[0][:k] if theta is not None else None), outs[1][:k], outs[2][:k], k
 
 
 def abc_strerror(status):

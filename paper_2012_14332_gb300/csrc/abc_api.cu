@@ -647,30 +647,58 @@ abc_status abc_kth_smallest(const double* dist, uint64_t n, uint64_t k, double* 
     cudaStream_t s = (cudaStream_t)cuda_stream;
     abc_status st;
     Scratch sc;
-    if ((st = alloc_scratch(sc, 257 * sizeof(unsigned long long), s)) != ABC_OK) return st;
+    const size_t bytes = 258 * sizeof(unsigned long long) + sizeof(abcgb::SelectState);
+    if ((st = alloc_scratch(sc, bytes, s)) != ABC_OK) return st;
     unsigned long long* hist_d = (unsigned long long*)sc.ptr;
-    unsigned long long hist[257];
-    uint64_t prefix = 0, mask = 0, rank = k;   // rank: 1-based rank within the current prefix
-    for (int shift = 56; shift >= 0; shift -= 8) {
-        CUDA_TRY(cudaMemsetAsync(hist_d, 0, sizeof hist, s), "cudaMemsetAsync(hist)");
-        if (injected("launch")) return fail(ABC_ERR_CUDA, "kernel launch failed (injected)");
-        CUDA_TRY(abcgb::launch_digit_histogram(dist, n, prefix, mask, shift, hist_d, s), "digit_histogram launch");
-        CUDA_TRY(cudaMemcpyAsync(hist, hist_d, sizeof hist, cudaMemcpyDeviceToHost, s), "cudaMemcpyAsync(hist)");
-        CUDA_TRY(cudaStreamSynchronize(s), "cudaStreamSynchronize");
-        // first pass: keys that are NaN or carry the sign bit do not order like values
-        if (shift == 56 && hist[256] != 0)
-            return fail(ABC_ERR_INVALID_ARG, "%llu distances are negative, -0 or NaN", hist[256]);
-        uint64_t below = 0;
-        int digit = 0;
-        for (; digit < 256; ++digit) {
-            if (below + hist[digit] >= rank) break;
-            below += hist[digit];
-        }
-        rank -= below;
-        prefix |= (uint64_t)digit << shift;
-        mask |= (uint64_t)0xFF << shift;
-    }
-    std::memcpy(eps_out, &prefix, sizeof prefix);
+    abcgb::SelectState* st_d = (abcgb::SelectState*)(hist_d + 258);   // 16-byte aligned after 257 counters
+    CUDA_TRY(cudaMemsetAsync(sc.ptr, 0, bytes, s), "cudaMemsetAsync(select scratch)");
+    if (injected("launch")) return fail(ABC_ERR_CUDA, "kernel launch failed (injected)");
+    CUDA_TRY(abcgb::launch_kth_select(dist, n, k, hist_d, st_d, s), "radix select launch");
+    abcgb::SelectState h;
+    CUDA_TRY(cudaMemcpyAsync(&h, st_d, sizeof h, cudaMemcpyDeviceToHost, s), "cudaMemcpyAsync(select state)");
+    CUDA_TRY(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+    // keys that are NaN or carry the sign bit do not order like values
+    if (h.bad != 0) return fail(ABC_ERR_INVALID_ARG, "%llu distances are negative, -0 or NaN", h.bad);
+    std::memcpy(eps_out, &h.prefix, sizeof h.prefix);
+    return ok();
+}
+
+abc_status abc_select_below(const double* dist, const float* theta, uint64_t n, double eps, uint64_t first_index,
+                            float* theta_out, double* dist_out, uint64_t* idx_out, uint64_t capacity,
+                            uint64_t* n_selected, void* cuda_stream)
+{
+    if (!n_selected) return fail(ABC_ERR_INVALID_ARG, "n_selected is NULL");
+    *n_selected = 0;
+    if (!(eps >= 0.0)) return fail(ABC_ERR_INVALID_ARG, "eps must be >= 0 and not NaN");
+    if (n > 0 && !dist) return fail(ABC_ERR_INVALID_ARG, "dist is NULL");
+    if (capacity > 0 && (!dist_out || !idx_out || (theta && !theta_out)))
+        return fail(ABC_ERR_INVALID_ARG, "an output buffer is NULL");
+    if (n > ~(uint64_t)0 - first_index) return fail(ABC_ERR_INVALID_ARG, "first_index + n overflows");
+    if (n == 0) return ok();
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    abc_status st;
+    Scratch sc;
+    if ((st = alloc_scratch(sc, sizeof(unsigned long long), s)) != ABC_OK) return st;
+    CUDA_TRY(cudaMemsetAsync(sc.ptr, 0, sizeof(unsigned long long), s), "cudaMemsetAsync(count)");
+    abcgb::SelectArgs a;
+    a.dist = dist;
+    a.theta = theta;
+    a.n = n;
+    a.first_index = first_index;
+    a.eps = eps;
+    a.theta_out = theta ? theta_out : nullptr;
+    a.dist_out = dist_out;
+    a.idx_out = idx_out;
+    a.capacity = capacity;
+    a.count = (unsigned long long*)sc.ptr;
+    if (injected("launch")) return fail(ABC_ERR_CUDA, "kernel launch failed (injected)");
+    CUDA_TRY(abcgb::launch_select_below(a, s), "select_below launch");
+    unsigned long long count = 0;
+    CUDA_TRY(cudaMemcpyAsync(&count, sc.ptr, sizeof count, cudaMemcpyDeviceToHost, s), "cudaMemcpyAsync(count)");
+    CUDA_TRY(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+    *n_selected = count;
+    if (count > capacity)
+        return fail(ABC_ERR_CAPACITY, "%llu samples accepted, capacity %llu", count, (unsigned long long)capacity);
     return ok();
 }
 

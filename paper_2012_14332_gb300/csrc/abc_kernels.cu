@@ -318,20 +318,24 @@ __global__ void __launch_bounds__(kBandThreads) band_kernel(const int32_t* __res
 }
 
 // ---------------------------------------------------------------------------
-// Radix select of the k-th smallest distance: histogram of one 8-bit digit of
-// the keys (the bit patterns of non-negative doubles order like the values)
-// among the keys whose higher digits equal `prefix`. On the first pass
-// (prefix_mask == 0) hist[256] counts the keys above +infinity's pattern:
+// Radix select of the k-th smallest distance: eight passes over the keys (the
+// bit patterns of non-negative doubles order like the values), one 8-bit
+// digit per pass from the top. A pass histograms that digit among the keys
+// whose higher digits equal the prefix chosen so far; the select kernel then
+// picks the digit holding the wanted rank and updates the state in device
+// memory, so the passes run back to back with no host round trip. On the
+// first pass (mask == 0) hist[256] counts the keys above +infinity's pattern:
 // NaN and anything with the sign bit set (negative values and -0), which
 // would not order like their values.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kBlockThreads) digit_histogram_kernel(const double* __restrict__ dist, uint64_t n,
-                                                                        uint64_t prefix, uint64_t prefix_mask,
-                                                                        int shift, unsigned long long* __restrict__ hist)
+                                                                        const SelectState* __restrict__ st, int shift,
+                                                                        unsigned long long* __restrict__ hist)
 {
     __shared__ unsigned int h[257];
     for (int b = threadIdx.x; b < 257; b += blockDim.x) h[b] = 0;
     __syncthreads();
+    const uint64_t prefix = st->prefix, prefix_mask = st->mask;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     const bool first = prefix_mask == 0;
     for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
@@ -342,6 +346,86 @@ __global__ void __launch_bounds__(kBlockThreads) digit_histogram_kernel(const do
     __syncthreads();
     for (int b = threadIdx.x; b < 257; b += blockDim.x)
         if (h[b]) atomicAdd(&hist[b], (unsigned long long)h[b]);
+}
+
+// One warp: the digit of this pass is the first whose running count reaches
+// the rank (k on the first pass); the rank becomes the rank within that
+// digit's keys. Lane j holds bins 8j .. 8j + 7: a warp scan of the lanes'
+// sums finds the lane, then that lane walks its eight bins. Zeroes the
+// histogram for the next pass.
+__global__ void __launch_bounds__(32) digit_select_kernel(unsigned long long* __restrict__ hist,
+                                                          SelectState* __restrict__ st, int shift, uint64_t k)
+{
+    const int lane = threadIdx.x;
+    unsigned long long h[8], sum = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        h[i] = hist[8 * lane + i];
+        sum += h[i];
+    }
+    const bool first = st->mask == 0;
+    const uint64_t rank = first ? k : st->rank;
+    if (first && lane == 0) st->bad = hist[256];
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < 8; ++i) hist[8 * lane + i] = 0;
+    if (lane == 0) hist[256] = 0;
+    // inclusive scan of the lanes' sums
+    unsigned long long incl = sum;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const unsigned long long v = __shfl_up_sync(0xFFFFFFFFu, incl, off);
+        if (lane >= off) incl += v;
+    }
+    const uint32_t reach = __ballot_sync(0xFFFFFFFFu, incl >= rank);
+    // the first lane whose running count reaches the rank (the last lane if
+    // none does, which only invalid input allows)
+    const int owner = reach ? __ffs(reach) - 1 : 31;
+    if (lane == owner) {
+        uint64_t below = incl - sum;
+        int i = 0;
+        for (; i < 7; ++i) {
+            if (below + h[i] >= rank) break;
+            below += h[i];
+        }
+        st->rank = rank - below;
+        st->prefix |= (uint64_t)(8 * lane + i) << shift;
+        st->mask |= (uint64_t)0xFF << shift;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Samples accepted at eps from distances already computed (Sec. 2.2: accept
+// when the distance is at most eps): sample j is accepted iff dist[j] <= eps.
+// Each warp takes 32 consecutive samples at a time, reserves the slots of its
+// accepts with one atomicAdd and writes index, distance and theta. Every
+// accept is counted; only slots below capacity are written.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kBlockThreads) select_below_kernel(const __grid_constant__ SelectArgs a)
+{
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x / 32);
+    for (uint64_t base = ((uint64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5)) * 32; base < a.n;
+         base += warps * 32) {
+        const uint64_t j = base + lane;
+        const bool take = j < a.n && a.dist[j] <= a.eps;
+        const uint32_t mask = __ballot_sync(0xFFFFFFFFu, take);
+        if (!mask) continue;
+        unsigned long long slot0 = 0;
+        if (lane == 0) slot0 = atomicAdd(a.count, (unsigned long long)__popc(mask));
+        slot0 = __shfl_sync(0xFFFFFFFFu, slot0, 0);
+        if (!take) continue;
+        const uint64_t slot = slot0 + __popc(mask & ((1u << lane) - 1u));
+        if (slot >= a.capacity) continue;
+        a.idx_out[slot] = a.first_index + j;
+        a.dist_out[slot] = a.dist[j];
+        if (a.theta_out) {
+            const float4* src = reinterpret_cast<const float4*>(a.theta + 8 * j);
+            float4* to = reinterpret_cast<float4*>(a.theta_out + 8 * slot);
+            to[0] = src[0];
+            to[1] = src[1];
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -505,14 +589,27 @@ cudaError_t launch_bands(const int32_t* traj, uint32_t B, int32_t T, const float
     return cudaGetLastError();
 }
 
-cudaError_t launch_digit_histogram(const double* dist, uint64_t n, uint64_t prefix, uint64_t prefix_mask, int shift,
-                                   unsigned long long* hist, cudaStream_t s)
+cudaError_t launch_select_below(const SelectArgs& a, cudaStream_t s)
+{
+    int grid = 0;
+    cudaError_t e = grid_for(select_below_kernel, 0, &grid);
+    if (e != cudaSuccess) return e;
+    grid = blocks_for(a.n, grid);
+    select_below_kernel<<<grid, kBlockThreads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_kth_select(const double* dist, uint64_t n, uint64_t k, unsigned long long* hist, SelectState* st,
+                              cudaStream_t s)
 {
     int grid = 0;
     cudaError_t e = grid_for(digit_histogram_kernel, 0, &grid);
     if (e != cudaSuccess) return e;
     grid = blocks_for(n, grid);
-    digit_histogram_kernel<<<grid, kBlockThreads, 0, s>>>(dist, n, prefix, prefix_mask, shift, hist);
+    for (int shift = 56; shift >= 0; shift -= 8) {
+        digit_histogram_kernel<<<grid, kBlockThreads, 0, s>>>(dist, n, st, shift, hist);
+        digit_select_kernel<<<1, 32, 0, s>>>(hist, st, shift, k);
+    }
     return cudaGetLastError();
 }
 

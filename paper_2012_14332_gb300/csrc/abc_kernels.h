@@ -106,9 +106,28 @@ cudaError_t launch_simulate(const ModelParams& p, const SimulateArgs& a, int mod
 cudaError_t launch_step(const ModelParams& p, const StepArgs& a, int mode, cudaStream_t s);
 cudaError_t launch_bands(const int32_t* traj, uint32_t B, int32_t T, const float* qpos, int32_t n_q, float* bands,
                          cudaStream_t s);
-// hist: 257 counters, zeroed by the caller; [256] counts invalid keys on the
-// first pass (prefix_mask == 0)
-cudaError_t launch_digit_histogram(const double* dist, uint64_t n, uint64_t prefix, uint64_t prefix_mask, int shift,
-                                   unsigned long long* hist, cudaStream_t s);
+// Radix select of the k-th smallest of n distances, all passes on the device:
+// hist (257 counters) and st zeroed by the caller; afterwards st->prefix is
+// the k-th smallest key and st->bad the number of invalid keys (NaN, sign bit
+// set), in which case the prefix is meaningless.
+struct SelectState {
+    unsigned long long prefix, mask, rank, bad;
+};
+// Compaction of the samples with dist[j] <= eps (theta, theta_out may both be
+// NULL); *count (zeroed by the caller) receives the number of accepts.
+struct SelectArgs {
+    const double* dist;
+    const float* theta;
+    uint64_t n, first_index;
+    double eps;
+    float* theta_out;
+    double* dist_out;
+    uint64_t* idx_out;
+    uint64_t capacity;
+    unsigned long long* count;
+};
+cudaError_t launch_select_below(const SelectArgs& a, cudaStream_t s);
+cudaError_t launch_kth_select(const double* dist, uint64_t n, uint64_t k, unsigned long long* hist, SelectState* st,
+                              cudaStream_t s);
 
 }  // namespace abcgb

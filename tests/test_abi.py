@@ -152,6 +152,17 @@ def test_other_entry_points_validate(L):
     out = ctypes.c_double()
     assert L.abc_kth_smallest(z, 10, 0, ctypes.byref(out), None) == ABC_ERR_INVALID_ARG
     assert L.abc_kth_smallest(z, 10, 11, ctypes.byref(out), None) == ABC_ERR_INVALID_ARG
+    m = ctypes.c_uint64(5)
+    assert L.abc_select_below(z, None, 10, -1.0, 0, None, z, z, 4, ctypes.byref(m), None) == ABC_ERR_INVALID_ARG
+    assert m.value == 0
+    assert L.abc_select_below(z, None, 10, float("nan"), 0, None, z, z, 4, ctypes.byref(m), None) \
+        == ABC_ERR_INVALID_ARG
+    assert L.abc_select_below(None, None, 10, 1.0, 0, None, z, z, 4, ctypes.byref(m), None) == ABC_ERR_INVALID_ARG
+    assert L.abc_select_below(z, z, 10, 1.0, 0, None, z, z, 4, ctypes.byref(m), None) == ABC_ERR_INVALID_ARG
+    assert L.abc_select_below(z, None, 10, 1.0, 0, None, z, z, 4, None, None) == ABC_ERR_INVALID_ARG
+    assert L.abc_select_below(z, None, 10, 1.0, ~0 & (2**64 - 1), None, z, z, 4, ctypes.byref(m), None) \
+        == ABC_ERR_INVALID_ARG
+    assert L.abc_select_below(None, None, 0, 1.0, 0, None, None, None, 0, ctypes.byref(m), None) == 0
     from paper_2012_14332_gb300.binding import prior_box
     box = prior_box()
     obs = np.zeros((3, 11), dtype=np.int32)

@@ -351,6 +351,40 @@ def test_kth_smallest_rejects_values_that_do_not_order(bad):
     assert abc.abc_kth_smallest(torch.from_numpy(x).to(DEV), 1) == 0.0
 
 
+@pytest.mark.parametrize("mode", ["exact", "fast"])
+def test_select_below_equals_rejection_at_eps(mode):
+    """The quantile pipeline of the small workload (P = 1e6, T = 49, 65,536
+    prior samples): every distance with theta, eps as the 66-th smallest
+    distance (0.1 %), then the samples at or below eps selected from those
+    distances. The selected (index, theta, distance) set equals the rejection
+    launch's at that eps bit for bit, in both modes (a mode's distances are the
+    same in both calls); in exact mode it is also the oracle's accept set."""
+    w = inputs.workload("region_1e6_T49")
+    obs, P, n, seed = w["observed"], w["P"], w["n_samples"], w["seed"]
+    d, th_all = abc.abc_distances(obs, P, n, seed, mode=mode, first_index=7, want_theta=True)
+    eps = abc.abc_kth_smallest(d, 66)
+    th, di, ix, m = abc.abc_select_below(d, eps, first_index=7, theta=th_all, capacity=1024)
+    assert m >= 66
+    ref = abc.abc_sample(obs, P, eps, n, seed, mode=mode, first_index=7, capacity=1024)
+    assert ref[3] == m
+    a, b = _sorted(th, di, ix), _sorted(*ref[:3])
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+    if mode == "exact":
+        res = oracle.abc(obs, P, eps, n, seed, first_index=7)
+        assert np.array_equal(a[2], np.asarray(res["idx"], dtype=np.uint64))
+        assert np.array_equal(a[1], np.asarray(res["dist"], dtype=np.float64))
+    # capacity below the count: the true count, and the call reports it
+    with pytest.raises(abc.AbcError) as e:
+        abc.abc_select_below(d, eps, first_index=7, theta=th_all, capacity=m - 1)
+    assert e.value.status == abc.binding.ABC_ERR_CAPACITY
+    # without theta: indices and distances only
+    none, di2, ix2, m2 = abc.abc_select_below(d, eps, first_index=7, capacity=1024)
+    assert none is None and m2 == m
+    o = np.argsort(ix2.cpu().numpy())
+    assert np.array_equal(ix2.cpu().numpy()[o], a[2]) and np.array_equal(di2.cpu().numpy()[o], a[1])
+
+
 def test_full_size_launch_sampled_against_oracle():
     """The benchmark's launch: 2^24 samples of the P = 6e7, T = 100 workload.
     Exact mode: every accepted sample is re-derived by the oracle (theta bits,
