@@ -1307,16 +1307,24 @@ __global__ void __launch_bounds__(256) grad_reduce_kernel(const float* __restric
 // One Adam update (Kingma, Ba 2015) of a parameter with gradient gr at step
 // t >= 1; the fused multiply-adds are written out, so both Adam kernels round
 // alike.
-__device__ __forceinline__ void adam_update(float& param, float& m, float& v, float gr, int t, float lr, float b1,
-                                            float b2, float eps)
+// c1 = 1 - b1^t and c2 = 1 - b2^t are the step's bias corrections (adam_bias),
+// the same for every parameter.
+__device__ __forceinline__ void adam_update(float& param, float& m, float& v, float gr, float c1, float c2, float lr,
+                                            float b1, float b2, float eps)
 {
     const float mi = __fmaf_rn(b1, m, __fmul_rn(1.f - b1, gr));
     const float vi = __fmaf_rn(b2, v, __fmul_rn(__fmul_rn(1.f - b2, gr), gr));
     m = mi;
     v = vi;
-    const float mh = __fdiv_rn(mi, 1.f - powf(b1, (float)t));
-    const float vh = __fdiv_rn(vi, 1.f - powf(b2, (float)t));
+    const float mh = __fdiv_rn(mi, c1);
+    const float vh = __fdiv_rn(vi, c2);
     param = __fmaf_rn(-lr, __fdiv_rn(mh, __fadd_rn(sqrtf(vh), eps)), param);
+}
+
+__device__ __forceinline__ void adam_bias(int t, float b1, float b2, float& c1, float& c2)
+{
+    c1 = 1.f - powf(b1, (float)t);
+    c2 = 1.f - powf(b2, (float)t);
 }
 
 __global__ void tick_kernel(int* step) { *step += 1; }
@@ -1380,15 +1388,16 @@ __global__ void __launch_bounds__(256) adam_publish_kernel(float* __restrict__ p
                                                            const TrainSlot* __restrict__ slots, float* __restrict__ m,
                                                            float* __restrict__ v, int* __restrict__ step,
                                                            unsigned* __restrict__ done, uint32_t* __restrict__ pub,
-                                                           int K, int H, int64_t n_params, float lr, float b1,
-                                                           float b2, float eps)
+                                                           int K, int H, const __grid_constant__ Layout L,
+                                                           int64_t n_params, float lr, float b1, float b2, float eps)
 {
     constexpr int E = 256 / G;
     __shared__ float gs[G][E];
-    __shared__ float w_s;
+    __shared__ float w_s, c_s[2];
     const int f = blockIdx.y, e = threadIdx.x % E, q = threadIdx.x / E;
     const int64_t p = (int64_t)blockIdx.x * E + e;
     const int t_step = *step + 1;
+    if (threadIdx.x == 32) adam_bias(t_step, b1, b2, c_s[0], c_s[1]);
     const bool has_rows = slots[f].n != 0;   // uniform over the block
     const float* base = part + (size_t)f * nblk * part_stride;
     if (threadIdx.x < 32) {
@@ -1418,11 +1427,10 @@ __global__ void __launch_bounds__(256) adam_publish_kernel(float* __restrict__ p
     if (has_rows && q == 0 && p < n_params && W > 0.f) {
         const int64_t i = (int64_t)f * n_params + p;
         float pi = params[i], mi = m[i], vi = v[i];
-        adam_update(pi, mi, vi, __fdiv_rn(g, W), t_step, lr, b1, b2, eps);
+        adam_update(pi, mi, vi, __fdiv_rn(g, W), c_s[0], c_s[1], lr, b1, b2, eps);
         params[i] = pi;
         m[i] = mi;
         v[i] = vi;
-        const Layout L = layout(H);
         const int mb = master_block(H), b = (int)(p / mb);
         publish_param(pub + ((size_t)f * K + b) * L.words, H, L, (int)(p - (int64_t)b * mb), pi);
     }
@@ -1449,7 +1457,9 @@ __global__ void adam_kernel(float* __restrict__ params, const float* __restrict_
     const float W = sums[2 * (i / n_params) + 1];
     if (!(W > 0.f)) return;
     float pi = params[i], mi = m[i], vi = v[i];
-    adam_update(pi, mi, vi, __fdiv_rn(grad[i], W), *step, lr, b1, b2, eps);
+    float c1, c2;
+    adam_bias(*step, b1, b2, c1, c2);
+    adam_update(pi, mi, vi, __fdiv_rn(grad[i], W), c1, c2, lr, b1, b2, eps);
     params[i] = pi;
     m[i] = mi;
     v[i] = vi;
@@ -1710,7 +1720,8 @@ void launch_adam_publish(abc_maf f, int nblk, float lr, cudaStream_t s)
 {
     maf::adam_publish_kernel<G><<<dim3((unsigned)((f->n_params + 256 / G - 1) / (256 / G)), f->R), 256, 0, s>>>(
         f->d_params, f->d_part, nblk, part_stride(f), f->d_slots, f->d_m, f->d_v, f->d_step,
-        reinterpret_cast<unsigned*>(f->d_step + 1), f->d_pub, f->K, f->H, f->n_params, lr, 0.9f, 0.999f, 1e-8f);
+        reinterpret_cast<unsigned*>(f->d_step + 1), f->d_pub, f->K, f->H, maf::layout(f->H), f->n_params, lr, 0.9f,
+        0.999f, 1e-8f);
 }
 
 // gradients of every flow's slot: with draw_step, `batch` rows per flow drawn
