@@ -123,7 +123,7 @@ def measured_peaks():
 # dram__bytes_read.sum + dram__bytes_write.sum per headline launch, taken by
 # ncu from a capture of the rejection kernel as it stands; None when the
 # kernel has changed since the last capture (the line then reports null).
-REJECT_TRAFFIC_BYTES = 217344
+REJECT_TRAFFIC_BYTES = 153088
 
 
 def roofline(sim_days_per_launch, launch_ms, sm_count, sm_max_mhz, traffic=None, samples_per_launch=0):
