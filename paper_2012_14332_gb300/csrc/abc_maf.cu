@@ -672,7 +672,7 @@ __global__ void __launch_bounds__(kFwdThreads, kSampMinBlocks) sample_kernel(con
 // up in warp order; in the paired form the two members add their partial
 // sums commutatively, so both hold the same values; and each CTA writes its
 // whole partial gradient to its own slot of a buffer whose slots are added in
-// a fixed tree (grad_reduce_kernel, adam_partials_kernel; no float atomics
+// a fixed tree (grad_reduce_kernel, adam_publish_kernel; no float atomics
 // anywhere).
 
 // compute warps per CTA: 4, or 15 when a step has enough tiles for more than
