@@ -385,6 +385,23 @@ def test_select_below_equals_rejection_at_eps(mode):
     assert np.array_equal(ix2.cpu().numpy()[o], a[2]) and np.array_equal(di2.cpu().numpy()[o], a[1])
 
 
+def test_local_k_smallest_for_the_distributed_quantile():
+    """A rank's part of the distributed quantile (sharding.local_k_smallest):
+    its k smallest distances, found on the device by the radix select and the
+    accept step, equal the first k of a sort; ties at the k-th value (more
+    of them than k) and k above n are handled."""
+    from paper_2012_14332_gb300.sharding import local_k_smallest
+    w = inputs.workload("region_1e6_T49")
+    d = abc.abc_distances(w["observed"], w["P"], 20000, w["seed"], mode="exact", first_index=3)
+    ref = np.sort(d.cpu().numpy())
+    for k in (1, 66, 1000):
+        assert np.array_equal(local_k_smallest(d, k), ref[:k])
+    x = np.concatenate([np.full(300, 2.5), inputs.rng(9).random(5000) * 10 + 3.0, [0.5, 1.0]])
+    t = torch.from_numpy(x).to(DEV)
+    assert np.array_equal(local_k_smallest(t, 10), np.sort(x)[:10])
+    assert np.array_equal(local_k_smallest(t[:50], 80), np.full(50, 2.5))
+
+
 def test_full_size_launch_sampled_against_oracle():
     """The benchmark's launch: 2^24 samples of the P = 6e7, T = 100 workload.
     Exact mode: every accepted sample is re-derived by the oracle (theta bits,
