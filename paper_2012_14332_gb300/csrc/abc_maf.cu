@@ -855,16 +855,18 @@ struct TrainSlot {
     uint64_t n;
 };
 
-// Flow f = blockIdx.y reads slots[f]: with draw_step, `batch` rows drawn for
-// training step *draw_step (batch_row; none if the flow has no points), else
-// all its n points.
+// Flow f = blockIdx.y reads slots[f]: with a ticket counter (a training step),
+// `batch` rows drawn for the step (batch_row; none if the flow has no points),
+// else all its n points. Each CTA of a training launch takes a ticket; the
+// step is the ticket over `ctas`, the launch's CTA count, whatever order the
+// CTAs start in, and after the launch the counter stands at (step + 1) ctas.
 // Dynamic shared memory: W slots of kTcSlot bytes, then the K blocks' published
 // operands.
 template <int K, int W, bool PAIR>
 __global__ void __launch_bounds__((W + 1) * 32, 1) grad_kernel(const uint32_t* __restrict__ pub, int H,
                                                                const __grid_constant__ Box box,
                                                                const TrainSlot* __restrict__ slots,
-                                                               const int* __restrict__ draw_step,
+                                                               unsigned* __restrict__ ticket, uint32_t ctas,
                                                                const __grid_constant__ ModelParams rp, uint32_t batch,
                                                                float* __restrict__ part, uint32_t part_stride,
                                                                int* __restrict__ err, int hold)
@@ -882,9 +884,10 @@ __global__ void __launch_bounds__((W + 1) * 32, 1) grad_kernel(const uint32_t* _
     const int mb = master_block(H);
     const int f = blockIdx.y;
     const TrainSlot slot = slots[f];
-    const uint64_t n_rows = draw_step ? (slot.n ? batch : 0) : slot.n;
+    __shared__ uint32_t step_s;
+    if (ticket && threadIdx.x == 0) step_s = atomicAdd(ticket, 1u) / ctas;   // before any CTA returns
+    const uint64_t n_rows = ticket ? (slot.n ? batch : 0) : slot.n;
     if (n_rows == 0) return;   // uniform over the block
-    const uint32_t step_now = draw_step ? (uint32_t)*draw_step : 0u;
     const float* __restrict__ theta = slot.theta;
     const float* __restrict__ weights = slot.w;
     pub += (size_t)f * K * L.words;
@@ -897,6 +900,7 @@ __global__ void __launch_bounds__((W + 1) * 32, 1) grad_kernel(const uint32_t* _
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
+    const uint32_t step_now = ticket ? step_s : 0u;
     stage_blocks_bulk(wsm, pub, K, 0, L.grad_words, L, smem_addr(&bar_stage));
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int C = (H + kTcM - 1) / kTcM;   // jobs (128-unit halves) per block
@@ -949,7 +953,7 @@ __global__ void __launch_bounds__((W + 1) * 32, 1) grad_kernel(const uint32_t* _
         for (uint64_t tile = (uint64_t)blockIdx.x * TPC + pair; tile < tiles; tile += tstride) {
             const uint64_t q0 = tile * 16 + g, q1 = q0 + 8;
             uint64_t i0 = q0 < n_rows ? q0 : 0, i1 = q1 < n_rows ? q1 : 0;
-            if (draw_step) {
+            if (ticket) {
                 // lanes t = 0 and 1 of the row group draw rows q0 and q1
                 const uint64_t qm = t ? q1 : q0;
                 const uint32_t mine = t < 2 && qm < n_rows ? batch_row(rp, (uint32_t)qm, step_now, f, slot.n) : 0u;
@@ -1377,17 +1381,18 @@ __device__ __forceinline__ void publish_param(uint32_t* __restrict__ pb, int H, 
 
 // A training step's Adam and publish in one launch: adam_kernel on the
 // gradient kernel's per-CTA partials, added here in the fixed tree of
-// group_sum, at step *step + 1; each updated parameter is published at once
-// (publish_param). A block updates 256 / G parameters of flow blockIdx.y; a
-// flow without rows this step keeps its parameters, moments and published
-// words. The last block to finish advances *step (done[0] counts finished
-// blocks and is back at 0 afterwards): every block has read the step by then.
+// group_sum; each updated parameter is published at once (publish_param). A
+// block updates 256 / G parameters of flow blockIdx.y; a flow without rows
+// this step keeps its parameters, moments and published words. The step t is
+// the gradient launch's ticket count over its CTA count (grad_kernel): the
+// counter stands at t grad_ctas after the gradient launch of step t - 1, so
+// no launch has to advance a step counter.
 template <int G>
 __global__ void __launch_bounds__(256) adam_publish_kernel(float* __restrict__ params, const float* __restrict__ part,
                                                            int nblk, uint32_t part_stride,
                                                            const TrainSlot* __restrict__ slots, float* __restrict__ m,
-                                                           float* __restrict__ v, int* __restrict__ step,
-                                                           unsigned* __restrict__ done, uint32_t* __restrict__ pub,
+                                                           float* __restrict__ v, const unsigned* __restrict__ ticket,
+                                                           uint32_t grad_ctas, uint32_t* __restrict__ pub,
                                                            int K, int H, const __grid_constant__ Layout L,
                                                            int64_t n_params, float lr, float b1, float b2, float eps)
 {
@@ -1396,7 +1401,7 @@ __global__ void __launch_bounds__(256) adam_publish_kernel(float* __restrict__ p
     __shared__ float w_s, c_s[2];
     const int f = blockIdx.y, e = threadIdx.x % E, q = threadIdx.x / E;
     const int64_t p = (int64_t)blockIdx.x * E + e;
-    const int t_step = *step + 1;
+    const int t_step = (int)(*ticket / grad_ctas);
     if (threadIdx.x == 32) adam_bias(t_step, b1, b2, c_s[0], c_s[1]);
     const bool has_rows = slots[f].n != 0;   // uniform over the block
     const float* base = part + (size_t)f * nblk * part_stride;
@@ -1433,16 +1438,6 @@ __global__ void __launch_bounds__(256) adam_publish_kernel(float* __restrict__ p
         v[i] = vi;
         const int mb = master_block(H), b = (int)(p / mb);
         publish_param(pub + ((size_t)f * K + b) * L.words, H, L, (int)(p - (int64_t)b * mb), pi);
-    }
-    // the tick: this block has read the step (the barrier), so the last
-    // block's increment comes after every read
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        if (atomicAdd(done, 1u) == gridDim.x * gridDim.y - 1) {
-            *step = t_step;
-            *done = 0u;
-        }
     }
 }
 
@@ -1488,7 +1483,7 @@ struct abc_maf_s {
     float* d_sums = nullptr;   // [R][2] (weighted loss sum, weight sum)
     int* d_err = nullptr;      // set by a gradient kernel whose bounded wait ran out
     int hold = 0;              // testing: the gradient kernel issues no products
-    int* d_step = nullptr;     // [0] the training step, [1] a training step's finished Adam blocks
+    int* d_step = nullptr;     // [0] the step of abc_maf_adam_step, [1] a training run's ticket counter
     maf::TrainSlot* d_slots = nullptr;   // [R] training data of each flow
     float* d_best = nullptr;   // [R][n_params] best parameters under validation (allocated on first use)
     cudaGraphExec_t graph = nullptr;
@@ -1714,22 +1709,24 @@ void launch_reduce(abc_maf f, bool drawn, uint32_t batch, int nblk, uint32_t str
         f->d_part, nblk, stride, np, f->d_slots, drawn ? 1 : 0, batch, f->d_grad, f->d_sums);
 }
 
-// d_step[0]: the training step; d_step[1]: the Adam launch's finished blocks
+// a training run's ticket counter (grad_kernel), zeroed when the run starts
+unsigned* train_ticket(abc_maf f) { return reinterpret_cast<unsigned*>(f->d_step + 1); }
+
 template <int G>
 void launch_adam_publish(abc_maf f, int nblk, float lr, cudaStream_t s)
 {
     maf::adam_publish_kernel<G><<<dim3((unsigned)((f->n_params + 256 / G - 1) / (256 / G)), f->R), 256, 0, s>>>(
-        f->d_params, f->d_part, nblk, part_stride(f), f->d_slots, f->d_m, f->d_v, f->d_step,
-        reinterpret_cast<unsigned*>(f->d_step + 1), f->d_pub, f->K, f->H, maf::layout(f->H), f->n_params, lr, 0.9f,
-        0.999f, 1e-8f);
+        f->d_params, f->d_part, nblk, part_stride(f), f->d_slots, f->d_m, f->d_v, train_ticket(f),
+        (uint32_t)nblk * (uint32_t)f->R, f->d_pub, f->K, f->H, maf::layout(f->H), f->n_params, lr, 0.9f, 0.999f,
+        1e-8f);
 }
 
-// gradients of every flow's slot: with draw_step, `batch` rows per flow drawn
-// for step *draw_step with rp's Philox key; else all max_n points (the
+// gradients of every flow's slot: with a ticket counter, `batch` rows per flow
+// drawn for the training step with rp's Philox key; else all max_n points (the
 // largest slot). The kernel writes per-CTA partials, the reduction adds them
 // in a fixed tree into d_grad and d_sums.
 template <int K, int W, bool PAIR>
-cudaError_t launch_grad_w(abc_maf f, const int* draw_step, const ModelParams& rp, uint32_t batch, int grid, bool reduce,
+cudaError_t launch_grad_w(abc_maf f, unsigned* ticket, const ModelParams& rp, uint32_t batch, int grid, bool reduce,
                           cudaStream_t s)
 {
     const size_t smem = grad_smem(f, W);
@@ -1739,14 +1736,15 @@ cudaError_t launch_grad_w(abc_maf f, const int* draw_step, const ModelParams& rp
     if ((size_t)f->R * grid * stride > f->part_floats) return cudaErrorInvalidValue;   // ensure_part first
     if (PAIR && (f->H + maf::kTcM - 1) / maf::kTcM != 2) return cudaErrorInvalidValue;
     maf::grad_kernel<K, W, PAIR><<<dim3(grid, f->R), (W + 1) * 32, smem, s>>>(
-        f->d_pub, f->H, f->box, f->d_slots, draw_step, rp, batch, f->d_part, stride, f->d_err, f->hold);
+        f->d_pub, f->H, f->box, f->d_slots, ticket, (uint32_t)grid * (uint32_t)f->R, rp, batch, f->d_part, stride,
+        f->d_err, f->hold);
     e = cudaGetLastError();
     if (e != cudaSuccess || !reduce) return e;
     switch (red_groups(grid)) {
-    case 1: launch_reduce<1>(f, draw_step != nullptr, batch, grid, stride, s); break;
-    case 2: launch_reduce<2>(f, draw_step != nullptr, batch, grid, stride, s); break;
-    case 4: launch_reduce<4>(f, draw_step != nullptr, batch, grid, stride, s); break;
-    default: launch_reduce<8>(f, draw_step != nullptr, batch, grid, stride, s); break;
+    case 1: launch_reduce<1>(f, ticket != nullptr, batch, grid, stride, s); break;
+    case 2: launch_reduce<2>(f, ticket != nullptr, batch, grid, stride, s); break;
+    case 4: launch_reduce<4>(f, ticket != nullptr, batch, grid, stride, s); break;
+    default: launch_reduce<8>(f, ticket != nullptr, batch, grid, stride, s); break;
     }
     return cudaGetLastError();
 }
@@ -1754,15 +1752,15 @@ cudaError_t launch_grad_w(abc_maf f, const int* draw_step, const ModelParams& rp
 // reduce: add the partials into d_grad and d_sums (a training step's Adam adds
 // them itself instead)
 template <int K>
-cudaError_t launch_grad(abc_maf f, const int* draw_step, const ModelParams& rp, uint32_t batch, uint64_t max_n, bool reduce,
+cudaError_t launch_grad(abc_maf f, unsigned* ticket, const ModelParams& rp, uint32_t batch, uint64_t max_n, bool reduce,
                         cudaStream_t s)
 {
-    const uint64_t tiles = ((draw_step ? batch : max_n) + 15) / 16;
+    const uint64_t tiles = ((ticket ? batch : max_n) + 15) / 16;
     const GradForm g = grad_form(f, tiles);
     if (g.W == maf::kGradWarpsWide)
-        return launch_grad_w<K, maf::kGradWarpsWide, false>(f, draw_step, rp, batch, g.grid, reduce, s);
-    if (g.pair) return launch_grad_w<K, maf::kGradWarpsNarrow, true>(f, draw_step, rp, batch, g.grid, reduce, s);
-    return launch_grad_w<K, maf::kGradWarpsNarrow, false>(f, draw_step, rp, batch, g.grid, reduce, s);
+        return launch_grad_w<K, maf::kGradWarpsWide, false>(f, ticket, rp, batch, g.grid, reduce, s);
+    if (g.pair) return launch_grad_w<K, maf::kGradWarpsNarrow, true>(f, ticket, rp, batch, g.grid, reduce, s);
+    return launch_grad_w<K, maf::kGradWarpsNarrow, false>(f, ticket, rp, batch, g.grid, reduce, s);
 }
 
 #define MAF_DISPATCH(fn, ...)                      \
@@ -1808,7 +1806,7 @@ cudaError_t launch_adam(abc_maf f, float lr, float b1, float b2, float eps, cuda
 // publishes every updated parameter and advances the step
 cudaError_t launch_train_step(abc_maf f, uint32_t batch, const ModelParams& p, float lr, cudaStream_t s)
 {
-    cudaError_t e = MAF_DISPATCH(launch_grad, f, f->d_step, p, batch, 0, false, s);
+    cudaError_t e = MAF_DISPATCH(launch_grad, f, train_ticket(f), p, batch, 0, false, s);
     if (e != cudaSuccess) return e;
     const int grid = grad_form(f, ((uint64_t)batch + 15) / 16).grid;
     switch (red_groups(grid)) {
