@@ -788,6 +788,32 @@ __device__ __forceinline__ void tc_ld16(uint32_t taddr, uint32_t (&v)[16])
                  : "memory");
 }
 
+// 32 consecutive 32-bit columns of this warp's 32 TMEM lanes (lane i: thread i)
+__device__ __forceinline__ void tc_ld32(uint32_t taddr, uint32_t (&v)[32])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+                 "tcgen05.wait::ld.sync.aligned;"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                   "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                   "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+                   "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
+                   "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                 : "r"(taddr)
+                 : "memory");
+}
+
+// one hidden unit's dW1 row (eight inputs, masked) as two 16-byte stores
+__device__ __forceinline__ void store_dw1(float* __restrict__ row, int l, const uint32_t* v)
+{
+    float w[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) w[j] = mask1(l, j) ? __uint_as_float(v[j]) : 0.f;
+    float4* r4 = reinterpret_cast<float4*>(row);
+    r4[0] = make_float4(w[0], w[1], w[2], w[3]);
+    r4[1] = make_float4(w[4], w[5], w[6], w[7]);
+}
+
 // mbarrier arrival that also adds `bytes` to the transaction count of the
 // current phase (the bytes bulk copies will complete on it)
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes)
@@ -1194,27 +1220,50 @@ __global__ void __launch_bounds__((W + 1) * 32, 1) grad_kernel(const uint32_t* _
         // quarter share its 2 D column groups. Every parameter of the CTA's
         // partial is written: masked entries and column groups this CTA never
         // accumulated (no tile) as 0.
+        // A row of the partial is 16-byte aligned (its stride and the block
+        // size 25 H + 16 are multiples of 4 floats, H of 16), so a unit's dW1
+        // row goes out as two 16-byte stores.
         const int quarter = warp & 3, per_quarter = (W - quarter + 3) / 4;
-        for (int cc = warp >> 2; cc < 2 * D; cc += per_quarter) {
-            const int d = cc >> 1;
-            uint32_t v[16];
-            if ((init >> d) & 1u) {   // uniform over the warp
-                tc_ld16(tmem + ((uint32_t)(32 * quarter) << 16) + 16 * cc, v);
-            } else {
+        if (per_quarter == 1) {
+            // one warp per lane quarter: both halves of a group in one load
+            for (int d = 0; d < D; ++d) {
+                uint32_t v[32];
+                if ((init >> d) & 1u) {   // uniform over the warp
+                    tc_ld32(tmem + ((uint32_t)(32 * quarter) << 16) + 32 * d, v);
+                } else {
 #pragma unroll
-                for (int o = 0; o < 16; ++o) v[o] = 0u;
-            }
-            const int b = d / C, c = d - b * C;
-            const int l = kTcM * c + 32 * quarter + lane;
-            if (l >= H) continue;
-            float* out = out_part + (size_t)b * mb;
-            if ((cc & 1) == 0) {
+                    for (int o = 0; o < 32; ++o) v[o] = 0u;
+                }
+                const int b = d / C, c = d - b * C;
+                const int l = kTcM * c + 32 * quarter + lane;
+                if (l >= H) continue;
+                float* out = out_part + (size_t)b * mb;
 #pragma unroll
                 for (int o = 0; o < 16; ++o) out[9 * H + o * H + l] = mask2(o, l) ? __uint_as_float(v[o]) : 0.f;
-            } else {
+                store_dw1(out + l * 8, l, v + 16);
+                out[8 * H + l] = __uint_as_float(v[24]);
+            }
+        } else {
+            for (int cc = warp >> 2; cc < 2 * D; cc += per_quarter) {
+                const int d = cc >> 1;
+                uint32_t v[16];
+                if ((init >> d) & 1u) {   // uniform over the warp
+                    tc_ld16(tmem + ((uint32_t)(32 * quarter) << 16) + 16 * cc, v);
+                } else {
 #pragma unroll
-                for (int j = 0; j < 8; ++j) out[l * 8 + j] = mask1(l, j) ? __uint_as_float(v[j]) : 0.f;
-                out[8 * H + l] = __uint_as_float(v[8]);
+                    for (int o = 0; o < 16; ++o) v[o] = 0u;
+                }
+                const int b = d / C, c = d - b * C;
+                const int l = kTcM * c + 32 * quarter + lane;
+                if (l >= H) continue;
+                float* out = out_part + (size_t)b * mb;
+                if ((cc & 1) == 0) {
+#pragma unroll
+                    for (int o = 0; o < 16; ++o) out[9 * H + o * H + l] = mask2(o, l) ? __uint_as_float(v[o]) : 0.f;
+                } else {
+                    store_dw1(out + l * 8, l, v);
+                    out[8 * H + l] = __uint_as_float(v[8]);
+                }
             }
         }
     }
