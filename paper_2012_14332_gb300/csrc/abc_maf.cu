@@ -1312,6 +1312,30 @@ __device__ __forceinline__ float group_sum(const float* __restrict__ q, int nblk
     return a;
 }
 
+// the same for entries e and e + off together, with both entries' loads of a
+// chunk in flight at once (has0, has1: whether each entry exists)
+template <int G>
+__device__ __forceinline__ void group_sum2(const float* __restrict__ q, int off, int nblk, uint32_t stride, int grp,
+                                           bool has0, bool has1, float& a0, float& a1)
+{
+    a0 = 0.f;
+    a1 = 0.f;
+    for (int c0 = grp; c0 < nblk; c0 += G * kRedUnroll) {
+        float x[kRedUnroll], y[kRedUnroll];
+#pragma unroll
+        for (int k = 0; k < kRedUnroll; ++k) {
+            const int c = c0 + G * k;
+            x[k] = has0 && c < nblk ? q[(size_t)c * stride] : 0.f;
+            y[k] = has1 && c < nblk ? q[(size_t)c * stride + off] : 0.f;
+        }
+#pragma unroll
+        for (int k = 0; k < kRedUnroll; ++k) {
+            a0 += x[k];
+            a1 += y[k];
+        }
+    }
+}
+
 // entry e's total over the block's G groups (group 0's sum first), valid in
 // group 0's threads; every thread of the block calls it
 template <int G>
@@ -1431,12 +1455,14 @@ __device__ __forceinline__ void publish_param(uint32_t* __restrict__ pb, int H, 
 // A training step's Adam and publish in one launch: adam_kernel on the
 // gradient kernel's per-CTA partials, added here in the fixed tree of
 // group_sum; each updated parameter is published at once (publish_param). A
-// block updates 256 / G parameters of flow blockIdx.y; a flow without rows
+// block updates ROWS x 256 / G parameters of flow blockIdx.y (two rows when
+// one group holds every partial: the block then has half as many loads per
+// row to wait on, and a launch of 16 flows fits one wave); a flow without rows
 // this step keeps its parameters, moments and published words. The step t is
 // the gradient launch's ticket count over its CTA count (grad_kernel): the
 // counter stands at t grad_ctas after the gradient launch of step t - 1, so
 // no launch has to advance a step counter.
-template <int G>
+template <int G, int ROWS>
 __global__ void __launch_bounds__(256) adam_publish_kernel(float* __restrict__ params, const float* __restrict__ part,
                                                            int nblk, uint32_t part_stride,
                                                            const TrainSlot* __restrict__ slots, float* __restrict__ m,
@@ -1445,11 +1471,12 @@ __global__ void __launch_bounds__(256) adam_publish_kernel(float* __restrict__ p
                                                            int K, int H, const __grid_constant__ Layout L,
                                                            int64_t n_params, float lr, float b1, float b2, float eps)
 {
+    static_assert(ROWS == 1 || ROWS == 2, "one or two rows per block");
     constexpr int E = 256 / G;
-    __shared__ float gs[G][E];
+    __shared__ float gs[ROWS][G][E];
     __shared__ float w_s, c_s[2];
     const int f = blockIdx.y, e = threadIdx.x % E, q = threadIdx.x / E;
-    const int64_t p = (int64_t)blockIdx.x * E + e;
+    const int64_t p0 = (int64_t)blockIdx.x * ROWS * E + e;
     const int t_step = (int)(*ticket / grad_ctas);
     if (threadIdx.x == 32) adam_bias(t_step, b1, b2, c_s[0], c_s[1]);
     const bool has_rows = slots[f].n != 0;   // uniform over the block
@@ -1474,19 +1501,32 @@ __global__ void __launch_bounds__(256) adam_publish_kernel(float* __restrict__ p
         for (int off = 16; off > 0; off >>= 1) w += __shfl_xor_sync(kFull, w, off);
         if (threadIdx.x == 0) w_s = w;
     }
-    const float mine = has_rows && p < n_params ? group_sum<G>(base + p, nblk, part_stride, q) : 0.f;
-    const float g = block_groups_total<G>(gs, mine, q, e);
+    float g[ROWS];
+    if constexpr (ROWS == 1) {
+        const float mine = has_rows && p0 < n_params ? group_sum<G>(base + p0, nblk, part_stride, q) : 0.f;
+        g[0] = block_groups_total<G>(gs[0], mine, q, e);
+    } else {
+        float mine0, mine1;
+        group_sum2<G>(base + p0, E, nblk, part_stride, q, has_rows && p0 < n_params, has_rows && p0 + E < n_params,
+                      mine0, mine1);
+        g[0] = block_groups_total<G>(gs[0], mine0, q, e);
+        g[1] = block_groups_total<G>(gs[1], mine1, q, e);
+    }
     __syncthreads();
     const float W = w_s;
-    if (has_rows && q == 0 && p < n_params && W > 0.f) {
-        const int64_t i = (int64_t)f * n_params + p;
-        float pi = params[i], mi = m[i], vi = v[i];
-        adam_update(pi, mi, vi, __fdiv_rn(g, W), c_s[0], c_s[1], lr, b1, b2, eps);
-        params[i] = pi;
-        m[i] = mi;
-        v[i] = vi;
-        const int mb = master_block(H), b = (int)(p / mb);
-        publish_param(pub + ((size_t)f * K + b) * L.words, H, L, (int)(p - (int64_t)b * mb), pi);
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r) {
+        const int64_t p = p0 + r * E;
+        if (has_rows && q == 0 && p < n_params && W > 0.f) {
+            const int64_t i = (int64_t)f * n_params + p;
+            float pi = params[i], mi = m[i], vi = v[i];
+            adam_update(pi, mi, vi, __fdiv_rn(g[r], W), c_s[0], c_s[1], lr, b1, b2, eps);
+            params[i] = pi;
+            m[i] = mi;
+            v[i] = vi;
+            const int mb = master_block(H), b = (int)(p / mb);
+            publish_param(pub + ((size_t)f * K + b) * L.words, H, L, (int)(p - (int64_t)b * mb), pi);
+        }
     }
 }
 
@@ -1764,7 +1804,8 @@ unsigned* train_ticket(abc_maf f) { return reinterpret_cast<unsigned*>(f->d_step
 template <int G>
 void launch_adam_publish(abc_maf f, int nblk, float lr, cudaStream_t s)
 {
-    maf::adam_publish_kernel<G><<<dim3((unsigned)((f->n_params + 256 / G - 1) / (256 / G)), f->R), 256, 0, s>>>(
+    constexpr int ROWS = G == 1 ? 2 : 1, PER = ROWS * (256 / G);
+    maf::adam_publish_kernel<G, ROWS><<<dim3((unsigned)((f->n_params + PER - 1) / PER), f->R), 256, 0, s>>>(
         f->d_params, f->d_part, nblk, part_stride(f), f->d_slots, f->d_m, f->d_v, train_ticket(f),
         (uint32_t)nblk * (uint32_t)f->R, f->d_pub, f->K, f->H, maf::layout(f->H), f->n_params, lr, 0.9f, 0.999f,
         1e-8f);
