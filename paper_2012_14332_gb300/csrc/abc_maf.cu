@@ -1575,7 +1575,8 @@ struct abc_maf_s {
     int* d_step = nullptr;     // [0] the step of abc_maf_adam_step, [1] a training run's ticket counter
     maf::TrainSlot* d_slots = nullptr;   // [R] training data of each flow
     float* d_best = nullptr;   // [R][n_params] best parameters under validation (allocated on first use)
-    cudaGraphExec_t graph = nullptr;
+    cudaGraphExec_t graph = nullptr;        // one training step, captured
+    cudaGraphExec_t graph_multi = nullptr;  // kGraphSteps training steps, captured together
     // what the captured training step was built for
     int32_t g_batch = 0;
     float g_lr = 0.f;
@@ -1759,6 +1760,27 @@ GradForm grad_form(abc_maf f, uint64_t tiles)
     return g;
 }
 
+// training steps per replay of the multi-step graph (the validation interval
+// of a training run with early stopping)
+constexpr int kGraphSteps = 25;
+
+void drop_graphs(abc_maf_s* f)
+{
+    if (f->graph) cudaGraphExecDestroy(f->graph);
+    if (f->graph_multi) cudaGraphExecDestroy(f->graph_multi);
+    f->graph = nullptr;
+    f->graph_multi = nullptr;
+}
+
+// n captured training steps: whole multi-step replays, then single steps
+cudaError_t run_steps(abc_maf f, int32_t n, cudaStream_t s)
+{
+    cudaError_t e = cudaSuccess;
+    for (; n >= kGraphSteps && e == cudaSuccess; n -= kGraphSteps) e = cudaGraphLaunch(f->graph_multi, s);
+    for (; n > 0 && e == cudaSuccess; --n) e = cudaGraphLaunch(f->graph, s);
+    return e;
+}
+
 // the partial buffer for any gradient over at most `tiles` tiles per flow:
 // sized for the paired 4-warp form's CTAs (two tiles each), never fewer than
 // the other forms' and growing with the tiles; allocates, so it is called
@@ -1769,10 +1791,7 @@ cudaError_t ensure_part(abc_maf f, uint64_t tiles)
     const size_t need = (size_t)f->R * grid * part_stride(f);
     if (need <= f->part_floats) return cudaSuccess;
     // a captured training step holds the old buffer's address
-    if (f->graph) {
-        cudaGraphExecDestroy(f->graph);
-        f->graph = nullptr;
-    }
+    drop_graphs(f);
     cudaFree(f->d_part);
     f->d_part = nullptr;
     f->part_floats = 0;
@@ -1979,10 +1998,7 @@ abc_status abc_maf_test_hold_products(abc_maf f, int32_t hold)
     abc_status st;
     if ((st = check(f)) != ABC_OK) return st;
     f->hold = hold != 0;
-    if (f->graph) {
-        cudaGraphExecDestroy(f->graph);
-        f->graph = nullptr;
-    }
+    drop_graphs(f);
     return plan_ok();
 }
 
@@ -2178,24 +2194,29 @@ abc_status abc_maf_train_flows(abc_maf f, const float* const* theta, const float
         // for (batch, lr, seed, stream) serves every data set
         const bool same = f->graph && f->g_batch == batch && f->g_lr == lr && f->g_seed == seed && f->g_stream == s;
         if (!same) {
-            if (f->graph) {
-                cudaGraphExecDestroy(f->graph);
-                f->graph = nullptr;
-            }
+            drop_graphs(f);
             const ModelParams p = plan_make_params(nullptr, 1, 1, seed, 0, nullptr);
-            cudaGraph_t gph = nullptr;
-            MAF_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
-            cudaError_t e = launch_train_step(f, (uint32_t)batch, p, lr, s);
-            cudaError_t ec = cudaStreamEndCapture(s, &gph);
-            if (e != cudaSuccess || ec != cudaSuccess) {
-                if (gph) cudaGraphDestroy(gph);
-                return plan_cuda_fail(e != cudaSuccess ? e : ec, "capturing the training step");
-            }
-            e = cudaGraphInstantiate(&f->graph, gph, 0);
-            cudaGraphDestroy(gph);
-            if (e != cudaSuccess) {
-                f->graph = nullptr;
-                return plan_cuda_fail(e, "cudaGraphInstantiate(training step)");
+            // one step, and kGraphSteps steps in one graph (the steps take
+            // their step number from the ticket counter, so every replay of
+            // either continues where the last one stopped)
+            for (int which = 0; which < 2; ++which) {
+                cudaGraph_t gph = nullptr;
+                MAF_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
+                cudaError_t e = cudaSuccess;
+                for (int i = 0; i < (which ? kGraphSteps : 1) && e == cudaSuccess; ++i)
+                    e = launch_train_step(f, (uint32_t)batch, p, lr, s);
+                cudaError_t ec = cudaStreamEndCapture(s, &gph);
+                if (e != cudaSuccess || ec != cudaSuccess) {
+                    if (gph) cudaGraphDestroy(gph);
+                    drop_graphs(f);
+                    return plan_cuda_fail(e != cudaSuccess ? e : ec, "capturing the training step");
+                }
+                e = cudaGraphInstantiate(which ? &f->graph_multi : &f->graph, gph, 0);
+                cudaGraphDestroy(gph);
+                if (e != cudaSuccess) {
+                    drop_graphs(f);
+                    return plan_cuda_fail(e, "cudaGraphInstantiate(training step)");
+                }
             }
             f->g_batch = batch;
             f->g_lr = lr;
@@ -2207,7 +2228,7 @@ abc_status abc_maf_train_flows(abc_maf f, const float* const* theta, const float
         // early stopping: every kCheck steps the validation loss of each flow;
         // a flow keeps its best parameters and stops after kPatience checks
         // without improvement
-        constexpr int kCheck = 25, kPatience = 3;
+        constexpr int kCheck = kGraphSteps, kPatience = 3;
         const size_t npb = sizeof(float) * f->n_params;
         if (!f->d_best) MAF_TRY(cudaMalloc(&f->d_best, npb * R), "cudaMalloc(best parameters)");
         uint64_t max_va = 0;
@@ -2246,7 +2267,7 @@ abc_status abc_maf_train_flows(abc_maf f, const float* const* theta, const float
             for (int r = 0; r < R; ++r) active = active || n_tr[r] > 0;
             if (!active) break;
             const int32_t k = n_steps - done < kCheck ? n_steps - done : kCheck;
-            for (int32_t i = 0; i < k; ++i) MAF_TRY(cudaGraphLaunch(f->graph, s), "cudaGraphLaunch");
+            MAF_TRY(run_steps(f, k, s), "cudaGraphLaunch");
             done += k;
             if ((st = val_losses()) != ABC_OK) return st;
         }
@@ -2269,7 +2290,7 @@ abc_status abc_maf_train_flows(abc_maf f, const float* const* theta, const float
     if (n_steps > 0) {
         // each step publishes every parameter it updates, the sampler's
         // operands included
-        for (int32_t i = 0; i < n_steps; ++i) MAF_TRY(cudaGraphLaunch(f->graph, s), "cudaGraphLaunch");
+        MAF_TRY(run_steps(f, n_steps, s), "cudaGraphLaunch");
     }
     if (loss_out) {
         MAF_TRY(full_gradient(f, max_n, s), "flow loss");
@@ -2314,7 +2335,7 @@ abc_status abc_maf_train(abc_maf f, uint64_t n, const float* theta, const float*
 abc_status abc_maf_destroy(abc_maf f)
 {
     if (!f) return plan_fail(ABC_ERR_INVALID_ARG, "flow is NULL");
-    if (f->graph) cudaGraphExecDestroy(f->graph);
+    drop_graphs(f);
     cudaFree(f->d_params);
     cudaFree(f->d_m);
     cudaFree(f->d_v);
