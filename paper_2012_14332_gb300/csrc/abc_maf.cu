@@ -1574,6 +1574,8 @@ struct abc_maf_s {
     int hold = 0;              // testing: the gradient kernel issues no products
     int* d_step = nullptr;     // [0] the step of abc_maf_adam_step, [1] a training run's ticket counter
     maf::TrainSlot* d_slots = nullptr;   // [R] training data of each flow
+    maf::TrainSlot* d_slots_val = nullptr;   // [R] validation data of each flow (early stopping)
+    float* h_io = nullptr;   // pinned host: the 2 R loss sums, then the error word
     float* d_best = nullptr;   // [R][n_params] best parameters under validation (allocated on first use)
     cudaGraphExec_t graph = nullptr;        // one training step, captured
     cudaGraphExec_t graph_multi = nullptr;  // kGraphSteps training steps, captured together
@@ -1810,11 +1812,12 @@ int red_groups(int nblk)
 }
 
 template <int G>
-void launch_reduce(abc_maf f, bool drawn, uint32_t batch, int nblk, uint32_t stride, cudaStream_t s)
+void launch_reduce(abc_maf f, const maf::TrainSlot* slots, bool drawn, uint32_t batch, int nblk, uint32_t stride,
+                   cudaStream_t s)
 {
     const int np = (int)f->n_params;
     maf::grad_reduce_kernel<G><<<dim3((np + 2 + 256 / G - 1) / (256 / G), f->R), 256, 0, s>>>(
-        f->d_part, nblk, stride, np, f->d_slots, drawn ? 1 : 0, batch, f->d_grad, f->d_sums);
+        f->d_part, nblk, stride, np, slots, drawn ? 1 : 0, batch, f->d_grad, f->d_sums);
 }
 
 // a training run's ticket counter (grad_kernel), zeroed when the run starts
@@ -1835,8 +1838,8 @@ void launch_adam_publish(abc_maf f, int nblk, float lr, cudaStream_t s)
 // largest slot). The kernel writes per-CTA partials, the reduction adds them
 // in a fixed tree into d_grad and d_sums.
 template <int K, int W, bool PAIR>
-cudaError_t launch_grad_w(abc_maf f, unsigned* ticket, const ModelParams& rp, uint32_t batch, int grid, bool reduce,
-                          cudaStream_t s)
+cudaError_t launch_grad_w(abc_maf f, const maf::TrainSlot* slots, unsigned* ticket, const ModelParams& rp,
+                          uint32_t batch, int grid, bool reduce, cudaStream_t s)
 {
     const size_t smem = grad_smem(f, W);
     cudaError_t e = allow_smem(maf::grad_kernel<K, W, PAIR>, smem);
@@ -1845,15 +1848,15 @@ cudaError_t launch_grad_w(abc_maf f, unsigned* ticket, const ModelParams& rp, ui
     if ((size_t)f->R * grid * stride > f->part_floats) return cudaErrorInvalidValue;   // ensure_part first
     if (PAIR && (f->H + maf::kTcM - 1) / maf::kTcM != 2) return cudaErrorInvalidValue;
     maf::grad_kernel<K, W, PAIR><<<dim3(grid, f->R), (W + 1) * 32, smem, s>>>(
-        f->d_pub, f->H, f->box, f->d_slots, ticket, (uint32_t)grid * (uint32_t)f->R, rp, batch, f->d_part, stride,
+        f->d_pub, f->H, f->box, slots, ticket, (uint32_t)grid * (uint32_t)f->R, rp, batch, f->d_part, stride,
         f->d_err, f->hold);
     e = cudaGetLastError();
     if (e != cudaSuccess || !reduce) return e;
     switch (red_groups(grid)) {
-    case 1: launch_reduce<1>(f, ticket != nullptr, batch, grid, stride, s); break;
-    case 2: launch_reduce<2>(f, ticket != nullptr, batch, grid, stride, s); break;
-    case 4: launch_reduce<4>(f, ticket != nullptr, batch, grid, stride, s); break;
-    default: launch_reduce<8>(f, ticket != nullptr, batch, grid, stride, s); break;
+    case 1: launch_reduce<1>(f, slots, ticket != nullptr, batch, grid, stride, s); break;
+    case 2: launch_reduce<2>(f, slots, ticket != nullptr, batch, grid, stride, s); break;
+    case 4: launch_reduce<4>(f, slots, ticket != nullptr, batch, grid, stride, s); break;
+    default: launch_reduce<8>(f, slots, ticket != nullptr, batch, grid, stride, s); break;
     }
     return cudaGetLastError();
 }
@@ -1861,15 +1864,15 @@ cudaError_t launch_grad_w(abc_maf f, unsigned* ticket, const ModelParams& rp, ui
 // reduce: add the partials into d_grad and d_sums (a training step's Adam adds
 // them itself instead)
 template <int K>
-cudaError_t launch_grad(abc_maf f, unsigned* ticket, const ModelParams& rp, uint32_t batch, uint64_t max_n, bool reduce,
-                        cudaStream_t s)
+cudaError_t launch_grad(abc_maf f, const maf::TrainSlot* slots, unsigned* ticket, const ModelParams& rp, uint32_t batch,
+                        uint64_t max_n, bool reduce, cudaStream_t s)
 {
     const uint64_t tiles = ((ticket ? batch : max_n) + 15) / 16;
     const GradForm g = grad_form(f, tiles);
     if (g.W == maf::kGradWarpsWide)
-        return launch_grad_w<K, maf::kGradWarpsWide, false>(f, ticket, rp, batch, g.grid, reduce, s);
-    if (g.pair) return launch_grad_w<K, maf::kGradWarpsNarrow, true>(f, ticket, rp, batch, g.grid, reduce, s);
-    return launch_grad_w<K, maf::kGradWarpsNarrow, false>(f, ticket, rp, batch, g.grid, reduce, s);
+        return launch_grad_w<K, maf::kGradWarpsWide, false>(f, slots, ticket, rp, batch, g.grid, reduce, s);
+    if (g.pair) return launch_grad_w<K, maf::kGradWarpsNarrow, true>(f, slots, ticket, rp, batch, g.grid, reduce, s);
+    return launch_grad_w<K, maf::kGradWarpsNarrow, false>(f, slots, ticket, rp, batch, g.grid, reduce, s);
 }
 
 #define MAF_DISPATCH(fn, ...)                      \
@@ -1882,7 +1885,7 @@ cudaError_t launch_grad(abc_maf f, unsigned* ticket, const ModelParams& rp, uint
 // The copy is from pageable memory, which the runtime has consumed when the
 // call returns, so tables can be uploaded back to back without a wait.
 cudaError_t upload_slots(abc_maf f, const float* const* theta, const float* const* w, const uint64_t* n,
-                         cudaStream_t s)
+                         cudaStream_t s, maf::TrainSlot* dst = nullptr)
 {
     std::vector<maf::TrainSlot> h((size_t)f->R);
     for (int r = 0; r < f->R; ++r) {
@@ -1890,14 +1893,16 @@ cudaError_t upload_slots(abc_maf f, const float* const* theta, const float* cons
         h[r].w = n[r] && w ? w[r] : nullptr;
         h[r].n = n[r];
     }
-    return cudaMemcpyAsync(f->d_slots, h.data(), sizeof(maf::TrainSlot) * f->R, cudaMemcpyHostToDevice, s);
+    return cudaMemcpyAsync(dst ? dst : f->d_slots, h.data(), sizeof(maf::TrainSlot) * f->R, cudaMemcpyHostToDevice,
+                           s);
 }
 
 // full-data gradients of the flows described by the slot table
-cudaError_t full_gradient(abc_maf f, uint64_t max_n, cudaStream_t s)
+cudaError_t full_gradient(abc_maf f, uint64_t max_n, cudaStream_t s, const maf::TrainSlot* slots = nullptr)
 {
     cudaError_t e = ensure_part(f, (max_n + 15) / 16);
-    if (e == cudaSuccess) e = MAF_DISPATCH(launch_grad, f, nullptr, ModelParams{}, 0u, max_n, true, s);
+    if (e == cudaSuccess)
+        e = MAF_DISPATCH(launch_grad, f, slots ? slots : f->d_slots, nullptr, ModelParams{}, 0u, max_n, true, s);
     return e;
 }
 
@@ -1915,7 +1920,7 @@ cudaError_t launch_adam(abc_maf f, float lr, float b1, float b2, float eps, cuda
 // publishes every updated parameter and advances the step
 cudaError_t launch_train_step(abc_maf f, uint32_t batch, const ModelParams& p, float lr, cudaStream_t s)
 {
-    cudaError_t e = MAF_DISPATCH(launch_grad, f, train_ticket(f), p, batch, 0, false, s);
+    cudaError_t e = MAF_DISPATCH(launch_grad, f, f->d_slots, train_ticket(f), p, batch, 0, false, s);
     if (e != cudaSuccess) return e;
     const int grid = grad_form(f, ((uint64_t)batch + 15) / 16).grid;
     switch (red_groups(grid)) {
@@ -1972,6 +1977,8 @@ abc_status abc_maf_create_multi(int32_t n_flows, int32_t n_blocks, int32_t hidde
         (e = cudaMalloc(&f->d_sums, 2 * sizeof(float) * f->R)) != cudaSuccess ||
         (e = cudaMalloc(&f->d_step, 2 * sizeof(int))) != cudaSuccess ||
         (e = cudaMalloc(&f->d_slots, sizeof(maf::TrainSlot) * f->R)) != cudaSuccess ||
+        (e = cudaMalloc(&f->d_slots_val, sizeof(maf::TrainSlot) * f->R)) != cudaSuccess ||
+        (e = cudaMallocHost(&f->h_io, sizeof(float) * (2 * (size_t)f->R + 4))) != cudaSuccess ||
         (e = cudaMalloc(&f->d_err, sizeof(int))) != cudaSuccess)
         return fail_free(plan_cuda_fail(e, "cudaMalloc(flow)"));
     if ((e = cudaMemset(f->d_params, 0, np)) != cudaSuccess || (e = cudaMemset(f->d_m, 0, np)) != cudaSuccess ||
@@ -2233,18 +2240,26 @@ abc_status abc_maf_train_flows(abc_maf f, const float* const* theta, const float
         if (!f->d_best) MAF_TRY(cudaMalloc(&f->d_best, npb * R), "cudaMalloc(best parameters)");
         uint64_t max_va = 0;
         for (int r = 0; r < R; ++r) max_va = n_va[r] > max_va ? n_va[r] : max_va;
-        std::vector<float> sums(2 * (size_t)R), best((size_t)R, INFINITY);
+        std::vector<float> best((size_t)R, INFINITY);
         std::vector<int> bad((size_t)R, 0);
+        // the validation sets have their own slot table, uploaded once; each
+        // check reads the loss sums and the error word back in one synchronisation
+        MAF_TRY(upload_slots(f, th_va.data(), w_va.data(), n_va.data(), s, f->d_slots_val), "cudaMemcpyAsync(slots)");
+        float* sums = f->h_io;
+        int* err_h = reinterpret_cast<int*>(f->h_io + 2 * (size_t)R);
         auto val_losses = [&]() -> abc_status {
-            MAF_TRY(upload_slots(f, th_va.data(), w_va.data(), n_va.data(), s), "cudaMemcpyAsync(slots)");
-            MAF_TRY(full_gradient(f, max_va, s), "validation loss");
-            MAF_TRY(cudaMemcpyAsync(sums.data(), f->d_sums, sizeof(float) * sums.size(), cudaMemcpyDeviceToHost, s),
+            MAF_TRY(full_gradient(f, max_va, s, f->d_slots_val), "validation loss");
+            MAF_TRY(cudaMemcpyAsync(sums, f->d_sums, sizeof(float) * 2 * (size_t)R, cudaMemcpyDeviceToHost, s),
                     "cudaMemcpyAsync(sums)");
+            MAF_TRY(cudaMemcpyAsync(err_h, f->d_err, sizeof(int), cudaMemcpyDeviceToHost, s),
+                    "cudaMemcpyAsync(error word)");
             MAF_TRY(cudaStreamSynchronize(s), "cudaStreamSynchronize");
-            {
-                const abc_status es = take_err(f);
-                if (es != ABC_OK) return es;
+            if (*err_h) {
+                MAF_TRY(cudaMemset(f->d_err, 0, sizeof(int)), "cudaMemset(error word)");
+                return plan_fail(ABC_ERR_TIMEOUT,
+                                 "a flow gradient kernel's wait for its tensor-core products ran out of time");
             }
+            bool stopped = false;
             for (int r = 0; r < R; ++r) {
                 if (n_va[r] == 0 || sums[2 * r + 1] <= 0.f) continue;
                 const float vl = sums[2 * r] / sums[2 * r + 1];
@@ -2256,9 +2271,11 @@ abc_status abc_maf_train_flows(abc_maf f, const float* const* theta, const float
                             "cudaMemcpyAsync(best parameters)");
                 } else if (++bad[r] >= kPatience && n_tr[r] > 0) {
                     n_tr[r] = 0;   // this flow stops training
+                    stopped = true;
                 }
             }
-            MAF_TRY(upload_slots(f, th_tr.data(), w_tr.data(), n_tr.data(), s), "cudaMemcpyAsync(slots)");
+            if (stopped)
+                MAF_TRY(upload_slots(f, th_tr.data(), w_tr.data(), n_tr.data(), s), "cudaMemcpyAsync(slots)");
             return ABC_OK;
         };
         if ((st = val_losses()) != ABC_OK) return st;
@@ -2345,6 +2362,8 @@ abc_status abc_maf_destroy(abc_maf f)
     cudaFree(f->d_sums);
     cudaFree(f->d_step);
     cudaFree(f->d_slots);
+    cudaFree(f->d_slots_val);
+    if (f->h_io) cudaFreeHost(f->h_io);
     cudaFree(f->d_err);
     cudaFree(f->d_best);
     delete f;
