@@ -1355,12 +1355,13 @@ __device__ __forceinline__ float block_groups_total(float (*gs)[256 / G], float 
 }
 
 // The flows' gradients and loss sums from the CTAs' partials, in the fixed
-// tree above: grad[f][p] (p < np), then the two loss sums. A flow without
-// rows gets zeros (its CTAs returned before writing). drawn: the gradient was
-// over `batch` drawn rows per flow, else over all of each flow's points.
+// tree above: grad[f][p] (p < np), then the two loss sums, for the entries
+// from p_first on (np: the loss sums alone). A flow without rows gets zeros
+// (its CTAs returned before writing). drawn: the gradient was over `batch`
+// drawn rows per flow, else over all of each flow's points.
 template <int G>
 __global__ void __launch_bounds__(256) grad_reduce_kernel(const float* __restrict__ part, int nblk,
-                                                          uint32_t part_stride, int np,
+                                                          uint32_t part_stride, int np, int p_first,
                                                           const TrainSlot* __restrict__ slots,
                                                           int drawn, uint32_t batch, float* __restrict__ grad,
                                                           float* __restrict__ sums)
@@ -1368,7 +1369,7 @@ __global__ void __launch_bounds__(256) grad_reduce_kernel(const float* __restric
     constexpr int E = 256 / G;
     __shared__ float gs[G][E];
     const int f = blockIdx.y, e = threadIdx.x % E, q = threadIdx.x / E;
-    const int p = blockIdx.x * E + e;
+    const int p = p_first + blockIdx.x * E + e;
     const uint64_t n_rows = drawn ? (slots[f].n ? batch : 0) : slots[f].n;
     const float mine =
         n_rows && p < np + 2 ? group_sum<G>(part + (size_t)f * nblk * part_stride + p, nblk, part_stride, q) : 0.f;
@@ -1813,11 +1814,11 @@ int red_groups(int nblk)
 
 template <int G>
 void launch_reduce(abc_maf f, const maf::TrainSlot* slots, bool drawn, uint32_t batch, int nblk, uint32_t stride,
-                   cudaStream_t s)
+                   bool sums_only, cudaStream_t s)
 {
-    const int np = (int)f->n_params;
-    maf::grad_reduce_kernel<G><<<dim3((np + 2 + 256 / G - 1) / (256 / G), f->R), 256, 0, s>>>(
-        f->d_part, nblk, stride, np, slots, drawn ? 1 : 0, batch, f->d_grad, f->d_sums);
+    const int np = (int)f->n_params, p_first = sums_only ? np : 0;
+    maf::grad_reduce_kernel<G><<<dim3((np + 2 - p_first + 256 / G - 1) / (256 / G), f->R), 256, 0, s>>>(
+        f->d_part, nblk, stride, np, p_first, slots, drawn ? 1 : 0, batch, f->d_grad, f->d_sums);
 }
 
 // a training run's ticket counter (grad_kernel), zeroed when the run starts
@@ -1839,7 +1840,7 @@ void launch_adam_publish(abc_maf f, int nblk, float lr, cudaStream_t s)
 // in a fixed tree into d_grad and d_sums.
 template <int K, int W, bool PAIR>
 cudaError_t launch_grad_w(abc_maf f, const maf::TrainSlot* slots, unsigned* ticket, const ModelParams& rp,
-                          uint32_t batch, int grid, bool reduce, cudaStream_t s)
+                          uint32_t batch, int grid, bool reduce, bool sums_only, cudaStream_t s)
 {
     const size_t smem = grad_smem(f, W);
     cudaError_t e = allow_smem(maf::grad_kernel<K, W, PAIR>, smem);
@@ -1853,10 +1854,10 @@ cudaError_t launch_grad_w(abc_maf f, const maf::TrainSlot* slots, unsigned* tick
     e = cudaGetLastError();
     if (e != cudaSuccess || !reduce) return e;
     switch (red_groups(grid)) {
-    case 1: launch_reduce<1>(f, slots, ticket != nullptr, batch, grid, stride, s); break;
-    case 2: launch_reduce<2>(f, slots, ticket != nullptr, batch, grid, stride, s); break;
-    case 4: launch_reduce<4>(f, slots, ticket != nullptr, batch, grid, stride, s); break;
-    default: launch_reduce<8>(f, slots, ticket != nullptr, batch, grid, stride, s); break;
+    case 1: launch_reduce<1>(f, slots, ticket != nullptr, batch, grid, stride, sums_only, s); break;
+    case 2: launch_reduce<2>(f, slots, ticket != nullptr, batch, grid, stride, sums_only, s); break;
+    case 4: launch_reduce<4>(f, slots, ticket != nullptr, batch, grid, stride, sums_only, s); break;
+    default: launch_reduce<8>(f, slots, ticket != nullptr, batch, grid, stride, sums_only, s); break;
     }
     return cudaGetLastError();
 }
@@ -1865,14 +1866,14 @@ cudaError_t launch_grad_w(abc_maf f, const maf::TrainSlot* slots, unsigned* tick
 // them itself instead)
 template <int K>
 cudaError_t launch_grad(abc_maf f, const maf::TrainSlot* slots, unsigned* ticket, const ModelParams& rp, uint32_t batch,
-                        uint64_t max_n, bool reduce, cudaStream_t s)
+                        uint64_t max_n, bool reduce, bool sums_only, cudaStream_t s)
 {
     const uint64_t tiles = ((ticket ? batch : max_n) + 15) / 16;
     const GradForm g = grad_form(f, tiles);
     if (g.W == maf::kGradWarpsWide)
-        return launch_grad_w<K, maf::kGradWarpsWide, false>(f, slots, ticket, rp, batch, g.grid, reduce, s);
-    if (g.pair) return launch_grad_w<K, maf::kGradWarpsNarrow, true>(f, slots, ticket, rp, batch, g.grid, reduce, s);
-    return launch_grad_w<K, maf::kGradWarpsNarrow, false>(f, slots, ticket, rp, batch, g.grid, reduce, s);
+        return launch_grad_w<K, maf::kGradWarpsWide, false>(f, slots, ticket, rp, batch, g.grid, reduce, sums_only, s);
+    if (g.pair) return launch_grad_w<K, maf::kGradWarpsNarrow, true>(f, slots, ticket, rp, batch, g.grid, reduce, sums_only, s);
+    return launch_grad_w<K, maf::kGradWarpsNarrow, false>(f, slots, ticket, rp, batch, g.grid, reduce, sums_only, s);
 }
 
 #define MAF_DISPATCH(fn, ...)                      \
@@ -1898,11 +1899,15 @@ cudaError_t upload_slots(abc_maf f, const float* const* theta, const float* cons
 }
 
 // full-data gradients of the flows described by the slot table
-cudaError_t full_gradient(abc_maf f, uint64_t max_n, cudaStream_t s, const maf::TrainSlot* slots = nullptr)
+// full-data gradients (sums_only: the loss sums alone reduced, d_grad left as
+// it was)
+cudaError_t full_gradient(abc_maf f, uint64_t max_n, cudaStream_t s, const maf::TrainSlot* slots = nullptr,
+                          bool sums_only = false)
 {
     cudaError_t e = ensure_part(f, (max_n + 15) / 16);
     if (e == cudaSuccess)
-        e = MAF_DISPATCH(launch_grad, f, slots ? slots : f->d_slots, nullptr, ModelParams{}, 0u, max_n, true, s);
+        e = MAF_DISPATCH(launch_grad, f, slots ? slots : f->d_slots, nullptr, ModelParams{}, 0u, max_n, true, sums_only,
+                         s);
     return e;
 }
 
@@ -1920,7 +1925,7 @@ cudaError_t launch_adam(abc_maf f, float lr, float b1, float b2, float eps, cuda
 // publishes every updated parameter and advances the step
 cudaError_t launch_train_step(abc_maf f, uint32_t batch, const ModelParams& p, float lr, cudaStream_t s)
 {
-    cudaError_t e = MAF_DISPATCH(launch_grad, f, f->d_slots, train_ticket(f), p, batch, 0, false, s);
+    cudaError_t e = MAF_DISPATCH(launch_grad, f, f->d_slots, train_ticket(f), p, batch, 0, false, false, s);
     if (e != cudaSuccess) return e;
     const int grid = grad_form(f, ((uint64_t)batch + 15) / 16).grid;
     switch (red_groups(grid)) {
@@ -2248,7 +2253,7 @@ abc_status abc_maf_train_flows(abc_maf f, const float* const* theta, const float
         float* sums = f->h_io;
         int* err_h = reinterpret_cast<int*>(f->h_io + 2 * (size_t)R);
         auto val_losses = [&]() -> abc_status {
-            MAF_TRY(full_gradient(f, max_va, s, f->d_slots_val), "validation loss");
+            MAF_TRY(full_gradient(f, max_va, s, f->d_slots_val, true), "validation loss");
             MAF_TRY(cudaMemcpyAsync(sums, f->d_sums, sizeof(float) * 2 * (size_t)R, cudaMemcpyDeviceToHost, s),
                     "cudaMemcpyAsync(sums)");
             MAF_TRY(cudaMemcpyAsync(err_h, f->d_err, sizeof(int), cudaMemcpyDeviceToHost, s),
