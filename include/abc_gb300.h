@@ -318,7 +318,9 @@ abc_status abc_plan_copy_results(abc_plan plan, int32_t region, float* theta_dst
 abc_status abc_plan_set_region(abc_plan plan, int32_t region, const float* theta_in, uint64_t first_index);
 
 /* Use one of the compiled launch shapes (as abc_plan_tune reports them; ms is
- * ignored) for the following runs, without tuning. Returns ABC_ERR_INVALID_ARG
+ * ignored) for the following runs, without tuning. A new plan starts with
+ * {256 threads, 2 day pairs, lean} in ABC_FAST and {256, 1, standard} in
+ * ABC_EXACT. Returns ABC_ERR_INVALID_ARG
  * for a shape the library is not compiled for, or a lean shape in exact mode.
  * Every shape gives the same accepted samples and day counts. As for
  * abc_plan_set_region, no run of the plan may be in flight. */

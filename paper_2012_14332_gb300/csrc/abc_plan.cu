@@ -184,6 +184,10 @@ abc_status abc_plan_create(const abc_prior_box* prior, const abc_region* regions
     abc_plan_s* pl = new abc_plan_s();
     PLAN_TRY(cudaGetDevice(&pl->device), "cudaGetDevice");
     pl->fast = mode == ABC_FAST;
+    // until tuned: in fast mode the shape the autotuner chose on the three-
+    // and sixteen-region workloads (the lean form, two day pairs per
+    // iteration); the standard one-pair form in exact mode
+    if (pl->fast) pl->shape = abcgb::BatchShape{256, 2, 0, 1};
     pl->p = abcgb::plan_make_params(prior, 1, 1, seed, 0, nullptr);
     pl->n_regions = n_regions;
     pl->total_chunks = chunks;
