@@ -129,28 +129,33 @@ __global__ void weight_kernel(const float* __restrict__ lw, uint64_t m, WeightSc
     }
 }
 
-// sum v and sum v^2 from the blocks' sums in block order (one block of 256):
-// thread t adds blocks t, t + 256, ... in turn, thread 0 adds the threads' sums
-// in turn, so the sums are the same in every run
-__global__ void weight_sums_kernel(const double* __restrict__ block_sums, unsigned nblk, WeightScratch* ws)
+// sum v and sum v^2 from the blocks' sums (one block of 256): thread t adds
+// blocks t, t + 256, ... in turn, then the threads' sums meet in a fixed
+// pairwise tree (t += t + 128, then t + 64, ...), so the sums are the same in
+// every run. (Thread 0 adding the 256 sums in turn took about 20 us: a chain of
+// 512 dependent double additions.)
+__global__ void __launch_bounds__(256) weight_sums_kernel(const double* __restrict__ block_sums, unsigned nblk,
+                                                          WeightScratch* ws)
 {
     __shared__ double part[2][256];
     double a = 0.0, b = 0.0;
-    for (unsigned k = threadIdx.x; k < nblk; k += blockDim.x) {
+    for (unsigned k = threadIdx.x; k < nblk; k += 256) {
         a += block_sums[2 * k];
         b += block_sums[2 * k + 1];
     }
     part[0][threadIdx.x] = a;
     part[1][threadIdx.x] = b;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double sa = 0.0, sb = 0.0;
-        for (int t = 0; t < (int)blockDim.x; ++t) {
-            sa += part[0][t];
-            sb += part[1][t];
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) {
+            part[0][threadIdx.x] += part[0][threadIdx.x + w];
+            part[1][threadIdx.x] += part[1][threadIdx.x + w];
         }
-        ws->sums[0] = sa;
-        ws->sums[1] = sb;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        ws->sums[0] = part[0][0];
+        ws->sums[1] = part[1][0];
     }
 }
 
