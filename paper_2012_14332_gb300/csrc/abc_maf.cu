@@ -1502,6 +1502,17 @@ __global__ void __launch_bounds__(256) adam_publish_kernel(float* __restrict__ p
         for (int off = 16; off > 0; off >>= 1) w += __shfl_xor_sync(kFull, w, off);
         if (threadIdx.x == 0) w_s = w;
     }
+    // the parameters and moments this thread updates, loaded with the
+    // partials (one round trip for both)
+    float pi[ROWS], mi[ROWS], vi[ROWS];
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r) {
+        const int64_t p = p0 + r * E, i = (int64_t)f * n_params + p;
+        const bool mine = has_rows && q == 0 && p < n_params;
+        pi[r] = mine ? params[i] : 0.f;
+        mi[r] = mine ? m[i] : 0.f;
+        vi[r] = mine ? v[i] : 0.f;
+    }
     float g[ROWS];
     if constexpr (ROWS == 1) {
         const float mine = has_rows && p0 < n_params ? group_sum<G>(base + p0, nblk, part_stride, q) : 0.f;
@@ -1520,13 +1531,12 @@ __global__ void __launch_bounds__(256) adam_publish_kernel(float* __restrict__ p
         const int64_t p = p0 + r * E;
         if (has_rows && q == 0 && p < n_params && W > 0.f) {
             const int64_t i = (int64_t)f * n_params + p;
-            float pi = params[i], mi = m[i], vi = v[i];
-            adam_update(pi, mi, vi, __fdiv_rn(g[r], W), c_s[0], c_s[1], lr, b1, b2, eps);
-            params[i] = pi;
-            m[i] = mi;
-            v[i] = vi;
+            adam_update(pi[r], mi[r], vi[r], __fdiv_rn(g[r], W), c_s[0], c_s[1], lr, b1, b2, eps);
+            params[i] = pi[r];
+            m[i] = mi[r];
+            v[i] = vi[r];
             const int mb = master_block(H), b = (int)(p / mb);
-            publish_param(pub + ((size_t)f * K + b) * L.words, H, L, (int)(p - (int64_t)b * mb), pi);
+            publish_param(pub + ((size_t)f * K + b) * L.words, H, L, (int)(p - (int64_t)b * mb), pi[r]);
         }
     }
 }

@@ -471,3 +471,33 @@ abc_status abc_plan_destroy(abc_plan plan)
 }
 
 }  // extern "C"
+
+namespace abcgb {
+
+// Every region's results of the last run at once: what abc_plan_results gives
+// for each region, read with one copy and one synchronisation of s. The
+// arrays hold n_regions entries each.
+abc_status plan_results_all(abc_plan plan, uint64_t* n_accepted, uint64_t* simulated_days, float** theta_out,
+                            double** dist_out, uint64_t** idx_out, void* cuda_stream)
+{
+    abc_status st;
+    if ((st = check_plan(plan)) != ABC_OK) return st;
+    const int32_t R = plan->n_regions;
+    std::vector<unsigned long long> c(2 * (size_t)R);
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    PLAN_TRY(cudaMemcpyAsync(c.data(), plan->d_counters, sizeof(unsigned long long) * c.size(), cudaMemcpyDeviceToHost,
+                             s),
+             "cudaMemcpyAsync(counters)");
+    PLAN_TRY(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+    for (int32_t g = 0; g < R; ++g) {
+        const abcgb::RegionDev& Rg = plan->regions[g];
+        n_accepted[g] = c[2 * (size_t)g];
+        simulated_days[g] = c[2 * (size_t)g + 1];
+        theta_out[g] = Rg.theta_out;
+        dist_out[g] = Rg.dist_out;
+        idx_out[g] = Rg.idx_out;
+    }
+    return plan_ok();
+}
+
+}  // namespace abcgb

@@ -21,6 +21,8 @@ abc_status plan_ok();
 bool plan_check_prior(const abc_prior_box* prior, abc_status* st);
 ModelParams plan_make_params(const abc_prior_box* prior, int32_t T, int64_t N_pop, uint64_t seed, uint32_t stream,
                              const int32_t* ard0);
+abc_status plan_results_all(abc_plan plan, uint64_t* n_accepted, uint64_t* simulated_days, float** theta_out,
+                            double** dist_out, uint64_t** idx_out, void* cuda_stream);
 }  // namespace abcgb
 
 namespace {
@@ -330,12 +332,13 @@ static abc_status shuffled_training_set(const float* theta, const W* w, uint64_t
 // Weights of a round's m accepted samples (logq: the round's proposal log
 // densities, NULL for prior draws): float training weights v_j into w_train,
 // optionally v_j in double into w_exact and the unnormalised weights of the
-// first pool_k samples into pool; *sum_v, *sum_v2 for the ESS. Synchronizes s.
-// d_block_sums: 2 doubles per 256 samples (the sums are added in block order).
-static abc_status round_weights(const float* logq, const uint64_t* idx, uint64_t first, uint64_t m, double log_prior,
-                                float* d_lw, float* w_train, double* w_exact, double* pool, uint64_t pool_k,
-                                WeightScratch* d_ws, double* d_block_sums, cudaStream_t s, double* sum_v,
-                                double* sum_v2, double power, uint64_t tail_first, uint64_t* n_tail)
+// first pool_k samples into pool; sum v, sum v^2 and the count of samples with
+// index >= tail_first into *d_ws. Asynchronous on s.
+// d_block_sums: 2 doubles per 256 samples.
+static abc_status launch_round_weights(const float* logq, const uint64_t* idx, uint64_t first, uint64_t m,
+                                       double log_prior, float* d_lw, float* w_train, double* w_exact, double* pool,
+                                       uint64_t pool_k, WeightScratch* d_ws, double* d_block_sums, cudaStream_t s,
+                                       double power, uint64_t tail_first)
 {
     SMC_TRY(cudaMemsetAsync(d_ws, 0, sizeof(WeightScratch), s), "cudaMemsetAsync(weight scratch)");
     const unsigned blocks = (unsigned)((m + 255) / 256);
@@ -343,6 +346,18 @@ static abc_status round_weights(const float* logq, const uint64_t* idx, uint64_t
     weight_kernel<<<blocks, 256, 0, s>>>(d_lw, m, d_ws, w_train, w_exact, pool, pool_k, power, d_block_sums);
     weight_sums_kernel<<<1, 256, 0, s>>>(d_block_sums, blocks, d_ws);
     SMC_TRY(cudaGetLastError(), "weight launch");
+    return ABC_OK;
+}
+
+// launch_round_weights, then *sum_v, *sum_v2 and *n_tail read back.
+// Synchronizes s.
+static abc_status round_weights(const float* logq, const uint64_t* idx, uint64_t first, uint64_t m, double log_prior,
+                                float* d_lw, float* w_train, double* w_exact, double* pool, uint64_t pool_k,
+                                WeightScratch* d_ws, double* d_block_sums, cudaStream_t s, double* sum_v,
+                                double* sum_v2, double power, uint64_t tail_first, uint64_t* n_tail)
+{
+    SMC_ST(launch_round_weights(logq, idx, first, m, log_prior, d_lw, w_train, w_exact, pool, pool_k, d_ws,
+                                d_block_sums, s, power, tail_first));
     WeightScratch h;
     SMC_TRY(cudaMemcpyAsync(&h, d_ws, sizeof h, cudaMemcpyDeviceToHost, s), "cudaMemcpyAsync(weight sums)");
     SMC_TRY(cudaStreamSynchronize(s), "cudaStreamSynchronize");
@@ -647,8 +662,8 @@ extern "C" abc_status abc_smc_run_regions(const abc_prior_box* prior, abc_smc_re
     gd.dev.push_back(d_logq);
     SMC_TRY(cudaMalloc(&d_acc_logq, sizeof(float) * cap), "cudaMalloc(log weights)");
     gd.dev.push_back(d_acc_logq);
-    WeightScratch* d_ws = nullptr;
-    SMC_TRY(cudaMalloc(&d_ws, sizeof(WeightScratch)), "cudaMalloc(weight scratch)");
+    WeightScratch* d_ws = nullptr;   // one per region, read back together
+    SMC_TRY(cudaMalloc(&d_ws, sizeof(WeightScratch) * R), "cudaMalloc(weight scratch)");
     gd.dev.push_back(d_ws);
     float* d_wround = nullptr;
     SMC_TRY(cudaMalloc(&d_wround, sizeof(float) * cap), "cudaMalloc(round weights)");
@@ -725,52 +740,72 @@ extern "C" abc_status abc_smc_run_regions(const abc_prior_box* prior, abc_smc_re
         SMC_ST(abc_plan_reset(gd.plan, s));
         SMC_ST(abc_plan_run(gd.plan, s));
         SMC_TRY(cudaEventRecord(gd.ev[2], s), "cudaEventRecord");
+        // The regions' results in two passes with one synchronisation between
+        // them: first, for every region, the accepted samples in index order,
+        // their weights (the sums kept on the device), the copies into the
+        // pool and this round's training set; then, with all regions' weight
+        // sums read back at once, what depends on them (the ESS, the pool's
+        // scale, the next proposal, a training set from the pool).
         bool any_train = false;
+        std::vector<uint64_t> n_acc_v((size_t)R), days_v((size_t)R), k_v((size_t)R, 0);
+        std::vector<float*> th_v((size_t)R);
+        std::vector<double*> di_v((size_t)R);
+        std::vector<uint64_t*> ix_v((size_t)R);
+        SMC_ST(abcgb::plan_results_all(gd.plan, n_acc_v.data(), days_v.data(), th_v.data(), di_v.data(), ix_v.data(),
+                                       s));
+        const bool pool = r >= S - 1;
         for (int32_t g = 0; g < R; ++g) {
-            uint64_t n_acc = 0, days = 0;
-            float* acc_theta = nullptr;
-            double* acc_dist = nullptr;
-            uint64_t* acc_idx = nullptr;
-            SMC_ST(abc_plan_results(gd.plan, g, &n_acc, &days, &acc_theta, &acc_dist, &acc_idx, s));
-            Rr[g].n_accepted = n_acc;
-            Rr[g].simulated_days = days;
-            const uint64_t m = std::min(n_acc, cap);
-            // the accepted samples in index order, the same in every run (the
-            // sorted copy is used up by this region's copies before the next)
-            SMC_ST(sort_accepted(acc_theta, acc_dist, acc_idx, m, first, N, ss, s));
-            acc_theta = ss.theta;
-            acc_dist = ss.dist;
-            acc_idx = ss.idx;
+            Rr[g].n_accepted = n_acc_v[g];
+            Rr[g].simulated_days = days_v[g];
             trainable[g] = 0;
             next_flow[g] = 0;
             tr_n[g] = 0;
+            const uint64_t m = std::min(n_acc_v[g], cap);
             if (m == 0) continue;
+            // the accepted samples in index order, the same in every run (the
+            // sorted copy is used up by this region's copies before the next)
+            SMC_ST(sort_accepted(th_v[g], di_v[g], ix_v[g], m, first, N, ss, s));
             // weights prior / q_mix (1 for prior draws)
             abc_smc_region& G = regions[g];
-            const bool pool = r >= S - 1;
             const uint64_t k = pool ? std::min(m, G.capacity - G.n_out) : 0;
-            double* pw = k ? G.weight_out + G.n_out : nullptr;
-            double sw = 0.0, sw2 = 0.0;
-            uint64_t n_tail = 0;
-            SMC_ST(round_weights(use_flow[g] ? d_logq + (size_t)g * N : nullptr, acc_idx, first, m, log_prior,
-                                 d_acc_logq, d_wround, nullptr, pw, k, d_ws, ss.block_sums, s, &sw, &sw2,
-                                 cfg->train_weight_power, use_flow[g] ? first + N - Rr[g].n_defensive : UINT64_MAX,
-                                 &n_tail));
+            k_v[g] = k;
+            SMC_ST(launch_round_weights(use_flow[g] ? d_logq + (size_t)g * N : nullptr, ss.idx, first, m, log_prior,
+                                        d_acc_logq, d_wround, nullptr, k ? G.weight_out + G.n_out : nullptr, k,
+                                        d_ws + g, ss.block_sums, s, cfg->train_weight_power,
+                                        use_flow[g] ? first + N - Rr[g].n_defensive : UINT64_MAX));
+            if (k > 0) {
+                SMC_TRY(cudaMemcpyAsync(G.theta_out + 8 * G.n_out, ss.theta, sizeof(float) * 8 * k, cudaMemcpyDefault,
+                                        s),
+                        "cudaMemcpyAsync(pooled theta)");
+                SMC_TRY(cudaMemcpyAsync(G.dist_out + G.n_out, ss.dist, sizeof(double) * k, cudaMemcpyDefault, s),
+                        "cudaMemcpyAsync(pooled dist)");
+            }
+            // before the final eps the flow trains on this round's weighted
+            // accepts, if the weights show it worth it (decided below)
+            if (!pool && r + 1 < cfg->rounds)
+                SMC_ST(shuffled_training_set(ss.theta, d_wround, m, m, cfg->seed + 131 * (uint64_t)r + (uint64_t)g,
+                                             d_train + (size_t)g * 8 * cap, d_w + (size_t)g * cap, s));
+        }
+        std::vector<WeightScratch> hws((size_t)R);
+        SMC_TRY(cudaMemcpyAsync(hws.data(), d_ws, sizeof(WeightScratch) * R, cudaMemcpyDeviceToHost, s),
+                "cudaMemcpyAsync(weight sums)");
+        SMC_TRY(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+        for (int32_t g = 0; g < R; ++g) {
+            const uint64_t n_acc = n_acc_v[g], m = std::min(n_acc, cap);
+            if (m == 0) continue;
+            abc_smc_region& G = regions[g];
+            const uint64_t k = k_v[g];
+            const double sw = hws[g].sums[0], sw2 = hws[g].sums[1];
             Rr[g].ess_fraction = sw2 > 0.0 ? sw * sw / sw2 / (double)m : 0.0;
-            Rr[g].n_defensive_accepted = n_tail;
+            Rr[g].n_defensive_accepted = hws[g].n_tail;
             // samples accepted at the region's final eps join the pool; the
             // rounds' self-normalised estimates are combined with weights
             // proportional to their ESS, i.e. sample weight v_j sum v / sum v^2
             if (pool) {
                 G.n_pooled += n_acc;
                 if (k > 0) {
-                    scale_kernel<<<(unsigned)((k + 255) / 256), 256, 0, s>>>(pw, k, sw / sw2);
+                    scale_kernel<<<(unsigned)((k + 255) / 256), 256, 0, s>>>(G.weight_out + G.n_out, k, sw / sw2);
                     SMC_TRY(cudaGetLastError(), "scale launch");
-                    SMC_TRY(cudaMemcpyAsync(G.theta_out + 8 * G.n_out, acc_theta, sizeof(float) * 8 * k,
-                                            cudaMemcpyDefault, s),
-                            "cudaMemcpyAsync(pooled theta)");
-                    SMC_TRY(cudaMemcpyAsync(G.dist_out + G.n_out, acc_dist, sizeof(double) * k, cudaMemcpyDefault, s),
-                            "cudaMemcpyAsync(pooled dist)");
                     G.n_out += k;
                 }
             }
@@ -788,9 +823,7 @@ extern "C" abc_status abc_smc_run_regions(const abc_prior_box* prior, abc_smc_re
                     SMC_ST(shuffled_training_set(G.theta_out, G.weight_out, G.n_out, tn,
                                                  cfg->seed + 131 * (uint64_t)r + (uint64_t)g, tt, tw, s));
                 } else if (!pool && good) {
-                    tn = m;
-                    SMC_ST(shuffled_training_set(acc_theta, d_wround, m, m, cfg->seed + 131 * (uint64_t)r + (uint64_t)g,
-                                                 tt, tw, s));
+                    tn = m;   // built above
                 }
                 if (tn > 0) {
                     trainable[g] = 1;
