@@ -237,13 +237,15 @@ def bench_streamed(abc, torch, dev, flush, sm_count, sm_max, chunks=16):
 def bench_config1(abc, torch, dev, reps=20, warmup=3):
     """Plain ABC on region_1e6_T49 (P = 1e6, T = 49): 65,536 prior samples,
     exact mode, eps at the 0.1 % distance quantile. One run is the whole
-    pipeline through the public calls: every distance and prior draw
-    (abc_distances), eps as the k-th smallest, k = ceil(0.001 n) = 66
-    (abc_kth_smallest, radix select on the device), then the accept step at
-    that eps on those distances (abc_select_below: the same accepted set as a
-    rejection launch at eps, without simulating again). The observed series
-    comes from host memory in each call; eps and the accepted count are
-    checked against the workload's own (written by the oracle)."""
+    pipeline through the public calls: every distance and prior draw, eps as
+    the k-th smallest, k = ceil(0.001 n) = 66 (radix select on the device),
+    then the samples at or below that eps from those distances (the same
+    accepted set as a rejection launch at eps, without simulating again).
+    Timed as one abc_sample_quantile call, and beside it as the three calls
+    abc_distances, abc_kth_smallest and abc_select_below (each with its own
+    synchronisation). The observed series comes from host memory in each
+    call; eps and the accepted count are checked against the workload's own
+    (written by the oracle)."""
     with open(os.path.join(ROOT, "tests", "golden", "workloads.json")) as f:
         w = json.load(f)["region_1e6_T49"]
     obs, P, T, n, seed = np.array(w["observed"], dtype=np.int32), w["P"], w["T"], w["n_samples"], w["seed"]
@@ -254,30 +256,38 @@ def bench_config1(abc, torch, dev, reps=20, warmup=3):
     dbuf = torch.empty((n,), dtype=torch.float64, device=dev)
     tbuf = torch.empty((n, 8), dtype=torch.float32, device=dev)
     stage = {"distances": [], "kth_smallest": [], "select": []}
-    walls, eps, n_acc = [], None, None
+    walls, walls3, eps, n_acc, eps3, n_acc3 = [], [], None, None, None, None
     for rep in range(warmup + reps):
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
         torch.cuda.synchronize()
         t0 = time.perf_counter()
+        _, _, _, n_acc, eps = abc.abc_sample_quantile(obs, P, n, k, seed, mode="exact", out=outs)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
         ev[0].record()
         d, th = abc.abc_distances(obs, P, n, seed, mode="exact", want_theta=True, out=(dbuf, tbuf))
         ev[1].record()
-        eps = abc.abc_kth_smallest(d, k)
+        eps3 = abc.abc_kth_smallest(d, k)
         ev[2].record()
-        _, _, _, n_acc = abc.abc_select_below(d, eps, theta=th, out=outs)
+        _, _, _, n_acc3 = abc.abc_select_below(d, eps3, theta=th, out=outs)
         ev[3].record()
         torch.cuda.synchronize()
+        t2 = time.perf_counter()
         if rep >= warmup:
-            walls.append(time.perf_counter() - t0)
+            walls.append(t1 - t0)
+            walls3.append(t2 - t1)
             for j, key in enumerate(stage):
                 stage[key].append(ev[j].elapsed_time(ev[j + 1]))
     ms = float(np.median(walls)) * 1e3
+    ms3 = float(np.median(walls3)) * 1e3
     out = {"workload": "region_1e6_T49: P=1e6, T=49, %d prior samples, exact mode, eps = %d-th smallest distance "
                        "(0.1 %% quantile)" % (n, k),
            "accepted": int(n_acc), "eps": eps, "eps_equals_workload": bool(eps == w["eps"]),
            "ms_per_run": ms, "accepted_per_s": n_acc / (ms * 1e-3),
            "sims_days_per_s": n * T / (ms * 1e-3),
-           "ms_by_stage": {key: float(np.median(v)) for key, v in stage.items()}, "runs": reps}
+           "three_calls": {"ms_per_run": ms3, "same_eps_and_count": bool(eps3 == eps and n_acc3 == n_acc),
+                           "ms_by_stage": {key: float(np.median(v)) for key, v in stage.items()}},
+           "runs": reps}
     return out
 
 
@@ -576,6 +586,7 @@ def summary(line):
     if c1:
         out["c1_exact_quantile"] = {"accepted": c1["accepted"], "ms_per_run": r4(c1["ms_per_run"]),
                                     "accepted_per_s": r4(c1["accepted_per_s"]), "eps_ok": c1["eps_equals_workload"],
+                                    "three_calls_ms": r4(c1["three_calls"]["ms_per_run"]),
                                     "oracle_s": r4((c1.get("cpu_baseline") or {}).get("seconds"))}
     b = line.get("batched_regions")
     if b:

@@ -30,6 +30,9 @@
  *    by the caller. cuda_stream is a cudaStream_t (NULL = legacy default stream).
  *    Every call is stream-ordered on cuda_stream; calls that return host results
  *    (n_accepted, eps) synchronize that stream before returning.
+ *  - Scratch that a call allocates stream-ordered comes from a memory pool the
+ *    library creates on each device's first use; it keeps up to 1 GiB of freed
+ *    scratch mapped for later calls (more is given back at synchronisations).
  *  - Errors: every call returns an abc_status. On error, abc_last_error() gives a
  *    thread-local message. No C++ exception crosses this boundary.
  */
@@ -213,6 +216,34 @@ abc_status abc_kth_smallest(const double* dist, uint64_t n, uint64_t k, double* 
 abc_status abc_select_below(const double* dist, const float* theta, uint64_t n, double eps, uint64_t first_index,
                             float* theta_out, double* dist_out, uint64_t* idx_out, uint64_t capacity,
                             uint64_t* n_selected, void* cuda_stream);
+
+/* ABC rejection with eps at a distance quantile, in one call (Sec. 2.2: a
+ * sample is accepted when its distance is at most eps; here eps is the k-th
+ * smallest distance among the n_samples samples [first_index, first_index +
+ * n_samples), 1 <= k <= n_samples <= 2^40). Computes every distance, eps, and
+ * the samples with distance <= eps (at least k; more where distances tie at
+ * eps): the same eps and accepted set as abc_distances, abc_kth_smallest and
+ * abc_select_below called in turn with the same arguments, with the three
+ * steps back to back on the device, one synchronisation, and no distance
+ * copied to the host.
+ *
+ *  theta_out  DEVICE float  [capacity][8]   accepted theta
+ *  dist_out   DEVICE double [capacity]      accepted distances
+ *  idx_out    DEVICE uint64 [capacity]      accepted sample indices
+ *  eps_out    HOST   double                 the k-th smallest distance
+ *  n_accepted HOST   uint64                 number of accepted samples
+ *
+ * Order of the outputs and capacity overflow (ABC_ERR_CAPACITY with the true
+ * count in *n_accepted) as in abc_sample. Device scratch: every distance and
+ * prior draw (40 bytes per sample, stream-ordered, freed before returning),
+ * and the per-thread cached scratch of abc_sample for the series and counters.
+ * Synchronizes cuda_stream. */
+abc_status abc_sample_quantile(const abc_prior_box* prior, const int32_t* observed, int32_t T,
+                               int64_t N_pop, uint64_t n_samples, uint64_t k, uint64_t seed,
+                               uint32_t stream, abc_mode mode, uint64_t first_index,
+                               float* theta_out, double* dist_out, uint64_t* idx_out,
+                               uint64_t capacity, double* eps_out, uint64_t* n_accepted,
+                               void* cuda_stream);
 
 /* Posterior-predictive projection (Sec. 5: accepted samples simulated forward
  * for 120 days, plotted as 5th to 95th percentile bands). For b < B simulate

@@ -22,7 +22,7 @@ PAPER_LO = (0.0,) * 8
 PAPER_HI = (1.0, 100.0, 2.0, 1.0, 1.0, 1.0, 1.0, 2.0)   # Sec. 2.1, Eq. 2
 
 EXPORTED = ("abc_sample", "abc_distances", "abc_simulate", "abc_step", "abc_kth_smallest", "abc_select_below",
-            "abc_strerror",
+            "abc_sample_quantile", "abc_strerror",
             "abc_last_error", "abc_version", "abc_last_simulated_days", "abc_sample_noalloc", "abc_plan_create",
             "abc_plan_reset", "abc_plan_run", "abc_plan_run_graph", "abc_plan_tune", "abc_plan_results",
             "abc_plan_copy_results", "abc_plan_set_region", "abc_plan_set_shape", "abc_plan_destroy", "abc_maf_create",
@@ -124,6 +124,8 @@ def load(path=None):
         L.abc_kth_smallest.argtypes = [vp, u64, u64, ctypes.POINTER(ctypes.c_double), vp]
         L.abc_select_below.argtypes = [vp, vp, u64, ctypes.c_double, u64, vp, vp, vp, u64,
                                        ctypes.POINTER(ctypes.c_uint64), vp]
+        L.abc_sample_quantile.argtypes = [box, vp, i32, i64, u64, u64, u64, u32, ctypes.c_int, u64, vp, vp, vp, u64,
+                                          ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_uint64), vp]
         L.abc_observed_create.argtypes = [vp, i32, i64, ctypes.POINTER(ctypes.c_void_p)]
         L.abc_observed_destroy.argtypes = [vp]
         L.abc_sample_async.argtypes = [box, vp, ctypes.c_double, u64, u64, u32, ctypes.c_int, u64, vp, vp, vp, u64,
@@ -131,8 +133,8 @@ def load(path=None):
         L.abc_sample_until.argtypes = [box, vp, ctypes.c_double, u64, u64, u64, u64, u32, ctypes.c_int, u64, vp, vp,
                                        vp, u64, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64), vp]
         for nm in ("abc_sample", "abc_sample_noalloc", "abc_distances", "abc_simulate", "abc_step",
-                   "abc_kth_smallest", "abc_select_below", "abc_observed_create", "abc_observed_destroy", "abc_sample_async",
-                   "abc_sample_until"):
+                   "abc_kth_smallest", "abc_select_below", "abc_sample_quantile", "abc_observed_create",
+                   "abc_observed_destroy", "abc_sample_async", "abc_sample_until"):
             getattr(L, nm).restype = ctypes.c_int
         L.abc_strerror.argtypes = [ctypes.c_int]
         L.abc_strerror.restype = ctypes.c_char_p
@@ -494,6 +496,38 @@ def abc_select_below(dist, eps, first_index=0, theta=None, capacity=1 << 16, out
     _check(L, st)
     k = int(m.value)
     return (outs[0][:k] if theta is not None else None), outs[1][:k], outs[2][:k], k
+
+
+def abc_sample_quantile(observed, N_pop, n_samples, k, seed, stream=0, mode="fast", first_index=0, lo=PAPER_LO,
+                        hi=PAPER_HI, capacity=None, out=None, cuda_stream=None):
+    """ABC rejection over [first_index, first_index + n_samples) with eps the
+    k-th smallest distance, in one call. observed: host int32 [3, T+1].
+    Returns (theta [m, 8] f32, dist [m] f64, idx [m] (int64 storage),
+    n_accepted, eps) with the accepted samples as CUDA tensors in unspecified
+    order. Raises AbcError when more than capacity samples are accepted."""
+    L = load()
+    obs, obs_p = _host_i32(observed)
+    T = obs.shape[1] - 1
+    dev = torch.device("cuda", torch.cuda.current_device())
+    if out is None:
+        if capacity is None:
+            capacity = max(1024, 2 * int(k))
+        theta = torch.empty((capacity, 8), dtype=torch.float32, device=dev)
+        dist = torch.empty((capacity,), dtype=torch.float64, device=dev)
+        idx = torch.empty((capacity,), dtype=torch.int64, device=dev)
+    else:
+        theta, dist, idx = out
+        capacity = dist.shape[0]
+    nacc = ctypes.c_uint64(0)
+    eps = ctypes.c_double(0.0)
+    b = prior_box(lo, hi)
+    st = L.abc_sample_quantile(ctypes.byref(b), obs_p, T, int(N_pop), int(n_samples), int(k), int(seed), int(stream),
+                               _mode(mode), int(first_index), _dev(theta, torch.float32, (capacity, 8)),
+                               _dev(dist, torch.float64, (capacity,)), _dev(idx, torch.int64, (capacity,)),
+                               int(capacity), ctypes.byref(eps), ctypes.byref(nacc), _stream(cuda_stream))
+    _check(L, st)
+    n = int(nacc.value)
+    return theta[:n], dist[:n], idx[:n], n, float(eps.value)
 
 
 def abc_strerror(status):

@@ -177,14 +177,55 @@ struct Scratch {
     }
 };
 
+constexpr int kMaxCachedDevices = 64;
+
+// Stream-ordered scratch comes from one memory pool per device that keeps up
+// to kPoolKeepBytes of freed memory mapped across synchronisations. (The
+// device's default pool gives all freed memory back at every synchronisation,
+// so each call mapped its scratch anew: about 150 us of host time per call,
+// and as much again at the caller's next synchronisation.) A pool is created
+// on a device's first use and kept for the life of the process; a failed
+// creation is not cached, so a later call tries again.
+constexpr uint64_t kPoolKeepBytes = 1ull << 30;
+std::mutex g_pool_mutex;
+cudaMemPool_t g_pools[kMaxCachedDevices] = {};
+
+abc_status scratch_pool(cudaMemPool_t* out)
+{
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev), "cudaGetDevice");
+    if (dev < 0 || dev >= kMaxCachedDevices) return fail(ABC_ERR_INVALID_ARG, "device ordinal %d too large", dev);
+    std::lock_guard<std::mutex> lock(g_pool_mutex);
+    if (!g_pools[dev]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool = nullptr;
+        CUDA_TRY(cudaMemPoolCreate(&pool, &props), "cudaMemPoolCreate");
+        uint64_t keep = kPoolKeepBytes;
+        const cudaError_t e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        if (e != cudaSuccess) {
+            cudaMemPoolDestroy(pool);
+            return cuda_fail(e, "cudaMemPoolSetAttribute(release threshold)");
+        }
+        g_pools[dev] = pool;
+    }
+    *out = g_pools[dev];
+    return ABC_OK;
+}
+
 abc_status alloc_scratch(Scratch& sc, size_t bytes, cudaStream_t s)
 {
     sc.s = s;
     if (injected("alloc")) return fail(ABC_ERR_NOMEM, "scratch allocation failed (injected)");
-    cudaError_t e = cudaMallocAsync(&sc.ptr, bytes, s);
+    cudaMemPool_t pool = nullptr;
+    abc_status st = scratch_pool(&pool);
+    if (st != ABC_OK) return st;
+    cudaError_t e = cudaMallocFromPoolAsync(&sc.ptr, bytes, pool, s);
     if (e != cudaSuccess) {
         sc.ptr = nullptr;
-        return cuda_fail(e, "cudaMallocAsync(scratch)");
+        return cuda_fail(e, "cudaMallocFromPoolAsync(scratch)");
     }
     return ABC_OK;
 }
@@ -199,7 +240,6 @@ struct SampleScratch {
     size_t bytes = 0;
 };
 
-constexpr int kMaxCachedDevices = 64;
 thread_local SampleScratch g_sample_scratch[kMaxCachedDevices];
 
 abc_status sample_scratch(size_t bytes, SampleScratch** out)
@@ -293,6 +333,21 @@ bool plan_check_prior(const abc_prior_box* prior, abc_status* st)
     return *st == ABC_OK;
 }
 uint64_t plan_acc_threshold(double eps) { return acc_threshold(eps); }
+// stream-ordered scratch from the per-device pool of this file (alloc_scratch);
+// free it with cudaFreeAsync
+abc_status plan_scratch_alloc(void** ptr, size_t bytes, cudaStream_t s)
+{
+    *ptr = nullptr;
+    cudaMemPool_t pool = nullptr;
+    const abc_status st = scratch_pool(&pool);
+    if (st != ABC_OK) return st;
+    const cudaError_t e = cudaMallocFromPoolAsync(ptr, bytes, pool, s);
+    if (e != cudaSuccess) {
+        *ptr = nullptr;
+        return cuda_fail(e, "cudaMallocFromPoolAsync(scratch)");
+    }
+    return ABC_OK;
+}
 ModelParams plan_make_params(const abc_prior_box* prior, int32_t T, int64_t N_pop, uint64_t seed, uint32_t stream,
                              const int32_t* ard0)
 {
@@ -650,7 +705,7 @@ abc_status abc_kth_smallest(const double* dist, uint64_t n, uint64_t k, double* 
     const size_t bytes = 258 * sizeof(unsigned long long) + sizeof(abcgb::SelectState);
     if ((st = alloc_scratch(sc, bytes, s)) != ABC_OK) return st;
     unsigned long long* hist_d = (unsigned long long*)sc.ptr;
-    abcgb::SelectState* st_d = (abcgb::SelectState*)(hist_d + 258);   // 16-byte aligned after 257 counters
+    abcgb::SelectState* st_d = (abcgb::SelectState*)(hist_d + 258);   // 16-byte aligned after the 258 counters
     CUDA_TRY(cudaMemsetAsync(sc.ptr, 0, bytes, s), "cudaMemsetAsync(select scratch)");
     if (injected("launch")) return fail(ABC_ERR_CUDA, "kernel launch failed (injected)");
     CUDA_TRY(abcgb::launch_kth_select(dist, n, k, hist_d, st_d, s), "radix select launch");
@@ -686,6 +741,7 @@ abc_status abc_select_below(const double* dist, const float* theta, uint64_t n, 
     a.n = n;
     a.first_index = first_index;
     a.eps = eps;
+    a.eps_key = nullptr;
     a.theta_out = theta ? theta_out : nullptr;
     a.dist_out = dist_out;
     a.idx_out = idx_out;
@@ -697,6 +753,100 @@ abc_status abc_select_below(const double* dist, const float* theta, uint64_t n, 
     CUDA_TRY(cudaMemcpyAsync(&count, sc.ptr, sizeof count, cudaMemcpyDeviceToHost, s), "cudaMemcpyAsync(count)");
     CUDA_TRY(cudaStreamSynchronize(s), "cudaStreamSynchronize");
     *n_selected = count;
+    if (count > capacity)
+        return fail(ABC_ERR_CAPACITY, "%llu samples accepted, capacity %llu", count, (unsigned long long)capacity);
+    return ok();
+}
+
+abc_status abc_sample_quantile(const abc_prior_box* prior, const int32_t* observed, int32_t T, int64_t N_pop,
+                               uint64_t n_samples, uint64_t k, uint64_t seed, uint32_t stream, abc_mode mode,
+                               uint64_t first_index, float* theta_out, double* dist_out, uint64_t* idx_out,
+                               uint64_t capacity, double* eps_out, uint64_t* n_accepted, void* cuda_stream)
+{
+    abc_status st;
+    if ((st = check_prior(prior)) != ABC_OK) return st;
+    if ((st = check_model(T, N_pop, stream)) != ABC_OK) return st;
+    if (!valid_mode(mode)) return fail(ABC_ERR_INVALID_ARG, "unknown mode %d", (int)mode);
+    if (!eps_out || !n_accepted) return fail(ABC_ERR_INVALID_ARG, "eps_out or n_accepted is NULL");
+    *n_accepted = 0;
+    if (k < 1 || k > n_samples)
+        return fail(ABC_ERR_INVALID_ARG, "k = %llu outside [1, n_samples = %llu]", (unsigned long long)k,
+                    (unsigned long long)n_samples);
+    if (capacity > 0 && (!theta_out || !dist_out || !idx_out))
+        return fail(ABC_ERR_INVALID_ARG, "output buffers are NULL");
+    if (n_samples > ~(uint64_t)0 - first_index)
+        return fail(ABC_ERR_INVALID_ARG, "first_index + n_samples overflows");
+    if (n_samples > (uint64_t)1 << 40) return fail(ABC_ERR_INVALID_ARG, "n_samples above 2^40");
+    std::vector<int4> obs;
+    if ((st = pack_observed(observed, T, N_pop, obs)) != ABC_OK) return st;
+    const int32_t ard0[3] = {obs[0].x, obs[0].y, obs[0].z};
+    const abcgb::ModelParams p = make_params(prior, T, N_pop, seed, stream, ard0);
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+
+    // every distance and prior draw: stream-ordered scratch, 40 bytes a sample
+    const size_t dist_bytes = ((sizeof(double) * n_samples + 255) / 256) * 256;
+    Scratch big;
+    if ((st = alloc_scratch(big, dist_bytes + sizeof(float) * 8 * n_samples, s)) != ABC_OK) return st;
+    double* dist_d = (double*)big.ptr;
+    float* theta_d = (float*)((char*)big.ptr + dist_bytes);
+    // the radix select's histogram (258 counters) and state, the accept
+    // counter, then the observed series: zeroed and uploaded in one copy
+    // from pinned staging
+    struct Tail {
+        abcgb::SelectState sel;
+        unsigned long long count;
+    };
+    const size_t tail_off = 258 * sizeof(unsigned long long), obs_off = 2112;
+    static_assert(258 * sizeof(unsigned long long) + sizeof(Tail) <= 2112, "select scratch overlaps the series");
+    SampleScratch* sc = nullptr;
+    if ((st = sample_scratch(obs_off + sizeof(int4) * obs.size(), &sc)) != ABC_OK) return st;
+    std::memset(sc->host, 0, obs_off);
+    std::memcpy((char*)sc->host + obs_off, obs.data(), sizeof(int4) * obs.size());
+    unsigned long long* hist_d = (unsigned long long*)sc->dev;
+    Tail* tail_d = (Tail*)((char*)sc->dev + tail_off);
+    Tail* tail_h = (Tail*)((char*)sc->host + tail_off);
+    if (injected("launch")) return fail(ABC_ERR_CUDA, "kernel launch failed (injected)");
+    // from here on the pinned staging buffer may be in use by the stream: every
+    // error return first waits for the stream so the next call can reuse it
+    auto drain = [s](abc_status e) {
+        cudaStreamSynchronize(s);
+        return e;
+    };
+    cudaError_t ce = cudaMemcpyAsync(sc->dev, sc->host, obs_off + sizeof(int4) * obs.size(), cudaMemcpyHostToDevice, s);
+    if (ce != cudaSuccess) return drain(cuda_fail(ce, "cudaMemcpyAsync(observed, counters)"));
+    abcgb::DistanceArgs da;
+    da.obs = (const int4*)((char*)sc->dev + obs_off);
+    da.first_index = first_index;
+    da.n_samples = n_samples;
+    da.dist_out = dist_d;
+    da.theta_out = theta_d;
+    ce = abcgb::launch_distances(p, da, kernel_mode(mode), s);
+    if (ce != cudaSuccess) return drain(cuda_fail(ce, "abc_distance_kernel launch"));
+    ce = abcgb::launch_kth_select(dist_d, n_samples, k, hist_d, &tail_d->sel, s);
+    if (ce != cudaSuccess) return drain(cuda_fail(ce, "radix select launch"));
+    abcgb::SelectArgs a;
+    a.dist = dist_d;
+    a.theta = theta_d;
+    a.n = n_samples;
+    a.first_index = first_index;
+    a.eps = 0.0;
+    a.eps_key = &tail_d->sel;
+    a.theta_out = theta_out;
+    a.dist_out = dist_out;
+    a.idx_out = idx_out;
+    a.capacity = capacity;
+    a.count = &tail_d->count;
+    ce = abcgb::launch_select_below(a, s);
+    if (ce != cudaSuccess) return drain(cuda_fail(ce, "select_below launch"));
+    ce = cudaMemcpyAsync(tail_h, tail_d, sizeof(Tail), cudaMemcpyDeviceToHost, s);
+    if (ce != cudaSuccess) return drain(cuda_fail(ce, "cudaMemcpyAsync(select state)"));
+    CUDA_TRY(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+    // the distances of the model are never NaN or negative
+    if (tail_h->sel.bad != 0)
+        return fail(ABC_ERR_CUDA, "%llu distances are negative, -0 or NaN", tail_h->sel.bad);
+    std::memcpy(eps_out, &tail_h->sel.prefix, sizeof(double));
+    const unsigned long long count = tail_h->count;
+    *n_accepted = count;
     if (count > capacity)
         return fail(ABC_ERR_CAPACITY, "%llu samples accepted, capacity %llu", count, (unsigned long long)capacity);
     return ok();

@@ -320,56 +320,25 @@ __global__ void __launch_bounds__(kBandThreads) band_kernel(const int32_t* __res
 // ---------------------------------------------------------------------------
 // Radix select of the k-th smallest distance: eight passes over the keys (the
 // bit patterns of non-negative doubles order like the values), one 8-bit
-// digit per pass from the top. A pass histograms that digit among the keys
-// whose higher digits equal the prefix chosen so far; the select kernel then
-// picks the digit holding the wanted rank and updates the state in device
-// memory, so the passes run back to back with no host round trip. On the
-// first pass (mask == 0) hist[256] counts the keys above +infinity's pattern:
-// NaN and anything with the sign bit set (negative values and -0), which
-// would not order like their values.
+// digit per pass from the top, one launch per pass. A pass histograms that
+// digit among the keys whose higher digits equal the prefix chosen so far;
+// the last block of the pass to finish (a ticket counter, after a memory
+// fence) picks the digit holding the wanted rank and updates the state in
+// device memory, so the passes run back to back with no host round trip. On
+// the first pass (mask == 0) hist[256] counts the keys above +infinity's
+// pattern: NaN and anything with the sign bit set (negative values and -0),
+// which would not order like their values. hist[257] is the ticket counter.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kBlockThreads) digit_histogram_kernel(const double* __restrict__ dist, uint64_t n,
-                                                                        const SelectState* __restrict__ st, int shift,
-                                                                        unsigned long long* __restrict__ hist)
-{
-    __shared__ unsigned int h[257];
-    for (int b = threadIdx.x; b < 257; b += blockDim.x) h[b] = 0;
-    __syncthreads();
-    const uint64_t prefix = st->prefix, prefix_mask = st->mask;
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    const bool first = prefix_mask == 0;
-    for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
-        const uint64_t key = (uint64_t)__double_as_longlong(dist[j]);
-        if ((key & prefix_mask) == prefix) atomicAdd(&h[(key >> shift) & 0xFFu], 1u);
-        if (first && key > 0x7FF0000000000000ull) atomicAdd(&h[256], 1u);
-    }
-    __syncthreads();
-    for (int b = threadIdx.x; b < 257; b += blockDim.x)
-        if (h[b]) atomicAdd(&hist[b], (unsigned long long)h[b]);
-}
 
 // One warp: the digit of this pass is the first whose running count reaches
 // the rank (k on the first pass); the rank becomes the rank within that
-// digit's keys. Lane j holds bins 8j .. 8j + 7: a warp scan of the lanes'
-// sums finds the lane, then that lane walks its eight bins. Zeroes the
-// histogram for the next pass.
-__global__ void __launch_bounds__(32) digit_select_kernel(unsigned long long* __restrict__ hist,
-                                                          SelectState* __restrict__ st, int shift, uint64_t k)
+// digit's keys. Lane j holds bins 8j .. 8j + 7 in h (their sum in sum): a
+// warp scan of the lanes' sums finds the lane, then that lane walks its eight
+// bins and updates the state.
+__device__ __forceinline__ void select_digit(const unsigned long long (&h)[8], unsigned long long sum,
+                                             SelectState* st, int shift, uint64_t rank)
 {
-    const int lane = threadIdx.x;
-    unsigned long long h[8], sum = 0;
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        h[i] = hist[8 * lane + i];
-        sum += h[i];
-    }
-    const bool first = st->mask == 0;
-    const uint64_t rank = first ? k : st->rank;
-    if (first && lane == 0) st->bad = hist[256];
-    __syncwarp();
-#pragma unroll
-    for (int i = 0; i < 8; ++i) hist[8 * lane + i] = 0;
-    if (lane == 0) hist[256] = 0;
+    const int lane = threadIdx.x & 31;
     // inclusive scan of the lanes' sums
     unsigned long long incl = sum;
 #pragma unroll
@@ -394,6 +363,53 @@ __global__ void __launch_bounds__(32) digit_select_kernel(unsigned long long* __
     }
 }
 
+__global__ void __launch_bounds__(kBlockThreads) digit_pass_kernel(const double* __restrict__ dist, uint64_t n,
+                                                                   SelectState* __restrict__ st, int shift,
+                                                                   uint64_t k, unsigned long long* __restrict__ hist)
+{
+    __shared__ unsigned int h[257];
+    __shared__ bool last;
+    for (int b = threadIdx.x; b < 257; b += blockDim.x) h[b] = 0;
+    __syncthreads();
+    const uint64_t prefix = st->prefix, prefix_mask = st->mask;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const bool first = prefix_mask == 0;
+    for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
+        const uint64_t key = (uint64_t)__double_as_longlong(dist[j]);
+        if ((key & prefix_mask) == prefix) atomicAdd(&h[(key >> shift) & 0xFFu], 1u);
+        if (first && key > 0x7FF0000000000000ull) atomicAdd(&h[256], 1u);
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < 257; b += blockDim.x)
+        if (h[b]) atomicAdd(&hist[b], (unsigned long long)h[b]);
+    // the block's counts are in before its ticket is taken
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(&hist[257], 1ull) == gridDim.x - 1;
+    __syncthreads();
+    if (!last || threadIdx.x >= 32) return;
+    // the last block: every block's counts are in; read them past L1
+    __threadfence();
+    const int lane = threadIdx.x;
+    unsigned long long hb[8], sum = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        hb[i] = __ldcg(&hist[8 * lane + i]);
+        sum += hb[i];
+    }
+    const uint64_t rank = first ? k : st->rank;
+    if (first && lane == 0) st->bad = __ldcg(&hist[256]);
+    __syncwarp();
+    // the histogram and the ticket counter zeroed for the next pass
+#pragma unroll
+    for (int i = 0; i < 8; ++i) hist[8 * lane + i] = 0;
+    if (lane == 0) {
+        hist[256] = 0;
+        hist[257] = 0;
+    }
+    select_digit(hb, sum, st, shift, rank);
+}
+
 // ---------------------------------------------------------------------------
 // Samples accepted at eps from distances already computed (Sec. 2.2: accept
 // when the distance is at most eps): sample j is accepted iff dist[j] <= eps.
@@ -405,10 +421,11 @@ __global__ void __launch_bounds__(kBlockThreads) select_below_kernel(const __gri
 {
     const uint32_t lane = threadIdx.x & 31u;
     const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x / 32);
+    const double eps = a.eps_key ? __longlong_as_double((long long)a.eps_key->prefix) : a.eps;
     for (uint64_t base = ((uint64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5)) * 32; base < a.n;
          base += warps * 32) {
         const uint64_t j = base + lane;
-        const bool take = j < a.n && a.dist[j] <= a.eps;
+        const bool take = j < a.n && a.dist[j] <= eps;
         const uint32_t mask = __ballot_sync(0xFFFFFFFFu, take);
         if (!mask) continue;
         unsigned long long slot0 = 0;
@@ -603,13 +620,11 @@ cudaError_t launch_kth_select(const double* dist, uint64_t n, uint64_t k, unsign
                               cudaStream_t s)
 {
     int grid = 0;
-    cudaError_t e = grid_for(digit_histogram_kernel, 0, &grid);
+    cudaError_t e = grid_for(digit_pass_kernel, 0, &grid);
     if (e != cudaSuccess) return e;
     grid = blocks_for(n, grid);
-    for (int shift = 56; shift >= 0; shift -= 8) {
-        digit_histogram_kernel<<<grid, kBlockThreads, 0, s>>>(dist, n, st, shift, hist);
-        digit_select_kernel<<<1, 32, 0, s>>>(hist, st, shift, k);
-    }
+    for (int shift = 56; shift >= 0; shift -= 8)
+        digit_pass_kernel<<<grid, kBlockThreads, 0, s>>>(dist, n, st, shift, k, hist);
     return cudaGetLastError();
 }
 

@@ -107,19 +107,23 @@ cudaError_t launch_step(const ModelParams& p, const StepArgs& a, int mode, cudaS
 cudaError_t launch_bands(const int32_t* traj, uint32_t B, int32_t T, const float* qpos, int32_t n_q, float* bands,
                          cudaStream_t s);
 // Radix select of the k-th smallest of n distances, all passes on the device:
-// hist (257 counters) and st zeroed by the caller; afterwards st->prefix is
+// hist (258 counters: the histogram and a ticket counter) and st zeroed by the
+// caller, and left zeroed and holding the result; afterwards st->prefix is
 // the k-th smallest key and st->bad the number of invalid keys (NaN, sign bit
 // set), in which case the prefix is meaningless.
 struct SelectState {
     unsigned long long prefix, mask, rank, bad;
 };
 // Compaction of the samples with dist[j] <= eps (theta, theta_out may both be
-// NULL); *count (zeroed by the caller) receives the number of accepts.
+// NULL); *count (zeroed by the caller) receives the number of accepts. With
+// eps_key set, eps is the value whose bit pattern is eps_key->prefix (the
+// radix select's k-th smallest, computed on the device) instead of `eps`.
 struct SelectArgs {
     const double* dist;
     const float* theta;
     uint64_t n, first_index;
     double eps;
+    const SelectState* eps_key;
     float* theta_out;
     double* dist_out;
     uint64_t* idx_out;

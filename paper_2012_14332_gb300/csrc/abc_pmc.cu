@@ -20,6 +20,7 @@ abc_status plan_ok();
 bool plan_check_prior(const abc_prior_box* prior, abc_status* st);
 ModelParams plan_make_params(const abc_prior_box* prior, int32_t T, int64_t N_pop, uint64_t seed, uint32_t stream,
                              const int32_t* ard0);
+abc_status plan_scratch_alloc(void** ptr, size_t bytes, cudaStream_t s);
 }  // namespace abcgb
 
 namespace {
@@ -225,7 +226,13 @@ abc_status abc_pmc_propose(const abc_prior_box* prior, const float* theta_old, c
     cudaStream_t s = (cudaStream_t)cuda_stream;
     // cumulative weights of the caller's device weights
     double* d_cumw = nullptr;
-    PMC_TRY(cudaMallocAsync(&d_cumw, sizeof(double) * m, s), "cudaMallocAsync(cumw)");
+    if ((st = abcgb::plan_scratch_alloc(reinterpret_cast<void**>(&d_cumw), sizeof(double) * m, s)) != ABC_OK)
+        return st;
+    struct FreeOnReturn {   // every return below gives the scratch back, stream-ordered
+        void* p;
+        cudaStream_t s;
+        ~FreeOnReturn() { cudaFreeAsync(p, s); }
+    } release{d_cumw, s};
     std::vector<double> w(m), tmp;
     PMC_TRY(cudaMemcpyAsync(w.data(), w_old, sizeof(double) * m, cudaMemcpyDeviceToHost, s), "cudaMemcpyAsync(w)");
     PMC_TRY(cudaStreamSynchronize(s), "cudaStreamSynchronize");
@@ -239,7 +246,6 @@ abc_status abc_pmc_propose(const abc_prior_box* prior, const float* theta_old, c
     propose_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p, 2u << 2, theta_old, d_cumw, m, to_mat(Ld), box,
                                                                first_index, n, theta_out);
     cudaError_t e = cudaGetLastError();
-    cudaFreeAsync(d_cumw, s);
     PMC_TRY(cudaStreamSynchronize(s), "cudaStreamSynchronize");
     PMC_TRY(e, "propose launch");
     return abcgb::plan_ok();

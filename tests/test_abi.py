@@ -168,6 +168,24 @@ def test_other_entry_points_validate(L):
     obs = np.zeros((3, 11), dtype=np.int32)
     assert L.abc_distances(ctypes.byref(box), obs.ctypes.data_as(ctypes.c_void_p), 10, 1000, 5, 1, 0, 1, 0, None,
                            None, None) == ABC_ERR_INVALID_ARG
+    # the one-call quantile form checks its arguments before any CUDA call
+    eps = ctypes.c_double(0.0)
+    obs_p = obs.ctypes.data_as(ctypes.c_void_p)
+
+    def quantile(n=100, k=5, outs=(z, z, z), eps_p=ctypes.byref(eps), m_p=ctypes.byref(m), mode=1, first=0):
+        return L.abc_sample_quantile(ctypes.byref(box), obs_p, 10, 1000, n, k, 1, 0, mode, first, *outs, 4, eps_p,
+                                     m_p, None)
+    m.value = 9
+    assert quantile(k=0) == ABC_ERR_INVALID_ARG
+    assert m.value == 0
+    assert quantile(k=101) == ABC_ERR_INVALID_ARG
+    assert quantile(n=0, k=1) == ABC_ERR_INVALID_ARG
+    assert quantile(outs=(None, z, z)) == ABC_ERR_INVALID_ARG
+    assert quantile(eps_p=None) == ABC_ERR_INVALID_ARG
+    assert quantile(m_p=None) == ABC_ERR_INVALID_ARG
+    assert quantile(mode=99) == ABC_ERR_INVALID_ARG
+    assert quantile(n=2**41, k=1) == ABC_ERR_INVALID_ARG
+    assert quantile(first=2**64 - 50) == ABC_ERR_INVALID_ARG
     n1, n2 = ctypes.c_uint64(7), ctypes.c_uint64(7)
     assert L.abc_sample_until(ctypes.byref(box), None, 1.0, 5, 10, 100, 1, 0, 1, 0, None, None, None, 0,
                               ctypes.byref(n1), ctypes.byref(n2), None) == ABC_ERR_INVALID_ARG

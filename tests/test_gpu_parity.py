@@ -329,12 +329,18 @@ def test_longest_horizon_and_tiny_population():
 
 
 def test_kth_smallest_matches_sort():
+    """The radix select against a sort (ties, zeros, 1e300 and +inf
+    included), from a pass of one block with a ragged tail to passes of many
+    blocks, where the last block to finish each pass picks its digit."""
     g = inputs.rng(2)
     x = np.concatenate([g.random(100_003) * 1e6, [0.0, 0.0, 5.0, 5.0, 1e300, np.inf]])
-    t = torch.from_numpy(x).to(DEV)
-    xs = np.sort(x)
-    for k in (1, 2, 3, 50, 100_000, len(x) - 1, len(x)):
-        assert abc.abc_kth_smallest(t, k) == xs[k - 1]
+    big = np.concatenate([x, g.random(200_000) * 1e3, x[:5000]])
+    for n in (7, 200, len(x), 1 << 17, (1 << 17) + 1, len(big)):
+        v = big[:n]
+        t = torch.from_numpy(v).to(DEV)
+        vs = np.sort(v)
+        for k in sorted({1, 2, 3, 50, n // 2, n - 1, n} & set(range(1, n + 1))):
+            assert abc.abc_kth_smallest(t, k) == vs[k - 1]
 
 
 @pytest.mark.parametrize("bad", [np.nan, -1.0, -0.0, -np.inf])
@@ -342,13 +348,14 @@ def test_kth_smallest_rejects_values_that_do_not_order(bad):
     """A NaN, a negative value or -0 would sort by its bit pattern above
     every distance: the call refuses the input instead of returning a wrong
     quantile."""
-    x = inputs.rng(6).random(5000) * 100.0
-    x[1234] = bad
-    with pytest.raises(abc.AbcError) as e:
-        abc.abc_kth_smallest(torch.from_numpy(x).to(DEV), 10)
-    assert e.value.status == abc.binding.ABC_ERR_INVALID_ARG
-    x[1234] = 0.0
-    assert abc.abc_kth_smallest(torch.from_numpy(x).to(DEV), 1) == 0.0
+    for n in (5000, 200_000):   # the one-block and the many-block form
+        x = inputs.rng(6).random(n) * 100.0
+        x[1234] = bad
+        with pytest.raises(abc.AbcError) as e:
+            abc.abc_kth_smallest(torch.from_numpy(x).to(DEV), 10)
+        assert e.value.status == abc.binding.ABC_ERR_INVALID_ARG
+        x[1234] = 0.0
+        assert abc.abc_kth_smallest(torch.from_numpy(x).to(DEV), 1) == 0.0
 
 
 @pytest.mark.parametrize("mode", ["exact", "fast"])
@@ -383,6 +390,44 @@ def test_select_below_equals_rejection_at_eps(mode):
     assert none is None and m2 == m
     o = np.argsort(ix2.cpu().numpy())
     assert np.array_equal(ix2.cpu().numpy()[o], a[2]) and np.array_equal(di2.cpu().numpy()[o], a[1])
+
+
+@pytest.mark.parametrize("mode", ["exact", "fast"])
+def test_sample_quantile_equals_the_three_calls(mode):
+    """abc_sample_quantile, the one-call form of the quantile pipeline, on the
+    small workload (P = 1e6, T = 49, 65,536 samples, k = 66): the same eps and
+    the same accepted (index, theta, distance) set as abc_distances,
+    abc_kth_smallest and abc_select_below in turn; in exact mode eps is the
+    oracle-written workload's and the set is the oracle's. Then the edges:
+    k = 1 (the minimum), k = n (every sample, eps the largest distance), a
+    ragged n with an offset first index, and a capacity below the count."""
+    w = inputs.workload("region_1e6_T49")
+    obs, P, n, seed = w["observed"], w["P"], w["n_samples"], w["seed"]
+    th, di, ix, m, eps = abc.abc_sample_quantile(obs, P, n, 66, seed, mode=mode, capacity=1024)
+    d, th_all = abc.abc_distances(obs, P, n, seed, mode=mode, want_theta=True)
+    assert eps == abc.abc_kth_smallest(d, 66)
+    ref = abc.abc_select_below(d, eps, theta=th_all, capacity=1024)
+    assert m == ref[3] >= 66
+    a, b = _sorted(th, di, ix), _sorted(*ref[:3])
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+    if mode == "exact":
+        assert eps == w["eps"]
+        want = oracle.abc(obs, P, eps, n, seed, capacity=n)
+        assert m == want["n_accepted"]
+        assert np.array_equal(a[2], np.asarray(want["idx"], dtype=np.uint64))
+        assert np.array_equal(a[0], want["theta"]) and np.array_equal(a[1], want["dist"])
+    dn = np.sort(d.cpu().numpy())
+    _, di1, _, m1, e1 = abc.abc_sample_quantile(obs, P, n, 1, seed, mode=mode, capacity=16)
+    assert e1 == dn[0] and m1 == int(np.count_nonzero(dn == dn[0])) and di1.cpu().numpy()[0] == dn[0]
+    n2, first = 3001, 10**10 + 5
+    _, _, ix2, m2, e2 = abc.abc_sample_quantile(obs, P, n2, n2, seed, mode=mode, first_index=first, capacity=n2)
+    d2 = abc.abc_distances(obs, P, n2, seed, mode=mode, first_index=first).cpu().numpy()
+    assert e2 == d2.max() and m2 == n2
+    assert np.array_equal(np.sort(ix2.cpu().numpy().astype(np.uint64)), first + np.arange(n2, dtype=np.uint64))
+    with pytest.raises(abc.AbcError) as e:
+        abc.abc_sample_quantile(obs, P, n, 66, seed, mode=mode, capacity=m - 1)
+    assert e.value.status == abc.binding.ABC_ERR_CAPACITY
 
 
 def test_local_k_smallest_for_the_distributed_quantile():
