@@ -565,13 +565,17 @@ def bench_learned(abc, torch, w, prior_value, peaks, sm_count, sm_max, reps=5, v
         macs = sum(16 - (l % 7 + 1) for l in range(H))
         n_flow = int(0.9 * n)
         flops = 2 * macs * blocks * n_flow
-        peak = (peaks or {}).get("bf16_tflops", 1900.0)
+        measured = "bf16_tflops" in (peaks or {})
+        peak = peaks["bf16_tflops"] if measured else 1900.0
         achieved = flops / (ms_prop * 1e-3) / 1e12
         out["sampler_roofline"] = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                                    "frac": achieved / peak, "traffic": None, "ms_propose": ms_prop,
+                                   "peak_source": "measured" if measured else "fallback",
                                    "basis": "%d FLOP per flow proposal (masked MADE nonzero multiply-adds), %d flow "
-                                            "proposals per round; peak = measured cuBLAS bf16 burst"
-                                            % (flops // n_flow, n_flow)}
+                                            "proposals per round; peak = %s"
+                                            % (flops // n_flow, n_flow,
+                                               "the measured cuBLAS bf16 burst" if measured
+                                               else "the fallback bf16 burst figure, 1.9 PFLOP/s (no measured peaks file)")}
     return out
 
 
