@@ -644,8 +644,12 @@ abc_status abc_smc_run_regions(const abc_prior_box* prior, abc_smc_region* regio
  * Gaussian mixture, constants cancelling), normalised to sum 1. Each round
  * simulates batches of `batch` proposals until it holds at least
  * n_particles accepted ones (at most max_batches); all accepted ones of those
- * batches form the population. Simulations use (seed, stream 0, index),
- * proposals (seed, stream 2, index). */
+ * batches form the population, in ascending sample index (so a seed fixes
+ * the whole run, outputs included, while no round accepts more than
+ * capacity; beyond it, which samples a round keeps depends on the accept
+ * order). Simulations use (seed, stream 0, index), proposals (seed, stream 2,
+ * index). theta_out (float [n][8]), weight_out and dist_out (double [n]) may
+ * be host or device memory; *n_out = n, the final population's size. */
 typedef struct {
     int32_t rounds;
     uint64_t n_particles;

@@ -388,21 +388,40 @@ abc_status abc_pmc_run(const abc_prior_box* prior, const int32_t* observed, int3
         R.n_sims = batches * B;
         float* acc_theta = nullptr;
         double* acc_dist = nullptr;
-        PMC_ST(abc_plan_results(guard.plan, 0, &n_acc, nullptr, &acc_theta, &acc_dist, nullptr, s));
+        uint64_t* acc_idx = nullptr;
+        PMC_ST(abc_plan_results(guard.plan, 0, &n_acc, nullptr, &acc_theta, &acc_dist, &acc_idx, s));
         const uint64_t mm = std::min(n_acc, cap);
         R.n_accepted = mm;
         if (mm < 2) return plan_fail(ABC_ERR_INVALID_ARG, "a round accepted fewer than 2 particles");
-        std::vector<double> w_new(mm, 1.0);
+        std::vector<double> w_slot(mm, 1.0), dist_slot(mm);
+        std::vector<float> pop_slot(8 * mm);
+        std::vector<uint64_t> idx_slot(mm);
         if (r > 0) {
             PMC_TRY(cudaMemcpyAsync(d_new, acc_theta, sizeof(float) * 8 * mm, cudaMemcpyDeviceToDevice, s), "copy");
             weights_kernel<<<(unsigned)((mm + kTile - 1) / kTile), kTile, 0, s>>>(d_new, mm, d_pop, d_w, m, to_mat(Li),
                                                                               d_wnew);
             PMC_TRY(cudaGetLastError(), "weights launch");
-            PMC_TRY(cudaMemcpyAsync(w_new.data(), d_wnew, sizeof(double) * mm, cudaMemcpyDeviceToHost, s), "download");
+            PMC_TRY(cudaMemcpyAsync(w_slot.data(), d_wnew, sizeof(double) * mm, cudaMemcpyDeviceToHost, s), "download");
         }
-        std::vector<float> pop(8 * mm);
-        PMC_TRY(cudaMemcpyAsync(pop.data(), acc_theta, sizeof(float) * 8 * mm, cudaMemcpyDeviceToHost, s), "download");
+        PMC_TRY(cudaMemcpyAsync(pop_slot.data(), acc_theta, sizeof(float) * 8 * mm, cudaMemcpyDeviceToHost, s),
+                "download");
+        PMC_TRY(cudaMemcpyAsync(dist_slot.data(), acc_dist, sizeof(double) * mm, cudaMemcpyDeviceToHost, s), "download");
+        PMC_TRY(cudaMemcpyAsync(idx_slot.data(), acc_idx, sizeof(uint64_t) * mm, cudaMemcpyDeviceToHost, s), "download");
         PMC_TRY(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+        // the population in ascending sample index: the plan's accept slots
+        // follow the order of its atomics, which changes from run to run, and
+        // the next round's resampling (by cumulative weight) and every sum
+        // below follow the population's order; so a seed fixes the whole run
+        std::vector<uint32_t> ord(mm);
+        for (uint64_t j = 0; j < mm; ++j) ord[j] = (uint32_t)j;
+        std::sort(ord.begin(), ord.end(), [&](uint32_t a, uint32_t b) { return idx_slot[a] < idx_slot[b]; });
+        std::vector<float> pop(8 * mm);
+        std::vector<double> w_new(mm), dist(mm);
+        for (uint64_t j = 0; j < mm; ++j) {
+            std::memcpy(&pop[8 * j], &pop_slot[8 * (size_t)ord[j]], 8 * sizeof(float));
+            w_new[j] = w_slot[ord[j]];
+            dist[j] = dist_slot[ord[j]];
+        }
         double sw = 0.0, sw2 = 0.0;
         for (double v : w_new) {
             sw += v;
@@ -415,9 +434,9 @@ abc_status abc_pmc_run(const abc_prior_box* prior, const int32_t* observed, int3
         m = mm;
         if (r + 1 == cfg->rounds) {
             if (theta_out)
-                PMC_TRY(cudaMemcpyAsync(theta_out, acc_theta, sizeof(float) * 8 * m, cudaMemcpyDefault, s), "out");
+                PMC_TRY(cudaMemcpyAsync(theta_out, h_pop.data(), sizeof(float) * 8 * m, cudaMemcpyDefault, s), "out");
             if (dist_out)
-                PMC_TRY(cudaMemcpyAsync(dist_out, acc_dist, sizeof(double) * m, cudaMemcpyDefault, s), "out");
+                PMC_TRY(cudaMemcpyAsync(dist_out, dist.data(), sizeof(double) * m, cudaMemcpyDefault, s), "out");
             if (weight_out)
                 PMC_TRY(cudaMemcpyAsync(weight_out, h_w.data(), sizeof(double) * m, cudaMemcpyDefault, s), "out");
         }

@@ -6,7 +6,8 @@ sequential drivers put each run's accepted samples in sample-index order
 before weighting, pooling and training. So a gradient computed twice is the
 same bit for bit, in both CTA forms, and two sequential-ABC runs with one seed
 give the same rounds, accepted samples, weights and distances bit for bit;
-another seed gives other ones."""
+another seed gives other ones. Population Monte Carlo ABC keeps each round's
+population in sample-index order, with the same consequence."""
 import numpy as np
 import pytest
 
@@ -95,3 +96,27 @@ def test_per_region_sequential_abc_is_the_same_for_one_seed():
         assert ra[3] == rb[3] and ra[3] > 0
         for x, y in zip(ra[:3], rb[:3]):
             assert np.array_equal(x, y)
+
+
+def test_population_monte_carlo_is_the_same_for_one_seed():
+    """Two population Monte Carlo runs with one seed (region_1e6_T49, four
+    rounds of at least 1000 particles): the same rounds, particles, weights and
+    distances bit for bit, although the accept slots of each round come from
+    atomics in whatever order the batches' warps finish; another seed gives
+    another population."""
+    w = inputs.workload("region_1e6_T49")
+    obs, P = w["observed"], w["P"]
+    eps0 = abc.abc_kth_smallest(abc.abc_distances(obs, P, 1 << 18, 99, mode="fast"), 1 << 11)
+
+    def run(seed):
+        info, th, wt, dist = abc.abc_pmc_run(obs, P, eps0, rounds=4, n_particles=1000, batch=1 << 16,
+                                             max_batches=64, eps_factor=0.7, seed=seed, capacity=1 << 17,
+                                             mode="fast")
+        return ([(r["n_sims"], r["n_accepted"], r["ess_fraction"]) for r in info], th.cpu().numpy(),
+                wt.cpu().numpy(), dist.cpu().numpy())
+
+    a, b, c = run(8), run(8), run(9)
+    assert a[0] == b[0]
+    for x, y in zip(a[1:], b[1:]):
+        assert np.array_equal(x, y)
+    assert a[0] != c[0] or not np.array_equal(a[1], c[1])
