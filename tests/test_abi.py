@@ -277,3 +277,23 @@ def test_sequential_drivers_validate_before_any_cuda_call(L):
     reg[1] = AbcSmcRegion(op, 10, 1000, 5.0, None, None, None, 8, 0, 0)
     cfg = AbcSmcStreamConfig(AbcSmcConfig(**good), 2, 5)
     assert L.abc_smc_run_regions(ctypes.byref(box), reg, 2, ctypes.byref(cfg), rounds, s) == ABC_ERR_INVALID_ARG
+
+
+def test_failed_scratch_allocation_is_reported(L, monkeypatch):
+    """A scratch allocation that fails (made to fail on the host) returns
+    ABC_ERR_NOMEM with a message, before any kernel is launched: the calls
+    that take stream-ordered scratch from the library's pool."""
+    from paper_2012_14332_gb300.binding import ABC_ERR_NOMEM, prior_box
+    monkeypatch.setenv("ABC_GB300_INJECT_FAULT", "alloc")
+    box = prior_box()
+    obs = np.zeros((3, 11), dtype=np.int32)
+    obs[0, 0] = 5
+    obs_p = obs.ctypes.data_as(ctypes.c_void_p)
+    z = ctypes.c_void_p(16)
+    eps, m = ctypes.c_double(), ctypes.c_uint64(3)
+    assert L.abc_distances(ctypes.byref(box), obs_p, 10, 1000, 64, 1, 0, 1, 0, z, None, None) == ABC_ERR_NOMEM
+    assert L.abc_sample_quantile(ctypes.byref(box), obs_p, 10, 1000, 64, 3, 1, 0, 1, 0, z, z, z, 4,
+                                 ctypes.byref(eps), ctypes.byref(m), None) == ABC_ERR_NOMEM
+    assert m.value == 0 and "injected" in L.abc_last_error().decode()
+    assert L.abc_kth_smallest(z, 10, 3, ctypes.byref(eps), None) == ABC_ERR_NOMEM
+    assert L.abc_select_below(z, None, 10, 1.0, 0, None, z, z, 4, ctypes.byref(m), None) == ABC_ERR_NOMEM
