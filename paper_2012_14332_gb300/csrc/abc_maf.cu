@@ -703,6 +703,15 @@ __device__ __forceinline__ unsigned long long global_ns()
     return t;
 }
 
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialization may start before the previous kernel in its stream has
+// finished. griddep_wait returns once that kernel has completed and its
+// memory is visible (at once for a plain launch); griddep_release lets the
+// next such kernel start launching once every CTA of this one has released
+// or exited.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
 {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
@@ -881,6 +890,35 @@ struct TrainSlot {
     uint64_t n;
 };
 
+// The rows of one tile for lane (g, t): sample indices, weights and the
+// lane's two coordinates of rows q0 = 16 tile + g and q1 = q0 + 8 (rows past
+// n_rows: weight 0, row 0's data). With a ticket (a training step) the rows
+// are batch_row draws, lanes t = 0 and 1 of the row group drawing q0 and q1.
+// Called by the whole warp.
+struct TileRows {
+    float w0, w1;
+    float2 ta, tb;
+};
+
+__device__ __forceinline__ TileRows tile_rows(uint64_t tile, int g, int t, int lane, uint64_t n_rows, bool drawn,
+                                              const ModelParams& rp, uint32_t step, int f, const TrainSlot& slot)
+{
+    const uint64_t q0 = tile * 16 + g, q1 = q0 + 8;
+    uint64_t i0 = q0 < n_rows ? q0 : 0, i1 = q1 < n_rows ? q1 : 0;
+    if (drawn) {
+        const uint64_t qm = t ? q1 : q0;
+        const uint32_t mine = t < 2 && qm < n_rows ? batch_row(rp, (uint32_t)qm, step, f, slot.n) : 0u;
+        i0 = __shfl_sync(kFull, mine, lane & ~3);
+        i1 = __shfl_sync(kFull, mine, (lane & ~3) | 1);
+    }
+    TileRows r;
+    r.w0 = q0 < n_rows ? (slot.w ? slot.w[i0] : 1.f) : 0.f;
+    r.w1 = q1 < n_rows ? (slot.w ? slot.w[i1] : 1.f) : 0.f;
+    r.ta = *reinterpret_cast<const float2*>(slot.theta + 8 * i0 + 2 * t);
+    r.tb = *reinterpret_cast<const float2*>(slot.theta + 8 * i1 + 2 * t);
+    return r;
+}
+
 // Flow f = blockIdx.y reads slots[f]: with a ticket counter (a training step),
 // `batch` rows drawn for the step (batch_row; none if the flow has no points),
 // else all its n points. Each CTA of a training launch takes a ticket; the
@@ -914,8 +952,6 @@ __global__ void __launch_bounds__((W + 1) * 32, 1) grad_kernel(const uint32_t* _
     if (ticket && threadIdx.x == 0) step_s = atomicAdd(ticket, 1u) / ctas;   // before any CTA returns
     const uint64_t n_rows = ticket ? (slot.n ? batch : 0) : slot.n;
     if (n_rows == 0) return;   // uniform over the block
-    const float* __restrict__ theta = slot.theta;
-    const float* __restrict__ weights = slot.w;
     pub += (size_t)f * K * L.words;
     // this CTA's partial: K blocks of mb parameters, then the two loss sums
     float* __restrict__ out_part = part + ((size_t)f * gridDim.x + blockIdx.x) * part_stride;
@@ -927,7 +963,6 @@ __global__ void __launch_bounds__((W + 1) * 32, 1) grad_kernel(const uint32_t* _
     }
     __syncthreads();
     const uint32_t step_now = ticket ? step_s : 0u;
-    stage_blocks_bulk(wsm, pub, K, 0, L.grad_words, L, smem_addr(&bar_stage));
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int C = (H + kTcM - 1) / kTcM;   // jobs (128-unit halves) per block
     const int D = K * C;                   // (block, half) accumulator pairs, 32 columns each
@@ -957,12 +992,23 @@ __global__ void __launch_bounds__((W + 1) * 32, 1) grad_kernel(const uint32_t* _
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
+    const uint64_t tiles = (n_rows + 15) / 16;
+    const uint64_t tstride = (uint64_t)gridDim.x * TPC;
+    // Up to here nothing depends on the previous kernel of the stream (in a
+    // training step, the previous step's Adam, which reads the ticket before
+    // it releases this launch): the set-up and the first tile's rows overlap
+    // it. The published operands and the partials wait for its completion.
+    const uint64_t tile0 = (uint64_t)blockIdx.x * TPC + (PAIR ? warp >> 1 : warp);
+    TileRows first{};
+    if (warp < W && tile0 < tiles)
+        first = tile_rows(tile0, lane >> 2, lane & 3, lane, n_rows, ticket != nullptr, rp, step_now, f, slot);
+    griddep_wait();
+    stage_blocks_bulk(wsm, pub, K, 0, L.grad_words, L, smem_addr(&bar_stage));
+    griddep_release();
     // the operands staged (a wait that runs out sets the error word; the
     // CTA's result is then not used, but it still runs to its end)
     if (!mbar_wait(smem_addr(&bar_stage), 0) && lane == 0) atomicExch(err, 1);
     const uint32_t tmem = tmem_s;
-    const uint64_t tiles = (n_rows + 15) / 16;
-    const uint64_t tstride = (uint64_t)gridDim.x * TPC;
     if (warp < W) {
         const int g = lane >> 2, t = lane & 3, rg = 16 * g + 4 * t, sw = g & 4;
         unsigned char* sA = smem + warp * kTcSlot;   // h at 0, g_a1 at kTcHalf, the B slot after
@@ -976,20 +1022,11 @@ __global__ void __launch_bounds__((W + 1) * 32, 1) grad_kernel(const uint32_t* _
         const int s_lo = PAIR ? 8 * member : 0, s_hi = PAIR ? min(s_lo + 8, chunks) : chunks;
         float* xbuf = xch[PAIR ? pair : 0];
         uint32_t xc = 0;   // the pair's exchanges so far
-        for (uint64_t tile = (uint64_t)blockIdx.x * TPC + pair; tile < tiles; tile += tstride) {
-            const uint64_t q0 = tile * 16 + g, q1 = q0 + 8;
-            uint64_t i0 = q0 < n_rows ? q0 : 0, i1 = q1 < n_rows ? q1 : 0;
-            if (ticket) {
-                // lanes t = 0 and 1 of the row group draw rows q0 and q1
-                const uint64_t qm = t ? q1 : q0;
-                const uint32_t mine = t < 2 && qm < n_rows ? batch_row(rp, (uint32_t)qm, step_now, f, slot.n) : 0u;
-                i0 = __shfl_sync(kFull, mine, lane & ~3);
-                i1 = __shfl_sync(kFull, mine, (lane & ~3) | 1);
-            }
-            const float w0 = q0 < n_rows ? (weights ? weights[i0] : 1.f) : 0.f;
-            const float w1 = q1 < n_rows ? (weights ? weights[i1] : 1.f) : 0.f;
-            const float2 ta = *reinterpret_cast<const float2*>(theta + 8 * i0 + 2 * t);
-            const float2 tb = *reinterpret_cast<const float2*>(theta + 8 * i1 + 2 * t);
+        for (uint64_t tile = tile0; tile < tiles; tile += tstride) {
+            const TileRows rows =
+                tile == tile0 ? first : tile_rows(tile, g, t, lane, n_rows, ticket != nullptr, rp, step_now, f, slot);
+            const float w0 = rows.w0, w1 = rows.w1;
+            const float2 ta = rows.ta, tb = rows.tb;
             float x[4], jac;
             to_y(box, 2 * t, ta.x, x[0], jac);
             to_y(box, 2 * t + 1, ta.y, x[1], jac);
@@ -1456,13 +1493,16 @@ __device__ __forceinline__ void publish_param(uint32_t* __restrict__ pb, int H, 
 // A training step's Adam and publish in one launch: adam_kernel on the
 // gradient kernel's per-CTA partials, added here in the fixed tree of
 // group_sum; each updated parameter is published at once (publish_param). A
-// block updates ROWS x 256 / G parameters of flow blockIdx.y (two rows when
-// one group holds every partial: the block then has half as many loads per
-// row to wait on, and a launch of 16 flows fits one wave); a flow without rows
-// this step keeps its parameters, moments and published words. The step t is
-// the gradient launch's ticket count over its CTA count (grad_kernel): the
-// counter stands at t grad_ctas after the gradient launch of step t - 1, so
-// no launch has to advance a step counter.
+// block updates ROWS x 256 / G parameters of flow blockIdx.y (launched with
+// two rows: a launch of 16 flows fits one wave, and a one-flow launch leaves
+// room on the SMs for the next step's gradient CTAs, which start during it);
+// a flow without rows this step keeps its parameters, moments and published
+// words. The step t is the gradient launch's ticket count over its CTA count
+// (grad_kernel): the counter stands at t grad_ctas after the gradient launch
+// of step t - 1, so no launch has to advance a step counter. Launched to
+// start during the gradient kernel, the kernel reads its partials and the
+// ticket only after that kernel has completed, and releases the next step's
+// gradient launch only once the whole block has read the ticket.
 template <int G, int ROWS>
 __global__ void __launch_bounds__(256) adam_publish_kernel(float* __restrict__ params, const float* __restrict__ part,
                                                            int nblk, uint32_t part_stride,
@@ -1476,6 +1516,9 @@ __global__ void __launch_bounds__(256) adam_publish_kernel(float* __restrict__ p
     constexpr int E = 256 / G;
     __shared__ float gs[ROWS][G][E];
     __shared__ float w_s, c_s[2];
+    // launched to start during the gradient kernel: its partials and ticket
+    // are read only after it has completed
+    griddep_wait();
     const int f = blockIdx.y, e = threadIdx.x % E, q = threadIdx.x / E;
     const int64_t p0 = (int64_t)blockIdx.x * ROWS * E + e;
     const int t_step = (int)(*ticket / grad_ctas);
@@ -1525,6 +1568,9 @@ __global__ void __launch_bounds__(256) adam_publish_kernel(float* __restrict__ p
         g[1] = block_groups_total<G>(gs[1], mine1, q, e);
     }
     __syncthreads();
+    // the block has read the ticket (its bias corrections are in c_s): the
+    // next step's gradient kernel may launch and take its tickets
+    griddep_release();
     const float W = w_s;
 #pragma unroll
     for (int r = 0; r < ROWS; ++r) {
@@ -1822,6 +1868,26 @@ int red_groups(int nblk)
     return g;
 }
 
+// a launch that may start while the previous kernel in stream s finishes
+// (programmatic stream serialization; the kernel calls griddep_wait before
+// it touches that kernel's results)
+template <typename... KArgs, typename... Args>
+cudaError_t launch_overlapped(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 template <int G>
 void launch_reduce(abc_maf f, const maf::TrainSlot* slots, bool drawn, uint32_t batch, int nblk, uint32_t stride,
                    bool sums_only, cudaStream_t s)
@@ -1835,13 +1901,13 @@ void launch_reduce(abc_maf f, const maf::TrainSlot* slots, bool drawn, uint32_t 
 unsigned* train_ticket(abc_maf f) { return reinterpret_cast<unsigned*>(f->d_step + 1); }
 
 template <int G>
-void launch_adam_publish(abc_maf f, int nblk, float lr, cudaStream_t s)
+cudaError_t launch_adam_publish(abc_maf f, int nblk, float lr, cudaStream_t s)
 {
-    constexpr int ROWS = G == 1 ? 2 : 1, PER = ROWS * (256 / G);
-    maf::adam_publish_kernel<G, ROWS><<<dim3((unsigned)((f->n_params + PER - 1) / PER), f->R), 256, 0, s>>>(
-        f->d_params, f->d_part, nblk, part_stride(f), f->d_slots, f->d_m, f->d_v, train_ticket(f),
-        (uint32_t)nblk * (uint32_t)f->R, f->d_pub, f->K, f->H, maf::layout(f->H), f->n_params, lr, 0.9f, 0.999f,
-        1e-8f);
+    constexpr int ROWS = 2, PER = ROWS * (256 / G);
+    return launch_overlapped(maf::adam_publish_kernel<G, ROWS>, dim3((unsigned)((f->n_params + PER - 1) / PER), f->R),
+                             dim3(256), 0, s, f->d_params, f->d_part, nblk, part_stride(f), f->d_slots, f->d_m, f->d_v,
+                             train_ticket(f), (uint32_t)nblk * (uint32_t)f->R, f->d_pub, f->K, f->H,
+                             maf::layout(f->H), f->n_params, lr, 0.9f, 0.999f, 1e-8f);
 }
 
 // gradients of every flow's slot: with a ticket counter, `batch` rows per flow
@@ -1858,9 +1924,15 @@ cudaError_t launch_grad_w(abc_maf f, const maf::TrainSlot* slots, unsigned* tick
     const uint32_t stride = part_stride(f);
     if ((size_t)f->R * grid * stride > f->part_floats) return cudaErrorInvalidValue;   // ensure_part first
     if (PAIR && (f->H + maf::kTcM - 1) / maf::kTcM != 2) return cudaErrorInvalidValue;
-    maf::grad_kernel<K, W, PAIR><<<dim3(grid, f->R), (W + 1) * 32, smem, s>>>(
-        f->d_pub, f->H, f->box, slots, ticket, (uint32_t)grid * (uint32_t)f->R, rp, batch, f->d_part, stride,
-        f->d_err, f->hold);
+    if (ticket)   // a training step: may start while the previous step's Adam finishes
+        e = launch_overlapped(maf::grad_kernel<K, W, PAIR>, dim3(grid, f->R), dim3((W + 1) * 32), smem, s, f->d_pub,
+                              f->H, f->box, slots, ticket, (uint32_t)grid * (uint32_t)f->R, rp, batch, f->d_part,
+                              stride, f->d_err, f->hold);
+    else
+        maf::grad_kernel<K, W, PAIR><<<dim3(grid, f->R), (W + 1) * 32, smem, s>>>(
+            f->d_pub, f->H, f->box, slots, ticket, (uint32_t)grid * (uint32_t)f->R, rp, batch, f->d_part, stride,
+            f->d_err, f->hold);
+    if (e != cudaSuccess) return e;
     e = cudaGetLastError();
     if (e != cudaSuccess || !reduce) return e;
     switch (red_groups(grid)) {
@@ -1931,20 +2003,22 @@ cudaError_t launch_adam(abc_maf f, float lr, float b1, float b2, float eps, cuda
 
 // one training step on `batch` drawn rows per flow, two launches (captured
 // once and replayed): the gradient kernel draws its rows for the current step
-// and writes per-CTA partials; Adam adds the partials in a fixed order,
-// publishes every updated parameter and advances the step
+// and writes per-CTA partials; Adam adds the partials in a fixed order and
+// publishes every updated parameter. Both launches are overlapped
+// (programmatic dependent launch): each starts while the previous kernel
+// finishes and waits for it before touching its results.
 cudaError_t launch_train_step(abc_maf f, uint32_t batch, const ModelParams& p, float lr, cudaStream_t s)
 {
     cudaError_t e = MAF_DISPATCH(launch_grad, f, f->d_slots, train_ticket(f), p, batch, 0, false, false, s);
     if (e != cudaSuccess) return e;
     const int grid = grad_form(f, ((uint64_t)batch + 15) / 16).grid;
     switch (red_groups(grid)) {
-    case 1: launch_adam_publish<1>(f, grid, lr, s); break;
-    case 2: launch_adam_publish<2>(f, grid, lr, s); break;
-    case 4: launch_adam_publish<4>(f, grid, lr, s); break;
-    default: launch_adam_publish<8>(f, grid, lr, s); break;
+    case 1: e = launch_adam_publish<1>(f, grid, lr, s); break;
+    case 2: e = launch_adam_publish<2>(f, grid, lr, s); break;
+    case 4: e = launch_adam_publish<4>(f, grid, lr, s); break;
+    default: e = launch_adam_publish<8>(f, grid, lr, s); break;
     }
-    return cudaGetLastError();
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 }  // namespace
