@@ -370,6 +370,10 @@ __global__ void __launch_bounds__(kBlockThreads) digit_pass_kernel(const double*
     __shared__ unsigned int h[257];
     __shared__ bool last;
     for (int b = threadIdx.x; b < 257; b += blockDim.x) h[b] = 0;
+    // the previous pass (or the kernel that wrote the distances) completes
+    // before the state and the keys are read; the next pass may launch now
+    griddep_wait();
+    griddep_release();
     __syncthreads();
     const uint64_t prefix = st->prefix, prefix_mask = st->mask;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
@@ -421,6 +425,7 @@ __global__ void __launch_bounds__(kBlockThreads) select_below_kernel(const __gri
 {
     const uint32_t lane = threadIdx.x & 31u;
     const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x / 32);
+    griddep_wait();   // the distances and the selected key are complete
     const double eps = a.eps_key ? __longlong_as_double((long long)a.eps_key->prefix) : a.eps;
     for (uint64_t base = ((uint64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5)) * 32; base < a.n;
          base += warps * 32) {
@@ -612,8 +617,8 @@ cudaError_t launch_select_below(const SelectArgs& a, cudaStream_t s)
     cudaError_t e = grid_for(select_below_kernel, 0, &grid);
     if (e != cudaSuccess) return e;
     grid = blocks_for(a.n, grid);
-    select_below_kernel<<<grid, kBlockThreads, 0, s>>>(a);
-    return cudaGetLastError();
+    e = launch_overlapped(select_below_kernel, dim3(grid), dim3(kBlockThreads), 0, s, a);
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t launch_kth_select(const double* dist, uint64_t n, uint64_t k, unsigned long long* hist, SelectState* st,
@@ -623,9 +628,9 @@ cudaError_t launch_kth_select(const double* dist, uint64_t n, uint64_t k, unsign
     cudaError_t e = grid_for(digit_pass_kernel, 0, &grid);
     if (e != cudaSuccess) return e;
     grid = blocks_for(n, grid);
-    for (int shift = 56; shift >= 0; shift -= 8)
-        digit_pass_kernel<<<grid, kBlockThreads, 0, s>>>(dist, n, st, shift, k, hist);
-    return cudaGetLastError();
+    for (int shift = 56; shift >= 0 && e == cudaSuccess; shift -= 8)
+        e = launch_overlapped(digit_pass_kernel, dim3(grid), dim3(kBlockThreads), 0, s, dist, n, st, shift, k, hist);
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 }  // namespace abcgb

@@ -8,6 +8,34 @@ namespace abcgb {
 
 constexpr int kBlockThreads = 256;
 
+// Programmatic dependent launch: a kernel launched with launch_overlapped may
+// start before the previous kernel in its stream has finished. griddep_wait
+// returns once that kernel has completed and its memory is visible (at once
+// for a plain launch); griddep_release lets the next overlapped launch start
+// once every CTA of this kernel has released or exited.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// A launch with programmatic stream serialization: the kernel must call
+// griddep_wait before it touches anything the previous kernel writes or
+// reads.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_overlapped(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                                     Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 struct ModelParams;
 
 struct RejectArgs {

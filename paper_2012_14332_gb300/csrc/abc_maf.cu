@@ -703,15 +703,6 @@ __device__ __forceinline__ unsigned long long global_ns()
     return t;
 }
 
-// Programmatic dependent launch: a kernel launched with programmatic stream
-// serialization may start before the previous kernel in its stream has
-// finished. griddep_wait returns once that kernel has completed and its
-// memory is visible (at once for a plain launch); griddep_release lets the
-// next such kernel start launching once every CTA of this one has released
-// or exited.
-__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-__device__ __forceinline__ void griddep_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
-
 __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
 {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
@@ -1866,26 +1857,6 @@ int red_groups(int nblk)
     int g = 1;
     while (g < 8 && nblk > g * maf::kRedUnroll) g *= 2;
     return g;
-}
-
-// a launch that may start while the previous kernel in stream s finishes
-// (programmatic stream serialization; the kernel calls griddep_wait before
-// it touches that kernel's results)
-template <typename... KArgs, typename... Args>
-cudaError_t launch_overlapped(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
-                              Args... args)
-{
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = grid;
-    cfg.blockDim = block;
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    at[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
 }
 
 template <int G>
