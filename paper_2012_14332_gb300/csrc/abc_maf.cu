@@ -942,7 +942,12 @@ __global__ void __launch_bounds__((W + 1) * 32, 1) grad_kernel(const uint32_t* _
     __shared__ uint32_t step_s;
     if (ticket && threadIdx.x == 0) step_s = atomicAdd(ticket, 1u) / ctas;   // before any CTA returns
     const uint64_t n_rows = ticket ? (slot.n ? batch : 0) : slot.n;
-    if (n_rows == 0) return;   // uniform over the block
+    if (n_rows == 0) {   // uniform over the block
+        // even a CTA with no rows completes only after the previous kernel of
+        // the stream, so this launch's completion implies that kernel's
+        griddep_wait();
+        return;
+    }
     pub += (size_t)f * K * L.words;
     // this CTA's partial: K blocks of mb parameters, then the two loss sums
     float* __restrict__ out_part = part + ((size_t)f * gridDim.x + blockIdx.x) * part_stride;
