@@ -75,7 +75,7 @@ __device__ __forceinline__ float key_float(unsigned int k)
     return __uint_as_float((k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k);
 }
 
-__global__ void logw_kernel(const float* __restrict__ logq, const uint64_t* __restrict__ idx, uint64_t first, uint64_t m,
+__device__ __forceinline__ void logw_body(const float* __restrict__ logq, const uint64_t* __restrict__ idx, uint64_t first, uint64_t m,
                             uint64_t tail_first, float log_prior, float* __restrict__ lw, WeightScratch* ws)
 {
     const uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -94,7 +94,13 @@ __global__ void logw_kernel(const float* __restrict__ logq, const uint64_t* __re
     }
 }
 
-__global__ void weight_kernel(const float* __restrict__ lw, uint64_t m, WeightScratch* ws, float* __restrict__ w_train,
+__global__ void logw_kernel(const float* __restrict__ logq, const uint64_t* __restrict__ idx, uint64_t first, uint64_t m,
+                            uint64_t tail_first, float log_prior, float* __restrict__ lw, WeightScratch* ws)
+{
+    logw_body(logq, idx, first, m, tail_first, log_prior, lw, ws);
+}
+
+__device__ __forceinline__ void weight_body(const float* __restrict__ lw, uint64_t m, WeightScratch* ws, float* __restrict__ w_train,
                               double* __restrict__ w_exact, double* __restrict__ pool, uint64_t pool_k, double power,
                               double* __restrict__ block_sums)
 {
@@ -131,12 +137,19 @@ __global__ void weight_kernel(const float* __restrict__ lw, uint64_t m, WeightSc
     }
 }
 
+__global__ void weight_kernel(const float* __restrict__ lw, uint64_t m, WeightScratch* ws, float* __restrict__ w_train,
+                              double* __restrict__ w_exact, double* __restrict__ pool, uint64_t pool_k, double power,
+                              double* __restrict__ block_sums)
+{
+    weight_body(lw, m, ws, w_train, w_exact, pool, pool_k, power, block_sums);
+}
+
 // sum v and sum v^2 from the blocks' sums (one block of 256): thread t adds
 // blocks t, t + 256, ... in turn, then the threads' sums meet in a fixed
 // pairwise tree (t += t + 128, then t + 64, ...), so the sums are the same in
 // every run. (Thread 0 adding the 256 sums in turn took about 20 us: a chain of
 // 512 dependent double additions.)
-__global__ void __launch_bounds__(256) weight_sums_kernel(const double* __restrict__ block_sums, unsigned nblk,
+__device__ __forceinline__ void weight_sums_body(const double* __restrict__ block_sums, unsigned nblk,
                                                           WeightScratch* ws)
 {
     __shared__ double part[2][256];
@@ -161,6 +174,12 @@ __global__ void __launch_bounds__(256) weight_sums_kernel(const double* __restri
     }
 }
 
+__global__ void __launch_bounds__(256) weight_sums_kernel(const double* __restrict__ block_sums, unsigned nblk,
+                                                          WeightScratch* ws)
+{
+    weight_sums_body(block_sums, nblk, ws);
+}
+
 // ---------------------------------------------------------------------------
 // The accepted samples of a run in ascending sample index. The batched kernel
 // hands out accept slots with atomicAdd, so its buffers' order changes from
@@ -174,11 +193,17 @@ __global__ void __launch_bounds__(256) weight_sums_kernel(const double* __restri
 constexpr uint32_t kNoSlot = 0xFFFFFFFFu;
 constexpr int kSortBlock = 1024;   // indices per scan block (256 threads x 4)
 
-__global__ void scatter_slots_kernel(const uint64_t* __restrict__ idx, uint64_t m, uint64_t first,
+__device__ __forceinline__ void scatter_slots_body(const uint64_t* __restrict__ idx, uint64_t m, uint64_t first,
                                      uint32_t* __restrict__ pos)
 {
     const uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j < m) pos[idx[j] - first] = (uint32_t)j;
+}
+
+__global__ void scatter_slots_kernel(const uint64_t* __restrict__ idx, uint64_t m, uint64_t first,
+                                     uint32_t* __restrict__ pos)
+{
+    scatter_slots_body(idx, m, first, pos);
 }
 
 // exclusive scan of the 256 threads' counts; returns this thread's offset, *total the block's sum
@@ -204,7 +229,7 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* t
     return before + x - v;
 }
 
-__global__ void __launch_bounds__(256) count_slots_kernel(const uint32_t* __restrict__ pos, uint64_t n,
+__device__ __forceinline__ void count_slots_body(const uint32_t* __restrict__ pos, uint64_t n,
                                                           uint32_t* __restrict__ block_count)
 {
     const uint64_t base = (uint64_t)blockIdx.x * kSortBlock + 4 * threadIdx.x;
@@ -216,8 +241,14 @@ __global__ void __launch_bounds__(256) count_slots_kernel(const uint32_t* __rest
     if (threadIdx.x == 0) block_count[blockIdx.x] = total;
 }
 
+__global__ void __launch_bounds__(256) count_slots_kernel(const uint32_t* __restrict__ pos, uint64_t n,
+                                                          uint32_t* __restrict__ block_count)
+{
+    count_slots_body(pos, n, block_count);
+}
+
 // in-place exclusive scan of nb block counts, one block of 256 threads, in order
-__global__ void __launch_bounds__(256) scan_counts_kernel(uint32_t* __restrict__ count, uint32_t nb)
+__device__ __forceinline__ void scan_counts_body(uint32_t* __restrict__ count, uint32_t nb)
 {
     uint32_t carry = 0;
     for (uint32_t b0 = 0; b0 < nb; b0 += 256) {
@@ -230,7 +261,12 @@ __global__ void __launch_bounds__(256) scan_counts_kernel(uint32_t* __restrict__
     }
 }
 
-__global__ void __launch_bounds__(256) gather_sorted_kernel(const uint32_t* __restrict__ pos, uint64_t n,
+__global__ void __launch_bounds__(256) scan_counts_kernel(uint32_t* __restrict__ count, uint32_t nb)
+{
+    scan_counts_body(count, nb);
+}
+
+__device__ __forceinline__ void gather_sorted_body(const uint32_t* __restrict__ pos, uint64_t n,
                                                             const uint32_t* __restrict__ block_off,
                                                             const float* __restrict__ theta,
                                                             const double* __restrict__ dist,
@@ -260,11 +296,22 @@ __global__ void __launch_bounds__(256) gather_sorted_kernel(const uint32_t* __re
     }
 }
 
+__global__ void __launch_bounds__(256) gather_sorted_kernel(const uint32_t* __restrict__ pos, uint64_t n,
+                                                            const uint32_t* __restrict__ block_off,
+                                                            const float* __restrict__ theta,
+                                                            const double* __restrict__ dist,
+                                                            const uint64_t* __restrict__ idx,
+                                                            float* __restrict__ theta_o, double* __restrict__ dist_o,
+                                                            uint64_t* __restrict__ idx_o)
+{
+    gather_sorted_body(pos, n, block_off, theta, dist, idx, theta_o, dist_o, idx_o);
+}
+
 // training set: dst[j] = src[(a j + b) mod m] for theta and weights, j < n <= m
 // (a coprime to m, so a permutation): the held-out tail of the training set is
 // then a spread-out subset of the data, not its highest sample indices
 template <typename W>
-__global__ void permute_kernel(const float* __restrict__ theta, const W* __restrict__ w, uint64_t m, uint64_t n,
+__device__ __forceinline__ void permute_body(const float* __restrict__ theta, const W* __restrict__ w, uint64_t m, uint64_t n,
                                uint64_t a, uint64_t b, float* __restrict__ theta_dst, float* __restrict__ w_dst)
 {
     const uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -277,10 +324,163 @@ __global__ void permute_kernel(const float* __restrict__ theta, const W* __restr
     w_dst[j] = (float)w[i];
 }
 
-__global__ void scale_kernel(double* __restrict__ w, uint64_t m, double f)
+template <typename W>
+__global__ void permute_kernel(const float* __restrict__ theta, const W* __restrict__ w, uint64_t m, uint64_t n,
+                               uint64_t a, uint64_t b, float* __restrict__ theta_dst, float* __restrict__ w_dst)
+{
+    permute_body<W>(theta, w, m, n, a, b, theta_dst, w_dst);
+}
+
+__device__ __forceinline__ void scale_body(double* __restrict__ w, uint64_t m, double f)
 {
     const uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j < m) w[j] *= f;
+}
+
+__global__ void scale_kernel(double* __restrict__ w, uint64_t m, double f)
+{
+    scale_body(w, m, f);
+}
+
+// ---------------------------------------------------------------------------
+// A round's results of many regions in one launch per step (grid row y =
+// region): the steps above, each region on its own slice of per-region
+// scratch. A block past its region's size returns at once.
+// ---------------------------------------------------------------------------
+struct RegionRound {
+    const float* acc_theta;    // the plan's accepted samples (accept-slot order)
+    const double* acc_dist;
+    const uint64_t* acc_idx;
+    uint64_t m;                // accepted samples kept: min(accepted, capacity)
+    const float* logq;         // the round's proposal log densities, NULL for prior draws
+    uint64_t tail_first;       // first index of the defensive prior draws (UINT64_MAX: none)
+    double* pool;              // the first pool_k weights go here (NULL: none)
+    float* pool_theta;         // and the first pool_k samples' theta and distance
+    double* pool_dist;
+    uint64_t pool_k;
+    float* train_theta;        // this round's training set (NULL: none): m rows in the
+    float* train_w;            // order j -> (perm_a j + perm_b) mod m
+    uint64_t perm_a, perm_b;
+};
+
+// per-region scratch of a round: positions over the round's n indices, block
+// counts, the sorted samples, log weights, training weights, block sums
+struct RegionScratch {
+    uint32_t* pos;      // [R][n]
+    uint32_t* count;    // [R][nb]
+    float* theta;       // [R][cap][8]
+    double* dist;       // [R][cap]
+    uint64_t* idx;      // [R][cap]
+    float* lw;          // [R][cap]
+    float* w;           // [R][cap]
+    double* bsum;       // [R][2 (cap / 256 + 1)]
+    WeightScratch* ws;  // [R]
+    uint64_t n, cap;
+    uint32_t nb;
+};
+
+__device__ __forceinline__ bool region_block_in(uint64_t count)
+{
+    return (uint64_t)blockIdx.x * blockDim.x < count;
+}
+
+__global__ void scatter_slots_regions(const RegionRound* __restrict__ tab, uint64_t first, RegionScratch sc)
+{
+    const RegionRound& T = tab[blockIdx.y];
+    if (!region_block_in(T.m)) return;
+    scatter_slots_body(T.acc_idx, T.m, first, sc.pos + blockIdx.y * sc.n);
+}
+
+__global__ void __launch_bounds__(256) count_slots_regions(const RegionRound* __restrict__ tab, RegionScratch sc)
+{
+    if (tab[blockIdx.y].m == 0) return;
+    count_slots_body(sc.pos + blockIdx.y * sc.n, sc.n, sc.count + (size_t)blockIdx.y * sc.nb);
+}
+
+__global__ void __launch_bounds__(256) scan_counts_regions(const RegionRound* __restrict__ tab, RegionScratch sc)
+{
+    if (tab[blockIdx.x].m == 0) return;
+    scan_counts_body(sc.count + (size_t)blockIdx.x * sc.nb, sc.nb);
+}
+
+__global__ void __launch_bounds__(256) gather_sorted_regions(const RegionRound* __restrict__ tab, RegionScratch sc)
+{
+    const RegionRound& T = tab[blockIdx.y];
+    if (T.m == 0) return;
+    const size_t g = blockIdx.y;
+    gather_sorted_body(sc.pos + g * sc.n, sc.n, sc.count + g * sc.nb, T.acc_theta, T.acc_dist, T.acc_idx,
+                       sc.theta + g * sc.cap * 8, sc.dist + g * sc.cap, sc.idx + g * sc.cap);
+}
+
+__global__ void logw_regions(const RegionRound* __restrict__ tab, uint64_t first, float log_prior, RegionScratch sc)
+{
+    const RegionRound& T = tab[blockIdx.y];
+    if (!region_block_in(T.m)) return;
+    const size_t g = blockIdx.y;
+    logw_body(T.logq, sc.idx + g * sc.cap, first, T.m, T.tail_first, log_prior, sc.lw + g * sc.cap, sc.ws + g);
+}
+
+__global__ void weight_regions(const RegionRound* __restrict__ tab, double power, RegionScratch sc)
+{
+    const RegionRound& T = tab[blockIdx.y];
+    if (!region_block_in(T.m)) return;
+    const size_t g = blockIdx.y;
+    weight_body(sc.lw + g * sc.cap, T.m, sc.ws + g, sc.w + g * sc.cap, nullptr, T.pool, T.pool_k, power,
+                sc.bsum + g * 2 * (sc.cap / 256 + 1));
+}
+
+__global__ void __launch_bounds__(256) weight_sums_regions(const RegionRound* __restrict__ tab, RegionScratch sc)
+{
+    const RegionRound& T = tab[blockIdx.x];
+    if (T.m == 0) return;
+    const size_t g = blockIdx.x;
+    weight_sums_body(sc.bsum + g * 2 * (sc.cap / 256 + 1), (unsigned)((T.m + 255) / 256), sc.ws + g);
+}
+
+// the pooled samples (theta, distance) and this round's training set
+__global__ void pool_and_train_regions(const RegionRound* __restrict__ tab, RegionScratch sc)
+{
+    const RegionRound& T = tab[blockIdx.y];
+    const size_t g = blockIdx.y;
+    const uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const float* th = sc.theta + g * sc.cap * 8;
+    if (j < T.pool_k) {
+        const float4* src = reinterpret_cast<const float4*>(th + 8 * j);
+        float4* dst = reinterpret_cast<float4*>(T.pool_theta + 8 * j);
+        dst[0] = src[0];
+        dst[1] = src[1];
+        T.pool_dist[j] = sc.dist[g * sc.cap + j];
+    }
+    if (T.train_theta && region_block_in(T.m))
+        permute_body<float>(th, sc.w + g * sc.cap, T.m, T.m, T.perm_a, T.perm_b, T.train_theta, T.train_w);
+}
+
+// The second pass of a round, once the weight sums are on the host: each
+// region's new pool weights scaled, then a training set drawn from its pool
+struct RegionPool {
+    double* w;                 // this round's pool weights, k of them, times f
+    uint64_t k;
+    double f;
+    const float* theta;        // the pool: m samples and weights
+    const double* pw;
+    uint64_t m, n;             // n rows of training set (0: none) in the order j -> (a j + b) mod m
+    uint64_t a, b;
+    float* train_theta;
+    float* train_w;
+};
+
+__global__ void scale_pools_regions(const RegionPool* __restrict__ tab)
+{
+    const RegionPool& T = tab[blockIdx.y];
+    if (!region_block_in(T.k)) return;
+    scale_body(T.w, T.k, T.f);
+}
+
+__global__ void train_from_pools_regions(const RegionPool* __restrict__ tab)
+{
+    const RegionPool& T = tab[blockIdx.y];
+    if (!region_block_in(T.n)) return;
+    permute_body<double>(T.theta, T.pw, T.m, T.n, T.a, T.b, T.train_theta, T.train_w);
 }
 
 struct Guard {
@@ -314,17 +514,25 @@ using abcgb::plan_fail;
         if (_s != ABC_OK) return _s;        \
     } while (0)
 
+// The permutation j -> (a j + b) mod m of a training set: a near m times the
+// golden ratio and coprime to m, b from the salt. m < 2^32.
+static void perm_params(uint64_t m, uint64_t salt, uint64_t* a_out, uint64_t* b_out)
+{
+    uint64_t a = (uint64_t)(0.6180339887498949 * (double)m) | 1u;
+    while (std::gcd(a, m) != 1) a += 2;
+    *a_out = a % m ? a % m : 1;
+    *b_out = (salt * 0x9E3779B97F4A7C15ull) % m;
+}
+
 // Shuffle m samples and their weights into a training set of the first
 // n <= m of the permuted order (permute_kernel). m < 2^32.
 template <typename W>
 static abc_status shuffled_training_set(const float* theta, const W* w, uint64_t m, uint64_t n, uint64_t salt,
                                         float* theta_dst, float* w_dst, cudaStream_t s)
 {
-    uint64_t a = (uint64_t)(0.6180339887498949 * (double)m) | 1u;
-    while (std::gcd(a, m) != 1) a += 2;
-    const uint64_t b = (salt * 0x9E3779B97F4A7C15ull) % m;
-    permute_kernel<W><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(theta, w, m, n, a % m ? a % m : 1, b, theta_dst,
-                                                                  w_dst);
+    uint64_t a = 0, b = 0;
+    perm_params(m, salt, &a, &b);
+    permute_kernel<W><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(theta, w, m, n, a, b, theta_dst, w_dst);
     SMC_TRY(cudaGetLastError(), "permute launch");
     return ABC_OK;
 }
@@ -655,25 +863,54 @@ extern "C" abc_status abc_smc_run_regions(const abc_prior_box* prior, abc_smc_re
     SMC_ST(abc_maf_create_multi(R, cfg->flow_blocks, cfg->flow_hidden, prior, &gd.flows));
     SMC_ST(abc_maf_set_proposal_scale(gd.flows, (float)cfg->proposal_scale));
     SMC_ST(abc_maf_init_random(gd.flows, cfg->seed ^ 0x5EED5EEDull, 0.3f));
-    float *d_prop = nullptr, *d_logq = nullptr, *d_acc_logq = nullptr, *d_w = nullptr, *d_train = nullptr;
+    float *d_prop = nullptr, *d_logq = nullptr, *d_w = nullptr, *d_train = nullptr;
     SMC_TRY(cudaMalloc(&d_prop, sizeof(float) * 8 * N * R), "cudaMalloc(proposals)");
     gd.dev.push_back(d_prop);
     SMC_TRY(cudaMalloc(&d_logq, sizeof(float) * N * R), "cudaMalloc(logq)");
     gd.dev.push_back(d_logq);
-    SMC_TRY(cudaMalloc(&d_acc_logq, sizeof(float) * cap), "cudaMalloc(log weights)");
-    gd.dev.push_back(d_acc_logq);
-    WeightScratch* d_ws = nullptr;   // one per region, read back together
-    SMC_TRY(cudaMalloc(&d_ws, sizeof(WeightScratch) * R), "cudaMalloc(weight scratch)");
-    gd.dev.push_back(d_ws);
-    float* d_wround = nullptr;
-    SMC_TRY(cudaMalloc(&d_wround, sizeof(float) * cap), "cudaMalloc(round weights)");
-    gd.dev.push_back(d_wround);
     SMC_TRY(cudaMalloc(&d_w, sizeof(float) * cap * R), "cudaMalloc(weights)");
     gd.dev.push_back(d_w);
     SMC_TRY(cudaMalloc(&d_train, sizeof(float) * 8 * cap * R), "cudaMalloc(training sets)");
     gd.dev.push_back(d_train);
-    SortScratch ss;
-    SMC_ST(alloc_sort_scratch(ss, N, cap, gd.dev));
+    // per-region scratch of a round's results (RegionScratch) and the tables
+    // of the two passes
+    RegionScratch rs{};
+    rs.n = N;
+    rs.cap = cap;
+    rs.nb = (uint32_t)((N + kSortBlock - 1) / kSortBlock);
+    {
+        const size_t Rz = (size_t)R;
+        void* q = nullptr;
+        auto grab = [&](size_t bytes, const char* what) -> abc_status {
+            SMC_TRY(cudaMalloc(&q, bytes), what);
+            gd.dev.push_back(q);
+            return ABC_OK;
+        };
+        SMC_ST(grab(sizeof(uint32_t) * N * Rz, "cudaMalloc(sort positions)"));
+        rs.pos = (uint32_t*)q;
+        SMC_ST(grab(sizeof(uint32_t) * rs.nb * Rz, "cudaMalloc(sort counts)"));
+        rs.count = (uint32_t*)q;
+        SMC_ST(grab(sizeof(float) * 8 * cap * Rz, "cudaMalloc(sorted theta)"));
+        rs.theta = (float*)q;
+        SMC_ST(grab(sizeof(double) * cap * Rz, "cudaMalloc(sorted dist)"));
+        rs.dist = (double*)q;
+        SMC_ST(grab(sizeof(uint64_t) * cap * Rz, "cudaMalloc(sorted idx)"));
+        rs.idx = (uint64_t*)q;
+        SMC_ST(grab(sizeof(float) * cap * Rz, "cudaMalloc(log weights)"));
+        rs.lw = (float*)q;
+        SMC_ST(grab(sizeof(float) * cap * Rz, "cudaMalloc(round weights)"));
+        rs.w = (float*)q;
+        SMC_ST(grab(sizeof(double) * 2 * (cap / 256 + 1) * Rz, "cudaMalloc(weight block sums)"));
+        rs.bsum = (double*)q;
+        SMC_ST(grab(sizeof(WeightScratch) * Rz, "cudaMalloc(weight scratch)"));
+        rs.ws = (WeightScratch*)q;
+    }
+    RegionRound* d_rr = nullptr;
+    RegionPool* d_rp = nullptr;
+    SMC_TRY(cudaMalloc(&d_rr, sizeof(RegionRound) * R), "cudaMalloc(round table)");
+    gd.dev.push_back(d_rr);
+    SMC_TRY(cudaMalloc(&d_rp, sizeof(RegionPool) * R), "cudaMalloc(pool table)");
+    gd.dev.push_back(d_rp);
     for (cudaEvent_t& e : gd.ev) SMC_TRY(cudaEventCreate(&e), "cudaEventCreate");
 
     // one plan for every round: the regions' eps, proposals and first indices
@@ -741,11 +978,12 @@ extern "C" abc_status abc_smc_run_regions(const abc_prior_box* prior, abc_smc_re
         SMC_ST(abc_plan_run(gd.plan, s));
         SMC_TRY(cudaEventRecord(gd.ev[2], s), "cudaEventRecord");
         // The regions' results in two passes with one synchronisation between
-        // them: first, for every region, the accepted samples in index order,
-        // their weights (the sums kept on the device), the copies into the
-        // pool and this round's training set; then, with all regions' weight
-        // sums read back at once, what depends on them (the ESS, the pool's
-        // scale, the next proposal, a training set from the pool).
+        // them, every step one launch over all regions (grid row = region):
+        // first the accepted samples in index order, their weights (the sums
+        // kept on the device), the copies into the pool and this round's
+        // training set; then, with all regions' weight sums read back at
+        // once, what depends on them (the ESS, the pool's scale, the next
+        // proposal, a training set from the pool).
         bool any_train = false;
         std::vector<uint64_t> n_acc_v((size_t)R), days_v((size_t)R), k_v((size_t)R, 0);
         std::vector<float*> th_v((size_t)R);
@@ -754,43 +992,72 @@ extern "C" abc_status abc_smc_run_regions(const abc_prior_box* prior, abc_smc_re
         SMC_ST(abcgb::plan_results_all(gd.plan, n_acc_v.data(), days_v.data(), th_v.data(), di_v.data(), ix_v.data(),
                                        s));
         const bool pool = r >= S - 1;
+        const bool round_sets = !pool && r + 1 < cfg->rounds;   // training sets from this round alone
+        std::vector<RegionRound> rr((size_t)R);
+        uint64_t max_m = 0, max_k = 0;
         for (int32_t g = 0; g < R; ++g) {
             Rr[g].n_accepted = n_acc_v[g];
             Rr[g].simulated_days = days_v[g];
             trainable[g] = 0;
             next_flow[g] = 0;
             tr_n[g] = 0;
-            const uint64_t m = std::min(n_acc_v[g], cap);
-            if (m == 0) continue;
-            // the accepted samples in index order, the same in every run (the
-            // sorted copy is used up by this region's copies before the next)
-            SMC_ST(sort_accepted(th_v[g], di_v[g], ix_v[g], m, first, N, ss, s));
-            // weights prior / q_mix (1 for prior draws)
+            RegionRound& T = rr[g];
+            T = RegionRound{};
+            T.m = std::min(n_acc_v[g], cap);
+            if (T.m == 0) continue;
             abc_smc_region& G = regions[g];
-            const uint64_t k = pool ? std::min(m, G.capacity - G.n_out) : 0;
-            k_v[g] = k;
-            SMC_ST(launch_round_weights(use_flow[g] ? d_logq + (size_t)g * N : nullptr, ss.idx, first, m, log_prior,
-                                        d_acc_logq, d_wround, nullptr, k ? G.weight_out + G.n_out : nullptr, k,
-                                        d_ws + g, ss.block_sums, s, cfg->train_weight_power,
-                                        use_flow[g] ? first + N - Rr[g].n_defensive : UINT64_MAX));
-            if (k > 0) {
-                SMC_TRY(cudaMemcpyAsync(G.theta_out + 8 * G.n_out, ss.theta, sizeof(float) * 8 * k, cudaMemcpyDefault,
-                                        s),
-                        "cudaMemcpyAsync(pooled theta)");
-                SMC_TRY(cudaMemcpyAsync(G.dist_out + G.n_out, ss.dist, sizeof(double) * k, cudaMemcpyDefault, s),
-                        "cudaMemcpyAsync(pooled dist)");
+            T.acc_theta = th_v[g];
+            T.acc_dist = di_v[g];
+            T.acc_idx = ix_v[g];
+            // weights prior / q_mix (1 for prior draws); a flow round's
+            // defensive prior draws are its last n_defensive indices
+            T.logq = use_flow[g] ? d_logq + (size_t)g * N : nullptr;
+            T.tail_first = use_flow[g] ? first + N - Rr[g].n_defensive : UINT64_MAX;
+            T.pool_k = k_v[g] = pool ? std::min(T.m, G.capacity - G.n_out) : 0;
+            if (T.pool_k) {
+                T.pool = G.weight_out + G.n_out;
+                T.pool_theta = G.theta_out + 8 * G.n_out;
+                T.pool_dist = G.dist_out + G.n_out;
             }
             // before the final eps the flow trains on this round's weighted
             // accepts, if the weights show it worth it (decided below)
-            if (!pool && r + 1 < cfg->rounds)
-                SMC_ST(shuffled_training_set(ss.theta, d_wround, m, m, cfg->seed + 131 * (uint64_t)r + (uint64_t)g,
-                                             d_train + (size_t)g * 8 * cap, d_w + (size_t)g * cap, s));
+            if (round_sets) {
+                T.train_theta = d_train + (size_t)g * 8 * cap;
+                T.train_w = d_w + (size_t)g * cap;
+                perm_params(T.m, cfg->seed + 131 * (uint64_t)r + (uint64_t)g, &T.perm_a, &T.perm_b);
+            }
+            max_m = std::max(max_m, T.m);
+            max_k = std::max(max_k, T.pool_k);
+        }
+        if (max_m > 0) {
+            const unsigned Ru = (unsigned)R, mb = (unsigned)((max_m + 255) / 256);
+            SMC_TRY(cudaMemcpyAsync(d_rr, rr.data(), sizeof(RegionRound) * R, cudaMemcpyHostToDevice, s),
+                    "cudaMemcpyAsync(round table)");
+            // the accepted samples in index order, the same in every run
+            SMC_TRY(cudaMemsetAsync(rs.pos, 0xFF, sizeof(uint32_t) * N * R, s), "cudaMemsetAsync(sort positions)");
+            scatter_slots_regions<<<dim3(mb, Ru), 256, 0, s>>>(d_rr, first, rs);
+            count_slots_regions<<<dim3(rs.nb, Ru), 256, 0, s>>>(d_rr, rs);
+            scan_counts_regions<<<Ru, 256, 0, s>>>(d_rr, rs);
+            gather_sorted_regions<<<dim3(rs.nb, Ru), 256, 0, s>>>(d_rr, rs);
+            SMC_TRY(cudaGetLastError(), "sort launch");
+            SMC_TRY(cudaMemsetAsync(rs.ws, 0, sizeof(WeightScratch) * R, s), "cudaMemsetAsync(weight scratch)");
+            logw_regions<<<dim3(mb, Ru), 256, 0, s>>>(d_rr, first, (float)log_prior, rs);
+            weight_regions<<<dim3(mb, Ru), 256, 0, s>>>(d_rr, cfg->train_weight_power, rs);
+            weight_sums_regions<<<Ru, 256, 0, s>>>(d_rr, rs);
+            if (max_k > 0 || round_sets)
+                pool_and_train_regions<<<dim3((unsigned)((std::max(max_k, round_sets ? max_m : 0) + 255) / 256), Ru),
+                                         256, 0, s>>>(d_rr, rs);
+            SMC_TRY(cudaGetLastError(), "weight launch");
         }
         std::vector<WeightScratch> hws((size_t)R);
-        SMC_TRY(cudaMemcpyAsync(hws.data(), d_ws, sizeof(WeightScratch) * R, cudaMemcpyDeviceToHost, s),
-                "cudaMemcpyAsync(weight sums)");
+        if (max_m > 0)
+            SMC_TRY(cudaMemcpyAsync(hws.data(), rs.ws, sizeof(WeightScratch) * R, cudaMemcpyDeviceToHost, s),
+                    "cudaMemcpyAsync(weight sums)");
         SMC_TRY(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+        std::vector<RegionPool> rp((size_t)R);
+        uint64_t max_scale = 0, max_set = 0;
         for (int32_t g = 0; g < R; ++g) {
+            rp[g] = RegionPool{};
             const uint64_t n_acc = n_acc_v[g], m = std::min(n_acc, cap);
             if (m == 0) continue;
             abc_smc_region& G = regions[g];
@@ -804,8 +1071,10 @@ extern "C" abc_status abc_smc_run_regions(const abc_prior_box* prior, abc_smc_re
             if (pool) {
                 G.n_pooled += n_acc;
                 if (k > 0) {
-                    scale_kernel<<<(unsigned)((k + 255) / 256), 256, 0, s>>>(G.weight_out + G.n_out, k, sw / sw2);
-                    SMC_TRY(cudaGetLastError(), "scale launch");
+                    rp[g].w = G.weight_out + G.n_out;
+                    rp[g].k = k;
+                    rp[g].f = sw / sw2;
+                    max_scale = std::max(max_scale, k);
                     G.n_out += k;
                 }
             }
@@ -820,8 +1089,15 @@ extern "C" abc_status abc_smc_run_regions(const abc_prior_box* prior, abc_smc_re
                 uint64_t tn = 0;
                 if (pool && G.n_out >= 64) {
                     tn = std::min(G.n_out, cap);
-                    SMC_ST(shuffled_training_set(G.theta_out, G.weight_out, G.n_out, tn,
-                                                 cfg->seed + 131 * (uint64_t)r + (uint64_t)g, tt, tw, s));
+                    RegionPool& P = rp[g];
+                    P.theta = G.theta_out;
+                    P.pw = G.weight_out;
+                    P.m = G.n_out;
+                    P.n = tn;
+                    perm_params(G.n_out, cfg->seed + 131 * (uint64_t)r + (uint64_t)g, &P.a, &P.b);
+                    P.train_theta = tt;
+                    P.train_w = tw;
+                    max_set = std::max(max_set, tn);
                 } else if (!pool && good) {
                     tn = m;   // built above
                 }
@@ -834,6 +1110,16 @@ extern "C" abc_status abc_smc_run_regions(const abc_prior_box* prior, abc_smc_re
                 }
             }
             next_flow[g] = good && (trainable[g] || use_flow[g]);
+        }
+        if (max_scale > 0 || max_set > 0) {
+            SMC_TRY(cudaMemcpyAsync(d_rp, rp.data(), sizeof(RegionPool) * R, cudaMemcpyHostToDevice, s),
+                    "cudaMemcpyAsync(pool table)");
+            // the scaled weights first: a training set from the pool reads them
+            if (max_scale > 0)
+                scale_pools_regions<<<dim3((unsigned)((max_scale + 255) / 256), (unsigned)R), 256, 0, s>>>(d_rp);
+            if (max_set > 0)
+                train_from_pools_regions<<<dim3((unsigned)((max_set + 255) / 256), (unsigned)R), 256, 0, s>>>(d_rp);
+            SMC_TRY(cudaGetLastError(), "pool launch");
         }
         if (any_train) {
             const int32_t steps = trained_once ? scfg->train_steps_warm : cfg->train_steps;
