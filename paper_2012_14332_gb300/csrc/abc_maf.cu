@@ -1440,6 +1440,50 @@ __device__ __forceinline__ void adam_bias(int t, float b1, float b2, float& c1, 
 
 __global__ void tick_kernel(int* step) { *step += 1; }
 
+// Early stopping of a training run, one check on the device (block r = flow
+// r): the flow's validation loss sum w nll / sum w from the loss sums; a
+// lower one than the best so far becomes the best, with a copy of the flow's
+// parameters; after `patience` checks in a row without one, the flow stops
+// training (its training slot gets no rows, so later steps leave it as it
+// is). flags[0] counts the flows still training after the check, flags[1]
+// takes the error word (zeroed by the caller).
+struct StopState {
+    float best;
+    int bad;
+};
+
+__global__ void __launch_bounds__(256) early_stop_kernel(const float* __restrict__ sums,
+                                                         const TrainSlot* __restrict__ val, StopState* st,
+                                                         TrainSlot* tr, const float* __restrict__ params,
+                                                         float* __restrict__ best, int64_t n_params, int patience,
+                                                         const int* __restrict__ err, int* flags)
+{
+    __shared__ int keep;
+    const int r = blockIdx.x;
+    if (threadIdx.x == 0) {
+        keep = 0;
+        const float w = sums[2 * r + 1];
+        if (val[r].n > 0 && !(w <= 0.f)) {
+            const float vl = __fdiv_rn(sums[2 * r], w);
+            StopState s = st[r];
+            if (vl < s.best) {
+                s.best = vl;
+                s.bad = 0;
+                keep = 1;
+            } else if (++s.bad >= patience && tr[r].n > 0) {
+                tr[r].n = 0;
+            }
+            st[r] = s;
+        }
+        if (tr[r].n > 0) atomicAdd(&flags[0], 1);
+        if (r == 0) flags[1] = *err;
+    }
+    __syncthreads();
+    if (keep)
+        for (int64_t i = threadIdx.x; i < n_params; i += blockDim.x)
+            best[(size_t)r * n_params + i] = params[(size_t)r * n_params + i];
+}
+
 // Master parameter r of one block (W1 [H][8], b1 [H], W2 [16][H], b2 [16]),
 // value val, written to every place the published layout holds it: the
 // forward and backward operands and the sampler's copy, as BF16 halves of
@@ -1628,8 +1672,9 @@ struct abc_maf_s {
     int* d_step = nullptr;     // [0] the step of abc_maf_adam_step, [1] a training run's ticket counter
     maf::TrainSlot* d_slots = nullptr;   // [R] training data of each flow
     maf::TrainSlot* d_slots_val = nullptr;   // [R] validation data of each flow (early stopping)
-    float* h_io = nullptr;   // pinned host: the 2 R loss sums, then the error word
+    float* h_io = nullptr;   // pinned host: 2 R floats, then the early-stopping flags [2][2] (int)
     float* d_best = nullptr;   // [R][n_params] best parameters under validation (allocated on first use)
+    void* d_stop = nullptr;    // early stopping: [R] StopState, then two pairs of flags (allocated on first use)
     cudaGraphExec_t graph = nullptr;        // one training step, captured
     cudaGraphExec_t graph_multi = nullptr;  // kGraphSteps training steps, captured together
     // what the captured training step was built for
@@ -2305,53 +2350,62 @@ abc_status abc_maf_train_flows(abc_maf f, const float* const* theta, const float
         if (!f->d_best) MAF_TRY(cudaMalloc(&f->d_best, npb * R), "cudaMalloc(best parameters)");
         uint64_t max_va = 0;
         for (int r = 0; r < R; ++r) max_va = n_va[r] > max_va ? n_va[r] : max_va;
-        std::vector<float> best((size_t)R, INFINITY);
-        std::vector<int> bad((size_t)R, 0);
-        // the validation sets have their own slot table, uploaded once; each
-        // check reads the loss sums and the error word back in one synchronisation
+        // the validation sets have their own slot table, uploaded once. Each
+        // check runs on the device (early_stop_kernel: best loss, the best
+        // parameters' copy, a stopped flow's training slot emptied), and the
+        // host reads its flags (flows still training, the error word) one
+        // check late: the GPU meanwhile runs the next steps and check, and at
+        // most one replay of steps runs after every flow has stopped (steps
+        // leave a flow without rows as it is).
         MAF_TRY(upload_slots(f, th_va.data(), w_va.data(), n_va.data(), s, f->d_slots_val), "cudaMemcpyAsync(slots)");
-        float* sums = f->h_io;
-        int* err_h = reinterpret_cast<int*>(f->h_io + 2 * (size_t)R);
-        auto val_losses = [&]() -> abc_status {
+        const size_t stop_bytes = sizeof(maf::StopState) * R;
+        if (!f->d_stop) MAF_TRY(cudaMalloc(&f->d_stop, stop_bytes + 4 * sizeof(int)), "cudaMalloc(early stopping)");
+        maf::StopState* d_st = static_cast<maf::StopState*>(f->d_stop);
+        int* d_flags = reinterpret_cast<int*>(static_cast<char*>(f->d_stop) + stop_bytes);   // [2][2]
+        {
+            const std::vector<maf::StopState> init((size_t)R, maf::StopState{INFINITY, 0});
+            MAF_TRY(cudaMemcpyAsync(d_st, init.data(), stop_bytes, cudaMemcpyHostToDevice, s),
+                    "cudaMemcpyAsync(early stopping)");
+        }
+        int* flags_h = reinterpret_cast<int*>(f->h_io + 2 * (size_t)R);   // [2][2] in pinned memory
+        struct Events {
+            cudaEvent_t e[2] = {nullptr, nullptr};
+            ~Events()
+            {
+                for (cudaEvent_t x : e)
+                    if (x) cudaEventDestroy(x);
+            }
+        } ev;
+        for (cudaEvent_t& x : ev.e) MAF_TRY(cudaEventCreateWithFlags(&x, cudaEventDisableTiming), "cudaEventCreate");
+        int checks = 0;
+        auto check = [&]() -> abc_status {
+            const int slot = checks & 1;
             MAF_TRY(full_gradient(f, max_va, s, f->d_slots_val, true), "validation loss");
-            MAF_TRY(cudaMemcpyAsync(sums, f->d_sums, sizeof(float) * 2 * (size_t)R, cudaMemcpyDeviceToHost, s),
-                    "cudaMemcpyAsync(sums)");
-            MAF_TRY(cudaMemcpyAsync(err_h, f->d_err, sizeof(int), cudaMemcpyDeviceToHost, s),
-                    "cudaMemcpyAsync(error word)");
-            MAF_TRY(cudaStreamSynchronize(s), "cudaStreamSynchronize");
-            if (*err_h) {
-                MAF_TRY(cudaMemset(f->d_err, 0, sizeof(int)), "cudaMemset(error word)");
-                return plan_fail(ABC_ERR_TIMEOUT,
-                                 "a flow gradient kernel's wait for its tensor-core products ran out of time");
-            }
-            bool stopped = false;
-            for (int r = 0; r < R; ++r) {
-                if (n_va[r] == 0 || sums[2 * r + 1] <= 0.f) continue;
-                const float vl = sums[2 * r] / sums[2 * r + 1];
-                if (vl < best[r]) {
-                    best[r] = vl;
-                    bad[r] = 0;
-                    MAF_TRY(cudaMemcpyAsync(f->d_best + (size_t)r * f->n_params, f->d_params + (size_t)r * f->n_params,
-                                            npb, cudaMemcpyDeviceToDevice, s),
-                            "cudaMemcpyAsync(best parameters)");
-                } else if (++bad[r] >= kPatience && n_tr[r] > 0) {
-                    n_tr[r] = 0;   // this flow stops training
-                    stopped = true;
-                }
-            }
-            if (stopped)
-                MAF_TRY(upload_slots(f, th_tr.data(), w_tr.data(), n_tr.data(), s), "cudaMemcpyAsync(slots)");
+            MAF_TRY(cudaMemsetAsync(d_flags + 2 * slot, 0, 2 * sizeof(int), s), "cudaMemsetAsync(flags)");
+            maf::early_stop_kernel<<<R, 256, 0, s>>>(f->d_sums, f->d_slots_val, d_st, f->d_slots, f->d_params,
+                                                     f->d_best, f->n_params, kPatience, f->d_err, d_flags + 2 * slot);
+            MAF_TRY(cudaGetLastError(), "early stopping launch");
+            MAF_TRY(cudaMemcpyAsync(flags_h + 2 * slot, d_flags + 2 * slot, 2 * sizeof(int), cudaMemcpyDeviceToHost, s),
+                    "cudaMemcpyAsync(flags)");
+            MAF_TRY(cudaEventRecord(ev.e[slot], s), "cudaEventRecord");
+            ++checks;
             return ABC_OK;
         };
-        if ((st = val_losses()) != ABC_OK) return st;
-        for (int32_t done = 0; done < n_steps;) {
-            bool active = false;
-            for (int r = 0; r < R; ++r) active = active || n_tr[r] > 0;
-            if (!active) break;
+        bool any = false;
+        for (int r = 0; r < R; ++r) any = any || n_tr[r] > 0;
+        if ((st = check()) != ABC_OK) return st;
+        for (int32_t done = 0; any && done < n_steps;) {
+            if (checks >= 2) {
+                // the check before the last one enqueued
+                const int slot = checks & 1;
+                MAF_TRY(cudaEventSynchronize(ev.e[slot]), "cudaEventSynchronize");
+                if (flags_h[2 * slot + 1]) break;   // a wait ran out: reported below
+                if (flags_h[2 * slot] == 0) break;  // every flow has stopped
+            }
             const int32_t k = n_steps - done < kCheck ? n_steps - done : kCheck;
             MAF_TRY(run_steps(f, k, s), "cudaGraphLaunch");
             done += k;
-            if ((st = val_losses()) != ABC_OK) return st;
+            if ((st = check()) != ABC_OK) return st;
         }
         // the kept parameters: each validated flow's best
         for (int r = 0; r < R; ++r)
@@ -2360,13 +2414,15 @@ abc_status abc_maf_train_flows(abc_maf f, const float* const* theta, const float
                                         cudaMemcpyDeviceToDevice, s),
                         "cudaMemcpyAsync(restore parameters)");
         MAF_TRY(publish(f, s), "publish");
+        std::vector<maf::StopState> fin((size_t)R);
+        MAF_TRY(cudaMemcpyAsync(fin.data(), d_st, stop_bytes, cudaMemcpyDeviceToHost, s), "cudaMemcpyAsync(early stopping)");
         MAF_TRY(cudaStreamSynchronize(s), "cudaStreamSynchronize");
         {
             const abc_status es = take_err(f);
             if (es != ABC_OK) return es;
         }
         if (loss_out)
-            for (int r = 0; r < R; ++r) loss_out[r] = n_va[r] > 0 && best[r] < INFINITY ? best[r] : 0.f;
+            for (int r = 0; r < R; ++r) loss_out[r] = n_va[r] > 0 && fin[r].best < INFINITY ? fin[r].best : 0.f;
         return plan_ok();
     }
     if (n_steps > 0) {
@@ -2431,6 +2487,7 @@ abc_status abc_maf_destroy(abc_maf f)
     if (f->h_io) cudaFreeHost(f->h_io);
     cudaFree(f->d_err);
     cudaFree(f->d_best);
+    cudaFree(f->d_stop);
     delete f;
     // leaves the thread's last error as it was: drivers destroy their flows
     // on the way out of a failed call
