@@ -43,7 +43,6 @@ ModelParams plan_make_params(const abc_prior_box* prior, int32_t T, int64_t N_po
 
 namespace maf {
 
-constexpr int kD = 8;
 constexpr int kHMax = 256;
 constexpr int kKMax = 4;
 constexpr float kAlphaMax = 6.0f;
